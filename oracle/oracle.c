@@ -1,0 +1,431 @@
+/*
+ * oracle.c -- plain, slow, FP64 reference of the delayed geometric-network
+ * simulation of Buibas & Silva, "A framework for simulating and estimating the
+ * state and functional topology of complex dynamic geometric networks"
+ * (arXiv:0908.3934).
+ *
+ * TEST INFRASTRUCTURE.  Only the test-suite, the smoke check and the timed
+ * CPU baseline of the benchmark may load this library.  It shares no code,
+ * header, table or helper with the CUDA library: the two sides meet only in
+ * the seeded input generators.
+ *
+ * What it computes, in the paper's order:
+ *   - geodesic delays tau_ij = |x_i - x_j| / s                (Eq. delaydist, Sec. 3.2.1;
+ *     quantised to whole steps of dt                           Eq. gendelay, Sec. 2)
+ *   - the delayed, weighted input of node j,
+ *       S_j(t) = sum_{i -> j} w_ij * v_i(t - tau_ij)           (Eq. Yjset, Sec. 2)
+ *   - the FitzHugh-Nagumo transition, forward Euler            (Eq. difform + the Euler form, Sec. 3.1;
+ *       V' = V + dt (aV - bV^3 - cW + S + U)                    FHN pair and Eq. fnstate, Sec. 3.1)
+ *       W' = W + dt  e (V + f - gW)
+ *   - the control input U_j(t)                                 (u_j in Eq. Htrans, Sec. 2)
+ *   - a linear low-pass readout of V and a noisy observation   (calcium model and fluorescence
+ *       I = n c + b + N(0, gamma^2)                             readout, Sec. 3.3; Eq. obsfun, Sec. 2)
+ *
+ * Readings where the paper is silent (each is listed in the design notes):
+ *   - D = max(1, llround(tau/dt)): half away from zero; a zero delay would need a
+ *     same-step value inside an explicit step, so it is clamped to one step.
+ *   - Coupling REST: S uses the voltage relative to the isolated rest point,
+ *     v~ = V - V*, so an unstimulated network stays exactly at rest.  Coupling RAW
+ *     uses V itself (V* for times before t = 0).
+ *   - The state is held relative to the rest point (v~ = V - V*, w~ = W - W*);
+ *     the FHN polynomial is expanded about (V*, W*) with the binomial theorem,
+ *     the constant part being zero by definition of the rest point.
+ *   - Jacobi step: every update reads only step-n values (Sec. 2, the component list
+ *     under Eq. Hj advances each variable from time t).
+ *   - Readout c: forward Euler of dc/dt = (v - c)/tau (the calcium model's Euler form
+ *     with the voltage in place of the spike train), sampled every `sample_every` steps;
+ *     y = gain (V* + c~) + offset + sigma xi.
+ *   - Events: upward crossing of V through theta (V(n) < theta <= V(n+1)).
+ *   - Arrival: first step at which v~ becomes non-zero.
+ *
+ * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11), written from the
+ * published definition; Box-Muller (1958) for the Gaussian.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared oracle.c -o liboracle.so -lm
+ * (no FMA contraction: the delay quantisation must round exactly as written).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_EINVAL -1
+#define ORC_ENOMEM -2
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10 (Salmon et al., SC'11): 10 rounds of the 4x32 S-box
+ * with multipliers 0xD2511F53 / 0xCD9E8D57 and Weyl key increments
+ * 0x9E3779B9 / 0xBB67AE85, the key being bumped before every round but the first. */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)x0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y1 = lo1;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        uint32_t y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* Counter layout shared by definition (not by code) with the CUDA side:
+ *   ctr = {node, index_lo, index_hi, stream}, key = {seed_lo, seed_hi}. */
+static void draw(uint64_t seed, uint32_t node, int64_t index, uint32_t stream, uint32_t out[4])
+{
+    uint32_t ctr[4] = {node, (uint32_t)((uint64_t)index & 0xffffffffu),
+                       (uint32_t)((uint64_t)index >> 32), stream};
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    orc_philox4x32_10(ctr, key, out);
+}
+
+#define STREAM_BACKGROUND 1u
+#define STREAM_OBSERVATION 2u
+
+/* Standard normal from one Philox draw: Box-Muller on the top 23 bits of two words,
+ * u = (k + 1/2) 2^-23, so u lies strictly inside (0, 1). */
+double orc_gauss(uint64_t seed, uint32_t node, int64_t sample)
+{
+    uint32_t r[4];
+    draw(seed, node, sample, STREAM_OBSERVATION, r);
+    double u1 = ((double)(r[0] >> 9) + 0.5) * (1.0 / 8388608.0);
+    double u2 = ((double)(r[1] >> 9) + 0.5) * (1.0 / 8388608.0);
+    return sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+}
+
+/* Per-step onset probability p = rate * dt, as a 32-bit threshold:
+ * an onset happens at step n iff the first Philox word is below it. */
+uint32_t orc_bg_threshold(double rate_hz, double dt_ms)
+{
+    double p = (rate_hz * dt_ms) / 1000.0;
+    if (!(p > 0.0)) return 0u;
+    double t = floor(ldexp(p, 32));
+    if (t >= 4294967295.0) return 4294967295u;
+    return (uint32_t)t;
+}
+
+int orc_bg_onset(uint64_t seed, uint32_t node, int64_t step, uint32_t threshold)
+{
+    uint32_t r[4];
+    draw(seed, node, step, STREAM_BACKGROUND, r);
+    return r[0] < threshold;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Rest point of the isolated FHN node (S = U = 0): the W-nullcline gives
+ * W = (V + f)/g, and V solves a V - b V^3 - c (V + f)/g + I = 0.  For
+ * a < c/g the left side is strictly decreasing, so the root is unique;
+ * it is bracketed, bisected, then polished by Newton. */
+int orc_rest_point(double a, double b, double c, double f, double g, double i_ext,
+                   double *v_rest, double *w_rest)
+{
+    if (!(g > 0.0) || !(b > 0.0) || !(a < c / g)) return ORC_EINVAL;
+    double lo = -1.0, hi = 1.0;
+#define RP_F(v) (a * (v) - b * (v) * (v) * (v) - c * ((v) + f) / g + i_ext)
+    while (RP_F(lo) < 0.0) lo *= 2.0;   /* F(-inf) = +inf */
+    while (RP_F(hi) > 0.0) hi *= 2.0;   /* F(+inf) = -inf */
+    for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (RP_F(mid) > 0.0) lo = mid; else hi = mid;
+    }
+    double v = 0.5 * (lo + hi);
+    for (int it = 0; it < 3; ++it) {
+        double fp = a - 3.0 * b * v * v - c / g;
+        v = v - RP_F(v) / fp;
+    }
+#undef RP_F
+    *v_rest = v;
+    *w_rest = (v + f) / g;
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Delay quantisation: tau = |x_src - x_dst| / s (Eq. delaydist, Sec. 3.2.1),
+ * D = max(1, llround(tau / dt)) with s*dt formed first.  Distances in mm,
+ * speeds in m/s (= mm/ms), dt in ms.  `speed` may be NULL, then `speed_scalar`
+ * applies to every edge.  clamped[e] = 1 where the rounded value was < 1. */
+int orc_delays(int32_t n_nodes, int32_t dim, const double *pos, int64_t n_edges,
+               const int32_t *src, const int32_t *dst, const double *speed,
+               double speed_scalar, double dt_ms, int32_t *delay, uint8_t *clamped)
+{
+    if (dim < 1 || dim > 3 || !(dt_ms > 0.0)) return ORC_EINVAL;
+    for (int64_t e = 0; e < n_edges; ++e) {
+        int32_t i = src[e], j = dst[e];
+        if (i < 0 || i >= n_nodes || j < 0 || j >= n_nodes) return ORC_EINVAL;
+        double sum = 0.0;
+        for (int k = 0; k < dim; ++k) {
+            double diff = pos[(int64_t)i * dim + k] - pos[(int64_t)j * dim + k];
+            sum = sum + diff * diff;
+        }
+        double dist = sqrt(sum);
+        double s = speed ? speed[e] : speed_scalar;
+        if (!(s > 0.0)) return ORC_EINVAL;
+        double q = dist / (s * dt_ms);
+        long long d = llround(q);
+        uint8_t cl = 0;
+        if (d < 1) { d = 1; cl = 1; }
+        if (d > 2147483647LL) return ORC_EINVAL;
+        delay[e] = (int32_t)d;
+        if (clamped) clamped[e] = cl;
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int32_t n_nodes;
+    int64_t n_edges;
+    const int32_t *src;      /* [E] source i of edge i -> j */
+    const int32_t *dst;      /* [E] target j */
+    const double *weight;    /* [E] omega_ij */
+    const int32_t *delay;    /* [E] whole steps, >= 1 */
+    double dt_ms;
+    /* FHN in the paper's notation (Sec. 3.1): dV = aV - bV^3 - cW + S + U + I_ext,
+     * dW = e (V + f - gW). */
+    double a, b, c, e, f, g, i_ext;
+    int32_t coupling;        /* 0 = REST (v - V*), 1 = RAW (V) */
+    double theta;            /* event threshold on V */
+    /* readout */
+    double tau_ms;
+    int32_t sample_every;
+    double gain, offset, sigma;
+    uint64_t obs_seed;
+    /* explicit pulses: amp on node during steps [on, off) */
+    int32_t n_pulses;
+    const int32_t *p_node;
+    const int64_t *p_on;
+    const int64_t *p_off;
+    const double *p_amp;
+    /* background: Bernoulli onsets per step, each starting a pulse of `bg_width`
+     * steps of amplitude bg_amp; a new onset restarts the count (no stacking). */
+    uint32_t bg_threshold;   /* 0 = off */
+    double bg_amp;
+    int32_t bg_width;
+    uint64_t bg_seed;
+} orc_net;
+
+typedef struct {
+    double *v, *w, *c;        /* [N] final state relative to rest (required) */
+    double *y;                /* [n_samples * N] observations, or NULL */
+    double *y_clean;          /* [n_samples * N] observations without noise, or NULL */
+    int32_t *first_arrival;   /* [N] first step n+1 with v~ != 0, -1 = none (or NULL) */
+    double *first_value;      /* [N] v~ at that step (or NULL) */
+    int32_t *ev_node;         /* [ev_cap] */
+    int64_t *ev_step;         /* [ev_cap] */
+    int64_t ev_cap;
+    int64_t ev_count;         /* out: total events (may exceed ev_cap) */
+    int32_t snap_every;       /* > 0: store the state after every snap_every steps */
+    double *snap_v, *snap_w, *snap_c; /* [n_steps/snap_every * N] */
+} orc_out;
+
+/* One Euler step of one node (the FHN transition about the rest point).
+ * Expanding a(V*+v) - b(V*+v)^3 - c(W*+w) + I and dropping the rest-point
+ * identity aV* - bV*^3 - cW* + I = 0 leaves
+ *   a v - b (3 V*^2 v + 3 V* v^2 + v^3) - c w;
+ * likewise e((V*+v) + f - g(W*+w)) = e (v - g w) since V* + f - g W* = 0. */
+static void node_step(const orc_net *net, double v_rest, double v, double w, double c,
+                      double S, double U, double *v1, double *w1, double *c1)
+{
+    double dt = net->dt_ms;
+    double dv = net->a * v
+              - net->b * (3.0 * v_rest * v_rest * v + 3.0 * v_rest * v * v + v * v * v)
+              - net->c * w + S + U;
+    double dw = net->e * (v - net->g * w);
+    double vn = v + dt * dv;
+    double wn = w + dt * dw;
+    double cn = c + (dt / net->tau_ms) * (vn - c);
+    *v1 = vn; *w1 = wn; *c1 = cn;
+}
+
+static double stimulus(const orc_net *net, int32_t j, int64_t n, int32_t *bg_count)
+{
+    double U = 0.0;
+    for (int32_t p = 0; p < net->n_pulses; ++p)
+        if (net->p_node[p] == j && net->p_on[p] <= n && n < net->p_off[p])
+            U += net->p_amp[p];
+    if (net->bg_threshold) {
+        int32_t cnt = bg_count[j];
+        if (orc_bg_onset(net->bg_seed, (uint32_t)j, n, net->bg_threshold)) cnt = net->bg_width;
+        if (cnt > 0) {
+            U += net->bg_amp;
+            cnt -= 1;
+        }
+        bg_count[j] = cnt;
+    }
+    return U;
+}
+
+/* history accessor: full (dense) or circular of depth H */
+typedef struct {
+    double *buf;
+    int64_t depth;   /* number of slots kept */
+    int dense;       /* 1: slot = time index, buf holds every step */
+    int32_t n;
+} history;
+
+static double hist_get(const history *h, int64_t t, int32_t i)
+{
+    if (t < 0) return 0.0;                      /* before t = 0 every node rests */
+    int64_t slot = h->dense ? t : (t % h->depth);
+    return h->buf[slot * h->n + i];
+}
+
+static void hist_put(history *h, int64_t t, int32_t i, double v)
+{
+    int64_t slot = h->dense ? t : (t % h->depth);
+    h->buf[slot * h->n + i] = v;
+}
+
+/* Optional starting state at step n0 > 0 (restart): the state relative to rest,
+ * the background counters and the history hist[k][j] = v~_j(n0 - k), k = 0..depth-1. */
+typedef struct {
+    int64_t n0;
+    const double *v, *w, *c;
+    const int32_t *bg_count;
+    const double *hist;
+    int32_t hist_depth;
+} orc_init;
+
+static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense,
+                    const orc_init *init)
+{
+    int32_t N = net->n_nodes;
+    int64_t E = net->n_edges;
+    if (N <= 0 || E < 0 || n_steps < 0 || !(net->dt_ms > 0.0) || !(net->tau_ms > 0.0))
+        return ORC_EINVAL;
+    double v_rest, w_rest;
+    if (orc_rest_point(net->a, net->b, net->c, net->f, net->g, net->i_ext, &v_rest, &w_rest))
+        return ORC_EINVAL;
+    int32_t dmax = 1;
+    for (int64_t e = 0; e < E; ++e) {
+        if (net->delay[e] < 1 || net->src[e] < 0 || net->src[e] >= N || net->dst[e] < 0 ||
+            net->dst[e] >= N || net->src[e] == net->dst[e])
+            return ORC_EINVAL;
+        if (net->delay[e] > dmax) dmax = net->delay[e];
+    }
+    int64_t n0 = init ? init->n0 : 0;
+    if (n0 < 0 || (init && dense)) return ORC_EINVAL;
+    if (init && n0 > 0 && init->hist_depth < dmax + 1 && init->hist_depth < n0 + 1) return ORC_EINVAL;
+    history h;
+    h.n = N;
+    h.dense = dense;
+    h.depth = dense ? (n_steps + 1) : ((int64_t)dmax + 1);
+    h.buf = (double *)calloc((size_t)(h.depth * N), sizeof(double));
+    double *v = (double *)calloc((size_t)N, sizeof(double));
+    double *w = (double *)calloc((size_t)N, sizeof(double));
+    double *c = (double *)calloc((size_t)N, sizeof(double));
+    double *S = (double *)calloc((size_t)N, sizeof(double));
+    int32_t *bgc = (int32_t *)calloc((size_t)N, sizeof(int32_t));
+    if (!h.buf || !v || !w || !c || !S || !bgc) {
+        free(h.buf); free(v); free(w); free(c); free(S); free(bgc);
+        return ORC_ENOMEM;
+    }
+    if (init) {
+        for (int32_t j = 0; j < N; ++j) {
+            v[j] = init->v[j];
+            w[j] = init->w[j];
+            c[j] = init->c[j];
+            bgc[j] = init->bg_count ? init->bg_count[j] : 0;
+        }
+        for (int64_t k = 1; k < h.depth && k < init->hist_depth; ++k)
+            if (n0 - k >= 0)
+                for (int32_t j = 0; j < N; ++j) hist_put(&h, n0 - k, j, init->hist[k * N + j]);
+    }
+    if (out->first_arrival)
+        for (int32_t j = 0; j < N; ++j) out->first_arrival[j] = -1;
+    if (out->first_value)
+        for (int32_t j = 0; j < N; ++j) out->first_value[j] = 0.0;
+    out->ev_count = 0;
+    double v_theta = net->theta;
+    int64_t snap_idx = 0;
+
+    for (int64_t n = n0; n < n0 + n_steps; ++n) {
+        /* record v~(n) before anything reads the history of this step */
+        for (int32_t j = 0; j < N; ++j) hist_put(&h, n, j, v[j]);
+        /* S_j(n) = sum over edges i -> j of w_ij * v_i(n - D_ij) */
+        for (int32_t j = 0; j < N; ++j) S[j] = 0.0;
+        for (int64_t e = 0; e < E; ++e) {
+            double past = hist_get(&h, n - net->delay[e], net->src[e]);
+            if (net->coupling == 1) past = v_rest + past;
+            S[net->dst[e]] += net->weight[e] * past;
+        }
+        int sample = ((n + 1) % net->sample_every) == 0;
+        int64_t k = (n + 1) / net->sample_every - 1;            /* absolute sample number */
+        int64_t k_out = (n + 1) / net->sample_every - n0 / net->sample_every - 1;  /* row of y */
+        for (int32_t j = 0; j < N; ++j) {
+            double U = stimulus(net, j, n, bgc);
+            double v1, w1, c1;
+            node_step(net, v_rest, v[j], w[j], c[j], S[j], U, &v1, &w1, &c1);
+            /* event: V crosses theta upward between n and n+1 */
+            if (v_rest + v[j] < v_theta && v_rest + v1 >= v_theta) {
+                if (out->ev_count < out->ev_cap) {
+                    out->ev_node[out->ev_count] = j;
+                    out->ev_step[out->ev_count] = n + 1;
+                }
+                out->ev_count++;
+            }
+            if (out->first_arrival && out->first_arrival[j] < 0 && v1 != 0.0) {
+                out->first_arrival[j] = (int32_t)(n + 1);
+                if (out->first_value) out->first_value[j] = v1;
+            }
+            if (sample) {
+                double clean = net->gain * (v_rest + c1) + net->offset;
+                if (out->y_clean) out->y_clean[k_out * N + j] = clean;
+                if (out->y) out->y[k_out * N + j] = clean + net->sigma * orc_gauss(net->obs_seed, (uint32_t)j, k);
+            }
+            v[j] = v1; w[j] = w1; c[j] = c1;
+        }
+        if (out->snap_every > 0 && ((n + 1 - n0) % out->snap_every) == 0) {
+            memcpy(out->snap_v + snap_idx * N, v, sizeof(double) * (size_t)N);
+            memcpy(out->snap_w + snap_idx * N, w, sizeof(double) * (size_t)N);
+            memcpy(out->snap_c + snap_idx * N, c, sizeof(double) * (size_t)N);
+            snap_idx++;
+        }
+    }
+    memcpy(out->v, v, sizeof(double) * (size_t)N);
+    memcpy(out->w, w, sizeof(double) * (size_t)N);
+    memcpy(out->c, c, sizeof(double) * (size_t)N);
+    free(h.buf); free(v); free(w); free(c); free(S); free(bgc);
+    return ORC_OK;
+}
+
+/* Circular history of depth D_max + 1 (the working oracle). */
+int orc_simulate(const orc_net *net, int64_t n_steps, orc_out *out)
+{
+    return simulate(net, n_steps, out, 0, NULL);
+}
+
+/* The same, continuing from a given state at step n0 (used to check a long run
+ * window by window from the state another implementation reached). */
+int orc_simulate_from(const orc_net *net, const orc_init *init, int64_t n_steps, orc_out *out)
+{
+    return simulate(net, n_steps, out, 0, init);
+}
+
+/* Brute force: the whole history [n_steps + 1][N] kept, v_i(t - tau) read by
+ * its time index directly, exactly as Eq. Yjset is written.  Tiny nets only. */
+int orc_simulate_dense(const orc_net *net, int64_t n_steps, orc_out *out)
+{
+    return simulate(net, n_steps, out, 1, NULL);
+}
+
+/* Whole step of a time in ms: llround(t / dt), half away from zero. */
+int64_t orc_ms_to_step(double t_ms, double dt_ms)
+{
+    return (int64_t)llround(t_ms / dt_ms);
+}
+
+int orc_rest_point_of(const orc_net *net, double *v_rest, double *w_rest)
+{
+    return orc_rest_point(net->a, net->b, net->c, net->f, net->g, net->i_ext, v_rest, w_rest);
+}

@@ -1,0 +1,253 @@
+"""Seeded synthetic inputs: node positions, directed edges, weights, speeds and
+stimulus schedules of geometric networks.
+
+This module is the one place both the CUDA path and the FP64 oracle take their
+inputs from.  It holds none of the method's arithmetic: no delays, no dynamics,
+no readout -- only the random draws that define a network and its controls.
+
+The paper's own test networks (Sec. 3.5, "available for download") are not
+available, so these generators stand in for them.  The recipes:
+
+* ``tiny``      N = 64 uniform in a 1 x 1 mm square; directed i -> j for every
+                ordered pair closer than 0.2 mm, kept with p = 0.5; w ~ U(0.1, 0.5);
+                one speed 0.1 m/s; +1.0 pulse on node 0 over [10, 12) ms.
+* ``large``     N = 100,000 uniform in a 1 mm cube; every ordered pair within the
+                radius that gives a mean in-degree of 100; w = lognormal(-2, 0.5)
+                with 20 % negated; speed U(0.05, 0.5) m/s per edge; 5 Hz
+                background pulses (1.0, 2 ms).
+* ``roofline``  N = 1,000,000 in a 1 mm cube, mean in-degree 50: 2.5 % hub nodes
+                take in-edges from their 1000 nearest nodes, the rest take every
+                node within the radius giving the remaining mean (about 25.6);
+                weight, speed and background as ``large``; ring of 256 steps.
+* ``batch``     many independent 2D nets, N log-uniform in [32, 4096]; pairs within
+                r = sqrt(40 / (pi N)) kept with p = 0.5 (mean kept in-degree about 20
+                away from the border); weight and speed as ``large``; 1-8 random
+                nodes get a 2 ms pulse with onset uniform in [5, 50) ms.
+* ``fig2``      the five-vertex network of Figs. 1-2 with the printed delays and
+                weights (delays are given explicitly, in steps of 0.05 ms).
+
+FHN parameters are given in the paper's notation (Sec. 3.1,
+dV = aV - bV^3 - cW + S + U, dW = e(V + f - gW)); the classic choice
+(0.7, 0.8, 0.08) is a = 1, b = 1/3, c = 1, e = 0.08, f = 0.7, g = 0.8.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+from scipy.spatial import cKDTree
+
+FHN_CLASSIC = dict(a=1.0, b=1.0 / 3.0, c=1.0, e=0.08, f=0.7, g=0.8, i_ext=0.0)
+OBS_DEFAULT = dict(tau_ms=5.0, sample_every=20, gain=1.0, offset=0.0, sigma=0.05, seed=2)
+
+
+@dataclasses.dataclass
+class NetSpec:
+    """One network and its controls, in the caller's node and edge order."""
+    pos: np.ndarray                 # [N, dim] float64, mm
+    src: np.ndarray                 # [E] int32, source i of edge i -> j
+    dst: np.ndarray                 # [E] int32, target j
+    weight: np.ndarray              # [E] float32
+    speed: np.ndarray | None        # [E] float64 m/s (= mm/ms), or None
+    speed_scalar: float = 0.0       # used when speed is None
+    delay: np.ndarray | None = None  # [E] int32 explicit delays in steps (bypasses geometry)
+    dt_ms: float = 0.05
+    fhn: dict = dataclasses.field(default_factory=lambda: dict(FHN_CLASSIC))
+    obs: dict = dataclasses.field(default_factory=lambda: dict(OBS_DEFAULT))
+    coupling: str = "rest"
+    theta: float = 0.0
+    pulses: list = dataclasses.field(default_factory=list)   # (node, t_on_ms, t_off_ms, amp)
+    background: dict | None = None  # dict(rate_hz, amp, dur_ms, seed)
+    ring_depth: int = 0             # 0 = smallest power of two that holds the delays
+    name: str = ""
+
+    @property
+    def n_nodes(self) -> int:
+        return int(self.pos.shape[0])
+
+    @property
+    def n_edges(self) -> int:
+        return int(self.src.shape[0])
+
+    @property
+    def dim(self) -> int:
+        return int(self.pos.shape[1])
+
+
+def _signed_lognormal(rng, n, mu=-2.0, sigma=0.5, neg_frac=0.2):
+    w = rng.lognormal(mu, sigma, n)
+    w[rng.random(n) < neg_frac] *= -1.0
+    return w.astype(np.float32)
+
+
+def _pairs_within(pos, r):
+    """All ordered pairs (i, j), i != j, with |x_i - x_j| < r (both directions)."""
+    tree = cKDTree(pos)
+    p = tree.query_pairs(r, output_type="ndarray")
+    if p.size == 0:
+        return np.zeros(0, np.int32), np.zeros(0, np.int32)
+    # query_pairs uses <= r; drop exact-distance ties so the rule is strict
+    d = np.sqrt(((pos[p[:, 0]] - pos[p[:, 1]]) ** 2).sum(1))
+    p = p[d < r]
+    src = np.concatenate([p[:, 0], p[:, 1]]).astype(np.int32)
+    dst = np.concatenate([p[:, 1], p[:, 0]]).astype(np.int32)
+    return src, dst
+
+
+def _sort_by_dst(src, dst, *extra):
+    """Edges in (dst, src) order: a deterministic caller order."""
+    order = np.lexsort((src, dst))
+    return (src[order], dst[order]) + tuple(x[order] for x in extra)
+
+
+def tiny(seed: int = 1, n: int = 64, radius: float = 0.2, keep: float = 0.5,
+         noise_seed: int = 2) -> NetSpec:
+    rng = np.random.default_rng(seed)
+    pos = rng.random((n, 2))
+    src, dst = _pairs_within(pos, radius)
+    keep_mask = rng.random(src.shape[0]) < keep
+    src, dst = src[keep_mask], dst[keep_mask]
+    src, dst = _sort_by_dst(src, dst)
+    w = rng.uniform(0.1, 0.5, src.shape[0]).astype(np.float32)
+    obs = dict(OBS_DEFAULT, seed=noise_seed)
+    return NetSpec(pos=pos, src=src, dst=dst, weight=w, speed=None, speed_scalar=0.1,
+                   obs=obs, pulses=[(0, 10.0, 12.0, 1.0)], name="tiny")
+
+
+def _radius_for_mean_degree(pos, mean_deg, n_probe=20000, seed=0):
+    """Radius at which the mean number of other nodes within r equals mean_deg
+    (bisection on a random probe set, so border losses are included)."""
+    n, dim = pos.shape
+    tree = cKDTree(pos)
+    rng = np.random.default_rng(seed)
+    probe = pos[rng.choice(n, min(n_probe, n), replace=False)]
+    unit = math.pi if dim == 2 else 4.0 * math.pi / 3.0
+    r0 = (mean_deg / (n * unit)) ** (1.0 / dim)
+    lo, hi = 0.5 * r0, 2.0 * r0
+    for _ in range(40):
+        mid = 0.5 * (lo + hi)
+        cnt = tree.query_ball_point(probe, mid, return_length=True, workers=-1).mean() - 1.0
+        if cnt < mean_deg:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def large(seed: int = 3, n: int = 100_000, mean_deg: float = 100.0, bg_rate_hz: float = 5.0,
+          noise_seed: int = 5, dim: int = 3) -> NetSpec:
+    rng = np.random.default_rng(seed)
+    pos = rng.random((n, dim))
+    r = _radius_for_mean_degree(pos, mean_deg, seed=seed)
+    src, dst = _pairs_within(pos, r)
+    src, dst = _sort_by_dst(src, dst)
+    E = src.shape[0]
+    w = _signed_lognormal(rng, E)
+    speed = rng.uniform(0.05, 0.5, E)
+    obs = dict(OBS_DEFAULT, seed=noise_seed)
+    bg = dict(rate_hz=bg_rate_hz, amp=1.0, dur_ms=2.0, seed=seed + 1000)
+    return NetSpec(pos=pos, src=src, dst=dst, weight=w, speed=speed, obs=obs, background=bg,
+                   ring_depth=256, name=f"large_n{n}")
+
+
+def roofline(seed: int = 4, n: int = 1_000_000, mean_deg: float = 50.0, hub_frac: float = 0.025,
+             hub_deg: int = 1000, bg_rate_hz: float = 5.0, noise_seed: int = 6) -> NetSpec:
+    rng = np.random.default_rng(seed)
+    pos = rng.random((n, 3))
+    n_hub = int(round(hub_frac * n))
+    hubs = rng.choice(n, n_hub, replace=False).astype(np.int64)
+    is_hub = np.zeros(n, bool)
+    is_hub[hubs] = True
+    # non-hub targets: every node within r (r set for the remaining mean in-degree)
+    rest_deg = (mean_deg * n - hub_deg * n_hub) / (n - n_hub)
+    r = _radius_for_mean_degree(pos, rest_deg, seed=seed)
+    s1, d1 = _pairs_within(pos, r)
+    m = ~is_hub[d1]
+    s1, d1 = s1[m], d1[m]
+    # hub targets: the hub_deg nearest other nodes
+    tree = cKDTree(pos)
+    _, nn = tree.query(pos[hubs], k=hub_deg + 1, workers=-1)
+    nn = nn[:, 1:]
+    s2 = nn.reshape(-1).astype(np.int32)
+    d2 = np.repeat(hubs, hub_deg).astype(np.int32)
+    src = np.concatenate([s1, s2])
+    dst = np.concatenate([d1, d2])
+    src, dst = _sort_by_dst(src, dst)
+    E = src.shape[0]
+    w = _signed_lognormal(rng, E)
+    speed = rng.uniform(0.05, 0.5, E)
+    obs = dict(OBS_DEFAULT, seed=noise_seed)
+    bg = dict(rate_hz=bg_rate_hz, amp=1.0, dur_ms=2.0, seed=seed + 1000)
+    return NetSpec(pos=pos, src=src, dst=dst, weight=w, speed=speed, obs=obs, background=bg,
+                   ring_depth=256, name=f"roofline_n{n}")
+
+
+def batch_member(seed: int, n: int | None = None, n_lo: int = 32, n_hi: int = 4096,
+                 kept_deg: float = 20.0, keep: float = 0.5) -> NetSpec:
+    """One network of the batched ensemble (its own seed decides its size)."""
+    rng = np.random.default_rng(seed)
+    if n is None:
+        n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+    pos = rng.random((n, 2))
+    r = math.sqrt(kept_deg / keep / (math.pi * n))
+    src, dst = _pairs_within(pos, r)
+    m = rng.random(src.shape[0]) < keep
+    src, dst = _sort_by_dst(src[m], dst[m])
+    E = src.shape[0]
+    w = _signed_lognormal(rng, E)
+    speed = rng.uniform(0.05, 0.5, E)
+    k = int(rng.integers(1, 9))
+    nodes = rng.choice(n, min(k, n), replace=False)
+    onsets = rng.uniform(5.0, 50.0, nodes.shape[0])
+    pulses = [(int(j), float(t), float(t) + 2.0, 1.0) for j, t in zip(nodes, onsets)]
+    obs = dict(OBS_DEFAULT, seed=seed + 7)
+    return NetSpec(pos=pos, src=src, dst=dst, weight=w, speed=speed, obs=obs, pulses=pulses,
+                   name=f"batch_s{seed}")
+
+
+def batch(n_nets: int = 4096, seed0: int = 1000, **kw) -> list:
+    return [batch_member(seed0 + i, **kw) for i in range(n_nets)]
+
+
+# Fig. 1 / Fig. 2 (Sec. 3): five vertices at the TikZ positions of Fig. 2 and the eight
+# edges with their printed delays (ms) and weights.  The delays are used as given.
+FIG2_POS = np.array([[0.0, 3.0], [3.0, 3.0], [6.0, 4.0], [2.0, 1.0], [6.0, 1.0]])
+FIG2_EDGES = [  # (from, to, delay_ms, weight), vertices numbered from 1 as in the figure
+    (1, 2, 3.6, -1.0), (1, 3, 7.4, 1.0), (3, 2, 3.8, 1.0), (2, 4, 2.6, 0.7),
+    (4, 5, 4.8, -2.0), (4, 1, 3.4, -2.0), (3, 5, 3.6, 1.0), (5, 2, 4.4, -1.0),
+]
+
+
+def fig2(delay_steps, t_on_ms: float = 10.0, amp: float = 1.0) -> NetSpec:
+    """The Fig. 2 network with explicit whole-step delays ``delay_steps`` (edge order
+    of ``FIG2_EDGES``) and one pulse on vertex 1."""
+    src = np.array([e[0] - 1 for e in FIG2_EDGES], np.int32)
+    dst = np.array([e[1] - 1 for e in FIG2_EDGES], np.int32)
+    w = np.array([e[3] for e in FIG2_EDGES], np.float32)
+    return NetSpec(pos=FIG2_POS.copy(), src=src, dst=dst, weight=w, speed=None, speed_scalar=1.0,
+                   delay=np.asarray(delay_steps, np.int32),
+                   pulses=[(0, t_on_ms, t_on_ms + 2.0, amp)], name="fig2")
+
+
+def chain2(dist_mm: float = 0.5, speed: float = 0.1, t_on_ms: float = 5.0, w: float = 0.5,
+           dt_ms: float = 0.05) -> NetSpec:
+    """Two nodes on the x axis, one edge 0 -> 1, a pulse on node 0."""
+    pos = np.array([[0.0, 0.0], [dist_mm, 0.0]])
+    return NetSpec(pos=pos, src=np.array([0], np.int32), dst=np.array([1], np.int32),
+                   weight=np.array([w], np.float32), speed=None, speed_scalar=speed, dt_ms=dt_ms,
+                   pulses=[(0, t_on_ms, t_on_ms + 2.0, 1.0)], name="chain2")
+
+
+def random_small(seed: int, n: int = 12, p_edge: float = 0.3, dim: int = 2, speed: float = 0.05,
+                 n_pulses: int = 2) -> NetSpec:
+    """A tiny random geometric net for brute-force checks (dense random edges)."""
+    rng = np.random.default_rng(seed)
+    pos = rng.random((n, dim)) * 0.3
+    ii, jj = np.nonzero((rng.random((n, n)) < p_edge) & ~np.eye(n, dtype=bool))
+    src, dst = _sort_by_dst(ii.astype(np.int32), jj.astype(np.int32))
+    w = rng.uniform(-1.0, 1.0, src.shape[0]).astype(np.float32)
+    nodes = rng.choice(n, n_pulses, replace=False)
+    pulses = [(int(j), float(rng.uniform(0.5, 3.0)), float(rng.uniform(3.5, 6.0)), 1.0) for j in nodes]
+    return NetSpec(pos=pos, src=src, dst=dst, weight=w, speed=None, speed_scalar=speed, pulses=pulses,
+                   obs=dict(OBS_DEFAULT, seed=seed + 11), name=f"small_s{seed}")
