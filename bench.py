@@ -1,0 +1,319 @@
+#!/usr/bin/env python
+"""Benchmark of the fused delayed-network step on one B300 per rank.
+
+One bench step = one simulation step of dt = 0.05 ms of the whole network: the
+delayed gather over every edge, the FHN update of every node, the history write,
+the low-pass readout and (every 20 steps) the noisy observation -- one launch of
+the fused step kernel.
+
+Workload (default ``roofline``): N = 1,000,000 nodes in a 1 mm cube, ~50M edges
+(2.5 % hubs of in-degree 1000, the rest a radius graph of mean ~25.6), weights
+lognormal(-2, 0.5) with 20 % negated, speeds U(0.05, 0.5) m/s, 5 Hz background
+pulses, a 256-step history ring.  Inputs are larger than L2 (the 400 MB edge stream
+is re-read every step), so no L2 flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Metric: edge-updates/s (E * K / time), whole job.
+With N > 1 (torchrun) every rank runs an independent replica of the workload with
+its own seed (the nets are independent problems: no exchange, weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_0908_3934_b300 import netgen  # noqa: E402
+
+METRIC = "edge-updates/s"
+EDGE_BYTES = 12        # packed record (src|D 4 B + weight 4 B) + the gathered FP32 value
+NODE_BYTES = 36.2      # v~ read 4, (w~,c~) read 8 + write 8, ring write 4, row_ptr 4,
+                       # background counter 4 + caller id 4, readout 4 B / 20 steps
+
+
+def workload(name: str, rank: int):
+    """The seeded network of a replica (cached under the temp dir: generating the
+    1M-node net takes ~40 s of host time and it is the same on every call)."""
+    import pickle
+    gens = {"roofline": lambda: netgen.roofline(seed=4 + 1000 * rank),
+            "large": lambda: netgen.large(seed=3 + 1000 * rank),
+            "tiny": lambda: netgen.tiny(seed=1 + 1000 * rank)}
+    if name not in gens:
+        raise SystemExit(f"unknown workload {name}")
+    src = open(os.path.join(ROOT, "paper_0908_3934_b300", "netgen.py"), "rb").read()
+    key = hashlib.sha256(src + f"{name}:{rank}".encode()).hexdigest()[:16]
+    path = os.path.join(tempfile.gettempdir(), f"geonet_{name}_{rank}_{key}.pkl")
+    if os.path.exists(path):
+        with open(path, "rb") as f:
+            return pickle.load(f)
+    spec = gens[name]()
+    tmp = path + f".{os.getpid()}"
+    with open(tmp, "wb") as f:
+        pickle.dump(spec, f, protocol=4)
+    os.replace(tmp, path)
+    return spec
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("k_step.cu", "internal.cuh", "philox.cuh"):
+        with open(os.path.join(ROOT, "paper_0908_3934_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(workload_name: str):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", f"k_step_{workload_name}.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        if p.get("kernel_hash") == kernel_hash():
+            return float(p["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu=timestamp,{self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if uuid:
+            cmd.insert(1, f"--id={uuid}")
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = [l.strip().split(", ") for l in self.tmp.read().splitlines() if l.strip()]
+        os.unlink(self.tmp.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for nm, val in zip(names, r[5:9]):
+                    if val.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_baseline(spec, steps: int):
+    """The FP64 oracle as it stands, single-threaded, on the first `steps` steps."""
+    import oracle
+    D = oracle.net_delays(spec)
+    t0 = time.perf_counter()
+    oracle.simulate(spec, steps, delay=D, want_y=False, ev_cap=1)
+    dt = time.perf_counter() - t0
+    return dict(value=spec.n_edges * steps / dt, unit=METRIC, cores=1, kind="oracle",
+                sample=f"first {steps} steps of the same {spec.n_nodes}-node network from rest "
+                       f"(FP64 C oracle, 1 thread; delays precomputed, untimed)",
+                seconds=dt)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    spec = workload(args.workload, 0)
+    steps = max(1, min(args.steps, args.ref_steps))
+    cb = cpu_baseline(spec, steps)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": METRIC, "n_gpus": args.gpus,
+            "steps": steps, "warmup": 0, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": config_of(args, spec, world),
+            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": cb["value"], "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(args, spec, world):
+    return {"workload": f"{args.workload}: N={spec.n_nodes}, E={spec.n_edges} per replica, dt=0.05 ms, "
+                        f"FHN nodes, 5 Hz background, ring 256",
+            "nodes_per_replica": spec.n_nodes, "edges_per_replica": spec.n_edges, "replicas": world,
+            "dt_ms": spec.dt_ms, "l2": "inputs larger than L2 (edge stream re-read every step)",
+            "parallelism": f"replicas{world}"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="roofline", choices=["roofline", "large", "tiny"])
+    ap.add_argument("--cpu-steps", type=int, default=30, help="oracle steps of the cpu_baseline sample")
+    ap.add_argument("--ref-steps", type=int, default=30, help="oracle steps timed by --impl reference")
+    ap.add_argument("--e2e-chunk", type=int, default=1000, help="steps per host round trip in the e2e run")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--obs-cap", type=int, default=4096, help="observation rows kept on the device")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_0908_3934_b300 import geonet
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    spec = workload(args.workload, rank)
+    stream = torch.cuda.Stream(device=dev)
+    net = geonet.Net(spec, device=local, stream=stream.cuda_stream, obs_capacity=args.obs_cap)
+    info = net.gn_net_get_info()
+    E, N = spec.n_edges, spec.n_nodes
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    # ---- device-resident throughput: W untimed steps, then exactly K timed steps
+    net.gn_step(args.warmup)
+    barrier()
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid)
+    time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    net.gn_step(args.steps)
+    ev1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    t = ev0.elapsed_time(ev1) / 1e3
+    launches = args.steps + args.steps // 64 + (1 if args.steps % 64 else 0)
+    net.gn_observe(discard=True)
+
+    # ---- end to end through the public API: every chunk uploads a new pulse set from
+    # host memory (the controls u_j), steps, and reads the observations back into a
+    # pinned host buffer
+    rng = np.random.default_rng(77 + rank)
+    chunk = max(1, min(args.e2e_chunk, args.steps))
+    n_chunks = max(1, args.steps // chunk)
+    t_sim = (net.gn_net_get_info()["step"] + chunk) * spec.dt_ms
+    pulses = [[(int(j), t_sim + (c * chunk + rng.uniform(0, chunk)) * spec.dt_ms,
+                t_sim + (c * chunk + rng.uniform(0, chunk)) * spec.dt_ms + 2.0, 1.0)
+               for j in rng.choice(N, 1000, replace=False)] for c in range(n_chunks + 1)]
+    max_rows = min(args.obs_cap, chunk // spec.obs["sample_every"] + 1)
+    host = torch.empty((max_rows, N), dtype=torch.float32, pin_memory=True).numpy()
+    net.gn_set_stimulus(pulses[0])
+    net.gn_step(chunk)
+    net.gn_observe(max_rows, out=host)
+    barrier()
+    h2d = d2h = 0
+    t0 = time.perf_counter()
+    for c in range(n_chunks):
+        net.gn_set_stimulus(pulses[c + 1])
+        h2d += 1000 * 24 + 4
+        net.gn_step(chunk)
+        y, _, _ = net.gn_observe(max_rows, out=host)
+        d2h += y.nbytes
+    barrier()
+    t_e2e = time.perf_counter() - t0
+    e2e_steps = n_chunks * chunk
+
+    if world > 1:
+        tt = torch.tensor([t, t_e2e], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t, t_e2e = tt.tolist()
+        ee = torch.tensor([float(E)], device=dev, dtype=torch.float64)
+        dist.all_reduce(ee, op=dist.ReduceOp.SUM)
+        E_total = ee.item()
+    else:
+        E_total = float(E)
+
+    value = E_total * args.steps / t
+    peak, peak_kind = peaks()
+    step_s = t / args.steps
+    bytes_step = E * EDGE_BYTES + N * NODE_BYTES
+    achieved = bytes_step / step_s / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_of(args, spec, world),
+        "node_steps_per_s": (value / E_total) * N * world, "rtf": spec.dt_ms * 1e-3 / step_s,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": peak_kind,
+                     "traffic": traffic_per_launch(args.workload),
+                     "algorithmic_bytes_per_launch": bytes_step, "kernel": "k_step"},
+        "e2e": {"value": E_total * e2e_steps / t_e2e, "unit": METRIC,
+                "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps},
+        "gpu_launches": launches, "clocks": clocks,
+        "layout": {"ring_depth": info["ring_depth"], "edge_format": info["edge_format"],
+                   "n_blocks": info["n_blocks"], "max_delay": info["max_delay"],
+                   "device_bytes": info["device_bytes"]},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(spec, args.cpu_steps)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    net.gn_net_destroy()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

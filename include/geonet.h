@@ -1,0 +1,220 @@
+/*
+ * geonet.h -- C ABI of libgeonet.so, a B300 (sm_103a) simulator of delayed,
+ * weighted signalling on geometric networks after Buibas & Silva, "A framework
+ * for simulating and estimating the state and functional topology of complex
+ * dynamic geometric networks" (arXiv:0908.3934).
+ *
+ * The model (all citations are to that paper):
+ *   - vertices j with a static position x_j and state y_j = {V_j, W_j}       (Sec. 2, Eq. yjstate)
+ *   - directed edges i -> j with weight omega_ij and delay tau_ij             (Sec. 2, Eq. Yjset)
+ *   - geodesic delays tau_ij = |x_i - x_j| / s_ij, quantised to whole steps   (Sec. 3.2.1, Eq. delaydist;
+ *                                                                              Sec. 2, Eq. gendelay)
+ *   - the delayed input S_j(t) = sum_{i->j} omega_ij v_i(t - tau_ij)           (Sec. 2, Eq. Yjset)
+ *   - FitzHugh-Nagumo vertex dynamics, forward Euler in steps of dt:          (Sec. 3.1, FHN pair and
+ *       V' = V + dt (aV - bV^3 - cW + S + U + I_ext),  W' = W + dt e (V + f - gW)   Eq. fnstate)
+ *   - a control input U_j(t) (pulses, background pulses)                      (Sec. 2, u_j in Eq. Htrans)
+ *   - the readout: a first-order low-pass c of V and a noisy observation      (Sec. 3.3, calcium model
+ *       y = gain (V* + c~) + offset + sigma N(0,1)                              and I = n c + b + N(0, g^2))
+ *
+ * Conventions shared by every call:
+ *   - Status codes, never exceptions.  gn_last_error() gives a message for the
+ *     last failing call on the calling thread.
+ *   - Every input array is copied during the call; the caller may free it on return.
+ *   - Host buffers are caller-owned and in the CALLER's node and edge order: the
+ *     library renumbers nodes internally (spatial order) and undoes it on output.
+ *   - State is reported relative to the isolated rest point (V*, W*):
+ *     v~ = V - V*, w~ = W - W*, c~ = c - V*.  gn_get_rest() gives (V*, W*).
+ *   - gn_step() is asynchronous on the net's stream; every call that returns data
+ *     to the host synchronises that stream first.
+ *   - A handle is not thread-safe: calls on one handle must not overlap.
+ */
+#ifndef GEONET_H
+#define GEONET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GN_API __attribute__((visibility("default")))
+#else
+#define GN_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GN_OK = 0,
+    GN_EINVAL = -1,      /* invalid argument or descriptor */
+    GN_ENOMEM = -2,      /* device or host allocation failed */
+    GN_ERANGE = -3,      /* a value does not fit: delay > ring_depth - 2, too many nodes/edges */
+    GN_ECUDA = -4,       /* a CUDA runtime call failed */
+    GN_ESTATE = -5,      /* call not valid in the handle's state */
+    GN_ETIMEOUT = -6,    /* a bounded device-side wait gave up */
+    GN_EINTERNAL = -7,   /* a device-side consistency check failed */
+    GN_EOVERFLOW = -8    /* a device buffer overflowed; the data returned is what was kept */
+} gn_status;
+
+enum { GN_COUPLE_REST = 0, GN_COUPLE_RAW = 1 };
+
+/* FitzHugh-Nagumo parameters in the paper's notation (Sec. 3.1):
+ *   dV/dt = aV - bV^3 - cW + S + U + i_ext,   dW/dt = e (V + f - gW).
+ * The classic (a, b, eps) = (0.7, 0.8, 0.08) model is a = 1, b = 1/3, c = 1,
+ * e = 0.08, f = 0.7, g = 0.8.  A unique rest point needs g > 0, b > 0, a < c/g
+ * (GN_EINVAL otherwise). */
+typedef struct {
+    double a, b, c, e, f, g, i_ext;
+} gn_fhn_params;
+
+/* Readout (Sec. 3.3): c~' = c~ + (dt/tau_ms)(v~' - c~) every step; every
+ * sample_every steps y = gain (V* + c~) + offset + sigma xi, xi ~ N(0, 1) drawn
+ * from Philox4x32-10 keyed by `seed` with counter (node, sample, 2). */
+typedef struct {
+    double tau_ms;
+    int32_t sample_every;
+    float gain, offset, sigma;
+    uint64_t seed;
+} gn_obs_params;
+
+/* A network.  pos [n_nodes*dim] (mm, row-major); edges src[e] -> dst[e] with
+ * weight[e]; delays from geometry with speed[e] (m/s = mm/ms; NULL: speed_scalar
+ * for all edges), or given explicitly in whole steps by delay_steps[e] (>= 1),
+ * which bypasses geometry.  Self-loops are rejected (Eq. Yjset sums over i != j);
+ * repeated (i, j) pairs are separate terms. */
+typedef struct {
+    int32_t n_nodes;
+    int32_t dim;                 /* 1, 2 or 3 */
+    const double *pos;
+    int64_t n_edges;
+    const int32_t *src;
+    const int32_t *dst;
+    const float *weight;
+    const double *speed;
+    double speed_scalar;
+    const int32_t *delay_steps;
+    double dt_ms;
+    gn_fhn_params fhn;
+    gn_obs_params obs;
+    int32_t coupling;            /* GN_COUPLE_REST: S uses V - V*; GN_COUPLE_RAW: S uses V */
+    double theta;                /* event threshold on V (events: V(n) < theta <= V(n+1)) */
+    int32_t ring_depth;          /* history slots, a power of two >= D_max + 2; 0 = smallest such */
+    int64_t obs_capacity;        /* samples kept on the device; 0 = 1024 */
+    int64_t event_capacity;      /* events kept on the device; 0 = 1 << 20 */
+    int32_t renumber;            /* 0: renumber nodes in spatial (Morton) order; -1: keep the caller's order */
+    int32_t edge_format;         /* 0: packed 32-bit keys when N * ring_depth <= 2^32, else 64-bit; 1: always 64-bit */
+    void *cuda_stream;           /* cudaStream_t to run on; NULL: the library makes its own */
+    int32_t device;              /* CUDA device ordinal */
+} gn_net_desc;
+
+/* A pulse of amplitude amp on node over [t_on_ms, t_off_ms): the steps
+ * n with llround(t_on/dt) <= n < llround(t_off/dt). */
+typedef struct {
+    int32_t node;
+    double t_on_ms, t_off_ms;
+    float amp;
+} gn_pulse;
+
+/* Sizes and layout chosen at create time. */
+typedef struct {
+    int32_t n_nodes;
+    int64_t n_edges;
+    int32_t dim;
+    int32_t ring_depth;
+    int32_t max_delay;
+    int32_t min_delay;
+    int64_t n_clamped;           /* geometric delays that rounded below one step */
+    int32_t edge_format;         /* 0: packed 32-bit (src << log2 R | D); 1: 64-bit (src, D) */
+    int32_t n_blocks;            /* row blocks of the step kernel */
+    int64_t step;                /* steps taken */
+    int64_t samples;             /* samples produced */
+    double v_rest, w_rest;
+    size_t device_bytes;         /* device memory held by the handle */
+} gn_net_info;
+
+typedef struct gn_net gn_net;
+
+/* Build a network on the device: copy the inputs, quantise the delays in FP64
+ * on the GPU (D = max(1, llround(|x_i - x_j| / (s dt))), Sec. 3.2.1, Eq. delaydist),
+ * renumber the nodes in Morton order, build the by-target edge list (CSR) and
+ * put every node at rest with a resting history.  *out receives the handle.
+ * GN_EINVAL: bad descriptor (NaN position, speed <= 0, id out of range,
+ * self-loop, dt <= 0, no unique rest point); GN_ERANGE: a delay does not fit
+ * the ring; GN_ENOMEM / GN_ECUDA as named. */
+GN_API gn_status gn_net_create(const gn_net_desc *desc, gn_net **out);
+
+/* Free every device and host resource of the handle (NULL is a no-op). */
+GN_API gn_status gn_net_destroy(gn_net *net);
+
+GN_API gn_status gn_net_get_info(const gn_net *net, gn_net_info *info);
+
+/* The whole-step delay of every edge, in the caller's edge order ([n_edges]). */
+GN_API gn_status gn_get_delays(const gn_net *net, int32_t *out);
+
+/* The isolated rest point (V*, W*) in FP64 (Sec. 3.1 FHN with S = U = 0). */
+GN_API gn_status gn_get_rest(const gn_net *net, double *v_rest, double *w_rest);
+
+/* Replace the pulse set (u_j of Eq. Htrans).  Pulses on the same node add. */
+GN_API gn_status gn_set_stimulus(gn_net *net, const gn_pulse *pulses, int32_t n_pulses);
+
+/* Background pulses: at every step a node starts, with probability
+ * p = rate_hz * dt, a pulse of amplitude amp lasting llround(dur_ms/dt) steps;
+ * an onset during a pulse restarts its count.  The draw at step n for node j is
+ * the first word of Philox4x32-10 keyed by `seed` at counter (j, n, 1), compared
+ * with floor(p 2^32).  rate_hz = 0 turns it off. */
+GN_API gn_status gn_set_background(gn_net *net, double rate_hz, float amp, double dur_ms, uint64_t seed);
+
+/* Advance n_steps steps of dt (asynchronous).  Each step is one launch of the
+ * fused step kernel: delayed gather, FHN update, history write, readout, noise,
+ * events and first arrivals. */
+GN_API gn_status gn_step(gn_net *net, int64_t n_steps);
+
+/* Wait for the net's stream; reports device-side errors. */
+GN_API gn_status gn_synchronize(gn_net *net);
+
+/* Copy up to max_samples observation rows not yet read, oldest first, into
+ * out[k][n_nodes] (host, caller node order), and advance the read cursor.
+ * *first_sample (may be NULL) receives the sample number of row 0 (sample k is
+ * taken after step (k+1) * sample_every).  out == NULL discards the rows instead
+ * of copying them.  If more than obs_capacity samples
+ * were produced since the last read, the oldest are lost and GN_EOVERFLOW is
+ * returned with the kept rows copied. */
+GN_API gn_status gn_observe(gn_net *net, float *out, int64_t max_samples, int64_t *first_sample,
+                     int64_t *written);
+
+/* State relative to rest, caller node order.  Any pointer may be NULL. */
+GN_API gn_status gn_get_state(gn_net *net, float *v, float *w, float *c, int32_t *bg_count, int64_t *step);
+
+/* Set the dynamic state (initial conditions y_j(t0), Sec. 2) at step `step`:
+ * hist[k][j] = v~_j(step - k) for k < depth (1 <= depth <= ring_depth; older slots
+ * are set to rest), w~ and c~ (NULL = 0) and background counters (NULL = 0), all
+ * in caller node order.  First arrivals are reset to -1, the event list is
+ * cleared and the observation cursor moves to the first sample after `step`. */
+GN_API gn_status gn_set_state(gn_net *net, const float *hist, int32_t depth, const float *w, const float *c,
+                              const int32_t *bg_count, int64_t step);
+
+/* History: out[k][j] = v~_j(step - k), k = 0..depth-1, depth <= ring_depth. */
+GN_API gn_status gn_get_history(gn_net *net, float *out, int32_t depth);
+
+/* First step at which v~_j became non-zero ([n_nodes], -1 = not yet). */
+GN_API gn_status gn_get_arrivals(gn_net *net, int64_t *first_arrival);
+
+/* Events (upward crossings of theta), sorted by (step, node), caller node ids.
+ * *n_total receives the number recorded; up to cap are copied.  GN_EOVERFLOW if
+ * the device buffer overflowed (then the kept ones are returned). */
+GN_API gn_status gn_get_events(gn_net *net, int32_t *node, int64_t *step, int64_t cap, int64_t *n_total);
+
+/* Checkpoint: the dynamic state (history ring, w~, c~, background counters,
+ * first arrivals, step counter).  With buf == NULL, *used receives the size
+ * needed.  Restoring into a handle created from the same descriptor makes the
+ * continuation bit-identical to an uninterrupted run. */
+GN_API gn_status gn_save_state(gn_net *net, void *buf, size_t cap, size_t *used);
+GN_API gn_status gn_load_state(gn_net *net, const void *buf, size_t size);
+
+/* Thread-local message of the last failing call ("" if none). */
+GN_API const char *gn_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GEONET_H */

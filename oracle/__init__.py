@@ -70,7 +70,8 @@ class _Out(C.Structure):
         ("first_arrival", C.c_void_p), ("first_value", C.c_void_p),
         ("ev_node", C.c_void_p), ("ev_step", C.c_void_p), ("ev_cap", C.c_int64), ("ev_count", C.c_int64),
         ("snap_every", C.c_int32),
-        ("snap_v", C.c_void_p), ("snap_w", C.c_void_p), ("snap_c", C.c_void_p),
+        ("snap_v", C.c_void_p), ("snap_w", C.c_void_p), ("snap_c", C.c_void_p), ("bg_count", C.c_void_p),
+        ("hist_out", C.c_void_p), ("hist_out_depth", C.c_int32),
     ]
 
 
@@ -167,16 +168,17 @@ def net_delays(spec) -> np.ndarray:
 
 def simulate(spec, n_steps: int, *, dense: bool = False, snap_every: int = 0,
              ev_cap: int = 1 << 16, want_y: bool = True, coupling: str | None = None,
-             init: dict | None = None, delay: np.ndarray | None = None):
+             init: dict | None = None, delay: np.ndarray | None = None, hist_depth: int = 0):
     """Run the FP64 oracle for ``n_steps`` steps of ``dt``.
 
     ``spec`` is a ``paper_0908_3934_b300.netgen.NetSpec``.  The run starts from
     rest at step 0, or, with ``init = dict(n0, v, w, c, bg_count, hist)``, from
     that state at step n0 (``hist[k, j]`` = v~_j(n0 - k)).  Returns a dict with
-    the final state relative to rest (v, w, c), observations y / y_clean
-    [n_samples, N] for the samples taken inside the run, first_arrival /
-    first_value [N], events (node, step) and, if ``snap_every`` > 0, state
-    snapshots [n_steps // snap_every, N].
+    the final state relative to rest (v, w, c), background counters, observations
+    y / y_clean [n_samples, N] for the samples taken inside the run, first_arrival /
+    first_value [N], events (node, step), if ``snap_every`` > 0 state snapshots
+    [n_steps // snap_every, N], and if ``hist_depth`` > 0 the final history
+    ``hist[k, j]`` = v~_j(n_end - k), k < hist_depth (at most D_max + 1).
     """
     L = lib()
     N = spec.n_nodes
@@ -223,7 +225,10 @@ def simulate(spec, n_steps: int, *, dense: bool = False, snap_every: int = 0,
     sv = np.zeros((n_snap, N)) if n_snap else None
     sw = np.zeros((n_snap, N)) if n_snap else None
     sc = np.zeros((n_snap, N)) if n_snap else None
-    out = _Out(v=_ptr(v), w=_ptr(w), c=_ptr(c), y=_ptr(y), y_clean=_ptr(yc),
+    bgc = np.zeros(N, np.int32)
+    hout = np.zeros((hist_depth, N)) if hist_depth > 0 else None
+    out = _Out(v=_ptr(v), w=_ptr(w), c=_ptr(c), y=_ptr(y), y_clean=_ptr(yc), bg_count=_ptr(bgc),
+               hist_out=_ptr(hout), hist_out_depth=hist_depth,
                first_arrival=_ptr(fa), first_value=_ptr(fv), ev_node=_ptr(evn), ev_step=_ptr(evs),
                ev_cap=ev_cap, ev_count=0, snap_every=snap_every if n_snap else 0,
                snap_v=_ptr(sv), snap_w=_ptr(sw), snap_c=_ptr(sc))
@@ -247,4 +252,5 @@ def simulate(spec, n_steps: int, *, dense: bool = False, snap_every: int = 0,
     ne = min(out.ev_count, ev_cap)
     return dict(v=v, w=w, c=c, y=y, y_clean=yc, first_arrival=fa, first_value=fv,
                 ev_node=evn[:ne].copy(), ev_step=evs[:ne].copy(), ev_count=out.ev_count,
-                snap_v=sv, snap_w=sw, snap_c=sc, delay=D, rest=rest_point(fhn))
+                snap_v=sv, snap_w=sw, snap_c=sc, bg_count=bgc, hist=hout, n_end=n0 + n_steps,
+                delay=D, rest=rest_point(fhn))

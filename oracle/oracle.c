@@ -226,6 +226,9 @@ typedef struct {
     int64_t ev_count;         /* out: total events (may exceed ev_cap) */
     int32_t snap_every;       /* > 0: store the state after every snap_every steps */
     double *snap_v, *snap_w, *snap_c; /* [n_steps/snap_every * N] */
+    int32_t *bg_count;        /* [N] final background counters (or NULL) */
+    double *hist_out;         /* [hist_out_depth * N]: v~_j(n_end - k), k < hist_out_depth (or NULL) */
+    int32_t hist_out_depth;   /* <= D_max + 1 */
 } orc_out;
 
 /* One Euler step of one node (the FHN transition about the rest point).
@@ -316,6 +319,7 @@ static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense
     int64_t n0 = init ? init->n0 : 0;
     if (n0 < 0 || (init && dense)) return ORC_EINVAL;
     if (init && n0 > 0 && init->hist_depth < dmax + 1 && init->hist_depth < n0 + 1) return ORC_EINVAL;
+    if (out->hist_out && (out->hist_out_depth < 1 || out->hist_out_depth > dmax + 1)) return ORC_EINVAL;
     history h;
     h.n = N;
     h.dense = dense;
@@ -395,6 +399,13 @@ static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense
     memcpy(out->v, v, sizeof(double) * (size_t)N);
     memcpy(out->w, w, sizeof(double) * (size_t)N);
     memcpy(out->c, c, sizeof(double) * (size_t)N);
+    if (out->bg_count) memcpy(out->bg_count, bgc, sizeof(int32_t) * (size_t)N);
+    if (out->hist_out) {
+        int64_t n_end = n0 + n_steps;
+        for (int32_t k = 0; k < out->hist_out_depth; ++k)
+            for (int32_t j = 0; j < N; ++j)
+                out->hist_out[(int64_t)k * N + j] = (k == 0) ? v[j] : hist_get(&h, n_end - k, j);
+    }
     free(h.buf); free(v); free(w); free(c); free(S); free(bgc);
     return ORC_OK;
 }

@@ -1,0 +1,80 @@
+// Internal layout of one network on the device, shared by the kernels and the
+// host runtime of libgeonet.so (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace gn {
+
+// Device arrays and constants of one network, in internal (Morton) node order.
+//
+// HBM layout:
+//   ring   float [R][N]  slot-major history: slot s holds v~ at the latest step
+//                        t == s (mod R) that is <= the current step; the current
+//                        state v~(n) is slot n & (R-1) (the ring *is* the state).
+//   wc     float2 [N]    (w~, c~)
+//   ekey   per edge, CSR by target, rows sorted by source:
+//            packed:  uint32 (src << dbits) | D, dbits = log2 R
+//            wide:    uint2  {src, D}
+//   ew     float [E]     weights, same order
+//   Edge arrays are padded by kEdgePad entries so 16-byte vector loads that
+//   start inside [0, E) never leave the allocation.
+struct StepArgs {
+    int32_t N;
+    int32_t ring_mask;       // R - 1
+    int32_t dbits;           // packed keys: bits of D
+    const void *ekey;
+    const float *ew;
+    const int32_t *row_ptr;  // [N + 1]
+    const int32_t *blk;      // [n_blocks + 1] first row of each row block
+    float *ring;
+    float2 *wc;
+    int32_t *bgc;            // [N] background pulse counters, or null
+    const float *bias;       // [N] RAW coupling: V* * sum of in-weights, or null
+    int64_t *first;          // [N] first step with v~ != 0, -1 = none
+    const int32_t *perm;     // [N] internal -> caller node id (RNG counters use caller ids)
+    // pulses sorted by internal node id; the count lives in device memory so a new
+    // pulse set can be copied in stream order without re-capturing the step graph
+    const int32_t *n_pulses;
+    const int32_t *p_node;
+    const int64_t *p_on;
+    const int64_t *p_off;
+    const float *p_amp;
+    // FHN about the rest point: dv = v (k1 + v (q2 + q3 v)) - cw w + S + U, dw = e (v - g w)
+    float dt, k1, q2, q3, cw, dte, g;
+    float alpha;             // dt / tau of the readout
+    float theta_s;           // event threshold relative to rest, theta - V*
+    float gain, offset, sigma, vrest;
+    int32_t sample_every;
+    uint64_t obs_seed;
+    uint32_t bg_thr;         // 0 = no background
+    float bg_amp;
+    int32_t bg_width;
+    uint64_t bg_seed;
+    float *obs;              // [obs_cap][N], rows in caller node order
+    int64_t obs_cap;
+    int32_t *ev_node;
+    int64_t *ev_step;
+    unsigned long long *ev_count;
+    int64_t ev_cap;
+    const int64_t *d_step;   // step counter: a launch with offset k runs step *d_step + k
+};
+
+constexpr int kEdgePad = 4096;
+
+// Launch geometry of the step kernel (row blocks hold at most kStepCap - 3 edges).
+constexpr int kStepThreads = 256;
+constexpr int kStepEPT = 8;
+constexpr int kStepCap = kStepThreads * kStepEPT;
+constexpr int kStepMaxRows = kStepThreads;
+
+// Kernel launchers (k_step.cu, k_delay.cu)
+cudaError_t launch_step(const StepArgs &a, int n_blocks, int k, bool packed, bool stream_edges,
+                        cudaStream_t s);
+cudaError_t launch_advance(int64_t *d_step, int64_t by, cudaStream_t s);
+cudaError_t launch_delay(int64_t n_edges, int32_t dim, const double *pos, const int32_t *src,
+                         const int32_t *dst, const double *speed, double speed_scalar, double dt_ms,
+                         int32_t *delay, uint8_t *clamped, cudaStream_t s);
+
+}  // namespace gn

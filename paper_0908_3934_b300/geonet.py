@@ -1,0 +1,265 @@
+"""ctypes binding of libgeonet.so (include/geonet.h): the same names, argument
+marshalling only.  Every step of the simulation runs in the library's CUDA
+kernels; nothing here computes.
+
+The library is built in-tree by ``python -m paper_0908_3934_b300.build``;
+loading raises ``RuntimeError`` if it is missing -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgeonet.so")
+
+GN_OK, GN_EINVAL, GN_ENOMEM, GN_ERANGE, GN_ECUDA, GN_ESTATE, GN_ETIMEOUT, GN_EINTERNAL, GN_EOVERFLOW = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8)
+STATUS_NAMES = {0: "GN_OK", -1: "GN_EINVAL", -2: "GN_ENOMEM", -3: "GN_ERANGE", -4: "GN_ECUDA", -5: "GN_ESTATE",
+                -6: "GN_ETIMEOUT", -7: "GN_EINTERNAL", -8: "GN_EOVERFLOW"}
+GN_COUPLE_REST, GN_COUPLE_RAW = 0, 1
+
+
+class GeonetError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class gn_fhn_params(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("a", "b", "c", "e", "f", "g", "i_ext")]
+
+
+class gn_obs_params(C.Structure):
+    _fields_ = [("tau_ms", C.c_double), ("sample_every", C.c_int32), ("gain", C.c_float),
+                ("offset", C.c_float), ("sigma", C.c_float), ("seed", C.c_uint64)]
+
+
+class gn_net_desc(C.Structure):
+    _fields_ = [
+        ("n_nodes", C.c_int32), ("dim", C.c_int32), ("pos", C.c_void_p), ("n_edges", C.c_int64),
+        ("src", C.c_void_p), ("dst", C.c_void_p), ("weight", C.c_void_p), ("speed", C.c_void_p),
+        ("speed_scalar", C.c_double), ("delay_steps", C.c_void_p), ("dt_ms", C.c_double),
+        ("fhn", gn_fhn_params), ("obs", gn_obs_params), ("coupling", C.c_int32), ("theta", C.c_double),
+        ("ring_depth", C.c_int32), ("obs_capacity", C.c_int64), ("event_capacity", C.c_int64),
+        ("renumber", C.c_int32), ("edge_format", C.c_int32), ("cuda_stream", C.c_void_p), ("device", C.c_int32),
+    ]
+
+
+class gn_pulse(C.Structure):
+    _fields_ = [("node", C.c_int32), ("t_on_ms", C.c_double), ("t_off_ms", C.c_double), ("amp", C.c_float)]
+
+
+class gn_net_info(C.Structure):
+    _fields_ = [
+        ("n_nodes", C.c_int32), ("n_edges", C.c_int64), ("dim", C.c_int32), ("ring_depth", C.c_int32),
+        ("max_delay", C.c_int32), ("min_delay", C.c_int32), ("n_clamped", C.c_int64),
+        ("edge_format", C.c_int32), ("n_blocks", C.c_int32), ("step", C.c_int64), ("samples", C.c_int64),
+        ("v_rest", C.c_double), ("w_rest", C.c_double), ("device_bytes", C.c_size_t),
+    ]
+
+
+_P = C.c_void_p
+_SIGS = {
+    "gn_net_create": ([C.POINTER(gn_net_desc), C.POINTER(C.c_void_p)], C.c_int),
+    "gn_net_destroy": ([_P], C.c_int),
+    "gn_net_get_info": ([_P, C.POINTER(gn_net_info)], C.c_int),
+    "gn_get_delays": ([_P, _P], C.c_int),
+    "gn_get_rest": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
+    "gn_set_stimulus": ([_P, C.POINTER(gn_pulse), C.c_int32], C.c_int),
+    "gn_set_background": ([_P, C.c_double, C.c_float, C.c_double, C.c_uint64], C.c_int),
+    "gn_step": ([_P, C.c_int64], C.c_int),
+    "gn_synchronize": ([_P], C.c_int),
+    "gn_observe": ([_P, _P, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int64)], C.c_int),
+    "gn_get_state": ([_P, _P, _P, _P, _P, C.POINTER(C.c_int64)], C.c_int),
+    "gn_get_history": ([_P, _P, C.c_int32], C.c_int),
+    "gn_set_state": ([_P, _P, C.c_int32, _P, _P, _P, C.c_int64], C.c_int),
+    "gn_get_arrivals": ([_P, _P], C.c_int),
+    "gn_get_events": ([_P, _P, _P, C.c_int64, C.POINTER(C.c_int64)], C.c_int),
+    "gn_save_state": ([_P, _P, C.c_size_t, C.POINTER(C.c_size_t)], C.c_int),
+    "gn_load_state": ([_P, _P, C.c_size_t], C.c_int),
+    "gn_last_error": ([], C.c_char_p),
+}
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_0908_3934_b300.build`")
+        L = C.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def check(status: int, allow=()):
+    if status != GN_OK and status not in allow:
+        raise GeonetError(status, lib().gn_last_error().decode())
+    return status
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _c(a, dt):
+    return None if a is None else np.ascontiguousarray(a, dtype=dt)
+
+
+class Net:
+    """One network on the GPU, created from a ``netgen.NetSpec``-like object."""
+
+    def __init__(self, spec, *, device: int = 0, stream=None, obs_capacity: int = 0,
+                 event_capacity: int = 0, renumber: bool = True, ring_depth: int | None = None,
+                 coupling: str | None = None, wide_edges: bool = False):
+        L = lib()
+        self._keep = dict(pos=_c(spec.pos, np.float64), src=_c(spec.src, np.int32), dst=_c(spec.dst, np.int32),
+                          weight=_c(spec.weight, np.float32), speed=_c(spec.speed, np.float64),
+                          delay=_c(spec.delay, np.int32))
+        k = self._keep
+        fhn = spec.fhn
+        obs = spec.obs
+        cpl = coupling or spec.coupling
+        d = gn_net_desc(
+            n_nodes=spec.n_nodes, dim=spec.dim, pos=_ptr(k["pos"]), n_edges=spec.n_edges,
+            src=_ptr(k["src"]), dst=_ptr(k["dst"]), weight=_ptr(k["weight"]), speed=_ptr(k["speed"]),
+            speed_scalar=float(spec.speed_scalar or 0.0), delay_steps=_ptr(k["delay"]), dt_ms=spec.dt_ms,
+            fhn=gn_fhn_params(**{x: fhn[x] for x in ("a", "b", "c", "e", "f", "g", "i_ext")}),
+            obs=gn_obs_params(tau_ms=obs["tau_ms"], sample_every=obs["sample_every"], gain=obs["gain"],
+                              offset=obs["offset"], sigma=obs["sigma"], seed=obs["seed"]),
+            coupling=GN_COUPLE_RAW if cpl == "raw" else GN_COUPLE_REST, theta=spec.theta,
+            ring_depth=spec.ring_depth if ring_depth is None else ring_depth,
+            obs_capacity=obs_capacity, event_capacity=event_capacity, renumber=0 if renumber else -1,
+            edge_format=1 if wide_edges else 0,
+            cuda_stream=stream, device=device)
+        h = C.c_void_p()
+        check(L.gn_net_create(C.byref(d), C.byref(h)))
+        self.h = h
+        self.n_nodes = spec.n_nodes
+        self.n_edges = spec.n_edges
+        self.spec = spec
+        del self._keep
+        if spec.pulses:
+            self.gn_set_stimulus(spec.pulses)
+        bg = spec.background
+        if bg:
+            self.gn_set_background(bg["rate_hz"], bg["amp"], bg["dur_ms"], bg["seed"])
+
+    # ---- the C ABI, one method per call ----
+    def gn_net_destroy(self):
+        if getattr(self, "h", None):
+            check(lib().gn_net_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.gn_net_destroy()
+        except Exception:
+            pass
+
+    def gn_net_get_info(self) -> dict:
+        i = gn_net_info()
+        check(lib().gn_net_get_info(self.h, C.byref(i)))
+        return {f: getattr(i, f) for f, _ in gn_net_info._fields_}
+
+    def gn_get_delays(self) -> np.ndarray:
+        out = np.zeros(self.n_edges, np.int32)
+        check(lib().gn_get_delays(self.h, _ptr(out)))
+        return out
+
+    def gn_get_rest(self):
+        v, w = C.c_double(), C.c_double()
+        check(lib().gn_get_rest(self.h, C.byref(v), C.byref(w)))
+        return v.value, w.value
+
+    def gn_set_stimulus(self, pulses):
+        arr = (gn_pulse * max(1, len(pulses)))()
+        for i, (node, t_on, t_off, amp) in enumerate(pulses):
+            arr[i] = gn_pulse(node=node, t_on_ms=t_on, t_off_ms=t_off, amp=amp)
+        check(lib().gn_set_stimulus(self.h, arr, len(pulses)))
+
+    def gn_set_background(self, rate_hz, amp, dur_ms, seed):
+        check(lib().gn_set_background(self.h, rate_hz, amp, dur_ms, seed))
+
+    def gn_step(self, n_steps: int):
+        check(lib().gn_step(self.h, n_steps))
+
+    def gn_synchronize(self):
+        check(lib().gn_synchronize(self.h))
+
+    def gn_observe(self, max_samples: int | None = None, out: np.ndarray | None = None,
+                   discard: bool = False):
+        """Unread observation rows [k, n_nodes] (caller order), the number of the
+        first, and the status (GN_OK or GN_EOVERFLOW)."""
+        info = self.gn_net_get_info()
+        if max_samples is None:
+            max_samples = info["samples"]
+        if out is None and not discard:
+            out = np.zeros((max(0, max_samples), self.n_nodes), np.float32)
+        first = C.c_int64()
+        wr = C.c_int64()
+        st = check(lib().gn_observe(self.h, None if discard else _ptr(out), max_samples, C.byref(first),
+                                    C.byref(wr)), allow=(GN_EOVERFLOW,))
+        return (None if discard else out[: wr.value]), first.value, st
+
+    def gn_get_state(self):
+        N = self.n_nodes
+        v, w, c = (np.zeros(N, np.float32) for _ in range(3))
+        bg = np.zeros(N, np.int32)
+        st = C.c_int64()
+        check(lib().gn_get_state(self.h, _ptr(v), _ptr(w), _ptr(c), _ptr(bg), C.byref(st)))
+        return dict(v=v, w=w, c=c, bg_count=bg, step=st.value)
+
+    def gn_set_state(self, hist, w=None, c=None, bg_count=None, step: int = 0):
+        hist = np.ascontiguousarray(hist, np.float32)
+        w, c = _c(w, np.float32), _c(c, np.float32)
+        bg = _c(bg_count, np.int32)
+        check(lib().gn_set_state(self.h, _ptr(hist), hist.shape[0], _ptr(w), _ptr(c), _ptr(bg), step))
+
+    def gn_get_history(self, depth: int) -> np.ndarray:
+        out = np.zeros((depth, self.n_nodes), np.float32)
+        check(lib().gn_get_history(self.h, _ptr(out), depth))
+        return out
+
+    def gn_get_arrivals(self) -> np.ndarray:
+        out = np.zeros(self.n_nodes, np.int64)
+        check(lib().gn_get_arrivals(self.h, _ptr(out)))
+        return out
+
+    def gn_get_events(self, cap: int = 1 << 22):
+        node = np.zeros(cap, np.int32)
+        step = np.zeros(cap, np.int64)
+        n = C.c_int64()
+        st = check(lib().gn_get_events(self.h, _ptr(node), _ptr(step), cap, C.byref(n)), allow=(GN_EOVERFLOW,))
+        m = min(cap, n.value)
+        return node[:m], step[:m], st
+
+    def gn_save_state(self) -> bytes:
+        used = C.c_size_t()
+        check(lib().gn_save_state(self.h, None, 0, C.byref(used)))
+        buf = (C.c_uint8 * used.value)()
+        check(lib().gn_save_state(self.h, buf, used.value, C.byref(used)))
+        return bytes(buf)
+
+    def gn_load_state(self, blob: bytes):
+        buf = (C.c_uint8 * len(blob)).from_buffer_copy(blob)
+        check(lib().gn_load_state(self.h, buf, len(blob)))
+
+
+def exported_symbols() -> list:
+    """Names of the gn_* functions declared in include/*.h."""
+    import glob
+    import re
+    names = []
+    for h in glob.glob(os.path.join(os.path.dirname(_HERE), "include", "*.h")):
+        names += re.findall(r"^\s*GN_API\s+(?:gn_status|const char \*)\s*(gn_\w+)\s*\(", open(h).read(), re.M)
+    return sorted(set(names))

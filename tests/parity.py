@@ -1,0 +1,84 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path and the FP64 oracle
+on the same seeded network and compare them.
+
+Tolerance (floating point): |gpu - oracle| <= max(1e-4 |oracle|, 1e-6) elementwise
+on v~, w~, c~ and y.  The oracle runs its own uninterrupted FP64 trajectory; at the
+start of every window of `window` steps (default one observation interval,
+20 steps = 1 ms) the GPU is loaded with the oracle's state rounded to FP32
+(gn_set_state) and its next `window` steps are compared with the oracle's.  Data
+flows only from the oracle to the GPU.  Windows are needed because the excitable
+dynamics amplify rounding: an FP32 emulation that changes nothing but the
+summation order of S drifts 3e-4 away from FP64 over 200 ms, so a comparison
+without windows measures the conditioning of the network, not the arithmetic of
+the step (the unwindowed drift is reported by its own test).
+
+Integers (delays, arrivals, background counters, events) must match exactly; an
+event may differ only where the oracle's V is within 1e-5 of the threshold at the
+crossing, where FP32 cannot decide it.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+
+REL, ABS = 1e-4, 1e-6
+EVENT_MARGIN = 1e-5
+
+
+def ratio(gpu, ref):
+    """Largest |gpu - ref| / max(REL |ref|, ABS); <= 1 passes."""
+    gpu = np.asarray(gpu, np.float64)
+    ref = np.asarray(ref, np.float64)
+    if gpu.size == 0:
+        return 0.0
+    return float(np.max(np.abs(gpu - ref) / np.maximum(REL * np.abs(ref), ABS)))
+
+
+def windowed(spec, net, n_steps, window=20, start=0, coupling=None):
+    """Compare `net` with the oracle over steps [start, start + n_steps) window by
+    window.  Returns the worst ratio per quantity and the number of oracle events;
+    raises AssertionError on an integer mismatch."""
+    D = oracle.net_delays(spec)
+    depth = int(D.max(initial=1)) + 1
+    ref = oracle.simulate(spec, start, coupling=coupling, hist_depth=depth, want_y=False)
+    vr = ref["rest"][0]
+    worst = dict(v=0.0, w=0.0, c=0.0, y=0.0)
+    n_events = 0
+    n0 = start
+    end = start + n_steps
+    while n0 < end:
+        K = min(window, end - n0)
+        net.gn_set_state(ref["hist"].astype(np.float32), ref["w"].astype(np.float32),
+                         ref["c"].astype(np.float32), ref["bg_count"], n0)
+        nxt = oracle.simulate(spec, K, coupling=coupling, hist_depth=depth, snap_every=1,
+                              init=dict(n0=n0, v=ref["v"], w=ref["w"], c=ref["c"], bg_count=ref["bg_count"],
+                                        hist=ref["hist"]))
+        net.gn_step(K)
+        g = net.gn_get_state()
+        y, _, _ = net.gn_observe()
+        for k in ("v", "w", "c"):
+            worst[k] = max(worst[k], ratio(g[k], nxt[k]))
+        if nxt["y"].shape[0]:
+            assert y.shape == nxt["y"].shape
+            worst["y"] = max(worst["y"], ratio(y, nxt["y"]))
+        assert np.array_equal(g["bg_count"], nxt["bg_count"]), f"background counters differ in [{n0}, {n0 + K})"
+        # events of the window; mismatches only where V sits on the threshold
+        V = vr + np.vstack([ref["v"][None, :], nxt["snap_v"]])
+        near = (np.abs(V[:-1]) < EVENT_MARGIN) | (np.abs(V[1:]) < EVENT_MARGIN)
+        t, j = np.nonzero(near)
+        excused = set(zip(j.tolist(), (n0 + t + 1).tolist()))
+        node, step, _ = net.gn_get_events()
+        got = set(zip(node.tolist(), step.tolist()))
+        want = set(zip(nxt["ev_node"].tolist(), nxt["ev_step"].tolist()))
+        bad = [e for e in got ^ want if e not in excused]
+        assert not bad, f"events differ in [{n0}, {n0 + K}): {bad[:5]}"
+        n_events += len(want)
+        ref = nxt
+        n0 += K
+    return worst, n_events
+
+
+def assert_windows(worst):
+    for k, r in worst.items():
+        assert r <= 1.0, f"{k}: {r:.3g} x tolerance"

@@ -1,0 +1,270 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (libgeonet.so).
+
+Integers are compared bit for bit; floating point within the tolerance stated in
+tests/parity.py (1e-4 relative, 1e-6 absolute, oracle re-synchronised every
+1 ms of simulated time)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0908_3934_b300 import netgen
+
+from parity import assert_windows, ratio, windowed
+
+pytestmark = pytest.mark.gpu
+
+
+def Net(spec, **kw):
+    from paper_0908_3934_b300 import geonet
+    return geonet.Net(spec, **kw)
+
+
+# ------------------------------------------------------------------ integers
+def test_delays_bit_exact_tiny_and_fig2():
+    spec = netgen.tiny()
+    net = Net(spec)
+    assert np.array_equal(net.gn_get_delays(), oracle.net_delays(spec))
+    f = netgen.fig2([72, 148, 76, 52, 96, 68, 72, 88])
+    assert Net(f).gn_get_delays().tolist() == [72, 148, 76, 52, 96, 68, 72, 88]
+
+
+def test_delays_bit_exact_per_edge_speed_3d():
+    spec = netgen.large(n=20000, mean_deg=40)
+    net = Net(spec)
+    D, cl = oracle.delays(spec.pos, spec.src, spec.dst, spec.speed, 0.0, spec.dt_ms)
+    assert np.array_equal(net.gn_get_delays(), D)
+    assert net.gn_net_get_info()["n_clamped"] == int(cl.sum())
+
+
+def test_exact_halves_and_clamp():
+    pos = np.array([[0.0, 0.0], [0.625, 0.0], [0.375, 0.0], [1e-4, 0.0]])
+    spec = netgen.NetSpec(pos=pos, src=np.array([0, 0, 0], np.int32), dst=np.array([1, 2, 3], np.int32),
+                          weight=np.ones(3, np.float32), speed=None, speed_scalar=1.0, dt_ms=0.25)
+    net = Net(spec)
+    assert net.gn_get_delays().tolist() == [3, 2, 1]
+    assert net.gn_net_get_info()["n_clamped"] == 1
+
+
+def test_fig2_arrivals_and_windows():
+    spec = netgen.fig2([72, 148, 76, 52, 96, 68, 72, 88])
+    net = Net(spec)
+    net.gn_step(1000)
+    assert net.gn_get_arrivals().tolist() == [201, 274, 350, 327, 423]
+    worst, _ = windowed(spec, Net(spec), 4000)
+    assert_windows(worst)
+
+
+def test_two_node_chain_arrival():
+    for d, s in [(0.5, 0.1), (0.25, 0.05)]:
+        spec = netgen.chain2(dist_mm=d, speed=s)
+        net = Net(spec)
+        net.gn_step(1000)
+        D = int(round(d / (s * 0.05)))
+        assert net.gn_get_arrivals().tolist() == [101, 101 + D + 1]
+
+
+# ------------------------------------------------------------------ config "tiny"
+def test_tiny_first_200ms_windows():
+    spec = netgen.tiny()
+    worst, n_ev = windowed(spec, Net(spec), 4000)
+    assert_windows(worst)
+    assert n_ev > 20
+
+
+def test_tiny_arrivals_and_early_events_bit_exact():
+    """Uninterrupted run from rest: every first arrival whose value is an FP32
+    normal number, and the events of the first 40 ms, match the oracle exactly."""
+    spec = netgen.tiny()
+    net = Net(spec)
+    net.gn_step(4000)
+    ref = oracle.simulate(spec, 4000)
+    fa = net.gn_get_arrivals()
+    ok = ref["first_arrival"] >= 0
+    normal = np.abs(ref["first_value"]) >= 2.0 ** -126
+    assert np.array_equal(fa[ok & normal], ref["first_arrival"][ok & normal])
+    assert np.all(fa[~ok] == -1)
+    node, step, _ = net.gn_get_events()
+    got = sorted((int(s), int(j)) for j, s in zip(node, step) if s <= 800)
+    want = sorted((int(s), int(j)) for j, s in zip(ref["ev_node"], ref["ev_step"]) if s <= 800)
+    assert got == want and len(want) > 0
+
+
+def test_tiny_full_horizon_runs_and_reports_drift():
+    """1000 ms without re-synchronisation: arrivals exact; the drift of the traces
+    is bounded by the conditioning of the network (see tests/parity.py)."""
+    spec = netgen.tiny()
+    net = Net(spec)
+    net.gn_step(20000)
+    ref = oracle.simulate(spec, 20000)
+    y, first, _ = net.gn_observe()
+    assert first == 0 and y.shape == ref["y"].shape
+    fa = net.gn_get_arrivals()
+    ok = (ref["first_arrival"] >= 0) & (np.abs(ref["first_value"]) >= 2.0 ** -126)
+    assert np.array_equal(fa[ok], ref["first_arrival"][ok])
+    # first 200 ms of the noisy observations, per-trace max-norm relative error
+    d = np.abs(y[:200] - ref["y"][:200]).max(0) / np.abs(ref["y"][:200]).max(0)
+    assert d.max() < 3e-3
+
+
+def test_unstimulated_network_stays_exactly_at_rest():
+    spec = netgen.tiny()
+    spec.pulses = []
+    net = Net(spec)
+    net.gn_step(3000)
+    st = net.gn_get_state()
+    assert not st["v"].any() and not st["w"].any() and not st["c"].any()
+    assert (net.gn_get_arrivals() == -1).all()
+    assert net.gn_get_events()[0].size == 0
+
+
+def test_zero_weights_windows():
+    spec = netgen.tiny()
+    spec.weight = np.zeros_like(spec.weight)
+    net = Net(spec)
+    worst, _ = windowed(spec, net, 2000)
+    assert_windows(worst)
+    st = net.gn_get_state()
+    assert not st["v"][1:].any()
+
+
+def test_raw_coupling_windows():
+    spec = netgen.tiny()
+    net = Net(spec, coupling="raw")
+    worst, _ = windowed(spec, net, 2000, coupling="raw")
+    assert_windows(worst)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_random_small_nets_windows(seed):
+    spec = netgen.random_small(seed, n=40, p_edge=0.2)
+    net = Net(spec)
+    worst, _ = windowed(spec, net, 1500)
+    assert_windows(worst)
+
+
+# ------------------------------------------------------------------ layouts and edge cases
+def test_wide_edge_format_and_caller_order():
+    spec = netgen.tiny()
+    for kw in (dict(wide_edges=True), dict(renumber=False), dict(wide_edges=True, renumber=False)):
+        net = Net(spec, **kw)
+        worst, _ = windowed(spec, net, 600)
+        assert_windows(worst)
+        assert net.gn_net_get_info()["edge_format"] == (1 if kw.get("wide_edges") else 0)
+
+
+def test_long_rows_take_the_whole_block_path():
+    """A hub with in-degree 5000 (> one block's edge capacity) and ragged rows."""
+    rng = np.random.default_rng(9)
+    n = 6000
+    pos = rng.random((n, 2))
+    src = np.concatenate([np.arange(1, 5001), rng.integers(0, n, 3000)]).astype(np.int32)
+    dst = np.concatenate([np.zeros(5000, np.int64), rng.integers(0, n, 3000)]).astype(np.int32)
+    keep = src != dst
+    src, dst = src[keep], dst[keep]
+    w = rng.uniform(-0.2, 0.4, src.size).astype(np.float32)
+    pulses = [(int(j), 2.0, 4.0, 1.0) for j in rng.choice(np.arange(1, 5001), 200, replace=False)]
+    spec = netgen.NetSpec(pos=pos, src=src, dst=dst, weight=w, speed=None, speed_scalar=0.05, pulses=pulses)
+    net = Net(spec)
+    assert net.gn_net_get_info()["n_blocks"] >= 2
+    worst, _ = windowed(spec, net, 800)
+    assert_windows(worst)
+
+
+def test_no_edges_and_one_node():
+    for n in (1, 37):
+        spec = netgen.NetSpec(pos=np.zeros((n, 3)), src=np.zeros(0, np.int32), dst=np.zeros(0, np.int32),
+                              weight=np.zeros(0, np.float32), speed=None, speed_scalar=1.0,
+                              pulses=[(n - 1, 1.0, 3.0, 1.0)])
+        net = Net(spec)
+        worst, _ = windowed(spec, net, 400)
+        assert_windows(worst)
+
+
+def test_largest_delay_that_fits_the_ring():
+    """D = R - 2 is the largest delay a ring of R slots holds; D = R - 1 is rejected."""
+    from paper_0908_3934_b300 import geonet
+    spec = netgen.fig2([62, 62, 30, 7, 1, 62, 2, 62])
+    net = Net(spec, ring_depth=64)
+    worst, _ = windowed(spec, net, 1200)
+    assert_windows(worst)
+    with pytest.raises(geonet.GeonetError) as e:
+        Net(netgen.fig2([63, 1, 1, 1, 1, 1, 1, 1]), ring_depth=64)
+    assert e.value.status == geonet.GN_ERANGE
+
+
+def test_background_counters_and_arrivals():
+    spec = netgen.large(n=3000, mean_deg=20, bg_rate_hz=200.0)
+    worst, _ = windowed(spec, Net(spec), 1000)
+    assert_windows(worst)
+    net = Net(spec)
+    net.gn_step(1000)
+    ref = oracle.simulate(spec, 1000)
+    ok = (ref["first_arrival"] >= 0) & (np.abs(ref["first_value"]) >= 2.0 ** -126)
+    assert np.array_equal(net.gn_get_arrivals()[ok], ref["first_arrival"][ok])
+    assert np.array_equal(net.gn_get_state()["bg_count"], ref["bg_count"])
+
+
+def test_checkpoint_resume_is_bit_exact():
+    spec = netgen.large(n=3000, mean_deg=20, bg_rate_hz=200.0)
+    a = Net(spec)
+    a.gn_step(777)
+    blob = a.gn_save_state()
+    a.gn_step(777)
+    b = Net(spec)
+    b.gn_load_state(blob)
+    b.gn_step(777)
+    sa, sb = a.gn_get_state(), b.gn_get_state()
+    for k in ("v", "w", "c", "bg_count"):
+        assert np.array_equal(sa[k], sb[k]), k
+    assert sa["step"] == sb["step"] == 1554
+    assert np.array_equal(a.gn_get_history(16), b.gn_get_history(16))
+
+
+def test_observation_overflow_keeps_the_latest():
+    from paper_0908_3934_b300 import geonet
+    spec = netgen.tiny()
+    net = Net(spec, obs_capacity=8)
+    net.gn_step(20 * 20)
+    y, first, st = net.gn_observe()
+    assert st == geonet.GN_EOVERFLOW and first == 12 and y.shape[0] == 8
+    ref = oracle.simulate(spec, 400)
+    assert ratio(y, ref["y"][12:]) <= 1.0
+
+
+def test_event_overflow_is_reported():
+    from paper_0908_3934_b300 import geonet
+    spec = netgen.tiny()
+    net = Net(spec, event_capacity=5)
+    net.gn_step(4000)
+    node, step, st = net.gn_get_events()
+    assert st == geonet.GN_EOVERFLOW and node.size == 5
+
+
+# ------------------------------------------------------------------ full sizes, bench launch configuration
+@pytest.fixture(scope="module")
+def large_spec():
+    return netgen.large()
+
+
+def test_large_full_size_sampled(large_spec):
+    """N = 100,000, ~10M edges, 5 Hz background: delays bit-exact; two 20-step
+    windows after 200 steps, compared on every node."""
+    spec = large_spec
+    net = Net(spec)
+    assert np.array_equal(net.gn_get_delays(), oracle.net_delays(spec))
+    worst, n_ev = windowed(spec, net, 40, start=200)
+    assert_windows(worst)
+
+
+def test_roofline_full_size_sampled():
+    """N = 1,000,000, ~50M edges with 2.5 % hubs of in-degree 1000, ring of 256
+    steps (the benchmark's network): delays bit-exact; one 20-step window after
+    40 steps, compared on every node."""
+    spec = netgen.roofline()
+    net = Net(spec)
+    D = oracle.net_delays(spec)
+    assert np.array_equal(net.gn_get_delays(), D)
+    info = net.gn_net_get_info()
+    assert info["ring_depth"] == 256 and info["edge_format"] == 0
+    worst, _ = windowed(spec, net, 20, start=40)
+    assert_windows(worst)
