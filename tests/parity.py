@@ -52,6 +52,7 @@ def windowed(spec, net, n_steps, window=20, start=0, coupling=None):
         net.gn_set_state(ref["hist"].astype(np.float32), ref["w"].astype(np.float32),
                          ref["c"].astype(np.float32), ref["bg_count"], n0)
         nxt = oracle.simulate(spec, K, coupling=coupling, hist_depth=depth, snap_every=1,
+                              ev_cap=spec.n_nodes * (K // 2 + 1) + 1024,
                               init=dict(n0=n0, v=ref["v"], w=ref["w"], c=ref["c"], bg_count=ref["bg_count"],
                                         hist=ref["hist"]))
         net.gn_step(K)
@@ -70,6 +71,7 @@ def windowed(spec, net, n_steps, window=20, start=0, coupling=None):
         excused = set(zip(j.tolist(), (n0 + t + 1).tolist()))
         node, step, _ = net.gn_get_events()
         got = set(zip(node.tolist(), step.tolist()))
+        assert nxt["ev_count"] == nxt["ev_node"].size, "oracle event buffer too small"
         want = set(zip(nxt["ev_node"].tolist(), nxt["ev_step"].tolist()))
         bad = [e for e in got ^ want if e not in excused]
         assert not bad, f"events differ in [{n0}, {n0 + K}): {bad[:5]}"
