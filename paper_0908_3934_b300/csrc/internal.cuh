@@ -10,7 +10,7 @@ namespace gn {
 // Device arrays and constants of one network, in internal (Morton) node order.
 //
 // HBM layout:
-//   ring   float [R][N]  slot-major history: slot s holds v~ at the latest step
+//   ring   float [R][ring_stride]  slot-major history: slot s holds v~ at the latest step
 //                        t == s (mod R) that is <= the current step; the current
 //                        state v~(n) is slot n & (R-1) (the ring *is* the state).
 //   wc     float2 [N]    (w~, c~)
@@ -22,6 +22,7 @@ namespace gn {
 //   start inside [0, E) never leave the allocation.
 struct StepArgs {
     int32_t N;
+    int32_t ring_stride;     // floats per ring slot: N rounded up (N + 4 -> multiple of 32)
     int32_t ring_mask;       // R - 1
     int32_t dbits;           // packed keys: bits of D
     const void *ekey;
@@ -59,7 +60,13 @@ struct StepArgs {
     unsigned long long *ev_count;
     int64_t ev_cap;
     const int64_t *d_step;   // step counter: a launch with offset k runs step *d_step + k
+    // persistent pipelined kernel
+    const int4 *bdesc;       // [n_blocks] {first row, end row, first edge, end edge}
+    int32_t n_blocks;
+    unsigned int *status;    // device error word (kStatus* bits), read by the host after a sync
 };
+
+constexpr unsigned int kStatusTimeout = 1u;  // a bounded mbarrier wait gave up
 
 constexpr int kEdgePad = 4096;
 
@@ -73,6 +80,10 @@ constexpr int kStepMaxRows = kStepThreads;
 cudaError_t launch_step(const StepArgs &a, int n_blocks, int k, bool packed, bool stream_edges,
                         cudaStream_t s);
 cudaError_t launch_advance(int64_t *d_step, int64_t by, cudaStream_t s);
+// persistent bulk-copy pipelined variant (k_step_pipe.cu); grid = CTAs to launch
+cudaError_t launch_step_pipe(const StepArgs &a, int grid, int k, bool packed, bool stream_edges, cudaStream_t s);
+int step_pipe_smem_bytes(bool packed);
+cudaError_t step_pipe_prepare(bool packed, bool stream_edges, int *ctas_per_sm);
 cudaError_t launch_delay(int64_t n_edges, int32_t dim, const double *pos, const int32_t *src,
                          const int32_t *dst, const double *speed, double speed_scalar, double dt_ms,
                          int32_t *delay, uint8_t *clamped, cudaStream_t s);

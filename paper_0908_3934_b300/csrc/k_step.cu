@@ -16,126 +16,12 @@
 // The kernel boundary is the step barrier: every read is of step n (or older),
 // every write is of step n + 1, and slot (n + 1) & (R - 1) is never read in step n
 // because every delay is at most R - 2.
-#include "internal.cuh"
-#include "philox.cuh"
+#include "step_common.cuh"
 
 namespace gn {
 namespace {
 
-template <bool kStream>
-__device__ __forceinline__ uint4 ld_edge4(const void *p)
-{
-    if constexpr (kStream)
-        return __ldcs(reinterpret_cast<const uint4 *>(p));
-    else
-        return __ldg(reinterpret_cast<const uint4 *>(p));
-}
-
-template <bool kStream>
-__device__ __forceinline__ float4 ld_weight4(const float *p)
-{
-    if constexpr (kStream)
-        return __ldcs(reinterpret_cast<const float4 *>(p));
-    else
-        return __ldg(reinterpret_cast<const float4 *>(p));
-}
-
-__device__ __forceinline__ float warp_sum(float x)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
-}
-
-// Edge e's source and delay from its packed or wide key.
-template <bool kPacked>
-struct EdgeQuad {
-    uint32_t src[4], d[4];
-};
-
-template <bool kPacked, bool kStream>
-__device__ __forceinline__ EdgeQuad<kPacked> load_quad(const StepArgs &a, int64_t eb)
-{
-    EdgeQuad<kPacked> q;
-    if constexpr (kPacked) {
-        const uint4 k = ld_edge4<kStream>(static_cast<const uint32_t *>(a.ekey) + eb);
-        const uint32_t m = (1u << a.dbits) - 1u;
-        const uint32_t kk[4] = {k.x, k.y, k.z, k.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            q.src[i] = kk[i] >> a.dbits;
-            q.d[i] = kk[i] & m;
-        }
-    } else {
-        const uint2 *base = static_cast<const uint2 *>(a.ekey) + eb;
-        const uint4 k0 = ld_edge4<kStream>(base);
-        const uint4 k1 = ld_edge4<kStream>(base + 2);
-        q.src[0] = k0.x; q.d[0] = k0.y; q.src[1] = k0.z; q.d[1] = k0.w;
-        q.src[2] = k1.x; q.d[2] = k1.y; q.src[3] = k1.z; q.d[3] = k1.w;
-    }
-    return q;
-}
-
-__device__ __forceinline__ float gather(const StepArgs &a, int64_t n, uint32_t src, uint32_t d)
-{
-    const int64_t slot = (n - static_cast<int64_t>(d)) & a.ring_mask;
-    return __ldg(a.ring + slot * a.N + src);
-}
-
-// Stimulus, FHN Euler step, history write, readout, noise, events, arrival.
-__device__ __forceinline__ void node_update(const StepArgs &a, int r, int64_t n, float v, float2 wc, float S)
-{
-    float U = 0.0f;
-    const int n_pulses = *a.n_pulses;
-    if (n_pulses > 0) {
-        int lo = 0, hi = n_pulses;  // first pulse with p_node >= r
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (a.p_node[mid] < r) lo = mid + 1; else hi = mid;
-        }
-        for (int p = lo; p < n_pulses && a.p_node[p] == r; ++p)
-            if (a.p_on[p] <= n && n < a.p_off[p]) U += a.p_amp[p];
-    }
-    int32_t orig = -1;
-    if (a.bg_thr) {
-        orig = __ldg(a.perm + r);
-        const int32_t c0 = a.bgc[r];
-        int32_t cnt = c0;
-        if (draw(a.bg_seed, static_cast<uint32_t>(orig), n, kStreamBackground).x < a.bg_thr) cnt = a.bg_width;
-        if (cnt > 0) {
-            U += a.bg_amp;
-            cnt -= 1;
-        }
-        if (cnt != c0) a.bgc[r] = cnt;
-    }
-    if (a.bias) S += __ldg(a.bias + r);
-
-    const float w = wc.x, c = wc.y;
-    const float dv = fmaf(v, fmaf(v, fmaf(a.q3, v, a.q2), a.k1), -a.cw * w) + S + U;
-    const float v1 = fmaf(a.dt, dv, v);
-    const float w1 = fmaf(a.dte, fmaf(-a.g, w, v), w);
-    const float c1 = fmaf(a.alpha, v1 - c, c);
-
-    a.ring[((n + 1) & a.ring_mask) * a.N + r] = v1;
-    a.wc[r] = make_float2(w1, c1);
-
-    if (v < a.theta_s && v1 >= a.theta_s) {
-        const unsigned long long i = atomicAdd(a.ev_count, 1ull);
-        if (i < static_cast<unsigned long long>(a.ev_cap)) {
-            a.ev_node[i] = r;
-            a.ev_step[i] = n + 1;
-        }
-    }
-    if (v1 != 0.0f && v == 0.0f && a.first[r] < 0) a.first[r] = n + 1;
-
-    if (((n + 1) % a.sample_every) == 0) {
-        const int64_t k = (n + 1) / a.sample_every - 1;
-        if (orig < 0) orig = __ldg(a.perm + r);
-        const float xi = gauss_from(draw(a.obs_seed, static_cast<uint32_t>(orig), k, kStreamObservation));
-        const float y = fmaf(a.gain, a.vrest + c1, a.offset) + a.sigma * xi;
-        a.obs[(k % a.obs_cap) * a.N + orig] = y;  // rows are written in the caller's node order
-    }
-}
+using namespace step;
 
 template <int T, int EPT, bool kPacked, bool kStream>
 __global__ void __launch_bounds__(T) k_step(const StepArgs a, const int k)
@@ -156,7 +42,7 @@ __global__ void __launch_bounds__(T) k_step(const StepArgs a, const int k)
     float v = 0.0f;
     float2 wc = make_float2(0.0f, 0.0f);
     if (t < nr) {
-        v = a.ring[(n & a.ring_mask) * a.N + r];
+        v = a.ring[(n & a.ring_mask) * a.ring_stride + r];
         wc = a.wc[r];
         s_rp[t] = a.row_ptr[r];
     }

@@ -124,6 +124,9 @@ struct gn_net {
     bool packed = true;
     bool stream_edges = true;
     int n_blocks = 0;
+    int step_kernel = 0;       // 0 persistent pipelined, 1 row block per CTA
+    int grid = 0;              // CTAs per launch
+    int32_t stride = 0;        // ring slot stride (floats)
     double v_rest = 0.0, w_rest = 0.0, dt = 0.0;
     int32_t sample_every = 1;
     int64_t obs_cap = 0, ev_cap = 0;
@@ -139,6 +142,8 @@ struct gn_net {
     int64_t pulse_cap = 0;
     DevArray<int64_t> first, p_on, p_off, ev_step, d_step;
     DevArray<unsigned long long> ev_count;
+    DevArray<int4> bdesc;
+    DevArray<unsigned int> status;
     gn::StepArgs args{};
     std::vector<uint8_t> stage_pulses;
     cudaGraphExec_t graph = nullptr;
@@ -153,6 +158,8 @@ struct gn_net {
         for (auto *a : {&row_ptr, &blk, &bgc, &d_perm, &p_node, &ev_node, &d_npulses}) a->release();
         for (auto *a : {&first, &p_on, &p_off, &ev_step, &d_step}) a->release();
         ev_count.release();
+        bdesc.release();
+        status.release();
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 };
@@ -162,6 +169,19 @@ namespace {
 void sync(gn_net *net)
 {
     cuda_check(cudaStreamSynchronize(net->stream), "kernel execution");
+    unsigned int st = 0;
+    cuda_check(cudaMemcpy(&st, net->status.p, 4, cudaMemcpyDeviceToHost), "D2H status");
+    if (st) {
+        cudaMemset(net->status.p, 0, 4);
+        if (st & gn::kStatusTimeout) fail(GN_ETIMEOUT, "a bounded device-side wait gave up (status %u)", st);
+        fail(GN_EINTERNAL, "device status word %u", st);
+    }
+}
+
+cudaError_t launch_one(const gn_net *net, int k, cudaStream_t s)
+{
+    if (net->step_kernel == 0) return gn::launch_step_pipe(net->args, net->grid, k, net->packed, net->stream_edges, s);
+    return gn::launch_step(net->args, net->n_blocks, k, net->packed, net->stream_edges, s);
 }
 
 template <class F>
@@ -192,8 +212,7 @@ void build_graph(gn_net *net)
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k)
-            e = gn::launch_step(net->args, net->n_blocks, k, net->packed, net->stream_edges, cs);
+        for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) e = launch_one(net, k, cs);
         if (e == cudaSuccess) e = gn::launch_advance(net->d_step.p, kGraphSteps, cs);
         cudaError_t e2 = cudaStreamEndCapture(cs, &g);
         if (e == cudaSuccess) e = e2;
@@ -220,6 +239,7 @@ void validate_desc(const gn_net_desc *d)
     if (d->coupling != GN_COUPLE_REST && d->coupling != GN_COUPLE_RAW) fail(GN_EINVAL, "unknown coupling");
     if (d->ring_depth < 0 || (d->ring_depth & (d->ring_depth - 1))) fail(GN_EINVAL, "ring_depth must be a power of two");
     if (d->edge_format != 0 && d->edge_format != 1) fail(GN_EINVAL, "edge_format must be 0 or 1");
+    if (d->step_kernel != 0 && d->step_kernel != 1) fail(GN_EINVAL, "step_kernel must be 0 or 1");
     const int64_t np = static_cast<int64_t>(d->n_nodes) * d->dim;
     for (int64_t i = 0; i < np; ++i)
         if (!std::isfinite(d->pos[i])) fail(GN_EINVAL, "position %lld is not finite", (long long)i);
@@ -369,9 +389,10 @@ void build_csr(gn_net *net, const gn_net_desc *d)
     }
     net->ew.alloc(Ep, &net->bytes);
     cuda_check(cudaMemcpy(net->ew.p, w.data(), Ep * 4, cudaMemcpyHostToDevice), "H2D weights");
-    net->row_ptr.alloc(static_cast<size_t>(N) + 1, &net->bytes);
-    cuda_check(cudaMemcpy(net->row_ptr.p, row_ptr.data(), (static_cast<size_t>(N) + 1) * 4, cudaMemcpyHostToDevice),
-               "H2D row_ptr");
+    // padded so 16-byte bulk copies of row_ptr[r0 & ~3 .. (r1 + 4) & ~3) stay inside
+    row_ptr.resize(static_cast<size_t>(N) + 1 + 8, row_ptr[N]);
+    net->row_ptr.alloc(row_ptr.size(), &net->bytes);
+    cuda_check(cudaMemcpy(net->row_ptr.p, row_ptr.data(), row_ptr.size() * 4, cudaMemcpyHostToDevice), "H2D row_ptr");
 
     // row blocks: consecutive rows with at most kStepCap - 3 edges and kStepMaxRows rows;
     // a longer row gets a block of its own
@@ -397,6 +418,11 @@ void build_csr(gn_net *net, const gn_net_desc *d)
     net->n_blocks = static_cast<int>(blk.size()) - 1;
     net->blk.alloc(blk.size(), &net->bytes);
     cuda_check(cudaMemcpy(net->blk.p, blk.data(), blk.size() * 4, cudaMemcpyHostToDevice), "H2D blocks");
+    std::vector<int4> desc(net->n_blocks);
+    for (int b = 0; b < net->n_blocks; ++b) desc[b] = make_int4(blk[b], blk[b + 1], row_ptr[blk[b]], row_ptr[blk[b + 1]]);
+    net->bdesc.alloc(desc.size(), &net->bytes);
+    if (!desc.empty())
+        cuda_check(cudaMemcpy(net->bdesc.p, desc.data(), desc.size() * sizeof(int4), cudaMemcpyHostToDevice), "H2D desc");
 }
 
 // Replace the pulse table: validated and sorted by internal node on the host, then
@@ -538,8 +564,11 @@ gn_status gn_net_create(const gn_net_desc *desc, gn_net **out)
         net->stream_edges = edge_bytes > 48e6;
 
         const int32_t N = net->N;
-        net->ring.alloc(static_cast<size_t>(R) * N, &net->bytes);
-        net->wc.alloc(N, &net->bytes);
+        net->stride = ((N + 4) + 31) / 32 * 32;
+        net->ring.alloc(static_cast<size_t>(R) * net->stride, &net->bytes);
+        net->wc.alloc(static_cast<size_t>(N) + 2, &net->bytes);
+        net->status.alloc(1, &net->bytes);
+        cuda_check(cudaMemset(net->status.p, 0, 4), "memset");
         net->bgc.alloc(N, &net->bytes);
         net->first.alloc(N, &net->bytes);
         net->d_perm.alloc(N, &net->bytes);
@@ -563,7 +592,11 @@ gn_status gn_net_create(const gn_net_desc *desc, gn_net **out)
 
         gn::StepArgs &a = net->args;
         a.N = N;
+        a.ring_stride = net->stride;
         a.ring_mask = R - 1;
+        a.bdesc = net->bdesc.p;
+        a.n_blocks = net->n_blocks;
+        a.status = net->status.p;
         a.dbits = net->dbits;
         a.ekey = net->ekey.p;
         a.ew = net->ew.p;
@@ -600,6 +633,16 @@ gn_status gn_net_create(const gn_net_desc *desc, gn_net **out)
         a.ev_count = net->ev_count.p;
         a.ev_cap = net->ev_cap;
         a.d_step = net->d_step.p;
+        net->step_kernel = desc->step_kernel;
+        if (net->step_kernel == 0) {
+            int per_sm = 0, sms = 0;
+            cuda_check(gn::step_pipe_prepare(net->packed, net->stream_edges, &per_sm), "step kernel setup");
+            cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, desc->device), "device query");
+            if (per_sm < 1) fail(GN_ECUDA, "the pipelined step kernel does not fit on an SM");
+            net->grid = std::min(net->n_blocks, per_sm * sms);
+        } else {
+            net->grid = net->n_blocks;
+        }
         cuda_check(cudaDeviceSynchronize(), "create");
     });
     if (st != GN_OK) {
@@ -634,6 +677,8 @@ gn_status gn_net_get_info(const gn_net *net, gn_net_info *info)
         info->n_clamped = net->n_clamped;
         info->edge_format = net->packed ? 0 : 1;
         info->n_blocks = net->n_blocks;
+        info->step_kernel = net->step_kernel;
+        info->grid = net->grid;
         info->step = net->step;
         info->samples = net->step / net->sample_every;
         info->v_rest = net->v_rest;
@@ -706,9 +751,7 @@ gn_status gn_step(gn_net *net, int64_t n_steps)
             left -= kGraphSteps;
         }
         for (int64_t k = 0; k < left; ++k)
-            cuda_check(gn::launch_step(net->args, net->n_blocks, static_cast<int>(k), net->packed,
-                                       net->stream_edges, net->stream),
-                       "step launch");
+            cuda_check(launch_one(net, static_cast<int>(k), net->stream), "step launch");
         if (left) cuda_check(gn::launch_advance(net->d_step.p, left, net->stream), "advance launch");
         net->step += n_steps;
     });
@@ -765,7 +808,9 @@ gn_status gn_get_state(gn_net *net, float *v, float *w, float *c, int32_t *bg_co
         const int32_t N = net->N;
         std::vector<float> tmp(N);
         if (v) {
-            cuda_check(cudaMemcpy(tmp.data(), net->ring.p + (net->step & (net->R - 1)) * N, N * 4, cudaMemcpyDeviceToHost), "D2H v");
+            cuda_check(cudaMemcpy(tmp.data(), net->ring.p + (net->step & (net->R - 1)) * net->stride, N * 4,
+                                  cudaMemcpyDeviceToHost),
+                       "D2H v");
             permute_rows_to_caller(net, tmp.data(), v, 1);
         }
         if (w || c) {
@@ -796,10 +841,11 @@ gn_status gn_set_state(gn_net *net, const float *hist, int32_t depth, const floa
         sync(net);
         const int32_t N = net->N;
         const size_t R = net->R;
-        std::vector<float> ring(R * N, 0.0f);
+        const size_t stride = net->stride;
+        std::vector<float> ring(R * stride, 0.0f);
         for (int32_t k = 0; k < depth; ++k) {
             const int64_t slot = (step - k) & (net->R - 1);
-            for (int32_t j = 0; j < N; ++j) ring[slot * N + net->inv[j]] = hist[static_cast<int64_t>(k) * N + j];
+            for (int32_t j = 0; j < N; ++j) ring[slot * stride + net->inv[j]] = hist[static_cast<int64_t>(k) * N + j];
         }
         std::vector<float2> wc(N, make_float2(0.0f, 0.0f));
         std::vector<int32_t> bg(N, 0);
@@ -808,7 +854,7 @@ gn_status gn_set_state(gn_net *net, const float *hist, int32_t depth, const floa
             wc[r] = make_float2(w ? w[j] : 0.0f, c ? c[j] : 0.0f);
             if (bg_count) bg[r] = bg_count[j];
         }
-        cuda_check(cudaMemcpy(net->ring.p, ring.data(), R * N * 4, cudaMemcpyHostToDevice), "H2D ring");
+        cuda_check(cudaMemcpy(net->ring.p, ring.data(), R * stride * 4, cudaMemcpyHostToDevice), "H2D ring");
         cuda_check(cudaMemcpy(net->wc.p, wc.data(), N * 8ull, cudaMemcpyHostToDevice), "H2D wc");
         cuda_check(cudaMemcpy(net->bgc.p, bg.data(), N * 4ull, cudaMemcpyHostToDevice), "H2D bg");
         cuda_check(cudaMemset(net->first.p, 0xff, N * 8ull), "memset");
@@ -831,7 +877,8 @@ gn_status gn_get_history(gn_net *net, float *out, int32_t depth)
         std::vector<float> tmp(N);
         for (int32_t k = 0; k < depth; ++k) {
             const int64_t slot = (net->step - k) & (net->R - 1);
-            cuda_check(cudaMemcpy(tmp.data(), net->ring.p + slot * N, N * 4, cudaMemcpyDeviceToHost), "D2H history");
+            cuda_check(cudaMemcpy(tmp.data(), net->ring.p + slot * net->stride, N * 4, cudaMemcpyDeviceToHost),
+                       "D2H history");
             permute_rows_to_caller(net, tmp.data(), out + static_cast<int64_t>(k) * N, 1);
         }
     });
@@ -891,8 +938,8 @@ gn_status gn_save_state(gn_net *net, void *buf, size_t cap, size_t *used)
 {
     return guarded([&] {
         check_net(net);
-        const size_t N = net->N, R = net->R;
-        const size_t need = sizeof(CkptHeader) + R * N * 4 + N * 8 + N * 4 + N * 8;
+        const size_t N = net->N, RS = net->ring.n;
+        const size_t need = sizeof(CkptHeader) + RS * 4 + N * 8 + N * 4 + N * 8;
         if (used) *used = need;
         if (!buf) return;
         if (cap < need) fail(GN_ERANGE, "checkpoint buffer too small (%zu < %zu)", cap, need);
@@ -902,8 +949,8 @@ gn_status gn_save_state(gn_net *net, void *buf, size_t cap, size_t *used)
         CkptHeader h{kCkptMagic, net->N, net->R, net->step};
         std::memcpy(p, &h, sizeof h);
         p += sizeof h;
-        cuda_check(cudaMemcpy(p, net->ring.p, R * N * 4, cudaMemcpyDeviceToHost), "D2H ring");
-        p += R * N * 4;
+        cuda_check(cudaMemcpy(p, net->ring.p, RS * 4, cudaMemcpyDeviceToHost), "D2H ring");
+        p += RS * 4;
         cuda_check(cudaMemcpy(p, net->wc.p, N * 8, cudaMemcpyDeviceToHost), "D2H wc");
         p += N * 8;
         cuda_check(cudaMemcpy(p, net->bgc.p, N * 4, cudaMemcpyDeviceToHost), "D2H bg");
@@ -917,8 +964,8 @@ gn_status gn_load_state(gn_net *net, const void *buf, size_t size)
     return guarded([&] {
         check_net(net);
         if (!buf) fail(GN_EINVAL, "buf is NULL");
-        const size_t N = net->N, R = net->R;
-        const size_t need = sizeof(CkptHeader) + R * N * 4 + N * 8 + N * 4 + N * 8;
+        const size_t N = net->N, RS = net->ring.n;
+        const size_t need = sizeof(CkptHeader) + RS * 4 + N * 8 + N * 4 + N * 8;
         if (size < need) fail(GN_EINVAL, "checkpoint is truncated");
         CkptHeader h;
         std::memcpy(&h, buf, sizeof h);
@@ -926,8 +973,8 @@ gn_status gn_load_state(gn_net *net, const void *buf, size_t size)
         DeviceGuard dg(net->device);
         sync(net);
         const auto *p = static_cast<const uint8_t *>(buf) + sizeof h;
-        cuda_check(cudaMemcpy(net->ring.p, p, R * N * 4, cudaMemcpyHostToDevice), "H2D ring");
-        p += R * N * 4;
+        cuda_check(cudaMemcpy(net->ring.p, p, RS * 4, cudaMemcpyHostToDevice), "H2D ring");
+        p += RS * 4;
         cuda_check(cudaMemcpy(net->wc.p, p, N * 8, cudaMemcpyHostToDevice), "H2D wc");
         p += N * 8;
         cuda_check(cudaMemcpy(net->bgc.p, p, N * 4, cudaMemcpyHostToDevice), "H2D bg");

@@ -44,7 +44,8 @@ class gn_net_desc(C.Structure):
         ("speed_scalar", C.c_double), ("delay_steps", C.c_void_p), ("dt_ms", C.c_double),
         ("fhn", gn_fhn_params), ("obs", gn_obs_params), ("coupling", C.c_int32), ("theta", C.c_double),
         ("ring_depth", C.c_int32), ("obs_capacity", C.c_int64), ("event_capacity", C.c_int64),
-        ("renumber", C.c_int32), ("edge_format", C.c_int32), ("cuda_stream", C.c_void_p), ("device", C.c_int32),
+        ("renumber", C.c_int32), ("edge_format", C.c_int32), ("step_kernel", C.c_int32),
+        ("cuda_stream", C.c_void_p), ("device", C.c_int32),
     ]
 
 
@@ -56,7 +57,8 @@ class gn_net_info(C.Structure):
     _fields_ = [
         ("n_nodes", C.c_int32), ("n_edges", C.c_int64), ("dim", C.c_int32), ("ring_depth", C.c_int32),
         ("max_delay", C.c_int32), ("min_delay", C.c_int32), ("n_clamped", C.c_int64),
-        ("edge_format", C.c_int32), ("n_blocks", C.c_int32), ("step", C.c_int64), ("samples", C.c_int64),
+        ("edge_format", C.c_int32), ("n_blocks", C.c_int32), ("step_kernel", C.c_int32), ("grid", C.c_int32),
+        ("step", C.c_int64), ("samples", C.c_int64),
         ("v_rest", C.c_double), ("w_rest", C.c_double), ("device_bytes", C.c_size_t),
     ]
 
@@ -120,7 +122,7 @@ class Net:
 
     def __init__(self, spec, *, device: int = 0, stream=None, obs_capacity: int = 0,
                  event_capacity: int = 0, renumber: bool = True, ring_depth: int | None = None,
-                 coupling: str | None = None, wide_edges: bool = False):
+                 coupling: str | None = None, wide_edges: bool = False, step_kernel: int = 0):
         L = lib()
         self._keep = dict(pos=_c(spec.pos, np.float64), src=_c(spec.src, np.int32), dst=_c(spec.dst, np.int32),
                           weight=_c(spec.weight, np.float32), speed=_c(spec.speed, np.float64),
@@ -139,7 +141,7 @@ class Net:
             coupling=GN_COUPLE_RAW if cpl == "raw" else GN_COUPLE_REST, theta=spec.theta,
             ring_depth=spec.ring_depth if ring_depth is None else ring_depth,
             obs_capacity=obs_capacity, event_capacity=event_capacity, renumber=0 if renumber else -1,
-            edge_format=1 if wide_edges else 0,
+            edge_format=1 if wide_edges else 0, step_kernel=step_kernel,
             cuda_stream=stream, device=device)
         h = C.c_void_p()
         check(L.gn_net_create(C.byref(d), C.byref(h)))

@@ -1,6 +1,7 @@
 """The C ABI library loads without a GPU, exports every entry point that
 include/*.h declares, and rejects invalid descriptors before touching the device."""
 import ctypes as C
+import os
 import subprocess
 
 import numpy as np
@@ -32,12 +33,26 @@ def test_only_the_abi_is_exported(L):
     assert ours and all(n.startswith("gn_") for n in ours), ours
 
 
-def test_struct_sizes_match_the_header(L):
-    # natural C layout of the header's structs on x86-64 / aarch64 (LP64)
-    assert C.sizeof(geonet.gn_fhn_params) == 56
-    assert C.sizeof(geonet.gn_obs_params) == 32
-    assert C.sizeof(geonet.gn_pulse) == 32
-    assert C.sizeof(geonet.gn_net_desc) == 232
+def test_struct_layouts_match_the_header(L, tmp_path):
+    """sizeof and offsetof of every ABI struct, from gcc on the header, equal the binding's."""
+    structs = {"gn_fhn_params": geonet.gn_fhn_params, "gn_obs_params": geonet.gn_obs_params,
+               "gn_net_desc": geonet.gn_net_desc, "gn_pulse": geonet.gn_pulse, "gn_net_info": geonet.gn_net_info}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "geonet.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.check_call(["gcc", "-I", inc, str(src), "-o", str(exe)])
+    got = dict(l.split() for l in subprocess.check_output([str(exe)], text=True).splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == C.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, f"{name}.{f}"
 
 
 def _desc(spec, **over):

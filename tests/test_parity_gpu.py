@@ -143,16 +143,31 @@ def test_random_small_nets_windows(seed):
 
 
 # ------------------------------------------------------------------ layouts and edge cases
-def test_wide_edge_format_and_caller_order():
+@pytest.mark.parametrize("step_kernel", [0, 1])
+def test_wide_edge_format_and_caller_order(step_kernel):
     spec = netgen.tiny()
     for kw in (dict(wide_edges=True), dict(renumber=False), dict(wide_edges=True, renumber=False)):
-        net = Net(spec, **kw)
+        net = Net(spec, step_kernel=step_kernel, **kw)
         worst, _ = windowed(spec, net, 600)
         assert_windows(worst)
-        assert net.gn_net_get_info()["edge_format"] == (1 if kw.get("wide_edges") else 0)
+        info = net.gn_net_get_info()
+        assert info["edge_format"] == (1 if kw.get("wide_edges") else 0) and info["step_kernel"] == step_kernel
 
 
-def test_long_rows_take_the_whole_block_path():
+@pytest.mark.parametrize("step_kernel", [0, 1])
+def test_both_step_kernels_on_a_multi_block_net(step_kernel):
+    """Thousands of row blocks, so the persistent kernel cycles every pipeline stage
+    many times per step."""
+    spec = netgen.large(n=30000, mean_deg=40, bg_rate_hz=100.0)
+    net = Net(spec, step_kernel=step_kernel)
+    info = net.gn_net_get_info()
+    assert info["n_blocks"] > 100 and info["step_kernel"] == step_kernel
+    worst, n_ev = windowed(spec, net, 200, start=60)
+    assert_windows(worst)
+
+
+@pytest.mark.parametrize("step_kernel", [0, 1])
+def test_long_rows_take_the_whole_block_path(step_kernel):
     """A hub with in-degree 5000 (> one block's edge capacity) and ragged rows."""
     rng = np.random.default_rng(9)
     n = 6000
@@ -164,7 +179,7 @@ def test_long_rows_take_the_whole_block_path():
     w = rng.uniform(-0.2, 0.4, src.size).astype(np.float32)
     pulses = [(int(j), 2.0, 4.0, 1.0) for j in rng.choice(np.arange(1, 5001), 200, replace=False)]
     spec = netgen.NetSpec(pos=pos, src=src, dst=dst, weight=w, speed=None, speed_scalar=0.05, pulses=pulses)
-    net = Net(spec)
+    net = Net(spec, step_kernel=step_kernel)
     assert net.gn_net_get_info()["n_blocks"] >= 2
     worst, _ = windowed(spec, net, 800)
     assert_windows(worst)
