@@ -77,7 +77,7 @@ def peaks():
 
 def kernel_hash() -> str:
     h = hashlib.sha256()
-    for f in ("k_step.cu", "internal.cuh", "philox.cuh"):
+    for f in ("k_step.cu", "k_step_pipe.cu", "step_common.cuh", "ptx.cuh", "internal.cuh", "philox.cuh"):
         with open(os.path.join(ROOT, "paper_0908_3934_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -196,6 +196,8 @@ def main():
     ap.add_argument("--e2e-chunk", type=int, default=1000, help="steps per host round trip in the e2e run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--obs-cap", type=int, default=4096, help="observation rows kept on the device")
+    ap.add_argument("--step-kernel", type=int, default=0, choices=[0, 1],
+                    help="0: persistent bulk-copy pipelined kernel, 1: one row block per CTA")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -215,7 +217,8 @@ def main():
 
     spec = workload(args.workload, rank)
     stream = torch.cuda.Stream(device=dev)
-    net = geonet.Net(spec, device=local, stream=stream.cuda_stream, obs_capacity=args.obs_cap)
+    net = geonet.Net(spec, device=local, stream=stream.cuda_stream, obs_capacity=args.obs_cap,
+                     step_kernel=args.step_kernel)
     info = net.gn_net_get_info()
     E, N = spec.n_edges, spec.n_nodes
 
@@ -297,11 +300,13 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_kind,
                      "traffic": traffic_per_launch(args.workload),
-                     "algorithmic_bytes_per_launch": bytes_step, "kernel": "k_step"},
+                     "algorithmic_bytes_per_launch": bytes_step,
+                     "kernel": "k_step_pipe" if info["step_kernel"] == 0 else "k_step"},
         "e2e": {"value": E_total * e2e_steps / t_e2e, "unit": METRIC,
                 "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps},
         "gpu_launches": launches, "clocks": clocks,
-        "layout": {"ring_depth": info["ring_depth"], "edge_format": info["edge_format"],
+        "layout": {"step_kernel": info["step_kernel"], "grid": info["grid"],
+                   "ring_depth": info["ring_depth"], "edge_format": info["edge_format"],
                    "n_blocks": info["n_blocks"], "max_delay": info["max_delay"],
                    "device_bytes": info["device_bytes"]},
     }
