@@ -1,116 +1,30 @@
-// Host runtime of libgeonet.so: the C ABI of include/geonet.h for one network.
+// Host runtime of libgeonet.so: the single-network part of the C ABI
+// (include/geonet.h).
 //
 // gn_net_create validates and copies the caller's network, quantises the delays
 // on the GPU in FP64, renumbers nodes along a Morton curve (so the sources of
 // neighbouring targets sit close in memory and their gathers share sectors),
 // builds the by-target edge list with each row sorted by source, packs each edge
 // as (src << log2 R) | D next to its FP32 weight, cuts the rows into blocks of at
-// most kStepCap - 3 edges for the step kernel, and captures a CUDA graph of
+// most kStepCap - 3 edges for the step kernels, and captures a CUDA graph of
 // kGraphSteps step launches.  Everything is held in device memory; the host keeps
 // only the permutations and the delay table for output in the caller's order.
 #include <algorithm>
 #include <cmath>
-#include <cstdarg>
-#include <cstdio>
 #include <cstring>
-#include <numeric>
 #include <string>
 #include <vector>
 
-#include "../../include/geonet.h"
-#include "internal.cuh"
+#include "runtime.h"
+
+using gnrt::cuda_check;
+using gnrt::DevArray;
+using gnrt::DeviceGuard;
+using gnrt::fail;
+using gnrt::guarded;
 
 namespace {
-
-thread_local std::string g_last_error;
-
-struct Fail {
-    gn_status st;
-};
-
-[[noreturn]] void fail(gn_status st, const char *fmt, ...)
-{
-    char buf[512];
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(buf, sizeof buf, fmt, ap);
-    va_end(ap);
-    g_last_error = buf;
-    throw Fail{st};
-}
-
-void cuda_check(cudaError_t e, const char *what)
-{
-    if (e == cudaSuccess) return;
-    if (e == cudaErrorMemoryAllocation) fail(GN_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
-    fail(GN_ECUDA, "%s: %s", what, cudaGetErrorString(e));
-}
-
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev)
-    {
-        cudaGetDevice(&prev);
-        if (prev != dev) cuda_check(cudaSetDevice(dev), "cudaSetDevice");
-    }
-    ~DeviceGuard()
-    {
-        int cur = -1;
-        cudaGetDevice(&cur);
-        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-    }
-};
-
-// Rest point of the isolated FHN vertex: W = (V + f)/g on the W-nullcline and
-// a V - b V^3 - c (V + f)/g + I = 0, strictly decreasing when a < c/g.
-bool rest_point(const gn_fhn_params &p, double *v_out, double *w_out)
-{
-    if (!(p.g > 0.0) || !(p.b > 0.0) || !(p.a < p.c / p.g)) return false;
-    auto F = [&](double v) { return p.a * v - p.b * v * v * v - p.c * (v + p.f) / p.g + p.i_ext; };
-    double lo = -1.0, hi = 1.0;
-    for (int i = 0; i < 2000 && F(lo) < 0.0; ++i) lo *= 2.0;
-    for (int i = 0; i < 2000 && F(hi) > 0.0; ++i) hi *= 2.0;
-    if (!(F(lo) >= 0.0) || !(F(hi) <= 0.0)) return false;
-    for (int i = 0; i < 200; ++i) {
-        const double m = 0.5 * (lo + hi);
-        (F(m) > 0.0 ? lo : hi) = m;
-    }
-    double v = 0.5 * (lo + hi);
-    for (int i = 0; i < 3; ++i) v -= F(v) / (p.a - 3.0 * p.b * v * v - p.c / p.g);
-    *v_out = v;
-    *w_out = (v + p.f) / p.g;
-    return true;
-}
-
-// Interleave the low `bits` bits of each coordinate (Morton / Z-order key).
-uint64_t spread(uint64_t x, int dims)
-{
-    uint64_t r = 0;
-    for (int b = 0; b < 64 / dims; ++b) r |= ((x >> b) & 1ull) << (b * dims);
-    return r;
-}
-
-template <class T>
-struct DevArray {
-    T *p = nullptr;
-    size_t n = 0;
-    void alloc(size_t count, size_t *total)
-    {
-        n = count;
-        if (count == 0) return;
-        cuda_check(cudaMalloc(reinterpret_cast<void **>(&p), count * sizeof(T)), "cudaMalloc");
-        *total += count * sizeof(T);
-    }
-    void release()
-    {
-        if (p) cudaFree(p);
-        p = nullptr;
-        n = 0;
-    }
-};
-
 constexpr int kGraphSteps = 64;
-
 }  // namespace
 
 struct gn_net {
@@ -170,6 +84,7 @@ void sync(gn_net *net)
 {
     cuda_check(cudaStreamSynchronize(net->stream), "kernel execution");
     unsigned int st = 0;
+    if (!net->status.p) return;
     cuda_check(cudaMemcpy(&st, net->status.p, 4, cudaMemcpyDeviceToHost), "D2H status");
     if (st) {
         cudaMemset(net->status.p, 0, 4);
@@ -182,23 +97,6 @@ cudaError_t launch_one(const gn_net *net, int k, cudaStream_t s)
 {
     if (net->step_kernel == 0) return gn::launch_step_pipe(net->args, net->grid, k, net->packed, net->stream_edges, s);
     return gn::launch_step(net->args, net->n_blocks, k, net->packed, net->stream_edges, s);
-}
-
-template <class F>
-gn_status guarded(F &&f)
-{
-    try {
-        f();
-        return GN_OK;
-    } catch (const Fail &e) {
-        return e.st;
-    } catch (const std::bad_alloc &) {
-        g_last_error = "host allocation failed";
-        return GN_ENOMEM;
-    } catch (...) {
-        g_last_error = "unexpected exception";
-        return GN_EINTERNAL;
-    }
 }
 
 void build_graph(gn_net *net)
@@ -224,232 +122,15 @@ void build_graph(gn_net *net)
     net->graph_stale = false;
 }
 
-void validate_desc(const gn_net_desc *d)
-{
-    if (!d) fail(GN_EINVAL, "descriptor is NULL");
-    if (d->n_nodes <= 0) fail(GN_EINVAL, "n_nodes must be positive");
-    if (d->dim < 1 || d->dim > 3) fail(GN_EINVAL, "dim must be 1, 2 or 3");
-    if (!d->pos) fail(GN_EINVAL, "pos is NULL");
-    if (d->n_edges < 0) fail(GN_EINVAL, "n_edges < 0");
-    if (d->n_edges > 2147483647LL - 4 * gn::kEdgePad) fail(GN_ERANGE, "too many edges (limit 2^31 - 16384)");
-    if (d->n_edges > 0 && (!d->src || !d->dst || !d->weight)) fail(GN_EINVAL, "edge arrays are NULL");
-    if (!(d->dt_ms > 0.0) || !std::isfinite(d->dt_ms)) fail(GN_EINVAL, "dt_ms must be positive");
-    if (!(d->obs.tau_ms > 0.0)) fail(GN_EINVAL, "obs.tau_ms must be positive");
-    if (d->obs.sample_every <= 0) fail(GN_EINVAL, "obs.sample_every must be positive");
-    if (d->coupling != GN_COUPLE_REST && d->coupling != GN_COUPLE_RAW) fail(GN_EINVAL, "unknown coupling");
-    if (d->ring_depth < 0 || (d->ring_depth & (d->ring_depth - 1))) fail(GN_EINVAL, "ring_depth must be a power of two");
-    if (d->edge_format != 0 && d->edge_format != 1) fail(GN_EINVAL, "edge_format must be 0 or 1");
-    if (d->step_kernel != 0 && d->step_kernel != 1) fail(GN_EINVAL, "step_kernel must be 0 or 1");
-    const int64_t np = static_cast<int64_t>(d->n_nodes) * d->dim;
-    for (int64_t i = 0; i < np; ++i)
-        if (!std::isfinite(d->pos[i])) fail(GN_EINVAL, "position %lld is not finite", (long long)i);
-    for (int64_t e = 0; e < d->n_edges; ++e) {
-        const int32_t i = d->src[e], j = d->dst[e];
-        if (i < 0 || i >= d->n_nodes || j < 0 || j >= d->n_nodes)
-            fail(GN_EINVAL, "edge %lld: node id out of range", (long long)e);
-        if (i == j) fail(GN_EINVAL, "edge %lld: self-loop (the input set excludes i = j)", (long long)e);
-        if (!std::isfinite(d->weight[e])) fail(GN_EINVAL, "edge %lld: weight not finite", (long long)e);
-        if (d->delay_steps) {
-            if (d->delay_steps[e] < 1) fail(GN_EINVAL, "edge %lld: explicit delay < 1 step", (long long)e);
-        } else {
-            const double s = d->speed ? d->speed[e] : d->speed_scalar;
-            if (!(s > 0.0) || !std::isfinite(s)) fail(GN_EINVAL, "edge %lld: speed must be positive", (long long)e);
-        }
-    }
-}
-
-void compute_delays(gn_net *net, const gn_net_desc *d)
-{
-    const int64_t E = d->n_edges;
-    net->delay.assign(E, 1);
-    net->n_clamped = 0;
-    if (E == 0) return;
-    if (d->delay_steps) {
-        std::copy(d->delay_steps, d->delay_steps + E, net->delay.begin());
-        return;
-    }
-    size_t tmp = 0;
-    DevArray<double> pos, speed;
-    DevArray<int32_t> src, dst, dl;
-    DevArray<uint8_t> cl;
-    try {
-        pos.alloc(static_cast<size_t>(d->n_nodes) * d->dim, &tmp);
-        src.alloc(E, &tmp);
-        dst.alloc(E, &tmp);
-        dl.alloc(E, &tmp);
-        cl.alloc(E, &tmp);
-        if (d->speed) speed.alloc(E, &tmp);
-        cuda_check(cudaMemcpyAsync(pos.p, d->pos, pos.n * sizeof(double), cudaMemcpyHostToDevice, net->stream), "H2D pos");
-        cuda_check(cudaMemcpyAsync(src.p, d->src, E * 4, cudaMemcpyHostToDevice, net->stream), "H2D src");
-        cuda_check(cudaMemcpyAsync(dst.p, d->dst, E * 4, cudaMemcpyHostToDevice, net->stream), "H2D dst");
-        if (d->speed)
-            cuda_check(cudaMemcpyAsync(speed.p, d->speed, E * 8, cudaMemcpyHostToDevice, net->stream), "H2D speed");
-        cuda_check(gn::launch_delay(E, d->dim, pos.p, src.p, dst.p, speed.p, d->speed_scalar, d->dt_ms, dl.p, cl.p,
-                                    net->stream),
-                   "delay kernel");
-        std::vector<uint8_t> hcl(E);
-        cuda_check(cudaMemcpyAsync(net->delay.data(), dl.p, E * 4, cudaMemcpyDeviceToHost, net->stream), "D2H delay");
-        cuda_check(cudaMemcpyAsync(hcl.data(), cl.p, E, cudaMemcpyDeviceToHost, net->stream), "D2H clamp");
-        sync(net);
-        for (int64_t e = 0; e < E; ++e) net->n_clamped += hcl[e];
-    } catch (...) {
-        pos.release(); speed.release(); src.release(); dst.release(); dl.release(); cl.release();
-        throw;
-    }
-    pos.release(); speed.release(); src.release(); dst.release(); dl.release(); cl.release();
-}
-
-void renumber(gn_net *net, const gn_net_desc *d)
-{
-    const int32_t N = d->n_nodes;
-    net->perm.resize(N);
-    std::iota(net->perm.begin(), net->perm.end(), 0);
-    if (d->renumber >= 0 && N > 1) {
-        const int dims = d->dim;
-        const int bits = 21;  // 21 bits per axis: a 63-bit key in 3D
-        std::vector<double> lo(dims, INFINITY), hi(dims, -INFINITY);
-        for (int32_t i = 0; i < N; ++i)
-            for (int k = 0; k < dims; ++k) {
-                lo[k] = std::min(lo[k], d->pos[(int64_t)i * dims + k]);
-                hi[k] = std::max(hi[k], d->pos[(int64_t)i * dims + k]);
-            }
-        double ext = 0.0;
-        for (int k = 0; k < dims; ++k) ext = std::max(ext, hi[k] - lo[k]);
-        const double scale = ext > 0.0 ? (std::ldexp(1.0, bits) - 1.0) / ext : 0.0;
-        std::vector<uint64_t> key(N);
-        for (int32_t i = 0; i < N; ++i) {
-            uint64_t code = 0;
-            for (int k = 0; k < dims; ++k) {
-                const uint64_t q = static_cast<uint64_t>((d->pos[(int64_t)i * dims + k] - lo[k]) * scale);
-                code |= spread(q, dims) << k;
-            }
-            key[i] = code;
-        }
-        std::stable_sort(net->perm.begin(), net->perm.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
-    }
-    net->inv.resize(N);
-    for (int32_t r = 0; r < N; ++r) net->inv[net->perm[r]] = r;
-}
-
-// By-target edge list with rows sorted by source (two stable counting sorts),
-// packed keys and weights, row pointers and row blocks; uploaded to the device.
-void build_csr(gn_net *net, const gn_net_desc *d)
-{
-    const int32_t N = d->n_nodes;
-    const int64_t E = d->n_edges;
-    std::vector<int32_t> order(E), tmp(E);
-    std::vector<int64_t> cnt(static_cast<size_t>(N) + 1, 0);
-    for (int64_t e = 0; e < E; ++e) cnt[net->inv[d->src[e]] + 1]++;
-    for (int32_t i = 0; i < N; ++i) cnt[i + 1] += cnt[i];
-    for (int64_t e = 0; e < E; ++e) tmp[cnt[net->inv[d->src[e]]]++] = static_cast<int32_t>(e);
-    std::fill(cnt.begin(), cnt.end(), 0);
-    for (int64_t e = 0; e < E; ++e) cnt[net->inv[d->dst[e]] + 1]++;
-    for (int32_t i = 0; i < N; ++i) cnt[i + 1] += cnt[i];
-    std::vector<int32_t> row_ptr(static_cast<size_t>(N) + 1);
-    for (int32_t i = 0; i <= N; ++i) row_ptr[i] = static_cast<int32_t>(cnt[i]);
-    for (int64_t k = 0; k < E; ++k) {
-        const int32_t e = tmp[k];
-        order[cnt[net->inv[d->dst[e]]]++] = e;
-    }
-    tmp.clear();
-    tmp.shrink_to_fit();
-
-    const size_t Ep = static_cast<size_t>(E) + gn::kEdgePad;
-    std::vector<float> w(Ep, 0.0f);
-    std::vector<float> bias;
-    if (d->coupling == GN_COUPLE_RAW) bias.assign(N, 0.0f);
-    if (net->packed) {
-        std::vector<uint32_t> key(Ep, 0u);
-        for (int64_t p = 0; p < E; ++p) {
-            const int32_t e = order[p];
-            key[p] = (static_cast<uint32_t>(net->inv[d->src[e]]) << net->dbits) | static_cast<uint32_t>(net->delay[e]);
-            w[p] = d->weight[e];
-        }
-        net->ekey.alloc(Ep * 4, &net->bytes);
-        cuda_check(cudaMemcpy(net->ekey.p, key.data(), Ep * 4, cudaMemcpyHostToDevice), "H2D keys");
-    } else {
-        std::vector<uint32_t> key(2 * Ep, 0u);
-        for (int64_t p = 0; p < E; ++p) {
-            const int32_t e = order[p];
-            key[2 * p] = static_cast<uint32_t>(net->inv[d->src[e]]);
-            key[2 * p + 1] = static_cast<uint32_t>(net->delay[e]);
-            w[p] = d->weight[e];
-        }
-        net->ekey.alloc(Ep * 8, &net->bytes);
-        cuda_check(cudaMemcpy(net->ekey.p, key.data(), Ep * 8, cudaMemcpyHostToDevice), "H2D keys");
-    }
-    if (!bias.empty()) {
-        for (int32_t r = 0; r < N; ++r) {
-            double s = 0.0;
-            for (int32_t p = row_ptr[r]; p < row_ptr[r + 1]; ++p) s += static_cast<double>(w[p]);
-            bias[r] = static_cast<float>(net->v_rest * s);
-        }
-        net->bias.alloc(N, &net->bytes);
-        cuda_check(cudaMemcpy(net->bias.p, bias.data(), N * 4, cudaMemcpyHostToDevice), "H2D bias");
-    }
-    net->ew.alloc(Ep, &net->bytes);
-    cuda_check(cudaMemcpy(net->ew.p, w.data(), Ep * 4, cudaMemcpyHostToDevice), "H2D weights");
-    // padded so 16-byte bulk copies of row_ptr[r0 & ~3 .. (r1 + 4) & ~3) stay inside
-    row_ptr.resize(static_cast<size_t>(N) + 1 + 8, row_ptr[N]);
-    net->row_ptr.alloc(row_ptr.size(), &net->bytes);
-    cuda_check(cudaMemcpy(net->row_ptr.p, row_ptr.data(), row_ptr.size() * 4, cudaMemcpyHostToDevice), "H2D row_ptr");
-
-    // row blocks: consecutive rows with at most kStepCap - 3 edges and kStepMaxRows rows;
-    // a longer row gets a block of its own
-    std::vector<int32_t> blk{0};
-    const int cap = gn::kStepCap - 3;
-    int32_t r = 0;
-    while (r < N) {
-        const int deg0 = row_ptr[r + 1] - row_ptr[r];
-        if (deg0 > cap) {
-            blk.push_back(++r);
-            continue;
-        }
-        int edges = 0, rows = 0;
-        while (r < N && rows < gn::kStepMaxRows) {
-            const int deg = row_ptr[r + 1] - row_ptr[r];
-            if (deg > cap || edges + deg > cap) break;
-            edges += deg;
-            ++rows;
-            ++r;
-        }
-        blk.push_back(r);
-    }
-    net->n_blocks = static_cast<int>(blk.size()) - 1;
-    net->blk.alloc(blk.size(), &net->bytes);
-    cuda_check(cudaMemcpy(net->blk.p, blk.data(), blk.size() * 4, cudaMemcpyHostToDevice), "H2D blocks");
-    std::vector<int4> desc(net->n_blocks);
-    for (int b = 0; b < net->n_blocks; ++b) desc[b] = make_int4(blk[b], blk[b + 1], row_ptr[blk[b]], row_ptr[blk[b + 1]]);
-    net->bdesc.alloc(desc.size(), &net->bytes);
-    if (!desc.empty())
-        cuda_check(cudaMemcpy(net->bdesc.p, desc.data(), desc.size() * sizeof(int4), cudaMemcpyHostToDevice), "H2D desc");
-}
-
 // Replace the pulse table: validated and sorted by internal node on the host, then
 // copied in stream order (steps already queued keep the old table).  The arrays
 // only grow; a growth re-points the kernel arguments, so the step graph is rebuilt.
 void upload_pulses(gn_net *net, const gn_pulse *pulses, int32_t n)
 {
-    struct P {
-        int32_t node;
-        int64_t on, off;
-        float amp;
-    };
-    std::vector<P> ps;
-    ps.reserve(n);
-    for (int32_t i = 0; i < n; ++i) {
-        const gn_pulse &p = pulses[i];
-        if (p.node < 0 || p.node >= net->N) fail(GN_EINVAL, "pulse %d: node out of range", i);
-        if (!std::isfinite(p.t_on_ms) || !std::isfinite(p.t_off_ms) || !std::isfinite(p.amp))
-            fail(GN_EINVAL, "pulse %d: not finite", i);
-        const long long on = llround(p.t_on_ms / net->dt), off = llround(p.t_off_ms / net->dt);
-        if (off <= on) continue;
-        ps.push_back(P{net->inv[p.node], on, off, p.amp});
-    }
-    std::stable_sort(ps.begin(), ps.end(), [](const P &a, const P &b) { return a.node < b.node; });
-    const int64_t m = static_cast<int64_t>(ps.size());
+    gnrt::PulseTable t = gnrt::make_pulses(pulses, n, net->N, net->dt, net->inv);
+    const int64_t m = static_cast<int64_t>(t.node.size());
     if (m > net->pulse_cap) {
-        sync(net);
+        cuda_check(cudaStreamSynchronize(net->stream), "pulse upload");
         net->p_node.release();
         net->p_on.release();
         net->p_off.release();
@@ -466,26 +147,15 @@ void upload_pulses(gn_net *net, const gn_pulse *pulses, int32_t n)
         net->args.p_amp = net->p_amp.p;
         net->graph_stale = true;
     }
-    net->stage_pulses.resize(static_cast<size_t>(m) * 24 + 4);
-    auto *nd = reinterpret_cast<int32_t *>(net->stage_pulses.data());
-    auto *on = reinterpret_cast<int64_t *>(nd + m + (m & 1));
-    auto *off = on + m;
-    auto *amp = reinterpret_cast<float *>(off + m);
-    for (int64_t i = 0; i < m; ++i) {
-        nd[i] = ps[i].node;
-        on[i] = ps[i].on;
-        off[i] = ps[i].off;
-        amp[i] = ps[i].amp;
-    }
-    if (m) {
-        cuda_check(cudaMemcpyAsync(net->p_node.p, nd, m * 4, cudaMemcpyHostToDevice, net->stream), "H2D pulses");
-        cuda_check(cudaMemcpyAsync(net->p_on.p, on, m * 8, cudaMemcpyHostToDevice, net->stream), "H2D pulses");
-        cuda_check(cudaMemcpyAsync(net->p_off.p, off, m * 8, cudaMemcpyHostToDevice, net->stream), "H2D pulses");
-        cuda_check(cudaMemcpyAsync(net->p_amp.p, amp, m * 4, cudaMemcpyHostToDevice, net->stream), "H2D pulses");
-    }
-    int32_t mm = static_cast<int32_t>(m);
     // a copy from pageable memory is staged before cudaMemcpyAsync returns, so the
     // host table may change right after; the device sees it in stream order
+    if (m) {
+        cuda_check(cudaMemcpyAsync(net->p_node.p, t.node.data(), m * 4, cudaMemcpyHostToDevice, net->stream), "H2D pulses");
+        cuda_check(cudaMemcpyAsync(net->p_on.p, t.on.data(), m * 8, cudaMemcpyHostToDevice, net->stream), "H2D pulses");
+        cuda_check(cudaMemcpyAsync(net->p_off.p, t.off.data(), m * 8, cudaMemcpyHostToDevice, net->stream), "H2D pulses");
+        cuda_check(cudaMemcpyAsync(net->p_amp.p, t.amp.data(), m * 4, cudaMemcpyHostToDevice, net->stream), "H2D pulses");
+    }
+    const int32_t mm = static_cast<int32_t>(m);
     cuda_check(cudaMemcpyAsync(net->d_npulses.p, &mm, 4, cudaMemcpyHostToDevice, net->stream), "H2D pulse count");
 }
 
@@ -506,72 +176,68 @@ void check_net(const gn_net *net)
 
 extern "C" {
 
-const char *gn_last_error(void) { return g_last_error.c_str(); }
+const char *gn_last_error(void) { return gnrt::last_error(); }
 
 gn_status gn_net_create(const gn_net_desc *desc, gn_net **out)
 {
     if (!out) {
-        g_last_error = "out is NULL";
+        gnrt::set_error("out is NULL");
         return GN_EINVAL;
     }
     *out = nullptr;
     gn_net *net = nullptr;
     gn_status st = guarded([&] {
-        validate_desc(desc);
-        double vr, wr;
-        if (!rest_point(desc->fhn, &vr, &wr)) fail(GN_EINVAL, "FHN parameters have no unique rest point (need g > 0, b > 0, a < c/g)");
+        gnrt::validate_desc(desc);
         net = new gn_net();
         net->device = desc->device;
         DeviceGuard dg(desc->device);
-        net->N = desc->n_nodes;
-        net->dim = desc->dim;
-        net->E = desc->n_edges;
-        net->v_rest = vr;
-        net->w_rest = wr;
-        net->dt = desc->dt_ms;
-        net->sample_every = desc->obs.sample_every;
         if (desc->cuda_stream) {
             net->stream = static_cast<cudaStream_t>(desc->cuda_stream);
         } else {
             cuda_check(cudaStreamCreateWithFlags(&net->stream, cudaStreamNonBlocking), "cudaStreamCreate");
             net->own_stream = true;
         }
-        compute_delays(net, desc);
-        int32_t dmax = 1, dmin = net->E ? INT32_MAX : 1;
-        for (int32_t D : net->delay) {
-            dmax = std::max(dmax, D);
-            dmin = std::min(dmin, D);
-        }
-        net->dmax = dmax;
-        net->dmin = dmin;
-        if (dmax > (1 << 30)) fail(GN_ERANGE, "delay of %d steps is out of range", dmax);
-        int32_t R = 2;
-        while (R < dmax + 2) R <<= 1;
-        if (desc->ring_depth) {
-            if (desc->ring_depth < dmax + 2)
-                fail(GN_ERANGE, "ring_depth %d cannot hold the largest delay %d (needs >= D_max + 2)", desc->ring_depth, dmax);
-            R = desc->ring_depth;
-        }
-        net->R = R;
-        net->dbits = 0;
-        while ((1 << net->dbits) < R) ++net->dbits;
-        net->packed = desc->edge_format == 0 && (static_cast<int64_t>(net->N) << net->dbits) <= (1ll << 32);
-        if (static_cast<double>(R) * net->N * 4.0 > 200e9) fail(GN_ERANGE, "history ring of %d x %d floats is too large", R, net->N);
-        renumber(net, desc);
-        build_csr(net, desc);
+        std::vector<std::vector<int32_t>> delays;
+        std::vector<int64_t> clamped;
+        gnrt::quantise_delays(desc, 1, net->stream, delays, clamped);
+        gnrt::HostNet h;
+        gnrt::host_build(desc, std::move(delays[0]), clamped[0], gn::kStepCap, gn::kStepMaxRows, h);
+
+        net->N = h.N;
+        net->dim = h.dim;
+        net->E = h.E;
+        net->R = h.R;
+        net->dbits = h.dbits;
+        net->dmax = h.dmax;
+        net->dmin = h.dmin;
+        net->n_clamped = h.n_clamped;
+        net->packed = h.packed;
+        net->stride = h.stride;
+        net->n_blocks = h.n_blocks();
+        net->v_rest = h.v_rest;
+        net->w_rest = h.w_rest;
+        net->dt = desc->dt_ms;
+        net->sample_every = desc->obs.sample_every;
+        net->perm = h.perm;
+        net->inv = h.inv;
+        net->delay = h.delay;
         // edges are streamed past L2 unless they fit comfortably in it
-        const double edge_bytes = static_cast<double>(net->E) * (net->packed ? 8.0 : 12.0);
-        net->stream_edges = edge_bytes > 48e6;
+        net->stream_edges = static_cast<double>(net->E) * (net->packed ? 8.0 : 12.0) > 48e6;
 
         const int32_t N = net->N;
-        net->stride = ((N + 4) + 31) / 32 * 32;
-        net->ring.alloc(static_cast<size_t>(R) * net->stride, &net->bytes);
+        net->ekey.alloc(h.key.size() * 4, &net->bytes);
+        cuda_check(cudaMemcpy(net->ekey.p, h.key.data(), h.key.size() * 4, cudaMemcpyHostToDevice), "H2D keys");
+        net->ew.upload(h.w, &net->bytes);
+        net->bias.upload(h.bias, &net->bytes);
+        net->row_ptr.upload(h.row_ptr, &net->bytes);
+        net->blk.upload(h.blk, &net->bytes);
+        net->bdesc.upload(h.desc, &net->bytes);
+        net->d_perm.upload(h.perm, &net->bytes);
+        net->ring.alloc(static_cast<size_t>(net->R) * net->stride, &net->bytes);
         net->wc.alloc(static_cast<size_t>(N) + 2, &net->bytes);
         net->status.alloc(1, &net->bytes);
-        cuda_check(cudaMemset(net->status.p, 0, 4), "memset");
         net->bgc.alloc(N, &net->bytes);
         net->first.alloc(N, &net->bytes);
-        net->d_perm.alloc(N, &net->bytes);
         net->obs_cap = desc->obs_capacity > 0 ? desc->obs_capacity : 1024;
         net->obs.alloc(static_cast<size_t>(net->obs_cap) * N, &net->bytes);
         net->ev_cap = desc->event_capacity > 0 ? desc->event_capacity : (1 << 20);
@@ -580,28 +246,23 @@ gn_status gn_net_create(const gn_net_desc *desc, gn_net **out)
         net->ev_count.alloc(1, &net->bytes);
         net->d_step.alloc(1, &net->bytes);
         net->d_npulses.alloc(1, &net->bytes);
-        cuda_check(cudaMemset(net->d_npulses.p, 0, 4), "memset");
         cuda_check(cudaMemset(net->ring.p, 0, net->ring.n * 4), "memset");
         cuda_check(cudaMemset(net->wc.p, 0, net->wc.n * 8), "memset");
+        cuda_check(cudaMemset(net->status.p, 0, 4), "memset");
         cuda_check(cudaMemset(net->bgc.p, 0, net->bgc.n * 4), "memset");
         cuda_check(cudaMemset(net->first.p, 0xff, net->first.n * 8), "memset");
         cuda_check(cudaMemset(net->obs.p, 0, net->obs.n * 4), "memset");
         cuda_check(cudaMemset(net->ev_count.p, 0, 8), "memset");
         cuda_check(cudaMemset(net->d_step.p, 0, 8), "memset");
-        cuda_check(cudaMemcpy(net->d_perm.p, net->perm.data(), N * 4, cudaMemcpyHostToDevice), "H2D perm");
+        cuda_check(cudaMemset(net->d_npulses.p, 0, 4), "memset");
 
         gn::StepArgs &a = net->args;
-        a.N = N;
-        a.ring_stride = net->stride;
-        a.ring_mask = R - 1;
-        a.bdesc = net->bdesc.p;
-        a.n_blocks = net->n_blocks;
-        a.status = net->status.p;
-        a.dbits = net->dbits;
+        gnrt::fill_step_params(desc, h, a);
         a.ekey = net->ekey.p;
         a.ew = net->ew.p;
         a.row_ptr = net->row_ptr.p;
         a.blk = net->blk.p;
+        a.bdesc = net->bdesc.p;
         a.ring = net->ring.p;
         a.wc = net->wc.p;
         a.bgc = net->bgc.p;
@@ -609,23 +270,6 @@ gn_status gn_net_create(const gn_net_desc *desc, gn_net **out)
         a.first = net->first.p;
         a.perm = net->d_perm.p;
         a.n_pulses = net->d_npulses.p;
-        const gn_fhn_params &f = desc->fhn;
-        a.dt = static_cast<float>(desc->dt_ms);
-        a.k1 = static_cast<float>(f.a - 3.0 * f.b * vr * vr);
-        a.q2 = static_cast<float>(-3.0 * f.b * vr);
-        a.q3 = static_cast<float>(-f.b);
-        a.cw = static_cast<float>(f.c);
-        a.dte = static_cast<float>(desc->dt_ms * f.e);
-        a.g = static_cast<float>(f.g);
-        a.alpha = static_cast<float>(desc->dt_ms / desc->obs.tau_ms);
-        a.theta_s = static_cast<float>(desc->theta - vr);
-        a.gain = desc->obs.gain;
-        a.offset = desc->obs.offset;
-        a.sigma = desc->obs.sigma;
-        a.vrest = static_cast<float>(vr);
-        a.sample_every = desc->obs.sample_every;
-        a.obs_seed = desc->obs.seed;
-        a.bg_thr = 0;
         a.obs = net->obs.p;
         a.obs_cap = net->obs_cap;
         a.ev_node = net->ev_node.p;
@@ -633,6 +277,8 @@ gn_status gn_net_create(const gn_net_desc *desc, gn_net **out)
         a.ev_count = net->ev_count.p;
         a.ev_cap = net->ev_cap;
         a.d_step = net->d_step.p;
+        a.status = net->status.p;
+
         net->step_kernel = desc->step_kernel;
         if (net->step_kernel == 0) {
             int per_sm = 0, sms = 0;
@@ -709,7 +355,6 @@ gn_status gn_set_stimulus(gn_net *net, const gn_pulse *pulses, int32_t n_pulses)
 {
     return guarded([&] {
         check_net(net);
-        if (n_pulses < 0 || (n_pulses > 0 && !pulses)) fail(GN_EINVAL, "bad pulse array");
         DeviceGuard dg(net->device);
         upload_pulses(net, pulses, n_pulses);
     });
@@ -723,12 +368,7 @@ gn_status gn_set_background(gn_net *net, double rate_hz, float amp, double dur_m
             fail(GN_EINVAL, "bad background parameters");
         DeviceGuard dg(net->device);
         sync(net);
-        const double p = (rate_hz * net->dt) / 1000.0;
-        uint32_t thr = 0;
-        if (p > 0.0) {
-            const double t = std::floor(std::ldexp(p, 32));
-            thr = t >= 4294967295.0 ? 4294967295u : static_cast<uint32_t>(t);
-        }
+        const uint32_t thr = gnrt::background_threshold(rate_hz, net->dt);
         net->args.bg_thr = thr;
         net->args.bg_amp = amp;
         net->args.bg_width = static_cast<int32_t>(llround(dur_ms / net->dt));

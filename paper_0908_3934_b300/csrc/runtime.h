@@ -1,0 +1,112 @@
+// Internal host runtime shared by the single-network (net.cu) and batched
+// (batch.cu) parts of libgeonet.so: error handling, device arrays, descriptor
+// validation, delay quantisation and the host-side build of one network.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/geonet.h"
+#include "internal.cuh"
+
+namespace gnrt {
+
+struct Fail {
+    gn_status st;
+};
+
+// Record a message for gn_last_error() and throw; only guarded() catches it.
+[[noreturn]] void fail(gn_status st, const char *fmt, ...);
+void set_error(const std::string &msg);
+const char *last_error();
+void cuda_check(cudaError_t e, const char *what);
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev);
+    ~DeviceGuard();
+};
+
+template <class T>
+struct DevArray {
+    T *p = nullptr;
+    size_t n = 0;
+    void alloc(size_t count, size_t *total)
+    {
+        n = count;
+        if (count == 0) return;
+        cuda_check(cudaMalloc(reinterpret_cast<void **>(&p), count * sizeof(T)), "cudaMalloc");
+        *total += count * sizeof(T);
+    }
+    void upload(const std::vector<T> &v, size_t *total)
+    {
+        alloc(v.size(), total);
+        if (!v.empty()) cuda_check(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), "H2D");
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+};
+
+gn_status guarded_call(void (*fn)(void *), void *ctx);
+
+template <class F>
+gn_status guarded(F &&f)
+{
+    return guarded_call([](void *c) { (*static_cast<F *>(c))(); }, &f);
+}
+
+// Rest point of the isolated FHN vertex (S = U = 0): W = (V + f)/g and
+// a V - b V^3 - c (V + f)/g + I = 0, unique when g > 0, b > 0, a < c/g.
+bool rest_point(const gn_fhn_params &p, double *v_out, double *w_out);
+
+void validate_desc(const gn_net_desc *d);
+
+// FP64 delay quantisation of several networks in one launch (geometric ones;
+// explicit tables are copied).  delay[i] in caller edge order of network i.
+void quantise_delays(const gn_net_desc *descs, int n_nets, cudaStream_t s, std::vector<std::vector<int32_t>> &delay,
+                     std::vector<int64_t> &n_clamped);
+
+// Host-side products of one network, ready to upload.
+struct HostNet {
+    int32_t N = 0, dim = 0;
+    int64_t E = 0;
+    int32_t R = 0, dbits = 0, dmax = 1, dmin = 1, stride = 0;
+    int64_t n_clamped = 0;
+    bool packed = true;
+    double v_rest = 0.0, w_rest = 0.0;
+    std::vector<int32_t> perm, inv, delay;   // perm: internal -> caller; delay: caller edge order
+    std::vector<uint32_t> key;               // [E + pad] packed, or [2 (E + pad)] wide
+    std::vector<float> w;                    // [E + pad]
+    std::vector<float> bias;                 // [N], RAW coupling only
+    std::vector<int32_t> row_ptr;            // [N + 1 + 8]
+    std::vector<int32_t> blk;                // [n_blocks + 1]
+    std::vector<int4> desc;                  // [n_blocks] {r0, r1, e0, e1}
+    int n_blocks() const { return static_cast<int>(blk.size()) - 1; }
+};
+
+// Ring depth, renumbering, CSR by target (rows sorted by source), edge packing and
+// row blocks of at most block_cap - 3 edges and block_rows rows.
+void host_build(const gn_net_desc *d, std::vector<int32_t> delay, int64_t n_clamped, int block_cap, int block_rows,
+                HostNet &h);
+
+// Scalar fields of the step arguments (FHN about the rest point, readout, sizes).
+void fill_step_params(const gn_net_desc *d, const HostNet &h, gn::StepArgs &a);
+
+// Pulses (caller node ids, ms) -> sorted by internal node, steps; invalid -> GN_EINVAL.
+struct PulseTable {
+    std::vector<int32_t> node;
+    std::vector<int64_t> on, off;
+    std::vector<float> amp;
+};
+PulseTable make_pulses(const gn_pulse *pulses, int32_t n, int32_t n_nodes, double dt, const std::vector<int32_t> &inv);
+
+// Background onset threshold floor(p 2^32), p = rate * dt.
+uint32_t background_threshold(double rate_hz, double dt_ms);
+
+}  // namespace gnrt
