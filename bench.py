@@ -196,8 +196,8 @@ def main():
     ap.add_argument("--e2e-chunk", type=int, default=1000, help="steps per host round trip in the e2e run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--obs-cap", type=int, default=4096, help="observation rows kept on the device")
-    ap.add_argument("--step-kernel", type=int, default=0, choices=[0, 1],
-                    help="0: persistent bulk-copy pipelined kernel, 1: one row block per CTA")
+    ap.add_argument("--step-kernel", type=int, default=0, choices=[0, 1, 2],
+                    help="0: autotuned, 1: one row block per CTA, 2: persistent bulk-copy pipelined kernel")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -231,6 +231,7 @@ def main():
     # ---- device-resident throughput: W untimed steps, then exactly K timed steps
     net.gn_step(args.warmup)
     barrier()
+    info = net.gn_net_get_info()  # the kernel is chosen on the first gn_step
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
     except Exception:
@@ -301,11 +302,12 @@ def main():
                      "frac": achieved / peak, "peak_source": peak_kind,
                      "traffic": traffic_per_launch(args.workload),
                      "algorithmic_bytes_per_launch": bytes_step,
-                     "kernel": "k_step_pipe" if info["step_kernel"] == 0 else "k_step"},
+                     "kernel": "k_step_pipe" if info["step_kernel"] == 2 else "k_step"},
         "e2e": {"value": E_total * e2e_steps / t_e2e, "unit": METRIC,
                 "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps},
         "gpu_launches": launches, "clocks": clocks,
-        "layout": {"step_kernel": info["step_kernel"], "grid": info["grid"],
+        "layout": {"step_kernel": info["step_kernel"], "grid": info["grid"], "cta_threads": info["step_threads"],
+                   "edges_per_thread": info["step_edges_per_thread"],
                    "ring_depth": info["ring_depth"], "edge_format": info["edge_format"],
                    "n_blocks": info["n_blocks"], "max_delay": info["max_delay"],
                    "device_bytes": info["device_bytes"]},

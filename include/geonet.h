@@ -103,7 +103,9 @@ typedef struct {
     int64_t event_capacity;      /* events kept on the device; 0 = 1 << 20 */
     int32_t renumber;            /* 0: renumber nodes in spatial (Morton) order; -1: keep the caller's order */
     int32_t edge_format;         /* 0: packed 32-bit keys when N * ring_depth <= 2^32, else 64-bit; 1: always 64-bit */
-    int32_t step_kernel;         /* 0: persistent kernel with bulk-copy pipeline; 1: one row block per CTA */
+    int32_t step_kernel;         /* 0: chosen by timing the candidates on the first gn_step (autotune);
+                                    1: one row block per CTA, chained launches; 2: persistent CTAs with a
+                                    bulk-copy pipeline of row blocks */
     void *cuda_stream;           /* cudaStream_t to run on; NULL: the library makes its own */
     int32_t device;              /* CUDA device ordinal */
 } gn_net_desc;
@@ -127,7 +129,9 @@ typedef struct {
     int64_t n_clamped;           /* geometric delays that rounded below one step */
     int32_t edge_format;         /* 0: packed 32-bit (src << log2 R | D); 1: 64-bit (src, D) */
     int32_t n_blocks;            /* row blocks of the step kernel */
-    int32_t step_kernel;         /* as in gn_net_desc */
+    int32_t step_kernel;         /* 1 or 2 once chosen (0 before the first gn_step when autotuning) */
+    int32_t step_threads;        /* CTA size of the chosen kernel */
+    int32_t step_edges_per_thread;
     int32_t grid;                /* CTAs per step launch */
     int64_t step;                /* steps taken */
     int64_t samples;             /* samples produced */

@@ -70,14 +70,17 @@ constexpr unsigned int kStatusTimeout = 1u;  // a bounded mbarrier wait gave up
 
 constexpr int kEdgePad = 4096;
 
-// Launch geometry of the step kernel (row blocks hold at most kStepCap - 3 edges).
-constexpr int kStepThreads = 256;
-constexpr int kStepEPT = 8;
-constexpr int kStepCap = kStepThreads * kStepEPT;
-constexpr int kStepMaxRows = kStepThreads;
+// CTA shapes of the row-block step kernel: T threads, EPT edges per thread; its
+// row blocks hold at most T * EPT - 3 edges and T rows.  The persistent pipelined
+// kernel uses shape 0.
+struct StepShape {
+    int threads, ept, min_ctas_per_sm;
+};
+constexpr int kNumStepShapes = 5;
+extern const StepShape kStepShapes[kNumStepShapes];
 
-// Kernel launchers (k_step.cu, k_delay.cu)
-cudaError_t launch_step(const StepArgs &a, int n_blocks, int k, bool packed, bool stream_edges,
+// Kernel launchers (k_step.cu, k_step_pipe.cu, k_delay.cu)
+cudaError_t launch_step(const StepArgs &a, int n_blocks, int k, int shape, bool packed, bool stream_edges,
                         cudaStream_t s);
 cudaError_t launch_advance(int64_t *d_step, int64_t by, cudaStream_t s);
 // persistent bulk-copy pipelined variant (k_step_pipe.cu); grid = CTAs to launch

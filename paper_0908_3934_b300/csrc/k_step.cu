@@ -1,21 +1,25 @@
 // The fused step kernel: one launch advances every node of a network by dt.
 //
 // One CTA owns a row block -- consecutive target nodes (rows of the by-target
-// edge list) holding at most kStepCap - 3 edges, or one longer row on its own.
-//   1. Each thread prefetches the state of "its" row (v~(n) from the ring, w~, c~).
-//   2. The CTA streams its edge chunk with 16-byte loads (coalesced: a warp reads
-//      512 contiguous bytes per load), gathers the delayed value of each edge,
-//      S_j(n) = sum_e w_e v~_src(n - D_e)      (Eq. Yjset, Sec. 2)
-//      read from ring slot (n - D_e) & (R - 1), and parks w_e * v~ in shared memory.
-//   3. Row sums: short rows by their own thread, long rows by a whole warp with a
-//      shuffle reduction.
-//   4. Per node: stimulus U (pulses, Philox background), the FHN Euler update about
-//      the rest point (Sec. 3.1, Eq. fnstate), the history write, the low-pass
-//      readout and, on sample steps, the noisy observation (Sec. 3.3), events
-//      and first arrivals.
-// The kernel boundary is the step barrier: every read is of step n (or older),
-// every write is of step n + 1, and slot (n + 1) & (R - 1) is never read in step n
-// because every delay is at most R - 2.
+// edge list) holding at most T * EPT - 3 edges and T rows, or one longer row on
+// its own.  Launches are chained with programmatic dependent launch:
+//   0. the CTA lets the next step's grid start as soon as SMs free up
+//      (griddepcontrol.launch_dependents);
+//   1. it loads everything that does not change between steps -- its block
+//      descriptor, row pointers, caller ids and its packed edge records
+//      (16-byte loads, a warp reads 512 contiguous bytes) -- while the previous
+//      step may still be finishing;
+//   2. griddepcontrol.wait: from here on the previous step's writes are visible;
+//      it reads the state of its rows (v~(n) from the ring, w~, c~, background
+//      counters) and gathers, for every edge,
+//        S_j(n) = sum_e w_e v~_src(n - D_e)      (Eq. Yjset, Sec. 2)
+//      from ring slot (n - D_e) & (R - 1), parking w_e * v~ in shared memory;
+//   3. row sums: short rows by their own thread, long rows by a warp (shuffle);
+//   4. per node: stimulus, the FHN Euler update about the rest point (Sec. 3.1,
+//      Eq. fnstate), the history write, the low-pass readout and, on sample
+//      steps, the noisy observation (Sec. 3.3), events and first arrivals.
+// Every read of step data is of step n (or older) and every write is of step n+1;
+// slot (n + 1) & (R - 1) is never read in step n because every delay is <= R - 2.
 #include "step_common.cuh"
 
 namespace gn {
@@ -23,44 +27,73 @@ namespace {
 
 using namespace step;
 
-template <int T, int EPT, bool kPacked, bool kStream>
-__global__ void __launch_bounds__(T) k_step(const StepArgs a, const int k)
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <int T, int EPT, int MINB, bool kPacked, bool kStream>
+__global__ void __launch_bounds__(T, MINB) k_step(const StepArgs a, const int k)
 {
     constexpr int CAP = T * EPT;
+    constexpr int NQ = EPT / 4;  // edge quads per thread
     constexpr int kWarpRow = 48;  // rows longer than this are summed by a warp
     __shared__ float s_prod[CAP];
     __shared__ float s_long[T];
     __shared__ int s_rp[T + 1];
 
-    const int64_t n = *a.d_step + k;
+    pdl_launch_dependents();
     const int t = threadIdx.x;
-    const int r0 = a.blk[blockIdx.x], r1 = a.blk[blockIdx.x + 1];
+    const int4 d = __ldg(a.bdesc + blockIdx.x);
+    const int r0 = d.x, r1 = d.y, e0 = d.z, e1 = d.w;
     const int nr = r1 - r0;
-    const int e0 = a.row_ptr[r0], e1 = a.row_ptr[r1];
     const int r = r0 + t;
 
+    // 1. step-invariant inputs
+    int32_t orig = kLoad;
+    if (t < nr) {
+        s_rp[t] = __ldg(a.row_ptr + r);
+        orig = __ldg(a.perm + r);
+    }
+    if (t == 0) s_rp[nr] = e1;
+    const bool lng = (nr == 1) && (e1 - e0 > CAP - 3);
+    const int ebase = e0 & ~3;
+    RawQuad<kPacked> q[NQ];
+    float4 wv[NQ];
+    if (!lng) {
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) {
+            const int eb = ebase + 4 * (t + T * i);
+            if (eb < e1) {
+                q[i] = load_raw<kPacked, kStream>(a, eb);
+                wv[i] = ld_weight4<kStream>(a.ew + eb);
+            }
+        }
+    }
+
+    // 2. step data of the previous launch
+    pdl_wait();
+    const int64_t n = *a.d_step + k;
     float v = 0.0f;
     float2 wc = make_float2(0.0f, 0.0f);
+    int32_t cnt0 = kLoad;
     if (t < nr) {
         v = a.ring[(n & a.ring_mask) * a.ring_stride + r];
         wc = a.wc[r];
-        s_rp[t] = a.row_ptr[r];
+        if (a.bg_thr) cnt0 = a.bgc[r];
     }
-    if (t == 0) s_rp[nr] = e1;
 
-    if (nr == 1 && e1 - e0 > CAP - 3) {
+    if (lng) {
         // one long row: the whole CTA loops over chunks of its edges
         float p = 0.0f;
-        for (int base = e0 & ~3; base < e1; base += CAP) {
+        for (int base = ebase; base < e1; base += CAP) {
 #pragma unroll
-            for (int i = 0; i < EPT / 4; ++i) {
+            for (int i = 0; i < NQ; ++i) {
                 const int eb = base + 4 * (t + T * i);
-                const EdgeQuad<kPacked> q = load_quad<kPacked, kStream>(a, eb);
-                const float4 wv = ld_weight4<kStream>(a.ew + eb);
-                const float wq[4] = {wv.x, wv.y, wv.z, wv.w};
+                const EdgeQuad<kPacked> qq = load_quad<kPacked, kStream>(a, eb);
+                const float4 ww = ld_weight4<kStream>(a.ew + eb);
+                const float wq[4] = {ww.x, ww.y, ww.z, ww.w};
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
-                    if (eb + j >= e0 && eb + j < e1) p = fmaf(wq[j], gather(a, n, q.src[j], q.d[j]), p);
+                    if (eb + j >= e0 && eb + j < e1) p = fmaf(wq[j], gather(a, n, qq.src[j], qq.d[j]), p);
             }
         }
         p = warp_sum(p);
@@ -69,24 +102,25 @@ __global__ void __launch_bounds__(T) k_step(const StepArgs a, const int k)
         if (t == 0) {
             float S = 0.0f;
             for (int i = 0; i < T / 32; ++i) S += s_long[i];
-            node_update(a, r0, n, v, wc, S);
+            node_update(a, r0, n, v, wc, S, orig, cnt0);
         }
         return;
     }
 
-    // 2. stream the chunk [e0, e1) and park the delayed products in shared memory
-    const int ebase = e0 & ~3;
+    // gathers: every edge of the block, products parked in shared memory
 #pragma unroll
-    for (int i = 0; i < EPT / 4; ++i) {
+    for (int i = 0; i < NQ; ++i) {
         const int eb = ebase + 4 * (t + T * i);
         if (eb >= e1) break;
-        const EdgeQuad<kPacked> q = load_quad<kPacked, kStream>(a, eb);
-        const float4 wv = ld_weight4<kStream>(a.ew + eb);
-        const float wq[4] = {wv.x, wv.y, wv.z, wv.w};
+        const float wq[4] = {wv[i].x, wv[i].y, wv[i].z, wv[i].w};
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int e = eb + j;
-            if (e >= e0 && e < e1) s_prod[e - e0] = wq[j] * gather(a, n, q.src[j], q.d[j]);
+            if (e >= e0 && e < e1) {
+                uint32_t src, dd;
+                decode<kPacked>(a, q[i], j, src, dd);
+                s_prod[e - e0] = wq[j] * gather(a, n, src, dd);
+            }
         }
     }
     __syncthreads();
@@ -116,7 +150,7 @@ __global__ void __launch_bounds__(T) k_step(const StepArgs a, const int k)
     if (warp_row) S = s_long[t];
 
     // 4. node update
-    if (t < nr) node_update(a, r, n, v, wc, S);
+    if (t < nr) node_update(a, r, n, v, wc, S, orig, cnt0);
 }
 
 __global__ void k_advance(int64_t *d_step, int64_t by)
@@ -124,25 +158,49 @@ __global__ void k_advance(int64_t *d_step, int64_t by)
     *d_step += by;
 }
 
+template <int T, int EPT, int MINB, bool kPacked, bool kStream>
+cudaError_t launch_pdl(const StepArgs &a, int n_blocks, int k, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(n_blocks));
+    cfg.blockDim = dim3(T);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_step<T, EPT, MINB, kPacked, kStream>, a, k);
+}
+
+template <int T, int EPT, int MINB>
+cudaError_t launch_shape(const StepArgs &a, int n_blocks, int k, bool packed, bool stream_edges, cudaStream_t s)
+{
+    if (packed)
+        return stream_edges ? launch_pdl<T, EPT, MINB, true, true>(a, n_blocks, k, s)
+                            : launch_pdl<T, EPT, MINB, true, false>(a, n_blocks, k, s);
+    return stream_edges ? launch_pdl<T, EPT, MINB, false, true>(a, n_blocks, k, s)
+                        : launch_pdl<T, EPT, MINB, false, false>(a, n_blocks, k, s);
+}
+
 }  // namespace
 
-cudaError_t launch_step(const StepArgs &a, int n_blocks, int k, bool packed, bool stream_edges,
+// {threads, edges per thread, CTAs per SM the register allocation must allow}
+const StepShape kStepShapes[kNumStepShapes] = {{256, 8, 1}, {256, 8, 8}, {128, 16, 1}, {128, 8, 16}, {512, 8, 1}};
+
+cudaError_t launch_step(const StepArgs &a, int n_blocks, int k, int shape, bool packed, bool stream_edges,
                         cudaStream_t s)
 {
-    constexpr int T = kStepThreads, EPT = kStepEPT;
     if (n_blocks <= 0) return cudaSuccess;
-    if (packed) {
-        if (stream_edges)
-            k_step<T, EPT, true, true><<<n_blocks, T, 0, s>>>(a, k);
-        else
-            k_step<T, EPT, true, false><<<n_blocks, T, 0, s>>>(a, k);
-    } else {
-        if (stream_edges)
-            k_step<T, EPT, false, true><<<n_blocks, T, 0, s>>>(a, k);
-        else
-            k_step<T, EPT, false, false><<<n_blocks, T, 0, s>>>(a, k);
+    switch (shape) {
+        case 0: return launch_shape<256, 8, 1>(a, n_blocks, k, packed, stream_edges, s);
+        case 1: return launch_shape<256, 8, 8>(a, n_blocks, k, packed, stream_edges, s);
+        case 2: return launch_shape<128, 16, 1>(a, n_blocks, k, packed, stream_edges, s);
+        case 3: return launch_shape<128, 8, 16>(a, n_blocks, k, packed, stream_edges, s);
+        case 4: return launch_shape<512, 8, 1>(a, n_blocks, k, packed, stream_edges, s);
+        default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_advance(int64_t *d_step, int64_t by, cudaStream_t s)

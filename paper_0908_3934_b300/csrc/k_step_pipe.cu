@@ -258,7 +258,7 @@ cudaError_t prepare_variant(int *ctas)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_step_pipe<T, EPT, S, KEYB, kStream>, T, smem);
 }
 
-constexpr int kT = 256, kEPT = 8, kS = 3;
+constexpr int kT = 256, kEPT = 8, kS = 3;  // shape 0 of kStepShapes
 
 }  // namespace
 

@@ -6,8 +6,9 @@
 // neighbouring targets sit close in memory and their gathers share sectors),
 // builds the by-target edge list with each row sorted by source, packs each edge
 // as (src << log2 R) | D next to its FP32 weight, cuts the rows into blocks of at
-// most kStepCap - 3 edges for the step kernels, and captures a CUDA graph of
-// kGraphSteps step launches.  Everything is held in device memory; the host keeps
+// most T * EPT - 3 edges for the step kernels (the CTA shape is picked by timing
+// the candidates on the first gn_step unless the caller fixes the kernel), and
+// captures a CUDA graph of kGraphSteps step launches.  Everything is held in device memory; the host keeps
 // only the permutations and the delay table for output in the caller's order.
 #include <algorithm>
 #include <cmath>
@@ -38,8 +39,10 @@ struct gn_net {
     bool packed = true;
     bool stream_edges = true;
     int n_blocks = 0;
-    int step_kernel = 0;       // 0 persistent pipelined, 1 row block per CTA
+    int step_kernel = 0;       // 0 not chosen yet (autotune), 1 row block per CTA, 2 persistent pipelined
+    int shape = 0;             // index into gn::kStepShapes (kernel 2 uses shape 0)
     int grid = 0;              // CTAs per launch
+    std::vector<int32_t> h_row_ptr;  // host copy, to cut row blocks for another shape
     int32_t stride = 0;        // ring slot stride (floats)
     double v_rest = 0.0, w_rest = 0.0, dt = 0.0;
     int32_t sample_every = 1;
@@ -93,10 +96,145 @@ void sync(gn_net *net)
     }
 }
 
+cudaError_t launch_kind(const gn::StepArgs &a, int kind, int shape, int grid, int k, bool packed, bool stream_edges,
+                        cudaStream_t s)
+{
+    if (kind == 2) return gn::launch_step_pipe(a, grid, k, packed, stream_edges, s);
+    return gn::launch_step(a, a.n_blocks, k, shape, packed, stream_edges, s);
+}
+
 cudaError_t launch_one(const gn_net *net, int k, cudaStream_t s)
 {
-    if (net->step_kernel == 0) return gn::launch_step_pipe(net->args, net->grid, k, net->packed, net->stream_edges, s);
-    return gn::launch_step(net->args, net->n_blocks, k, net->packed, net->stream_edges, s);
+    return launch_kind(net->args, net->step_kernel, net->shape, net->grid, k, net->packed, net->stream_edges, s);
+}
+
+// Cut the row blocks for a CTA shape and point the kernel arguments at them.
+void set_blocks(gn_net *net, int shape)
+{
+    std::vector<int32_t> blk;
+    std::vector<int4> desc;
+    const gn::StepShape sh = gn::kStepShapes[shape];
+    gnrt::make_blocks(net->h_row_ptr, net->N, sh.threads * sh.ept, sh.threads, blk, desc);
+    net->blk.release();
+    net->bdesc.release();
+    net->blk.upload(blk, &net->bytes);
+    net->bdesc.upload(desc, &net->bytes);
+    net->n_blocks = static_cast<int>(desc.size());
+    net->args.blk = net->blk.p;
+    net->args.bdesc = net->bdesc.p;
+    net->args.n_blocks = net->n_blocks;
+    net->shape = shape;
+}
+
+void configure(gn_net *net, int kind, int shape)
+{
+    if (kind == 2) shape = 0;
+    set_blocks(net, shape);
+    net->step_kernel = kind;
+    if (kind == 2) {
+        int per_sm = 0, sms = 0;
+        cuda_check(gn::step_pipe_prepare(net->packed, net->stream_edges, &per_sm), "step kernel setup");
+        cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, net->device), "device query");
+        if (per_sm < 1) fail(GN_ECUDA, "the pipelined step kernel does not fit on an SM");
+        net->grid = std::min(net->n_blocks, per_sm * sms);
+    } else {
+        net->grid = net->n_blocks;
+    }
+    net->graph_stale = true;
+}
+
+// Autotuner: time every candidate (row-block kernel in each CTA shape, and the
+// persistent pipelined kernel) for a few steps on a scratch copy of the dynamic
+// state -- the network's own state is not touched -- and keep the fastest.
+void autotune(gn_net *net)
+{
+    const int32_t N = net->N;
+    size_t scratch_bytes = 0;
+    DevArray<float> ring, obs;
+    DevArray<float2> wc;
+    DevArray<int32_t> bgc, evn;
+    DevArray<int64_t> first, evs, dstep;
+    DevArray<unsigned long long> evc;
+    DevArray<unsigned int> status;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    auto cleanup = [&] {
+        ring.release(); obs.release(); wc.release(); bgc.release(); evn.release(); first.release();
+        evs.release(); dstep.release(); evc.release(); status.release();
+        if (t0) cudaEventDestroy(t0);
+        if (t1) cudaEventDestroy(t1);
+    };
+    int best_kind = 1, best_shape = 0;
+    try {
+        ring.alloc(net->ring.n, &scratch_bytes);
+        wc.alloc(net->wc.n, &scratch_bytes);
+        bgc.alloc(N, &scratch_bytes);
+        first.alloc(N, &scratch_bytes);
+        obs.alloc(N, &scratch_bytes);
+        evn.alloc(1024, &scratch_bytes);
+        evs.alloc(1024, &scratch_bytes);
+        evc.alloc(1, &scratch_bytes);
+        dstep.alloc(1, &scratch_bytes);
+        status.alloc(1, &scratch_bytes);
+        cuda_check(cudaMemsetAsync(ring.p, 0, ring.n * 4, net->stream), "memset");
+        cuda_check(cudaMemsetAsync(wc.p, 0, wc.n * 8, net->stream), "memset");
+        cuda_check(cudaMemsetAsync(bgc.p, 0, bgc.n * 4, net->stream), "memset");
+        cuda_check(cudaMemsetAsync(first.p, 0xff, first.n * 8, net->stream), "memset");
+        cuda_check(cudaMemsetAsync(evc.p, 0, 8, net->stream), "memset");
+        cuda_check(cudaMemsetAsync(status.p, 0, 4, net->stream), "memset");
+        cuda_check(cudaMemcpyAsync(dstep.p, &net->step, 8, cudaMemcpyHostToDevice, net->stream), "H2D");
+        cuda_check(cudaEventCreate(&t0), "event");
+        cuda_check(cudaEventCreate(&t1), "event");
+        float best = 1e30f;
+        struct Cand {
+            int kind, shape;
+        };
+        std::vector<Cand> cands;
+        for (int sh = 0; sh < gn::kNumStepShapes; ++sh) cands.push_back({1, sh});
+        cands.push_back({2, 0});
+        for (const Cand &c : cands) {
+            configure(net, c.kind, c.shape);
+            gn::StepArgs a = net->args;
+            a.ring = ring.p;
+            a.wc = wc.p;
+            a.bgc = bgc.p;
+            a.first = first.p;
+            a.obs = obs.p;
+            a.obs_cap = 1;
+            a.ev_node = evn.p;
+            a.ev_step = evs.p;
+            a.ev_count = evc.p;
+            a.ev_cap = 1024;
+            a.d_step = dstep.p;
+            a.status = status.p;
+            const int warm = 3, timed = 8;
+            for (int k = 0; k < warm; ++k)
+                cuda_check(launch_kind(a, c.kind, net->shape, net->grid, k, net->packed, net->stream_edges,
+                                       net->stream),
+                           "autotune launch");
+            cuda_check(cudaEventRecord(t0, net->stream), "event");
+            for (int k = 0; k < timed; ++k)
+                cuda_check(launch_kind(a, c.kind, net->shape, net->grid, k, net->packed, net->stream_edges,
+                                       net->stream),
+                           "autotune launch");
+            cuda_check(cudaEventRecord(t1, net->stream), "event");
+            cuda_check(cudaEventSynchronize(t1), "autotune");
+            float ms = 0.0f;
+            cuda_check(cudaEventElapsedTime(&ms, t0, t1), "event");
+            if (ms < best) {
+                best = ms;
+                best_kind = c.kind;
+                best_shape = c.shape;
+            }
+        }
+        unsigned int st = 0;
+        cuda_check(cudaMemcpy(&st, status.p, 4, cudaMemcpyDeviceToHost), "D2H status");
+        if (st) fail(GN_ETIMEOUT, "a bounded device-side wait gave up while autotuning");
+    } catch (...) {
+        cleanup();
+        throw;
+    }
+    cleanup();
+    configure(net, best_kind, best_shape);
 }
 
 void build_graph(gn_net *net)
@@ -201,7 +339,8 @@ gn_status gn_net_create(const gn_net_desc *desc, gn_net **out)
         std::vector<int64_t> clamped;
         gnrt::quantise_delays(desc, 1, net->stream, delays, clamped);
         gnrt::HostNet h;
-        gnrt::host_build(desc, std::move(delays[0]), clamped[0], gn::kStepCap, gn::kStepMaxRows, h);
+        const gn::StepShape sh0 = gn::kStepShapes[0];
+        gnrt::host_build(desc, std::move(delays[0]), clamped[0], sh0.threads * sh0.ept, sh0.threads, h);
 
         net->N = h.N;
         net->dim = h.dim;
@@ -221,6 +360,7 @@ gn_status gn_net_create(const gn_net_desc *desc, gn_net **out)
         net->perm = h.perm;
         net->inv = h.inv;
         net->delay = h.delay;
+        net->h_row_ptr = h.row_ptr;
         // edges are streamed past L2 unless they fit comfortably in it
         net->stream_edges = static_cast<double>(net->E) * (net->packed ? 8.0 : 12.0) > 48e6;
 
@@ -230,8 +370,6 @@ gn_status gn_net_create(const gn_net_desc *desc, gn_net **out)
         net->ew.upload(h.w, &net->bytes);
         net->bias.upload(h.bias, &net->bytes);
         net->row_ptr.upload(h.row_ptr, &net->bytes);
-        net->blk.upload(h.blk, &net->bytes);
-        net->bdesc.upload(h.desc, &net->bytes);
         net->d_perm.upload(h.perm, &net->bytes);
         net->ring.alloc(static_cast<size_t>(net->R) * net->stride, &net->bytes);
         net->wc.alloc(static_cast<size_t>(N) + 2, &net->bytes);
@@ -261,8 +399,6 @@ gn_status gn_net_create(const gn_net_desc *desc, gn_net **out)
         a.ekey = net->ekey.p;
         a.ew = net->ew.p;
         a.row_ptr = net->row_ptr.p;
-        a.blk = net->blk.p;
-        a.bdesc = net->bdesc.p;
         a.ring = net->ring.p;
         a.wc = net->wc.p;
         a.bgc = net->bgc.p;
@@ -279,16 +415,9 @@ gn_status gn_net_create(const gn_net_desc *desc, gn_net **out)
         a.d_step = net->d_step.p;
         a.status = net->status.p;
 
-        net->step_kernel = desc->step_kernel;
-        if (net->step_kernel == 0) {
-            int per_sm = 0, sms = 0;
-            cuda_check(gn::step_pipe_prepare(net->packed, net->stream_edges, &per_sm), "step kernel setup");
-            cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, desc->device), "device query");
-            if (per_sm < 1) fail(GN_ECUDA, "the pipelined step kernel does not fit on an SM");
-            net->grid = std::min(net->n_blocks, per_sm * sms);
-        } else {
-            net->grid = net->n_blocks;
-        }
+        // the kernel is fixed now or timed on the first gn_step (kind 0)
+        configure(net, desc->step_kernel == 2 ? 2 : 1, 0);
+        if (desc->step_kernel == 0) net->step_kernel = 0;
         cuda_check(cudaDeviceSynchronize(), "create");
     });
     if (st != GN_OK) {
@@ -324,6 +453,8 @@ gn_status gn_net_get_info(const gn_net *net, gn_net_info *info)
         info->edge_format = net->packed ? 0 : 1;
         info->n_blocks = net->n_blocks;
         info->step_kernel = net->step_kernel;
+        info->step_threads = gn::kStepShapes[net->shape].threads;
+        info->step_edges_per_thread = gn::kStepShapes[net->shape].ept;
         info->grid = net->grid;
         info->step = net->step;
         info->samples = net->step / net->sample_every;
@@ -384,6 +515,7 @@ gn_status gn_step(gn_net *net, int64_t n_steps)
         if (n_steps < 0) fail(GN_EINVAL, "n_steps < 0");
         if (n_steps == 0) return;
         DeviceGuard dg(net->device);
+        if (net->step_kernel == 0) autotune(net);
         if (net->graph_stale) build_graph(net);
         int64_t left = n_steps;
         while (left >= kGraphSteps) {

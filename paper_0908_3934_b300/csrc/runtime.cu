@@ -97,7 +97,7 @@ void validate_desc(const gn_net_desc *d)
     if (d->coupling != GN_COUPLE_REST && d->coupling != GN_COUPLE_RAW) fail(GN_EINVAL, "unknown coupling");
     if (d->ring_depth < 0 || (d->ring_depth & (d->ring_depth - 1))) fail(GN_EINVAL, "ring_depth must be a power of two");
     if (d->edge_format != 0 && d->edge_format != 1) fail(GN_EINVAL, "edge_format must be 0 or 1");
-    if (d->step_kernel != 0 && d->step_kernel != 1) fail(GN_EINVAL, "step_kernel must be 0 or 1");
+    if (d->step_kernel < 0 || d->step_kernel > 2) fail(GN_EINVAL, "step_kernel must be 0, 1 or 2");
     const int64_t np = static_cast<int64_t>(d->n_nodes) * d->dim;
     for (int64_t i = 0; i < np; ++i)
         if (!std::isfinite(d->pos[i])) fail(GN_EINVAL, "position %lld is not finite", (long long)i);
@@ -334,31 +334,34 @@ void host_build(const gn_net_desc *d, std::vector<int32_t> delay, int64_t n_clam
         }
     }
 
-    // row blocks: consecutive rows with at most block_cap - 3 edges and block_rows
-    // rows; a longer row gets a block of its own
-    h.blk.assign(1, 0);
-    const int cap = block_cap - 3;
+    make_blocks(h.row_ptr, N, block_cap, block_rows, h.blk, h.desc);
+}
+
+void make_blocks(const std::vector<int32_t> &row_ptr, int32_t N, int cap_edges, int max_rows, std::vector<int32_t> &blk,
+                 std::vector<int4> &desc)
+{
+    blk.assign(1, 0);
+    const int cap = cap_edges - 3;
     int32_t r = 0;
     while (r < N) {
-        const int deg0 = h.row_ptr[r + 1] - h.row_ptr[r];
+        const int deg0 = row_ptr[r + 1] - row_ptr[r];
         if (deg0 > cap) {
-            h.blk.push_back(++r);
+            blk.push_back(++r);
             continue;
         }
         int edges = 0, rows = 0;
-        while (r < N && rows < block_rows) {
-            const int deg = h.row_ptr[r + 1] - h.row_ptr[r];
+        while (r < N && rows < max_rows) {
+            const int deg = row_ptr[r + 1] - row_ptr[r];
             if (deg > cap || edges + deg > cap) break;
             edges += deg;
             ++rows;
             ++r;
         }
-        h.blk.push_back(r);
+        blk.push_back(r);
     }
-    const int nb = h.n_blocks();
-    h.desc.resize(nb);
-    for (int b = 0; b < nb; ++b)
-        h.desc[b] = make_int4(h.blk[b], h.blk[b + 1], h.row_ptr[h.blk[b]], h.row_ptr[h.blk[b + 1]]);
+    const int nb = static_cast<int>(blk.size()) - 1;
+    desc.resize(nb);
+    for (int b = 0; b < nb; ++b) desc[b] = make_int4(blk[b], blk[b + 1], row_ptr[blk[b]], row_ptr[blk[b + 1]]);
 }
 
 void fill_step_params(const gn_net_desc *d, const HostNet &h, gn::StepArgs &a)

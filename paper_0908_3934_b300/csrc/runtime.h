@@ -95,6 +95,11 @@ struct HostNet {
 void host_build(const gn_net_desc *d, std::vector<int32_t> delay, int64_t n_clamped, int block_cap, int block_rows,
                 HostNet &h);
 
+// Row blocks of consecutive rows with at most cap - 3 edges and max_rows rows
+// (a longer row alone), and their {r0, r1, e0, e1} descriptors.
+void make_blocks(const std::vector<int32_t> &row_ptr, int32_t N, int cap, int max_rows, std::vector<int32_t> &blk,
+                 std::vector<int4> &desc);
+
 // Scalar fields of the step arguments (FHN about the rest point, readout, sizes).
 void fill_step_params(const gn_net_desc *d, const HostNet &h, gn::StepArgs &a);
 

@@ -5,6 +5,8 @@
 #include "philox.cuh"
 #include "ptx.cuh"
 
+#include <climits>
+
 namespace gn {
 namespace step {
 
@@ -62,6 +64,46 @@ __device__ __forceinline__ EdgeQuad<kPacked> load_quad(const StepArgs &a, int64_
     return q;
 }
 
+// Raw edge records of four consecutive edges, held in registers until they are
+// decoded: one 16-byte word (packed keys) or two (wide keys).
+template <bool kPacked>
+struct RawQuad {
+    uint4 k0;
+};
+template <>
+struct RawQuad<false> {
+    uint4 k0, k1;
+};
+
+template <bool kPacked, bool kStream>
+__device__ __forceinline__ RawQuad<kPacked> load_raw(const StepArgs &a, int64_t eb)
+{
+    RawQuad<kPacked> r;
+    if constexpr (kPacked) {
+        r.k0 = ld_edge4<kStream>(static_cast<const uint32_t *>(a.ekey) + eb);
+    } else {
+        const uint2 *base = static_cast<const uint2 *>(a.ekey) + eb;
+        r.k0 = ld_edge4<kStream>(base);
+        r.k1 = ld_edge4<kStream>(base + 2);
+    }
+    return r;
+}
+
+template <bool kPacked>
+__device__ __forceinline__ void decode(const StepArgs &a, const RawQuad<kPacked> &r, int j, uint32_t &src,
+                                       uint32_t &d)
+{
+    if constexpr (kPacked) {
+        const uint32_t k = j == 0 ? r.k0.x : j == 1 ? r.k0.y : j == 2 ? r.k0.z : r.k0.w;
+        src = k >> a.dbits;
+        d = k & ((1u << a.dbits) - 1u);
+    } else {
+        const uint4 &h = j < 2 ? r.k0 : r.k1;
+        src = (j & 1) ? h.z : h.x;
+        d = (j & 1) ? h.w : h.y;
+    }
+}
+
 __device__ __forceinline__ float gather(const StepArgs &a, int64_t n, uint32_t src, uint32_t d)
 {
     const int64_t slot = (n - static_cast<int64_t>(d)) & a.ring_mask;
@@ -76,8 +118,13 @@ __device__ __forceinline__ float gather_hint(const StepArgs &a, int64_t n, uint3
     return ldg_hint(a.ring + slot * a.ring_stride + src, pol);
 }
 
+constexpr int32_t kLoad = INT32_MIN;  // "not prefetched" marker for node_update
+
 // Stimulus, FHN Euler step, history write, readout, noise, events, arrival.
-__device__ __forceinline__ void node_update(const StepArgs &a, int r, int64_t n, float v, float2 wc, float S)
+// `orig` (caller id) and `cnt0` (background counter) may be prefetched by the
+// caller; kLoad makes node_update read them itself.
+__device__ __forceinline__ void node_update(const StepArgs &a, int r, int64_t n, float v, float2 wc, float S,
+                                            int32_t orig = kLoad, int32_t cnt0 = kLoad)
 {
     float U = 0.0f;
     const int n_pulses = *a.n_pulses;
@@ -90,10 +137,9 @@ __device__ __forceinline__ void node_update(const StepArgs &a, int r, int64_t n,
         for (int p = lo; p < n_pulses && a.p_node[p] == r; ++p)
             if (a.p_on[p] <= n && n < a.p_off[p]) U += a.p_amp[p];
     }
-    int32_t orig = -1;
     if (a.bg_thr) {
-        orig = __ldg(a.perm + r);
-        const int32_t c0 = a.bgc[r];
+        if (orig == kLoad) orig = __ldg(a.perm + r);
+        const int32_t c0 = cnt0 == kLoad ? a.bgc[r] : cnt0;
         int32_t cnt = c0;
         if (draw(a.bg_seed, static_cast<uint32_t>(orig), n, kStreamBackground).x < a.bg_thr) cnt = a.bg_width;
         if (cnt > 0) {
@@ -124,7 +170,7 @@ __device__ __forceinline__ void node_update(const StepArgs &a, int r, int64_t n,
 
     if (((n + 1) % a.sample_every) == 0) {
         const int64_t k = (n + 1) / a.sample_every - 1;
-        if (orig < 0) orig = __ldg(a.perm + r);
+        if (orig == kLoad) orig = __ldg(a.perm + r);
         const float xi = gauss_from(draw(a.obs_seed, static_cast<uint32_t>(orig), k, kStreamObservation));
         const float y = fmaf(a.gain, a.vrest + c1, a.offset) + a.sigma * xi;
         a.obs[(k % a.obs_cap) * a.N + orig] = y;  // rows are written in the caller's node order

@@ -57,7 +57,8 @@ class gn_net_info(C.Structure):
     _fields_ = [
         ("n_nodes", C.c_int32), ("n_edges", C.c_int64), ("dim", C.c_int32), ("ring_depth", C.c_int32),
         ("max_delay", C.c_int32), ("min_delay", C.c_int32), ("n_clamped", C.c_int64),
-        ("edge_format", C.c_int32), ("n_blocks", C.c_int32), ("step_kernel", C.c_int32), ("grid", C.c_int32),
+        ("edge_format", C.c_int32), ("n_blocks", C.c_int32), ("step_kernel", C.c_int32),
+        ("step_threads", C.c_int32), ("step_edges_per_thread", C.c_int32), ("grid", C.c_int32),
         ("step", C.c_int64), ("samples", C.c_int64),
         ("v_rest", C.c_double), ("w_rest", C.c_double), ("device_bytes", C.c_size_t),
     ]

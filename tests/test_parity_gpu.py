@@ -143,7 +143,7 @@ def test_random_small_nets_windows(seed):
 
 
 # ------------------------------------------------------------------ layouts and edge cases
-@pytest.mark.parametrize("step_kernel", [0, 1])
+@pytest.mark.parametrize("step_kernel", [1, 2])
 def test_wide_edge_format_and_caller_order(step_kernel):
     spec = netgen.tiny()
     for kw in (dict(wide_edges=True), dict(renumber=False), dict(wide_edges=True, renumber=False)):
@@ -154,19 +154,20 @@ def test_wide_edge_format_and_caller_order(step_kernel):
         assert info["edge_format"] == (1 if kw.get("wide_edges") else 0) and info["step_kernel"] == step_kernel
 
 
-@pytest.mark.parametrize("step_kernel", [0, 1])
+@pytest.mark.parametrize("step_kernel", [0, 1, 2])
 def test_both_step_kernels_on_a_multi_block_net(step_kernel):
     """Thousands of row blocks, so the persistent kernel cycles every pipeline stage
     many times per step."""
     spec = netgen.large(n=30000, mean_deg=40, bg_rate_hz=100.0)
     net = Net(spec, step_kernel=step_kernel)
-    info = net.gn_net_get_info()
-    assert info["n_blocks"] > 100 and info["step_kernel"] == step_kernel
     worst, n_ev = windowed(spec, net, 200, start=60)
     assert_windows(worst)
+    info = net.gn_net_get_info()
+    assert info["n_blocks"] > 100
+    assert info["step_kernel"] == step_kernel if step_kernel else info["step_kernel"] in (1, 2)
 
 
-@pytest.mark.parametrize("step_kernel", [0, 1])
+@pytest.mark.parametrize("step_kernel", [1, 2])
 def test_long_rows_take_the_whole_block_path(step_kernel):
     """A hub with in-degree 5000 (> one block's edge capacity) and ragged rows."""
     rng = np.random.default_rng(9)
