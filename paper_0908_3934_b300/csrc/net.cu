@@ -12,6 +12,8 @@
 // only the permutations and the delay table for output in the caller's order.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -143,11 +145,64 @@ void configure(gn_net *net, int kind, int shape)
     net->graph_stale = true;
 }
 
+// Key of a tuning result: device, sizes and the options that change the kernel.
+std::string tune_key(const gn_net *net)
+{
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, net->device);
+    std::string name(prop.name);
+    for (char &ch : name)
+        if (ch == ' ') ch = '_';
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s|sm%d|N%d|E%lld|R%d|p%d|s%d|bg%d", name.c_str(), prop.multiProcessorCount, net->N,
+             static_cast<long long>(net->E), net->R, net->packed ? 1 : 0, net->stream_edges ? 1 : 0,
+             net->args.bg_thr ? 1 : 0);
+    return buf;
+}
+
+// Autotune cache: the file named by GN_AUTOTUNE_CACHE holds lines "key kind shape".
+bool tune_cache_lookup(const std::string &key, int *kind, int *shape)
+{
+    const char *path = getenv("GN_AUTOTUNE_CACHE");
+    if (!path || !*path) return false;
+    FILE *f = fopen(path, "r");
+    if (!f) return false;
+    char k[256];
+    int a = 0, b = 0;
+    bool found = false;
+    while (fscanf(f, "%255s %d %d", k, &a, &b) == 3)
+        if (key == k && (a == 1 || a == 2) && b >= 0 && b < gn::kNumStepShapes) {
+            *kind = a;
+            *shape = b;
+            found = true;
+        }
+    fclose(f);
+    return found;
+}
+
+void tune_cache_store(const std::string &key, int kind, int shape)
+{
+    const char *path = getenv("GN_AUTOTUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d %d\n", key.c_str(), kind, shape);
+    fclose(f);
+}
+
 // Autotuner: time every candidate (row-block kernel in each CTA shape, and the
 // persistent pipelined kernel) for a few steps on a scratch copy of the dynamic
-// state -- the network's own state is not touched -- and keep the fastest.
+// state -- the network's own state is not touched -- and keep the fastest.  With
+// GN_AUTOTUNE_CACHE set, a cached choice for the same device and network sizes is
+// reused and new choices are appended.
 void autotune(gn_net *net)
 {
+    const std::string key = tune_key(net);
+    int cached_kind = 0, cached_shape = 0;
+    if (tune_cache_lookup(key, &cached_kind, &cached_shape)) {
+        configure(net, cached_kind, cached_shape);
+        return;
+    }
     const int32_t N = net->N;
     size_t scratch_bytes = 0;
     DevArray<float> ring, obs;
@@ -235,6 +290,7 @@ void autotune(gn_net *net)
     }
     cleanup();
     configure(net, best_kind, best_shape);
+    tune_cache_store(key, best_kind, best_shape);
 }
 
 void build_graph(gn_net *net)
