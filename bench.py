@@ -49,7 +49,8 @@ def workload(name: str, rank: int):
     import pickle
     gens = {"roofline": lambda: netgen.roofline(seed=4 + 1000 * rank),
             "large": lambda: netgen.large(seed=3 + 1000 * rank),
-            "tiny": lambda: netgen.tiny(seed=1 + 1000 * rank)}
+            "tiny": lambda: netgen.tiny(seed=1 + 1000 * rank),
+            "batch": lambda: netgen.batch(4096, seed0=1000 + 100000 * rank)}
     if name not in gens:
         raise SystemExit(f"unknown workload {name}")
     src = open(os.path.join(ROOT, "paper_0908_3934_b300", "netgen.py"), "rb").read()
@@ -184,6 +185,55 @@ def config_of(args, spec, world):
             "parallelism": f"replicas{world}"}
 
 
+def run_batched(args, local, stream, rank):
+    """4096 independent 2D networks (N log-uniform in [32, 4096]) advanced
+    `batch_steps` steps by one persistent launch, against looping the
+    single-network path over a random sample of the same networks."""
+    import torch
+    from paper_0908_3934_b300 import geonet
+    specs = workload("batch", rank)
+    E = sum(sp.n_edges for sp in specs)
+    N = sum(sp.n_nodes for sp in specs)
+    b = geonet.Batch(specs, device=local, stream=stream.cuda_stream, obs_capacity=64)
+    b.gn_batch_step(20)  # chooses the CTA size, warms up
+    b.gn_batch_synchronize()
+    steps = args.batch_steps
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    b.gn_batch_step(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t = ev0.elapsed_time(ev1) / 1e3
+    info = b.gn_batch_get_info()
+    b.gn_batch_destroy()
+    # looping the single-network path (one network after another, each replaying its
+    # own graph of step launches) over a random sample, extrapolated by count
+    rng = np.random.default_rng(11)
+    pick = rng.choice(len(specs), args.loop_sample, replace=False)
+    t_sample = 0.0
+    for i in pick:
+        net = geonet.Net(specs[i], device=local, stream=stream.cuda_stream, obs_capacity=64)
+        net.gn_step(20)
+        net.gn_synchronize()
+        ev0.record(stream)
+        net.gn_step(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t_sample += ev0.elapsed_time(ev1) / 1e3
+        net.gn_net_destroy()
+    t_loop = t_sample / len(pick) * len(specs)
+    return {"workload": f"{len(specs)} independent 2D nets, N log-uniform in [32, 4096], "
+                        f"{N} nodes, {E} edges, {steps} steps ({steps * 0.05:.0f} ms)",
+            "value": E * steps / t, "unit": METRIC, "seconds": t, "ms_per_step": t / steps * 1e3,
+            "rtf": steps * 0.05e-3 / t, "cta_threads": info["cta_threads"], "grid": info["grid"],
+            "gpu_launches": 1,
+            "loop_plain": {"value": E * steps / t_loop, "seconds_extrapolated": t_loop,
+                           "sample": f"{len(pick)} random nets timed one after another, "
+                                     f"{t_sample:.3f} s, extrapolated by count to {len(specs)}"},
+            "speedup_vs_loop": t_loop / t}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -196,6 +246,9 @@ def main():
     ap.add_argument("--e2e-chunk", type=int, default=1000, help="steps per host round trip in the e2e run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--obs-cap", type=int, default=4096, help="observation rows kept on the device")
+    ap.add_argument("--batch-steps", type=int, default=10000, help="steps of the batched measurement")
+    ap.add_argument("--loop-sample", type=int, default=32, help="networks timed by the looped comparison")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--step-kernel", type=int, default=0, choices=[0, 1, 2],
                     help="0: autotuned, 1: one row block per CTA, 2: persistent bulk-copy pipelined kernel")
     args = ap.parse_args()
@@ -312,6 +365,14 @@ def main():
                    "n_blocks": info["n_blocks"], "max_delay": info["max_delay"],
                    "device_bytes": info["device_bytes"]},
     }
+    if not args.no_batched:
+        bt = run_batched(args, local, stream, rank)
+        if world > 1:
+            tt = torch.tensor([bt["seconds"]], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            bt["value"] = bt["value"] * bt["seconds"] / tt.item() * world
+            bt["seconds"] = tt.item()
+        line["batched"] = bt
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(spec, args.cpu_steps)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}

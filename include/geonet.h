@@ -218,6 +218,63 @@ GN_API gn_status gn_get_events(gn_net *net, int32_t *node, int64_t *step, int64_
 GN_API gn_status gn_save_state(gn_net *net, void *buf, size_t cap, size_t *used);
 GN_API gn_status gn_load_state(gn_net *net, const void *buf, size_t size);
 
+/* ---------------------------------------------------------------------------
+ * Batched form: many independent networks (of any sizes) advanced together by
+ * one persistent launch per gn_batch_step, replayed from a captured CUDA graph.
+ * CTAs take networks from a work queue ordered largest first and run all the
+ * requested steps of a network before taking the next; the CTA size is chosen by
+ * timing the candidates on the first gn_batch_step.  Every network follows the
+ * same model and conventions as gn_net (Sec. 2, 3.1, 3.2.1, 3.3); per-network
+ * calls take the network's index in the descriptor array.
+ * ------------------------------------------------------------------------- */
+typedef struct gn_batch gn_batch;
+
+typedef struct {
+    int32_t n_nets;
+    int64_t n_nodes;             /* over all networks */
+    int64_t n_edges;
+    int64_t step;                /* common step counter */
+    int32_t cta_threads;         /* chosen CTA size (0 before the first step) */
+    int32_t grid;                /* persistent CTAs */
+    size_t device_bytes;
+} gn_batch_info;
+
+/* Copy and build n_nets networks on one device (descs[i].device must agree; the
+ * stream of descs[0] is used; obs_capacity of descs[0] applies to all, 0 = 256).
+ * Errors as gn_net_create, for the first network that fails. */
+GN_API gn_status gn_batch_create(const gn_net_desc *descs, int32_t n_nets, gn_batch **out);
+GN_API gn_status gn_batch_destroy(gn_batch *batch);
+GN_API gn_status gn_batch_get_info(const gn_batch *batch, gn_batch_info *info);
+GN_API gn_status gn_batch_get_net_info(const gn_batch *batch, int32_t net, gn_net_info *info);
+GN_API gn_status gn_batch_get_delays(const gn_batch *batch, int32_t net, int32_t *out);
+
+/* Replace every network's pulses at once: network i takes counts[i] consecutive
+ * entries of `pulses` (caller node ids of network i). */
+GN_API gn_status gn_batch_set_stimulus_all(gn_batch *batch, const gn_pulse *pulses, const int32_t *counts);
+GN_API gn_status gn_batch_set_background(gn_batch *batch, int32_t net, double rate_hz, float amp, double dur_ms,
+                                         uint64_t seed);
+
+/* Advance every network n_steps (one persistent launch; asynchronous). */
+GN_API gn_status gn_batch_step(gn_batch *batch, int64_t n_steps);
+GN_API gn_status gn_batch_synchronize(gn_batch *batch);
+
+/* Per-network views, as the gn_net calls of the same name. */
+GN_API gn_status gn_batch_observe(gn_batch *batch, int32_t net, float *out, int64_t max_samples,
+                                  int64_t *first_sample, int64_t *written);
+GN_API gn_status gn_batch_get_state(gn_batch *batch, int32_t net, float *v, float *w, float *c, int32_t *bg_count,
+                                    int64_t *step);
+GN_API gn_status gn_batch_get_history(gn_batch *batch, int32_t net, float *out, int32_t depth);
+GN_API gn_status gn_batch_get_arrivals(gn_batch *batch, int32_t net, int64_t *first_arrival);
+GN_API gn_status gn_batch_get_events(gn_batch *batch, int32_t net, int32_t *node, int64_t *step, int64_t cap,
+                                     int64_t *n_total);
+
+/* Move the common step counter (clears every network's events and resets the
+ * observation cursors), then set one network's state at that step as
+ * gn_set_state does. */
+GN_API gn_status gn_batch_set_step(gn_batch *batch, int64_t step);
+GN_API gn_status gn_batch_set_state(gn_batch *batch, int32_t net, const float *hist, int32_t depth, const float *w,
+                                    const float *c, const int32_t *bg_count);
+
 /* Thread-local message of the last failing call ("" if none). */
 GN_API const char *gn_last_error(void);
 

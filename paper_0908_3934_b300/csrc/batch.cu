@@ -1,0 +1,754 @@
+// Host runtime of the batched form (gn_batch_* in include/geonet.h): many
+// independent networks in pooled device arrays, advanced together by one
+// persistent launch of k_batch replayed from a captured graph.
+//
+// gn_batch_create builds every network exactly as gn_net_create does (one FP64
+// delay launch for the whole batch, Morton renumbering and the by-target edge list
+// per network), then concatenates their arrays into pools; each network's step
+// arguments point into the pools.  The work queue is ordered largest first.  The
+// CTA size of k_batch is picked on the first gn_batch_step by timing the
+// candidates on a scratch copy of the dynamic state.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "runtime.h"
+
+using gnrt::cuda_check;
+using gnrt::DevArray;
+using gnrt::DeviceGuard;
+using gnrt::fail;
+using gnrt::guarded;
+
+namespace {
+
+// Host view of one member network.
+struct Member {
+    int32_t N = 0;
+    int64_t E = 0;
+    int32_t R = 0, stride = 0, dmax = 0, dmin = 0;
+    int64_t n_clamped = 0;
+    bool packed = true;
+    double v_rest = 0.0, w_rest = 0.0, dt = 0.0;
+    int32_t sample_every = 1;
+    int64_t node_off = 0, ring_off = 0, edge_off = 0, keyw_off = 0, rp_off = 0, obs_off = 0, ev_off = 0;
+    int64_t ev_cap = 0, pulse_off = 0, pulse_cap = 0, read_cursor = 0;
+    int64_t desc_off[gn::kNumBatchShapes] = {};
+    int32_t n_blocks[gn::kNumBatchShapes] = {};
+    std::vector<int32_t> perm, inv, delay;
+};
+
+}  // namespace
+
+struct gn_batch {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int32_t n_nets = 0;
+    int64_t obs_cap = 0;
+    int64_t step = 0;
+    int shape = -1;  // -1: autotune on the first step
+    int grid = 0;
+    size_t bytes = 0;
+    std::vector<Member> m;
+    std::vector<gn::StepArgs> args;  // host copy, shape-independent fields
+    std::vector<int32_t> order;      // largest first
+    DevArray<uint8_t> ekey;
+    DevArray<float> ew, ring, bias, obs, p_amp;
+    DevArray<float2> wc;
+    DevArray<int32_t> row_ptr, bgc, perm, ev_node, p_node, npulses, d_order, queue;
+    DevArray<int64_t> first, ev_step, p_on, p_off, d_step;
+    DevArray<unsigned long long> ev_count;
+    DevArray<unsigned int> status;
+    DevArray<int4> bdesc[gn::kNumBatchShapes];
+    DevArray<gn::StepArgs> d_args;
+    cudaGraphExec_t graph = nullptr;
+    int64_t graph_steps = 0;
+
+    ~gn_batch()
+    {
+        if (graph) cudaGraphExecDestroy(graph);
+        ekey.release();
+        for (auto *a : {&ew, &ring, &bias, &obs, &p_amp}) a->release();
+        wc.release();
+        for (auto *a : {&row_ptr, &bgc, &perm, &ev_node, &p_node, &npulses, &d_order, &queue}) a->release();
+        for (auto *a : {&first, &ev_step, &p_on, &p_off, &d_step}) a->release();
+        ev_count.release();
+        status.release();
+        for (auto &a : bdesc) a.release();
+        d_args.release();
+        if (own_stream && stream) cudaStreamDestroy(stream);
+    }
+};
+
+namespace {
+
+void check_batch(const gn_batch *b, int32_t net = 0)
+{
+    if (!b) fail(GN_EINVAL, "batch handle is NULL");
+    if (net < 0 || net >= b->n_nets) fail(GN_EINVAL, "network index %d out of range", net);
+}
+
+void sync(gn_batch *b)
+{
+    cuda_check(cudaStreamSynchronize(b->stream), "kernel execution");
+    unsigned int st = 0;
+    cuda_check(cudaMemcpy(&st, b->status.p, 4, cudaMemcpyDeviceToHost), "D2H status");
+    if (st) {
+        cudaMemset(b->status.p, 0, 4);
+        fail(st & gn::kStatusTimeout ? GN_ETIMEOUT : GN_EINTERNAL, "device status word %u", st);
+    }
+}
+
+// Device array of step arguments for a CTA shape (block descriptors differ per shape).
+std::vector<gn::StepArgs> args_for_shape(const gn_batch *b, int shape)
+{
+    std::vector<gn::StepArgs> out = b->args;
+    for (int i = 0; i < b->n_nets; ++i) {
+        out[i].bdesc = b->bdesc[shape].p + b->m[i].desc_off[shape];
+        out[i].n_blocks = b->m[i].n_blocks[shape];
+    }
+    return out;
+}
+
+void upload_args(gn_batch *b, int shape)
+{
+    const std::vector<gn::StepArgs> a = args_for_shape(b, shape);
+    cuda_check(cudaMemcpy(b->d_args.p, a.data(), a.size() * sizeof(gn::StepArgs), cudaMemcpyHostToDevice), "H2D args");
+}
+
+void set_shape(gn_batch *b, int shape)
+{
+    int per_sm = 0, sms = 0;
+    cuda_check(gn::batch_occupancy(shape, &per_sm), "occupancy");
+    cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device), "device query");
+    if (per_sm < 1) fail(GN_ECUDA, "the batch kernel does not fit on an SM");
+    b->shape = shape;
+    b->grid = std::max(1, std::min(b->n_nets, per_sm * sms));
+    upload_args(b, shape);
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+}
+
+void launch_steps(gn_batch *b, const gn::StepArgs *args, int64_t *d_step, int n_steps, int shape, int grid,
+                  cudaStream_t s)
+{
+    cuda_check(cudaMemsetAsync(b->queue.p, 0, 4, s), "queue reset");
+    cuda_check(gn::launch_batch(args, b->d_order.p, b->n_nets, b->queue.p, d_step, n_steps, shape, grid, s),
+               "batch launch");
+}
+
+// Time each CTA shape for a few steps on a scratch copy of the dynamic state.
+void autotune(gn_batch *b)
+{
+    size_t tmp = 0;
+    DevArray<float> ring, obs;
+    DevArray<float2> wc;
+    DevArray<int32_t> bgc, evn;
+    DevArray<int64_t> first, evs, dstep;
+    DevArray<unsigned long long> evc;
+    DevArray<gn::StepArgs> dargs;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    auto cleanup = [&] {
+        ring.release(); obs.release(); wc.release(); bgc.release(); evn.release(); first.release();
+        evs.release(); dstep.release(); evc.release(); dargs.release();
+        if (t0) cudaEventDestroy(t0);
+        if (t1) cudaEventDestroy(t1);
+    };
+    int best = 0;
+    try {
+        int64_t total_nodes = 0;
+        for (const Member &mm : b->m) total_nodes += mm.N;
+        ring.alloc(b->ring.n, &tmp);
+        wc.alloc(b->wc.n, &tmp);
+        bgc.alloc(total_nodes, &tmp);
+        first.alloc(total_nodes, &tmp);
+        obs.alloc(total_nodes, &tmp);
+        evn.alloc(b->n_nets, &tmp);
+        evs.alloc(b->n_nets, &tmp);
+        evc.alloc(b->n_nets, &tmp);
+        dstep.alloc(1, &tmp);
+        dargs.alloc(b->n_nets, &tmp);
+        cuda_check(cudaMemset(ring.p, 0, ring.n * 4), "memset");
+        cuda_check(cudaMemset(wc.p, 0, wc.n * 8), "memset");
+        cuda_check(cudaMemset(bgc.p, 0, bgc.n * 4), "memset");
+        cuda_check(cudaMemset(first.p, 0xff, first.n * 8), "memset");
+        cuda_check(cudaMemset(evc.p, 0, evc.n * 8), "memset");
+        cuda_check(cudaMemcpy(dstep.p, &b->step, 8, cudaMemcpyHostToDevice), "H2D");
+        cuda_check(cudaEventCreate(&t0), "event");
+        cuda_check(cudaEventCreate(&t1), "event");
+        float best_ms = 1e30f;
+        for (int shape = 0; shape < gn::kNumBatchShapes; ++shape) {
+            std::vector<gn::StepArgs> a = args_for_shape(b, shape);
+            for (int i = 0; i < b->n_nets; ++i) {
+                const Member &mm = b->m[i];
+                a[i].ring = ring.p + mm.ring_off;
+                a[i].wc = wc.p + mm.node_off + 2 * i;
+                a[i].bgc = bgc.p + mm.node_off;
+                a[i].first = first.p + mm.node_off;
+                a[i].obs = obs.p + mm.node_off;
+                a[i].obs_cap = 1;
+                a[i].ev_node = evn.p + i;
+                a[i].ev_step = evs.p + i;
+                a[i].ev_count = evc.p + i;
+                a[i].ev_cap = 1;
+            }
+            cuda_check(cudaMemcpy(dargs.p, a.data(), a.size() * sizeof(gn::StepArgs), cudaMemcpyHostToDevice), "H2D");
+            int per_sm = 0, sms = 0;
+            cuda_check(gn::batch_occupancy(shape, &per_sm), "occupancy");
+            cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device), "device query");
+            const int grid = std::max(1, std::min(b->n_nets, per_sm * sms));
+            launch_steps(b, dargs.p, dstep.p, 2, shape, grid, b->stream);
+            cuda_check(cudaEventRecord(t0, b->stream), "event");
+            launch_steps(b, dargs.p, dstep.p, 16, shape, grid, b->stream);
+            cuda_check(cudaEventRecord(t1, b->stream), "event");
+            cuda_check(cudaEventSynchronize(t1), "autotune");
+            float ms = 0.0f;
+            cuda_check(cudaEventElapsedTime(&ms, t0, t1), "event");
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = shape;
+            }
+        }
+    } catch (...) {
+        cleanup();
+        throw;
+    }
+    cleanup();
+    set_shape(b, best);
+}
+
+void build_graph(gn_batch *b, int64_t n_steps)
+{
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    cudaStream_t cs;
+    cuda_check(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "cudaStreamCreate");
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        e = cudaMemsetAsync(b->queue.p, 0, 4, cs);
+        if (e == cudaSuccess)
+            e = gn::launch_batch(b->d_args.p, b->d_order.p, b->n_nets, b->queue.p, b->d_step.p,
+                                 static_cast<int>(n_steps), b->shape, b->grid, cs);
+        if (e == cudaSuccess) e = gn::launch_advance(b->d_step.p, n_steps, cs);
+        cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    cuda_check(e, "graph capture of the batch step");
+    b->graph_steps = n_steps;
+}
+
+template <class T>
+void to_caller(const Member &mm, const T *internal, T *out)
+{
+    for (int32_t r = 0; r < mm.N; ++r) out[mm.perm[r]] = internal[r];
+}
+
+}  // namespace
+
+extern "C" {
+
+gn_status gn_batch_create(const gn_net_desc *descs, int32_t n_nets, gn_batch **out)
+{
+    if (!out) {
+        gnrt::set_error("out is NULL");
+        return GN_EINVAL;
+    }
+    *out = nullptr;
+    gn_batch *b = nullptr;
+    gn_status st = guarded([&] {
+        if (!descs || n_nets <= 0) fail(GN_EINVAL, "need at least one network");
+        for (int i = 0; i < n_nets; ++i) {
+            gnrt::validate_desc(descs + i);
+            if (descs[i].device != descs[0].device) fail(GN_EINVAL, "all networks of a batch share one device");
+        }
+        b = new gn_batch();
+        b->device = descs[0].device;
+        b->n_nets = n_nets;
+        DeviceGuard dg(b->device);
+        if (descs[0].cuda_stream) {
+            b->stream = static_cast<cudaStream_t>(descs[0].cuda_stream);
+        } else {
+            cuda_check(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking), "cudaStreamCreate");
+            b->own_stream = true;
+        }
+        std::vector<std::vector<int32_t>> delays;
+        std::vector<int64_t> clamped;
+        gnrt::quantise_delays(descs, n_nets, b->stream, delays, clamped);
+
+        // host build of every member, then pooled layout
+        b->m.resize(n_nets);
+        b->args.resize(n_nets);
+        std::vector<gnrt::HostNet> hs(n_nets);
+        int64_t nodes = 0, ring = 0, keyw = 0, edges = 0, rp = 0, obs = 0, ev = 0;
+        int64_t descs_n[gn::kNumBatchShapes] = {};
+        b->obs_cap = descs[0].obs_capacity > 0 ? descs[0].obs_capacity : 256;
+        std::vector<std::vector<int4>> shape_desc(gn::kNumBatchShapes);
+        for (int i = 0; i < n_nets; ++i) {
+            gnrt::HostNet &h = hs[i];
+            const int cap0 = gn::batch_block_cap(0);
+            gnrt::host_build(descs + i, std::move(delays[i]), clamped[i], cap0, gn::kBatchThreads[0], h);
+            Member &mm = b->m[i];
+            mm.N = h.N;
+            mm.E = h.E;
+            mm.R = h.R;
+            mm.stride = h.stride;
+            mm.dmax = h.dmax;
+            mm.dmin = h.dmin;
+            mm.n_clamped = h.n_clamped;
+            mm.packed = h.packed;
+            mm.v_rest = h.v_rest;
+            mm.w_rest = h.w_rest;
+            mm.dt = descs[i].dt_ms;
+            mm.sample_every = descs[i].obs.sample_every;
+            mm.perm = h.perm;
+            mm.inv = h.inv;
+            mm.delay = h.delay;
+            mm.node_off = nodes;
+            mm.ring_off = ring;
+            mm.keyw_off = keyw;
+            mm.edge_off = edges;
+            mm.rp_off = rp;
+            mm.obs_off = obs;
+            mm.ev_off = ev;
+            mm.ev_cap = std::max<int64_t>(1024, 8 * static_cast<int64_t>(h.N));
+            for (int s = 0; s < gn::kNumBatchShapes; ++s) {
+                std::vector<int32_t> blk;
+                std::vector<int4> d;
+                gnrt::make_blocks(h.row_ptr, h.N, gn::batch_block_cap(s), gn::kBatchThreads[s], blk, d);
+                mm.desc_off[s] = descs_n[s];
+                mm.n_blocks[s] = static_cast<int32_t>(d.size());
+                descs_n[s] += static_cast<int64_t>(d.size());
+                shape_desc[s].insert(shape_desc[s].end(), d.begin(), d.end());
+            }
+            nodes += h.N;
+            ring += static_cast<int64_t>(h.R) * h.stride;
+            // every network's key bytes and weights start on a 256-byte boundary
+            // (the kernel reads them with 16-byte vector loads)
+            keyw += (static_cast<int64_t>(h.key.size()) * 4 + 255) / 256 * 256;
+            edges += (static_cast<int64_t>(h.w.size()) + 63) / 64 * 64;
+            rp += static_cast<int64_t>(h.row_ptr.size());
+            obs += b->obs_cap * h.N;
+            ev += mm.ev_cap;
+            gnrt::fill_step_params(descs + i, h, b->args[i]);
+        }
+        // pools
+        b->ekey.alloc(keyw, &b->bytes);
+        b->ew.alloc(edges, &b->bytes);
+        b->row_ptr.alloc(rp, &b->bytes);
+        b->perm.alloc(nodes, &b->bytes);
+        for (int i = 0; i < n_nets; ++i) {
+            const gnrt::HostNet &h = hs[i];
+            const Member &mm = b->m[i];
+            cuda_check(cudaMemcpy(b->ekey.p + mm.keyw_off, h.key.data(), h.key.size() * 4, cudaMemcpyHostToDevice), "H2D");
+            cuda_check(cudaMemcpy(b->ew.p + mm.edge_off, h.w.data(), h.w.size() * 4, cudaMemcpyHostToDevice), "H2D");
+            cuda_check(cudaMemcpy(b->row_ptr.p + mm.rp_off, h.row_ptr.data(), h.row_ptr.size() * 4, cudaMemcpyHostToDevice),
+                       "H2D");
+            cuda_check(cudaMemcpy(b->perm.p + mm.node_off, h.perm.data(), h.perm.size() * 4, cudaMemcpyHostToDevice), "H2D");
+        }
+        bool any_raw = false;
+        for (int i = 0; i < n_nets; ++i) any_raw = any_raw || !hs[i].bias.empty();
+        if (any_raw) {
+            b->bias.alloc(nodes, &b->bytes);
+            for (int i = 0; i < n_nets; ++i)
+                if (!hs[i].bias.empty())
+                    cuda_check(cudaMemcpy(b->bias.p + b->m[i].node_off, hs[i].bias.data(), hs[i].bias.size() * 4,
+                                          cudaMemcpyHostToDevice),
+                               "H2D");
+        }
+        for (int s = 0; s < gn::kNumBatchShapes; ++s) b->bdesc[s].upload(shape_desc[s], &b->bytes);
+        hs.clear();
+        b->ring.alloc(ring, &b->bytes);
+        b->wc.alloc(nodes + 2 * static_cast<int64_t>(n_nets), &b->bytes);
+        b->bgc.alloc(nodes, &b->bytes);
+        b->first.alloc(nodes, &b->bytes);
+        b->obs.alloc(obs, &b->bytes);
+        b->ev_node.alloc(ev, &b->bytes);
+        b->ev_step.alloc(ev, &b->bytes);
+        b->ev_count.alloc(n_nets, &b->bytes);
+        b->npulses.alloc(n_nets, &b->bytes);
+        b->status.alloc(1, &b->bytes);
+        b->d_step.alloc(1, &b->bytes);
+        b->queue.alloc(1, &b->bytes);
+        b->d_args.alloc(n_nets, &b->bytes);
+        cuda_check(cudaMemset(b->ring.p, 0, b->ring.n * 4), "memset");
+        cuda_check(cudaMemset(b->wc.p, 0, b->wc.n * 8), "memset");
+        cuda_check(cudaMemset(b->bgc.p, 0, b->bgc.n * 4), "memset");
+        cuda_check(cudaMemset(b->first.p, 0xff, b->first.n * 8), "memset");
+        cuda_check(cudaMemset(b->obs.p, 0, b->obs.n * 4), "memset");
+        cuda_check(cudaMemset(b->ev_count.p, 0, b->ev_count.n * 8), "memset");
+        cuda_check(cudaMemset(b->npulses.p, 0, b->npulses.n * 4), "memset");
+        cuda_check(cudaMemset(b->status.p, 0, 4), "memset");
+        cuda_check(cudaMemset(b->d_step.p, 0, 8), "memset");
+        for (int i = 0; i < n_nets; ++i) {
+            const Member &mm = b->m[i];
+            gn::StepArgs &a = b->args[i];
+            a.ekey = b->ekey.p + mm.keyw_off;
+            a.ew = b->ew.p + mm.edge_off;
+            a.row_ptr = b->row_ptr.p + mm.rp_off;
+            a.blk = nullptr;
+            a.ring = b->ring.p + mm.ring_off;
+            a.wc = b->wc.p + mm.node_off + 2 * i;
+            a.bgc = b->bgc.p + mm.node_off;
+            a.bias = (b->bias.p && descs[i].coupling == GN_COUPLE_RAW) ? b->bias.p + mm.node_off : nullptr;
+            a.first = b->first.p + mm.node_off;
+            a.perm = b->perm.p + mm.node_off;
+            a.n_pulses = b->npulses.p + i;
+            a.p_node = nullptr;
+            a.p_on = nullptr;
+            a.p_off = nullptr;
+            a.p_amp = nullptr;
+            a.obs = b->obs.p + mm.obs_off;
+            a.obs_cap = b->obs_cap;
+            a.ev_node = b->ev_node.p + mm.ev_off;
+            a.ev_step = b->ev_step.p + mm.ev_off;
+            a.ev_count = b->ev_count.p + i;
+            a.ev_cap = mm.ev_cap;
+            a.d_step = b->d_step.p;
+            a.status = b->status.p;
+        }
+        // largest networks first
+        b->order.resize(n_nets);
+        std::iota(b->order.begin(), b->order.end(), 0);
+        std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) {
+            return b->m[x].E + b->m[x].N > b->m[y].E + b->m[y].N;
+        });
+        b->d_order.upload(b->order, &b->bytes);
+        upload_args(b, 0);
+        b->shape = -1;
+        cuda_check(cudaDeviceSynchronize(), "create");
+    });
+    if (st != GN_OK) {
+        delete b;
+        return st;
+    }
+    *out = b;
+    return GN_OK;
+}
+
+gn_status gn_batch_destroy(gn_batch *b)
+{
+    if (!b) return GN_OK;
+    return guarded([&] {
+        DeviceGuard dg(b->device);
+        cudaStreamSynchronize(b->stream);
+        delete b;
+    });
+}
+
+gn_status gn_batch_get_info(const gn_batch *b, gn_batch_info *info)
+{
+    return guarded([&] {
+        check_batch(b);
+        if (!info) fail(GN_EINVAL, "info is NULL");
+        info->n_nets = b->n_nets;
+        info->n_nodes = 0;
+        info->n_edges = 0;
+        for (const Member &mm : b->m) {
+            info->n_nodes += mm.N;
+            info->n_edges += mm.E;
+        }
+        info->step = b->step;
+        info->cta_threads = b->shape >= 0 ? gn::kBatchThreads[b->shape] : 0;
+        info->grid = b->grid;
+        info->device_bytes = b->bytes;
+    });
+}
+
+gn_status gn_batch_get_net_info(const gn_batch *b, int32_t net, gn_net_info *info)
+{
+    return guarded([&] {
+        check_batch(b, net);
+        if (!info) fail(GN_EINVAL, "info is NULL");
+        const Member &mm = b->m[net];
+        std::memset(info, 0, sizeof *info);
+        info->n_nodes = mm.N;
+        info->n_edges = mm.E;
+        info->ring_depth = mm.R;
+        info->max_delay = mm.dmax;
+        info->min_delay = mm.dmin;
+        info->n_clamped = mm.n_clamped;
+        info->edge_format = mm.packed ? 0 : 1;
+        info->n_blocks = b->shape >= 0 ? mm.n_blocks[b->shape] : mm.n_blocks[0];
+        info->step = b->step;
+        info->samples = b->step / mm.sample_every;
+        info->v_rest = mm.v_rest;
+        info->w_rest = mm.w_rest;
+    });
+}
+
+gn_status gn_batch_get_delays(const gn_batch *b, int32_t net, int32_t *out)
+{
+    return guarded([&] {
+        check_batch(b, net);
+        if (!out && b->m[net].E) fail(GN_EINVAL, "out is NULL");
+        std::copy(b->m[net].delay.begin(), b->m[net].delay.end(), out);
+    });
+}
+
+gn_status gn_batch_set_stimulus_all(gn_batch *b, const gn_pulse *pulses, const int32_t *counts)
+{
+    return guarded([&] {
+        check_batch(b);
+        if (!counts) fail(GN_EINVAL, "counts is NULL");
+        DeviceGuard dg(b->device);
+        sync(b);
+        std::vector<int32_t> nd;
+        std::vector<int64_t> on, off;
+        std::vector<float> amp;
+        std::vector<int32_t> cnt(b->n_nets);
+        int64_t k = 0;
+        for (int i = 0; i < b->n_nets; ++i) {
+            if (counts[i] < 0) fail(GN_EINVAL, "negative pulse count");
+            gnrt::PulseTable t = gnrt::make_pulses(pulses ? pulses + k : nullptr, counts[i], b->m[i].N, b->m[i].dt,
+                                                   b->m[i].inv);
+            k += counts[i];
+            b->m[i].pulse_off = static_cast<int64_t>(nd.size());
+            cnt[i] = static_cast<int32_t>(t.node.size());
+            nd.insert(nd.end(), t.node.begin(), t.node.end());
+            on.insert(on.end(), t.on.begin(), t.on.end());
+            off.insert(off.end(), t.off.begin(), t.off.end());
+            amp.insert(amp.end(), t.amp.begin(), t.amp.end());
+        }
+        b->p_node.release();
+        b->p_on.release();
+        b->p_off.release();
+        b->p_amp.release();
+        b->p_node.upload(nd, &b->bytes);
+        b->p_on.upload(on, &b->bytes);
+        b->p_off.upload(off, &b->bytes);
+        b->p_amp.upload(amp, &b->bytes);
+        cuda_check(cudaMemcpy(b->npulses.p, cnt.data(), cnt.size() * 4, cudaMemcpyHostToDevice), "H2D");
+        for (int i = 0; i < b->n_nets; ++i) {
+            gn::StepArgs &a = b->args[i];
+            const bool has = cnt[i] > 0;
+            a.p_node = has ? b->p_node.p + b->m[i].pulse_off : nullptr;
+            a.p_on = has ? b->p_on.p + b->m[i].pulse_off : nullptr;
+            a.p_off = has ? b->p_off.p + b->m[i].pulse_off : nullptr;
+            a.p_amp = has ? b->p_amp.p + b->m[i].pulse_off : nullptr;
+        }
+        upload_args(b, b->shape >= 0 ? b->shape : 0);
+    });
+}
+
+gn_status gn_batch_set_background(gn_batch *b, int32_t net, double rate_hz, float amp, double dur_ms, uint64_t seed)
+{
+    return guarded([&] {
+        check_batch(b, net);
+        if (!(rate_hz >= 0.0) || !std::isfinite(rate_hz) || !std::isfinite(amp) || !(dur_ms >= 0.0))
+            fail(GN_EINVAL, "bad background parameters");
+        DeviceGuard dg(b->device);
+        sync(b);
+        gn::StepArgs &a = b->args[net];
+        a.bg_thr = gnrt::background_threshold(rate_hz, b->m[net].dt);
+        a.bg_amp = amp;
+        a.bg_width = static_cast<int32_t>(llround(dur_ms / b->m[net].dt));
+        a.bg_seed = seed;
+        upload_args(b, b->shape >= 0 ? b->shape : 0);
+    });
+}
+
+gn_status gn_batch_step(gn_batch *b, int64_t n_steps)
+{
+    return guarded([&] {
+        check_batch(b);
+        if (n_steps < 0 || n_steps > 2147483647LL) fail(GN_EINVAL, "n_steps out of range");
+        if (n_steps == 0) return;
+        DeviceGuard dg(b->device);
+        if (b->shape < 0) autotune(b);
+        if (!b->graph || b->graph_steps != n_steps) build_graph(b, n_steps);
+        cuda_check(cudaGraphLaunch(b->graph, b->stream), "cudaGraphLaunch");
+        b->step += n_steps;
+    });
+}
+
+gn_status gn_batch_synchronize(gn_batch *b)
+{
+    return guarded([&] {
+        check_batch(b);
+        DeviceGuard dg(b->device);
+        sync(b);
+    });
+}
+
+gn_status gn_batch_observe(gn_batch *b, int32_t net, float *out, int64_t max_samples, int64_t *first_sample,
+                           int64_t *written)
+{
+    return guarded([&] {
+        check_batch(b, net);
+        if (max_samples < 0) fail(GN_EINVAL, "max_samples < 0");
+        DeviceGuard dg(b->device);
+        sync(b);
+        Member &mm = b->m[net];
+        const int64_t produced = b->step / mm.sample_every;
+        bool lost = false;
+        if (produced - mm.read_cursor > b->obs_cap) {
+            mm.read_cursor = produced - b->obs_cap;
+            lost = true;
+        }
+        const int64_t m = std::min(max_samples, produced - mm.read_cursor);
+        if (first_sample) *first_sample = mm.read_cursor;
+        if (written) *written = m;
+        const float *base = b->obs.p + mm.obs_off;
+        int64_t done = out ? 0 : m;
+        while (done < m) {
+            const int64_t k = (mm.read_cursor + done) % b->obs_cap;
+            const int64_t len = std::min(m - done, b->obs_cap - k);
+            cuda_check(cudaMemcpy(out + done * mm.N, base + k * mm.N, len * mm.N * 4, cudaMemcpyDeviceToHost),
+                       "D2H observations");
+            done += len;
+        }
+        mm.read_cursor += m;
+        if (lost) fail(GN_EOVERFLOW, "observation buffer overflowed: older samples were lost");
+    });
+}
+
+gn_status gn_batch_get_state(gn_batch *b, int32_t net, float *v, float *w, float *c, int32_t *bg_count,
+                             int64_t *step)
+{
+    return guarded([&] {
+        check_batch(b, net);
+        DeviceGuard dg(b->device);
+        sync(b);
+        const Member &mm = b->m[net];
+        std::vector<float> t(mm.N);
+        if (v) {
+            cuda_check(cudaMemcpy(t.data(), b->ring.p + mm.ring_off + (b->step & (mm.R - 1)) * mm.stride, mm.N * 4,
+                                  cudaMemcpyDeviceToHost),
+                       "D2H v");
+            to_caller(mm, t.data(), v);
+        }
+        if (w || c) {
+            std::vector<float2> t2(mm.N);
+            cuda_check(cudaMemcpy(t2.data(), b->wc.p + mm.node_off + 2 * net, mm.N * 8, cudaMemcpyDeviceToHost), "D2H wc");
+            for (int32_t r = 0; r < mm.N; ++r) {
+                if (w) w[mm.perm[r]] = t2[r].x;
+                if (c) c[mm.perm[r]] = t2[r].y;
+            }
+        }
+        if (bg_count) {
+            std::vector<int32_t> t3(mm.N);
+            cuda_check(cudaMemcpy(t3.data(), b->bgc.p + mm.node_off, mm.N * 4, cudaMemcpyDeviceToHost), "D2H bg");
+            to_caller(mm, t3.data(), bg_count);
+        }
+        if (step) *step = b->step;
+    });
+}
+
+gn_status gn_batch_set_step(gn_batch *b, int64_t step)
+{
+    return guarded([&] {
+        check_batch(b);
+        if (step < 0) fail(GN_EINVAL, "step < 0");
+        DeviceGuard dg(b->device);
+        sync(b);
+        cuda_check(cudaMemcpy(b->d_step.p, &step, 8, cudaMemcpyHostToDevice), "H2D step");
+        cuda_check(cudaMemset(b->ev_count.p, 0, b->ev_count.n * 8), "memset");
+        b->step = step;
+        for (Member &mm : b->m) mm.read_cursor = step / mm.sample_every;
+    });
+}
+
+gn_status gn_batch_set_state(gn_batch *b, int32_t net, const float *hist, int32_t depth, const float *w,
+                             const float *c, const int32_t *bg_count)
+{
+    return guarded([&] {
+        check_batch(b, net);
+        const Member &mm = b->m[net];
+        if (depth < 1 || depth > mm.R || !hist) fail(GN_EINVAL, "hist must hold 1..ring_depth rows");
+        DeviceGuard dg(b->device);
+        sync(b);
+        const int32_t N = mm.N;
+        std::vector<float> ring(static_cast<size_t>(mm.R) * mm.stride, 0.0f);
+        for (int32_t k = 0; k < depth; ++k) {
+            const int64_t slot = (b->step - k) & (mm.R - 1);
+            for (int32_t j = 0; j < N; ++j) ring[slot * mm.stride + mm.inv[j]] = hist[static_cast<int64_t>(k) * N + j];
+        }
+        std::vector<float2> wc(N);
+        std::vector<int32_t> bg(N, 0);
+        for (int32_t j = 0; j < N; ++j) {
+            wc[mm.inv[j]] = make_float2(w ? w[j] : 0.0f, c ? c[j] : 0.0f);
+            if (bg_count) bg[mm.inv[j]] = bg_count[j];
+        }
+        cuda_check(cudaMemcpy(b->ring.p + mm.ring_off, ring.data(), ring.size() * 4, cudaMemcpyHostToDevice), "H2D");
+        cuda_check(cudaMemcpy(b->wc.p + mm.node_off + 2 * net, wc.data(), N * 8ull, cudaMemcpyHostToDevice), "H2D");
+        cuda_check(cudaMemcpy(b->bgc.p + mm.node_off, bg.data(), N * 4ull, cudaMemcpyHostToDevice), "H2D");
+        cuda_check(cudaMemset(b->first.p + mm.node_off, 0xff, N * 8ull), "memset");
+        cuda_check(cudaMemset(b->ev_count.p + net, 0, 8), "memset");
+    });
+}
+
+gn_status gn_batch_get_history(gn_batch *b, int32_t net, float *out, int32_t depth)
+{
+    return guarded([&] {
+        check_batch(b, net);
+        const Member &mm = b->m[net];
+        if (depth < 1 || depth > mm.R || !out) fail(GN_EINVAL, "depth must be in [1, ring_depth]");
+        DeviceGuard dg(b->device);
+        sync(b);
+        std::vector<float> t(mm.N);
+        for (int32_t k = 0; k < depth; ++k) {
+            const int64_t slot = (b->step - k) & (mm.R - 1);
+            cuda_check(cudaMemcpy(t.data(), b->ring.p + mm.ring_off + slot * mm.stride, mm.N * 4, cudaMemcpyDeviceToHost),
+                       "D2H");
+            to_caller(mm, t.data(), out + static_cast<int64_t>(k) * mm.N);
+        }
+    });
+}
+
+gn_status gn_batch_get_arrivals(gn_batch *b, int32_t net, int64_t *first_arrival)
+{
+    return guarded([&] {
+        check_batch(b, net);
+        if (!first_arrival) fail(GN_EINVAL, "out is NULL");
+        DeviceGuard dg(b->device);
+        sync(b);
+        const Member &mm = b->m[net];
+        std::vector<int64_t> t(mm.N);
+        cuda_check(cudaMemcpy(t.data(), b->first.p + mm.node_off, mm.N * 8, cudaMemcpyDeviceToHost), "D2H");
+        to_caller(mm, t.data(), first_arrival);
+    });
+}
+
+gn_status gn_batch_get_events(gn_batch *b, int32_t net, int32_t *node, int64_t *step, int64_t cap, int64_t *n_total)
+{
+    return guarded([&] {
+        check_batch(b, net);
+        if (cap < 0 || (cap > 0 && (!node || !step))) fail(GN_EINVAL, "bad output buffers");
+        DeviceGuard dg(b->device);
+        sync(b);
+        const Member &mm = b->m[net];
+        unsigned long long cnt = 0;
+        cuda_check(cudaMemcpy(&cnt, b->ev_count.p + net, 8, cudaMemcpyDeviceToHost), "D2H");
+        const int64_t kept = std::min<int64_t>(static_cast<int64_t>(cnt), mm.ev_cap);
+        std::vector<int32_t> nd(kept);
+        std::vector<int64_t> st(kept);
+        if (kept) {
+            cuda_check(cudaMemcpy(nd.data(), b->ev_node.p + mm.ev_off, kept * 4, cudaMemcpyDeviceToHost), "D2H");
+            cuda_check(cudaMemcpy(st.data(), b->ev_step.p + mm.ev_off, kept * 8, cudaMemcpyDeviceToHost), "D2H");
+        }
+        std::vector<std::pair<int64_t, int32_t>> ev(kept);
+        for (int64_t i = 0; i < kept; ++i) ev[i] = {st[i], mm.perm[nd[i]]};
+        std::sort(ev.begin(), ev.end());
+        const int64_t m = std::min(cap, kept);
+        for (int64_t i = 0; i < m; ++i) {
+            step[i] = ev[i].first;
+            node[i] = ev[i].second;
+        }
+        if (n_total) *n_total = kept;
+        if (static_cast<int64_t>(cnt) > mm.ev_cap) fail(GN_EOVERFLOW, "event buffer overflowed (%llu events)", cnt);
+    });
+}
+
+}  // extern "C"

@@ -25,6 +25,7 @@ struct StepArgs {
     int32_t ring_stride;     // floats per ring slot: N rounded up (N + 4 -> multiple of 32)
     int32_t ring_mask;       // R - 1
     int32_t dbits;           // packed keys: bits of D
+    int32_t packed;          // 1: 32-bit packed keys, 0: 64-bit {src, D}
     const void *ekey;
     const float *ew;
     const int32_t *row_ptr;  // [N + 1]
@@ -87,6 +88,14 @@ cudaError_t launch_advance(int64_t *d_step, int64_t by, cudaStream_t s);
 cudaError_t launch_step_pipe(const StepArgs &a, int grid, int k, bool packed, bool stream_edges, cudaStream_t s);
 int step_pipe_smem_bytes(bool packed);
 cudaError_t step_pipe_prepare(bool packed, bool stream_edges, int *ctas_per_sm);
+// batched form (k_batch.cu): one persistent launch over many networks
+constexpr int kNumBatchShapes = 3;
+extern const int kBatchThreads[kNumBatchShapes];
+int batch_block_cap(int shape);
+cudaError_t launch_batch(const StepArgs *nets, const int *order, int n_nets, int *queue, const int64_t *d_step,
+                         int n_steps, int shape, int grid, cudaStream_t s);
+cudaError_t batch_occupancy(int shape, int *ctas_per_sm);
+
 cudaError_t launch_delay(int64_t n_edges, int32_t dim, const double *pos, const int32_t *src,
                          const int32_t *dst, const double *speed, double speed_scalar, double dt_ms,
                          int32_t *delay, uint8_t *clamped, cudaStream_t s);

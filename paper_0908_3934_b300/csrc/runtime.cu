@@ -372,6 +372,7 @@ void fill_step_params(const gn_net_desc *d, const HostNet &h, gn::StepArgs &a)
     a.ring_stride = h.stride;
     a.ring_mask = h.R - 1;
     a.dbits = h.dbits;
+    a.packed = h.packed ? 1 : 0;
     a.n_blocks = h.n_blocks();
     a.dt = static_cast<float>(d->dt_ms);
     a.k1 = static_cast<float>(f.a - 3.0 * f.b * vr * vr);

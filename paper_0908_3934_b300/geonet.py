@@ -53,6 +53,11 @@ class gn_pulse(C.Structure):
     _fields_ = [("node", C.c_int32), ("t_on_ms", C.c_double), ("t_off_ms", C.c_double), ("amp", C.c_float)]
 
 
+class gn_batch_info(C.Structure):
+    _fields_ = [("n_nets", C.c_int32), ("n_nodes", C.c_int64), ("n_edges", C.c_int64), ("step", C.c_int64),
+                ("cta_threads", C.c_int32), ("grid", C.c_int32), ("device_bytes", C.c_size_t)]
+
+
 class gn_net_info(C.Structure):
     _fields_ = [
         ("n_nodes", C.c_int32), ("n_edges", C.c_int64), ("dim", C.c_int32), ("ring_depth", C.c_int32),
@@ -84,6 +89,22 @@ _SIGS = {
     "gn_save_state": ([_P, _P, C.c_size_t, C.POINTER(C.c_size_t)], C.c_int),
     "gn_load_state": ([_P, _P, C.c_size_t], C.c_int),
     "gn_last_error": ([], C.c_char_p),
+    "gn_batch_create": ([C.POINTER(gn_net_desc), C.c_int32, C.POINTER(C.c_void_p)], C.c_int),
+    "gn_batch_destroy": ([_P], C.c_int),
+    "gn_batch_get_info": ([_P, _P], C.c_int),
+    "gn_batch_get_net_info": ([_P, C.c_int32, C.POINTER(gn_net_info)], C.c_int),
+    "gn_batch_get_delays": ([_P, C.c_int32, _P], C.c_int),
+    "gn_batch_set_stimulus_all": ([_P, _P, _P], C.c_int),
+    "gn_batch_set_background": ([_P, C.c_int32, C.c_double, C.c_float, C.c_double, C.c_uint64], C.c_int),
+    "gn_batch_step": ([_P, C.c_int64], C.c_int),
+    "gn_batch_synchronize": ([_P], C.c_int),
+    "gn_batch_observe": ([_P, C.c_int32, _P, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int64)], C.c_int),
+    "gn_batch_get_state": ([_P, C.c_int32, _P, _P, _P, _P, C.POINTER(C.c_int64)], C.c_int),
+    "gn_batch_get_history": ([_P, C.c_int32, _P, C.c_int32], C.c_int),
+    "gn_batch_get_arrivals": ([_P, C.c_int32, _P], C.c_int),
+    "gn_batch_get_events": ([_P, C.c_int32, _P, _P, C.c_int64, C.POINTER(C.c_int64)], C.c_int),
+    "gn_batch_set_step": ([_P, C.c_int64], C.c_int),
+    "gn_batch_set_state": ([_P, C.c_int32, _P, C.c_int32, _P, _P, _P], C.c_int),
 }
 
 _lib = None
@@ -118,6 +139,31 @@ def _c(a, dt):
     return None if a is None else np.ascontiguousarray(a, dtype=dt)
 
 
+def make_desc(spec, keep: list, *, device: int = 0, stream=None, obs_capacity: int = 0, event_capacity: int = 0,
+              renumber: bool = True, ring_depth: int | None = None, coupling: str | None = None,
+              wide_edges: bool = False, step_kernel: int = 0) -> gn_net_desc:
+    """Marshal a ``netgen.NetSpec``-like object into a gn_net_desc; the arrays it
+    points to are appended to ``keep`` (they must live until the create call)."""
+    k = dict(pos=_c(spec.pos, np.float64), src=_c(spec.src, np.int32), dst=_c(spec.dst, np.int32),
+             weight=_c(spec.weight, np.float32), speed=_c(spec.speed, np.float64), delay=_c(spec.delay, np.int32))
+    keep.append(k)
+    fhn = spec.fhn
+    obs = spec.obs
+    cpl = coupling or spec.coupling
+    return gn_net_desc(
+        n_nodes=spec.n_nodes, dim=spec.dim, pos=_ptr(k["pos"]), n_edges=spec.n_edges,
+        src=_ptr(k["src"]), dst=_ptr(k["dst"]), weight=_ptr(k["weight"]), speed=_ptr(k["speed"]),
+        speed_scalar=float(spec.speed_scalar or 0.0), delay_steps=_ptr(k["delay"]), dt_ms=spec.dt_ms,
+        fhn=gn_fhn_params(**{x: fhn[x] for x in ("a", "b", "c", "e", "f", "g", "i_ext")}),
+        obs=gn_obs_params(tau_ms=obs["tau_ms"], sample_every=obs["sample_every"], gain=obs["gain"],
+                          offset=obs["offset"], sigma=obs["sigma"], seed=obs["seed"]),
+        coupling=GN_COUPLE_RAW if cpl == "raw" else GN_COUPLE_REST, theta=spec.theta,
+        ring_depth=spec.ring_depth if ring_depth is None else ring_depth,
+        obs_capacity=obs_capacity, event_capacity=event_capacity, renumber=0 if renumber else -1,
+        edge_format=1 if wide_edges else 0, step_kernel=step_kernel,
+        cuda_stream=stream, device=device)
+
+
 class Net:
     """One network on the GPU, created from a ``netgen.NetSpec``-like object."""
 
@@ -125,32 +171,16 @@ class Net:
                  event_capacity: int = 0, renumber: bool = True, ring_depth: int | None = None,
                  coupling: str | None = None, wide_edges: bool = False, step_kernel: int = 0):
         L = lib()
-        self._keep = dict(pos=_c(spec.pos, np.float64), src=_c(spec.src, np.int32), dst=_c(spec.dst, np.int32),
-                          weight=_c(spec.weight, np.float32), speed=_c(spec.speed, np.float64),
-                          delay=_c(spec.delay, np.int32))
-        k = self._keep
-        fhn = spec.fhn
-        obs = spec.obs
-        cpl = coupling or spec.coupling
-        d = gn_net_desc(
-            n_nodes=spec.n_nodes, dim=spec.dim, pos=_ptr(k["pos"]), n_edges=spec.n_edges,
-            src=_ptr(k["src"]), dst=_ptr(k["dst"]), weight=_ptr(k["weight"]), speed=_ptr(k["speed"]),
-            speed_scalar=float(spec.speed_scalar or 0.0), delay_steps=_ptr(k["delay"]), dt_ms=spec.dt_ms,
-            fhn=gn_fhn_params(**{x: fhn[x] for x in ("a", "b", "c", "e", "f", "g", "i_ext")}),
-            obs=gn_obs_params(tau_ms=obs["tau_ms"], sample_every=obs["sample_every"], gain=obs["gain"],
-                              offset=obs["offset"], sigma=obs["sigma"], seed=obs["seed"]),
-            coupling=GN_COUPLE_RAW if cpl == "raw" else GN_COUPLE_REST, theta=spec.theta,
-            ring_depth=spec.ring_depth if ring_depth is None else ring_depth,
-            obs_capacity=obs_capacity, event_capacity=event_capacity, renumber=0 if renumber else -1,
-            edge_format=1 if wide_edges else 0, step_kernel=step_kernel,
-            cuda_stream=stream, device=device)
+        keep = []
+        d = make_desc(spec, keep, device=device, stream=stream, obs_capacity=obs_capacity,
+                      event_capacity=event_capacity, renumber=renumber, ring_depth=ring_depth, coupling=coupling,
+                      wide_edges=wide_edges, step_kernel=step_kernel)
         h = C.c_void_p()
         check(L.gn_net_create(C.byref(d), C.byref(h)))
         self.h = h
         self.n_nodes = spec.n_nodes
         self.n_edges = spec.n_edges
         self.spec = spec
-        del self._keep
         if spec.pulses:
             self.gn_set_stimulus(spec.pulses)
         bg = spec.background
@@ -256,6 +286,116 @@ class Net:
     def gn_load_state(self, blob: bytes):
         buf = (C.c_uint8 * len(blob)).from_buffer_copy(blob)
         check(lib().gn_load_state(self.h, buf, len(blob)))
+
+
+class Batch:
+    """Many independent networks advanced together (gn_batch_*); ``specs`` are
+    ``netgen.NetSpec``-like objects, their pulses and background are applied."""
+
+    def __init__(self, specs, *, device: int = 0, stream=None, obs_capacity: int = 0):
+        L = lib()
+        keep = []
+        n = len(specs)
+        descs = (gn_net_desc * n)()
+        for i, sp in enumerate(specs):
+            descs[i] = make_desc(sp, keep, device=device, stream=stream, obs_capacity=obs_capacity)
+        h = C.c_void_p()
+        check(L.gn_batch_create(descs, n, C.byref(h)))
+        self.h = h
+        self.specs = list(specs)
+        self.n_nets = n
+        counts = np.array([len(sp.pulses or []) for sp in specs], np.int32)
+        if counts.sum():
+            allp = (gn_pulse * int(counts.sum()))()
+            k = 0
+            for sp in specs:
+                for (node, t_on, t_off, amp) in sp.pulses or []:
+                    allp[k] = gn_pulse(node=node, t_on_ms=t_on, t_off_ms=t_off, amp=amp)
+                    k += 1
+            check(L.gn_batch_set_stimulus_all(h, allp, _ptr(counts)))
+        for i, sp in enumerate(specs):
+            bg = sp.background
+            if bg:
+                check(L.gn_batch_set_background(h, i, bg["rate_hz"], bg["amp"], bg["dur_ms"], bg["seed"]))
+
+    def gn_batch_destroy(self):
+        if getattr(self, "h", None):
+            check(lib().gn_batch_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.gn_batch_destroy()
+        except Exception:
+            pass
+
+    def gn_batch_get_info(self) -> dict:
+        i = gn_batch_info()
+        check(lib().gn_batch_get_info(self.h, C.byref(i)))
+        return {f: getattr(i, f) for f, _ in gn_batch_info._fields_}
+
+    def gn_batch_get_net_info(self, net: int) -> dict:
+        i = gn_net_info()
+        check(lib().gn_batch_get_net_info(self.h, net, C.byref(i)))
+        return {f: getattr(i, f) for f, _ in gn_net_info._fields_}
+
+    def gn_batch_get_delays(self, net: int) -> np.ndarray:
+        out = np.zeros(self.specs[net].n_edges, np.int32)
+        check(lib().gn_batch_get_delays(self.h, net, _ptr(out)))
+        return out
+
+    def gn_batch_step(self, n_steps: int):
+        check(lib().gn_batch_step(self.h, n_steps))
+
+    def gn_batch_synchronize(self):
+        check(lib().gn_batch_synchronize(self.h))
+
+    def gn_batch_observe(self, net: int, max_samples: int | None = None):
+        info = self.gn_batch_get_net_info(net)
+        if max_samples is None:
+            max_samples = info["samples"]
+        out = np.zeros((max(0, max_samples), self.specs[net].n_nodes), np.float32)
+        first = C.c_int64()
+        wr = C.c_int64()
+        st = check(lib().gn_batch_observe(self.h, net, _ptr(out), max_samples, C.byref(first), C.byref(wr)),
+                   allow=(GN_EOVERFLOW,))
+        return out[: wr.value], first.value, st
+
+    def gn_batch_get_state(self, net: int):
+        N = self.specs[net].n_nodes
+        v, w, c = (np.zeros(N, np.float32) for _ in range(3))
+        bg = np.zeros(N, np.int32)
+        st = C.c_int64()
+        check(lib().gn_batch_get_state(self.h, net, _ptr(v), _ptr(w), _ptr(c), _ptr(bg), C.byref(st)))
+        return dict(v=v, w=w, c=c, bg_count=bg, step=st.value)
+
+    def gn_batch_get_history(self, net: int, depth: int) -> np.ndarray:
+        out = np.zeros((depth, self.specs[net].n_nodes), np.float32)
+        check(lib().gn_batch_get_history(self.h, net, _ptr(out), depth))
+        return out
+
+    def gn_batch_get_arrivals(self, net: int) -> np.ndarray:
+        out = np.zeros(self.specs[net].n_nodes, np.int64)
+        check(lib().gn_batch_get_arrivals(self.h, net, _ptr(out)))
+        return out
+
+    def gn_batch_get_events(self, net: int, cap: int = 1 << 20):
+        node = np.zeros(cap, np.int32)
+        step = np.zeros(cap, np.int64)
+        n = C.c_int64()
+        st = check(lib().gn_batch_get_events(self.h, net, _ptr(node), _ptr(step), cap, C.byref(n)),
+                   allow=(GN_EOVERFLOW,))
+        m = min(cap, n.value)
+        return node[:m], step[:m], st
+
+    def gn_batch_set_step(self, step: int):
+        check(lib().gn_batch_set_step(self.h, step))
+
+    def gn_batch_set_state(self, net: int, hist, w=None, c=None, bg_count=None):
+        hist = np.ascontiguousarray(hist, np.float32)
+        w, c = _c(w, np.float32), _c(c, np.float32)
+        bg = _c(bg_count, np.int32)
+        check(lib().gn_batch_set_state(self.h, net, _ptr(hist), hist.shape[0], _ptr(w), _ptr(c), _ptr(bg)))
 
 
 def exported_symbols() -> list:

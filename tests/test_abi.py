@@ -18,7 +18,7 @@ def L():
 
 def test_every_declared_symbol_is_exported(L):
     names = geonet.exported_symbols()
-    assert len(names) >= 17
+    assert len(names) >= 34
     out = subprocess.run(["nm", "-D", "--defined-only", geonet.LIB_PATH], capture_output=True, text=True).stdout
     exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
     missing = [n for n in names if n not in exported]
@@ -36,7 +36,8 @@ def test_only_the_abi_is_exported(L):
 def test_struct_layouts_match_the_header(L, tmp_path):
     """sizeof and offsetof of every ABI struct, from gcc on the header, equal the binding's."""
     structs = {"gn_fhn_params": geonet.gn_fhn_params, "gn_obs_params": geonet.gn_obs_params,
-               "gn_net_desc": geonet.gn_net_desc, "gn_pulse": geonet.gn_pulse, "gn_net_info": geonet.gn_net_info}
+               "gn_net_desc": geonet.gn_net_desc, "gn_pulse": geonet.gn_pulse, "gn_net_info": geonet.gn_net_info,
+               "gn_batch_info": geonet.gn_batch_info}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "geonet.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
