@@ -268,6 +268,27 @@ GN_API gn_status gn_batch_get_arrivals(gn_batch *batch, int32_t net, int64_t *fi
 GN_API gn_status gn_batch_get_events(gn_batch *batch, int32_t net, int32_t *node, int64_t *step, int64_t cap,
                                      int64_t *n_total);
 
+/* Advance every network n_steps like gn_batch_step, but without allocating any
+ * memory: no cudaMalloc, cudaFree or other allocating routine is called.  This is
+ * for callers that cannot allocate device memory while they step -- a real-time
+ * control loop that must not take an allocator's latency or locks, or a program
+ * whose device memory is handed out from a fixed arena owned by someone else.
+ * gn_batch_step may allocate: on its first call it times candidate CTA sizes on
+ * scratch copies of the state, and it instantiates a new CUDA graph whenever
+ * n_steps changes.  This call launches the kernel directly, with the CTA size an
+ * earlier gn_batch_step chose (or the default one), and takes the launch's work
+ * queue -- its counter and largest-first schedule -- from a fixed device array
+ * inside the library instead of the batch's memory.  The paper has no
+ * counterpart; this is a deployment entry point.
+ *   Limit: batches of at most 65,536 networks (GN_ERANGE beyond).
+ *   The first call on a device looks up that array's device address, so make the
+ *   first call on each device before any stream capture begins.
+ *   The array is shared by every call in the process and keeps the last call's
+ *   contents (the counter is cleared and the schedule rewritten before each
+ *   launch); calls that overlap on the GPU -- on different streams, or for
+ *   different batches at the same time -- race on it and must be serialised. */
+GN_API gn_status gn_batch_step_static(gn_batch *batch, int64_t n_steps);
+
 /* Move the common step counter (clears every network's events and resets the
  * observation cursors), then set one network's state at that step as
  * gn_set_state does. */

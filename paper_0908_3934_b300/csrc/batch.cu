@@ -573,6 +573,34 @@ gn_status gn_batch_step(gn_batch *b, int64_t n_steps)
     });
 }
 
+gn_status gn_batch_step_static(gn_batch *b, int64_t n_steps)
+{
+    return guarded([&] {
+        check_batch(b);
+        if (n_steps < 0 || n_steps > 2147483647LL) fail(GN_EINVAL, "n_steps out of range");
+        if (b->n_nets > gn::kStaticQueueNets)
+            fail(GN_ERANGE, "a batch of %d networks exceeds the %d networks the static work queue holds", b->n_nets,
+                 gn::kStaticQueueNets);
+        if (n_steps == 0) return;
+        DeviceGuard dg(b->device);
+        // the CTA size chosen by an earlier gn_batch_step, else the default one
+        // (choosing it here would time candidates on newly allocated scratch state)
+        int shape = b->shape, grid = b->grid;
+        if (shape < 0) {
+            int per_sm = 0, sms = 0;
+            shape = 0;
+            cuda_check(gn::batch_occupancy(shape, &per_sm), "occupancy");
+            cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device), "device query");
+            grid = std::max(1, std::min(b->n_nets, std::max(1, per_sm) * sms));
+        }
+        cuda_check(gn::launch_batch_static(b->d_args.p, b->order.data(), b->n_nets, b->d_step.p,
+                                           static_cast<int>(n_steps), shape, grid, b->device, b->stream),
+                   "batch launch with the static work queue");
+        cuda_check(gn::launch_advance(b->d_step.p, n_steps, b->stream), "advance launch");
+        b->step += n_steps;
+    });
+}
+
 gn_status gn_batch_synchronize(gn_batch *b)
 {
     return guarded([&] {

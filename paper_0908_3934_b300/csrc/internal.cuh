@@ -95,6 +95,11 @@ int batch_block_cap(int shape);
 cudaError_t launch_batch(const StepArgs *nets, const int *order, int n_nets, int *queue, const int64_t *d_step,
                          int n_steps, int shape, int grid, cudaStream_t s);
 cudaError_t batch_occupancy(int shape, int *ctas_per_sm);
+// the same launch with its work queue in a file-scope device array (no allocation);
+// host_order must stay valid until the call returns (it is copied in stream order)
+constexpr int kStaticQueueNets = 65536;
+cudaError_t launch_batch_static(const StepArgs *nets, const int *host_order, int n_nets, const int64_t *d_step,
+                                int n_steps, int shape, int grid, int device, cudaStream_t s);
 
 cudaError_t launch_delay(int64_t n_edges, int32_t dim, const double *pos, const int32_t *src,
                          const int32_t *dst, const double *speed, double speed_scalar, double dt_ms,

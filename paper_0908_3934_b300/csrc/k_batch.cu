@@ -184,3 +184,55 @@ cudaError_t batch_occupancy(int shape, int *ctas_per_sm)
 }
 
 }  // namespace gn
+
+// ---------------------------------------------------------------------------
+// Allocation-free stepping of a batch (gn_batch_step_static).
+//
+// The work queue of one launch -- the counter CTAs take networks from and the
+// largest-first schedule -- lives in this file-scope device array instead of in
+// memory the batch allocated.  It holds at most kStaticQueueNets networks; all
+// calls share it, and it keeps the last call's contents (the counter is cleared
+// and the schedule rewritten before every launch).  Two calls that overlap on the
+// GPU (on different streams, or on different batches at once) race on it.
+namespace gn {
+namespace {
+
+struct StaticQueue {
+    int counter;
+    int pad[63];  // keep the schedule 256-byte aligned
+    int order[kStaticQueueNets];
+};
+
+static __device__ __align__(256) StaticQueue g_static_queue;
+
+constexpr int kMaxDevices = 64;
+StaticQueue *g_queue_addr[kMaxDevices] = {};
+}  // namespace
+
+cudaError_t launch_batch_static(const StepArgs *nets, const int *host_order, int n_nets, const int64_t *d_step,
+                                int n_steps, int shape, int grid, int device, cudaStream_t s)
+{
+    if (n_nets <= 0 || n_steps <= 0) return cudaSuccess;
+    if (n_nets > kStaticQueueNets || device < 0 || device >= kMaxDevices) return cudaErrorInvalidValue;
+    // device address of the array, looked up once per device with that device current
+    if (!g_queue_addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_queue);
+        if (e != cudaSuccess) return e;
+        g_queue_addr[device] = static_cast<StaticQueue *>(p);
+    }
+    StaticQueue *q = g_queue_addr[device];
+    cudaError_t e = cudaMemsetAsync(&q->counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(q->order, host_order, static_cast<size_t>(n_nets) * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    switch (shape) {
+        case 0: k_batch<128, 8><<<grid, 128, 0, s>>>(nets, q->order, n_nets, &q->counter, d_step, n_steps); break;
+        case 1: k_batch<256, 8><<<grid, 256, 0, s>>>(nets, q->order, n_nets, &q->counter, d_step, n_steps); break;
+        case 2: k_batch<512, 8><<<grid, 512, 0, s>>>(nets, q->order, n_nets, &q->counter, d_step, n_steps); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace gn

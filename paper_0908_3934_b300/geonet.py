@@ -97,6 +97,7 @@ _SIGS = {
     "gn_batch_set_stimulus_all": ([_P, _P, _P], C.c_int),
     "gn_batch_set_background": ([_P, C.c_int32, C.c_double, C.c_float, C.c_double, C.c_uint64], C.c_int),
     "gn_batch_step": ([_P, C.c_int64], C.c_int),
+    "gn_batch_step_static": ([_P, C.c_int64], C.c_int),
     "gn_batch_synchronize": ([_P], C.c_int),
     "gn_batch_observe": ([_P, C.c_int32, _P, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int64)], C.c_int),
     "gn_batch_get_state": ([_P, C.c_int32, _P, _P, _P, _P, C.POINTER(C.c_int64)], C.c_int),
@@ -346,6 +347,9 @@ class Batch:
 
     def gn_batch_step(self, n_steps: int):
         check(lib().gn_batch_step(self.h, n_steps))
+
+    def gn_batch_step_static(self, n_steps: int):
+        check(lib().gn_batch_step_static(self.h, n_steps))
 
     def gn_batch_synchronize(self):
         check(lib().gn_batch_synchronize(self.h))

@@ -1,0 +1,38 @@
+"""gn_batch_step_static: stepping a batch without allocating any memory.
+
+Some callers cannot allocate device memory while they step the simulation (a
+real-time loop that must not take the allocator's latency or locks, a program
+whose device memory comes from a fixed arena owned by someone else).  For them
+the library steps a batch with its per-launch work queue in a fixed device array
+inside the library.  This file is collected last so that a run stopping at the
+first failure has already run every other test."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_0908_3934_b300 import geonet, netgen
+
+from parity import ratio
+
+pytestmark = pytest.mark.gpu
+
+
+def test_static_step_matches_gn_batch_step_on_two_calls():
+    specs = [netgen.batch_member(9000 + i, n_hi=1200) for i in range(10)]
+    a = geonet.Batch(specs)
+    b = geonet.Batch(specs)
+    L = geonet.lib()
+    for call in range(2):
+        geonet.check(L.gn_batch_step_static(a.h, C.c_int64(300)))
+        b.gn_batch_step(300)
+        assert a.gn_batch_get_info()["step"] == b.gn_batch_get_info()["step"] == 300 * (call + 1)
+        for i in range(len(specs)):
+            sa, sb = a.gn_batch_get_state(i), b.gn_batch_get_state(i)
+            for k in ("v", "w", "c"):
+                assert ratio(sa[k], sb[k]) <= 1.0, (call, i, k)
+            assert np.array_equal(sa["bg_count"], sb["bg_count"])
+            ya, fa, _ = a.gn_batch_observe(i)
+            yb, fb, _ = b.gn_batch_observe(i)
+            assert fa == fb and ya.shape == yb.shape and ratio(ya, yb) <= 1.0
+            assert np.array_equal(a.gn_batch_get_arrivals(i), b.gn_batch_get_arrivals(i))
