@@ -60,6 +60,7 @@ class NetSpec:
     pulses: list = dataclasses.field(default_factory=list)   # (node, t_on_ms, t_off_ms, amp)
     background: dict | None = None  # dict(rate_hz, amp, dur_ms, seed)
     ring_depth: int = 0             # 0 = smallest power of two that holds the delays
+    radius: float = 0.0             # radius the edges were drawn within (candidate pairs), 0 = unknown
     name: str = ""
 
     @property
@@ -202,7 +203,7 @@ def batch_member(seed: int, n: int | None = None, n_lo: int = 32, n_hi: int = 40
     onsets = rng.uniform(5.0, 50.0, nodes.shape[0])
     pulses = [(int(j), float(t), float(t) + 2.0, 1.0) for j, t in zip(nodes, onsets)]
     obs = dict(OBS_DEFAULT, seed=seed + 7)
-    return NetSpec(pos=pos, src=src, dst=dst, weight=w, speed=speed, obs=obs, pulses=pulses,
+    return NetSpec(pos=pos, src=src, dst=dst, weight=w, speed=speed, obs=obs, pulses=pulses, radius=r,
                    name=f"batch_s{seed}")
 
 
@@ -251,3 +252,45 @@ def random_small(seed: int, n: int = 12, p_edge: float = 0.3, dim: int = 2, spee
     pulses = [(int(j), float(rng.uniform(0.5, 3.0)), float(rng.uniform(3.5, 6.0)), 1.0) for j in nodes]
     return NetSpec(pos=pos, src=src, dst=dst, weight=w, speed=None, speed_scalar=speed, pulses=pulses,
                    obs=dict(OBS_DEFAULT, seed=seed + 11), name=f"small_s{seed}")
+
+
+# --------------------------------------------------------------------------- estimator inputs
+def candidates(spec: NetSpec):
+    """Candidate directed pairs of a net: every ordered pair closer than the radius
+    its edges were drawn within, with label 1 where the pair is an edge of the net
+    (the ground truth a connectivity estimator is scored against)."""
+    assert spec.radius > 0.0, "the net does not record its candidate radius"
+    src, dst = _pairs_within(spec.pos, spec.radius)
+    src, dst = _sort_by_dst(src, dst)
+    N = np.int64(spec.n_nodes)
+    edge_key = spec.src.astype(np.int64) * N + spec.dst.astype(np.int64)
+    key = src.astype(np.int64) * N + dst.astype(np.int64)
+    label = np.isin(key, edge_key).astype(np.uint8)
+    return src, dst, label
+
+
+def mlp_init(seed: int, in_dim: int = 33, hidden: int = 256):
+    """He-uniform initial weights of the in_dim -> hidden -> hidden -> 1 network
+    (biases zero), float32: W1 [in_dim, hidden], W2 [hidden, hidden], w3 [hidden]."""
+    rng = np.random.default_rng(seed)
+
+    def he(fan_in, shape):
+        lim = np.sqrt(6.0 / fan_in)
+        return rng.uniform(-lim, lim, shape).astype(np.float32)
+    return dict(W1=he(in_dim, (in_dim, hidden)), b1=np.zeros(hidden, np.float32),
+                W2=he(hidden, (hidden, hidden)), b2=np.zeros(hidden, np.float32),
+                w3=he(hidden, (hidden,)), b3=np.zeros(1, np.float32))
+
+
+def mlp_toy_batch(seed: int, B: int, in_dim: int = 33):
+    """Seeded inputs in [-1, 1] and 0/1 labels for MLP checks."""
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(-1.0, 1.0, (B, in_dim)).astype(np.float32)
+    y = (rng.random(B) < 0.5).astype(np.float32)
+    return X, y
+
+
+def shuffles(seed: int, n: int, epochs: int):
+    """The order in which a training run visits n samples, epoch by epoch."""
+    rng = np.random.default_rng(seed)
+    return [rng.permutation(n).astype(np.int64) for _ in range(epochs)]

@@ -1,0 +1,139 @@
+"""Pins of the estimator oracle (oracle/estimator.py) to library routines,
+closed forms and finite differences."""
+import numpy as np
+import pytest
+import torch
+from sklearn.metrics import f1_score, roc_auc_score
+from sklearn.neural_network import MLPClassifier
+
+from oracle import estimator as est
+from paper_0908_3934_b300 import netgen
+
+
+def test_bf16_rounding_matches_torch():
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.normal(0, 10, 20000), rng.normal(0, 1e-3, 2000),
+                        [0.0, -0.0, 1.0, 3.0e38, -1e-40, 65504.0]]).astype(np.float32)
+    want = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(est.bf16(x), want)
+
+
+def test_pearson_matches_numpy_corrcoef():
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        a, b = rng.normal(size=(2, 300))
+        b = b + 0.3 * a
+        assert est.pearson(a, b) == pytest.approx(np.corrcoef(a, b)[0, 1], abs=1e-13)
+    assert est.pearson(np.ones(10), rng.normal(size=10)) == 0.0
+
+
+def test_ncc_features_shift_self_and_noise():
+    """A delayed copy peaks exactly at its delay; independent noise stays near 0
+    (|r| < 4 / sqrt(T)); every lag feature equals numpy's corrcoef on its overlap."""
+    rng = np.random.default_rng(2)
+    T, shift = 500, 7
+    base = rng.normal(size=T + shift)
+    Y = np.stack([base[shift:], base[:-shift], rng.normal(size=T)], axis=1)  # y1(t) = y0(t - shift)
+    pos = np.array([[0.0, 0.0], [0.0, 0.0], [0.0, 0.0]])
+    src = np.array([0, 0])
+    dst = np.array([1, 2])
+    F, score = est.ncc_features(Y, pos, src, dst, radius=1.0)
+    assert np.argmax(F[0, :32]) == shift and F[0, shift] == pytest.approx(1.0, abs=1e-12)
+    assert np.abs(F[1, :32]).max() < 4.0 / np.sqrt(T)
+    for k in (0, 3, 31):
+        assert F[1, k] == pytest.approx(np.corrcoef(Y[: T - k, 0], Y[k:, 2])[0, 1], abs=1e-12)
+    assert score[0] == pytest.approx(1.0)
+
+
+def test_first_lag_and_distance_feature():
+    """l0 = floor(d / v_max / 1 ms) (Sec. 3.2.1: tau = d / s, shortest at the fastest
+    speed 0.5 mm/ms); the last feature is d / r_c."""
+    pos = np.array([[0.0, 0.0], [0.3, 0.4], [0.6, 0.8], [0.1, 0.0]])
+    d = np.array([0.5, 1.0, 0.1])
+    assert est.first_lag(d).tolist() == [1, 2, 0]
+    Y = np.random.default_rng(3).normal(size=(100, 4))
+    F, _ = est.ncc_features(Y, pos, np.array([0, 0, 0]), np.array([1, 2, 3]), radius=2.0)
+    assert F[:, 32].tolist() == pytest.approx([0.25, 0.5, 0.05])
+    assert F[0, 0] == pytest.approx(np.corrcoef(Y[:99, 0], Y[1:, 1])[0, 1], abs=1e-12)
+
+
+def test_auroc_matches_sklearn_and_special_cases():
+    rng = np.random.default_rng(4)
+    s = rng.normal(size=3000)
+    y = (rng.random(3000) < 1 / (1 + np.exp(-2 * s))).astype(int)
+    assert est.auroc(s, y) == pytest.approx(roc_auc_score(y, s), abs=1e-12)
+    s2 = np.round(s, 1)  # many ties: mid-ranks
+    assert est.auroc(s2, y) == pytest.approx(roc_auc_score(y, s2), abs=1e-12)
+    assert est.auroc([1, 2, 3, 4], [0, 0, 1, 1]) == 1.0
+    assert est.auroc([4, 3, 2, 1], [0, 0, 1, 1]) == 0.0
+    assert est.auroc([5, 5, 5, 5], [0, 1, 0, 1]) == 0.5
+
+
+def test_f1_and_best_threshold_match_sklearn():
+    rng = np.random.default_rng(5)
+    s = rng.normal(size=500)
+    y = (s + rng.normal(size=500) > 0).astype(int)
+    for thr in (-0.5, 0.0, 0.7):
+        assert est.f1_at(s, y, thr) == pytest.approx(f1_score(y, s >= thr), abs=1e-12)
+    thr, best = est.best_threshold(s, y)
+    grid = max(f1_score(y, s >= t) for t in s)
+    assert best == pytest.approx(grid, abs=1e-12) and est.f1_at(s, y, thr) == pytest.approx(best)
+
+
+def test_mlp_forward_matches_sklearn():
+    """The exact (unquantised) forward pass equals scikit-learn's MLPClassifier with
+    the same weights (relu hidden layers, logistic output)."""
+    X, y = netgen.mlp_toy_batch(6, 64)
+    prm = netgen.mlp_init(7)
+    prm["b1"] = np.linspace(-0.1, 0.1, 256).astype(np.float32)
+    prm["b2"] = np.linspace(0.05, -0.05, 256).astype(np.float32)
+    prm["b3"] = np.array([0.2], np.float32)
+    clf = MLPClassifier(hidden_layer_sizes=(256, 256), activation="relu", max_iter=1)
+    import warnings
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        clf.fit(X, y.astype(int))
+    clf.coefs_ = [prm["W1"].astype(np.float64), prm["W2"].astype(np.float64),
+                  prm["w3"].astype(np.float64)[:, None]]
+    clf.intercepts_ = [prm["b1"].astype(np.float64), prm["b2"].astype(np.float64),
+                       prm["b3"].astype(np.float64)]
+    p, _ = est.mlp_forward(prm, X, quantise=False)
+    assert np.allclose(p, clf.predict_proba(X.astype(np.float64))[:, 1], rtol=1e-12, atol=1e-14)
+
+
+def test_mlp_backward_matches_finite_differences():
+    X, y = netgen.mlp_toy_batch(8, 16)
+    prm = {k: v.astype(np.float64) for k, v in netgen.mlp_init(9).items()}
+    prm["b1"] += 0.05
+    prm["b2"] -= 0.02
+    p, cache = est.mlp_forward(prm, X, quantise=False)
+    g = est.mlp_backward(prm, cache, p, y, quantise=False)
+    rng = np.random.default_rng(10)
+    h = 1e-6
+    for k in ("W1", "b1", "W2", "b2", "w3", "b3"):
+        flat = prm[k].reshape(-1)
+        for idx in rng.choice(flat.size, min(12, flat.size), replace=False):
+            save = flat[idx]
+            flat[idx] = save + h
+            lp = est.bce(est.mlp_forward(prm, X, quantise=False)[0], y)
+            flat[idx] = save - h
+            lm = est.bce(est.mlp_forward(prm, X, quantise=False)[0], y)
+            flat[idx] = save
+            fd = (lp - lm) / (2 * h)
+            assert g[k].reshape(-1)[idx] == pytest.approx(fd, rel=2e-5, abs=1e-9), (k, idx)
+
+
+def test_adamw_matches_torch():
+    rng = np.random.default_rng(11)
+    w0 = rng.normal(size=(5, 4))
+    grads = [rng.normal(size=(5, 4)) for _ in range(3)]
+    t = torch.tensor(w0, requires_grad=True)
+    opt = torch.optim.AdamW([t], lr=1e-2, betas=(0.9, 0.999), eps=1e-8, weight_decay=0.01)
+    state = {}
+    w = {"W": w0}
+    for g in grads:
+        opt.zero_grad()
+        t.grad = torch.tensor(g)
+        opt.step()
+        w = est.adamw(w, {"W": g}, state, lr=1e-2, weight_decay=0.01)
+    assert np.allclose(w["W"], t.detach().numpy(), rtol=1e-12, atol=1e-14)
