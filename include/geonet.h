@@ -296,6 +296,66 @@ GN_API gn_status gn_batch_set_step(gn_batch *batch, int64_t step);
 GN_API gn_status gn_batch_set_state(gn_batch *batch, int32_t net, const float *hist, int32_t depth, const float *w,
                                     const float *c, const int32_t *bg_count);
 
+/* ---------------------------------------------------------------------------
+ * Connectivity estimator.  Correlating the activity of two cells is the common way
+ * to map functional connections (Sec. 1); the framework's test networks exist to
+ * score such mappings against a known topology (Sec. 3.5, Sec. 4).
+ * ------------------------------------------------------------------------- */
+
+/* Node-major traces of every network of a batch: out[(o_i + j) * n_samples + t] =
+ * observation sample first_sample + t of node j (caller order) of network i, with
+ * o_i the number of nodes of networks 0 .. i-1.  `out` is a device buffer of
+ * (total nodes) x n_samples floats.  GN_ERANGE if a sample was not taken yet or no
+ * longer held (obs_capacity). */
+GN_API gn_status gn_batch_export_traces(gn_batch *batch, int64_t first_sample, int32_t n_samples, float *out);
+
+/* Lagged normalised cross-correlation features of candidate pairs i -> j, all
+ * pointers on the device.  traces [n_nodes][n_samples] (node-major), pos
+ * [n_nodes][dim] (mm), pairs src/dst [n_pairs], radius [n_pairs] (the candidate
+ * radius r_c of the pair's network).  With d = |x_i - x_j| and the first lag
+ * l0 = floor((d / v_max) / sample_ms) (the shortest delay, Sec. 3.2.1), feature k < 32
+ * is the Pearson correlation of y_i(t) and y_j(t + l0 + k) over their overlap, each
+ * segment about its own mean (0 if one is constant); feature 32 is d / r_c.
+ * features [n_pairs][33]; score [n_pairs] = max of features 0..31 (the plain
+ * peak-correlation estimator).  Runs on `cuda_stream` (may be NULL). */
+GN_API gn_status gn_xcorr_features(const float *traces, int64_t n_nodes, int32_t n_samples, const double *pos,
+                                   int32_t dim, int64_t n_pairs, const int32_t *src, const int32_t *dst,
+                                   const double *radius, double v_max, double sample_ms, float *features,
+                                   float *score, void *cuda_stream);
+
+/* Learned estimator: an MLP in_dim -> 256 -> 256 -> 1 (ReLU, sigmoid output)
+ * trained on labelled candidate pairs with binary cross-entropy and AdamW
+ * (beta 0.9 / 0.999, eps 1e-8, decoupled weight decay).  BF16 tensor-core GEMMs
+ * with FP32 accumulation; inputs, weight copies, the first hidden activation and
+ * the backward activations are BF16, masters and reductions FP32, every reduction
+ * in a fixed order.  Parameters are exchanged as one packed FP32 host array
+ * [W1 (in_dim x 256, row-major) | b1 (256) | W2 (256 x 256) | b2 | w3 (256) | b3 (1)];
+ * X [rows][in_dim], y [rows] and p [B] are device buffers; with idx (device int64
+ * [B], may be NULL) row b of the batch is X[idx[b]] / y[idx[b]], so a resident
+ * training set is visited in any order without copies. */
+typedef struct gn_mlp gn_mlp;
+GN_API gn_status gn_mlp_create(int32_t in_dim, int32_t max_batch, const float *params, int32_t device,
+                               void *cuda_stream, gn_mlp **out);
+GN_API gn_status gn_mlp_destroy(gn_mlp *mlp);
+GN_API gn_status gn_mlp_get_params(gn_mlp *mlp, float *params);
+/* Gradients of the mean loss over the batch (packed layout, host) without an update. */
+GN_API gn_status gn_mlp_gradients(gn_mlp *mlp, const float *X, const float *y, const int64_t *idx, int32_t B,
+                                  float *grads, float *loss);
+/* One AdamW step on one batch (B <= max_batch); *loss (may be NULL) receives the mean loss. */
+GN_API gn_status gn_mlp_train_step(gn_mlp *mlp, const float *X, const float *y, const int64_t *idx, int32_t B,
+                                   float lr, float weight_decay, float *loss);
+/* Probabilities p = sigmoid(MLP(X)) for any number of rows (asynchronous). */
+GN_API gn_status gn_mlp_infer(gn_mlp *mlp, const float *X, int64_t B, float *p);
+GN_API gn_status gn_mlp_synchronize(gn_mlp *mlp);
+
+/* Scores of a mapping (host buffers): area under the ROC curve (Mann-Whitney U
+ * with mid-ranks for ties; NaN if one class is empty), F1 of "edge iff score >=
+ * threshold", and the threshold among the scores that maximises F1. */
+GN_API gn_status gn_score_auroc(const float *scores, const uint8_t *labels, int64_t n, double *auroc);
+GN_API gn_status gn_score_f1(const float *scores, const uint8_t *labels, int64_t n, double threshold, double *f1);
+GN_API gn_status gn_score_best_f1(const float *scores, const uint8_t *labels, int64_t n, double *threshold,
+                                  double *f1);
+
 /* Thread-local message of the last failing call ("" if none). */
 GN_API const char *gn_last_error(void);
 

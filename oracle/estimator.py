@@ -128,7 +128,7 @@ def mlp_backward(params: dict, cache: dict, p: np.ndarray, y: np.ndarray, quanti
     g["b2"] = dh2.sum(0)
     dh2q = q(dh2)
     g["W2"] = cache["h1"].T @ dh2q
-    dh1 = (dh2q @ cache["W2"].T) * (cache["z1"] > 0.0)
+    dh1 = (dh2q @ cache["W2"].T) * (cache["h1"] > 0.0)  # the stored activation gates the gradient
     g["b1"] = dh1.sum(0)
     dh1q = q(dh1)
     g["W1"] = cache["X"].T @ dh1q

@@ -601,6 +601,40 @@ gn_status gn_batch_step_static(gn_batch *b, int64_t n_steps)
     });
 }
 
+gn_status gn_batch_export_traces(gn_batch *b, int64_t first_sample, int32_t n_samples, float *out)
+{
+    return guarded([&] {
+        check_batch(b);
+        if (n_samples < 1 || first_sample < 0 || !out) fail(GN_EINVAL, "bad trace window or output");
+        DeviceGuard dg(b->device);
+        int max_nodes = 0;
+        std::vector<gn::ExportNet> nets(b->n_nets);
+        int64_t node_off = 0;
+        for (int i = 0; i < b->n_nets; ++i) {
+            const Member &mm = b->m[i];
+            const int64_t produced = b->step / mm.sample_every;
+            if (first_sample + n_samples > produced) fail(GN_ERANGE, "network %d has only %lld samples", i, (long long)produced);
+            if (produced - first_sample > b->obs_cap)
+                fail(GN_ERANGE, "network %d no longer holds sample %lld (observation capacity %lld)", i,
+                     (long long)first_sample, (long long)b->obs_cap);
+            nets[i] = gn::ExportNet{mm.obs_off, node_off, mm.N, 0};
+            node_off += mm.N;
+            max_nodes = std::max(max_nodes, mm.N);
+        }
+        gn::ExportNet *d_nets = nullptr;
+        cuda_check(cudaMallocAsync(reinterpret_cast<void **>(&d_nets), nets.size() * sizeof(gn::ExportNet), b->stream),
+                   "cudaMallocAsync");
+        cudaError_t e = cudaMemcpyAsync(d_nets, nets.data(), nets.size() * sizeof(gn::ExportNet), cudaMemcpyHostToDevice,
+                                        b->stream);
+        if (e == cudaSuccess)
+            e = gn::launch_export_traces(b->obs.p, d_nets, b->n_nets, max_nodes, first_sample, n_samples, b->obs_cap,
+                                         out, b->stream);
+        cudaFreeAsync(d_nets, b->stream);
+        cuda_check(e, "trace export");
+        sync(b);
+    });
+}
+
 gn_status gn_batch_synchronize(gn_batch *b)
 {
     return guarded([&] {

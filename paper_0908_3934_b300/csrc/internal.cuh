@@ -101,6 +101,35 @@ constexpr int kStaticQueueNets = 65536;
 cudaError_t launch_batch_static(const StepArgs *nets, const int *host_order, int n_nets, const int64_t *d_step,
                                 int n_steps, int shape, int grid, int device, cudaStream_t s);
 
+// estimator (k_est.cu)
+struct ExportNet {
+    int64_t obs_off;   // first float of the network's observation ring in the pool
+    int64_t node_off;  // first row of the network in the node-major output
+    int32_t n_nodes;
+    int32_t pad;
+};
+cudaError_t launch_export_traces(const float *obs_pool, const ExportNet *nets, int n_nets, int max_nodes,
+                                 int64_t first, int T, int64_t cap, float *out, cudaStream_t s);
+cudaError_t launch_ncc(const float *X, int64_t M, int T, float *mean_scratch, const double *pos, int dim, int64_t P,
+                       const int *src, const int *dst, const double *radius, double v_max, double sample_ms,
+                       float *feat, float *score, cudaStream_t s);
+
+// MLP of the learned estimator (k_mlp.cu); hidden width 256, inputs padded to 64
+constexpr int kMlpHidden = 256;
+constexpr int kMlpInPad = 64;
+cudaError_t mlp_prepare();
+cudaError_t mlp_launch_cast(const float *X, const int64_t *idx, int B, int in_dim, int Bp, void *Xb, cudaStream_t s);
+cudaError_t mlp_launch_layer(int epi, const void *A, int Bp, int K, const void *Bt, const float *bias, const void *mask,
+                             void *out, float *col_partial, cudaStream_t s);
+cudaError_t mlp_launch_wgrad(const void *A, int Bp, int K, const void *G, int chunk, float *partial, cudaStream_t s);
+cudaError_t mlp_launch_head(const float *H2, const float *w3, const float *b3, const float *y, const int64_t *idx, int B,
+                            int Bp, int rows_per_cta, float *p, void *dH2, float *partial, cudaStream_t s);
+cudaError_t mlp_launch_sum(const float *part, int n, int64_t len, float *out, cudaStream_t s);
+cudaError_t mlp_launch_adamw(float *w, const float *g, float *m, float *v, int64_t n, float lr, float beta1, float beta2,
+                             float eps, float wd, float bc1, float bc2, cudaStream_t s);
+cudaError_t mlp_launch_refresh(const float *W1, int in_dim, const float *W2, void *W1t, void *W2t, void *W2b,
+                               cudaStream_t s);
+
 cudaError_t launch_delay(int64_t n_edges, int32_t dim, const double *pos, const int32_t *src,
                          const int32_t *dst, const double *speed, double speed_scalar, double dt_ms,
                          int32_t *delay, uint8_t *clamped, cudaStream_t s);

@@ -1,0 +1,136 @@
+// Connectivity-estimator kernels: trace export and lagged normalised
+// cross-correlation features.
+//
+// Correlating the activity of two cells is the common way to map functional
+// connections (Sec. 1); on geometric networks the signal of i reaches j after the
+// delay |x_i - x_j| / s (Sec. 3.2.1, Eq. delaydist), so the features of a
+// candidate pair i -> j are the correlations of y_i(t) with y_j(t + l) for 32
+// lags l starting at the shortest geometric delay d / v_max, plus d / r_c.
+#include "internal.cuh"
+
+namespace gn {
+namespace {
+
+// Node-major traces from the observation rings of a batch: out[(node_off + j) * T + t]
+// = obs[((first + t) mod cap) * N + j], one 32 x 32 tile per CTA (coalesced both ways).
+__global__ void k_export_traces(const float *__restrict__ obs_pool, const ExportNet *__restrict__ nets,
+                                int64_t first, int T, int64_t cap, float *__restrict__ out)
+{
+    __shared__ float tile[32][33];
+    const ExportNet e = nets[blockIdx.z];
+    const int j0 = blockIdx.x * 32, t0 = blockIdx.y * 32;
+    if (j0 >= e.n_nodes || t0 >= T) return;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    for (int r = ty; r < 32; r += 8) {
+        const int t = t0 + r, j = j0 + tx;
+        if (t < T && j < e.n_nodes) tile[r][tx] = obs_pool[e.obs_off + ((first + t) % cap) * e.n_nodes + j];
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int j = j0 + r, t = t0 + tx;
+        if (t < T && j < e.n_nodes) out[(e.node_off + j) * static_cast<int64_t>(T) + t] = tile[tx][r];
+    }
+}
+
+// Mean of each node's trace (the centring constant of the correlation sums).
+__global__ void k_trace_mean(const float *__restrict__ X, int64_t M, int T, float *__restrict__ mean)
+{
+    const int64_t node = blockIdx.x * static_cast<int64_t>(blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (node >= M) return;
+    float s = 0.0f;
+    for (int t = lane; t < T; t += 32) s += X[node * T + t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) mean[node] = s / static_cast<float>(T);
+}
+
+// One warp per candidate pair, lane k = lag l0 + k.  Per lag, the five sums of the
+// overlap t < T - l of a = y_i(t) - m_i and b = y_j(t + l) - m_j give the Pearson
+// correlation of the two segments about their own means:
+//   r = (S_ab - S_a S_b / n) / sqrt((S_aa - S_a^2 / n)(S_bb - S_b^2 / n)),
+// 0 when either segment is constant.  The distance and the first lag are FP64 in
+// the order of their definition (d = sqrt(sum of squared coordinate differences),
+// l0 = floor((d / v_max) / sample)), so the integer lag is the same as the oracle's.
+__global__ void k_ncc(const float *__restrict__ X, int T, const float *__restrict__ mean, const double *__restrict__ pos,
+                      int dim, int64_t P, const int *__restrict__ src, const int *__restrict__ dst,
+                      const double *__restrict__ radius, double v_max, double sample_ms, float *__restrict__ feat,
+                      float *__restrict__ score)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x / 32);
+    for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x / 32) + threadIdx.x / 32; p < P; p += warps) {
+        const int64_t i = src[p], j = dst[p];
+        double s2 = 0.0;
+        for (int k = 0; k < dim; ++k) {
+            const double diff = __dsub_rn(pos[i * dim + k], pos[j * dim + k]);
+            s2 = __dadd_rn(s2, __dmul_rn(diff, diff));
+        }
+        const double d = __dsqrt_rn(s2);
+        const int l0 = static_cast<int>(floor(__ddiv_rn(__ddiv_rn(d, v_max), sample_ms)));
+        const int lag = l0 + lane;
+        const int n = T - lag;
+        const float mi = mean[i], mj = mean[j];
+        const float *xi = X + i * T;
+        const float *xj = X + j * T + lag;
+        float sa = 0.0f, sb = 0.0f, saa = 0.0f, sbb = 0.0f, sab = 0.0f;
+        const int tmax = T - l0;  // the longest overlap (lane 0)
+        for (int t = 0; t < tmax; ++t) {
+            const float a = __ldg(xi + t) - mi;
+            if (t < n) {
+                const float b = __ldg(xj + t) - mj;
+                sa += a;
+                sb += b;
+                saa = fmaf(a, a, saa);
+                sbb = fmaf(b, b, sbb);
+                sab = fmaf(a, b, sab);
+            }
+        }
+        float r = 0.0f;
+        if (n >= 2) {
+            const float inv_n = 1.0f / static_cast<float>(n);
+            const float cov = sab - sa * sb * inv_n;
+            const float va = saa - sa * sa * inv_n;
+            const float vb = sbb - sb * sb * inv_n;
+            if (va > 0.0f && vb > 0.0f) r = cov * rsqrtf(va * vb);
+        }
+        feat[p * 33 + lane] = r;
+        float m = r;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) {
+            feat[p * 33 + 32] = static_cast<float>(__ddiv_rn(d, radius[p]));
+            score[p] = m;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_export_traces(const float *obs_pool, const ExportNet *nets, int n_nets, int max_nodes,
+                                 int64_t first, int T, int64_t cap, float *out, cudaStream_t s)
+{
+    if (n_nets <= 0 || T <= 0) return cudaSuccess;
+    dim3 grid((max_nodes + 31) / 32, (T + 31) / 32, n_nets);
+    k_export_traces<<<grid, dim3(32, 8), 0, s>>>(obs_pool, nets, first, T, cap, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ncc(const float *X, int64_t M, int T, float *mean_scratch, const double *pos, int dim, int64_t P,
+                       const int *src, const int *dst, const double *radius, double v_max, double sample_ms,
+                       float *feat, float *score, cudaStream_t s)
+{
+    if (M > 0) {
+        k_trace_mean<<<static_cast<unsigned>((M + 7) / 8), 256, 0, s>>>(X, M, T, mean_scratch);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (P <= 0) return cudaSuccess;
+    int64_t blocks = (P + 7) / 8;
+    if (blocks > 148 * 64) blocks = 148 * 64;
+    k_ncc<<<static_cast<unsigned>(blocks), 256, 0, s>>>(X, T, mean_scratch, pos, dim, P, src, dst, radius, v_max,
+                                                         sample_ms, feat, score);
+    return cudaGetLastError();
+}
+
+}  // namespace gn

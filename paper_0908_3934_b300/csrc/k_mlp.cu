@@ -1,0 +1,469 @@
+// Kernels of the learned connectivity estimator: an MLP in -> 256 -> 256 -> 1
+// (ReLU hidden layers, sigmoid output, binary cross-entropy), BF16 tensor-core
+// GEMMs with FP32 accumulation, FP32 master weights and AdamW.
+//
+// Precision (mirrored by the FP64 oracle): inputs, weight copies, the first hidden
+// activation and the backward activations are BF16; every accumulation is FP32;
+// the second hidden activation, the output layer and all reductions are FP32.
+// Every reduction is done in a fixed order (per-CTA partials, then a reduction
+// kernel), so results do not depend on scheduling.
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+#include "ptx.cuh"
+
+namespace gn {
+namespace {
+
+constexpr int kH = 256;    // hidden width
+constexpr int kKP = 64;    // padded input width
+constexpr int kPad = 8;    // smem row padding (bf16) against ldmatrix bank conflicts
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void *p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void *p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// ---------------------------------------------------------------------------
+// Row b of the batch is X[idx[b]] (or X[b] without idx), FP32 -> Xb [Bp][64]
+// BF16, zero padded (columns >= in, rows >= B).
+__global__ void k_cast_x(const float *__restrict__ X, const int64_t *__restrict__ idx, int B, int in_dim, int Bp,
+                         __nv_bfloat16 *__restrict__ Xb)
+{
+    const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (i >= static_cast<int64_t>(Bp) * kKP) return;
+    const int r = static_cast<int>(i / kKP), c = static_cast<int>(i % kKP);
+    float v = 0.0f;
+    if (r < B && c < in_dim) {
+        const int64_t row = idx ? idx[r] : r;
+        v = X[row * in_dim + c];
+    }
+    Xb[i] = __float2bfloat16_rn(v);
+}
+
+// ---------------------------------------------------------------------------
+// C[m][n] = sum_k A[m][k] Bt[n][k] for a CTA tile of 64 rows x 256 columns,
+// K a multiple of 64 (A row-major [M][K], Bt row-major [256][K]); 8 warps as
+// 2 (rows) x 4 (columns), 32 x 64 per warp; K in chunks of 64, double buffered.
+enum Epi { kReluBf16 = 0, kReluF32 = 1, kMaskBf16 = 2 };
+
+template <int EPI>
+__global__ void __launch_bounds__(256) k_layer(const __nv_bfloat16 *__restrict__ A, int K,
+                                               const __nv_bfloat16 *__restrict__ Bt, const float *__restrict__ bias,
+                                               const __nv_bfloat16 *__restrict__ mask, void *__restrict__ out,
+                                               float *__restrict__ col_partial)
+{
+    constexpr int BM = 64, BK = 64, LD = BK + kPad;
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    __nv_bfloat16 *sA = reinterpret_cast<__nv_bfloat16 *>(smem_raw);  // [2][BM][LD]
+    __nv_bfloat16 *sB = sA + 2 * BM * LD;                               // [2][256][LD]
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int wm = warp >> 2, wn = warp & 3;
+    const int64_t m0 = static_cast<int64_t>(blockIdx.x) * BM;
+
+    auto load = [&](int stage, int k0) {
+        __nv_bfloat16 *a = sA + stage * BM * LD;
+        __nv_bfloat16 *b = sB + stage * kH * LD;
+        for (int c = t; c < BM * BK / 8; c += 256) {
+            const int r = c / (BK / 8), k = (c % (BK / 8)) * 8;
+            cp_async16(a + r * LD + k, A + (m0 + r) * K + k0 + k);
+        }
+        for (int c = t; c < kH * BK / 8; c += 256) {
+            const int r = c / (BK / 8), k = (c % (BK / 8)) * 8;
+            cp_async16(b + r * LD + k, Bt + static_cast<int64_t>(r) * K + k0 + k);
+        }
+        cp_async_commit();
+    };
+
+    float acc[2][8][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
+
+    const int nk = K / BK;
+    load(0, 0);
+    for (int kc = 0; kc < nk; ++kc) {
+        if (kc + 1 < nk) {
+            load((kc + 1) & 1, (kc + 1) * BK);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const __nv_bfloat16 *a = sA + (kc & 1) * BM * LD;
+        const __nv_bfloat16 *b = sB + (kc & 1) * kH * LD;
+#pragma unroll
+        for (int ks = 0; ks < BK / 16; ++ks) {
+            uint32_t af[2][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+                ldsm_x4(af[mt], a + (wm * 32 + mt * 16 + (lane & 15)) * LD + ks * 16 + (lane >> 4) * 8);
+#pragma unroll
+            for (int np = 0; np < 4; ++np) {
+                uint32_t bf[4];
+                ldsm_x4(bf, b + (wn * 64 + np * 16 + (lane & 7) + ((lane >> 4) << 3)) * LD + ks * 16 +
+                                ((lane >> 3) & 1) * 8);
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    mma16816(acc[mt][2 * np], af[mt], bf[0], bf[1]);
+                    mma16816(acc[mt][2 * np + 1], af[mt], bf[2], bf[3]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    // epilogue: thread holds rows wm*32 + mt*16 + g (+8), columns wn*64 + nt*8 + 2c (+1)
+    const int g = lane >> 2, c = lane & 3;
+    float colsum[8][2];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) colsum[nt][0] = colsum[nt][1] = 0.0f;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int64_t row = m0 + wm * 32 + mt * 16 + g + half * 8;
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                const int col = wn * 64 + nt * 8 + 2 * c;
+                float v0 = acc[mt][nt][2 * half], v1 = acc[mt][nt][2 * half + 1];
+                if constexpr (EPI == kMaskBf16) {
+                    const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162 *>(mask + row * kH + col);
+                    v0 = __bfloat162float(mk.x) > 0.0f ? v0 : 0.0f;
+                    v1 = __bfloat162float(mk.y) > 0.0f ? v1 : 0.0f;
+                    colsum[nt][0] += v0;
+                    colsum[nt][1] += v1;
+                    *reinterpret_cast<__nv_bfloat162 *>(static_cast<__nv_bfloat16 *>(out) + row * kH + col) =
+                        __floats2bfloat162_rn(v0, v1);
+                } else {
+                    v0 = fmaxf(v0 + bias[col], 0.0f);
+                    v1 = fmaxf(v1 + bias[col + 1], 0.0f);
+                    if constexpr (EPI == kReluBf16) {
+                        *reinterpret_cast<__nv_bfloat162 *>(static_cast<__nv_bfloat16 *>(out) + row * kH + col) =
+                            __floats2bfloat162_rn(v0, v1);
+                    } else {
+                        *reinterpret_cast<float2 *>(static_cast<float *>(out) + row * kH + col) = make_float2(v0, v1);
+                    }
+                }
+            }
+        }
+    if constexpr (EPI == kMaskBf16) {
+        // column sums of this CTA's 64 rows, in a fixed order: shuffle over the 8 row
+        // groups of a warp, then the two row-warps through shared memory
+        __syncthreads();
+        float *s_part = reinterpret_cast<float *>(smem_raw);  // [2][256]
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float v = colsum[nt][h];
+                v += __shfl_xor_sync(0xffffffffu, v, 4);
+                v += __shfl_xor_sync(0xffffffffu, v, 8);
+                v += __shfl_xor_sync(0xffffffffu, v, 16);
+                if (g == 0) s_part[wm * kH + wn * 64 + nt * 8 + 2 * c + h] = v;
+            }
+        __syncthreads();
+        col_partial[static_cast<int64_t>(blockIdx.x) * kH + t] = s_part[t] + s_part[kH + t];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradient partials: Cp[k][n] = sum_{m in chunk} A[m][k] G[m][n] for a CTA
+// tile of 64 k x 256 n over `chunk` rows of the batch (A [M][K], G [M][256] row-major
+// BF16); operands are loaded transposed from shared memory (ldmatrix .trans).
+__global__ void __launch_bounds__(256) k_wgrad(const __nv_bfloat16 *__restrict__ A, int K,
+                                               const __nv_bfloat16 *__restrict__ G, int chunk,
+                                               float *__restrict__ partial)
+{
+    constexpr int BM = 32, LDA = 64 + kPad, LDG = kH + kPad;
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    __nv_bfloat16 *sA = reinterpret_cast<__nv_bfloat16 *>(smem_raw);  // [2][BM][LDA]
+    __nv_bfloat16 *sG = sA + 2 * BM * LDA;                              // [2][BM][LDG]
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int wk = warp >> 2, wn = warp & 3;
+    const int k0 = blockIdx.x * 64;
+    const int64_t mbeg = static_cast<int64_t>(blockIdx.y) * chunk;
+
+    auto load = [&](int stage, int64_t m) {
+        __nv_bfloat16 *a = sA + stage * BM * LDA;
+        __nv_bfloat16 *gg = sG + stage * BM * LDG;
+        for (int c = t; c < BM * 64 / 8; c += 256) {
+            const int r = c / 8, k = (c % 8) * 8;
+            cp_async16(a + r * LDA + k, A + (m + r) * K + k0 + k);
+        }
+        for (int c = t; c < BM * kH / 8; c += 256) {
+            const int r = c / (kH / 8), n = (c % (kH / 8)) * 8;
+            cp_async16(gg + r * LDG + n, G + (m + r) * kH + n);
+        }
+        cp_async_commit();
+    };
+
+    float acc[2][8][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
+
+    const int steps = chunk / BM;
+    load(0, mbeg);
+    for (int s = 0; s < steps; ++s) {
+        if (s + 1 < steps) {
+            load((s + 1) & 1, mbeg + static_cast<int64_t>(s + 1) * BM);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const __nv_bfloat16 *a = sA + (s & 1) * BM * LDA;
+        const __nv_bfloat16 *gg = sG + (s & 1) * BM * LDG;
+#pragma unroll
+        for (int ms = 0; ms < BM / 16; ++ms) {
+            uint32_t af[2][4];
+#pragma unroll
+            for (int kt = 0; kt < 2; ++kt)
+                ldsm_x4_t(af[kt], a + (ms * 16 + (lane & 7) + ((lane >> 4) << 3)) * LDA + wk * 32 + kt * 16 +
+                                      ((lane >> 3) & 1) * 8);
+#pragma unroll
+            for (int np = 0; np < 4; ++np) {
+                uint32_t bf[4];
+                ldsm_x4_t(bf, gg + (ms * 16 + (lane & 7) + ((lane >> 3) & 1) * 8) * LDG + wn * 64 + np * 16 +
+                                  (lane >> 4) * 8);
+#pragma unroll
+                for (int kt = 0; kt < 2; ++kt) {
+                    mma16816(acc[kt][2 * np], af[kt], bf[0], bf[1]);
+                    mma16816(acc[kt][2 * np + 1], af[kt], bf[2], bf[3]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    const int g = lane >> 2, c = lane & 3;
+    float *out = partial + static_cast<int64_t>(blockIdx.y) * K * kH;
+#pragma unroll
+    for (int kt = 0; kt < 2; ++kt)
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int k = k0 + wk * 32 + kt * 16 + g + half * 8;
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                const int n = wn * 64 + nt * 8 + 2 * c;
+                *reinterpret_cast<float2 *>(out + static_cast<int64_t>(k) * kH + n) =
+                    make_float2(acc[kt][nt][2 * half], acc[kt][nt][2 * half + 1]);
+            }
+        }
+}
+
+// ---------------------------------------------------------------------------
+// Output layer and loss: z = h2 . w3 + b3, p = sigmoid(z).  With labels, also the
+// first backward step: dz = (p - y) / B, dh2 = dz w3 [h2 > 0] (BF16 for the
+// GEMMs), and per-CTA partial sums (fixed order) of dw3 = sum dz h2,
+// db2 = sum dh2, db3 = sum dz and the BCE loss.  One warp per row, 8 warps per CTA,
+// `rows_per_cta` rows per CTA.
+__global__ void __launch_bounds__(256) k_head(const float *__restrict__ H2, const float *__restrict__ w3,
+                                              const float *__restrict__ b3p, const float *__restrict__ y,
+                                              const int64_t *__restrict__ idx, int B, int rows_per_cta,
+                                              float *__restrict__ p_out, __nv_bfloat16 *__restrict__ dH2,
+                                              float *__restrict__ partial)
+{
+    __shared__ float s_w3[kH];
+    __shared__ float s_acc[8][2 * kH + 2];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    s_w3[t] = w3[t];
+    for (int i = t; i < 8 * (2 * kH + 2); i += 256) (&s_acc[0][0])[i] = 0.0f;
+    __syncthreads();
+    const int64_t r0 = static_cast<int64_t>(blockIdx.x) * rows_per_cta;
+    const float b3 = *b3p;
+    const bool train = y != nullptr;
+    const float inv_b = 1.0f / static_cast<float>(B);
+    for (int rr = warp; rr < rows_per_cta; rr += 8) {
+        const int64_t r = r0 + rr;
+        float h[8];
+        float z = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            h[q] = H2[r * kH + q * 32 + lane];
+            z = fmaf(h[q], s_w3[q * 32 + lane], z);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+        z += b3;
+        const float p = 1.0f / (1.0f + expf(-z));
+        if (lane == 0 && r < B) p_out[r] = p;
+        if (!train) continue;
+        const bool valid = r < B;
+        const float yy = valid ? y[idx ? idx[r] : r] : 0.0f;
+        const float dz = valid ? (p - yy) * inv_b : 0.0f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int k = q * 32 + lane;
+            const float d = h[q] > 0.0f ? dz * s_w3[k] : 0.0f;
+            dH2[r * kH + k] = __float2bfloat16_rn(d);
+            s_acc[warp][k] += dz * h[q];      // dw3
+            s_acc[warp][kH + k] += d;         // db2
+        }
+        if (lane == 0 && valid) {
+            s_acc[warp][2 * kH] += dz;
+            const float eps = 1e-12f;
+            s_acc[warp][2 * kH + 1] += -(yy * logf(p + eps) + (1.0f - yy) * logf(1.0f - p + eps));
+        }
+    }
+    if (!train) return;
+    __syncthreads();
+    for (int i = t; i < 2 * kH + 2; i += 256) {
+        float s = 0.0f;
+        for (int w = 0; w < 8; ++w) s += s_acc[w][i];
+        partial[static_cast<int64_t>(blockIdx.x) * (2 * kH + 2) + i] = s;
+    }
+}
+
+// Sum n partial vectors of length len in order: out[i] = sum_j part[j][i].
+__global__ void k_sum_partials(const float *__restrict__ part, int n, int64_t len, float *__restrict__ out)
+{
+    const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (i >= len) return;
+    float s = 0.0f;
+    for (int j = 0; j < n; ++j) s += part[static_cast<int64_t>(j) * len + i];
+    out[i] = s;
+}
+
+// AdamW on FP32 masters (decoupled weight decay), then the BF16 copies:
+// W1t[n][k] (k < 64), W2t[n][k] and W2b[k][n] = W2[k][n].
+__global__ void k_adamw(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m, float *__restrict__ v,
+                        int64_t n, float lr, float beta1, float beta2, float eps, float wd, float bc1, float bc2)
+{
+    const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = beta1 * m[i] + (1.0f - beta1) * gi;
+    const float vi = beta2 * v[i] + (1.0f - beta2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float mhat = mi / bc1, vhat = vi / bc2;
+    w[i] = w[i] * (1.0f - lr * wd) - lr * mhat / (sqrtf(vhat) + eps);
+}
+
+__global__ void k_refresh_bf16(const float *__restrict__ W1, int in_dim, const float *__restrict__ W2,
+                               __nv_bfloat16 *__restrict__ W1t, __nv_bfloat16 *__restrict__ W2t,
+                               __nv_bfloat16 *__restrict__ W2b)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kH * kKP) {
+        const int n = i / kKP, k = i % kKP;
+        W1t[i] = __float2bfloat16_rn(k < in_dim ? W1[k * kH + n] : 0.0f);
+    }
+    if (i < kH * kH) {
+        const int n = i / kH, k = i % kH;
+        W2t[i] = __float2bfloat16_rn(W2[k * kH + n]);
+        W2b[i] = __float2bfloat16_rn(W2[i]);
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+cudaError_t mlp_launch_cast(const float *X, const int64_t *idx, int B, int in_dim, int Bp, void *Xb, cudaStream_t s)
+{
+    const int64_t n = static_cast<int64_t>(Bp) * kKP;
+    k_cast_x<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(X, idx, B, in_dim, Bp,
+                                                                   static_cast<__nv_bfloat16 *>(Xb));
+    return cudaGetLastError();
+}
+
+static int layer_smem() { return (2 * 64 * (64 + kPad) + 2 * kH * (64 + kPad)) * 2; }
+static int wgrad_smem() { return (2 * 32 * (64 + kPad) + 2 * 32 * (kH + kPad)) * 2; }
+
+cudaError_t mlp_prepare()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_layer<kReluBf16>, cudaFuncAttributeMaxDynamicSharedMemorySize, layer_smem());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_layer<kReluF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, layer_smem());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_layer<kMaskBf16>, cudaFuncAttributeMaxDynamicSharedMemorySize, layer_smem());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, wgrad_smem());
+    return e;
+}
+
+cudaError_t mlp_launch_layer(int epi, const void *A, int Bp, int K, const void *Bt, const float *bias, const void *mask,
+                             void *out, float *col_partial, cudaStream_t s)
+{
+    const dim3 grid(Bp / 64);
+    const auto *a = static_cast<const __nv_bfloat16 *>(A);
+    const auto *b = static_cast<const __nv_bfloat16 *>(Bt);
+    const auto *mk = static_cast<const __nv_bfloat16 *>(mask);
+    switch (epi) {
+        case kReluBf16: k_layer<kReluBf16><<<grid, 256, layer_smem(), s>>>(a, K, b, bias, mk, out, col_partial); break;
+        case kReluF32: k_layer<kReluF32><<<grid, 256, layer_smem(), s>>>(a, K, b, bias, mk, out, col_partial); break;
+        case kMaskBf16: k_layer<kMaskBf16><<<grid, 256, layer_smem(), s>>>(a, K, b, bias, mk, out, col_partial); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_launch_wgrad(const void *A, int Bp, int K, const void *G, int chunk, float *partial, cudaStream_t s)
+{
+    const dim3 grid(K / 64, Bp / chunk);
+    k_wgrad<<<grid, 256, wgrad_smem(), s>>>(static_cast<const __nv_bfloat16 *>(A), K,
+                                            static_cast<const __nv_bfloat16 *>(G), chunk, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_launch_head(const float *H2, const float *w3, const float *b3, const float *y, const int64_t *idx, int B,
+                            int Bp, int rows_per_cta, float *p, void *dH2, float *partial, cudaStream_t s)
+{
+    k_head<<<Bp / rows_per_cta, 256, 0, s>>>(H2, w3, b3, y, idx, B, rows_per_cta, p,
+                                              static_cast<__nv_bfloat16 *>(dH2), partial);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_launch_sum(const float *part, int n, int64_t len, float *out, cudaStream_t s)
+{
+    k_sum_partials<<<static_cast<unsigned>((len + 255) / 256), 256, 0, s>>>(part, n, len, out);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_launch_adamw(float *w, const float *g, float *m, float *v, int64_t n, float lr, float beta1, float beta2,
+                             float eps, float wd, float bc1, float bc2, cudaStream_t s)
+{
+    k_adamw<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(w, g, m, v, n, lr, beta1, beta2, eps, wd, bc1, bc2);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_launch_refresh(const float *W1, int in_dim, const float *W2, void *W1t, void *W2t, void *W2b,
+                               cudaStream_t s)
+{
+    k_refresh_bf16<<<(kH * kH + 255) / 256, 256, 0, s>>>(W1, in_dim, W2, static_cast<__nv_bfloat16 *>(W1t),
+                                                          static_cast<__nv_bfloat16 *>(W2t),
+                                                          static_cast<__nv_bfloat16 *>(W2b));
+    return cudaGetLastError();
+}
+
+}  // namespace gn

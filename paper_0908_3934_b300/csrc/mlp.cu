@@ -1,0 +1,257 @@
+// Host runtime of the learned estimator (gn_mlp_* in include/geonet.h): an MLP
+// in -> 256 -> 256 -> 1 trained with the project's own forward, backward and
+// AdamW kernels (k_mlp.cu) on device-resident batches.
+//
+// Parameters, gradients and Adam moments are packed FP32 buffers in one layout,
+// [W1 (in x 256) | b1 | W2 (256 x 256) | b2 | w3 | b3], so AdamW is one
+// elementwise launch; BF16 copies of W1 and W2 in the layouts the GEMMs read are
+// refreshed after every update.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "runtime.h"
+
+using gnrt::cuda_check;
+using gnrt::DevArray;
+using gnrt::DeviceGuard;
+using gnrt::fail;
+using gnrt::guarded;
+
+namespace {
+constexpr int H = gn::kMlpHidden;
+constexpr int KP = gn::kMlpInPad;
+constexpr int kChunk = 128;  // batch rows per weight-gradient partial
+constexpr int kHeadRows = 64;
+}  // namespace
+
+struct gn_mlp {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int in_dim = 0;
+    int max_bp = 0;  // workspace rows (multiple of 128)
+    int64_t n_params = 0;
+    int64_t off_W1 = 0, off_b1 = 0, off_W2 = 0, off_b2 = 0, off_w3 = 0, off_b3 = 0;
+    int64_t adam_t = 0;
+    size_t bytes = 0;
+    DevArray<float> params, grads, m, v;
+    DevArray<uint16_t> W1t, W2t, W2b;                 // BF16 copies
+    DevArray<uint16_t> Xb, H1, dH2, dH1;              // BF16 activations [max_bp][.]
+    DevArray<float> H2, p, part_w2, part_w1, part_head, part_b1, tmp_w1, tmp_head;
+
+    ~gn_mlp()
+    {
+        for (auto *a : {&params, &grads, &m, &v, &H2, &p, &part_w2, &part_w1, &part_head, &part_b1, &tmp_w1, &tmp_head})
+            a->release();
+        for (auto *a : {&W1t, &W2t, &W2b, &Xb, &H1, &dH2, &dH1}) a->release();
+        if (own_stream && stream) cudaStreamDestroy(stream);
+    }
+};
+
+namespace {
+
+void check_mlp(const gn_mlp *m)
+{
+    if (!m) fail(GN_EINVAL, "MLP handle is NULL");
+}
+
+void refresh(gn_mlp *m)
+{
+    cuda_check(gn::mlp_launch_refresh(m->params.p + m->off_W1, m->in_dim, m->params.p + m->off_W2, m->W1t.p, m->W2t.p,
+                                      m->W2b.p, m->stream),
+               "refresh");
+}
+
+// Forward pass of B rows (Bp padded); with y, also the backward pass into m->grads
+// and the mean loss into *loss.
+void run(gn_mlp *m, const float *X, const float *y, const int64_t *idx, int B, float *p_out, float *loss)
+{
+    const int Bp = (B + kChunk - 1) / kChunk * kChunk;
+    cudaStream_t s = m->stream;
+    const float *P = m->params.p;
+    cuda_check(gn::mlp_launch_cast(X, idx, B, m->in_dim, Bp, m->Xb.p, s), "cast");
+    cuda_check(gn::mlp_launch_layer(0, m->Xb.p, Bp, KP, m->W1t.p, P + m->off_b1, nullptr, m->H1.p, nullptr, s),
+               "layer 1");
+    cuda_check(gn::mlp_launch_layer(1, m->H1.p, Bp, H, m->W2t.p, P + m->off_b2, nullptr, m->H2.p, nullptr, s),
+               "layer 2");
+    cuda_check(gn::mlp_launch_head(m->H2.p, P + m->off_w3, P + m->off_b3, y, idx, B, Bp, kHeadRows, p_out, m->dH2.p,
+                                   m->part_head.p, s),
+               "head");
+    if (!y) return;
+    float *G = m->grads.p;
+    // dH1 = (dH2 W2^T) [h1 > 0] and its column sums (db1)
+    cuda_check(gn::mlp_launch_layer(2, m->dH2.p, Bp, H, m->W2b.p, nullptr, m->H1.p, m->dH1.p, m->part_b1.p, s),
+               "layer 2 backward");
+    cuda_check(gn::mlp_launch_wgrad(m->H1.p, Bp, H, m->dH2.p, kChunk, m->part_w2.p, s), "dW2");
+    cuda_check(gn::mlp_launch_wgrad(m->Xb.p, Bp, KP, m->dH1.p, kChunk, m->part_w1.p, s), "dW1");
+    const int nchunk = Bp / kChunk, nhead = Bp / kHeadRows;
+    cuda_check(gn::mlp_launch_sum(m->part_w2.p, nchunk, static_cast<int64_t>(H) * H, G + m->off_W2, s), "sum");
+    cuda_check(gn::mlp_launch_sum(m->part_w1.p, nchunk, static_cast<int64_t>(KP) * H, m->tmp_w1.p, s), "sum");
+    cuda_check(gn::mlp_launch_sum(m->part_b1.p, nhead, H, G + m->off_b1, s), "sum");
+    cuda_check(gn::mlp_launch_sum(m->part_head.p, nhead, 2 * H + 2, m->tmp_head.p, s), "sum");
+    cuda_check(cudaMemcpyAsync(G + m->off_W1, m->tmp_w1.p, sizeof(float) * m->in_dim * H, cudaMemcpyDeviceToDevice, s),
+               "D2D");
+    cuda_check(cudaMemcpyAsync(G + m->off_w3, m->tmp_head.p, sizeof(float) * H, cudaMemcpyDeviceToDevice, s), "D2D");
+    cuda_check(cudaMemcpyAsync(G + m->off_b2, m->tmp_head.p + H, sizeof(float) * H, cudaMemcpyDeviceToDevice, s), "D2D");
+    cuda_check(cudaMemcpyAsync(G + m->off_b3, m->tmp_head.p + 2 * H, sizeof(float), cudaMemcpyDeviceToDevice, s), "D2D");
+    if (loss) {
+        float sum = 0.0f;
+        cuda_check(cudaMemcpyAsync(&sum, m->tmp_head.p + 2 * H + 1, sizeof(float), cudaMemcpyDeviceToHost, s), "D2H");
+        cuda_check(cudaStreamSynchronize(s), "MLP step");
+        *loss = sum / static_cast<float>(B);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+gn_status gn_mlp_create(int32_t in_dim, int32_t max_batch, const float *params, int32_t device, void *cuda_stream,
+                        gn_mlp **out)
+{
+    if (!out) {
+        gnrt::set_error("out is NULL");
+        return GN_EINVAL;
+    }
+    *out = nullptr;
+    gn_mlp *m = nullptr;
+    gn_status st = guarded([&] {
+        if (in_dim < 1 || in_dim > KP) fail(GN_EINVAL, "in_dim must be in [1, %d]", KP);
+        if (max_batch < 1 || max_batch > (1 << 24)) fail(GN_EINVAL, "max_batch out of range");
+        if (!params) fail(GN_EINVAL, "params is NULL");
+        m = new gn_mlp();
+        m->device = device;
+        DeviceGuard dg(device);
+        if (cuda_stream) {
+            m->stream = static_cast<cudaStream_t>(cuda_stream);
+        } else {
+            cuda_check(cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking), "cudaStreamCreate");
+            m->own_stream = true;
+        }
+        m->in_dim = in_dim;
+        m->max_bp = (max_batch + kChunk - 1) / kChunk * kChunk;
+        m->off_W1 = 0;
+        m->off_b1 = m->off_W1 + static_cast<int64_t>(in_dim) * H;
+        m->off_W2 = m->off_b1 + H;
+        m->off_b2 = m->off_W2 + static_cast<int64_t>(H) * H;
+        m->off_w3 = m->off_b2 + H;
+        m->off_b3 = m->off_w3 + H;
+        m->n_params = m->off_b3 + 1;
+        for (int64_t i = 0; i < m->n_params; ++i)
+            if (!std::isfinite(params[i])) fail(GN_EINVAL, "parameter %lld is not finite", (long long)i);
+        cuda_check(gn::mlp_prepare(), "MLP kernel setup");
+        const size_t bp = m->max_bp;
+        m->params.alloc(m->n_params, &m->bytes);
+        m->grads.alloc(m->n_params, &m->bytes);
+        m->m.alloc(m->n_params, &m->bytes);
+        m->v.alloc(m->n_params, &m->bytes);
+        m->W1t.alloc(static_cast<size_t>(H) * KP, &m->bytes);
+        m->W2t.alloc(static_cast<size_t>(H) * H, &m->bytes);
+        m->W2b.alloc(static_cast<size_t>(H) * H, &m->bytes);
+        m->Xb.alloc(bp * KP, &m->bytes);
+        m->H1.alloc(bp * H, &m->bytes);
+        m->dH2.alloc(bp * H, &m->bytes);
+        m->dH1.alloc(bp * H, &m->bytes);
+        m->H2.alloc(bp * H, &m->bytes);
+        m->p.alloc(bp, &m->bytes);
+        m->part_w2.alloc(bp / kChunk * H * H, &m->bytes);
+        m->part_w1.alloc(bp / kChunk * KP * H, &m->bytes);
+        m->part_head.alloc(bp / kHeadRows * (2 * H + 2), &m->bytes);
+        m->part_b1.alloc(bp / kHeadRows * H, &m->bytes);
+        m->tmp_w1.alloc(static_cast<size_t>(KP) * H, &m->bytes);
+        m->tmp_head.alloc(2 * H + 2, &m->bytes);
+        cuda_check(cudaMemcpy(m->params.p, params, m->n_params * 4, cudaMemcpyHostToDevice), "H2D params");
+        cuda_check(cudaMemset(m->grads.p, 0, m->n_params * 4), "memset");
+        cuda_check(cudaMemset(m->m.p, 0, m->n_params * 4), "memset");
+        cuda_check(cudaMemset(m->v.p, 0, m->n_params * 4), "memset");
+        refresh(m);
+        cuda_check(cudaStreamSynchronize(m->stream), "create");
+    });
+    if (st != GN_OK) {
+        delete m;
+        return st;
+    }
+    *out = m;
+    return GN_OK;
+}
+
+gn_status gn_mlp_destroy(gn_mlp *m)
+{
+    if (!m) return GN_OK;
+    return guarded([&] {
+        DeviceGuard dg(m->device);
+        cudaStreamSynchronize(m->stream);
+        delete m;
+    });
+}
+
+gn_status gn_mlp_get_params(gn_mlp *m, float *params)
+{
+    return guarded([&] {
+        check_mlp(m);
+        if (!params) fail(GN_EINVAL, "params is NULL");
+        DeviceGuard dg(m->device);
+        cuda_check(cudaStreamSynchronize(m->stream), "MLP");
+        cuda_check(cudaMemcpy(params, m->params.p, m->n_params * 4, cudaMemcpyDeviceToHost), "D2H params");
+    });
+}
+
+gn_status gn_mlp_gradients(gn_mlp *m, const float *X, const float *y, const int64_t *idx, int32_t B, float *grads,
+                           float *loss)
+{
+    return guarded([&] {
+        check_mlp(m);
+        if (B < 1 || B > m->max_bp || !X || !y || !grads) fail(GN_EINVAL, "bad batch (1 <= B <= max_batch)");
+        DeviceGuard dg(m->device);
+        float l = 0.0f;
+        run(m, X, y, idx, B, m->p.p, &l);
+        cuda_check(cudaMemcpy(grads, m->grads.p, m->n_params * 4, cudaMemcpyDeviceToHost), "D2H grads");
+        if (loss) *loss = l;
+    });
+}
+
+gn_status gn_mlp_train_step(gn_mlp *m, const float *X, const float *y, const int64_t *idx, int32_t B, float lr,
+                            float weight_decay, float *loss)
+{
+    return guarded([&] {
+        check_mlp(m);
+        if (B < 1 || B > m->max_bp || !X || !y) fail(GN_EINVAL, "bad batch (1 <= B <= max_batch)");
+        if (!(lr > 0.0f) || !(weight_decay >= 0.0f)) fail(GN_EINVAL, "bad learning rate or weight decay");
+        DeviceGuard dg(m->device);
+        run(m, X, y, idx, B, m->p.p, loss);
+        // AdamW (beta1 0.9, beta2 0.999, eps 1e-8) on the FP32 masters
+        m->adam_t += 1;
+        const double t = static_cast<double>(m->adam_t);
+        const float bc1 = static_cast<float>(1.0 - std::pow(0.9, t));
+        const float bc2 = static_cast<float>(1.0 - std::pow(0.999, t));
+        cuda_check(gn::mlp_launch_adamw(m->params.p, m->grads.p, m->m.p, m->v.p, m->n_params, lr, 0.9f, 0.999f, 1e-8f,
+                                        weight_decay, bc1, bc2, m->stream),
+                   "AdamW");
+        refresh(m);
+    });
+}
+
+gn_status gn_mlp_infer(gn_mlp *m, const float *X, int64_t B, float *p)
+{
+    return guarded([&] {
+        check_mlp(m);
+        if (B < 0 || (B > 0 && (!X || !p))) fail(GN_EINVAL, "bad batch");
+        DeviceGuard dg(m->device);
+        for (int64_t b0 = 0; b0 < B; b0 += m->max_bp) {
+            const int nb = static_cast<int>(std::min<int64_t>(m->max_bp, B - b0));
+            run(m, X + b0 * m->in_dim, nullptr, nullptr, nb, p + b0, nullptr);
+        }
+    });
+}
+
+gn_status gn_mlp_synchronize(gn_mlp *m)
+{
+    return guarded([&] {
+        check_mlp(m);
+        DeviceGuard dg(m->device);
+        cuda_check(cudaStreamSynchronize(m->stream), "MLP");
+    });
+}
+
+}  // extern "C"

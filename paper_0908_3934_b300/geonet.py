@@ -106,6 +106,19 @@ _SIGS = {
     "gn_batch_get_events": ([_P, C.c_int32, _P, _P, C.c_int64, C.POINTER(C.c_int64)], C.c_int),
     "gn_batch_set_step": ([_P, C.c_int64], C.c_int),
     "gn_batch_set_state": ([_P, C.c_int32, _P, C.c_int32, _P, _P, _P], C.c_int),
+    "gn_batch_export_traces": ([_P, C.c_int64, C.c_int32, _P], C.c_int),
+    "gn_xcorr_features": ([_P, C.c_int64, C.c_int32, _P, C.c_int32, C.c_int64, _P, _P, _P, C.c_double, C.c_double,
+                           _P, _P, _P], C.c_int),
+    "gn_score_auroc": ([_P, _P, C.c_int64, C.POINTER(C.c_double)], C.c_int),
+    "gn_score_f1": ([_P, _P, C.c_int64, C.c_double, C.POINTER(C.c_double)], C.c_int),
+    "gn_score_best_f1": ([_P, _P, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
+    "gn_mlp_create": ([C.c_int32, C.c_int32, _P, C.c_int32, _P, C.POINTER(C.c_void_p)], C.c_int),
+    "gn_mlp_destroy": ([_P], C.c_int),
+    "gn_mlp_get_params": ([_P, _P], C.c_int),
+    "gn_mlp_gradients": ([_P, _P, _P, _P, C.c_int32, _P, C.POINTER(C.c_float)], C.c_int),
+    "gn_mlp_train_step": ([_P, _P, _P, _P, C.c_int32, C.c_float, C.c_float, C.POINTER(C.c_float)], C.c_int),
+    "gn_mlp_infer": ([_P, _P, C.c_int64, _P], C.c_int),
+    "gn_mlp_synchronize": ([_P], C.c_int),
 }
 
 _lib = None
@@ -400,6 +413,127 @@ class Batch:
         w, c = _c(w, np.float32), _c(c, np.float32)
         bg = _c(bg_count, np.int32)
         check(lib().gn_batch_set_state(self.h, net, _ptr(hist), hist.shape[0], _ptr(w), _ptr(c), _ptr(bg)))
+
+
+# --------------------------------------------------------------------------- estimator
+def _dptr(t):
+    """Device address of a torch CUDA tensor (or None)."""
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def gn_batch_export_traces(batch: "Batch", first_sample: int, n_samples: int, out):
+    """Node-major traces [total nodes, n_samples] of every network of `batch` into
+    the CUDA tensor `out`."""
+    check(lib().gn_batch_export_traces(batch.h, first_sample, n_samples, _dptr(out)))
+    return out
+
+
+def gn_xcorr_features(traces, pos, src, dst, radius, features, score, v_max: float = 0.5, sample_ms: float = 1.0,
+                      stream=None):
+    """Lagged normalised cross-correlation features of candidate pairs; every
+    argument but v_max / sample_ms is a CUDA tensor (traces f32 [M, T], pos f64
+    [M, dim], src / dst i32 [P], radius f64 [P], features f32 [P, 33], score f32 [P])."""
+    M, T = traces.shape
+    check(lib().gn_xcorr_features(_dptr(traces), M, T, _dptr(pos), pos.shape[1], src.shape[0], _dptr(src),
+                                  _dptr(dst), _dptr(radius), v_max, sample_ms, _dptr(features), _dptr(score),
+                                  stream))
+
+
+def _host_scores(scores, labels):
+    s = np.ascontiguousarray(scores, np.float32)
+    y = np.ascontiguousarray(labels, np.uint8)
+    return s, y
+
+
+def gn_score_auroc(scores, labels) -> float:
+    s, y = _host_scores(scores, labels)
+    out = C.c_double()
+    check(lib().gn_score_auroc(_ptr(s), _ptr(y), s.size, C.byref(out)))
+    return out.value
+
+
+def gn_score_f1(scores, labels, threshold: float) -> float:
+    s, y = _host_scores(scores, labels)
+    out = C.c_double()
+    check(lib().gn_score_f1(_ptr(s), _ptr(y), s.size, threshold, C.byref(out)))
+    return out.value
+
+
+def gn_score_best_f1(scores, labels):
+    s, y = _host_scores(scores, labels)
+    thr, f1 = C.c_double(), C.c_double()
+    check(lib().gn_score_best_f1(_ptr(s), _ptr(y), s.size, C.byref(thr), C.byref(f1)))
+    return thr.value, f1.value
+
+
+MLP_HIDDEN = 256
+
+
+def mlp_pack(params: dict) -> np.ndarray:
+    """Packed parameter array [W1 | b1 | W2 | b2 | w3 | b3] (FP32)."""
+    return np.concatenate([np.asarray(params[k], np.float32).reshape(-1)
+                           for k in ("W1", "b1", "W2", "b2", "w3", "b3")])
+
+
+def mlp_unpack(flat: np.ndarray, in_dim: int) -> dict:
+    H = MLP_HIDDEN
+    sizes = dict(W1=(in_dim, H), b1=(H,), W2=(H, H), b2=(H,), w3=(H,), b3=(1,))
+    out, o = {}, 0
+    for k, shp in sizes.items():
+        n = int(np.prod(shp))
+        out[k] = np.asarray(flat[o:o + n]).reshape(shp)
+        o += n
+    return out
+
+
+class Mlp:
+    """The learned estimator's network on the GPU (gn_mlp_*); batches are CUDA tensors."""
+
+    def __init__(self, params: dict, max_batch: int, *, device: int = 0, stream=None):
+        self.in_dim = int(np.asarray(params["W1"]).shape[0])
+        flat = mlp_pack(params)
+        self.n_params = flat.size
+        h = C.c_void_p()
+        check(lib().gn_mlp_create(self.in_dim, max_batch, _ptr(flat), device, stream, C.byref(h)))
+        self.h = h
+
+    def gn_mlp_destroy(self):
+        if getattr(self, "h", None):
+            check(lib().gn_mlp_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.gn_mlp_destroy()
+        except Exception:
+            pass
+
+    def gn_mlp_get_params(self) -> dict:
+        flat = np.zeros(self.n_params, np.float32)
+        check(lib().gn_mlp_get_params(self.h, _ptr(flat)))
+        return mlp_unpack(flat, self.in_dim)
+
+    def gn_mlp_gradients(self, X, y, idx=None):
+        flat = np.zeros(self.n_params, np.float32)
+        loss = C.c_float()
+        B = X.shape[0] if idx is None else idx.shape[0]
+        check(lib().gn_mlp_gradients(self.h, _dptr(X), _dptr(y), _dptr(idx), B, _ptr(flat), C.byref(loss)))
+        return mlp_unpack(flat, self.in_dim), loss.value
+
+    def gn_mlp_train_step(self, X, y, idx=None, lr: float = 1e-3, weight_decay: float = 0.0,
+                          want_loss: bool = True):
+        loss = C.c_float()
+        B = X.shape[0] if idx is None else idx.shape[0]
+        check(lib().gn_mlp_train_step(self.h, _dptr(X), _dptr(y), _dptr(idx), B, lr, weight_decay,
+                                      C.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def gn_mlp_infer(self, X, out):
+        check(lib().gn_mlp_infer(self.h, _dptr(X), X.shape[0], _dptr(out)))
+        return out
+
+    def gn_mlp_synchronize(self):
+        check(lib().gn_mlp_synchronize(self.h))
 
 
 def exported_symbols() -> list:

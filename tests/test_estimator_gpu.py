@@ -1,0 +1,162 @@
+"""The connectivity estimator on the GPU (features, MLP forward / backward /
+AdamW, the trained estimator against the plain one) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import estimator as est
+from paper_0908_3934_b300 import netgen
+
+pytestmark = pytest.mark.gpu
+
+# Features: FP32 sums of <= 500 products of centred traces; the rounding of the
+# correlation is ~ sqrt(T) * 2^-24 relative to its denominator, far below 1e-5.
+FEAT_ATOL = 1e-5
+# MLP: BF16 operands (2^-8 relative) with FP32 accumulation on the GPU vs FP64 on
+# the same BF16-rounded operands in the oracle: the only differences are FP32
+# accumulation order and an occasional one-ulp BF16 rounding of an activation.
+GRAD_COS, GRAD_REL, P_ATOL = 0.999, 2e-2, 5e-3
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _seeded_traces(seed, n_nodes=300, T=500):
+    """Traces with delayed, noisy copies along random geometric pairs (input shared
+    by both sides)."""
+    rng = np.random.default_rng(seed)
+    pos = rng.random((n_nodes, 2)) * 0.6
+    Y = rng.normal(0.0, 0.05, (T, n_nodes)) - 1.2
+    drive = rng.normal(0.0, 1.0, T + 64)
+    for j in range(n_nodes):
+        if rng.random() < 0.5:
+            sh = int(rng.integers(0, 40))
+            Y[:, j] += 0.3 * drive[sh:sh + T]
+    src = rng.integers(0, n_nodes, 4000).astype(np.int32)
+    dst = rng.integers(0, n_nodes, 4000).astype(np.int32)
+    keep = src != dst
+    return Y.astype(np.float32), pos, src[keep], dst[keep]
+
+
+def test_features_match_the_oracle():
+    torch = _torch()
+    from paper_0908_3934_b300 import geonet
+    Y, pos, src, dst = _seeded_traces(1)
+    r = 0.35
+    F, S = est.ncc_features(Y.astype(np.float64), pos, src, dst, r)
+    dev = torch.device("cuda")
+    X = torch.from_numpy(np.ascontiguousarray(Y.T)).to(dev)
+    feats = torch.empty((src.size, 33), dtype=torch.float32, device=dev)
+    score = torch.empty(src.size, dtype=torch.float32, device=dev)
+    geonet.gn_xcorr_features(X, torch.from_numpy(pos).to(dev), torch.from_numpy(src).to(dev),
+                             torch.from_numpy(dst).to(dev), torch.full((src.size,), r, dtype=torch.float64, device=dev),
+                             feats, score)
+    g = feats.cpu().numpy().astype(np.float64)
+    assert np.abs(g - F).max() <= FEAT_ATOL
+    assert np.abs(score.cpu().numpy() - S).max() <= FEAT_ATOL
+
+
+def _cos(a, b):
+    a, b = np.ravel(a), np.ravel(b)
+    return float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-300))
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / (np.linalg.norm(np.ravel(b)) + 1e-300))
+
+
+@pytest.mark.parametrize("B", [1000, 4096])
+def test_mlp_forward_and_gradients_match_the_oracle(B):
+    torch = _torch()
+    from paper_0908_3934_b300 import geonet
+    X, y = netgen.mlp_toy_batch(3, B)
+    prm = netgen.mlp_init(4)
+    prm["b1"] = np.linspace(-0.1, 0.1, 256).astype(np.float32)
+    prm["b2"] = np.linspace(0.05, -0.05, 256).astype(np.float32)
+    prm["b3"] = np.array([0.1], np.float32)
+    m = geonet.Mlp(prm, max_batch=4096)
+    dev = torch.device("cuda")
+    Xd, yd = torch.from_numpy(X).to(dev), torch.from_numpy(y).to(dev)
+    p = torch.empty(B, device=dev)
+    m.gn_mlp_infer(Xd, p)
+    m.gn_mlp_synchronize()
+    pr, cache = est.mlp_forward(prm, X)
+    assert np.abs(p.cpu().numpy() - pr).max() <= P_ATOL
+    g, loss = m.gn_mlp_gradients(Xd, yd)
+    go = est.mlp_backward(prm, cache, pr, y)
+    assert loss == pytest.approx(est.bce(pr, y), rel=1e-3)
+    for k in ("W1", "b1", "W2", "b2", "w3", "b3"):
+        assert _cos(g[k], go[k]) >= GRAD_COS, k
+        assert _rel(g[k], go[k]) <= GRAD_REL, k
+    # rows gathered through an index array give the gradients of those rows
+    idx = np.random.default_rng(5).permutation(B)[: B // 2]
+    g2, _ = m.gn_mlp_gradients(Xd, yd, torch.from_numpy(idx).to(dev))
+    pr2, c2 = est.mlp_forward(prm, X[idx])
+    go2 = est.mlp_backward(prm, c2, pr2, y[idx])
+    assert _cos(g2["W2"], go2["W2"]) >= GRAD_COS and _rel(g2["W2"], go2["W2"]) <= GRAD_REL
+
+
+def test_adamw_training_matches_the_oracle():
+    torch = _torch()
+    from paper_0908_3934_b300 import geonet
+    X, y = netgen.mlp_toy_batch(6, 2048)
+    prm = netgen.mlp_init(7)
+    m = geonet.Mlp(prm, max_batch=2048)
+    dev = torch.device("cuda")
+    Xd, yd = torch.from_numpy(X).to(dev), torch.from_numpy(y).to(dev)
+    ref = {k: v.astype(np.float64) for k, v in prm.items()}
+    state = {}
+    for step in range(5):
+        loss = m.gn_mlp_train_step(Xd, yd, lr=1e-3)
+        pr, cache = est.mlp_forward(ref, X)
+        assert loss == pytest.approx(est.bce(pr, y), rel=2e-3), step
+        ref = est.adamw(ref, est.mlp_backward(ref, cache, pr, y), state, lr=1e-3)
+    got = m.gn_mlp_get_params()
+    # Adam moves every weight by about lr whatever the gradient's size, so a weight
+    # whose gradient is at BF16 rounding level can step the other way: the update
+    # is compared normwise with room for that, the weights themselves tightly.
+    for k in ("W1", "W2", "w3"):
+        assert _rel(got[k] - prm[k], ref[k] - prm[k]) <= 0.25, k
+        assert _rel(got[k], ref[k]) <= 1e-2, k
+
+
+def test_learned_estimator_beats_the_plain_one_and_plain_matches_the_oracle():
+    """Nets with known topology, simulated on the GPU: the MLP trained on 48 of them
+    beats the peak-correlation estimator on 12 held-out ones (AUROC), and the plain
+    estimator's AUROC on the GPU agrees with the FP64 oracle's own pipeline."""
+    torch = _torch()
+    from paper_0908_3934_b300 import geonet, pipeline
+    train_specs = [netgen.batch_member(20000 + i, n_lo=128, n_hi=512) for i in range(48)]
+    test_specs = [netgen.batch_member(30000 + i, n_lo=128, n_hi=512) for i in range(12)]
+    tr = pipeline.simulate_features(train_specs, n_samples=500)
+    te = pipeline.simulate_features(test_specs, n_samples=500)
+    plain = pipeline.scores(te["score"], te["label"])
+    mlp = geonet.Mlp(netgen.mlp_init(8), max_batch=2048)
+    losses = pipeline.train(mlp, tr["features"], tr["label"], epochs=6, batch=2048, seed=9)
+    assert losses[-1] < losses[0]
+    p = torch.empty(te["features"].shape[0], device=te["features"].device)
+    mlp.gn_mlp_infer(te["features"], p)
+    mlp.gn_mlp_synchronize()
+    learned = pipeline.scores(p, te["label"])
+    assert learned["auroc"] > plain["auroc"] + 0.02, (learned, plain)
+    # the oracle's own pipeline (FP64 simulation and features) on 4 of the test nets
+    sub = list(range(4))
+    Fo, So, lab = [], [], []
+    for i in sub:
+        sp = test_specs[i]
+        ref = oracle_sim(sp)
+        s, d, lb = netgen.candidates(sp)
+        F, S = est.ncc_features(ref, sp.pos, s, d, sp.radius)
+        So.append(S)
+        lab.append(lb)
+    So, lab = np.concatenate(So), np.concatenate(lab)
+    sel = np.isin(te["net"], sub)
+    auc_gpu = geonet.gn_score_auroc(te["score"].cpu().numpy()[sel], te["label"][sel])
+    assert abs(auc_gpu - est.auroc(So, lab)) <= 0.02
+
+
+def oracle_sim(spec):
+    import oracle
+    r = oracle.simulate(spec, 500 * spec.obs["sample_every"])
+    return r["y"]
