@@ -234,6 +234,65 @@ def run_batched(args, local, stream, rank):
             "speedup_vs_loop": t_loop / t}
 
 
+def run_estimator(args, local, stream):
+    """Connectivity estimation with config-5 laws: networks of N = 512 (2D, kept
+    in-degree ~20, 1-8 pulsed nodes, 500 ms observed at 1 ms); the MLP is trained on
+    `est_train` networks (seeds 10^6 + i) and both estimators are scored on
+    `est_test` held-out ones (seeds 2 10^6 + i).  Thresholds for F1 are chosen on
+    the training networks.  Throughput: candidate pairs scored per second by
+    features + inference on resident traces."""
+    import torch
+    from paper_0908_3934_b300 import geonet, pipeline
+    t0 = time.perf_counter()
+    tr_specs = [netgen.batch_member(10**6 + i, n=512) for i in range(args.est_train)]
+    te_specs = [netgen.batch_member(2 * 10**6 + i, n=512) for i in range(args.est_test)]
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    tr = pipeline.simulate_features(tr_specs, n_samples=500, device=local, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    t_sim_train = time.perf_counter() - t0
+    mlp = geonet.Mlp(netgen.mlp_init(2024), max_batch=8192, device=local, stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    losses = pipeline.train(mlp, tr["features"], tr["label"], epochs=args.est_epochs, batch=8192, seed=2025)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    P_tr = tr["features"].shape[0]
+    p_tr = torch.empty(P_tr, device=tr["features"].device)
+    mlp.gn_mlp_infer(tr["features"], p_tr)
+    mlp.gn_mlp_synchronize()
+    thr_learned, _ = geonet.gn_score_best_f1(p_tr.cpu().numpy(), tr["label"])
+    thr_plain, _ = geonet.gn_score_best_f1(tr["score"].cpu().numpy(), tr["label"])
+    te = pipeline.simulate_features(te_specs, n_samples=500, device=local, stream=stream.cuda_stream)
+    # throughput of scoring: features + inference from resident traces
+    tab = pipeline.candidate_table(te_specs)
+    dev = te["features"].device
+    pos, srcd = torch.from_numpy(tab["pos"]).to(dev), torch.from_numpy(tab["src"]).to(dev)
+    dstd, rad = torch.from_numpy(tab["dst"]).to(dev), torch.from_numpy(tab["radius"]).to(dev)
+    P = srcd.shape[0]
+    feats = torch.empty((P, 33), dtype=torch.float32, device=dev)
+    sc = torch.empty(P, dtype=torch.float32, device=dev)
+    p_te = torch.empty(P, device=dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    geonet.gn_xcorr_features(te["traces"], pos, srcd, dstd, rad, feats, sc, stream=stream.cuda_stream)
+    mlp.gn_mlp_infer(feats, p_te)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_score = ev0.elapsed_time(ev1) / 1e3
+    learned = pipeline.scores(p_te, te["label"], thr_learned)
+    plain = pipeline.scores(sc, te["label"], thr_plain)
+    return {"workload": f"{args.est_train} training + {args.est_test} held-out nets of N=512 (config-5 laws), "
+                        f"{P_tr} + {P} candidate pairs, {args.est_epochs} epochs of batch 8192",
+            "auroc_learned": learned["auroc"], "auroc_plain": plain["auroc"],
+            "f1_learned": learned["f1"], "f1_plain": plain["f1"],
+            "pairs_scored_per_s": P / t_score, "unit": "candidate pairs/s (features + inference)",
+            "train_samples_per_s": P_tr * args.est_epochs / t_train, "loss_first_last": [losses[0], losses[-1]],
+            "seconds": {"generate_host": t_gen, "simulate_and_features_train": t_sim_train, "train": t_train,
+                        "score": t_score}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -249,6 +308,10 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=10000, help="steps of the batched measurement")
     ap.add_argument("--loop-sample", type=int, default=32, help="networks timed by the looped comparison")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--est-train", type=int, default=2000, help="training nets of the estimator measurement")
+    ap.add_argument("--est-test", type=int, default=200, help="held-out nets of the estimator measurement")
+    ap.add_argument("--est-epochs", type=int, default=8)
+    ap.add_argument("--no-estimator", action="store_true")
     ap.add_argument("--step-kernel", type=int, default=0, choices=[0, 1, 2],
                     help="0: autotuned, 1: one row block per CTA, 2: persistent bulk-copy pipelined kernel")
     args = ap.parse_args()
@@ -373,6 +436,8 @@ def main():
             bt["value"] = bt["value"] * bt["seconds"] / tt.item() * world
             bt["seconds"] = tt.item()
         line["batched"] = bt
+    if not args.no_estimator and rank == 0:
+        line["estimator"] = run_estimator(args, local, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(spec, args.cpu_steps)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
