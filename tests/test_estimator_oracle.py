@@ -3,8 +3,6 @@ closed forms and finite differences."""
 import numpy as np
 import pytest
 import torch
-from sklearn.metrics import f1_score, roc_auc_score
-from sklearn.neural_network import MLPClassifier
 
 from oracle import estimator as est
 from paper_0908_3934_b300 import netgen
@@ -57,7 +55,14 @@ def test_first_lag_and_distance_feature():
     assert F[0, 0] == pytest.approx(np.corrcoef(Y[:99, 0], Y[1:, 1])[0, 1], abs=1e-12)
 
 
+def _sklearn():
+    """scikit-learn is a test-only dependency that not every machine has."""
+    return pytest.importorskip("sklearn")
+
+
 def test_auroc_matches_sklearn_and_special_cases():
+    _sklearn()
+    from sklearn.metrics import roc_auc_score
     rng = np.random.default_rng(4)
     s = rng.normal(size=3000)
     y = (rng.random(3000) < 1 / (1 + np.exp(-2 * s))).astype(int)
@@ -70,6 +75,8 @@ def test_auroc_matches_sklearn_and_special_cases():
 
 
 def test_f1_and_best_threshold_match_sklearn():
+    _sklearn()
+    from sklearn.metrics import f1_score
     rng = np.random.default_rng(5)
     s = rng.normal(size=500)
     y = (s + rng.normal(size=500) > 0).astype(int)
@@ -83,6 +90,8 @@ def test_f1_and_best_threshold_match_sklearn():
 def test_mlp_forward_matches_sklearn():
     """The exact (unquantised) forward pass equals scikit-learn's MLPClassifier with
     the same weights (relu hidden layers, logistic output)."""
+    _sklearn()
+    from sklearn.neural_network import MLPClassifier
     X, y = netgen.mlp_toy_batch(6, 64)
     prm = netgen.mlp_init(7)
     prm["b1"] = np.linspace(-0.1, 0.1, 256).astype(np.float32)
