@@ -41,6 +41,19 @@ METRIC = "edge-updates/s"
 EDGE_BYTES = 12        # packed record (src|D 4 B + weight 4 B) + the gathered FP32 value
 NODE_BYTES = 36.2      # v~ read 4, (w~,c~) read 8 + write 8, ring write 4, row_ptr 4,
                        # background counter 4 + caller id 4, readout 4 B / 20 steps
+# staged kernel: per edge its weight 4 B + gather index 2 B; per distinct (source,
+# delay) of a tile its packed key 4 B + the FP32 history value 4 B
+STAGED_EDGE_BYTES = 6
+STAGED_GATHER_BYTES = 8
+KERNEL_NAMES = {1: "k_step", 2: "k_step_pipe", 3: "k_step_staged"}
+
+
+def algorithmic_bytes(info: dict, E: int, N: int) -> float:
+    """Bytes one step must move under the chosen kernel's edge format (padding and
+    re-reads excluded)."""
+    if info["step_kernel"] == 3:
+        return E * STAGED_EDGE_BYTES + info["step_gathers"] * STAGED_GATHER_BYTES + N * NODE_BYTES
+    return E * EDGE_BYTES + N * NODE_BYTES
 
 
 def workload(name: str, rank: int):
@@ -78,7 +91,8 @@ def peaks():
 
 def kernel_hash() -> str:
     h = hashlib.sha256()
-    for f in ("k_step.cu", "k_step_pipe.cu", "step_common.cuh", "ptx.cuh", "internal.cuh", "philox.cuh"):
+    for f in ("k_step.cu", "k_step_pipe.cu", "k_step_staged.cu", "staged.cu", "step_common.cuh", "ptx.cuh",
+              "internal.cuh", "philox.cuh"):
         with open(os.path.join(ROOT, "paper_0908_3934_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -147,6 +161,22 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def replica_rate(units: float, seconds: float, device="cpu"):
+    """Whole-job rate of independent replicas: the units every rank processed over
+    the slowest rank's timed region (sum and max over ranks; no data-path
+    collective).  Returns (rate, total units, max seconds); one process returns
+    its own."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return units / seconds, units, seconds
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    sec = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(sec, op=dist.ReduceOp.MAX)
+    return u.item() / sec.item(), u.item(), sec.item()
 
 
 def cpu_baseline(spec, steps: int):
@@ -312,8 +342,9 @@ def main():
     ap.add_argument("--est-test", type=int, default=200, help="held-out nets of the estimator measurement")
     ap.add_argument("--est-epochs", type=int, default=8)
     ap.add_argument("--no-estimator", action="store_true")
-    ap.add_argument("--step-kernel", type=int, default=0, choices=[0, 1, 2],
-                    help="0: autotuned, 1: one row block per CTA, 2: persistent bulk-copy pipelined kernel")
+    ap.add_argument("--step-kernel", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="0: autotuned, 1: one row block per CTA, 2: persistent bulk-copy pipelined kernel, "
+                         "3: staged tiles (distinct gathers in shared memory)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -394,20 +425,12 @@ def main():
     t_e2e = time.perf_counter() - t0
     e2e_steps = n_chunks * chunk
 
-    if world > 1:
-        tt = torch.tensor([t, t_e2e], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t, t_e2e = tt.tolist()
-        ee = torch.tensor([float(E)], device=dev, dtype=torch.float64)
-        dist.all_reduce(ee, op=dist.ReduceOp.SUM)
-        E_total = ee.item()
-    else:
-        E_total = float(E)
-
-    value = E_total * args.steps / t
+    value, _, t = replica_rate(float(E) * args.steps, t, dev)
+    e2e_value, _, t_e2e = replica_rate(float(E) * e2e_steps, t_e2e, dev)
+    E_total = value * t / args.steps
     peak, peak_kind = peaks()
     step_s = t / args.steps
-    bytes_step = E * EDGE_BYTES + N * NODE_BYTES
+    bytes_step = algorithmic_bytes(info, E, N)
     achieved = bytes_step / step_s / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
@@ -418,8 +441,8 @@ def main():
                      "frac": achieved / peak, "peak_source": peak_kind,
                      "traffic": traffic_per_launch(args.workload),
                      "algorithmic_bytes_per_launch": bytes_step,
-                     "kernel": "k_step_pipe" if info["step_kernel"] == 2 else "k_step"},
-        "e2e": {"value": E_total * e2e_steps / t_e2e, "unit": METRIC,
+                     "kernel": KERNEL_NAMES[info["step_kernel"]]},
+        "e2e": {"value": e2e_value, "unit": METRIC,
                 "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps},
         "gpu_launches": launches, "clocks": clocks,
         "layout": {"step_kernel": info["step_kernel"], "grid": info["grid"], "cta_threads": info["step_threads"],
@@ -430,11 +453,7 @@ def main():
     }
     if not args.no_batched:
         bt = run_batched(args, local, stream, rank)
-        if world > 1:
-            tt = torch.tensor([bt["seconds"]], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            bt["value"] = bt["value"] * bt["seconds"] / tt.item() * world
-            bt["seconds"] = tt.item()
+        bt["value"], _, bt["seconds"] = replica_rate(bt["value"] * bt["seconds"], bt["seconds"], dev)
         line["batched"] = bt
     if not args.no_estimator and rank == 0:
         line["estimator"] = run_estimator(args, local, stream)

@@ -105,7 +105,14 @@ typedef struct {
     int32_t edge_format;         /* 0: packed 32-bit keys when N * ring_depth <= 2^32, else 64-bit; 1: always 64-bit */
     int32_t step_kernel;         /* 0: chosen by timing the candidates on the first gn_step (autotune);
                                     1: one row block per CTA, chained launches; 2: persistent CTAs with a
-                                    bulk-copy pipeline of row blocks */
+                                    bulk-copy pipeline of row blocks; 3: staged tiles -- each CTA fetches
+                                    the distinct (source, delay) history values of a tile of rows once into
+                                    shared memory, then sums each row from there.  3 fails with GN_EINVAL
+                                    if a single row needs more shared memory than a CTA may have
+                                    (in-degree above about 20,000).  Every kernel sums a node's inputs
+                                    in the same order, so results do not depend on this choice.  The
+                                    environment variable GN_STEP_SHAPE=i picks the CTA shape of an
+                                    explicitly chosen kernel 1 or 3 (default 0) */
     void *cuda_stream;           /* cudaStream_t to run on; NULL: the library makes its own */
     int32_t device;              /* CUDA device ordinal */
 } gn_net_desc;
@@ -128,15 +135,20 @@ typedef struct {
     int32_t min_delay;
     int64_t n_clamped;           /* geometric delays that rounded below one step */
     int32_t edge_format;         /* 0: packed 32-bit (src << log2 R | D); 1: 64-bit (src, D) */
-    int32_t n_blocks;            /* row blocks of the step kernel */
-    int32_t step_kernel;         /* 1 or 2 once chosen (0 before the first gn_step when autotuning) */
+    int32_t n_blocks;            /* row blocks (kernels 1, 2) or tiles (kernel 3) of the step kernel */
+    int32_t step_kernel;         /* 1, 2 or 3 once chosen (0 before the first gn_step when autotuning) */
     int32_t step_threads;        /* CTA size of the chosen kernel */
-    int32_t step_edges_per_thread;
+    int32_t step_edges_per_thread; /* kernels 1, 2: edges per thread of a row block; 3: longest row summed
+                                      by one thread (longer rows: 32 lane-strided pieces) */
     int32_t grid;                /* CTAs per step launch */
     int64_t step;                /* steps taken */
     int64_t samples;             /* samples produced */
     double v_rest, w_rest;
     size_t device_bytes;         /* device memory held by the handle */
+    int64_t step_gathers;        /* history values fetched per step: n_edges for kernels 1 and 2; for
+                                    kernel 3 the distinct (source, delay) pairs summed over its tiles */
+    int64_t step_entries;        /* edge records read per step: n_edges for kernels 1 and 2; for kernel 3
+                                    the stored entries including the padding of its slices */
 } gn_net_info;
 
 typedef struct gn_net gn_net;

@@ -65,11 +65,32 @@ struct StepArgs {
     const int4 *bdesc;       // [n_blocks] {first row, end row, first edge, end edge}
     int32_t n_blocks;
     unsigned int *status;    // device error word (kStatus* bits), read by the host after a sync
+    // staged kernel (k_step_staged.cu): tiles of rows with their distinct gathers
+    const int4 *st_tile;     // [tiles] {first row, rows, first gather, gathers}
+    const int4 *st_tile2;    // [tiles] {first slice, slices, pieces, 0}
+    const void *st_ukey;     // per gather: packed key, or {src, D} when wide
+    const int2 *st_slice;    // {first entry, length}
+    const float *st_w;       // entry weights, column-major in slices of 32 pieces
+    const uint16_t *st_u;    // entry gather index within its tile
+    const int32_t *st_rq;    // [N + 1] first piece-list entry of each row
+    const uint16_t *st_plist;  // lane slot of each piece
+    int32_t st_ucap;         // gather slots of a CTA's shared memory (largest padded gather count)
+    int32_t st_xcap;         // entry slots of a CTA's shared memory (largest entry count)
 };
 
 constexpr unsigned int kStatusTimeout = 1u;  // a bounded mbarrier wait gave up
 
 constexpr int kEdgePad = 4096;
+
+// Summation order of a node's input S_j, the same in every step kernel and in the
+// batched kernel, so the kernel the autotuner picks never changes a result: a row
+// of at most kWarpRow edges is summed in row order by one thread; a longer row is
+// split over 32 lanes (lane l takes edges l, l + 32, ... in order) whose partial
+// sums are combined by the butterfly x_l += x_(l xor o), o = 16, 8, 4, 2, 1.  Each
+// term w_e * v~ is rounded to FP32 before it is added (no fused multiply-add).
+// (Rows longer than one row block's capacity are summed in a shape-dependent order
+// by kernels 1, 2 and the batched kernel.)
+constexpr int kWarpRow = 48;
 
 // CTA shapes of the row-block step kernel: T threads, EPT edges per thread; its
 // row blocks hold at most T * EPT - 3 edges and T rows.  The persistent pipelined
@@ -84,6 +105,19 @@ extern const StepShape kStepShapes[kNumStepShapes];
 cudaError_t launch_step(const StepArgs &a, int n_blocks, int k, int shape, bool packed, bool stream_edges,
                         cudaStream_t s);
 cudaError_t launch_advance(int64_t *d_step, int64_t by, cudaStream_t s);
+// staged kernel (k_step_staged.cu): one CTA of `threads` per tile, smem_bytes of
+// dynamic shared memory; prepare raises the kernel's shared-memory limit
+// stage_entries: 1 copies a tile's edge entries into shared memory with its gather
+// keys; 0 keeps only the keys there and prefetches the entries into L2 (less
+// shared memory per CTA, more CTAs per SM)
+constexpr int kNumStagedShapes = 4;
+struct StagedShape {
+    int threads, ucap, ecap, pcap, stage_entries;
+};
+extern const StagedShape kStagedShapes[kNumStagedShapes];
+cudaError_t launch_step_staged(const StepArgs &a, int n_tiles, int k, const StagedShape &shape, bool packed,
+                               bool stream_edges, size_t smem_bytes, cudaStream_t s);
+cudaError_t step_staged_prepare(const StagedShape &shape, bool packed, bool stream_edges, size_t smem_bytes);
 // persistent bulk-copy pipelined variant (k_step_pipe.cu); grid = CTAs to launch
 cudaError_t launch_step_pipe(const StepArgs &a, int grid, int k, bool packed, bool stream_edges, cudaStream_t s);
 int step_pipe_smem_bytes(bool packed);

@@ -33,7 +33,6 @@ __device__ __forceinline__ void batch_block(const StepArgs &a, int64_t n, int b,
 {
     constexpr int CAP = T * EPT;
     constexpr int NQ = EPT / 4;
-    constexpr int kWarpRow = 48;
     const int t = threadIdx.x;
     const int4 d = __ldg(a.bdesc + b);
     const int r0 = d.x, r1 = d.y, e0 = d.z, e1 = d.w;

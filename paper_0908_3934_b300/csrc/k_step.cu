@@ -35,7 +35,6 @@ __global__ void __launch_bounds__(T, MINB) k_step(const StepArgs a, const int k)
 {
     constexpr int CAP = T * EPT;
     constexpr int NQ = EPT / 4;  // edge quads per thread
-    constexpr int kWarpRow = 48;  // rows longer than this are summed by a warp
     __shared__ float s_prod[CAP];
     __shared__ float s_long[T];
     __shared__ int s_rp[T + 1];

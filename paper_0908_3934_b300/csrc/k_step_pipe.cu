@@ -84,7 +84,6 @@ __global__ void __launch_bounds__(T) k_step_pipe(const StepArgs a, const int k)
 {
     using L = PipeLayout<T, EPT, KEYB>;
     constexpr int CAP = L::CAP;
-    constexpr int kWarpRow = 48;
     constexpr bool kPacked = KEYB == 4;
     extern __shared__ __align__(128) uint8_t smem[];
     uint8_t *stages = smem;

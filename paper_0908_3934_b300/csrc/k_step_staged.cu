@@ -1,0 +1,264 @@
+// The staged step kernel: one launch advances every node by dt, one CTA per tile
+// of consecutive target nodes (the layout is built by build_staged).
+//
+//   0. the CTA lets the next step's grid start (griddepcontrol.launch_dependents),
+//      and one thread starts bulk copies (cp.async.bulk, completion on an
+//      mbarrier) of what does not change between steps -- the tile's gather keys
+//      and its edge entries (weight, gather index) -- into shared memory, while
+//      the other threads load the piece list and caller id of their row.  All of
+//      this may overlap the end of the previous step;
+//   1. griddepcontrol.wait; the CTA reads the state of its rows and, once the
+//      copies have landed, fetches each distinct history value its edges read,
+//      v~_src(n - D) from ring slot (n - D) & (R - 1), once, into shared memory.
+//      The gathers are sorted by (D, src), so a warp's 32 reads fall in a few lines
+//      of one ring slot;
+//   2. each lane sums one piece of a row in a register, S_piece = sum_e w_e
+//      v~_src(n - D_e) over its edges in order, all from shared memory (Eq. Yjset,
+//      Sec. 2).  A row of at most kWarpRow edges is one piece; a longer row is 32
+//      lane-strided pieces -- the summation order of every step kernel;
+//   3. one thread per row combines its pieces (a long row's 32 by the butterfly
+//      tree of a warp reduction) and runs the node update:
+//      stimulus, FHN Euler step about the rest point (Sec. 3.1, Eq. fnstate),
+//      history write, low-pass readout, noisy observation (Sec. 3.3), events and
+//      first arrivals.
+// Reads of step data are of step n (or older), writes are of step n + 1, and slot
+// (n + 1) & (R - 1) is never read in step n because every delay is <= R - 2.
+// The copy wait is bounded: if it gives up, the CTA sets kStatusTimeout in the
+// status word (the host reports GN_ETIMEOUT), waits once more for its copies and
+// leaves its rows untouched.
+#include "step_common.cuh"
+
+namespace gn {
+namespace {
+
+using namespace step;
+
+constexpr uint32_t kWaitLimit = 1u << 22;
+
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <int T, bool kSE, bool kPacked, bool kStream>
+__global__ void __launch_bounds__(T, (kSE ? 1024 : 1536) / T) k_step_staged(const StepArgs a, const int k)
+{
+    constexpr int G = 8;  // gathers in flight per thread
+    // [mbarrier 16 B][keys][values (wide keys only)][entry weights][entry indices][piece sums];
+    // without entry staging (kSE false) the entry arrays are absent
+    extern __shared__ __align__(128) unsigned char s_raw[];
+    __shared__ int s_fail;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(s_raw);
+    uint32_t *s_key = reinterpret_cast<uint32_t *>(s_raw + 16);
+    float *s_val = kPacked ? reinterpret_cast<float *>(s_key)
+                           : reinterpret_cast<float *>(s_raw + 16 + static_cast<size_t>(a.st_ucap) * 8);
+    float *s_w = reinterpret_cast<float *>(s_raw + 16 + static_cast<size_t>(a.st_ucap) * (kPacked ? 4 : 12));
+    uint16_t *s_u = reinterpret_cast<uint16_t *>(s_w + a.st_xcap);
+    float *s_part = kSE ? reinterpret_cast<float *>(s_u + a.st_xcap) : s_w;
+
+    pdl_launch_dependents();
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int4 td = __ldg(a.st_tile + blockIdx.x);   // {r0, rows, u0, gathers}
+    const int4 td2 = __ldg(a.st_tile2 + blockIdx.x); // {s0, slices, x0, entries}
+    const int nu = td.w, nx = td2.w;
+    const uint32_t kbytes = static_cast<uint32_t>((nu + 3) & ~3) * (kPacked ? 4u : 8u);
+    const uint32_t bytes = kbytes + (kSE ? static_cast<uint32_t>(nx) * 6u : 0u);
+    if (t == 0) {
+        s_fail = 0;
+        if (bytes) {
+            mbar_init(bar, 1);
+            fence_barrier_init();
+            mbar_arrive_expect_tx(bar, bytes);
+            const char *keys = static_cast<const char *>(a.st_ukey) + static_cast<size_t>(td.z) * (kPacked ? 4 : 8);
+            // a stream larger than L2 is read once per step: evict it first
+            const uint64_t pol = kStream ? l2_evict_first() : l2_evict_last();
+            if (kbytes) bulk_g2s_hint(s_key, keys, kbytes, bar, pol);
+            if (kSE && nx) {
+                bulk_g2s_hint(s_w, a.st_w + td2.z, static_cast<uint32_t>(nx) * 4u, bar, pol);
+                bulk_g2s_hint(s_u, a.st_u + td2.z, static_cast<uint32_t>(nx) * 2u, bar, pol);
+            }
+        }
+        if (!kSE && nx) {
+            bulk_prefetch_l2(a.st_w + td2.z, static_cast<uint32_t>(nx) * 4u);
+            bulk_prefetch_l2(a.st_u + td2.z, static_cast<uint32_t>(nx) * 2u);
+        }
+    }
+    const int r = td.x + t;
+    const bool own = t < td.y;
+    int q0 = 0, q1 = 0;
+    int32_t orig = kLoad;
+    if (own) {
+        q0 = __ldg(a.st_rq + r);
+        q1 = __ldg(a.st_rq + r + 1);
+        orig = __ldg(a.perm + r);
+    }
+    int2 sd0 = make_int2(0, 0);
+    if (warp < td2.y) sd0 = __ldg(a.st_slice + td2.x + warp);
+
+    pdl_wait();
+    const int64_t n = *a.d_step + k;
+    float v = 0.0f;
+    float2 wc = make_float2(0.0f, 0.0f);
+    int32_t cnt0 = kLoad;
+    if (own) {
+        v = a.ring[(n & a.ring_mask) * a.ring_stride + r];
+        wc = a.wc[r];
+        if (a.bg_thr) cnt0 = a.bgc[r];
+    }
+    if (t == 0 && bytes && !mbar_wait_bounded(bar, 0, kWaitLimit)) {
+        atomicOr(a.status, kStatusTimeout);
+        s_fail = 1;
+        mbar_wait_bounded(bar, 0, kWaitLimit);  // the copies must land before the CTA leaves
+    }
+    __syncthreads();
+    if (s_fail) return;
+
+    // 1. the tile's distinct history values (packed keys are overwritten in place)
+    const uint32_t dmask = (1u << a.dbits) - 1u;
+    for (int base = 0; base < nu; base += G * T) {
+        float val[G];
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+            const int u = base + t + i * T;
+            if (u < nu) {
+                uint32_t src, d;
+                if constexpr (kPacked) {
+                    const uint32_t kk = s_key[u];
+                    src = kk >> a.dbits;
+                    d = kk & dmask;
+                } else {
+                    const uint2 kk = reinterpret_cast<const uint2 *>(s_key)[u];
+                    src = kk.x;
+                    d = kk.y;
+                }
+                val[i] = gather(a, n, src, d);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+            const int u = base + t + i * T;
+            if (u < nu) s_val[u] = val[i];
+        }
+    }
+    __syncthreads();
+
+    // 2. one piece per lane, 32 pieces per warp at a time
+    for (int sl = warp; sl < td2.y; sl += T / 32) {
+        const int2 sd = sl == warp ? sd0 : __ldg(a.st_slice + td2.x + sl);
+        float acc = 0.0f;
+        if constexpr (kSE) {
+            const float *wp = s_w + sd.x + lane;
+            const uint16_t *up = s_u + sd.x + lane;
+#pragma unroll 4
+            for (int kk = 0; kk < sd.y; ++kk) acc = __fadd_rn(acc, __fmul_rn(wp[kk * 32], s_val[up[kk * 32]]));
+        } else {
+            const float *wp = a.st_w + td2.z + sd.x + lane;
+            const uint16_t *up = a.st_u + td2.z + sd.x + lane;
+            int kk = 0;
+            for (; kk + 8 <= sd.y; kk += 8) {
+                float w8[8];
+                uint16_t u8[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    w8[i] = __ldcs(wp + (kk + i) * 32);
+                    u8[i] = __ldcs(up + (kk + i) * 32);
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) acc = __fadd_rn(acc, __fmul_rn(w8[i], s_val[u8[i]]));
+            }
+            for (; kk < sd.y; ++kk) acc = __fadd_rn(acc, __fmul_rn(__ldcs(wp + kk * 32), s_val[__ldcs(up + kk * 32)]));
+        }
+        s_part[sl * 32 + lane] = acc;
+    }
+    __syncthreads();
+
+    // 3. row sums and the node update
+    if (own) {
+        float S = 0.0f;
+        if (q1 - q0 == 1) {
+            S = s_part[__ldg(a.st_plist + q0)];
+        } else if (q1 - q0 == 32) {
+            float x[32];
+#pragma unroll
+            for (int l = 0; l < 32; ++l) x[l] = s_part[__ldg(a.st_plist + q0 + l)];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int l = 0; l < o; ++l) x[l] = __fadd_rn(x[l], x[l + o]);
+            S = x[0];
+        }
+        node_update(a, r, n, v, wc, S, orig, cnt0);
+    }
+}
+
+template <int T, bool kSE, bool kPacked, bool kStream>
+cudaError_t launch_t(const StepArgs &a, int n_tiles, int k, size_t smem, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(n_tiles));
+    cfg.blockDim = dim3(T);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_step_staged<T, kSE, kPacked, kStream>, a, k);
+}
+
+// The kernel instance of a shape and edge format: launch it (smem > 0 with a
+// launch) or raise its dynamic shared-memory limit (launch false).
+template <int T, bool kSE>
+cudaError_t dispatch_fmt(bool launch, const StepArgs *a, int n_tiles, int k, bool packed, bool stream_edges,
+                         size_t smem, cudaStream_t s)
+{
+    if (launch) {
+        if (packed)
+            return stream_edges ? launch_t<T, kSE, true, true>(*a, n_tiles, k, smem, s)
+                                : launch_t<T, kSE, true, false>(*a, n_tiles, k, smem, s);
+        return stream_edges ? launch_t<T, kSE, false, true>(*a, n_tiles, k, smem, s)
+                            : launch_t<T, kSE, false, false>(*a, n_tiles, k, smem, s);
+    }
+    const int b = static_cast<int>(smem);
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if (packed)
+        return stream_edges ? cudaFuncSetAttribute(k_step_staged<T, kSE, true, true>, at, b)
+                            : cudaFuncSetAttribute(k_step_staged<T, kSE, true, false>, at, b);
+    return stream_edges ? cudaFuncSetAttribute(k_step_staged<T, kSE, false, true>, at, b)
+                        : cudaFuncSetAttribute(k_step_staged<T, kSE, false, false>, at, b);
+}
+
+cudaError_t dispatch(bool launch, const StagedShape &sh, const StepArgs *a, int n_tiles, int k, bool packed,
+                     bool stream_edges, size_t smem, cudaStream_t s)
+{
+    const bool se = sh.stage_entries != 0;
+    switch (sh.threads) {
+        case 128:
+            return se ? dispatch_fmt<128, true>(launch, a, n_tiles, k, packed, stream_edges, smem, s)
+                      : dispatch_fmt<128, false>(launch, a, n_tiles, k, packed, stream_edges, smem, s);
+        case 256:
+            return se ? dispatch_fmt<256, true>(launch, a, n_tiles, k, packed, stream_edges, smem, s)
+                      : dispatch_fmt<256, false>(launch, a, n_tiles, k, packed, stream_edges, smem, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+// {threads, gathers / edges / pieces per tile, stage entries}: shared memory per CTA
+// on a net of mean in-degree 50 about 41, 13, 81 and 26 KB
+const StagedShape kStagedShapes[kNumStagedShapes] = {
+    {128, 3072, 4096, 256, 1}, {128, 3072, 4096, 256, 0}, {256, 6144, 8192, 512, 1}, {256, 6144, 8192, 512, 0}};
+
+cudaError_t launch_step_staged(const StepArgs &a, int n_tiles, int k, const StagedShape &shape, bool packed,
+                               bool stream_edges, size_t smem_bytes, cudaStream_t s)
+{
+    if (n_tiles <= 0) return cudaSuccess;
+    return dispatch(true, shape, &a, n_tiles, k, packed, stream_edges, smem_bytes, s);
+}
+
+cudaError_t step_staged_prepare(const StagedShape &shape, bool packed, bool stream_edges, size_t smem_bytes)
+{
+    return dispatch(false, shape, nullptr, 0, 0, packed, stream_edges, smem_bytes, nullptr);
+}
+
+}  // namespace gn

@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -41,8 +42,9 @@ struct gn_net {
     bool packed = true;
     bool stream_edges = true;
     int n_blocks = 0;
-    int step_kernel = 0;       // 0 not chosen yet (autotune), 1 row block per CTA, 2 persistent pipelined
-    int shape = 0;             // index into gn::kStepShapes (kernel 2 uses shape 0)
+    int step_kernel = 0;       // 0 not chosen yet (autotune), 1 row block per CTA, 2 persistent pipelined,
+                               // 3 staged tiles
+    int shape = 0;             // index into gn::kStepShapes (kernel 2 uses shape 0; kernel 3: gn::kStagedShapes)
     int grid = 0;              // CTAs per launch
     std::vector<int32_t> h_row_ptr;  // host copy, to cut row blocks for another shape
     int32_t stride = 0;        // ring slot stride (floats)
@@ -67,6 +69,34 @@ struct gn_net {
     std::vector<uint8_t> stage_pulses;
     cudaGraphExec_t graph = nullptr;
     bool graph_stale = true;
+    // staged layout (kernel 3), built from the host edge list, which is kept until
+    // the kernel is final
+    int st_shape = -1;
+    int n_tiles = 0;
+    size_t st_smem = 0;
+    int64_t st_gathers = 0, st_entries = 0;
+    int st_max_u = 0, st_max_x = 0, st_max_p = 0;
+    DevArray<int4> st_tile, st_tile2;
+    DevArray<uint32_t> st_ukey;
+    DevArray<int2> st_slice;
+    DevArray<float> st_w;
+    DevArray<uint16_t> st_u, st_plist;
+    DevArray<int32_t> st_rq;
+    std::unique_ptr<gnrt::HostNet> host;
+
+    void release_staged()
+    {
+        st_tile.release();
+        st_tile2.release();
+        st_ukey.release();
+        st_slice.release();
+        st_w.release();
+        st_u.release();
+        st_plist.release();
+        st_rq.release();
+        st_shape = -1;
+        n_tiles = 0;
+    }
 
     ~gn_net()
     {
@@ -79,6 +109,7 @@ struct gn_net {
         ev_count.release();
         bdesc.release();
         status.release();
+        release_staged();
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 };
@@ -98,16 +129,80 @@ void sync(gn_net *net)
     }
 }
 
-cudaError_t launch_kind(const gn::StepArgs &a, int kind, int shape, int grid, int k, bool packed, bool stream_edges,
-                        cudaStream_t s)
+// One step launch of the configured kernel with arguments `a` (the network's own,
+// or a scratch copy while autotuning).
+cudaError_t launch_kind(const gn::StepArgs &a, const gn_net *net, int k, cudaStream_t s)
 {
-    if (kind == 2) return gn::launch_step_pipe(a, grid, k, packed, stream_edges, s);
-    return gn::launch_step(a, a.n_blocks, k, shape, packed, stream_edges, s);
+    switch (net->step_kernel) {
+        case 2: return gn::launch_step_pipe(a, net->grid, k, net->packed, net->stream_edges, s);
+        case 3:
+            return gn::launch_step_staged(a, net->grid, k, gn::kStagedShapes[net->shape], net->packed,
+                                          net->stream_edges, net->st_smem, s);
+        default: return gn::launch_step(a, a.n_blocks, k, net->shape, net->packed, net->stream_edges, s);
+    }
 }
 
-cudaError_t launch_one(const gn_net *net, int k, cudaStream_t s)
+cudaError_t launch_one(const gn_net *net, int k, cudaStream_t s) { return launch_kind(net->args, net, k, s); }
+
+bool same_tiles(const gn::StagedShape &a, const gn::StagedShape &b)
 {
-    return launch_kind(net->args, net->step_kernel, net->shape, net->grid, k, net->packed, net->stream_edges, s);
+    return a.threads == b.threads && a.ucap == b.ucap && a.ecap == b.ecap && a.pcap == b.pcap;
+}
+
+// Build and upload the staged layout for a shape (shapes that cut the same tiles
+// share it); false if it cannot hold the network (a tile needs more shared memory
+// than a CTA may have).
+bool set_staged(gn_net *net, int shape)
+{
+    if (net->st_shape == shape) return true;
+    const gn::StagedShape sh = gn::kStagedShapes[shape];
+    if (net->st_shape < 0 || !same_tiles(gn::kStagedShapes[net->st_shape], sh)) {
+        if (!net->host) return false;
+        gnrt::StagedLayout L;
+        if (!gnrt::build_staged(*net->host, sh.threads, sh.ucap, sh.ecap, sh.pcap, L)) return false;
+        net->release_staged();
+        net->st_tile.upload(L.tile, &net->bytes);
+        net->st_tile2.upload(L.tile2, &net->bytes);
+        net->st_ukey.upload(L.ukey, &net->bytes);
+        net->st_slice.upload(L.slice, &net->bytes);
+        net->st_w.upload(L.w, &net->bytes);
+        net->st_u.upload(L.u, &net->bytes);
+        net->st_plist.upload(L.plist, &net->bytes);
+        net->st_rq.upload(L.rq, &net->bytes);
+        gn::StepArgs &a = net->args;
+        a.st_tile = net->st_tile.p;
+        a.st_tile2 = net->st_tile2.p;
+        a.st_ukey = net->st_ukey.p;
+        a.st_slice = net->st_slice.p;
+        a.st_w = net->st_w.p;
+        a.st_u = net->st_u.p;
+        a.st_rq = net->st_rq.p;
+        a.st_plist = net->st_plist.p;
+        a.st_ucap = L.max_u;
+        a.st_xcap = L.max_x;
+        net->st_max_u = L.max_u;
+        net->st_max_x = L.max_x;
+        net->st_max_p = L.max_p;
+        net->n_tiles = static_cast<int>(L.tile.size());
+        net->st_gathers = static_cast<int64_t>(L.ukey.size()) / (net->packed ? 1 : 2);
+        net->st_entries = static_cast<int64_t>(L.w.size());
+        if (net->E == 0) net->st_gathers = net->st_entries = 0;  // the placeholder entries of an empty layout
+        else {
+            int64_t g = 0;  // gathers without the alignment padding of each tile's key block
+            for (const int4 &t : L.tile) g += t.w;
+            net->st_gathers = g;
+        }
+    }
+    int max_smem = 0;
+    cuda_check(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, net->device), "device query");
+    const size_t smem = 16 + static_cast<size_t>(net->st_max_u) * (net->packed ? 4 : 12) +
+                        (sh.stage_entries ? static_cast<size_t>(net->st_max_x) * 6 : 0) +
+                        static_cast<size_t>(net->st_max_p) * 4;
+    if (smem > static_cast<size_t>(max_smem)) return false;
+    cuda_check(gn::step_staged_prepare(sh, net->packed, net->stream_edges, smem), "staged kernel setup");
+    net->st_smem = smem;
+    net->st_shape = shape;
+    return true;
 }
 
 // Cut the row blocks for a CTA shape and point the kernel arguments at them.
@@ -130,6 +225,16 @@ void set_blocks(gn_net *net, int shape)
 
 void configure(gn_net *net, int kind, int shape)
 {
+    if (kind == 3) {
+        if (!set_staged(net, shape))
+            fail(GN_EINVAL, "the staged step kernel cannot hold this network (a tile needs more shared memory "
+                            "than a CTA may have)");
+        net->step_kernel = 3;
+        net->shape = shape;
+        net->grid = net->n_tiles;
+        net->graph_stale = true;
+        return;
+    }
     if (kind == 2) shape = 0;
     set_blocks(net, shape);
     net->step_kernel = kind;
@@ -171,7 +276,8 @@ bool tune_cache_lookup(const std::string &key, int *kind, int *shape)
     int a = 0, b = 0;
     bool found = false;
     while (fscanf(f, "%255s %d %d", k, &a, &b) == 3)
-        if (key == k && (a == 1 || a == 2) && b >= 0 && b < gn::kNumStepShapes) {
+        if (key == k && b >= 0 &&
+            (((a == 1 || a == 2) && b < gn::kNumStepShapes) || (a == 3 && b < gn::kNumStagedShapes))) {
             *kind = a;
             *shape = b;
             found = true;
@@ -190,16 +296,17 @@ void tune_cache_store(const std::string &key, int kind, int shape)
     fclose(f);
 }
 
-// Autotuner: time every candidate (row-block kernel in each CTA shape, and the
-// persistent pipelined kernel) for a few steps on a scratch copy of the dynamic
+// Autotuner: time every candidate (row-block kernel in each CTA shape, the
+// persistent pipelined kernel and the staged kernel in each of its shapes) for a few steps on a scratch copy of the dynamic
 // state -- the network's own state is not touched -- and keep the fastest.  With
 // GN_AUTOTUNE_CACHE set, a cached choice for the same device and network sizes is
-// reused and new choices are appended.
+// reused and new choices are appended; with GN_AUTOTUNE_LOG set, every candidate's
+// time is appended to that file.
 void autotune(gn_net *net)
 {
     const std::string key = tune_key(net);
     int cached_kind = 0, cached_shape = 0;
-    if (tune_cache_lookup(key, &cached_kind, &cached_shape)) {
+    if (tune_cache_lookup(key, &cached_kind, &cached_shape) && (cached_kind != 3 || set_staged(net, cached_shape))) {
         configure(net, cached_kind, cached_shape);
         return;
     }
@@ -246,7 +353,9 @@ void autotune(gn_net *net)
         std::vector<Cand> cands;
         for (int sh = 0; sh < gn::kNumStepShapes; ++sh) cands.push_back({1, sh});
         cands.push_back({2, 0});
+        for (int sh = 0; sh < gn::kNumStagedShapes; ++sh) cands.push_back({3, sh});
         for (const Cand &c : cands) {
+            if (c.kind == 3 && !set_staged(net, c.shape)) continue;
             configure(net, c.kind, c.shape);
             gn::StepArgs a = net->args;
             a.ring = ring.p;
@@ -263,18 +372,20 @@ void autotune(gn_net *net)
             a.status = status.p;
             const int warm = 3, timed = 8;
             for (int k = 0; k < warm; ++k)
-                cuda_check(launch_kind(a, c.kind, net->shape, net->grid, k, net->packed, net->stream_edges,
-                                       net->stream),
-                           "autotune launch");
+                cuda_check(launch_kind(a, net, k, net->stream), "autotune launch");
             cuda_check(cudaEventRecord(t0, net->stream), "event");
             for (int k = 0; k < timed; ++k)
-                cuda_check(launch_kind(a, c.kind, net->shape, net->grid, k, net->packed, net->stream_edges,
-                                       net->stream),
-                           "autotune launch");
+                cuda_check(launch_kind(a, net, k, net->stream), "autotune launch");
             cuda_check(cudaEventRecord(t1, net->stream), "event");
             cuda_check(cudaEventSynchronize(t1), "autotune");
             float ms = 0.0f;
             cuda_check(cudaEventElapsedTime(&ms, t0, t1), "event");
+            if (const char *log = getenv("GN_AUTOTUNE_LOG")) {
+                if (FILE *f = fopen(log, "a")) {
+                    fprintf(f, "%s kind %d shape %d ms_per_step %.5f\n", key.c_str(), c.kind, c.shape, ms / timed);
+                    fclose(f);
+                }
+            }
             if (ms < best) {
                 best = ms;
                 best_kind = c.kind;
@@ -291,6 +402,13 @@ void autotune(gn_net *net)
     cleanup();
     configure(net, best_kind, best_shape);
     tune_cache_store(key, best_kind, best_shape);
+}
+
+// The kernel is final: drop the host edge list and any staged layout it does not use.
+void finalize_kernel(gn_net *net)
+{
+    if (net->step_kernel != 3) net->release_staged();
+    net->host.reset();
 }
 
 void build_graph(gn_net *net)
@@ -472,8 +590,21 @@ gn_status gn_net_create(const gn_net_desc *desc, gn_net **out)
         a.status = net->status.p;
 
         // the kernel is fixed now or timed on the first gn_step (kind 0)
-        configure(net, desc->step_kernel == 2 ? 2 : 1, 0);
-        if (desc->step_kernel == 0) net->step_kernel = 0;
+        if (desc->step_kernel == 0 || desc->step_kernel == 3) net->host = std::make_unique<gnrt::HostNet>(std::move(h));
+        // GN_STEP_SHAPE=i picks the CTA shape of an explicitly chosen kernel 1 or 3
+        int shape = 0;
+        if (const char *e = getenv("GN_STEP_SHAPE"); e && *e && (desc->step_kernel == 1 || desc->step_kernel == 3)) {
+            shape = atoi(e);
+            const int n_shapes = desc->step_kernel == 1 ? gn::kNumStepShapes : gn::kNumStagedShapes;
+            if (shape < 0 || shape >= n_shapes) fail(GN_EINVAL, "GN_STEP_SHAPE=%s is not a shape of kernel %d", e,
+                                                       desc->step_kernel);
+        }
+        configure(net, desc->step_kernel == 2 ? 2 : 1, desc->step_kernel == 1 ? shape : 0);
+        if (desc->step_kernel == 3) configure(net, 3, shape);
+        if (desc->step_kernel == 0)
+            net->step_kernel = 0;
+        else
+            finalize_kernel(net);
         cuda_check(cudaDeviceSynchronize(), "create");
     });
     if (st != GN_OK) {
@@ -507,16 +638,19 @@ gn_status gn_net_get_info(const gn_net *net, gn_net_info *info)
         info->min_delay = net->dmin;
         info->n_clamped = net->n_clamped;
         info->edge_format = net->packed ? 0 : 1;
-        info->n_blocks = net->n_blocks;
+        const bool staged = net->step_kernel == 3;
+        info->n_blocks = staged ? net->n_tiles : net->n_blocks;
         info->step_kernel = net->step_kernel;
-        info->step_threads = gn::kStepShapes[net->shape].threads;
-        info->step_edges_per_thread = gn::kStepShapes[net->shape].ept;
+        info->step_threads = staged ? gn::kStagedShapes[net->shape].threads : gn::kStepShapes[net->shape].threads;
+        info->step_edges_per_thread = staged ? gn::kWarpRow : gn::kStepShapes[net->shape].ept;
         info->grid = net->grid;
         info->step = net->step;
         info->samples = net->step / net->sample_every;
         info->v_rest = net->v_rest;
         info->w_rest = net->w_rest;
         info->device_bytes = net->bytes;
+        info->step_gathers = staged ? net->st_gathers : net->E;
+        info->step_entries = staged ? net->st_entries : net->E;
     });
 }
 
@@ -571,7 +705,10 @@ gn_status gn_step(gn_net *net, int64_t n_steps)
         if (n_steps < 0) fail(GN_EINVAL, "n_steps < 0");
         if (n_steps == 0) return;
         DeviceGuard dg(net->device);
-        if (net->step_kernel == 0) autotune(net);
+        if (net->step_kernel == 0) {
+            autotune(net);
+            finalize_kernel(net);
+        }
         if (net->graph_stale) build_graph(net);
         int64_t left = n_steps;
         while (left >= kGraphSteps) {

@@ -100,6 +100,47 @@ void host_build(const gn_net_desc *d, std::vector<int32_t> delay, int64_t n_clam
 void make_blocks(const std::vector<int32_t> &row_ptr, int32_t N, int cap, int max_rows, std::vector<int32_t> &blk,
                  std::vector<int4> &desc);
 
+// Staged layout of the by-target edge list (k_step_staged.cu).  Consecutive rows
+// form a tile of at most `threads` rows.  A tile lists the distinct (source, delay)
+// pairs its edges read -- its gathers -- sorted by (delay, source), so one CTA
+// fetches each history value once per step into shared memory.  Every row is cut
+// into pieces in the shared summation order (kWarpRow in internal.cuh): a row of at
+// most kWarpRow edges is one piece, a longer row 32 lane-strided pieces.  A tile's
+// pieces are sorted by length (longest first) and each lane of the CTA sums one
+// piece, reading its edges as (weight, index of the gather) column by column in
+// slices of 32 pieces.
+//
+// A tile's gather keys and its entries are contiguous and 16-byte aligned, so the
+// CTA copies them into shared memory with two or three bulk copies: keys start at
+// a multiple of 4 and are padded to a multiple of 4; entries come in slices of
+// 32 x length.
+struct StagedLayout {
+    int threads = 0;
+    std::vector<int4> tile;        // {first row, rows, first gather (multiple of 4), gathers}
+    std::vector<int4> tile2;       // {first slice, slices, first entry, entries}
+    std::vector<uint32_t> ukey;    // per gather: packed key, or {src, D} (wide)
+    std::vector<int2> slice;       // {first entry relative to the tile's, length}: entries k * 32 + lane
+    std::vector<float> w;          // entry weights (0 in the padding)
+    std::vector<uint16_t> u;       // entry gather index within the tile (0 in the padding)
+    std::vector<int32_t> rq;       // [N + 1] first piece-list entry of each row
+    std::vector<uint16_t> plist;   // lane slot (32 * slice + lane) of each piece, rows in order
+    int max_u = 0, max_x = 0, max_p = 0;  // largest padded gather count, entries, lane slots of a tile
+    // shared memory of one CTA: mbarrier, keys (wide keys need a separate value
+    // array; packed values overwrite their keys), entry weights and indices when
+    // they are staged, piece sums
+    size_t smem_bytes(bool packed, bool stage_entries = true) const
+    {
+        return 16 + static_cast<size_t>(max_u) * (packed ? 4 : 12) +
+               (stage_entries ? static_cast<size_t>(max_x) * 6 : 0) + static_cast<size_t>(max_p) * 4;
+    }
+};
+
+// Build the staged layout from the CSR of `h`: tiles close at `threads` rows,
+// `ucap` gathers, `ecap` edges or `pcap` pieces (a row that alone exceeds a cap
+// gets a tile of its own).  Returns false if a tile would need more than 65535
+// gathers or lane slots, or 2^31 entries in total.
+bool build_staged(const HostNet &h, int threads, int ucap, int ecap, int pcap, StagedLayout &out);
+
 // Scalar fields of the step arguments (FHN about the rest point, readout, sizes).
 void fill_step_params(const gn_net_desc *d, const HostNet &h, gn::StepArgs &a);
 

@@ -66,6 +66,7 @@ class gn_net_info(C.Structure):
         ("step_threads", C.c_int32), ("step_edges_per_thread", C.c_int32), ("grid", C.c_int32),
         ("step", C.c_int64), ("samples", C.c_int64),
         ("v_rest", C.c_double), ("w_rest", C.c_double), ("device_bytes", C.c_size_t),
+        ("step_gathers", C.c_int64), ("step_entries", C.c_int64),
     ]
 
 

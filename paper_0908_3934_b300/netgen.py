@@ -13,16 +13,22 @@ available, so these generators stand in for them.  The recipes:
                 one speed 0.1 m/s; +1.0 pulse on node 0 over [10, 12) ms.
 * ``large``     N = 100,000 uniform in a 1 mm cube; every ordered pair within the
                 radius that gives a mean in-degree of 100; w = lognormal(-2, 0.5)
-                with 20 % negated; speed U(0.05, 0.5) m/s per edge; 5 Hz
+                with 20 % negated, then the in-weights of a target with k > 20
+                inputs scaled by 20 / k; speed U(0.05, 0.5) m/s per edge; 5 Hz
                 background pulses (1.0, 2 ms).
 * ``roofline``  N = 1,000,000 in a 1 mm cube, mean in-degree 50: 2.5 % hub nodes
                 take in-edges from their 1000 nearest nodes, the rest take every
                 node within the radius giving the remaining mean (about 25.6);
-                weight, speed and background as ``large``; ring of 256 steps.
+                weight (with the same in-degree scaling), speed and background
+                as ``large``; ring of 256 steps.
 * ``batch``     many independent 2D nets, N log-uniform in [32, 4096]; pairs within
                 r = sqrt(40 / (pi N)) kept with p = 0.5 (mean kept in-degree about 20
                 away from the border); weight and speed as ``large``; 1-8 random
                 nodes get a 2 ms pulse with onset uniform in [5, 50) ms.
+  The in-degree scaling keeps a node's total input on the scale of the 20-input
+  nets the weight law comes from: unscaled, a hub summing 1000 inputs of mean
+  |w| 0.15 drives explicit Euler at dt = 0.05 ms past the cubic's stability
+  bound within tens of milliseconds and the run ends in NaN.
 * ``fig2``      the five-vertex network of Figs. 1-2 with the printed delays and
                 weights (delays are given explicitly, in steps of 0.05 ms).
 
@@ -136,6 +142,13 @@ def _radius_for_mean_degree(pos, mean_deg, n_probe=20000, seed=0):
     return 0.5 * (lo + hi)
 
 
+def _in_degree_scaled(w: np.ndarray, dst: np.ndarray, n: int, k0: float = 20.0) -> np.ndarray:
+    """w_e * min(1, k0 / k_dst(e)): targets with more than k0 inputs get their
+    in-weights scaled so their total input stays on the scale of a k0-input node."""
+    k = np.bincount(dst, minlength=n).astype(np.float64)
+    return (w * np.minimum(1.0, k0 / np.maximum(k[dst], 1.0))).astype(np.float32)
+
+
 def large(seed: int = 3, n: int = 100_000, mean_deg: float = 100.0, bg_rate_hz: float = 5.0,
           noise_seed: int = 5, dim: int = 3) -> NetSpec:
     rng = np.random.default_rng(seed)
@@ -144,7 +157,7 @@ def large(seed: int = 3, n: int = 100_000, mean_deg: float = 100.0, bg_rate_hz: 
     src, dst = _pairs_within(pos, r)
     src, dst = _sort_by_dst(src, dst)
     E = src.shape[0]
-    w = _signed_lognormal(rng, E)
+    w = _in_degree_scaled(_signed_lognormal(rng, E), dst, n)
     speed = rng.uniform(0.05, 0.5, E)
     obs = dict(OBS_DEFAULT, seed=noise_seed)
     bg = dict(rate_hz=bg_rate_hz, amp=1.0, dur_ms=2.0, seed=seed + 1000)
@@ -176,7 +189,7 @@ def roofline(seed: int = 4, n: int = 1_000_000, mean_deg: float = 50.0, hub_frac
     dst = np.concatenate([d1, d2])
     src, dst = _sort_by_dst(src, dst)
     E = src.shape[0]
-    w = _signed_lognormal(rng, E)
+    w = _in_degree_scaled(_signed_lognormal(rng, E), dst, n)
     speed = rng.uniform(0.05, 0.5, E)
     obs = dict(OBS_DEFAULT, seed=noise_seed)
     bg = dict(rate_hz=bg_rate_hz, amp=1.0, dur_ms=2.0, seed=seed + 1000)
