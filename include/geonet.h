@@ -329,7 +329,9 @@ GN_API gn_status gn_batch_export_traces(gn_batch *batch, int64_t first_sample, i
  * is the Pearson correlation of y_i(t) and y_j(t + l0 + k) over their overlap, each
  * segment about its own mean (0 if one is constant); feature 32 is d / r_c.
  * features [n_pairs][33]; score [n_pairs] = max of features 0..31 (the plain
- * peak-correlation estimator).  Runs on `cuda_stream` (may be NULL). */
+ * peak-correlation estimator).  Runs on `cuda_stream` (may be NULL); takes stream-
+ * ordered scratch of about 3 x the traces (centred traces and their prefix sums),
+ * GN_ECUDA if it cannot be allocated. */
 GN_API gn_status gn_xcorr_features(const float *traces, int64_t n_nodes, int32_t n_samples, const double *pos,
                                    int32_t dim, int64_t n_pairs, const int32_t *src, const int32_t *dst,
                                    const double *radius, double v_max, double sample_ms, float *features,

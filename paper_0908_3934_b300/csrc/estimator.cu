@@ -35,12 +35,12 @@ gn_status gn_xcorr_features(const float *traces, int64_t n_nodes, int32_t n_samp
         if (n_pairs > 0 && (!traces || !pos || !src || !dst || !radius || !features || !score))
             fail(GN_EINVAL, "a device pointer is NULL");
         cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-        float *mean = nullptr;
-        cuda_check(cudaMallocAsync(reinterpret_cast<void **>(&mean), std::max<int64_t>(1, n_nodes) * sizeof(float), s),
-                   "cudaMallocAsync");
-        cudaError_t e = gn::launch_ncc(traces, n_nodes, n_samples, mean, pos, dim, n_pairs, src, dst, radius, v_max,
+        float *scratch = nullptr;
+        const int64_t nf = std::max<int64_t>(1, gn::ncc_scratch_floats(n_nodes, n_samples));
+        cuda_check(cudaMallocAsync(reinterpret_cast<void **>(&scratch), nf * sizeof(float), s), "cudaMallocAsync");
+        cudaError_t e = gn::launch_ncc(traces, n_nodes, n_samples, scratch, pos, dim, n_pairs, src, dst, radius, v_max,
                                        sample_ms, features, score, s);
-        cudaFreeAsync(mean, s);
+        cudaFreeAsync(scratch, s);
         cuda_check(e, "correlation kernel");
     });
 }

@@ -76,7 +76,10 @@ struct StepArgs {
     const uint16_t *st_plist;  // lane slot of each piece
     int32_t st_ucap;         // gather slots of a CTA's shared memory (largest padded gather count)
     int32_t st_xcap;         // entry slots of a CTA's shared memory (largest entry count)
+    uint32_t wait_limit;     // polls of a bounded mbarrier wait before it reports kStatusTimeout
 };
+
+constexpr uint32_t kDefaultWaitLimit = 1u << 22;
 
 constexpr unsigned int kStatusTimeout = 1u;  // a bounded mbarrier wait gave up
 
@@ -144,9 +147,11 @@ struct ExportNet {
 };
 cudaError_t launch_export_traces(const float *obs_pool, const ExportNet *nets, int n_nets, int max_nodes,
                                  int64_t first, int T, int64_t cap, float *out, cudaStream_t s);
-cudaError_t launch_ncc(const float *X, int64_t M, int T, float *mean_scratch, const double *pos, int dim, int64_t P,
+// scratch: ncc_scratch_floats(M, T) floats (centred traces and their prefix sums)
+cudaError_t launch_ncc(const float *X, int64_t M, int T, float *scratch, const double *pos, int dim, int64_t P,
                        const int *src, const int *dst, const double *radius, double v_max, double sample_ms,
                        float *feat, float *score, cudaStream_t s);
+int64_t ncc_scratch_floats(int64_t M, int T);
 
 // MLP of the learned estimator (k_mlp.cu); hidden width 256, inputs padded to 64
 constexpr int kMlpHidden = 256;

@@ -33,15 +33,19 @@ namespace {
 
 using namespace step;
 
-constexpr uint32_t kWaitLimit = 1u << 22;
 
 __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// threads per SM the register allocation must allow, with and without entry
+// staging (measured on the 1M-node net: 1536 threads at 40 registers beat 1280 at
+// 48 and 2048 at 32, which spills)
+constexpr int kThreadsSE = 1024;
+constexpr int kThreadsL2 = 1536;
+
 template <int T, bool kSE, bool kPacked, bool kStream>
-__global__ void __launch_bounds__(T, (kSE ? 1024 : 1536) / T) k_step_staged(const StepArgs a, const int k)
+__global__ void __launch_bounds__(T, (kSE ? kThreadsSE : kThreadsL2) / T) k_step_staged(const StepArgs a, const int k)
 {
-    constexpr int G = 8;  // gathers in flight per thread
     // [mbarrier 16 B][keys][values (wide keys only)][entry weights][entry indices][piece sums];
     // without entry staging (kSE false) the entry arrays are absent
     extern __shared__ __align__(128) unsigned char s_raw[];
@@ -77,8 +81,9 @@ __global__ void __launch_bounds__(T, (kSE ? 1024 : 1536) / T) k_step_staged(cons
             }
         }
         if (!kSE && nx) {
-            bulk_prefetch_l2(a.st_w + td2.z, static_cast<uint32_t>(nx) * 4u);
-            bulk_prefetch_l2(a.st_u + td2.z, static_cast<uint32_t>(nx) * 2u);
+            const uint64_t pol = kStream ? l2_evict_first() : l2_evict_last();
+            bulk_prefetch_l2(a.st_w + td2.z, static_cast<uint32_t>(nx) * 4u, pol);
+            bulk_prefetch_l2(a.st_u + td2.z, static_cast<uint32_t>(nx) * 2u, pol);
         }
     }
     const int r = td.x + t;
@@ -103,41 +108,36 @@ __global__ void __launch_bounds__(T, (kSE ? 1024 : 1536) / T) k_step_staged(cons
         wc = a.wc[r];
         if (a.bg_thr) cnt0 = a.bgc[r];
     }
-    if (t == 0 && bytes && !mbar_wait_bounded(bar, 0, kWaitLimit)) {
+    if (t == 0 && bytes && !mbar_wait_bounded(bar, 0, a.wait_limit)) {
         atomicOr(a.status, kStatusTimeout);
         s_fail = 1;
-        mbar_wait_bounded(bar, 0, kWaitLimit);  // the copies must land before the CTA leaves
+        mbar_wait_bounded(bar, 0, kDefaultWaitLimit);  // the copies must land before the CTA leaves
     }
     __syncthreads();
     if (s_fail) return;
 
-    // 1. the tile's distinct history values (packed keys are overwritten in place)
+    // 1. the tile's distinct history values, copied asynchronously straight into
+    // shared memory (packed keys are overwritten in place: a thread reads key u
+    // before it issues the copy of value u); the live ring slots are kept in L2
+    // ahead of the streamed edge data
     const uint32_t dmask = (1u << a.dbits) - 1u;
-    for (int base = 0; base < nu; base += G * T) {
-        float val[G];
-#pragma unroll
-        for (int i = 0; i < G; ++i) {
-            const int u = base + t + i * T;
-            if (u < nu) {
-                uint32_t src, d;
-                if constexpr (kPacked) {
-                    const uint32_t kk = s_key[u];
-                    src = kk >> a.dbits;
-                    d = kk & dmask;
-                } else {
-                    const uint2 kk = reinterpret_cast<const uint2 *>(s_key)[u];
-                    src = kk.x;
-                    d = kk.y;
-                }
-                val[i] = gather(a, n, src, d);
-            }
+    const uint64_t pol_ring = l2_evict_last();
+#pragma unroll 4
+    for (int u = t; u < nu; u += T) {
+        uint32_t src, d;
+        if constexpr (kPacked) {
+            const uint32_t kk = s_key[u];
+            src = kk >> a.dbits;
+            d = kk & dmask;
+        } else {
+            const uint2 kk = reinterpret_cast<const uint2 *>(s_key)[u];
+            src = kk.x;
+            d = kk.y;
         }
-#pragma unroll
-        for (int i = 0; i < G; ++i) {
-            const int u = base + t + i * T;
-            if (u < nu) s_val[u] = val[i];
-        }
+        const int64_t slot = (n - static_cast<int64_t>(d)) & a.ring_mask;
+        cp_async4_hint(s_val + u, a.ring + slot * a.ring_stride + src, pol_ring);
     }
+    cp_async_wait_all();
     __syncthreads();
 
     // 2. one piece per lane, 32 pieces per warp at a time

@@ -70,11 +70,23 @@ __device__ __forceinline__ void bulk_g2s_hint(void *dst, const void *src, uint32
         : "memory");
 }
 
-// Bulk prefetch of [src, src + bytes) into L2 (no completion to wait for).
-// src 16-byte aligned; bytes a multiple of 16.
-__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes)
+// 4-byte asynchronous copy global -> shared (no register staging) with an L2 cache
+// policy; completes at cp_async_wait_all.
+__device__ __forceinline__ void cp_async4_hint(void *dst, const void *src, uint64_t policy)
 {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+    asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src),
+                 "l"(policy)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Bulk prefetch of [src, src + bytes) into L2 with a cache policy (no completion
+// to wait for).  src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes, uint64_t policy)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], %1, %2;" ::"l"(src), "r"(bytes), "l"(policy)
+                 : "memory");
 }
 
 __device__ __forceinline__ uint64_t l2_evict_first()

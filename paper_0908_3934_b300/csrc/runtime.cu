@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <numeric>
 
 #include "runtime.h"
@@ -371,6 +372,11 @@ void fill_step_params(const gn_net_desc *d, const HostNet &h, gn::StepArgs &a)
     a.N = h.N;
     a.ring_stride = h.stride;
     a.ring_mask = h.R - 1;
+    // GN_TEST_WAIT_LIMIT=k makes the staged kernel's first copy wait give up after k
+    // polls: a test of the timeout path that needs no fault (the kernel still waits
+    // the full bound for its copies before it leaves)
+    a.wait_limit = gn::kDefaultWaitLimit;
+    if (const char *e = getenv("GN_TEST_WAIT_LIMIT"); e && *e) a.wait_limit = static_cast<uint32_t>(strtoul(e, nullptr, 10));
     a.dbits = h.dbits;
     a.packed = h.packed ? 1 : 0;
     a.n_blocks = h.n_blocks();

@@ -29,16 +29,20 @@ struct DeviceGuard {
     ~DeviceGuard();
 };
 
+// A device allocation that keeps the owner's byte count (`total`) current: alloc
+// adds its size, release subtracts it.
 template <class T>
 struct DevArray {
     T *p = nullptr;
     size_t n = 0;
+    size_t *counted = nullptr;
     void alloc(size_t count, size_t *total)
     {
         n = count;
         if (count == 0) return;
         cuda_check(cudaMalloc(reinterpret_cast<void **>(&p), count * sizeof(T)), "cudaMalloc");
         *total += count * sizeof(T);
+        counted = total;
     }
     void upload(const std::vector<T> &v, size_t *total)
     {
@@ -47,9 +51,13 @@ struct DevArray {
     }
     void release()
     {
-        if (p) cudaFree(p);
+        if (p) {
+            cudaFree(p);
+            if (counted) *counted -= n * sizeof(T);
+        }
         p = nullptr;
         n = 0;
+        counted = nullptr;
     }
 };
 

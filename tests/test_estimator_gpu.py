@@ -39,10 +39,15 @@ def _seeded_traces(seed, n_nodes=300, T=500):
     return Y.astype(np.float32), pos, src[keep], dst[keep]
 
 
-def test_features_match_the_oracle():
+@pytest.mark.parametrize("T", [500, 499, 37])
+def test_features_match_the_oracle(T):
+    """Every lag feature and the plain score within 1e-5 of the FP64 oracle; T = 500
+    takes the four-sample path, 499 its ragged tail, 37 leaves the longest lags with
+    fewer than two samples (feature 0)."""
     torch = _torch()
     from paper_0908_3934_b300 import geonet
     Y, pos, src, dst = _seeded_traces(1)
+    Y = np.ascontiguousarray(Y[:T])
     r = 0.35
     F, S = est.ncc_features(Y.astype(np.float64), pos, src, dst, r)
     dev = torch.device("cuda")

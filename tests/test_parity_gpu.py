@@ -231,6 +231,29 @@ def test_staged_kernel_refuses_a_row_beyond_shared_memory():
     assert net.gn_net_get_info()["step_kernel"] in (1, 2)
 
 
+def test_a_copy_wait_that_gives_up_reports_a_timeout(monkeypatch):
+    """The staged kernel's bounded wait for its bulk copies: with the poll budget set
+    to zero the first wait gives up, the CTA records kStatusTimeout, waits the full
+    bound for its copies and leaves its rows untouched; the host reports
+    GN_ETIMEOUT at the next synchronising call and the context stays usable."""
+    spec = netgen.large(n=3000, mean_deg=20)
+    monkeypatch.setenv("GN_TEST_WAIT_LIMIT", "0")
+    net = Net(spec, step_kernel=3)
+    net.gn_step(3)
+    with pytest.raises(geonet.GeonetError) as e:
+        net.gn_synchronize()
+    assert e.value.status == geonet.GN_ETIMEOUT
+    st = net.gn_get_state()  # the status word was cleared; no row was updated
+    assert not st["v"].any() and not st["w"].any()
+    monkeypatch.delenv("GN_TEST_WAIT_LIMIT")
+    ok = Net(spec, step_kernel=3)
+    ok.gn_step(40)
+    ok.gn_synchronize()
+    ref = Net(spec, step_kernel=1)
+    ref.gn_step(40)
+    assert np.array_equal(ok.gn_get_state()["v"], ref.gn_get_state()["v"])
+
+
 def test_no_edges_and_one_node():
     for n in (1, 37):
         spec = netgen.NetSpec(pos=np.zeros((n, 3)), src=np.zeros(0, np.int32), dst=np.zeros(0, np.int32),
