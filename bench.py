@@ -98,10 +98,10 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_per_launch(workload_name: str):
+def traffic_per_launch(kernel: str, workload_name: str):
     """DRAM bytes per launch of the step kernel from the committed ncu summary,
     if it was taken on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", f"k_step_{workload_name}.json")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload_name}.json")
     try:
         with open(path) as f:
             p = json.load(f)
@@ -439,7 +439,7 @@ def main():
         "node_steps_per_s": (value / E_total) * N * world, "rtf": spec.dt_ms * 1e-3 / step_s,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_kind,
-                     "traffic": traffic_per_launch(args.workload),
+                     "traffic": traffic_per_launch(KERNEL_NAMES[info["step_kernel"]], args.workload),
                      "algorithmic_bytes_per_launch": bytes_step,
                      "kernel": KERNEL_NAMES[info["step_kernel"]]},
         "e2e": {"value": e2e_value, "unit": METRIC,
