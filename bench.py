@@ -257,7 +257,9 @@ def run_batched(args, local, stream, rank):
                         f"{N} nodes, {E} edges, {steps} steps ({steps * 0.05:.0f} ms)",
             "value": E * steps / t, "unit": METRIC, "seconds": t, "ms_per_step": t / steps * 1e3,
             "rtf": steps * 0.05e-3 / t, "cta_threads": info["cta_threads"], "grid": info["grid"],
-            "gpu_launches": 1,
+            "step_kernel": info["step_kernel"],
+            # kernel 1: one persistent launch; kernel 3: one per step + one advance per 64-step graph
+            "gpu_launches": 1 if info["step_kernel"] == 1 else steps + (steps + 63) // 64,
             "loop_plain": {"value": E * steps / t_loop, "seconds_extrapolated": t_loop,
                            "sample": f"{len(pick)} random nets timed one after another, "
                                      f"{t_sample:.3f} s, extrapolated by count to {len(specs)}"},

@@ -247,8 +247,10 @@ typedef struct {
     int64_t n_edges;
     int64_t step;                /* common step counter */
     int32_t cta_threads;         /* chosen CTA size (0 before the first step) */
-    int32_t grid;                /* persistent CTAs */
+    int32_t grid;                /* CTAs per launch: persistent CTAs (kernel 1) or tiles (kernel 3) */
     size_t device_bytes;
+    int32_t step_kernel;         /* 1: persistent k_batch, one launch per gn_batch_step; 3: staged tiles of
+                                    every member, one launch per step; 0 before the first step */
 } gn_batch_info;
 
 /* Copy and build n_nets networks on one device (descs[i].device must agree; the
@@ -266,7 +268,11 @@ GN_API gn_status gn_batch_set_stimulus_all(gn_batch *batch, const gn_pulse *puls
 GN_API gn_status gn_batch_set_background(gn_batch *batch, int32_t net, double rate_hz, float amp, double dur_ms,
                                          uint64_t seed);
 
-/* Advance every network n_steps (one persistent launch; asynchronous). */
+/* Advance every network n_steps (asynchronous): one persistent launch (kernel 1)
+ * or one launch per step replayed from a captured graph (kernel 3), whichever the
+ * first call measured faster; GN_BATCH_KERNEL=1 or 3 in the environment restricts
+ * the choice.  Both sum a node's inputs in the order of the single-network kernels,
+ * so results are bit-identical either way. */
 GN_API gn_status gn_batch_step(gn_batch *batch, int64_t n_steps);
 GN_API gn_status gn_batch_synchronize(gn_batch *batch);
 

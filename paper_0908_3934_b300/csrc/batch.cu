@@ -5,11 +5,19 @@
 // gn_batch_create builds every network exactly as gn_net_create does (one FP64
 // delay launch for the whole batch, Morton renumbering and the by-target edge list
 // per network), then concatenates their arrays into pools; each network's step
-// arguments point into the pools.  The work queue is ordered largest first.  The
-// CTA size of k_batch is picked on the first gn_batch_step by timing the
-// candidates on a scratch copy of the dynamic state.
+// arguments point into the pools.  The work queue is ordered largest first.
+//
+// Two kernels step a batch: the persistent k_batch (CTAs take whole networks off
+// the queue and run every step of them) and the staged form (each member's staged
+// layout -- see build_staged -- pooled, one launch per step over every member's
+// tiles, steps chained with programmatic dependent launch and replayed from a
+// graph).  Both sum a node's inputs in the order every step kernel uses, so the
+// choice never changes a result.  The first gn_batch_step picks the kernel (and
+// k_batch's CTA size) by timing the candidates on a scratch copy of the dynamic
+// state; GN_BATCH_KERNEL=1 or 3 restricts the choice to k_batch or the staged form.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <string>
@@ -24,6 +32,9 @@ using gnrt::fail;
 using gnrt::guarded;
 
 namespace {
+
+constexpr int kGraphSteps = 64;             // staged form: steps per captured graph
+constexpr int kStaged = gn::kNumBatchShapes;  // shape index of the staged form
 
 // Host view of one member network.
 struct Member {
@@ -67,6 +78,16 @@ struct gn_batch {
     DevArray<gn::StepArgs> d_args;
     cudaGraphExec_t graph = nullptr;
     int64_t graph_steps = 0;
+    // staged form: pooled layouts of every member (tile_net: member of each tile)
+    bool staged_ok = false, st_packed = true, st_stream = false;
+    int n_tiles = 0;
+    size_t st_smem = 0;
+    DevArray<int4> st_tile, st_tile2;
+    DevArray<uint32_t> st_ukey;
+    DevArray<int2> st_slice;
+    DevArray<float> st_w;
+    DevArray<uint16_t> st_u, st_plist;
+    DevArray<int32_t> st_rq, st_tile_net;
 
     ~gn_batch()
     {
@@ -80,6 +101,15 @@ struct gn_batch {
         status.release();
         for (auto &a : bdesc) a.release();
         d_args.release();
+        st_tile.release();
+        st_tile2.release();
+        st_ukey.release();
+        st_slice.release();
+        st_w.release();
+        st_u.release();
+        st_plist.release();
+        st_rq.release();
+        st_tile_net.release();
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 };
@@ -122,6 +152,17 @@ void upload_args(gn_batch *b, int shape)
 
 void set_shape(gn_batch *b, int shape)
 {
+    if (shape == kStaged) {
+        cuda_check(gn::batch_staged_prepare(b->st_packed, b->st_stream, b->st_smem), "staged kernel setup");
+        b->shape = kStaged;
+        b->grid = b->n_tiles;
+        upload_args(b, 0);
+        if (b->graph) {
+            cudaGraphExecDestroy(b->graph);
+            b->graph = nullptr;
+        }
+        return;
+    }
     int per_sm = 0, sms = 0;
     cuda_check(gn::batch_occupancy(shape, &per_sm), "occupancy");
     cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device), "device query");
@@ -138,13 +179,21 @@ void set_shape(gn_batch *b, int shape)
 void launch_steps(gn_batch *b, const gn::StepArgs *args, int64_t *d_step, int n_steps, int shape, int grid,
                   cudaStream_t s)
 {
+    if (shape == kStaged) {
+        for (int k = 0; k < n_steps; ++k)
+            cuda_check(gn::launch_batch_staged(args, b->st_tile_net.p, b->n_tiles, k, b->st_packed, b->st_stream,
+                                               b->st_smem, s),
+                       "staged batch launch");
+        return;
+    }
     cuda_check(cudaMemsetAsync(b->queue.p, 0, 4, s), "queue reset");
     cuda_check(gn::launch_batch(args, b->d_order.p, b->n_nets, b->queue.p, d_step, n_steps, shape, grid, s),
                "batch launch");
 }
 
-// Time each CTA shape for a few steps on a scratch copy of the dynamic state.
-void autotune(gn_batch *b)
+// Time each candidate (k_batch in each CTA shape, the staged form) for a few steps
+// on a scratch copy of the dynamic state.
+void autotune(gn_batch *b, bool persistent, bool staged)
 {
     size_t tmp = 0;
     DevArray<float> ring, obs;
@@ -183,8 +232,10 @@ void autotune(gn_batch *b)
         cuda_check(cudaEventCreate(&t0), "event");
         cuda_check(cudaEventCreate(&t1), "event");
         float best_ms = 1e30f;
-        for (int shape = 0; shape < gn::kNumBatchShapes; ++shape) {
-            std::vector<gn::StepArgs> a = args_for_shape(b, shape);
+        best = persistent ? 0 : kStaged;
+        for (int shape = 0; shape <= kStaged; ++shape) {
+            if (shape == kStaged ? !(staged && b->staged_ok) : !persistent) continue;
+            std::vector<gn::StepArgs> a = args_for_shape(b, shape == kStaged ? 0 : shape);
             for (int i = 0; i < b->n_nets; ++i) {
                 const Member &mm = b->m[i];
                 a[i].ring = ring.p + mm.ring_off;
@@ -199,10 +250,15 @@ void autotune(gn_batch *b)
                 a[i].ev_cap = 1;
             }
             cuda_check(cudaMemcpy(dargs.p, a.data(), a.size() * sizeof(gn::StepArgs), cudaMemcpyHostToDevice), "H2D");
-            int per_sm = 0, sms = 0;
-            cuda_check(gn::batch_occupancy(shape, &per_sm), "occupancy");
-            cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device), "device query");
-            const int grid = std::max(1, std::min(b->n_nets, per_sm * sms));
+            int grid = b->n_tiles;
+            if (shape == kStaged) {
+                cuda_check(gn::batch_staged_prepare(b->st_packed, b->st_stream, b->st_smem), "staged kernel setup");
+            } else {
+                int per_sm = 0, sms = 0;
+                cuda_check(gn::batch_occupancy(shape, &per_sm), "occupancy");
+                cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device), "device query");
+                grid = std::max(1, std::min(b->n_nets, per_sm * sms));
+            }
             launch_steps(b, dargs.p, dstep.p, 2, shape, grid, b->stream);
             cuda_check(cudaEventRecord(t0, b->stream), "event");
             launch_steps(b, dargs.p, dstep.p, 16, shape, grid, b->stream);
@@ -234,10 +290,16 @@ void build_graph(gn_batch *b, int64_t n_steps)
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        e = cudaMemsetAsync(b->queue.p, 0, 4, cs);
-        if (e == cudaSuccess)
-            e = gn::launch_batch(b->d_args.p, b->d_order.p, b->n_nets, b->queue.p, b->d_step.p,
-                                 static_cast<int>(n_steps), b->shape, b->grid, cs);
+        if (b->shape == kStaged) {
+            for (int k = 0; k < n_steps && e == cudaSuccess; ++k)
+                e = gn::launch_batch_staged(b->d_args.p, b->st_tile_net.p, b->n_tiles, k, b->st_packed, b->st_stream,
+                                            b->st_smem, cs);
+        } else {
+            e = cudaMemsetAsync(b->queue.p, 0, 4, cs);
+            if (e == cudaSuccess)
+                e = gn::launch_batch(b->d_args.p, b->d_order.p, b->n_nets, b->queue.p, b->d_step.p,
+                                     static_cast<int>(n_steps), b->shape, b->grid, cs);
+        }
         if (e == cudaSuccess) e = gn::launch_advance(b->d_step.p, n_steps, cs);
         cudaError_t e2 = cudaStreamEndCapture(cs, &g);
         if (e == cudaSuccess) e = e2;
@@ -247,6 +309,88 @@ void build_graph(gn_batch *b, int64_t n_steps)
     cudaStreamDestroy(cs);
     cuda_check(e, "graph capture of the batch step");
     b->graph_steps = n_steps;
+}
+
+// Staged layouts of every member, pooled: tile descriptors point into the pools,
+// each member's row piece lists keep member-local rows (its args point at its part
+// of st_rq).  Sets b->staged_ok (false if a member's layout does not fit or the
+// members mix edge formats) and returns each member's offset into st_rq.
+std::vector<int64_t> build_staged_pool(gn_batch *b, const std::vector<gnrt::HostNet> &hs)
+{
+    const int n = static_cast<int>(hs.size());
+    std::vector<int64_t> rq_off(n, 0);
+    b->staged_ok = true;
+    b->st_packed = hs[0].packed;
+    for (const gnrt::HostNet &h : hs) b->staged_ok = b->staged_ok && h.packed == b->st_packed;
+    if (!b->staged_ok) return rq_off;
+    const gn::StagedShape sh = gn::kBatchStagedShape;
+    const int kw = b->st_packed ? 1 : 2;
+    std::vector<int4> tile, tile2;
+    std::vector<uint32_t> ukey;
+    std::vector<int2> slice;
+    std::vector<float> w;
+    std::vector<uint16_t> u, plist;
+    std::vector<int32_t> rq, tile_net;
+    int max_u = 0, max_x = 0, max_p = 0;
+    for (int i = 0; i < n; ++i) {
+        gnrt::StagedLayout L;
+        if (!gnrt::build_staged(hs[i], sh.threads, sh.ucap, sh.ecap, sh.pcap, L)) {
+            b->staged_ok = false;
+            return rq_off;
+        }
+        while (w.size() % 32) {  // tile entry blocks stay 128-byte aligned
+            w.push_back(0.0f);
+            u.push_back(0);
+        }
+        const int64_t u_off = static_cast<int64_t>(ukey.size()) / kw, s_off = static_cast<int64_t>(slice.size());
+        const int64_t x_off = static_cast<int64_t>(w.size()), q_off = static_cast<int64_t>(plist.size());
+        if (x_off + static_cast<int64_t>(L.w.size()) >= (1ll << 31) || u_off + static_cast<int64_t>(L.ukey.size()) >= (1ll << 31)) {
+            b->staged_ok = false;
+            return rq_off;
+        }
+        for (size_t t = 0; t < L.tile.size(); ++t) {
+            int4 a = L.tile[t], c = L.tile2[t];
+            a.z += static_cast<int>(u_off);
+            c.x += static_cast<int>(s_off);
+            c.z += static_cast<int>(x_off);
+            tile.push_back(a);
+            tile2.push_back(c);
+            tile_net.push_back(i);
+        }
+        ukey.insert(ukey.end(), L.ukey.begin(), L.ukey.end());
+        slice.insert(slice.end(), L.slice.begin(), L.slice.end());
+        w.insert(w.end(), L.w.begin(), L.w.end());
+        u.insert(u.end(), L.u.begin(), L.u.end());
+        plist.insert(plist.end(), L.plist.begin(), L.plist.end());
+        rq_off[i] = static_cast<int64_t>(rq.size());
+        for (int32_t q : L.rq) rq.push_back(static_cast<int32_t>(q + q_off));
+        max_u = std::max(max_u, L.max_u);
+        max_x = std::max(max_x, L.max_x);
+        max_p = std::max(max_p, L.max_p);
+    }
+    int max_smem = 0;
+    cuda_check(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device), "device query");
+    b->st_smem = 16 + static_cast<size_t>(max_u) * (b->st_packed ? 4 : 12) + static_cast<size_t>(max_p) * 4;
+    if (b->st_smem > static_cast<size_t>(max_smem)) {
+        b->staged_ok = false;
+        return rq_off;
+    }
+    b->st_stream = static_cast<double>(w.size()) * 6.0 + static_cast<double>(ukey.size()) * 4.0 > 48e6;
+    b->n_tiles = static_cast<int>(tile.size());
+    b->st_tile.upload(tile, &b->bytes);
+    b->st_tile2.upload(tile2, &b->bytes);
+    b->st_ukey.upload(ukey, &b->bytes);
+    b->st_slice.upload(slice, &b->bytes);
+    b->st_w.upload(w, &b->bytes);
+    b->st_u.upload(u, &b->bytes);
+    b->st_plist.upload(plist, &b->bytes);
+    b->st_rq.upload(rq, &b->bytes);
+    b->st_tile_net.upload(tile_net, &b->bytes);
+    for (int i = 0; i < n; ++i) {
+        b->args[i].st_ucap = max_u;
+        b->args[i].st_xcap = max_x;
+    }
+    return rq_off;
 }
 
 template <class T>
@@ -368,6 +512,7 @@ gn_status gn_batch_create(const gn_net_desc *descs, int32_t n_nets, gn_batch **o
                                "H2D");
         }
         for (int s = 0; s < gn::kNumBatchShapes; ++s) b->bdesc[s].upload(shape_desc[s], &b->bytes);
+        std::vector<int64_t> rq_off = build_staged_pool(b, hs);
         hs.clear();
         b->ring.alloc(ring, &b->bytes);
         b->wc.alloc(nodes + 2 * static_cast<int64_t>(n_nets), &b->bytes);
@@ -417,6 +562,16 @@ gn_status gn_batch_create(const gn_net_desc *descs, int32_t n_nets, gn_batch **o
             a.ev_cap = mm.ev_cap;
             a.d_step = b->d_step.p;
             a.status = b->status.p;
+            if (b->staged_ok) {
+                a.st_tile = b->st_tile.p;
+                a.st_tile2 = b->st_tile2.p;
+                a.st_ukey = b->st_ukey.p;
+                a.st_slice = b->st_slice.p;
+                a.st_w = b->st_w.p;
+                a.st_u = b->st_u.p;
+                a.st_plist = b->st_plist.p;
+                a.st_rq = b->st_rq.p + rq_off[i];
+            }
         }
         // largest networks first
         b->order.resize(n_nets);
@@ -460,9 +615,12 @@ gn_status gn_batch_get_info(const gn_batch *b, gn_batch_info *info)
             info->n_edges += mm.E;
         }
         info->step = b->step;
-        info->cta_threads = b->shape >= 0 ? gn::kBatchThreads[b->shape] : 0;
+        info->cta_threads = b->shape == kStaged ? gn::kBatchStagedShape.threads
+                            : b->shape >= 0       ? gn::kBatchThreads[b->shape]
+                                                  : 0;
         info->grid = b->grid;
         info->device_bytes = b->bytes;
+        info->step_kernel = b->shape == kStaged ? 3 : b->shape >= 0 ? 1 : 0;
     });
 }
 
@@ -566,9 +724,26 @@ gn_status gn_batch_step(gn_batch *b, int64_t n_steps)
         if (n_steps < 0 || n_steps > 2147483647LL) fail(GN_EINVAL, "n_steps out of range");
         if (n_steps == 0) return;
         DeviceGuard dg(b->device);
-        if (b->shape < 0) autotune(b);
-        if (!b->graph || b->graph_steps != n_steps) build_graph(b, n_steps);
-        cuda_check(cudaGraphLaunch(b->graph, b->stream), "cudaGraphLaunch");
+        if (b->shape < 0) {
+            const char *e = getenv("GN_BATCH_KERNEL");
+            const int only = e && *e ? atoi(e) : 0;
+            if (only != 0 && only != 1 && only != 3) fail(GN_EINVAL, "GN_BATCH_KERNEL must be 1 or 3");
+            if (only == 3 && !b->staged_ok) fail(GN_EINVAL, "the staged batch kernel cannot hold this batch");
+            autotune(b, only != 3, only != 1);
+        }
+        if (b->shape == kStaged) {
+            if (!b->graph) build_graph(b, kGraphSteps);
+            int64_t left = n_steps;
+            for (; left >= kGraphSteps; left -= kGraphSteps)
+                cuda_check(cudaGraphLaunch(b->graph, b->stream), "cudaGraphLaunch");
+            if (left) {
+                launch_steps(b, b->d_args.p, b->d_step.p, static_cast<int>(left), kStaged, b->grid, b->stream);
+                cuda_check(gn::launch_advance(b->d_step.p, left, b->stream), "advance launch");
+            }
+        } else {
+            if (!b->graph || b->graph_steps != n_steps) build_graph(b, n_steps);
+            cuda_check(cudaGraphLaunch(b->graph, b->stream), "cudaGraphLaunch");
+        }
         b->step += n_steps;
     });
 }
@@ -586,7 +761,7 @@ gn_status gn_batch_step_static(gn_batch *b, int64_t n_steps)
         // the CTA size chosen by an earlier gn_batch_step, else the default one
         // (choosing it here would time candidates on newly allocated scratch state)
         int shape = b->shape, grid = b->grid;
-        if (shape < 0) {
+        if (shape < 0 || shape == kStaged) {
             int per_sm = 0, sms = 0;
             shape = 0;
             cuda_check(gn::batch_occupancy(shape, &per_sm), "occupancy");

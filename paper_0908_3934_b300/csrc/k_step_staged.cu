@@ -43,8 +43,9 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 constexpr int kThreadsSE = 1024;
 constexpr int kThreadsL2 = 1536;
 
+// One tile's step (the CTA's work) for network `a`; `tile` indexes a.st_tile.
 template <int T, bool kSE, bool kPacked, bool kStream>
-__global__ void __launch_bounds__(T, (kSE ? kThreadsSE : kThreadsL2) / T) k_step_staged(const StepArgs a, const int k)
+__device__ __forceinline__ void staged_tile(const StepArgs &a, const int tile, const int k)
 {
     // [mbarrier 16 B][keys][values (wide keys only)][entry weights][entry indices][piece sums];
     // without entry staging (kSE false) the entry arrays are absent
@@ -60,8 +61,8 @@ __global__ void __launch_bounds__(T, (kSE ? kThreadsSE : kThreadsL2) / T) k_step
 
     pdl_launch_dependents();
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int4 td = __ldg(a.st_tile + blockIdx.x);   // {r0, rows, u0, gathers}
-    const int4 td2 = __ldg(a.st_tile2 + blockIdx.x); // {s0, slices, x0, entries}
+    const int4 td = __ldg(a.st_tile + tile);   // {r0, rows, u0, gathers}
+    const int4 td2 = __ldg(a.st_tile2 + tile); // {s0, slices, x0, entries}
     const int nu = td.w, nx = td2.w;
     const uint32_t kbytes = static_cast<uint32_t>((nu + 3) & ~3) * (kPacked ? 4u : 8u);
     const uint32_t bytes = kbytes + (kSE ? static_cast<uint32_t>(nx) * 6u : 0u);
@@ -190,6 +191,27 @@ __global__ void __launch_bounds__(T, (kSE ? kThreadsSE : kThreadsL2) / T) k_step
 }
 
 template <int T, bool kSE, bool kPacked, bool kStream>
+__global__ void __launch_bounds__(T, (kSE ? kThreadsSE : kThreadsL2) / T) k_step_staged(const StepArgs a, const int k)
+{
+    staged_tile<T, kSE, kPacked, kStream>(a, blockIdx.x, k);
+}
+
+// Batched form, one launch per step over the tiles of every member network: the
+// CTA copies its network's arguments into shared memory, then runs the same tile
+// step (tiles never straddle networks).
+template <int T, bool kPacked, bool kStream>
+__global__ void __launch_bounds__(T, kThreadsL2 / T) k_batch_staged(const StepArgs *__restrict__ nets,
+                                                                    const int *__restrict__ tile_net, const int k)
+{
+    __shared__ StepArgs s_a;
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(nets + __ldg(tile_net + blockIdx.x));
+    uint32_t *dst = reinterpret_cast<uint32_t *>(&s_a);
+    for (int i = threadIdx.x; i < static_cast<int>(sizeof(StepArgs) / 4); i += T) dst[i] = __ldg(src + i);
+    __syncthreads();
+    staged_tile<T, false, kPacked, kStream>(s_a, blockIdx.x, k);
+}
+
+template <int T, bool kSE, bool kPacked, bool kStream>
 cudaError_t launch_t(const StepArgs &a, int n_tiles, int k, size_t smem, cudaStream_t s)
 {
     cudaLaunchConfig_t cfg = {};
@@ -259,6 +281,53 @@ cudaError_t launch_step_staged(const StepArgs &a, int n_tiles, int k, const Stag
 cudaError_t step_staged_prepare(const StagedShape &shape, bool packed, bool stream_edges, size_t smem_bytes)
 {
     return dispatch(false, shape, nullptr, 0, 0, packed, stream_edges, smem_bytes, nullptr);
+}
+
+namespace {
+
+template <bool kPacked, bool kStream>
+cudaError_t batch_staged_t(bool launch, const StepArgs *nets, const int *tile_net, int n_tiles, int k, size_t smem,
+                           cudaStream_t s)
+{
+    constexpr int T = kBatchStagedShape.threads;
+    if (!launch)
+        return cudaFuncSetAttribute(k_batch_staged<T, kPacked, kStream>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(smem));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(n_tiles));
+    cfg.blockDim = dim3(T);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_batch_staged<T, kPacked, kStream>, nets, tile_net, k);
+}
+
+cudaError_t batch_staged(bool launch, const StepArgs *nets, const int *tile_net, int n_tiles, int k, bool packed,
+                         bool stream_edges, size_t smem, cudaStream_t s)
+{
+    if (packed)
+        return stream_edges ? batch_staged_t<true, true>(launch, nets, tile_net, n_tiles, k, smem, s)
+                            : batch_staged_t<true, false>(launch, nets, tile_net, n_tiles, k, smem, s);
+    return stream_edges ? batch_staged_t<false, true>(launch, nets, tile_net, n_tiles, k, smem, s)
+                        : batch_staged_t<false, false>(launch, nets, tile_net, n_tiles, k, smem, s);
+}
+
+}  // namespace
+
+cudaError_t launch_batch_staged(const StepArgs *nets, const int *tile_net, int n_tiles, int k, bool packed,
+                                bool stream_edges, size_t smem_bytes, cudaStream_t s)
+{
+    if (n_tiles <= 0) return cudaSuccess;
+    return batch_staged(true, nets, tile_net, n_tiles, k, packed, stream_edges, smem_bytes, s);
+}
+
+cudaError_t batch_staged_prepare(bool packed, bool stream_edges, size_t smem_bytes)
+{
+    return batch_staged(false, nullptr, nullptr, 0, 0, packed, stream_edges, smem_bytes, nullptr);
 }
 
 }  // namespace gn

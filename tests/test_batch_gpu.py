@@ -1,5 +1,6 @@
-"""Batched form (gn_batch_*): many independent networks of uneven size in one
-persistent launch, checked against the single-network path and the FP64 oracle."""
+"""Batched form (gn_batch_*): many independent networks of uneven size stepped
+together -- by the persistent k_batch or by one staged launch per step over every
+member's tiles -- checked against the single-network path and the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -11,13 +12,21 @@ from parity import REL, ABS, ratio
 pytestmark = pytest.mark.gpu
 
 
+@pytest.fixture(params=[1, 3], ids=["persistent", "staged"], autouse=True)
+def batch_kernel(request, monkeypatch):
+    """Every test runs with each batch kernel (GN_BATCH_KERNEL)."""
+    monkeypatch.setenv("GN_BATCH_KERNEL", str(request.param))
+    return request.param
+
+
 def _specs(n, seed0=1000, n_hi=1500):
     return [netgen.batch_member(seed0 + i, n_hi=n_hi) for i in range(n)]
 
 
-def test_batch_equals_single_networks_bit_for_bit():
+def test_batch_equals_single_networks_bit_for_bit(batch_kernel):
     """A member of the batch follows exactly the trajectory of the same network run
-    alone (same per-row summation order and node update), over 2000 steps."""
+    alone (same per-row summation order and node update), over 2000 steps (1500 =
+    23 graphs of 64 steps and a ragged tail for the staged kernel)."""
     from paper_0908_3934_b300 import geonet
     specs = _specs(24)
     b = geonet.Batch(specs)
@@ -25,6 +34,7 @@ def test_batch_equals_single_networks_bit_for_bit():
     b.gn_batch_step(500)
     info = b.gn_batch_get_info()
     assert info["n_nets"] == 24 and info["step"] == 2000 and info["cta_threads"] in (128, 256, 512)
+    assert info["step_kernel"] == batch_kernel
     for i in range(0, 24, 3):
         net = geonet.Net(specs[i], step_kernel=1)
         net.gn_step(2000)
