@@ -164,8 +164,9 @@ constexpr int kMlpHidden = 256;
 constexpr int kMlpInPad = 64;
 cudaError_t mlp_prepare();
 cudaError_t mlp_launch_cast(const float *X, const int64_t *idx, int B, int in_dim, int Bp, void *Xb, cudaStream_t s);
+// Bp a multiple of 128, K of 64; *status gets kStatusTimeout if a bounded wait gave up
 cudaError_t mlp_launch_layer(int epi, const void *A, int Bp, int K, const void *Bt, const float *bias, const void *mask,
-                             void *out, float *col_partial, cudaStream_t s);
+                             void *out, float *col_partial, unsigned int *status, cudaStream_t s);
 cudaError_t mlp_launch_wgrad(const void *A, int Bp, int K, const void *G, int chunk, float *partial, cudaStream_t s);
 cudaError_t mlp_launch_head(const float *H2, const float *w3, const float *b3, const float *y, const int64_t *idx, int B,
                             int Bp, int rows_per_cta, float *p, void *dH2, float *partial, cudaStream_t s);

@@ -27,12 +27,6 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void *p)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_u32(p)));
-}
 __device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void *p)
 {
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
@@ -66,131 +60,173 @@ __global__ void k_cast_x(const float *__restrict__ X, const int64_t *__restrict_
 }
 
 // ---------------------------------------------------------------------------
-// C[m][n] = sum_k A[m][k] Bt[n][k] for a CTA tile of 64 rows x 256 columns,
-// K a multiple of 64 (A row-major [M][K], Bt row-major [256][K]); 8 warps as
-// 2 (rows) x 4 (columns), 32 x 64 per warp; K in chunks of 64, double buffered.
+// Layer GEMM C[m][n] = sum_k A[m][k] Bt[n][k] (A row-major [M][K] BF16, Bt row-major
+// [256][K] BF16, FP32 accumulation, K a multiple of 64) with a fused epilogue:
+// kReluBf16: BF16 relu(C + bias); kReluF32: FP32 relu(C + bias); kMaskBf16: BF16
+// C where mask > 0 (else 0), plus per-64-row column sums of that output.
 enum Epi { kReluBf16 = 0, kReluF32 = 1, kMaskBf16 = 2 };
 
+// ---------------------------------------------------------------------------
+// tcgen05 implementation: one CTA of 128 threads computes a 128-row x 128-column
+// tile (blockIdx.y picks the column half) with its FP32 accumulator in tensor memory.
+// K is staged in chunks of 64 (two buffers): the 128 threads copy A and B rows with
+// 16-byte cp.async into the K-major core-matrix layout (8 rows x 16 bytes per core
+// matrix, 128 bytes apart along K, 1024 bytes apart along rows -- thread c writes
+// bytes [16c, 16c + 16) of a buffer), one thread issues four 128 x 128 x 16 MMAs per
+// chunk and commits them to the chunk's mbarrier.  Epilogue: warp w reads TMEM lanes
+// 32w .. 32w + 31 (its rows) with tcgen05.ld, 32 columns at a time, and applies the
+// same bias / ReLU / mask and rounding as k_layer.  Column sums of the mask epilogue
+// go to col_partial[row / 64][col] in a fixed order (a reduce-scatter over the warp's
+// 32 rows, then the two warps of each 64-row group).  Every wait is bounded: on a
+// time-out the CTA sets *status, waits once more for its MMAs, frees its tensor
+// memory and leaves.
 template <int EPI>
-__global__ void __launch_bounds__(256) k_layer(const __nv_bfloat16 *__restrict__ A, int K,
-                                               const __nv_bfloat16 *__restrict__ Bt, const float *__restrict__ bias,
-                                               const __nv_bfloat16 *__restrict__ mask, void *__restrict__ out,
-                                               float *__restrict__ col_partial)
+__global__ void __launch_bounds__(128) k_layer_tc(const __nv_bfloat16 *__restrict__ A, int K,
+                                                  const __nv_bfloat16 *__restrict__ Bt,
+                                                  const float *__restrict__ bias,
+                                                  const __nv_bfloat16 *__restrict__ mask, void *__restrict__ out,
+                                                  float *__restrict__ col_partial, unsigned int *status)
 {
-    constexpr int BM = 64, BK = 64, LD = BK + kPad;
-    extern __shared__ __align__(16) uint8_t smem_raw[];
-    __nv_bfloat16 *sA = reinterpret_cast<__nv_bfloat16 *>(smem_raw);  // [2][BM][LD]
-    __nv_bfloat16 *sB = sA + 2 * BM * LD;                               // [2][256][LD]
+    constexpr int BM = 128, BN = 128, BK = 64;
+    constexpr int kStage = BM * BK * 2;  // bytes of one operand buffer (A and B alike)
+    constexpr uint32_t kIdesc = idesc_bf16_f32(BM, BN);
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *sA = smem_raw;                  // [2][kStage]
+    uint8_t *sB = smem_raw + 2 * kStage;     // [2][kStage]
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_fail;
+    __shared__ float s_cs[4][BN];
+
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int wm = warp >> 2, wn = warp & 3;
     const int64_t m0 = static_cast<int64_t>(blockIdx.x) * BM;
+    const int n0 = blockIdx.y * BN;
+    if (warp == 0) {
+        tmem_alloc(&s_tmem, BN);
+        tmem_relinquish();
+    }
+    if (t == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        fence_barrier_init();
+        s_fail = 0;
+    }
+    tc_fence_before_sync();
+    __syncthreads();
+    tc_fence_after_sync();
+    const uint32_t tmem = s_tmem;
 
     auto load = [&](int stage, int k0) {
-        __nv_bfloat16 *a = sA + stage * BM * LD;
-        __nv_bfloat16 *b = sB + stage * kH * LD;
-        for (int c = t; c < BM * BK / 8; c += 256) {
-            const int r = c / (BK / 8), k = (c % (BK / 8)) * 8;
-            cp_async16(a + r * LD + k, A + (m0 + r) * K + k0 + k);
-        }
-        for (int c = t; c < kH * BK / 8; c += 256) {
-            const int r = c / (BK / 8), k = (c % (BK / 8)) * 8;
-            cp_async16(b + r * LD + k, Bt + static_cast<int64_t>(r) * K + k0 + k);
+        uint8_t *a = sA + stage * kStage;
+        uint8_t *b = sB + stage * kStage;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int c = t + 128 * i;  // 16-byte piece: row (c & 7) + 8 (c >> 6), K piece (c >> 3) & 7
+            const int r = (c & 7) + 8 * (c >> 6), kp = (c >> 3) & 7;
+            cp_async16(a + 16 * c, A + (m0 + r) * K + k0 + kp * 8);
+            cp_async16(b + 16 * c, Bt + static_cast<int64_t>(n0 + r) * K + k0 + kp * 8);
         }
         cp_async_commit();
     };
 
-    float acc[2][8][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
-
     const int nk = K / BK;
+    bool ok = true;
     load(0, 0);
     for (int kc = 0; kc < nk; ++kc) {
         if (kc + 1 < nk) {
+            // buffer (kc + 1) & 1 was last read by the MMAs of chunk kc - 1
+            if (kc >= 1 && !mbar_wait_bounded(&s_bar[(kc - 1) & 1], ((kc - 1) >> 1) & 1, kDefaultWaitLimit)) ok = false;
             load((kc + 1) & 1, (kc + 1) * BK);
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
         }
+        fence_async_shared();
         __syncthreads();
-        const __nv_bfloat16 *a = sA + (kc & 1) * BM * LD;
-        const __nv_bfloat16 *b = sB + (kc & 1) * kH * LD;
+        if (t == 0) {
+            tc_fence_after_sync();
+            const uint8_t *a = sA + (kc & 1) * kStage;
+            const uint8_t *b = sB + (kc & 1) * kStage;
 #pragma unroll
-        for (int ks = 0; ks < BK / 16; ++ks) {
-            uint32_t af[2][4];
+            for (int ks = 0; ks < BK / 16; ++ks)
+                tc_mma_bf16(tmem, smem_desc_kmajor(a + ks * 256, 128, 1024), smem_desc_kmajor(b + ks * 256, 128, 1024),
+                            kIdesc, (kc | ks) != 0);
+            tc_commit(&s_bar[kc & 1]);
+        }
+    }
+    // the last chunk's commit covers every MMA of the tile
+    if (!mbar_wait_bounded(&s_bar[(nk - 1) & 1], ((nk - 1) >> 1) & 1, kDefaultWaitLimit)) ok = false;
+    if (!ok) {
+        s_fail = 1;
+        atomicOr(status, kStatusTimeout);
+        mbar_wait_bounded(&s_bar[(nk - 1) & 1], ((nk - 1) >> 1) & 1, kDefaultWaitLimit);
+    }
+    tc_fence_before_sync();
+    __syncthreads();
+    tc_fence_after_sync();
+
+    if (!s_fail) {
+        const int64_t row = m0 + 32 * warp + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+            uint32_t raw[32];
+            tmem_ld32(tmem + (static_cast<uint32_t>(32 * warp) << 16) + c0, raw);
+            tmem_ld_wait();
+            float v[32];
+            const int col0 = n0 + c0;
 #pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
-                ldsm_x4(af[mt], a + (wm * 32 + mt * 16 + (lane & 15)) * LD + ks * 16 + (lane >> 4) * 8);
+            for (int j = 0; j < 32; ++j) {
+                const float acc = __uint_as_float(raw[j]);
+                if constexpr (EPI == kMaskBf16)
+                    v[j] = __bfloat162float(mask[row * kH + col0 + j]) > 0.0f ? acc : 0.0f;
+                else
+                    v[j] = fmaxf(acc + bias[col0 + j], 0.0f);
+            }
+            if constexpr (EPI == kReluF32) {
+                float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(out) + row * kH + col0);
 #pragma unroll
-            for (int np = 0; np < 4; ++np) {
-                uint32_t bf[4];
-                ldsm_x4(bf, b + (wn * 64 + np * 16 + (lane & 7) + ((lane >> 4) << 3)) * LD + ks * 16 +
-                                ((lane >> 3) & 1) * 8);
+                for (int q = 0; q < 8; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            } else {
+                uint4 *o = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(out) + row * kH + col0);
 #pragma unroll
-                for (int mt = 0; mt < 2; ++mt) {
-                    mma16816(acc[mt][2 * np], af[mt], bf[0], bf[1]);
-                    mma16816(acc[mt][2 * np + 1], af[mt], bf[2], bf[3]);
+                for (int q = 0; q < 4; ++q) {
+                    uint32_t w[4];
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const __nv_bfloat162 pr = __floats2bfloat162_rn(v[8 * q + 2 * h], v[8 * q + 2 * h + 1]);
+                        w[h] = *reinterpret_cast<const uint32_t *>(&pr);
+                    }
+                    o[q] = make_uint4(w[0], w[1], w[2], w[3]);
                 }
             }
-        }
-        __syncthreads();
-    }
-
-    // epilogue: thread holds rows wm*32 + mt*16 + g (+8), columns wn*64 + nt*8 + 2c (+1)
-    const int g = lane >> 2, c = lane & 3;
-    float colsum[8][2];
+            if constexpr (EPI == kMaskBf16) {
+                // reduce-scatter over the warp's rows: lane l ends with column c0 + l
 #pragma unroll
-    for (int nt = 0; nt < 8; ++nt) colsum[nt][0] = colsum[nt][1] = 0.0f;
+                for (int o = 16; o >= 1; o >>= 1) {
+                    const bool upper = (lane & o) != 0;
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int64_t row = m0 + wm * 32 + mt * 16 + g + half * 8;
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                const int col = wn * 64 + nt * 8 + 2 * c;
-                float v0 = acc[mt][nt][2 * half], v1 = acc[mt][nt][2 * half + 1];
-                if constexpr (EPI == kMaskBf16) {
-                    const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162 *>(mask + row * kH + col);
-                    v0 = __bfloat162float(mk.x) > 0.0f ? v0 : 0.0f;
-                    v1 = __bfloat162float(mk.y) > 0.0f ? v1 : 0.0f;
-                    colsum[nt][0] += v0;
-                    colsum[nt][1] += v1;
-                    *reinterpret_cast<__nv_bfloat162 *>(static_cast<__nv_bfloat16 *>(out) + row * kH + col) =
-                        __floats2bfloat162_rn(v0, v1);
-                } else {
-                    v0 = fmaxf(v0 + bias[col], 0.0f);
-                    v1 = fmaxf(v1 + bias[col + 1], 0.0f);
-                    if constexpr (EPI == kReluBf16) {
-                        *reinterpret_cast<__nv_bfloat162 *>(static_cast<__nv_bfloat16 *>(out) + row * kH + col) =
-                            __floats2bfloat162_rn(v0, v1);
-                    } else {
-                        *reinterpret_cast<float2 *>(static_cast<float *>(out) + row * kH + col) = make_float2(v0, v1);
+                    for (int i = 0; i < o; ++i) {
+                        const float send = upper ? v[i] : v[i + o];
+                        const float keep = upper ? v[i + o] : v[i];
+                        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
                     }
                 }
+                s_cs[warp][c0 + lane] = v[0];
             }
         }
-    if constexpr (EPI == kMaskBf16) {
-        // column sums of this CTA's 64 rows, in a fixed order: shuffle over the 8 row
-        // groups of a warp, then the two row-warps through shared memory
-        __syncthreads();
-        float *s_part = reinterpret_cast<float *>(smem_raw);  // [2][256]
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                float v = colsum[nt][h];
-                v += __shfl_xor_sync(0xffffffffu, v, 4);
-                v += __shfl_xor_sync(0xffffffffu, v, 8);
-                v += __shfl_xor_sync(0xffffffffu, v, 16);
-                if (g == 0) s_part[wm * kH + wn * 64 + nt * 8 + 2 * c + h] = v;
-            }
-        __syncthreads();
-        col_partial[static_cast<int64_t>(blockIdx.x) * kH + t] = s_part[t] + s_part[kH + t];
+        if constexpr (EPI == kMaskBf16) {
+            __syncthreads();
+            // t = column: rows 0..63 are warps 0, 1; rows 64..127 warps 2, 3
+            const int64_t g = static_cast<int64_t>(blockIdx.x) * 2;
+            col_partial[g * kH + n0 + t] = s_cs[0][t] + s_cs[1][t];
+            col_partial[(g + 1) * kH + n0 + t] = s_cs[2][t] + s_cs[3][t];
+        }
+    }
+    tc_fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after_sync();
+        tmem_dealloc(tmem, BN);
     }
 }
 
@@ -398,31 +434,39 @@ cudaError_t mlp_launch_cast(const float *X, const int64_t *idx, int B, int in_di
     return cudaGetLastError();
 }
 
-static int layer_smem() { return (2 * 64 * (64 + kPad) + 2 * kH * (64 + kPad)) * 2; }
+static int layer_smem() { return 4 * 128 * 64 * 2; }  // two buffers each of A and B chunks
 static int wgrad_smem() { return (2 * 32 * (64 + kPad) + 2 * 32 * (kH + kPad)) * 2; }
 
 cudaError_t mlp_prepare()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_layer<kReluBf16>, cudaFuncAttributeMaxDynamicSharedMemorySize, layer_smem());
+    cudaError_t e =
+        cudaFuncSetAttribute(k_layer_tc<kReluBf16>, cudaFuncAttributeMaxDynamicSharedMemorySize, layer_smem());
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_layer<kReluF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, layer_smem());
+        e = cudaFuncSetAttribute(k_layer_tc<kReluF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, layer_smem());
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_layer<kMaskBf16>, cudaFuncAttributeMaxDynamicSharedMemorySize, layer_smem());
+        e = cudaFuncSetAttribute(k_layer_tc<kMaskBf16>, cudaFuncAttributeMaxDynamicSharedMemorySize, layer_smem());
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, wgrad_smem());
     return e;
 }
 
 cudaError_t mlp_launch_layer(int epi, const void *A, int Bp, int K, const void *Bt, const float *bias, const void *mask,
-                             void *out, float *col_partial, cudaStream_t s)
+                             void *out, float *col_partial, unsigned int *status, cudaStream_t s)
 {
-    const dim3 grid(Bp / 64);
+    if (Bp % 128 != 0 || K % 64 != 0) return cudaErrorInvalidValue;
+    const dim3 grid(Bp / 128, kH / 128);
     const auto *a = static_cast<const __nv_bfloat16 *>(A);
     const auto *b = static_cast<const __nv_bfloat16 *>(Bt);
     const auto *mk = static_cast<const __nv_bfloat16 *>(mask);
     switch (epi) {
-        case kReluBf16: k_layer<kReluBf16><<<grid, 256, layer_smem(), s>>>(a, K, b, bias, mk, out, col_partial); break;
-        case kReluF32: k_layer<kReluF32><<<grid, 256, layer_smem(), s>>>(a, K, b, bias, mk, out, col_partial); break;
-        case kMaskBf16: k_layer<kMaskBf16><<<grid, 256, layer_smem(), s>>>(a, K, b, bias, mk, out, col_partial); break;
+        case kReluBf16:
+            k_layer_tc<kReluBf16><<<grid, 128, layer_smem(), s>>>(a, K, b, bias, mk, out, col_partial, status);
+            break;
+        case kReluF32:
+            k_layer_tc<kReluF32><<<grid, 128, layer_smem(), s>>>(a, K, b, bias, mk, out, col_partial, status);
+            break;
+        case kMaskBf16:
+            k_layer_tc<kMaskBf16><<<grid, 128, layer_smem(), s>>>(a, K, b, bias, mk, out, col_partial, status);
+            break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

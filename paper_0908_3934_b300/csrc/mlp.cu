@@ -39,9 +39,11 @@ struct gn_mlp {
     DevArray<uint16_t> W1t, W2t, W2b;                 // BF16 copies
     DevArray<uint16_t> Xb, H1, dH2, dH1;              // BF16 activations [max_bp][.]
     DevArray<float> H2, p, part_w2, part_w1, part_head, part_b1, tmp_w1, tmp_head;
+    DevArray<unsigned int> status;  // kStatusTimeout when a kernel's bounded wait gave up
 
     ~gn_mlp()
     {
+        status.release();
         for (auto *a : {&params, &grads, &m, &v, &H2, &p, &part_w2, &part_w1, &part_head, &part_b1, &tmp_w1, &tmp_head})
             a->release();
         for (auto *a : {&W1t, &W2t, &W2b, &Xb, &H1, &dH2, &dH1}) a->release();
@@ -50,6 +52,18 @@ struct gn_mlp {
 };
 
 namespace {
+
+// Wait for the stream and report a device-side time-out.
+void sync(gn_mlp *m, const char *what)
+{
+    cuda_check(cudaStreamSynchronize(m->stream), what);
+    unsigned int st = 0;
+    cuda_check(cudaMemcpy(&st, m->status.p, 4, cudaMemcpyDeviceToHost), "D2H status");
+    if (st) {
+        cudaMemset(m->status.p, 0, 4);
+        fail(GN_ETIMEOUT, "a bounded device-side wait gave up (status %u)", st);
+    }
+}
 
 void check_mlp(const gn_mlp *m)
 {
@@ -71,9 +85,9 @@ void run(gn_mlp *m, const float *X, const float *y, const int64_t *idx, int B, f
     cudaStream_t s = m->stream;
     const float *P = m->params.p;
     cuda_check(gn::mlp_launch_cast(X, idx, B, m->in_dim, Bp, m->Xb.p, s), "cast");
-    cuda_check(gn::mlp_launch_layer(0, m->Xb.p, Bp, KP, m->W1t.p, P + m->off_b1, nullptr, m->H1.p, nullptr, s),
+    cuda_check(gn::mlp_launch_layer(0, m->Xb.p, Bp, KP, m->W1t.p, P + m->off_b1, nullptr, m->H1.p, nullptr, m->status.p, s),
                "layer 1");
-    cuda_check(gn::mlp_launch_layer(1, m->H1.p, Bp, H, m->W2t.p, P + m->off_b2, nullptr, m->H2.p, nullptr, s),
+    cuda_check(gn::mlp_launch_layer(1, m->H1.p, Bp, H, m->W2t.p, P + m->off_b2, nullptr, m->H2.p, nullptr, m->status.p, s),
                "layer 2");
     cuda_check(gn::mlp_launch_head(m->H2.p, P + m->off_w3, P + m->off_b3, y, idx, B, Bp, kHeadRows, p_out, m->dH2.p,
                                    m->part_head.p, s),
@@ -81,7 +95,7 @@ void run(gn_mlp *m, const float *X, const float *y, const int64_t *idx, int B, f
     if (!y) return;
     float *G = m->grads.p;
     // dH1 = (dH2 W2^T) [h1 > 0] and its column sums (db1)
-    cuda_check(gn::mlp_launch_layer(2, m->dH2.p, Bp, H, m->W2b.p, nullptr, m->H1.p, m->dH1.p, m->part_b1.p, s),
+    cuda_check(gn::mlp_launch_layer(2, m->dH2.p, Bp, H, m->W2b.p, nullptr, m->H1.p, m->dH1.p, m->part_b1.p, m->status.p, s),
                "layer 2 backward");
     cuda_check(gn::mlp_launch_wgrad(m->H1.p, Bp, H, m->dH2.p, kChunk, m->part_w2.p, s), "dW2");
     cuda_check(gn::mlp_launch_wgrad(m->Xb.p, Bp, KP, m->dH1.p, kChunk, m->part_w1.p, s), "dW1");
@@ -98,7 +112,7 @@ void run(gn_mlp *m, const float *X, const float *y, const int64_t *idx, int B, f
     if (loss) {
         float sum = 0.0f;
         cuda_check(cudaMemcpyAsync(&sum, m->tmp_head.p + 2 * H + 1, sizeof(float), cudaMemcpyDeviceToHost, s), "D2H");
-        cuda_check(cudaStreamSynchronize(s), "MLP step");
+        sync(m, "MLP step");
         *loss = sum / static_cast<float>(B);
     }
 }
@@ -161,6 +175,8 @@ gn_status gn_mlp_create(int32_t in_dim, int32_t max_batch, const float *params, 
         m->part_b1.alloc(bp / kHeadRows * H, &m->bytes);
         m->tmp_w1.alloc(static_cast<size_t>(KP) * H, &m->bytes);
         m->tmp_head.alloc(2 * H + 2, &m->bytes);
+        m->status.alloc(1, &m->bytes);
+        cuda_check(cudaMemset(m->status.p, 0, 4), "memset");
         cuda_check(cudaMemcpy(m->params.p, params, m->n_params * 4, cudaMemcpyHostToDevice), "H2D params");
         cuda_check(cudaMemset(m->grads.p, 0, m->n_params * 4), "memset");
         cuda_check(cudaMemset(m->m.p, 0, m->n_params * 4), "memset");
@@ -192,7 +208,7 @@ gn_status gn_mlp_get_params(gn_mlp *m, float *params)
         check_mlp(m);
         if (!params) fail(GN_EINVAL, "params is NULL");
         DeviceGuard dg(m->device);
-        cuda_check(cudaStreamSynchronize(m->stream), "MLP");
+        sync(m, "MLP");
         cuda_check(cudaMemcpy(params, m->params.p, m->n_params * 4, cudaMemcpyDeviceToHost), "D2H params");
     });
 }
@@ -250,7 +266,7 @@ gn_status gn_mlp_synchronize(gn_mlp *m)
     return guarded([&] {
         check_mlp(m);
         DeviceGuard dg(m->device);
-        cuda_check(cudaStreamSynchronize(m->stream), "MLP");
+        sync(m, "MLP");
     });
 }
 
