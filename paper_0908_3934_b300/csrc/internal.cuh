@@ -164,10 +164,17 @@ constexpr int kMlpHidden = 256;
 constexpr int kMlpInPad = 64;
 cudaError_t mlp_prepare();
 cudaError_t mlp_launch_cast(const float *X, const int64_t *idx, int B, int in_dim, int Bp, void *Xb, cudaStream_t s);
-// Bp a multiple of 128, K of 64; *status gets kStatusTimeout if a bounded wait gave up
+// Every GEMM runs on tcgen05 (k_mlp.cu); *status gets kStatusTimeout if a bounded
+// wait gave up.  Layer: out = epilogue(A [Bp][K] x Bt[256][K]^T), Bp a multiple of
+// 128, K of 64; out_t (may be null) receives the BF16 output transposed, [256][Bp].
 cudaError_t mlp_launch_layer(int epi, const void *A, int Bp, int K, const void *Bt, const float *bias, const void *mask,
-                             void *out, float *col_partial, unsigned int *status, cudaStream_t s);
-cudaError_t mlp_launch_wgrad(const void *A, int Bp, int K, const void *G, int chunk, float *partial, cudaStream_t s);
+                             void *out, void *out_t, float *col_partial, unsigned int *status, cudaStream_t s);
+// Weight-gradient partials over the batch: AT [M][Bp], BT [N][Bp] (batch-contiguous);
+// split z covers rows [z chunk, (z + 1) chunk) of the batch and writes
+// partial[z][M][N] (N = 256) or, transposed, partial[z][N][M] (N = 64).
+cudaError_t mlp_launch_wgrad(const void *AT, int M, const void *BT, int N, int Bp, int chunk, bool transposed,
+                             float *partial, unsigned int *status, cudaStream_t s);
+cudaError_t mlp_launch_transpose(const void *in, int R, int C, void *out, cudaStream_t s);
 cudaError_t mlp_launch_head(const float *H2, const float *w3, const float *b3, const float *y, const int64_t *idx, int B,
                             int Bp, int rows_per_cta, float *p, void *dH2, float *partial, cudaStream_t s);
 cudaError_t mlp_launch_sum(const float *part, int n, int64_t len, float *out, cudaStream_t s);

@@ -17,7 +17,6 @@ namespace {
 
 constexpr int kH = 256;    // hidden width
 constexpr int kKP = 64;    // padded input width
-constexpr int kPad = 8;    // smem row padding (bf16) against ldmatrix bank conflicts
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
@@ -26,21 +25,6 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void *p)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_u32(p)));
-}
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
 
 // ---------------------------------------------------------------------------
 // Row b of the batch is X[idx[b]] (or X[b] without idx), FP32 -> Xb [Bp][64]
@@ -67,32 +51,52 @@ __global__ void k_cast_x(const float *__restrict__ X, const int64_t *__restrict_
 enum Epi { kReluBf16 = 0, kReluF32 = 1, kMaskBf16 = 2 };
 
 // ---------------------------------------------------------------------------
-// tcgen05 implementation: one CTA of 128 threads computes a 128-row x 128-column
-// tile (blockIdx.y picks the column half) with its FP32 accumulator in tensor memory.
-// K is staged in chunks of 64 (two buffers): the 128 threads copy A and B rows with
-// 16-byte cp.async into the K-major core-matrix layout (8 rows x 16 bytes per core
-// matrix, 128 bytes apart along K, 1024 bytes apart along rows -- thread c writes
-// bytes [16c, 16c + 16) of a buffer), one thread issues four 128 x 128 x 16 MMAs per
-// chunk and commits them to the chunk's mbarrier.  Epilogue: warp w reads TMEM lanes
-// 32w .. 32w + 31 (its rows) with tcgen05.ld, 32 columns at a time, and applies the
-// same bias / ReLU / mask and rounding as k_layer.  Column sums of the mask epilogue
-// go to col_partial[row / 64][col] in a fixed order (a reduce-scatter over the warp's
-// 32 rows, then the two warps of each 64-row group).  Every wait is bounded: on a
-// time-out the CTA sets *status, waits once more for its MMAs, frees its tensor
-// memory and leaves.
-template <int EPI>
-__global__ void __launch_bounds__(128) k_layer_tc(const __nv_bfloat16 *__restrict__ A, int K,
-                                                  const __nv_bfloat16 *__restrict__ Bt,
-                                                  const float *__restrict__ bias,
-                                                  const __nv_bfloat16 *__restrict__ mask, void *__restrict__ out,
-                                                  float *__restrict__ col_partial, unsigned int *status)
+// Every GEMM of the MLP on tcgen05: C[m][n] = sum_k A[m][k] B[n][k] (both operands
+// K-contiguous BF16, FP32 accumulation in tensor memory).  One CTA of 128 threads
+// computes a 128 x BN tile over `kc` chunks of 64 along K (CTA z of a split-K grid
+// starts at chunk z * kc).  Chunks are double-buffered: the 128 threads copy A and B
+// rows with 16-byte cp.async into the K-major core-matrix layout (8 rows x 16 bytes
+// per core matrix, 128 bytes apart along K, 1024 bytes apart along rows -- thread c
+// writes bytes [16c, 16c + 16) of a buffer), one thread issues four 128 x BN x 16
+// MMAs per chunk and commits them to the chunk's mbarrier.  Epilogue: warp w reads
+// TMEM lanes 32w .. 32w + 31 (its rows) with tcgen05.ld, 32 columns at a time:
+//   kReluBf16   BF16 relu(C + bias) (+ a transposed copy [col][row])
+//   kReluF32    FP32 relu(C + bias)
+//   kMaskBf16   BF16 C where mask > 0, else 0 (+ transposed copy), and per-64-row
+//               column sums of it to col_partial[row / 64][col] in a fixed order
+//               (reduce-scatter over a warp's 32 rows, then the two warps of a group)
+//   kPartF32    FP32 C tile of split z to partial[z][row][col]
+//   kPartF32T   the same transposed, partial[z][col][row]
+// Every wait is bounded: on a time-out the CTA sets *status, waits once more for its
+// MMAs, frees its tensor memory and leaves.
+enum GemmEpi { kPartF32 = 3, kPartF32T = 4 };
+
+struct GemmArgs {
+    const __nv_bfloat16 *A;  // [.][lda], rows m0 ..
+    int64_t lda;
+    const __nv_bfloat16 *B;  // [.][ldb], rows n0 ..
+    int64_t ldb;
+    int kc;                  // chunks of 64 along K per CTA
+    const float *bias;
+    const __nv_bfloat16 *mask;
+    void *out;               // row-major, kH columns
+    __nv_bfloat16 *out_t;    // transposed BF16 copy [kH][ldt], or null
+    int64_t ldt;
+    float *col_partial;
+    float *partial;          // split-K tiles
+    int64_t partial_stride;  // floats between the tiles of consecutive splits
+    unsigned int *status;
+};
+
+template <int EPI, int BN>
+__global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs g)
 {
-    constexpr int BM = 128, BN = 128, BK = 64;
-    constexpr int kStage = BM * BK * 2;  // bytes of one operand buffer (A and B alike)
+    constexpr int BM = 128, BK = 64;
+    constexpr int kStageA = BM * BK * 2, kStageB = BN * BK * 2;  // bytes of one buffer
     constexpr uint32_t kIdesc = idesc_bf16_f32(BM, BN);
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    uint8_t *sA = smem_raw;                  // [2][kStage]
-    uint8_t *sB = smem_raw + 2 * kStage;     // [2][kStage]
+    uint8_t *sA = smem_raw;                  // [2][kStageA]
+    uint8_t *sB = smem_raw + 2 * kStageA;    // [2][kStageB]
     __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ uint32_t s_tmem;
     __shared__ int s_fail;
@@ -101,6 +105,7 @@ __global__ void __launch_bounds__(128) k_layer_tc(const __nv_bfloat16 *__restric
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int64_t m0 = static_cast<int64_t>(blockIdx.x) * BM;
     const int n0 = blockIdx.y * BN;
+    const int64_t kbase = static_cast<int64_t>(blockIdx.z) * g.kc * BK;
     if (warp == 0) {
         tmem_alloc(&s_tmem, BN);
         tmem_relinquish();
@@ -116,27 +121,27 @@ __global__ void __launch_bounds__(128) k_layer_tc(const __nv_bfloat16 *__restric
     tc_fence_after_sync();
     const uint32_t tmem = s_tmem;
 
-    auto load = [&](int stage, int k0) {
-        uint8_t *a = sA + stage * kStage;
-        uint8_t *b = sB + stage * kStage;
+    auto load = [&](int stage, int64_t k0) {
+        uint8_t *a = sA + stage * kStageA;
+        uint8_t *b = sB + stage * kStageB;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
+        for (int i = 0; i < BM * 8 / 128; ++i) {
             const int c = t + 128 * i;  // 16-byte piece: row (c & 7) + 8 (c >> 6), K piece (c >> 3) & 7
             const int r = (c & 7) + 8 * (c >> 6), kp = (c >> 3) & 7;
-            cp_async16(a + 16 * c, A + (m0 + r) * K + k0 + kp * 8);
-            cp_async16(b + 16 * c, Bt + static_cast<int64_t>(n0 + r) * K + k0 + kp * 8);
+            cp_async16(a + 16 * c, g.A + (m0 + r) * g.lda + k0 + kp * 8);
+            if (c < BN * 8) cp_async16(b + 16 * c, g.B + static_cast<int64_t>(n0 + r) * g.ldb + k0 + kp * 8);
         }
         cp_async_commit();
     };
 
-    const int nk = K / BK;
+    const int nk = g.kc;
     bool ok = true;
-    load(0, 0);
+    load(0, kbase);
     for (int kc = 0; kc < nk; ++kc) {
         if (kc + 1 < nk) {
             // buffer (kc + 1) & 1 was last read by the MMAs of chunk kc - 1
             if (kc >= 1 && !mbar_wait_bounded(&s_bar[(kc - 1) & 1], ((kc - 1) >> 1) & 1, kDefaultWaitLimit)) ok = false;
-            load((kc + 1) & 1, (kc + 1) * BK);
+            load((kc + 1) & 1, kbase + static_cast<int64_t>(kc + 1) * BK);
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
@@ -145,8 +150,8 @@ __global__ void __launch_bounds__(128) k_layer_tc(const __nv_bfloat16 *__restric
         __syncthreads();
         if (t == 0) {
             tc_fence_after_sync();
-            const uint8_t *a = sA + (kc & 1) * kStage;
-            const uint8_t *b = sB + (kc & 1) * kStage;
+            const uint8_t *a = sA + (kc & 1) * kStageA;
+            const uint8_t *b = sB + (kc & 1) * kStageB;
 #pragma unroll
             for (int ks = 0; ks < BK / 16; ++ks)
                 tc_mma_bf16(tmem, smem_desc_kmajor(a + ks * 256, 128, 1024), smem_desc_kmajor(b + ks * 256, 128, 1024),
@@ -158,7 +163,7 @@ __global__ void __launch_bounds__(128) k_layer_tc(const __nv_bfloat16 *__restric
     if (!mbar_wait_bounded(&s_bar[(nk - 1) & 1], ((nk - 1) >> 1) & 1, kDefaultWaitLimit)) ok = false;
     if (!ok) {
         s_fail = 1;
-        atomicOr(status, kStatusTimeout);
+        atomicOr(g.status, kStatusTimeout);
         mbar_wait_bounded(&s_bar[(nk - 1) & 1], ((nk - 1) >> 1) & 1, kDefaultWaitLimit);
     }
     tc_fence_before_sync();
@@ -178,16 +183,25 @@ __global__ void __launch_bounds__(128) k_layer_tc(const __nv_bfloat16 *__restric
             for (int j = 0; j < 32; ++j) {
                 const float acc = __uint_as_float(raw[j]);
                 if constexpr (EPI == kMaskBf16)
-                    v[j] = __bfloat162float(mask[row * kH + col0 + j]) > 0.0f ? acc : 0.0f;
+                    v[j] = __bfloat162float(g.mask[row * kH + col0 + j]) > 0.0f ? acc : 0.0f;
+                else if constexpr (EPI == kReluBf16 || EPI == kReluF32)
+                    v[j] = fmaxf(acc + g.bias[col0 + j], 0.0f);
                 else
-                    v[j] = fmaxf(acc + bias[col0 + j], 0.0f);
+                    v[j] = acc;
             }
-            if constexpr (EPI == kReluF32) {
-                float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(out) + row * kH + col0);
+            if constexpr (EPI == kReluF32 || EPI == kPartF32) {
+                float *base = EPI == kReluF32 ? static_cast<float *>(g.out) + row * kH + col0
+                                              : g.partial + blockIdx.z * g.partial_stride + row * kH + col0;
+                float4 *o = reinterpret_cast<float4 *>(base);
 #pragma unroll
                 for (int q = 0; q < 8; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            } else if constexpr (EPI == kPartF32T) {
+                // [col][row]: the warp's lanes write 32 consecutive rows of each column
+                float *base = g.partial + blockIdx.z * g.partial_stride;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) base[static_cast<int64_t>(col0 + j) * kH + row] = v[j];
             } else {
-                uint4 *o = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(out) + row * kH + col0);
+                uint4 *o = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(g.out) + row * kH + col0);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     uint32_t w[4];
@@ -197,6 +211,11 @@ __global__ void __launch_bounds__(128) k_layer_tc(const __nv_bfloat16 *__restric
                         w[h] = *reinterpret_cast<const uint32_t *>(&pr);
                     }
                     o[q] = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+                if (g.out_t) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        g.out_t[static_cast<int64_t>(col0 + j) * g.ldt + row] = __float2bfloat16_rn(v[j]);
                 }
             }
             if constexpr (EPI == kMaskBf16) {
@@ -217,9 +236,11 @@ __global__ void __launch_bounds__(128) k_layer_tc(const __nv_bfloat16 *__restric
         if constexpr (EPI == kMaskBf16) {
             __syncthreads();
             // t = column: rows 0..63 are warps 0, 1; rows 64..127 warps 2, 3
-            const int64_t g = static_cast<int64_t>(blockIdx.x) * 2;
-            col_partial[g * kH + n0 + t] = s_cs[0][t] + s_cs[1][t];
-            col_partial[(g + 1) * kH + n0 + t] = s_cs[2][t] + s_cs[3][t];
+            const int64_t grp = static_cast<int64_t>(blockIdx.x) * 2;
+            if (t < BN) {
+                g.col_partial[grp * kH + n0 + t] = s_cs[0][t] + s_cs[1][t];
+                g.col_partial[(grp + 1) * kH + n0 + t] = s_cs[2][t] + s_cs[3][t];
+            }
         }
     }
     tc_fence_before_sync();
@@ -230,92 +251,17 @@ __global__ void __launch_bounds__(128) k_layer_tc(const __nv_bfloat16 *__restric
     }
 }
 
-// ---------------------------------------------------------------------------
-// Weight gradient partials: Cp[k][n] = sum_{m in chunk} A[m][k] G[m][n] for a CTA
-// tile of 64 k x 256 n over `chunk` rows of the batch (A [M][K], G [M][256] row-major
-// BF16); operands are loaded transposed from shared memory (ldmatrix .trans).
-__global__ void __launch_bounds__(256) k_wgrad(const __nv_bfloat16 *__restrict__ A, int K,
-                                               const __nv_bfloat16 *__restrict__ G, int chunk,
-                                               float *__restrict__ partial)
+// BF16 transpose in[R][C] -> out[C][R] through 32 x 32 shared-memory tiles.
+__global__ void k_transpose_bf16(const __nv_bfloat16 *__restrict__ in, int R, int C, __nv_bfloat16 *__restrict__ out)
 {
-    constexpr int BM = 32, LDA = 64 + kPad, LDG = kH + kPad;
-    extern __shared__ __align__(16) uint8_t smem_raw[];
-    __nv_bfloat16 *sA = reinterpret_cast<__nv_bfloat16 *>(smem_raw);  // [2][BM][LDA]
-    __nv_bfloat16 *sG = sA + 2 * BM * LDA;                              // [2][BM][LDG]
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int wk = warp >> 2, wn = warp & 3;
-    const int k0 = blockIdx.x * 64;
-    const int64_t mbeg = static_cast<int64_t>(blockIdx.y) * chunk;
-
-    auto load = [&](int stage, int64_t m) {
-        __nv_bfloat16 *a = sA + stage * BM * LDA;
-        __nv_bfloat16 *gg = sG + stage * BM * LDG;
-        for (int c = t; c < BM * 64 / 8; c += 256) {
-            const int r = c / 8, k = (c % 8) * 8;
-            cp_async16(a + r * LDA + k, A + (m + r) * K + k0 + k);
-        }
-        for (int c = t; c < BM * kH / 8; c += 256) {
-            const int r = c / (kH / 8), n = (c % (kH / 8)) * 8;
-            cp_async16(gg + r * LDG + n, G + (m + r) * kH + n);
-        }
-        cp_async_commit();
-    };
-
-    float acc[2][8][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
-
-    const int steps = chunk / BM;
-    load(0, mbeg);
-    for (int s = 0; s < steps; ++s) {
-        if (s + 1 < steps) {
-            load((s + 1) & 1, mbeg + static_cast<int64_t>(s + 1) * BM);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        __syncthreads();
-        const __nv_bfloat16 *a = sA + (s & 1) * BM * LDA;
-        const __nv_bfloat16 *gg = sG + (s & 1) * BM * LDG;
-#pragma unroll
-        for (int ms = 0; ms < BM / 16; ++ms) {
-            uint32_t af[2][4];
-#pragma unroll
-            for (int kt = 0; kt < 2; ++kt)
-                ldsm_x4_t(af[kt], a + (ms * 16 + (lane & 7) + ((lane >> 4) << 3)) * LDA + wk * 32 + kt * 16 +
-                                      ((lane >> 3) & 1) * 8);
-#pragma unroll
-            for (int np = 0; np < 4; ++np) {
-                uint32_t bf[4];
-                ldsm_x4_t(bf, gg + (ms * 16 + (lane & 7) + ((lane >> 3) & 1) * 8) * LDG + wn * 64 + np * 16 +
-                                  (lane >> 4) * 8);
-#pragma unroll
-                for (int kt = 0; kt < 2; ++kt) {
-                    mma16816(acc[kt][2 * np], af[kt], bf[0], bf[1]);
-                    mma16816(acc[kt][2 * np + 1], af[kt], bf[2], bf[3]);
-                }
-            }
-        }
-        __syncthreads();
-    }
-    const int g = lane >> 2, c = lane & 3;
-    float *out = partial + static_cast<int64_t>(blockIdx.y) * K * kH;
-#pragma unroll
-    for (int kt = 0; kt < 2; ++kt)
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int k = k0 + wk * 32 + kt * 16 + g + half * 8;
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                const int n = wn * 64 + nt * 8 + 2 * c;
-                *reinterpret_cast<float2 *>(out + static_cast<int64_t>(k) * kH + n) =
-                    make_float2(acc[kt][nt][2 * half], acc[kt][nt][2 * half + 1]);
-            }
-        }
+    __shared__ __nv_bfloat16 tile[32][34];
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    for (int i = ty; i < 32; i += 8)
+        if (r0 + i < R && c0 + tx < C) tile[i][tx] = in[static_cast<int64_t>(r0 + i) * C + c0 + tx];
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8)
+        if (c0 + i < C && r0 + tx < R) out[static_cast<int64_t>(c0 + i) * R + r0 + tx] = tile[tx][i];
 }
 
 // ---------------------------------------------------------------------------
@@ -434,49 +380,79 @@ cudaError_t mlp_launch_cast(const float *X, const int64_t *idx, int B, int in_di
     return cudaGetLastError();
 }
 
-static int layer_smem() { return 4 * 128 * 64 * 2; }  // two buffers each of A and B chunks
-static int wgrad_smem() { return (2 * 32 * (64 + kPad) + 2 * 32 * (kH + kPad)) * 2; }
+template <int BN>
+constexpr int gemm_smem() { return 2 * 128 * 64 * 2 + 2 * BN * 64 * 2; }  // two buffers each of A and B chunks
+
+template <int EPI, int BN>
+cudaError_t gemm_attr()
+{
+    return cudaFuncSetAttribute(k_gemm_tc<EPI, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_smem<BN>());
+}
 
 cudaError_t mlp_prepare()
 {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_layer_tc<kReluBf16>, cudaFuncAttributeMaxDynamicSharedMemorySize, layer_smem());
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_layer_tc<kReluF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, layer_smem());
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_layer_tc<kMaskBf16>, cudaFuncAttributeMaxDynamicSharedMemorySize, layer_smem());
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, wgrad_smem());
+    cudaError_t e = gemm_attr<kReluBf16, 128>();
+    if (e == cudaSuccess) e = gemm_attr<kReluF32, 128>();
+    if (e == cudaSuccess) e = gemm_attr<kMaskBf16, 128>();
+    if (e == cudaSuccess) e = gemm_attr<kPartF32, 128>();
+    if (e == cudaSuccess) e = gemm_attr<kPartF32T, 64>();
     return e;
 }
 
 cudaError_t mlp_launch_layer(int epi, const void *A, int Bp, int K, const void *Bt, const float *bias, const void *mask,
-                             void *out, float *col_partial, unsigned int *status, cudaStream_t s)
+                             void *out, void *out_t, float *col_partial, unsigned int *status, cudaStream_t s)
 {
     if (Bp % 128 != 0 || K % 64 != 0) return cudaErrorInvalidValue;
+    GemmArgs g{};
+    g.A = static_cast<const __nv_bfloat16 *>(A);
+    g.lda = K;
+    g.B = static_cast<const __nv_bfloat16 *>(Bt);
+    g.ldb = K;
+    g.kc = K / 64;
+    g.bias = bias;
+    g.mask = static_cast<const __nv_bfloat16 *>(mask);
+    g.out = out;
+    g.out_t = static_cast<__nv_bfloat16 *>(out_t);
+    g.ldt = Bp;
+    g.col_partial = col_partial;
+    g.status = status;
     const dim3 grid(Bp / 128, kH / 128);
-    const auto *a = static_cast<const __nv_bfloat16 *>(A);
-    const auto *b = static_cast<const __nv_bfloat16 *>(Bt);
-    const auto *mk = static_cast<const __nv_bfloat16 *>(mask);
     switch (epi) {
-        case kReluBf16:
-            k_layer_tc<kReluBf16><<<grid, 128, layer_smem(), s>>>(a, K, b, bias, mk, out, col_partial, status);
-            break;
-        case kReluF32:
-            k_layer_tc<kReluF32><<<grid, 128, layer_smem(), s>>>(a, K, b, bias, mk, out, col_partial, status);
-            break;
-        case kMaskBf16:
-            k_layer_tc<kMaskBf16><<<grid, 128, layer_smem(), s>>>(a, K, b, bias, mk, out, col_partial, status);
-            break;
+        case kReluBf16: k_gemm_tc<kReluBf16, 128><<<grid, 128, gemm_smem<128>(), s>>>(g); break;
+        case kReluF32: k_gemm_tc<kReluF32, 128><<<grid, 128, gemm_smem<128>(), s>>>(g); break;
+        case kMaskBf16: k_gemm_tc<kMaskBf16, 128><<<grid, 128, gemm_smem<128>(), s>>>(g); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-cudaError_t mlp_launch_wgrad(const void *A, int Bp, int K, const void *G, int chunk, float *partial, cudaStream_t s)
+cudaError_t mlp_launch_wgrad(const void *AT, int M, const void *BT, int N, int Bp, int chunk, bool transposed,
+                             float *partial, unsigned int *status, cudaStream_t s)
 {
-    const dim3 grid(K / 64, Bp / chunk);
-    k_wgrad<<<grid, 256, wgrad_smem(), s>>>(static_cast<const __nv_bfloat16 *>(A), K,
-                                            static_cast<const __nv_bfloat16 *>(G), chunk, partial);
+    if (M % 128 != 0 || Bp % chunk != 0 || chunk % 64 != 0 || (N != 256 && N != 64) || (N == 64) != transposed)
+        return cudaErrorInvalidValue;
+    GemmArgs g{};
+    g.A = static_cast<const __nv_bfloat16 *>(AT);
+    g.lda = Bp;
+    g.B = static_cast<const __nv_bfloat16 *>(BT);
+    g.ldb = Bp;
+    g.kc = chunk / 64;
+    g.partial = partial;
+    g.partial_stride = static_cast<int64_t>(M) * N;
+    g.status = status;
+    if (transposed) {
+        k_gemm_tc<kPartF32T, 64><<<dim3(M / 128, 1, Bp / chunk), 128, gemm_smem<64>(), s>>>(g);
+    } else {
+        k_gemm_tc<kPartF32, 128><<<dim3(M / 128, N / 128, Bp / chunk), 128, gemm_smem<128>(), s>>>(g);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_launch_transpose(const void *in, int R, int C, void *out, cudaStream_t s)
+{
+    const dim3 grid((C + 31) / 32, (R + 31) / 32);
+    k_transpose_bf16<<<grid, dim3(32, 8), 0, s>>>(static_cast<const __nv_bfloat16 *>(in), R, C,
+                                                  static_cast<__nv_bfloat16 *>(out));
     return cudaGetLastError();
 }
 

@@ -21,7 +21,7 @@ using gnrt::guarded;
 namespace {
 constexpr int H = gn::kMlpHidden;
 constexpr int KP = gn::kMlpInPad;
-constexpr int kChunk = 128;  // batch rows per weight-gradient partial
+constexpr int kChunk = 128;  // batch padding granularity and the smallest weight-gradient split
 constexpr int kHeadRows = 64;
 }  // namespace
 
@@ -38,6 +38,7 @@ struct gn_mlp {
     DevArray<float> params, grads, m, v;
     DevArray<uint16_t> W1t, W2t, W2b;                 // BF16 copies
     DevArray<uint16_t> Xb, H1, dH2, dH1;              // BF16 activations [max_bp][.]
+    DevArray<uint16_t> XT, H1T, dH2T, dH1T;           // the same transposed, [.][Bp] (weight-gradient operands)
     DevArray<float> H2, p, part_w2, part_w1, part_head, part_b1, tmp_w1, tmp_head;
     DevArray<unsigned int> status;  // kStatusTimeout when a kernel's bounded wait gave up
 
@@ -46,7 +47,7 @@ struct gn_mlp {
         status.release();
         for (auto *a : {&params, &grads, &m, &v, &H2, &p, &part_w2, &part_w1, &part_head, &part_b1, &tmp_w1, &tmp_head})
             a->release();
-        for (auto *a : {&W1t, &W2t, &W2b, &Xb, &H1, &dH2, &dH1}) a->release();
+        for (auto *a : {&W1t, &W2t, &W2b, &Xb, &H1, &dH2, &dH1, &XT, &H1T, &dH2T, &dH1T}) a->release();
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 };
@@ -77,6 +78,15 @@ void refresh(gn_mlp *m)
                "refresh");
 }
 
+// Rows of the batch per weight-gradient split: the largest of 512, 256, 128 that
+// divides Bp (16 splits at the usual batch of 8192).
+int wgrad_chunk(int Bp)
+{
+    for (int c : {512, 256})
+        if (Bp % c == 0) return c;
+    return kChunk;
+}
+
 // Forward pass of B rows (Bp padded); with y, also the backward pass into m->grads
 // and the mean loss into *loss.
 void run(gn_mlp *m, const float *X, const float *y, const int64_t *idx, int B, float *p_out, float *loss)
@@ -85,9 +95,12 @@ void run(gn_mlp *m, const float *X, const float *y, const int64_t *idx, int B, f
     cudaStream_t s = m->stream;
     const float *P = m->params.p;
     cuda_check(gn::mlp_launch_cast(X, idx, B, m->in_dim, Bp, m->Xb.p, s), "cast");
-    cuda_check(gn::mlp_launch_layer(0, m->Xb.p, Bp, KP, m->W1t.p, P + m->off_b1, nullptr, m->H1.p, nullptr, m->status.p, s),
+    const bool train = y != nullptr;
+    cuda_check(gn::mlp_launch_layer(0, m->Xb.p, Bp, KP, m->W1t.p, P + m->off_b1, nullptr, m->H1.p,
+                                    train ? m->H1T.p : nullptr, nullptr, m->status.p, s),
                "layer 1");
-    cuda_check(gn::mlp_launch_layer(1, m->H1.p, Bp, H, m->W2t.p, P + m->off_b2, nullptr, m->H2.p, nullptr, m->status.p, s),
+    cuda_check(gn::mlp_launch_layer(1, m->H1.p, Bp, H, m->W2t.p, P + m->off_b2, nullptr, m->H2.p, nullptr, nullptr,
+                                    m->status.p, s),
                "layer 2");
     cuda_check(gn::mlp_launch_head(m->H2.p, P + m->off_w3, P + m->off_b3, y, idx, B, Bp, kHeadRows, p_out, m->dH2.p,
                                    m->part_head.p, s),
@@ -95,11 +108,17 @@ void run(gn_mlp *m, const float *X, const float *y, const int64_t *idx, int B, f
     if (!y) return;
     float *G = m->grads.p;
     // dH1 = (dH2 W2^T) [h1 > 0] and its column sums (db1)
-    cuda_check(gn::mlp_launch_layer(2, m->dH2.p, Bp, H, m->W2b.p, nullptr, m->H1.p, m->dH1.p, m->part_b1.p, m->status.p, s),
+    cuda_check(gn::mlp_launch_layer(2, m->dH2.p, Bp, H, m->W2b.p, nullptr, m->H1.p, m->dH1.p, m->dH1T.p, m->part_b1.p,
+                                    m->status.p, s),
                "layer 2 backward");
-    cuda_check(gn::mlp_launch_wgrad(m->H1.p, Bp, H, m->dH2.p, kChunk, m->part_w2.p, s), "dW2");
-    cuda_check(gn::mlp_launch_wgrad(m->Xb.p, Bp, KP, m->dH1.p, kChunk, m->part_w1.p, s), "dW1");
-    const int nchunk = Bp / kChunk, nhead = Bp / kHeadRows;
+    // weight gradients reduce over the batch: operands batch-contiguous, split over
+    // `chunk` rows of the batch, partials summed in a fixed order
+    cuda_check(gn::mlp_launch_transpose(m->dH2.p, Bp, H, m->dH2T.p, s), "transpose");
+    cuda_check(gn::mlp_launch_transpose(m->Xb.p, Bp, KP, m->XT.p, s), "transpose");
+    const int chunk = wgrad_chunk(Bp);
+    cuda_check(gn::mlp_launch_wgrad(m->H1T.p, H, m->dH2T.p, H, Bp, chunk, false, m->part_w2.p, m->status.p, s), "dW2");
+    cuda_check(gn::mlp_launch_wgrad(m->dH1T.p, H, m->XT.p, KP, Bp, chunk, true, m->part_w1.p, m->status.p, s), "dW1");
+    const int nchunk = Bp / chunk, nhead = Bp / kHeadRows;
     cuda_check(gn::mlp_launch_sum(m->part_w2.p, nchunk, static_cast<int64_t>(H) * H, G + m->off_W2, s), "sum");
     cuda_check(gn::mlp_launch_sum(m->part_w1.p, nchunk, static_cast<int64_t>(KP) * H, m->tmp_w1.p, s), "sum");
     cuda_check(gn::mlp_launch_sum(m->part_b1.p, nhead, H, G + m->off_b1, s), "sum");
@@ -167,6 +186,10 @@ gn_status gn_mlp_create(int32_t in_dim, int32_t max_batch, const float *params, 
         m->H1.alloc(bp * H, &m->bytes);
         m->dH2.alloc(bp * H, &m->bytes);
         m->dH1.alloc(bp * H, &m->bytes);
+        m->XT.alloc(bp * KP, &m->bytes);
+        m->H1T.alloc(bp * H, &m->bytes);
+        m->dH2T.alloc(bp * H, &m->bytes);
+        m->dH1T.alloc(bp * H, &m->bytes);
         m->H2.alloc(bp * H, &m->bytes);
         m->p.alloc(bp, &m->bytes);
         m->part_w2.alloc(bp / kChunk * H * H, &m->bytes);
