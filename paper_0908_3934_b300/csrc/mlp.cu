@@ -41,9 +41,28 @@ struct gn_mlp {
     DevArray<uint16_t> XT, H1T, dH2T, dH1T;           // the same transposed, [.][Bp] (weight-gradient operands)
     DevArray<float> H2, p, part_w2, part_w1, part_head, part_b1, tmp_w1, tmp_head;
     DevArray<unsigned int> status;  // kStatusTimeout when a kernel's bounded wait gave up
+    // replayed training epochs: batch cursor, bias-correction table, per-step losses
+    DevArray<int64_t> ep_cursor;
+    DevArray<float> ep_bc, ep_losses;
+    cudaGraphExec_t ep_graph = nullptr;
+    struct EpochKey {
+        const void *X, *y, *idx;
+        int B;
+        float lr, wd;
+        const void *bc, *losses;
+        bool operator==(const EpochKey &o) const
+        {
+            return X == o.X && y == o.y && idx == o.idx && B == o.B && lr == o.lr && wd == o.wd && bc == o.bc &&
+                   losses == o.losses;
+        }
+    } ep_key{};
 
     ~gn_mlp()
     {
+        if (ep_graph) cudaGraphExecDestroy(ep_graph);
+        ep_cursor.release();
+        ep_bc.release();
+        ep_losses.release();
         status.release();
         for (auto *a : {&params, &grads, &m, &v, &H2, &p, &part_w2, &part_w1, &part_head, &part_b1, &tmp_w1, &tmp_head})
             a->release();
@@ -71,30 +90,26 @@ void check_mlp(const gn_mlp *m)
     if (!m) fail(GN_EINVAL, "MLP handle is NULL");
 }
 
-void refresh(gn_mlp *m)
+void refresh(gn_mlp *m, cudaStream_t s)
 {
     cuda_check(gn::mlp_launch_refresh(m->params.p + m->off_W1, m->in_dim, m->params.p + m->off_W2, m->W1t.p, m->W2t.p,
-                                      m->W2b.p, m->stream),
+                                      m->W2b.p, s),
                "refresh");
 }
 
-// Rows of the batch per weight-gradient split: the largest of 512, 256, 128 that
-// divides Bp (16 splits at the usual batch of 8192).
-int wgrad_chunk(int Bp)
-{
-    for (int c : {512, 256})
-        if (Bp % c == 0) return c;
-    return kChunk;
-}
+// Rows of the batch per weight-gradient split: 256 when it divides Bp (32 splits,
+// 128 CTAs for dW2 at the usual batch of 8192), else 128.
+int wgrad_chunk(int Bp) { return Bp % 256 == 0 ? 256 : kChunk; }
 
-// Forward pass of B rows (Bp padded); with y, also the backward pass into m->grads
-// and the mean loss into *loss.
-void run(gn_mlp *m, const float *X, const float *y, const int64_t *idx, int B, float *p_out, float *loss)
+// Forward pass of B rows (Bp padded) on stream s; with y, also the backward pass into
+// m->grads and the mean loss into *loss (may be NULL).  With a device batch cursor the
+// rows are idx[cursor B + b].
+void run(gn_mlp *m, const float *X, const float *y, const int64_t *idx, int B, float *p_out, float *loss,
+         const int64_t *cursor, cudaStream_t s)
 {
     const int Bp = (B + kChunk - 1) / kChunk * kChunk;
-    cudaStream_t s = m->stream;
     const float *P = m->params.p;
-    cuda_check(gn::mlp_launch_cast(X, idx, B, m->in_dim, Bp, m->Xb.p, s), "cast");
+    cuda_check(gn::mlp_launch_cast(X, idx, cursor, B, m->in_dim, Bp, m->Xb.p, s), "cast");
     const bool train = y != nullptr;
     cuda_check(gn::mlp_launch_layer(0, m->Xb.p, Bp, KP, m->W1t.p, P + m->off_b1, nullptr, m->H1.p,
                                     train ? m->H1T.p : nullptr, nullptr, m->status.p, s),
@@ -102,7 +117,7 @@ void run(gn_mlp *m, const float *X, const float *y, const int64_t *idx, int B, f
     cuda_check(gn::mlp_launch_layer(1, m->H1.p, Bp, H, m->W2t.p, P + m->off_b2, nullptr, m->H2.p, nullptr, nullptr,
                                     m->status.p, s),
                "layer 2");
-    cuda_check(gn::mlp_launch_head(m->H2.p, P + m->off_w3, P + m->off_b3, y, idx, B, Bp, kHeadRows, p_out, m->dH2.p,
+    cuda_check(gn::mlp_launch_head(m->H2.p, P + m->off_w3, P + m->off_b3, y, idx, cursor, B, Bp, kHeadRows, p_out, m->dH2.p,
                                    m->part_head.p, s),
                "head");
     if (!y) return;
@@ -204,7 +219,7 @@ gn_status gn_mlp_create(int32_t in_dim, int32_t max_batch, const float *params, 
         cuda_check(cudaMemset(m->grads.p, 0, m->n_params * 4), "memset");
         cuda_check(cudaMemset(m->m.p, 0, m->n_params * 4), "memset");
         cuda_check(cudaMemset(m->v.p, 0, m->n_params * 4), "memset");
-        refresh(m);
+        refresh(m, m->stream);
         cuda_check(cudaStreamSynchronize(m->stream), "create");
     });
     if (st != GN_OK) {
@@ -244,7 +259,7 @@ gn_status gn_mlp_gradients(gn_mlp *m, const float *X, const float *y, const int6
         if (B < 1 || B > m->max_bp || !X || !y || !grads) fail(GN_EINVAL, "bad batch (1 <= B <= max_batch)");
         DeviceGuard dg(m->device);
         float l = 0.0f;
-        run(m, X, y, idx, B, m->p.p, &l);
+        run(m, X, y, idx, B, m->p.p, &l, nullptr, m->stream);
         cuda_check(cudaMemcpy(grads, m->grads.p, m->n_params * 4, cudaMemcpyDeviceToHost), "D2H grads");
         if (loss) *loss = l;
     });
@@ -258,16 +273,90 @@ gn_status gn_mlp_train_step(gn_mlp *m, const float *X, const float *y, const int
         if (B < 1 || B > m->max_bp || !X || !y) fail(GN_EINVAL, "bad batch (1 <= B <= max_batch)");
         if (!(lr > 0.0f) || !(weight_decay >= 0.0f)) fail(GN_EINVAL, "bad learning rate or weight decay");
         DeviceGuard dg(m->device);
-        run(m, X, y, idx, B, m->p.p, loss);
+        run(m, X, y, idx, B, m->p.p, loss, nullptr, m->stream);
         // AdamW (beta1 0.9, beta2 0.999, eps 1e-8) on the FP32 masters
         m->adam_t += 1;
         const double t = static_cast<double>(m->adam_t);
         const float bc1 = static_cast<float>(1.0 - std::pow(0.9, t));
         const float bc2 = static_cast<float>(1.0 - std::pow(0.999, t));
         cuda_check(gn::mlp_launch_adamw(m->params.p, m->grads.p, m->m.p, m->v.p, m->n_params, lr, 0.9f, 0.999f, 1e-8f,
-                                        weight_decay, bc1, bc2, m->stream),
+                                        weight_decay, bc1, bc2, nullptr, nullptr, m->stream),
                    "AdamW");
-        refresh(m);
+        refresh(m, m->stream);
+    });
+}
+
+gn_status gn_mlp_train_epoch(gn_mlp *m, const float *X, const float *y, const int64_t *idx, int32_t n_batches,
+                             int32_t B, float lr, float weight_decay, float *losses)
+{
+    return guarded([&] {
+        check_mlp(m);
+        if (B < 1 || B > m->max_bp || !X || !y || !idx || n_batches < 0)
+            fail(GN_EINVAL, "bad batch (1 <= B <= max_batch, X, y, idx on the device)");
+        if (!(lr > 0.0f) || !(weight_decay >= 0.0f)) fail(GN_EINVAL, "bad learning rate or weight decay");
+        if (n_batches == 0) return;
+        DeviceGuard dg(m->device);
+        // AdamW bias corrections of steps adam_t + 1 .. adam_t + n_batches, as gn_mlp_train_step computes them
+        std::vector<float> bc(2 * static_cast<size_t>(n_batches));
+        for (int32_t j = 0; j < n_batches; ++j) {
+            const double t = static_cast<double>(m->adam_t + 1 + j);
+            bc[2 * j] = static_cast<float>(1.0 - std::pow(0.9, t));
+            bc[2 * j + 1] = static_cast<float>(1.0 - std::pow(0.999, t));
+        }
+        if (m->ep_bc.n < bc.size() || m->ep_losses.n < static_cast<size_t>(n_batches) || !m->ep_cursor.p) {
+            sync(m, "MLP");
+            m->ep_bc.release();
+            m->ep_losses.release();
+            m->ep_bc.alloc(bc.size(), &m->bytes);
+            m->ep_losses.alloc(n_batches, &m->bytes);
+            if (!m->ep_cursor.p) m->ep_cursor.alloc(1, &m->bytes);
+        }
+        cuda_check(cudaMemcpyAsync(m->ep_bc.p, bc.data(), bc.size() * 4, cudaMemcpyHostToDevice, m->stream), "H2D");
+        cuda_check(cudaMemsetAsync(m->ep_cursor.p, 0, 8, m->stream), "memset");
+        const gn_mlp::EpochKey key{X, y, idx, B, lr, weight_decay, m->ep_bc.p, m->ep_losses.p};
+        if (!m->ep_graph || !(key == m->ep_key)) {
+            if (m->ep_graph) {
+                cudaGraphExecDestroy(m->ep_graph);
+                m->ep_graph = nullptr;
+            }
+            // one training step, the batch picked by the device cursor
+            cudaStream_t cs;
+            cuda_check(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "cudaStreamCreate");
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                try {
+                    run(m, X, y, idx, B, m->p.p, nullptr, m->ep_cursor.p, cs);
+                    cuda_check(gn::mlp_launch_adamw(m->params.p, m->grads.p, m->m.p, m->v.p, m->n_params, lr, 0.9f,
+                                                    0.999f, 1e-8f, weight_decay, 1.0f, 1.0f, m->ep_bc.p,
+                                                    m->ep_cursor.p, cs),
+                               "AdamW");
+                    refresh(m, cs);
+                    cuda_check(gn::mlp_launch_epoch_tail(m->tmp_head.p + 2 * H + 1, B, m->ep_cursor.p, m->ep_losses.p,
+                                                         cs),
+                               "epoch tail");
+                } catch (...) {
+                    cudaStreamEndCapture(cs, &g);
+                    if (g) cudaGraphDestroy(g);
+                    cudaStreamDestroy(cs);
+                    throw;
+                }
+                e = cudaStreamEndCapture(cs, &g);
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&m->ep_graph, g, 0);
+            if (g) cudaGraphDestroy(g);
+            cudaStreamDestroy(cs);
+            cuda_check(e, "graph capture of the training step");
+            m->ep_key = key;
+        }
+        for (int32_t j = 0; j < n_batches; ++j) cuda_check(cudaGraphLaunch(m->ep_graph, m->stream), "cudaGraphLaunch");
+        m->adam_t += n_batches;
+        if (losses) {
+            cuda_check(cudaMemcpyAsync(losses, m->ep_losses.p, static_cast<size_t>(n_batches) * 4,
+                                       cudaMemcpyDeviceToHost, m->stream),
+                       "D2H losses");
+            sync(m, "MLP epoch");
+        }
     });
 }
 
@@ -279,7 +368,7 @@ gn_status gn_mlp_infer(gn_mlp *m, const float *X, int64_t B, float *p)
         DeviceGuard dg(m->device);
         for (int64_t b0 = 0; b0 < B; b0 += m->max_bp) {
             const int nb = static_cast<int>(std::min<int64_t>(m->max_bp, B - b0));
-            run(m, X + b0 * m->in_dim, nullptr, nullptr, nb, p + b0, nullptr);
+            run(m, X + b0 * m->in_dim, nullptr, nullptr, nb, p + b0, nullptr, nullptr, m->stream);
         }
     });
 }

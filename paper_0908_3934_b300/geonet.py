@@ -119,6 +119,7 @@ _SIGS = {
     "gn_mlp_get_params": ([_P, _P], C.c_int),
     "gn_mlp_gradients": ([_P, _P, _P, _P, C.c_int32, _P, C.POINTER(C.c_float)], C.c_int),
     "gn_mlp_train_step": ([_P, _P, _P, _P, C.c_int32, C.c_float, C.c_float, C.POINTER(C.c_float)], C.c_int),
+    "gn_mlp_train_epoch": ([_P, _P, _P, _P, C.c_int32, C.c_int32, C.c_float, C.c_float, _P], C.c_int),
     "gn_mlp_infer": ([_P, _P, C.c_int64, _P], C.c_int),
     "gn_mlp_synchronize": ([_P], C.c_int),
 }
@@ -529,6 +530,15 @@ class Mlp:
         check(lib().gn_mlp_train_step(self.h, _dptr(X), _dptr(y), _dptr(idx), B, lr, weight_decay,
                                       C.byref(loss) if want_loss else None))
         return loss.value if want_loss else None
+
+    def gn_mlp_train_epoch(self, X, y, idx, n_batches: int, B: int, lr: float = 1e-3, weight_decay: float = 0.0,
+                           want_losses: bool = True):
+        """n_batches AdamW steps on rows idx[j B .. (j + 1) B) (device int64), one
+        replayed graph launch per step; returns the per-step losses (numpy) or None."""
+        losses = np.zeros(n_batches, np.float32) if want_losses else None
+        check(lib().gn_mlp_train_epoch(self.h, _dptr(X), _dptr(y), _dptr(idx), n_batches, B, lr, weight_decay,
+                                       _ptr(losses) if want_losses else None))
+        return losses
 
     def gn_mlp_infer(self, X, out):
         check(lib().gn_mlp_infer(self.h, _dptr(X), X.shape[0], _dptr(out)))

@@ -55,21 +55,24 @@ def simulate_features(specs, n_samples: int = 500, device: int = 0, stream=None)
 
 
 def train(mlp: geonet.Mlp, feats, labels, epochs: int, batch: int, seed: int, lr: float = 1e-3,
-          weight_decay: float = 0.0):
+          weight_decay: float = 0.0, orders=None):
     """Minibatch AdamW over resident features: each epoch visits the samples in the
-    order netgen.shuffles(seed, ...) draws (full batches only).  Returns the mean
-    loss of each epoch."""
+    order netgen.shuffles(seed, ...) draws (full batches only), as one
+    gn_mlp_train_epoch call (`orders`: the same orders already on the device, to
+    keep drawing them out of a timed region).  Returns the mean loss of each epoch."""
     import torch
     P = feats.shape[0]
     y = labels if hasattr(labels, "data_ptr") else torch.from_numpy(np.asarray(labels, np.float32)).to(feats.device)
     losses = []
-    for order in netgen.shuffles(seed, P, epochs):
-        idx = torch.from_numpy(order).to(feats.device)
-        tot, n = 0.0, 0
-        for b0 in range(0, P - batch + 1, batch):
-            tot += mlp.gn_mlp_train_step(feats, y, idx[b0:b0 + batch], lr=lr, weight_decay=weight_decay)
-            n += 1
-        losses.append(tot / max(n, 1))
+    n_batches = P // batch
+    if orders is None:
+        orders = (torch.from_numpy(o).to(feats.device) for o in netgen.shuffles(seed, P, epochs))
+    for idx in orders:
+        if n_batches == 0:
+            losses.append(0.0)
+            continue
+        step_losses = mlp.gn_mlp_train_epoch(feats, y, idx, n_batches, batch, lr=lr, weight_decay=weight_decay)
+        losses.append(float(np.mean(step_losses.astype(np.float64))))
     return losses
 
 
