@@ -53,6 +53,10 @@ class _Net(C.Structure):
         ("p_amp", C.c_void_p),
         ("bg_threshold", C.c_uint32), ("bg_amp", C.c_double), ("bg_width", C.c_int32),
         ("bg_seed", C.c_uint64),
+        ("model", C.c_int32),
+        ("iz_C", C.c_double), ("iz_k", C.c_double), ("iz_vr", C.c_double), ("iz_vt", C.c_double),
+        ("iz_vpeak", C.c_double), ("iz_vreset", C.c_double), ("iz_a", C.c_double), ("iz_b", C.c_double),
+        ("iz_d", C.c_double), ("iz_iext", C.c_double), ("psc_a", C.c_double), ("tau_c", C.c_double),
     ]
 
 
@@ -60,6 +64,7 @@ class _Init(C.Structure):
     _fields_ = [
         ("n0", C.c_int64), ("v", C.c_void_p), ("w", C.c_void_p), ("c", C.c_void_p),
         ("bg_count", C.c_void_p), ("hist", C.c_void_p), ("hist_depth", C.c_int32),
+        ("r", C.c_void_p), ("p", C.c_void_p),
     ]
 
 
@@ -72,6 +77,7 @@ class _Out(C.Structure):
         ("snap_every", C.c_int32),
         ("snap_v", C.c_void_p), ("snap_w", C.c_void_p), ("snap_c", C.c_void_p), ("bg_count", C.c_void_p),
         ("hist_out", C.c_void_p), ("hist_out_depth", C.c_int32),
+        ("r", C.c_void_p), ("p", C.c_void_p), ("min_peak_gap", C.c_void_p),
     ]
 
 
@@ -179,6 +185,12 @@ def simulate(spec, n_steps: int, *, dense: bool = False, snap_every: int = 0,
     first_value [N], events (node, step), if ``snap_every`` > 0 state snapshots
     [n_steps // snap_every, N], and if ``hist_depth`` > 0 the final history
     ``hist[k, j]`` = v~_j(n_end - k), k < hist_depth (at most D_max + 1).
+
+    With ``spec.model == "izh"`` (Izhikevich + alpha PSC + calcium) the state is
+    absolute (v = V, w = W, c = calcium, plus r, p returned and accepted in
+    ``init``), the history holds spd(V) in {0, 1}, events are spikes, the arrival
+    of a node is its first spike, and ``min_peak_gap`` [N] is the smallest
+    |V - V_peak| seen during the run.
     """
     L = lib()
     N = spec.n_nodes
@@ -196,6 +208,8 @@ def simulate(spec, n_steps: int, *, dense: bool = False, snap_every: int = 0,
     p_amp = np.array([float(np.float32(p[3])) for p in pulses], np.float64)
     bg = spec.background
     cpl = coupling or spec.coupling
+    izh = spec.model == "izh"
+    iz = spec.izh
     net = _Net(
         n_nodes=N, n_edges=E, src=_ptr(src), dst=_ptr(dst), weight=_ptr(wgt), delay=_ptr(D),
         dt_ms=spec.dt_ms, a=fhn["a"], b=fhn["b"], c=fhn["c"], e=fhn["e"], f=fhn["f"], g=fhn["g"],
@@ -208,6 +222,10 @@ def simulate(spec, n_steps: int, *, dense: bool = False, snap_every: int = 0,
         bg_amp=float(np.float32(bg["amp"])) if bg else 0.0,
         bg_width=ms_to_step(bg["dur_ms"], spec.dt_ms) if bg else 0,
         bg_seed=bg["seed"] if bg else 0,
+        model=1 if izh else 0,
+        iz_C=iz["C"], iz_k=iz["k"], iz_vr=iz["vr"], iz_vt=iz["vt"], iz_vpeak=iz["vpeak"],
+        iz_vreset=iz["vreset"], iz_a=iz["a"], iz_b=iz["b"], iz_d=iz["d"], iz_iext=iz["i_ext"],
+        psc_a=iz["psc_a"], tau_c=iz["tau_c"],
     )
     v = np.zeros(N)
     w = np.zeros(N)
@@ -227,7 +245,11 @@ def simulate(spec, n_steps: int, *, dense: bool = False, snap_every: int = 0,
     sc = np.zeros((n_snap, N)) if n_snap else None
     bgc = np.zeros(N, np.int32)
     hout = np.zeros((hist_depth, N)) if hist_depth > 0 else None
+    r_out = np.zeros(N)
+    p_out = np.zeros(N)
+    gap = np.zeros(N)
     out = _Out(v=_ptr(v), w=_ptr(w), c=_ptr(c), y=_ptr(y), y_clean=_ptr(yc), bg_count=_ptr(bgc),
+               r=_ptr(r_out), p=_ptr(p_out), min_peak_gap=_ptr(gap) if izh else None,
                hist_out=_ptr(hout), hist_out_depth=hist_depth,
                first_arrival=_ptr(fa), first_value=_ptr(fv), ev_node=_ptr(evn), ev_step=_ptr(evs),
                ev_cap=ev_cap, ev_count=0, snap_every=snap_every if n_snap else 0,
@@ -242,7 +264,8 @@ def simulate(spec, n_steps: int, *, dense: bool = False, snap_every: int = 0,
         hist = np.ascontiguousarray(init["hist"], np.float64)
         ini = _Init(n0=n0, v=arr(init["v"], np.float64), w=arr(init["w"], np.float64),
                     c=arr(init["c"], np.float64), bg_count=arr(init.get("bg_count"), np.int32),
-                    hist=_ptr(hist), hist_depth=hist.shape[0])
+                    hist=_ptr(hist), hist_depth=hist.shape[0],
+                    r=arr(init.get("r"), np.float64), p=arr(init.get("p"), np.float64))
         rc = L.orc_simulate_from(C.byref(net), C.byref(ini), n_steps, C.byref(out))
     else:
         fn = L.orc_simulate_dense if dense else L.orc_simulate
@@ -253,4 +276,5 @@ def simulate(spec, n_steps: int, *, dense: bool = False, snap_every: int = 0,
     return dict(v=v, w=w, c=c, y=y, y_clean=yc, first_arrival=fa, first_value=fv,
                 ev_node=evn[:ne].copy(), ev_step=evs[:ne].copy(), ev_count=out.ev_count,
                 snap_v=sv, snap_w=sw, snap_c=sc, bg_count=bgc, hist=hout, n_end=n0 + n_steps,
-                delay=D, rest=rest_point(fhn))
+                delay=D, rest=None if izh else rest_point(fhn), r=r_out, p=p_out,
+                min_peak_gap=gap if izh else None)

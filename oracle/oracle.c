@@ -38,6 +38,20 @@
  *   - Events: upward crossing of V through theta (V(n) < theta <= V(n+1)).
  *   - Arrival: first step at which v~ becomes non-zero.
  *
+ * Second node model (model = 1): the Izhikevich simple model with an alpha-function
+ * post-synaptic current and the calcium readout, all in their forward-Euler forms
+ * (Eq. izsimple / izpsc, Eq. alphapsc, Eq. spd, Eq. casimple, Sec. 3.1-3.3):
+ *       V' = V + dt/C [k (V - Vr)(V - Vt) - W + r + U + I]   if V < V_peak, else V_reset
+ *       W' = W + dt a (b (V - Vr) - W)                       if V < V_peak, else W + d
+ *       r' = r + dt p
+ *       p' = p + dt (-a_s^2 r - 2 a_s p + S),   S_j = sum_{i -> j} w_ij spd(V_i(t - tau_ij))
+ *       c' = c + dt (-c / tau_c + spd(V)),      spd(V) = 1 if V >= V_peak else 0
+ *       y  = gain c' + offset + sigma xi
+ *   The history holds spd(V) (the only quantity another node reads, Sec. 3.2.1); the
+ *   state V, W, r, p, c is absolute; the model starts from V = Vr, W = r = p = c = 0
+ *   (the fixed point without input), with no spike before t = 0.  Events are spikes
+ *   (V(n+1) >= V_peak) and the arrival of a node is its first spike.
+ *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11), written from the
  * published definition; Box-Muller (1958) for the Gaussian.
  *
@@ -212,6 +226,11 @@ typedef struct {
     double bg_amp;
     int32_t bg_width;
     uint64_t bg_seed;
+    /* node model: 0 = FitzHugh-Nagumo (above), 1 = Izhikevich + alpha PSC + calcium */
+    int32_t model;
+    double iz_C, iz_k, iz_vr, iz_vt, iz_vpeak, iz_vreset, iz_a, iz_b, iz_d, iz_iext;
+    double psc_a;            /* alpha-function rate a_s (1/ms) */
+    double tau_c;            /* calcium removal time (ms) */
 } orc_net;
 
 typedef struct {
@@ -229,6 +248,8 @@ typedef struct {
     int32_t *bg_count;        /* [N] final background counters (or NULL) */
     double *hist_out;         /* [hist_out_depth * N]: v~_j(n_end - k), k < hist_out_depth (or NULL) */
     int32_t hist_out_depth;   /* <= D_max + 1 */
+    double *r, *p;            /* model 1: [N] final PSC state (or NULL) */
+    double *min_peak_gap;     /* model 1: [N] min over the run of |V - V_peak| (or NULL) */
 } orc_out;
 
 /* One Euler step of one node (the FHN transition about the rest point).
@@ -248,6 +269,24 @@ static void node_step(const orc_net *net, double v_rest, double v, double w, dou
     double wn = w + dt * dw;
     double cn = c + (dt / net->tau_ms) * (vn - c);
     *v1 = vn; *w1 = wn; *c1 = cn;
+}
+
+/* One Euler step of the Izhikevich + alpha-PSC + calcium node (model 1). */
+static void izh_step(const orc_net *net, double V, double W, double r, double p, double c, double S, double U,
+                     double *V1, double *W1, double *r1, double *p1, double *c1)
+{
+    double dt = net->dt_ms;
+    double spike = V >= net->iz_vpeak ? 1.0 : 0.0;
+    if (V < net->iz_vpeak) {
+        *V1 = V + dt / net->iz_C * (net->iz_k * (V - net->iz_vr) * (V - net->iz_vt) - W + r + U + net->iz_iext);
+        *W1 = W + dt * net->iz_a * (net->iz_b * (V - net->iz_vr) - W);
+    } else {
+        *V1 = net->iz_vreset;
+        *W1 = W + net->iz_d;
+    }
+    *r1 = r + dt * p;
+    *p1 = p + dt * (-net->psc_a * net->psc_a * r - 2.0 * net->psc_a * p + S);
+    *c1 = c + dt * (-c / net->tau_c + spike);
 }
 
 static double stimulus(const orc_net *net, int32_t j, int64_t n, int32_t *bg_count)
@@ -297,6 +336,7 @@ typedef struct {
     const int32_t *bg_count;
     const double *hist;
     int32_t hist_depth;
+    const double *r, *p;      /* model 1: PSC state (NULL = 0) */
 } orc_init;
 
 static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense,
@@ -304,10 +344,12 @@ static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense
 {
     int32_t N = net->n_nodes;
     int64_t E = net->n_edges;
-    if (N <= 0 || E < 0 || n_steps < 0 || !(net->dt_ms > 0.0) || !(net->tau_ms > 0.0))
+    const int izh = net->model == 1;
+    if (N <= 0 || E < 0 || n_steps < 0 || !(net->dt_ms > 0.0) || (net->model != 0 && !izh))
         return ORC_EINVAL;
-    double v_rest, w_rest;
-    if (orc_rest_point(net->a, net->b, net->c, net->f, net->g, net->i_ext, &v_rest, &w_rest))
+    if (izh ? !(net->iz_C > 0.0) || !(net->tau_c > 0.0) : !(net->tau_ms > 0.0)) return ORC_EINVAL;
+    double v_rest = 0.0, w_rest = 0.0;
+    if (!izh && orc_rest_point(net->a, net->b, net->c, net->f, net->g, net->i_ext, &v_rest, &w_rest))
         return ORC_EINVAL;
     int32_t dmax = 1;
     for (int64_t e = 0; e < E; ++e) {
@@ -330,16 +372,26 @@ static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense
     double *c = (double *)calloc((size_t)N, sizeof(double));
     double *S = (double *)calloc((size_t)N, sizeof(double));
     int32_t *bgc = (int32_t *)calloc((size_t)N, sizeof(int32_t));
-    if (!h.buf || !v || !w || !c || !S || !bgc) {
-        free(h.buf); free(v); free(w); free(c); free(S); free(bgc);
+    double *r = (double *)calloc((size_t)N, sizeof(double));
+    double *p = (double *)calloc((size_t)N, sizeof(double));
+    if (!h.buf || !v || !w || !c || !S || !bgc || !r || !p) {
+        free(h.buf); free(v); free(w); free(c); free(S); free(bgc); free(r); free(p);
         return ORC_ENOMEM;
     }
+    if (izh)
+        for (int32_t j = 0; j < N; ++j) v[j] = net->iz_vr;
+    if (out->min_peak_gap)
+        for (int32_t j = 0; j < N; ++j) out->min_peak_gap[j] = INFINITY;
     if (init) {
         for (int32_t j = 0; j < N; ++j) {
             v[j] = init->v[j];
             w[j] = init->w[j];
             c[j] = init->c[j];
             bgc[j] = init->bg_count ? init->bg_count[j] : 0;
+            if (izh) {
+                r[j] = init->r ? init->r[j] : 0.0;
+                p[j] = init->p ? init->p[j] : 0.0;
+            }
         }
         for (int64_t k = 1; k < h.depth && k < init->hist_depth; ++k)
             if (n0 - k >= 0)
@@ -354,13 +406,13 @@ static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense
     int64_t snap_idx = 0;
 
     for (int64_t n = n0; n < n0 + n_steps; ++n) {
-        /* record v~(n) before anything reads the history of this step */
-        for (int32_t j = 0; j < N; ++j) hist_put(&h, n, j, v[j]);
+        /* record v~(n) (model 1: spd(V(n))) before anything reads the history of this step */
+        for (int32_t j = 0; j < N; ++j) hist_put(&h, n, j, izh ? (v[j] >= net->iz_vpeak ? 1.0 : 0.0) : v[j]);
         /* S_j(n) = sum over edges i -> j of w_ij * v_i(n - D_ij) */
         for (int32_t j = 0; j < N; ++j) S[j] = 0.0;
         for (int64_t e = 0; e < E; ++e) {
             double past = hist_get(&h, n - net->delay[e], net->src[e]);
-            if (net->coupling == 1) past = v_rest + past;
+            if (!izh && net->coupling == 1) past = v_rest + past;
             S[net->dst[e]] += net->weight[e] * past;
         }
         int sample = ((n + 1) % net->sample_every) == 0;
@@ -369,6 +421,35 @@ static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense
         for (int32_t j = 0; j < N; ++j) {
             double U = stimulus(net, j, n, bgc);
             double v1, w1, c1;
+            if (izh) {
+                double r1, p1;
+                izh_step(net, v[j], w[j], r[j], p[j], c[j], S[j], U, &v1, &w1, &r1, &p1, &c1);
+                r[j] = r1;
+                p[j] = p1;
+                if (out->min_peak_gap) {
+                    double gap = fabs(v1 - net->iz_vpeak);
+                    if (gap < out->min_peak_gap[j]) out->min_peak_gap[j] = gap;
+                }
+                int spike = v1 >= net->iz_vpeak;
+                if (spike) {
+                    if (out->ev_count < out->ev_cap) {
+                        out->ev_node[out->ev_count] = j;
+                        out->ev_step[out->ev_count] = n + 1;
+                    }
+                    out->ev_count++;
+                }
+                if (out->first_arrival && out->first_arrival[j] < 0 && spike) {
+                    out->first_arrival[j] = (int32_t)(n + 1);
+                    if (out->first_value) out->first_value[j] = v1;
+                }
+                if (sample) {
+                    double clean = net->gain * c1 + net->offset;
+                    if (out->y_clean) out->y_clean[k_out * N + j] = clean;
+                    if (out->y) out->y[k_out * N + j] = clean + net->sigma * orc_gauss(net->obs_seed, (uint32_t)j, k);
+                }
+                v[j] = v1; w[j] = w1; c[j] = c1;
+                continue;
+            }
             node_step(net, v_rest, v[j], w[j], c[j], S[j], U, &v1, &w1, &c1);
             /* event: V crosses theta upward between n and n+1 */
             if (v_rest + v[j] < v_theta && v_rest + v1 >= v_theta) {
@@ -400,13 +481,17 @@ static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense
     memcpy(out->w, w, sizeof(double) * (size_t)N);
     memcpy(out->c, c, sizeof(double) * (size_t)N);
     if (out->bg_count) memcpy(out->bg_count, bgc, sizeof(int32_t) * (size_t)N);
+    if (out->r) memcpy(out->r, r, sizeof(double) * (size_t)N);
+    if (out->p) memcpy(out->p, p, sizeof(double) * (size_t)N);
     if (out->hist_out) {
         int64_t n_end = n0 + n_steps;
         for (int32_t k = 0; k < out->hist_out_depth; ++k)
-            for (int32_t j = 0; j < N; ++j)
-                out->hist_out[(int64_t)k * N + j] = (k == 0) ? v[j] : hist_get(&h, n_end - k, j);
+            for (int32_t j = 0; j < N; ++j) {
+                double now = izh ? (v[j] >= net->iz_vpeak ? 1.0 : 0.0) : v[j];
+                out->hist_out[(int64_t)k * N + j] = (k == 0) ? now : hist_get(&h, n_end - k, j);
+            }
     }
-    free(h.buf); free(v); free(w); free(c); free(S); free(bgc);
+    free(h.buf); free(v); free(w); free(c); free(S); free(bgc); free(r); free(p);
     return ORC_OK;
 }
 

@@ -46,6 +46,12 @@ from scipy.spatial import cKDTree
 
 FHN_CLASSIC = dict(a=1.0, b=1.0 / 3.0, c=1.0, e=0.08, f=0.7, g=0.8, i_ext=0.0)
 OBS_DEFAULT = dict(tau_ms=5.0, sample_every=20, gain=1.0, offset=0.0, sigma=0.05, seed=2)
+# Izhikevich simple model (Sec. 3.1, Eq. izsimple) with regular-spiking cortical
+# parameters -- C pF, k nS/mV, mV, a 1/ms, b nS, d pA -- an alpha-function PSC of rate
+# psc_a 1/ms (Eq. alphapsc) and a calcium removal time tau_c ms (Eq. casimple).  The
+# paper gives the model, not these numbers.
+IZH_RS = dict(C=100.0, k=0.7, vr=-60.0, vt=-40.0, vpeak=35.0, vreset=-50.0, a=0.03, b=-2.0, d=100.0,
+              i_ext=0.0, psc_a=0.2, tau_c=20.0)
 
 
 @dataclasses.dataclass
@@ -68,6 +74,8 @@ class NetSpec:
     ring_depth: int = 0             # 0 = smallest power of two that holds the delays
     radius: float = 0.0             # radius the edges were drawn within (candidate pairs), 0 = unknown
     name: str = ""
+    model: str = "fhn"              # "fhn" or "izh" (Izhikevich + alpha PSC + calcium)
+    izh: dict = dataclasses.field(default_factory=lambda: dict(IZH_RS))
 
     @property
     def n_nodes(self) -> int:
@@ -80,6 +88,21 @@ class NetSpec:
     @property
     def dim(self) -> int:
         return int(self.pos.shape[1])
+
+
+def izhikevich(spec: "NetSpec", w_scale: float = 2000.0, pulse_amp: float = 2500.0, obs_gain: float = 20.0):
+    """The same network and controls with Izhikevich + alpha-PSC nodes: weights
+    scaled to PSC units (a spike through an edge of weight w adds dt w to p, so r
+    peaks at dt w / (a_s e): 2000 x a weight of 0.3 gives 55 pA at dt = 0.05 ms),
+    pulses and background pulses of pulse_amp pA (2 ms at 2500 pA make a resting
+    node spike), and the calcium readout scaled by obs_gain (one spike adds dt to c).
+    With these defaults the 2.5 %-hub nets fire near their 5 Hz background; the
+    tiny net needs a scale near 7000 before its spikes propagate."""
+    return dataclasses.replace(
+        spec, model="izh", izh=dict(IZH_RS), weight=(np.asarray(spec.weight) * w_scale).astype(np.float32),
+        pulses=[(j, t0, t1, pulse_amp) for (j, t0, t1, _) in spec.pulses],
+        background=None if spec.background is None else dict(spec.background, amp=pulse_amp),
+        obs=dict(spec.obs, gain=obs_gain), name=spec.name + "_izh")
 
 
 def _signed_lognormal(rng, n, mu=-2.0, sigma=0.5, neg_frac=0.2):
