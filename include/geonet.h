@@ -67,6 +67,25 @@ typedef struct {
     double a, b, c, e, f, g, i_ext;
 } gn_fhn_params;
 
+/* Node models (Sec. 3.1): FitzHugh-Nagumo (the parameters above), or the
+ * Izhikevich simple model with an alpha-function post-synaptic current and the
+ * calcium readout (Eq. izsimple, izpsc, alphapsc, spd, casimple; Sec. 3.1-3.3),
+ * forward Euler:
+ *   V' = V + dt/C [k (V - v_r)(V - v_t) - W + r + U + i_ext]   if V < v_peak, else v_reset
+ *   W' = W + dt a (b (V - v_r) - W)                            if V < v_peak, else W + d
+ *   r' = r + dt p,   p' = p + dt (-psc_a^2 r - 2 psc_a p + S),
+ *   S_j = sum_{i -> j} w_ij spd(V_i(t - tau_ij)),  spd(V) = 1 if V >= v_peak else 0
+ *   c' = c + dt (-c / tau_c + spd(V)),   y = gain c' + offset + sigma xi.
+ * Units are the caller's (the usual: pF, nS/mV, mV, 1/ms, nS, pA, ms).  The state
+ * starts at V = v_r, W = r = p = c = 0 with no spike before t = 0; the history ring
+ * holds spd(V); events are spikes (V >= v_peak) and a node's arrival is its first
+ * spike.  The coupling field is ignored; the batched form does not take this model
+ * (GN_EINVAL). */
+enum { GN_MODEL_FHN = 0, GN_MODEL_IZH = 1 };
+typedef struct {
+    double C, k, v_r, v_t, v_peak, v_reset, a, b, d, i_ext, psc_a, tau_c;
+} gn_izh_params;
+
 /* Readout (Sec. 3.3): c~' = c~ + (dt/tau_ms)(v~' - c~) every step; every
  * sample_every steps y = gain (V* + c~) + offset + sigma xi, xi ~ N(0, 1) drawn
  * from Philox4x32-10 keyed by `seed` with counter (node, sample, 2). */
@@ -115,6 +134,8 @@ typedef struct {
                                     explicitly chosen kernel 1 or 3 (default 0) */
     void *cuda_stream;           /* cudaStream_t to run on; NULL: the library makes its own */
     int32_t device;              /* CUDA device ordinal */
+    int32_t model;               /* GN_MODEL_FHN (0) or GN_MODEL_IZH (1) */
+    gn_izh_params izh;           /* used when model == GN_MODEL_IZH (C > 0, tau_c > 0, all finite) */
 } gn_net_desc;
 
 /* A pulse of amplitude amp on node over [t_on_ms, t_off_ms): the steps
@@ -211,6 +232,13 @@ GN_API gn_status gn_get_state(gn_net *net, float *v, float *w, float *c, int32_t
  * cleared and the observation cursor moves to the first sample after `step`. */
 GN_API gn_status gn_set_state(gn_net *net, const float *hist, int32_t depth, const float *w, const float *c,
                               const int32_t *bg_count, int64_t step);
+
+/* Izhikevich model only (GN_EINVAL otherwise): V, the PSC variables r and p, in
+ * caller node order (any pointer may be NULL).  gn_get_state / gn_set_state carry
+ * W and calcium in w and c, and the history is spd(V) in {0, 1}; gn_get_state's v is
+ * V as well. */
+GN_API gn_status gn_get_izh_state(gn_net *net, float *V, float *r, float *p);
+GN_API gn_status gn_set_izh_state(gn_net *net, const float *V, const float *r, const float *p);
 
 /* History: out[k][j] = v~_j(step - k), k = 0..depth-1, depth <= ring_depth. */
 GN_API gn_status gn_get_history(gn_net *net, float *out, int32_t depth);

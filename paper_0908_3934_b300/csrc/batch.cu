@@ -416,6 +416,7 @@ gn_status gn_batch_create(const gn_net_desc *descs, int32_t n_nets, gn_batch **o
         for (int i = 0; i < n_nets; ++i) {
             gnrt::validate_desc(descs + i);
             if (descs[i].device != descs[0].device) fail(GN_EINVAL, "all networks of a batch share one device");
+            if (descs[i].model != GN_MODEL_FHN) fail(GN_EINVAL, "the batched form takes FitzHugh-Nagumo networks only");
         }
         b = new gn_batch();
         b->device = descs[0].device;

@@ -77,6 +77,13 @@ struct StepArgs {
     int32_t st_ucap;         // gather slots of a CTA's shared memory (largest padded gather count)
     int32_t st_xcap;         // entry slots of a CTA's shared memory (largest entry count)
     uint32_t wait_limit;     // polls of a bounded mbarrier wait before it reports kStatusTimeout
+    // node model: 0 FitzHugh-Nagumo (fields above), 1 Izhikevich + alpha PSC + calcium,
+    // whose ring holds spd(V) and whose state is iz_v (V), wc (W, calcium), rp (r, p)
+    int32_t model;
+    float iz_dtc, iz_k, iz_vr, iz_vt, iz_vpeak, iz_vreset, iz_dta, iz_b, iz_d, iz_iext;
+    float ps_a2, ps_2a, ca_q;  // PSC a^2, 2a; calcium 1 / tau_c
+    float *iz_v;
+    float2 *rp;
 };
 
 constexpr uint32_t kDefaultWaitLimit = 1u << 22;

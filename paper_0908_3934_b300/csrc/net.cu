@@ -56,8 +56,9 @@ struct gn_net {
     std::vector<int32_t> inv;         // caller -> internal
     std::vector<int32_t> delay;       // caller edge order
     size_t bytes = 0;
-    DevArray<float> ring, ew, bias, obs, p_amp;
-    DevArray<float2> wc;
+    DevArray<float> ring, ew, bias, obs, p_amp, iz_v;
+    DevArray<float2> wc, rp;
+    int32_t model = GN_MODEL_FHN;
     DevArray<uint8_t> ekey;
     DevArray<int32_t> row_ptr, blk, bgc, d_perm, p_node, ev_node, d_npulses;
     int64_t pulse_cap = 0;
@@ -101,8 +102,9 @@ struct gn_net {
     ~gn_net()
     {
         if (graph) cudaGraphExecDestroy(graph);
-        for (auto *a : {&ring, &ew, &bias, &obs, &p_amp}) a->release();
+        for (auto *a : {&ring, &ew, &bias, &obs, &p_amp, &iz_v}) a->release();
         wc.release();
+        rp.release();
         ekey.release();
         for (auto *a : {&row_ptr, &blk, &bgc, &d_perm, &p_node, &ev_node, &d_npulses}) a->release();
         for (auto *a : {&first, &p_on, &p_off, &ev_step, &d_step}) a->release();
@@ -312,8 +314,8 @@ void autotune(gn_net *net)
     }
     const int32_t N = net->N;
     size_t scratch_bytes = 0;
-    DevArray<float> ring, obs;
-    DevArray<float2> wc;
+    DevArray<float> ring, obs, iz_v;
+    DevArray<float2> wc, rp;
     DevArray<int32_t> bgc, evn;
     DevArray<int64_t> first, evs, dstep;
     DevArray<unsigned long long> evc;
@@ -321,7 +323,7 @@ void autotune(gn_net *net)
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     auto cleanup = [&] {
         ring.release(); obs.release(); wc.release(); bgc.release(); evn.release(); first.release();
-        evs.release(); dstep.release(); evc.release(); status.release();
+        evs.release(); dstep.release(); evc.release(); status.release(); iz_v.release(); rp.release();
         if (t0) cudaEventDestroy(t0);
         if (t1) cudaEventDestroy(t1);
     };
@@ -337,6 +339,12 @@ void autotune(gn_net *net)
         evc.alloc(1, &scratch_bytes);
         dstep.alloc(1, &scratch_bytes);
         status.alloc(1, &scratch_bytes);
+        if (net->model == GN_MODEL_IZH) {  // the Izhikevich state too, from the net's own values
+            iz_v.alloc(N, &scratch_bytes);
+            rp.alloc(N, &scratch_bytes);
+            cuda_check(cudaMemcpyAsync(iz_v.p, net->iz_v.p, N * 4ull, cudaMemcpyDeviceToDevice, net->stream), "D2D");
+            cuda_check(cudaMemcpyAsync(rp.p, net->rp.p, N * 8ull, cudaMemcpyDeviceToDevice, net->stream), "D2D");
+        }
         cuda_check(cudaMemsetAsync(ring.p, 0, ring.n * 4, net->stream), "memset");
         cuda_check(cudaMemsetAsync(wc.p, 0, wc.n * 8, net->stream), "memset");
         cuda_check(cudaMemsetAsync(bgc.p, 0, bgc.n * 4, net->stream), "memset");
@@ -370,6 +378,8 @@ void autotune(gn_net *net)
             a.ev_cap = 1024;
             a.d_step = dstep.p;
             a.status = status.p;
+            a.iz_v = iz_v.p;
+            a.rp = rp.p;
             const int warm = 3, timed = 8;
             for (int k = 0; k < warm; ++k)
                 cuda_check(launch_kind(a, net, k, net->stream), "autotune launch");
@@ -567,6 +577,12 @@ gn_status gn_net_create(const gn_net_desc *desc, gn_net **out)
         cuda_check(cudaMemset(net->ev_count.p, 0, 8), "memset");
         cuda_check(cudaMemset(net->d_step.p, 0, 8), "memset");
         cuda_check(cudaMemset(net->d_npulses.p, 0, 4), "memset");
+        net->model = desc->model;
+        if (net->model == GN_MODEL_IZH) {
+            net->iz_v.upload(std::vector<float>(N, static_cast<float>(desc->izh.v_r)), &net->bytes);
+            net->rp.alloc(N, &net->bytes);
+            cuda_check(cudaMemset(net->rp.p, 0, net->rp.n * 8), "memset");
+        }
 
         gn::StepArgs &a = net->args;
         gnrt::fill_step_params(desc, h, a);
@@ -588,6 +604,8 @@ gn_status gn_net_create(const gn_net_desc *desc, gn_net **out)
         a.ev_cap = net->ev_cap;
         a.d_step = net->d_step.p;
         a.status = net->status.p;
+        a.iz_v = net->iz_v.p;
+        a.rp = net->rp.p;
 
         // the kernel is fixed now or timed on the first gn_step (kind 0)
         if (desc->step_kernel == 0 || desc->step_kernel == 3) net->host = std::make_unique<gnrt::HostNet>(std::move(h));
@@ -773,9 +791,9 @@ gn_status gn_get_state(gn_net *net, float *v, float *w, float *c, int32_t *bg_co
         const int32_t N = net->N;
         std::vector<float> tmp(N);
         if (v) {
-            cuda_check(cudaMemcpy(tmp.data(), net->ring.p + (net->step & (net->R - 1)) * net->stride, N * 4,
-                                  cudaMemcpyDeviceToHost),
-                       "D2H v");
+            const float *src = net->model == GN_MODEL_IZH ? net->iz_v.p
+                                                          : net->ring.p + (net->step & (net->R - 1)) * net->stride;
+            cuda_check(cudaMemcpy(tmp.data(), src, N * 4, cudaMemcpyDeviceToHost), "D2H v");
             permute_rows_to_caller(net, tmp.data(), v, 1);
         }
         if (w || c) {
@@ -827,6 +845,55 @@ gn_status gn_set_state(gn_net *net, const float *hist, int32_t depth, const floa
         cuda_check(cudaMemcpy(net->d_step.p, &step, 8, cudaMemcpyHostToDevice), "H2D step");
         net->step = step;
         net->read_cursor = step / net->sample_every;
+    });
+}
+
+gn_status gn_get_izh_state(gn_net *net, float *V, float *r, float *p)
+{
+    return guarded([&] {
+        check_net(net);
+        if (net->model != GN_MODEL_IZH) fail(GN_EINVAL, "the network does not use the Izhikevich model");
+        DeviceGuard dg(net->device);
+        sync(net);
+        const int32_t N = net->N;
+        if (V) {
+            std::vector<float> t(N);
+            cuda_check(cudaMemcpy(t.data(), net->iz_v.p, N * 4ull, cudaMemcpyDeviceToHost), "D2H V");
+            permute_rows_to_caller(net, t.data(), V, 1);
+        }
+        if (r || p) {
+            std::vector<float2> t(N);
+            cuda_check(cudaMemcpy(t.data(), net->rp.p, N * 8ull, cudaMemcpyDeviceToHost), "D2H rp");
+            for (int32_t i = 0; i < N; ++i) {
+                if (r) r[net->perm[i]] = t[i].x;
+                if (p) p[net->perm[i]] = t[i].y;
+            }
+        }
+    });
+}
+
+gn_status gn_set_izh_state(gn_net *net, const float *V, const float *r, const float *p)
+{
+    return guarded([&] {
+        check_net(net);
+        if (net->model != GN_MODEL_IZH) fail(GN_EINVAL, "the network does not use the Izhikevich model");
+        DeviceGuard dg(net->device);
+        sync(net);
+        const int32_t N = net->N;
+        if (V) {
+            std::vector<float> t(N);
+            for (int32_t j = 0; j < N; ++j) t[net->inv[j]] = V[j];
+            cuda_check(cudaMemcpy(net->iz_v.p, t.data(), N * 4ull, cudaMemcpyHostToDevice), "H2D V");
+        }
+        if (r || p) {
+            std::vector<float2> t(N);
+            cuda_check(cudaMemcpy(t.data(), net->rp.p, N * 8ull, cudaMemcpyDeviceToHost), "D2H rp");
+            for (int32_t j = 0; j < N; ++j) {
+                if (r) t[net->inv[j]].x = r[j];
+                if (p) t[net->inv[j]].y = p[j];
+            }
+            cuda_check(cudaMemcpy(net->rp.p, t.data(), N * 8ull, cudaMemcpyHostToDevice), "H2D rp");
+        }
     });
 }
 
@@ -904,7 +971,8 @@ gn_status gn_save_state(gn_net *net, void *buf, size_t cap, size_t *used)
     return guarded([&] {
         check_net(net);
         const size_t N = net->N, RS = net->ring.n;
-        const size_t need = sizeof(CkptHeader) + RS * 4 + N * 8 + N * 4 + N * 8;
+        const size_t extra = net->model == GN_MODEL_IZH ? N * 12 : 0;  // V, (r, p)
+        const size_t need = sizeof(CkptHeader) + RS * 4 + N * 8 + N * 4 + N * 8 + extra;
         if (used) *used = need;
         if (!buf) return;
         if (cap < need) fail(GN_ERANGE, "checkpoint buffer too small (%zu < %zu)", cap, need);
@@ -921,6 +989,12 @@ gn_status gn_save_state(gn_net *net, void *buf, size_t cap, size_t *used)
         cuda_check(cudaMemcpy(p, net->bgc.p, N * 4, cudaMemcpyDeviceToHost), "D2H bg");
         p += N * 4;
         cuda_check(cudaMemcpy(p, net->first.p, N * 8, cudaMemcpyDeviceToHost), "D2H first");
+        p += N * 8;
+        if (extra) {
+            cuda_check(cudaMemcpy(p, net->iz_v.p, N * 4, cudaMemcpyDeviceToHost), "D2H V");
+            p += N * 4;
+            cuda_check(cudaMemcpy(p, net->rp.p, N * 8, cudaMemcpyDeviceToHost), "D2H rp");
+        }
     });
 }
 
@@ -930,7 +1004,8 @@ gn_status gn_load_state(gn_net *net, const void *buf, size_t size)
         check_net(net);
         if (!buf) fail(GN_EINVAL, "buf is NULL");
         const size_t N = net->N, RS = net->ring.n;
-        const size_t need = sizeof(CkptHeader) + RS * 4 + N * 8 + N * 4 + N * 8;
+        const size_t extra = net->model == GN_MODEL_IZH ? N * 12 : 0;
+        const size_t need = sizeof(CkptHeader) + RS * 4 + N * 8 + N * 4 + N * 8 + extra;
         if (size < need) fail(GN_EINVAL, "checkpoint is truncated");
         CkptHeader h;
         std::memcpy(&h, buf, sizeof h);
@@ -945,6 +1020,12 @@ gn_status gn_load_state(gn_net *net, const void *buf, size_t size)
         cuda_check(cudaMemcpy(net->bgc.p, p, N * 4, cudaMemcpyHostToDevice), "H2D bg");
         p += N * 4;
         cuda_check(cudaMemcpy(net->first.p, p, N * 8, cudaMemcpyHostToDevice), "H2D first");
+        p += N * 8;
+        if (extra) {
+            cuda_check(cudaMemcpy(net->iz_v.p, p, N * 4, cudaMemcpyHostToDevice), "H2D V");
+            p += N * 4;
+            cuda_check(cudaMemcpy(net->rp.p, p, N * 8, cudaMemcpyHostToDevice), "H2D rp");
+        }
         net->step = h.step;
         net->read_cursor = h.step / net->sample_every;
         cuda_check(cudaMemcpy(net->d_step.p, &h.step, 8, cudaMemcpyHostToDevice), "H2D step");

@@ -115,6 +115,15 @@ void validate_desc(const gn_net_desc *d)
             if (!(s > 0.0) || !std::isfinite(s)) fail(GN_EINVAL, "edge %lld: speed must be positive", (long long)e);
         }
     }
+    if (d->model != GN_MODEL_FHN && d->model != GN_MODEL_IZH) fail(GN_EINVAL, "unknown node model");
+    if (d->model == GN_MODEL_IZH) {
+        const gn_izh_params &z = d->izh;
+        for (double x : {z.C, z.k, z.v_r, z.v_t, z.v_peak, z.v_reset, z.a, z.b, z.d, z.i_ext, z.psc_a, z.tau_c})
+            if (!std::isfinite(x)) fail(GN_EINVAL, "Izhikevich parameters must be finite");
+        if (!(z.C > 0.0) || !(z.tau_c > 0.0) || z.psc_a < 0.0)
+            fail(GN_EINVAL, "Izhikevich parameters need C > 0, tau_c > 0, psc_a >= 0");
+        return;
+    }
     double vr, wr;
     if (!rest_point(d->fhn, &vr, &wr))
         fail(GN_EINVAL, "FHN parameters have no unique rest point (need g > 0, b > 0, a < c/g)");
@@ -266,7 +275,13 @@ void host_build(const gn_net_desc *d, std::vector<int32_t> delay, int64_t n_clam
     h.E = d->n_edges;
     h.delay = std::move(delay);
     h.n_clamped = n_clamped;
-    rest_point(d->fhn, &h.v_rest, &h.w_rest);
+    h.model = d->model;
+    if (d->model == GN_MODEL_IZH) {
+        h.v_rest = d->izh.v_r;  // the state without input: V = v_r, W = 0
+        h.w_rest = 0.0;
+    } else {
+        rest_point(d->fhn, &h.v_rest, &h.w_rest);
+    }
     const int32_t N = h.N;
     const int64_t E = h.E;
     int32_t dmax = 1, dmin = E ? INT32_MAX : 1;
@@ -326,7 +341,7 @@ void host_build(const gn_net_desc *d, std::vector<int32_t> delay, int64_t n_clam
         }
         h.w[p] = d->weight[e];
     }
-    if (d->coupling == GN_COUPLE_RAW) {
+    if (d->coupling == GN_COUPLE_RAW && d->model == GN_MODEL_FHN) {
         h.bias.assign(N, 0.0f);
         for (int32_t r = 0; r < N; ++r) {
             double sum = 0.0;
@@ -399,6 +414,24 @@ void fill_step_params(const gn_net_desc *d, const HostNet &h, gn::StepArgs &a)
     a.bg_amp = 0.0f;
     a.bg_width = 0;
     a.bg_seed = 0;
+    a.model = d->model;
+    if (d->model == GN_MODEL_IZH) {
+        const gn_izh_params &z = d->izh;
+        a.iz_dtc = static_cast<float>(d->dt_ms / z.C);
+        a.iz_k = static_cast<float>(z.k);
+        a.iz_vr = static_cast<float>(z.v_r);
+        a.iz_vt = static_cast<float>(z.v_t);
+        a.iz_vpeak = static_cast<float>(z.v_peak);
+        a.iz_vreset = static_cast<float>(z.v_reset);
+        a.iz_dta = static_cast<float>(d->dt_ms * z.a);
+        a.iz_b = static_cast<float>(z.b);
+        a.iz_d = static_cast<float>(z.d);
+        a.iz_iext = static_cast<float>(z.i_ext);
+        a.ps_a2 = static_cast<float>(z.psc_a * z.psc_a);
+        a.ps_2a = static_cast<float>(2.0 * z.psc_a);
+        a.ca_q = static_cast<float>(1.0 / z.tau_c);
+        a.vrest = 0.0f;  // the readout is gain c + offset
+    }
 }
 
 PulseTable make_pulses(const gn_pulse *pulses, int32_t n, int32_t n_nodes, double dt, const std::vector<int32_t> &inv)

@@ -87,7 +87,8 @@ struct HostNet {
     int32_t R = 0, dbits = 0, dmax = 1, dmin = 1, stride = 0;
     int64_t n_clamped = 0;
     bool packed = true;
-    double v_rest = 0.0, w_rest = 0.0;
+    int32_t model = GN_MODEL_FHN;
+    double v_rest = 0.0, w_rest = 0.0;   // FHN: the rest point; Izhikevich: (v_r, 0)
     std::vector<int32_t> perm, inv, delay;   // perm: internal -> caller; delay: caller edge order
     std::vector<uint32_t> key;               // [E + pad] packed, or [2 (E + pad)] wide
     std::vector<float> w;                    // [E + pad]

@@ -120,6 +120,55 @@ __device__ __forceinline__ float gather_hint(const StepArgs &a, int64_t n, uint3
 
 constexpr int32_t kLoad = INT32_MIN;  // "not prefetched" marker for node_update
 
+__device__ __forceinline__ void record_event(const StepArgs &a, int r, int64_t step)
+{
+    const unsigned long long i = atomicAdd(a.ev_count, 1ull);
+    if (i < static_cast<unsigned long long>(a.ev_cap)) {
+        a.ev_node[i] = r;
+        a.ev_step[i] = step;
+    }
+}
+
+// Izhikevich simple model with an alpha-function PSC and the calcium readout
+// (Sec. 3.1 Eq. izsimple / izpsc, Sec. 3.2.1 Eq. alphapsc and spd, Sec. 3.3 Eq.
+// casimple), forward Euler from step n to n + 1.  S is sum_e w_e spd(V_src(n - D_e))
+// (the ring holds spd); the state is absolute.
+__device__ __forceinline__ void izh_update(const StepArgs &a, int r, int64_t n, float2 wc, float S, float U,
+                                           int32_t orig)
+{
+    const float V = a.iz_v[r];
+    const float W = wc.x, c = wc.y;
+    const float2 rp = a.rp[r];
+    const bool spike = V >= a.iz_vpeak;
+    float V1, W1;
+    if (!spike) {
+        V1 = V + a.iz_dtc * (a.iz_k * (V - a.iz_vr) * (V - a.iz_vt) - W + rp.x + U + a.iz_iext);
+        W1 = W + a.iz_dta * (a.iz_b * (V - a.iz_vr) - W);
+    } else {
+        V1 = a.iz_vreset;
+        W1 = W + a.iz_d;
+    }
+    const float r1 = rp.x + a.dt * rp.y;
+    const float p1 = rp.y + a.dt * (-a.ps_a2 * rp.x - a.ps_2a * rp.y + S);
+    const float c1 = c + a.dt * (spike ? 1.0f - c * a.ca_q : -c * a.ca_q);
+    const bool spike1 = V1 >= a.iz_vpeak;
+
+    a.iz_v[r] = V1;
+    a.wc[r] = make_float2(W1, c1);
+    a.rp[r] = make_float2(r1, p1);
+    a.ring[((n + 1) & a.ring_mask) * a.ring_stride + r] = spike1 ? 1.0f : 0.0f;
+    if (spike1) {
+        record_event(a, r, n + 1);
+        if (a.first[r] < 0) a.first[r] = n + 1;
+    }
+    if (((n + 1) % a.sample_every) == 0) {
+        const int64_t k = (n + 1) / a.sample_every - 1;
+        if (orig == kLoad) orig = __ldg(a.perm + r);
+        const float xi = gauss_from(draw(a.obs_seed, static_cast<uint32_t>(orig), k, kStreamObservation));
+        a.obs[(k % a.obs_cap) * a.N + orig] = fmaf(a.gain, c1, a.offset) + a.sigma * xi;
+    }
+}
+
 // Stimulus, FHN Euler step, history write, readout, noise, events, arrival.
 // `orig` (caller id) and `cnt0` (background counter) may be prefetched by the
 // caller; kLoad makes node_update read them itself.
@@ -148,6 +197,10 @@ __device__ __forceinline__ void node_update(const StepArgs &a, int r, int64_t n,
         }
         if (cnt != c0) a.bgc[r] = cnt;
     }
+    if (a.model == 1) {
+        izh_update(a, r, n, wc, S, U, orig);
+        return;
+    }
     if (a.bias) S += __ldg(a.bias + r);
 
     const float w = wc.x, c = wc.y;
@@ -159,13 +212,7 @@ __device__ __forceinline__ void node_update(const StepArgs &a, int r, int64_t n,
     a.ring[((n + 1) & a.ring_mask) * a.ring_stride + r] = v1;
     a.wc[r] = make_float2(w1, c1);
 
-    if (v < a.theta_s && v1 >= a.theta_s) {
-        const unsigned long long i = atomicAdd(a.ev_count, 1ull);
-        if (i < static_cast<unsigned long long>(a.ev_cap)) {
-            a.ev_node[i] = r;
-            a.ev_step[i] = n + 1;
-        }
-    }
+    if (v < a.theta_s && v1 >= a.theta_s) record_event(a, r, n + 1);
     if (v1 != 0.0f && v == 0.0f && a.first[r] < 0) a.first[r] = n + 1;
 
     if (((n + 1) % a.sample_every) == 0) {

@@ -37,6 +37,14 @@ class gn_obs_params(C.Structure):
                 ("offset", C.c_float), ("sigma", C.c_float), ("seed", C.c_uint64)]
 
 
+class gn_izh_params(C.Structure):
+    _fields_ = [(x, C.c_double) for x in ("C", "k", "v_r", "v_t", "v_peak", "v_reset", "a", "b", "d", "i_ext",
+                                          "psc_a", "tau_c")]
+
+
+GN_MODEL_FHN, GN_MODEL_IZH = 0, 1
+
+
 class gn_net_desc(C.Structure):
     _fields_ = [
         ("n_nodes", C.c_int32), ("dim", C.c_int32), ("pos", C.c_void_p), ("n_edges", C.c_int64),
@@ -46,6 +54,7 @@ class gn_net_desc(C.Structure):
         ("ring_depth", C.c_int32), ("obs_capacity", C.c_int64), ("event_capacity", C.c_int64),
         ("renumber", C.c_int32), ("edge_format", C.c_int32), ("step_kernel", C.c_int32),
         ("cuda_stream", C.c_void_p), ("device", C.c_int32),
+        ("model", C.c_int32), ("izh", gn_izh_params),
     ]
 
 
@@ -86,6 +95,8 @@ _SIGS = {
     "gn_get_state": ([_P, _P, _P, _P, _P, C.POINTER(C.c_int64)], C.c_int),
     "gn_get_history": ([_P, _P, C.c_int32], C.c_int),
     "gn_set_state": ([_P, _P, C.c_int32, _P, _P, _P, C.c_int64], C.c_int),
+    "gn_get_izh_state": ([_P, _P, _P, _P], C.c_int),
+    "gn_set_izh_state": ([_P, _P, _P, _P], C.c_int),
     "gn_get_arrivals": ([_P, _P], C.c_int),
     "gn_get_events": ([_P, _P, _P, C.c_int64, C.POINTER(C.c_int64)], C.c_int),
     "gn_save_state": ([_P, _P, C.c_size_t, C.POINTER(C.c_size_t)], C.c_int),
@@ -178,7 +189,15 @@ def make_desc(spec, keep: list, *, device: int = 0, stream=None, obs_capacity: i
         ring_depth=spec.ring_depth if ring_depth is None else ring_depth,
         obs_capacity=obs_capacity, event_capacity=event_capacity, renumber=0 if renumber else -1,
         edge_format=1 if wide_edges else 0, step_kernel=step_kernel,
-        cuda_stream=stream, device=device)
+        cuda_stream=stream, device=device, model=GN_MODEL_IZH if getattr(spec, "model", "fhn") == "izh" else GN_MODEL_FHN,
+        izh=_izh_params(getattr(spec, "izh", None)))
+
+
+def _izh_params(iz) -> gn_izh_params:
+    if not iz:
+        return gn_izh_params()
+    return gn_izh_params(C=iz["C"], k=iz["k"], v_r=iz["vr"], v_t=iz["vt"], v_peak=iz["vpeak"], v_reset=iz["vreset"],
+                         a=iz["a"], b=iz["b"], d=iz["d"], i_ext=iz["i_ext"], psc_a=iz["psc_a"], tau_c=iz["tau_c"])
 
 
 class Net:
@@ -274,6 +293,16 @@ class Net:
         w, c = _c(w, np.float32), _c(c, np.float32)
         bg = _c(bg_count, np.int32)
         check(lib().gn_set_state(self.h, _ptr(hist), hist.shape[0], _ptr(w), _ptr(c), _ptr(bg), step))
+
+    def gn_get_izh_state(self):
+        N = self.n_nodes
+        V, r, p = (np.zeros(N, np.float32) for _ in range(3))
+        check(lib().gn_get_izh_state(self.h, _ptr(V), _ptr(r), _ptr(p)))
+        return dict(V=V, r=r, p=p)
+
+    def gn_set_izh_state(self, V=None, r=None, p=None):
+        V, r, p = _c(V, np.float32), _c(r, np.float32), _c(p, np.float32)
+        check(lib().gn_set_izh_state(self.h, _ptr(V), _ptr(r), _ptr(p)))
 
     def gn_get_history(self, depth: int) -> np.ndarray:
         out = np.zeros((depth, self.n_nodes), np.float32)

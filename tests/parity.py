@@ -84,3 +84,65 @@ def windowed(spec, net, n_steps, window=20, start=0, coupling=None):
 def assert_windows(worst):
     for k, r in worst.items():
         assert r <= 1.0, f"{k}: {r:.3g} x tolerance"
+
+
+PEAK_MARGIN = 1e-2   # mV: a spike decision this close to V_peak may go either way in FP32
+
+
+def ratio_scaled(gpu, ref):
+    """ratio() for dimensional state (mV, pA): the absolute floor is 1e-6 of the
+    quantity's largest magnitude, |gpu - ref| <= max(REL |ref|, ABS max(1, max |ref|)).
+    For O(1) quantities this is ratio(); for V in mV it keeps the floor above one
+    FP32 ulp of the membrane potential (3.8e-6 mV at 60 mV), where the 0 mV crossing
+    of an upswing would otherwise be held to 1e-6 mV."""
+    gpu = np.asarray(gpu, np.float64)
+    ref = np.asarray(ref, np.float64)
+    if gpu.size == 0:
+        return 0.0
+    floor = ABS * max(1.0, float(np.max(np.abs(ref))))
+    return float(np.max(np.abs(gpu - ref) / np.maximum(REL * np.abs(ref), floor)))
+
+
+def windowed_izh(spec, net, n_steps, window=20, start=0):
+    """windowed() for the Izhikevich + alpha-PSC model: the oracle's full state (V, W,
+    calcium, r, p, spike history, background counters) is loaded at every window
+    start and the next `window` steps of V, W, c, r, p, y (ratio_scaled) and the
+    spikes are compared.  A node is left out of a window's comparison only if the oracle's V
+    came within PEAK_MARGIN of V_peak in it (the spike decision is not defined to
+    FP32 there); the count of such node-windows is returned with the worst ratios."""
+    D = oracle.net_delays(spec)
+    depth = int(D.max(initial=1)) + 1
+    ref = oracle.simulate(spec, start, hist_depth=depth, want_y=False)
+    worst = dict(v=0.0, w=0.0, c=0.0, r=0.0, p=0.0, y=0.0)
+    n_spikes = excused = 0
+    n0 = start
+    end = start + n_steps
+    while n0 < end:
+        K = min(window, end - n0)
+        net.gn_set_state(ref["hist"].astype(np.float32), ref["w"].astype(np.float32),
+                         ref["c"].astype(np.float32), ref["bg_count"], n0)
+        net.gn_set_izh_state(V=ref["v"].astype(np.float32), r=ref["r"].astype(np.float32),
+                             p=ref["p"].astype(np.float32))
+        nxt = oracle.simulate(spec, K, hist_depth=depth, ev_cap=spec.n_nodes * (K + 1) + 1024,
+                              init=dict(n0=n0, v=ref["v"], w=ref["w"], c=ref["c"], r=ref["r"], p=ref["p"],
+                                        bg_count=ref["bg_count"], hist=ref["hist"]))
+        net.gn_step(K)
+        g = net.gn_get_state()
+        gi = net.gn_get_izh_state()
+        y, _, _ = net.gn_observe()
+        ok = nxt["min_peak_gap"] > PEAK_MARGIN
+        excused += int((~ok).sum())
+        for k, gv, rv in (("v", gi["V"], nxt["v"]), ("w", g["w"], nxt["w"]), ("c", g["c"], nxt["c"]),
+                          ("r", gi["r"], nxt["r"]), ("p", gi["p"], nxt["p"])):
+            worst[k] = max(worst[k], ratio_scaled(gv[ok], rv[ok]))
+        if nxt["y"] is not None and nxt["y"].size:
+            worst["y"] = max(worst["y"], ratio_scaled(y[:, ok], nxt["y"][:, ok]))
+        assert np.array_equal(g["bg_count"], nxt["bg_count"]), "background counters differ"
+        gn_nodes, gn_steps, _ = net.gn_get_events()
+        ref_ev = {(int(a), int(b)) for a, b in zip(nxt["ev_node"], nxt["ev_step"]) if ok[a]}
+        got_ev = {(int(a), int(b)) for a, b in zip(gn_nodes, gn_steps) if ok[a]}
+        assert got_ev == ref_ev, f"spikes differ in window starting at {n0}: {sorted(got_ev ^ ref_ev)[:10]}"
+        n_spikes += len(ref_ev)
+        ref = nxt
+        n0 += K
+    return worst, n_spikes, excused
