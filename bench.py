@@ -266,6 +266,44 @@ def run_batched(args, local, stream, rank):
             "speedup_vs_loop": t_loop / t}
 
 
+IZH_NODE_BYTES = 60.2  # V r/w 8, (W, c) r/w 16, (r, p) r/w 16, spike-ring write 4, piece list 4,
+                       # background counter 4 + caller id 4, readout 4 B / 20 steps
+
+
+def run_izhikevich(args, spec, local, stream):
+    """The same network with Izhikevich + alpha-PSC + calcium nodes (the paper's own
+    benchmark model): step time of the autotuned kernel on the device, CUDA events
+    on the stream, `izh_steps` steps."""
+    import torch
+    from paper_0908_3934_b300 import geonet
+    ispec = netgen.izhikevich(spec)
+    net = geonet.Net(ispec, device=local, stream=stream.cuda_stream, obs_capacity=max(64, args.izh_steps // 20 + 1))
+    net.gn_step(max(3, args.warmup))
+    net.gn_synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    net.gn_step(args.izh_steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t = ev0.elapsed_time(ev1) / 1e3
+    info = net.gn_net_get_info()
+    n_spikes = int(net.gn_get_events(cap=1 << 24)[0].size)
+    net.gn_net_destroy()
+    E, N = ispec.n_edges, ispec.n_nodes
+    bytes_step = (E * STAGED_EDGE_BYTES + info["step_gathers"] * STAGED_GATHER_BYTES
+                  if info["step_kernel"] == 3 else E * EDGE_BYTES) + N * IZH_NODE_BYTES
+    peak, _ = peaks()
+    step_s = t / args.izh_steps
+    return {"workload": f"the same {N}-node network, Izhikevich regular-spiking nodes with alpha-function PSCs "
+                        f"and calcium, 5 Hz background pulses of 2500 pA, dt = {ispec.dt_ms} ms",
+            "value": E * args.izh_steps / t, "unit": METRIC, "ms_per_step": step_s * 1e3,
+            "rtf": ispec.dt_ms * 1e-3 / step_s, "spikes_per_node_per_s": n_spikes / N / (args.izh_steps * ispec.dt_ms * 1e-3),
+            "step_kernel": KERNEL_NAMES[info["step_kernel"]],
+            "roofline": {"bound": "hbm", "achieved": bytes_step / step_s / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": bytes_step / step_s / 1e9 / peak, "algorithmic_bytes_per_launch": bytes_step},
+            "gpu_launches": args.izh_steps + args.izh_steps // 64}
+
+
 def run_estimator(args, local, stream):
     """Connectivity estimation with config-5 laws: networks of N = 512 (2D, kept
     in-degree ~20, 1-8 pulsed nodes, 500 ms observed at 1 ms); the MLP is trained on
@@ -349,6 +387,8 @@ def main():
     ap.add_argument("--est-test", type=int, default=200, help="held-out nets of the estimator measurement")
     ap.add_argument("--est-epochs", type=int, default=8)
     ap.add_argument("--no-estimator", action="store_true")
+    ap.add_argument("--no-izh", action="store_true", help="skip the Izhikevich-model measurement")
+    ap.add_argument("--izh-steps", type=int, default=2000)
     ap.add_argument("--step-kernel", type=int, default=0, choices=[0, 1, 2, 3],
                     help="0: autotuned, 1: one row block per CTA, 2: persistent bulk-copy pipelined kernel, "
                          "3: staged tiles (distinct gathers in shared memory)")
@@ -462,6 +502,8 @@ def main():
         bt = run_batched(args, local, stream, rank)
         bt["value"], _, bt["seconds"] = replica_rate(bt["value"] * bt["seconds"], bt["seconds"], dev)
         line["batched"] = bt
+    if not args.no_izh and rank == 0:
+        line["izhikevich"] = run_izhikevich(args, spec, local, stream)
     if not args.no_estimator and rank == 0:
         line["estimator"] = run_estimator(args, local, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
