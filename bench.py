@@ -304,6 +304,44 @@ def run_izhikevich(args, spec, local, stream):
             "gpu_launches": args.izh_steps + args.izh_steps // 64}
 
 
+def run_test_set(args, local, stream):
+    """The paper's own benchmark layout (Sec. 3.4, Sec. 3.5): the 80 networks of the
+    standard test set (2 dimensions x 5 sizes x 4 classes x 2 densities) with
+    Izhikevich + alpha-PSC nodes at dt = 1 ms, each simulated for `test_set_steps`
+    steps (10 s of simulated time by default); real-time factor = simulated time /
+    device time (CUDA events), one network after another, each from its own graph."""
+    import statistics as st
+    import torch
+    from paper_0908_3934_b300 import geonet
+    rows = []
+    for sp in netgen.test_set():
+        ispec = netgen.test_set_izh(sp)
+        net = geonet.Net(ispec, device=local, stream=stream.cuda_stream, obs_capacity=64)
+        net.gn_step(128)
+        net.gn_synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        net.gn_step(args.test_set_steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t = ev0.elapsed_time(ev1) / 1e3
+        net.gn_net_destroy()
+        rows.append((sp.name, sp.n_nodes, sp.n_edges, args.test_set_steps * ispec.dt_ms * 1e-3 / t))
+    rtf = [r[3] for r in rows]
+    by_class = {}
+    for cls in netgen.TEST_SET_CLASSES:
+        big = [r[3] for r in rows if f"_{cls}_" in r[0] and r[1] == max(netgen.TEST_SET_SIZES)]
+        by_class[cls] = {"min": min(big), "max": max(big)}
+    return {"workload": f"the 80 test-set networks (N = 10 .. 1000, 2D / 3D, lattice / small world / scale free / "
+                        f"random, low / high density), Izhikevich + alpha-PSC nodes, dt = 1 ms, "
+                        f"{args.test_set_steps} steps each, 20 Hz background pulses",
+            "metric": "real-time factor (simulated time / device time)",
+            "rtf_min": min(rtf), "rtf_median": st.median(rtf), "rtf_max": max(rtf),
+            "rtf_n1000_by_class": by_class,
+            "largest": max(rows, key=lambda r: r[2])[0],
+            "networks": [{"name": r[0], "N": r[1], "E": r[2], "rtf": round(r[3], 1)} for r in rows]}
+
+
 def run_estimator(args, local, stream):
     """Connectivity estimation with config-5 laws: networks of N = 512 (2D, kept
     in-degree ~20, 1-8 pulsed nodes, 500 ms observed at 1 ms); the MLP is trained on
@@ -389,6 +427,8 @@ def main():
     ap.add_argument("--no-estimator", action="store_true")
     ap.add_argument("--no-izh", action="store_true", help="skip the Izhikevich-model measurement")
     ap.add_argument("--izh-steps", type=int, default=2000)
+    ap.add_argument("--no-test-set", action="store_true", help="skip the 80-network test-set sweep")
+    ap.add_argument("--test-set-steps", type=int, default=10000)
     ap.add_argument("--step-kernel", type=int, default=0, choices=[0, 1, 2, 3],
                     help="0: autotuned, 1: one row block per CTA, 2: persistent bulk-copy pipelined kernel, "
                          "3: staged tiles (distinct gathers in shared memory)")
@@ -504,6 +544,8 @@ def main():
         line["batched"] = bt
     if not args.no_izh and rank == 0:
         line["izhikevich"] = run_izhikevich(args, spec, local, stream)
+    if not args.no_test_set and rank == 0:
+        line["test_set"] = run_test_set(args, local, stream)
     if not args.no_estimator and rank == 0:
         line["estimator"] = run_estimator(args, local, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -330,3 +330,118 @@ def shuffles(seed: int, n: int, epochs: int):
     """The order in which a training run visits n samples, epoch by epoch."""
     rng = np.random.default_rng(seed)
     return [rng.permutation(n).astype(np.int64) for _ in range(epochs)]
+
+
+# ---------------------------------------------------------------------------
+# The paper's standard test set (Sec. 3.5, Table modelspace): N vertices placed at
+# random in a square or cube of side L with a minimum distance between any two,
+# numbered from the centre outwards, connected by one of four graph classes at a
+# low and a high edge density; delays from distance over one speed (Eq. delaydist).
+TEST_SET_SIZES = (10, 30, 100, 300, 1000)
+TEST_SET_CLASSES = ("lattice", "small_world", "scale_free", "random")
+# (low, high) density parameter of each class: nearest neighbours, rewiring
+# probability, edges per new vertex, fraction of the N^2 ordered pairs
+TEST_SET_DENSITY = {"lattice": (3, 8), "small_world": (0.05, 0.15), "scale_free": (2, 4), "random": (0.10, 0.20)}
+
+
+def min_distance_placement(rng, n: int, dim: int, side: float, d_min: float, max_tries: int = 1_000_000):
+    """Random positions in [0, side)^dim, each candidate kept only if it is at least
+    d_min from every vertex kept so far; vertices are then numbered by distance from
+    the centre of the region (nearest first)."""
+    pos = np.empty((n, dim))
+    k = 0
+    tries = 0
+    while k < n:
+        tries += 1
+        if tries > max_tries:
+            raise ValueError(f"cannot place {n} vertices {d_min} apart in a side of {side}")
+        x = rng.random(dim) * side
+        if k and np.min(np.sum((pos[:k] - x) ** 2, axis=1)) < d_min * d_min:
+            continue
+        pos[k] = x
+        k += 1
+    order = np.argsort(np.sum((pos - side / 2.0) ** 2, axis=1), kind="stable")
+    return pos[order]
+
+
+def _knn_in_edges(pos, k):
+    """Directed edges i -> j from each vertex's k nearest neighbours i."""
+    tree = cKDTree(pos)
+    _, nn = tree.query(pos, k=k + 1)
+    src = nn[:, 1:].reshape(-1)
+    dst = np.repeat(np.arange(pos.shape[0]), k)
+    return src.astype(np.int32), dst.astype(np.int32)
+
+
+def test_set_net(n: int, dim: int, cls: str, density: str, seed: int = 0, side: float = 1.0,
+                 d_min_frac: float = 0.5, speed: float = 0.1, dt_ms: float = 1.0) -> NetSpec:
+    """One network of the test set.  Placement: d_min = d_min_frac * side * n^(-1/dim)
+    (the cubic-packing distance, reduced to leave room for random placement).
+    Classes (each vertex's in-edges; `density` "low" or "high" picks the parameter):
+      lattice      its k nearest vertices (k = 3 or 8);
+      small_world  the lattice, each edge's source re-drawn uniformly at random with
+                   probability p (5 % or 15 %);
+      scale_free   growth in the centre-out order: vertex v >= m links to m earlier
+                   vertices drawn with probability proportional to their degree + 1
+                   (m = 2 or 4), each link's direction drawn at random;
+      random       every ordered pair i != j with probability p (10 % or 20 %).
+    Weights U(0.1, 0.5), one speed (mm/ms), dt = 1 ms (the paper's Izhikevich
+    benchmark step)."""
+    if cls not in TEST_SET_CLASSES or density not in ("low", "high"):
+        raise ValueError(f"unknown class {cls!r} or density {density!r}")
+    rng = np.random.default_rng(seed)
+    pos = min_distance_placement(rng, n, dim, side, d_min_frac * side * n ** (-1.0 / dim))
+    par = TEST_SET_DENSITY[cls][0 if density == "low" else 1]
+    if cls == "lattice":
+        src, dst = _knn_in_edges(pos, min(par, n - 1))
+    elif cls == "small_world":
+        src, dst = _knn_in_edges(pos, min(3, n - 1) if density == "low" else min(8, n - 1))
+        rewire = rng.random(src.size) < par
+        for e in np.nonzero(rewire)[0]:
+            s = int(rng.integers(0, n - 1))
+            src[e] = s + (s >= dst[e])          # any vertex but the target
+    elif cls == "scale_free":
+        m = par
+        deg = np.zeros(n)
+        edges = []
+        for v in range(1, n):
+            cand = np.arange(v)
+            k = min(m, v)
+            p = (deg[:v] + 1.0) / np.sum(deg[:v] + 1.0)
+            for u in rng.choice(cand, size=k, replace=False, p=p):
+                edges.append((v, int(u)) if rng.random() < 0.5 else (int(u), v))
+                deg[u] += 1
+                deg[v] += 1
+        src = np.array([a for a, _ in edges], np.int32)
+        dst = np.array([b for _, b in edges], np.int32)
+    else:
+        mask = rng.random((n, n)) < par
+        np.fill_diagonal(mask, False)
+        src, dst = np.nonzero(mask)
+        src, dst = src.astype(np.int32), dst.astype(np.int32)
+    src, dst = _sort_by_dst(src.astype(np.int32), dst.astype(np.int32))
+    w = rng.uniform(0.1, 0.5, src.size).astype(np.float32)
+    obs = dict(OBS_DEFAULT, sample_every=max(1, int(round(1.0 / dt_ms))), seed=seed + 17)
+    return NetSpec(pos=pos, src=src, dst=dst, weight=w, speed=None, speed_scalar=speed, dt_ms=dt_ms, obs=obs,
+                   name=f"testset_{cls}_{density}_{dim}d_n{n}")
+
+
+def test_set(seed0: int = 500, **kw) -> list:
+    """The 80 networks: 2 dimensions x 5 sizes x 4 classes x 2 densities."""
+    out = []
+    i = 0
+    for dim in (2, 3):
+        for n in TEST_SET_SIZES:
+            for cls in TEST_SET_CLASSES:
+                for density in ("low", "high"):
+                    out.append(test_set_net(n, dim, cls, density, seed=seed0 + i, **kw))
+                    i += 1
+    return out
+
+
+def test_set_izh(spec: NetSpec, bg_rate_hz: float = 20.0, w_scale: float = 100.0, seed: int = 0) -> NetSpec:
+    """A test-set network with Izhikevich + alpha-PSC nodes driven by background pulses
+    (2 ms of 2500 pA at bg_rate_hz per node); at dt = 1 ms a weight scale of 100 puts
+    the PSC peak near 55 pA for a weight of 0.3."""
+    bg = dict(rate_hz=bg_rate_hz, amp=1.0, dur_ms=2.0, seed=seed + 4242)
+    return izhikevich(dataclasses.replace(spec, background=bg), w_scale=w_scale)

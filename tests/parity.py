@@ -103,13 +103,17 @@ def ratio_scaled(gpu, ref):
     return float(np.max(np.abs(gpu - ref) / np.maximum(REL * np.abs(ref), floor)))
 
 
-def windowed_izh(spec, net, n_steps, window=20, start=0):
+def windowed_izh(spec, net, n_steps, window=None, start=0):
     """windowed() for the Izhikevich + alpha-PSC model: the oracle's full state (V, W,
     calcium, r, p, spike history, background counters) is loaded at every window
     start and the next `window` steps of V, W, c, r, p, y (ratio_scaled) and the
     spikes are compared.  A node is left out of a window's comparison only if the oracle's V
     came within PEAK_MARGIN of V_peak in it (the spike decision is not defined to
-    FP32 there); the count of such node-windows is returned with the worst ratios."""
+    FP32 there); the count of such node-windows is returned with the worst ratios.
+    The window defaults to one observation interval (1 ms: 20 steps at dt = 0.05 ms,
+    one step at dt = 1 ms, where a spike's upswing amplifies a perturbation more than
+    twofold per step)."""
+    window = window or spec.obs["sample_every"]
     D = oracle.net_delays(spec)
     depth = int(D.max(initial=1)) + 1
     ref = oracle.simulate(spec, start, hist_depth=depth, want_y=False)

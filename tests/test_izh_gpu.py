@@ -89,3 +89,15 @@ def test_model_specific_calls_are_checked():
     with pytest.raises(geonet.GeonetError) as e:
         geonet.Batch([netgen.izhikevich(netgen.tiny())])
     assert e.value.status == geonet.GN_EINVAL
+
+
+@pytest.mark.parametrize("cls", ["small_world", "scale_free", "random"])
+def test_test_set_networks_at_one_millisecond_steps(cls):
+    """Networks of the standard test set (Sec. 3.5) with Izhikevich nodes at the
+    paper's benchmark step dt = 1 ms, 20 Hz background pulses: 500 steps, one 1 ms
+    observation interval (one step) per window."""
+    spec = netgen.test_set_izh(netgen.test_set_net(300, 2, cls, "high", seed=7))
+    net = geonet.Net(spec)
+    worst, n_spikes, _ = windowed_izh(spec, net, 500)
+    assert_windows(worst)
+    assert n_spikes > 50
