@@ -57,6 +57,9 @@ class _Net(C.Structure):
         ("iz_C", C.c_double), ("iz_k", C.c_double), ("iz_vr", C.c_double), ("iz_vt", C.c_double),
         ("iz_vpeak", C.c_double), ("iz_vreset", C.c_double), ("iz_a", C.c_double), ("iz_b", C.c_double),
         ("iz_d", C.c_double), ("iz_iext", C.c_double), ("psc_a", C.c_double), ("tau_c", C.c_double),
+        ("hh_C", C.c_double), ("hh_gna", C.c_double), ("hh_gk", C.c_double), ("hh_gl", C.c_double),
+        ("hh_ena", C.c_double), ("hh_ek", C.c_double), ("hh_el", C.c_double), ("hh_vpeak", C.c_double),
+        ("hh_iext", C.c_double),
     ]
 
 
@@ -65,6 +68,7 @@ class _Init(C.Structure):
         ("n0", C.c_int64), ("v", C.c_void_p), ("w", C.c_void_p), ("c", C.c_void_p),
         ("bg_count", C.c_void_p), ("hist", C.c_void_p), ("hist_depth", C.c_int32),
         ("r", C.c_void_p), ("p", C.c_void_p),
+        ("m", C.c_void_p), ("n", C.c_void_p), ("h", C.c_void_p),
     ]
 
 
@@ -77,7 +81,8 @@ class _Out(C.Structure):
         ("snap_every", C.c_int32),
         ("snap_v", C.c_void_p), ("snap_w", C.c_void_p), ("snap_c", C.c_void_p), ("bg_count", C.c_void_p),
         ("hist_out", C.c_void_p), ("hist_out_depth", C.c_int32),
-        ("r", C.c_void_p), ("p", C.c_void_p), ("min_peak_gap", C.c_void_p),
+        ("r", C.c_void_p), ("p", C.c_void_p),
+        ("m", C.c_void_p), ("n", C.c_void_p), ("h", C.c_void_p), ("min_peak_gap", C.c_void_p),
     ]
 
 
@@ -101,6 +106,7 @@ def lib():
             L.orc_simulate.argtypes = [C.POINTER(_Net), C.c_int64, C.POINTER(_Out)]
             L.orc_simulate_dense.argtypes = [C.POINTER(_Net), C.c_int64, C.POINTER(_Out)]
             L.orc_simulate_from.argtypes = [C.POINTER(_Net), C.POINTER(_Init), C.c_int64, C.POINTER(_Out)]
+            L.orc_hh_rest_gates.argtypes = [C.POINTER(C.c_double)] * 3
             _lib = L
     return _lib
 
@@ -164,6 +170,13 @@ def ms_to_step(t_ms: float, dt_ms: float) -> int:
     return int(lib().orc_ms_to_step(t_ms, dt_ms))
 
 
+def hh_rest_gates():
+    """Hodgkin-Huxley gates m, n, h at rest (-65 mV): alpha / (alpha + beta)."""
+    m, n, h = C.c_double(), C.c_double(), C.c_double()
+    lib().orc_hh_rest_gates(C.byref(m), C.byref(n), C.byref(h))
+    return m.value, n.value, h.value
+
+
 def net_delays(spec) -> np.ndarray:
     """Delay table of a generated network: explicit if given, else geometric."""
     if spec.delay is not None:
@@ -190,7 +203,9 @@ def simulate(spec, n_steps: int, *, dense: bool = False, snap_every: int = 0,
     absolute (v = V, w = W, c = calcium, plus r, p returned and accepted in
     ``init``), the history holds spd(V) in {0, 1}, events are spikes, the arrival
     of a node is its first spike, and ``min_peak_gap`` [N] is the smallest
-    |V - V_peak| seen during the run.
+    |V - V_peak| seen during the run.  With ``spec.model == "hh"`` (Hodgkin-Huxley
+    + alpha PSC + calcium) the same holds with W = 0, the gates m, n, h returned
+    (and accepted in ``init``), and events the upward crossings of V_peak.
     """
     L = lib()
     N = spec.n_nodes
@@ -209,7 +224,12 @@ def simulate(spec, n_steps: int, *, dense: bool = False, snap_every: int = 0,
     bg = spec.background
     cpl = coupling or spec.coupling
     izh = spec.model == "izh"
+    hh = spec.model == "hh"
+    spiking = izh or hh
     iz = spec.izh
+    hp = getattr(spec, "hh", None) or {}
+    # the PSC rate and calcium time are shared by the spiking models
+    psc = hp if hh else iz
     net = _Net(
         n_nodes=N, n_edges=E, src=_ptr(src), dst=_ptr(dst), weight=_ptr(wgt), delay=_ptr(D),
         dt_ms=spec.dt_ms, a=fhn["a"], b=fhn["b"], c=fhn["c"], e=fhn["e"], f=fhn["f"], g=fhn["g"],
@@ -222,10 +242,12 @@ def simulate(spec, n_steps: int, *, dense: bool = False, snap_every: int = 0,
         bg_amp=float(np.float32(bg["amp"])) if bg else 0.0,
         bg_width=ms_to_step(bg["dur_ms"], spec.dt_ms) if bg else 0,
         bg_seed=bg["seed"] if bg else 0,
-        model=1 if izh else 0,
+        model=2 if hh else 1 if izh else 0,
         iz_C=iz["C"], iz_k=iz["k"], iz_vr=iz["vr"], iz_vt=iz["vt"], iz_vpeak=iz["vpeak"],
         iz_vreset=iz["vreset"], iz_a=iz["a"], iz_b=iz["b"], iz_d=iz["d"], iz_iext=iz["i_ext"],
-        psc_a=iz["psc_a"], tau_c=iz["tau_c"],
+        psc_a=psc["psc_a"], tau_c=psc["tau_c"],
+        **({f"hh_{k}": hp[k] for k in ("C", "gna", "gk", "gl", "ena", "ek", "el", "vpeak")} if hh else {}),
+        hh_iext=hp.get("i_ext", 0.0),
     )
     v = np.zeros(N)
     w = np.zeros(N)
@@ -247,9 +269,11 @@ def simulate(spec, n_steps: int, *, dense: bool = False, snap_every: int = 0,
     hout = np.zeros((hist_depth, N)) if hist_depth > 0 else None
     r_out = np.zeros(N)
     p_out = np.zeros(N)
+    gates = [np.zeros(N) for _ in range(3)]
     gap = np.zeros(N)
     out = _Out(v=_ptr(v), w=_ptr(w), c=_ptr(c), y=_ptr(y), y_clean=_ptr(yc), bg_count=_ptr(bgc),
-               r=_ptr(r_out), p=_ptr(p_out), min_peak_gap=_ptr(gap) if izh else None,
+               r=_ptr(r_out), p=_ptr(p_out), min_peak_gap=_ptr(gap) if spiking else None,
+               m=_ptr(gates[0]), n=_ptr(gates[1]), h=_ptr(gates[2]),
                hist_out=_ptr(hout), hist_out_depth=hist_depth,
                first_arrival=_ptr(fa), first_value=_ptr(fv), ev_node=_ptr(evn), ev_step=_ptr(evs),
                ev_cap=ev_cap, ev_count=0, snap_every=snap_every if n_snap else 0,
@@ -265,7 +289,9 @@ def simulate(spec, n_steps: int, *, dense: bool = False, snap_every: int = 0,
         ini = _Init(n0=n0, v=arr(init["v"], np.float64), w=arr(init["w"], np.float64),
                     c=arr(init["c"], np.float64), bg_count=arr(init.get("bg_count"), np.int32),
                     hist=_ptr(hist), hist_depth=hist.shape[0],
-                    r=arr(init.get("r"), np.float64), p=arr(init.get("p"), np.float64))
+                    r=arr(init.get("r"), np.float64), p=arr(init.get("p"), np.float64),
+                    m=arr(init.get("m"), np.float64), n=arr(init.get("n"), np.float64),
+                    h=arr(init.get("h"), np.float64))
         rc = L.orc_simulate_from(C.byref(net), C.byref(ini), n_steps, C.byref(out))
     else:
         fn = L.orc_simulate_dense if dense else L.orc_simulate
@@ -276,5 +302,5 @@ def simulate(spec, n_steps: int, *, dense: bool = False, snap_every: int = 0,
     return dict(v=v, w=w, c=c, y=y, y_clean=yc, first_arrival=fa, first_value=fv,
                 ev_node=evn[:ne].copy(), ev_step=evs[:ne].copy(), ev_count=out.ev_count,
                 snap_v=sv, snap_w=sw, snap_c=sc, bg_count=bgc, hist=hout, n_end=n0 + n_steps,
-                delay=D, rest=None if izh else rest_point(fhn), r=r_out, p=p_out,
-                min_peak_gap=gap if izh else None)
+                delay=D, rest=None if spiking else rest_point(fhn), r=r_out, p=p_out,
+                min_peak_gap=gap if spiking else None, m=gates[0], n=gates[1], h=gates[2])

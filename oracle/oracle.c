@@ -52,6 +52,19 @@
  *   (the fixed point without input), with no spike before t = 0.  Events are spikes
  *   (V(n+1) >= V_peak) and the arrival of a node is its first spike.
  *
+ * Third node model (model = 2): Hodgkin-Huxley (the paper names it, Sec. 3.1 and
+ * 3.4, with four state variables {v, m, n, h}; the equations are the classic squid
+ * axon ones in the modern convention, rest near -65 mV), with the same
+ * alpha-function PSC, spike indicator and calcium readout as model 1:
+ *       V' = V + dt/C [-gNa m^3 h (V - ENa) - gK n^4 (V - EK) - gL (V - EL) + r + U + I]
+ *       x' = x + dt (alpha_x(V) (1 - x) - beta_x(V) x),   x in {m, n, h}
+ *   alpha_m = 0.1 (V + 40) / (1 - e^-(V+40)/10), beta_m = 4 e^-(V+65)/18,
+ *   alpha_h = 0.07 e^-(V+65)/20,                 beta_h = 1 / (1 + e^-(V+35)/10),
+ *   alpha_n = 0.01 (V + 55) / (1 - e^-(V+55)/10), beta_n = 0.125 e^-(V+65)/80,
+ *   the removable 0/0 at V = -40, -55 evaluated as x / (-expm1(-x / y)) (limit y).
+ *   No reset: spd(V) = 1 while V >= V_peak; events are upward crossings of V_peak.
+ *   The state starts at V = -65 mV with each gate at alpha / (alpha + beta) there.
+ *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11), written from the
  * published definition; Box-Muller (1958) for the Gaussian.
  *
@@ -231,6 +244,8 @@ typedef struct {
     double iz_C, iz_k, iz_vr, iz_vt, iz_vpeak, iz_vreset, iz_a, iz_b, iz_d, iz_iext;
     double psc_a;            /* alpha-function rate a_s (1/ms) */
     double tau_c;            /* calcium removal time (ms) */
+    /* model 2: Hodgkin-Huxley */
+    double hh_C, hh_gna, hh_gk, hh_gl, hh_ena, hh_ek, hh_el, hh_vpeak, hh_iext;
 } orc_net;
 
 typedef struct {
@@ -248,7 +263,8 @@ typedef struct {
     int32_t *bg_count;        /* [N] final background counters (or NULL) */
     double *hist_out;         /* [hist_out_depth * N]: v~_j(n_end - k), k < hist_out_depth (or NULL) */
     int32_t hist_out_depth;   /* <= D_max + 1 */
-    double *r, *p;            /* model 1: [N] final PSC state (or NULL) */
+    double *r, *p;            /* models 1, 2: [N] final PSC state (or NULL) */
+    double *m, *n, *h;        /* model 2: [N] final gates (or NULL) */
     double *min_peak_gap;     /* model 1: [N] min over the run of |V - V_peak| (or NULL) */
 } orc_out;
 
@@ -287,6 +303,52 @@ static void izh_step(const orc_net *net, double V, double W, double r, double p,
     *r1 = r + dt * p;
     *p1 = p + dt * (-net->psc_a * net->psc_a * r - 2.0 * net->psc_a * p + S);
     *c1 = c + dt * (-c / net->tau_c + spike);
+}
+
+/* x / (1 - exp(-x / y)), its limit y at x = 0 */
+static double hh_trap(double x, double y)
+{
+    return x == 0.0 ? y : x / -expm1(-x / y);
+}
+
+static void hh_rates(double V, double *am, double *bm, double *ah, double *bh, double *an, double *bn)
+{
+    *am = 0.1 * hh_trap(V + 40.0, 10.0);
+    *bm = 4.0 * exp(-(V + 65.0) / 18.0);
+    *ah = 0.07 * exp(-(V + 65.0) / 20.0);
+    *bh = 1.0 / (1.0 + exp(-(V + 35.0) / 10.0));
+    *an = 0.01 * hh_trap(V + 55.0, 10.0);
+    *bn = 0.125 * exp(-(V + 65.0) / 80.0);
+}
+
+/* Gates at rest: x_inf(-65 mV) = alpha / (alpha + beta). */
+void orc_hh_rest_gates(double *m, double *n, double *h)
+{
+    double am, bm, ah, bh, an, bn;
+    hh_rates(-65.0, &am, &bm, &ah, &bh, &an, &bn);
+    *m = am / (am + bm);
+    *n = an / (an + bn);
+    *h = ah / (ah + bh);
+}
+
+/* One Euler step of the Hodgkin-Huxley + alpha-PSC + calcium node (model 2). */
+static void hh_step(const orc_net *net, double V, double m, double n, double h, double r, double p, double c,
+                    double S, double U, double *V1, double *m1, double *n1, double *h1, double *r1, double *p1,
+                    double *c1)
+{
+    double dt = net->dt_ms;
+    double am, bm, ah, bh, an, bn;
+    hh_rates(V, &am, &bm, &ah, &bh, &an, &bn);
+    double ina = net->hh_gna * m * m * m * h * (V - net->hh_ena);
+    double ik = net->hh_gk * n * n * n * n * (V - net->hh_ek);
+    double il = net->hh_gl * (V - net->hh_el);
+    *V1 = V + dt / net->hh_C * (-ina - ik - il + r + U + net->hh_iext);
+    *m1 = m + dt * (am * (1.0 - m) - bm * m);
+    *n1 = n + dt * (an * (1.0 - n) - bn * n);
+    *h1 = h + dt * (ah * (1.0 - h) - bh * h);
+    *r1 = r + dt * p;
+    *p1 = p + dt * (-net->psc_a * net->psc_a * r - 2.0 * net->psc_a * p + S);
+    *c1 = c + dt * (-c / net->tau_c + (V >= net->hh_vpeak ? 1.0 : 0.0));
 }
 
 static double stimulus(const orc_net *net, int32_t j, int64_t n, int32_t *bg_count)
@@ -336,7 +398,8 @@ typedef struct {
     const int32_t *bg_count;
     const double *hist;
     int32_t hist_depth;
-    const double *r, *p;      /* model 1: PSC state (NULL = 0) */
+    const double *r, *p;      /* models 1, 2: PSC state (NULL = 0) */
+    const double *m, *n, *h;  /* model 2: gates (NULL = their values at -65 mV) */
 } orc_init;
 
 static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense,
@@ -344,12 +407,15 @@ static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense
 {
     int32_t N = net->n_nodes;
     int64_t E = net->n_edges;
-    const int izh = net->model == 1;
-    if (N <= 0 || E < 0 || n_steps < 0 || !(net->dt_ms > 0.0) || (net->model != 0 && !izh))
+    const int izh = net->model == 1, hh = net->model == 2, spiking = izh || hh;
+    if (N <= 0 || E < 0 || n_steps < 0 || !(net->dt_ms > 0.0) || (net->model != 0 && !spiking))
         return ORC_EINVAL;
-    if (izh ? !(net->iz_C > 0.0) || !(net->tau_c > 0.0) : !(net->tau_ms > 0.0)) return ORC_EINVAL;
+    if (izh && !(net->iz_C > 0.0)) return ORC_EINVAL;
+    if (hh && !(net->hh_C > 0.0)) return ORC_EINVAL;
+    if (spiking ? !(net->tau_c > 0.0) : !(net->tau_ms > 0.0)) return ORC_EINVAL;
+    const double vpeak = hh ? net->hh_vpeak : net->iz_vpeak;
     double v_rest = 0.0, w_rest = 0.0;
-    if (!izh && orc_rest_point(net->a, net->b, net->c, net->f, net->g, net->i_ext, &v_rest, &w_rest))
+    if (!spiking && orc_rest_point(net->a, net->b, net->c, net->f, net->g, net->i_ext, &v_rest, &w_rest))
         return ORC_EINVAL;
     int32_t dmax = 1;
     for (int64_t e = 0; e < E; ++e) {
@@ -374,12 +440,25 @@ static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense
     int32_t *bgc = (int32_t *)calloc((size_t)N, sizeof(int32_t));
     double *r = (double *)calloc((size_t)N, sizeof(double));
     double *p = (double *)calloc((size_t)N, sizeof(double));
-    if (!h.buf || !v || !w || !c || !S || !bgc || !r || !p) {
-        free(h.buf); free(v); free(w); free(c); free(S); free(bgc); free(r); free(p);
+    double *gm = (double *)calloc((size_t)N, sizeof(double));
+    double *gn = (double *)calloc((size_t)N, sizeof(double));
+    double *gh = (double *)calloc((size_t)N, sizeof(double));
+    if (!h.buf || !v || !w || !c || !S || !bgc || !r || !p || !gm || !gn || !gh) {
+        free(h.buf); free(v); free(w); free(c); free(S); free(bgc); free(r); free(p); free(gm); free(gn); free(gh);
         return ORC_ENOMEM;
     }
     if (izh)
         for (int32_t j = 0; j < N; ++j) v[j] = net->iz_vr;
+    if (hh) {
+        double m0, n0_, h0;
+        orc_hh_rest_gates(&m0, &n0_, &h0);
+        for (int32_t j = 0; j < N; ++j) {
+            v[j] = -65.0;
+            gm[j] = m0;
+            gn[j] = n0_;
+            gh[j] = h0;
+        }
+    }
     if (out->min_peak_gap)
         for (int32_t j = 0; j < N; ++j) out->min_peak_gap[j] = INFINITY;
     if (init) {
@@ -388,9 +467,14 @@ static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense
             w[j] = init->w[j];
             c[j] = init->c[j];
             bgc[j] = init->bg_count ? init->bg_count[j] : 0;
-            if (izh) {
+            if (spiking) {
                 r[j] = init->r ? init->r[j] : 0.0;
                 p[j] = init->p ? init->p[j] : 0.0;
+            }
+            if (hh) {
+                if (init->m) gm[j] = init->m[j];
+                if (init->n) gn[j] = init->n[j];
+                if (init->h) gh[j] = init->h[j];
             }
         }
         for (int64_t k = 1; k < h.depth && k < init->hist_depth; ++k)
@@ -407,12 +491,12 @@ static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense
 
     for (int64_t n = n0; n < n0 + n_steps; ++n) {
         /* record v~(n) (model 1: spd(V(n))) before anything reads the history of this step */
-        for (int32_t j = 0; j < N; ++j) hist_put(&h, n, j, izh ? (v[j] >= net->iz_vpeak ? 1.0 : 0.0) : v[j]);
+        for (int32_t j = 0; j < N; ++j) hist_put(&h, n, j, spiking ? (v[j] >= vpeak ? 1.0 : 0.0) : v[j]);
         /* S_j(n) = sum over edges i -> j of w_ij * v_i(n - D_ij) */
         for (int32_t j = 0; j < N; ++j) S[j] = 0.0;
         for (int64_t e = 0; e < E; ++e) {
             double past = hist_get(&h, n - net->delay[e], net->src[e]);
-            if (!izh && net->coupling == 1) past = v_rest + past;
+            if (!spiking && net->coupling == 1) past = v_rest + past;
             S[net->dst[e]] += net->weight[e] * past;
         }
         int sample = ((n + 1) % net->sample_every) == 0;
@@ -421,16 +505,28 @@ static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense
         for (int32_t j = 0; j < N; ++j) {
             double U = stimulus(net, j, n, bgc);
             double v1, w1, c1;
-            if (izh) {
+            if (spiking) {
                 double r1, p1;
-                izh_step(net, v[j], w[j], r[j], p[j], c[j], S[j], U, &v1, &w1, &r1, &p1, &c1);
+                int spike;
+                if (izh) {
+                    izh_step(net, v[j], w[j], r[j], p[j], c[j], S[j], U, &v1, &w1, &r1, &p1, &c1);
+                    spike = v1 >= vpeak;
+                } else {
+                    double m1, n1, h1;
+                    hh_step(net, v[j], gm[j], gn[j], gh[j], r[j], p[j], c[j], S[j], U, &v1, &m1, &n1, &h1, &r1, &p1,
+                            &c1);
+                    gm[j] = m1;
+                    gn[j] = n1;
+                    gh[j] = h1;
+                    w1 = 0.0;
+                    spike = v[j] < vpeak && v1 >= vpeak;   /* an upward crossing (no reset) */
+                }
                 r[j] = r1;
                 p[j] = p1;
                 if (out->min_peak_gap) {
-                    double gap = fabs(v1 - net->iz_vpeak);
+                    double gap = fabs(v1 - vpeak);
                     if (gap < out->min_peak_gap[j]) out->min_peak_gap[j] = gap;
                 }
-                int spike = v1 >= net->iz_vpeak;
                 if (spike) {
                     if (out->ev_count < out->ev_cap) {
                         out->ev_node[out->ev_count] = j;
@@ -483,15 +579,18 @@ static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense
     if (out->bg_count) memcpy(out->bg_count, bgc, sizeof(int32_t) * (size_t)N);
     if (out->r) memcpy(out->r, r, sizeof(double) * (size_t)N);
     if (out->p) memcpy(out->p, p, sizeof(double) * (size_t)N);
+    if (out->m) memcpy(out->m, gm, sizeof(double) * (size_t)N);
+    if (out->n) memcpy(out->n, gn, sizeof(double) * (size_t)N);
+    if (out->h) memcpy(out->h, gh, sizeof(double) * (size_t)N);
     if (out->hist_out) {
         int64_t n_end = n0 + n_steps;
         for (int32_t k = 0; k < out->hist_out_depth; ++k)
             for (int32_t j = 0; j < N; ++j) {
-                double now = izh ? (v[j] >= net->iz_vpeak ? 1.0 : 0.0) : v[j];
+                double now = spiking ? (v[j] >= vpeak ? 1.0 : 0.0) : v[j];
                 out->hist_out[(int64_t)k * N + j] = (k == 0) ? now : hist_get(&h, n_end - k, j);
             }
     }
-    free(h.buf); free(v); free(w); free(c); free(S); free(bgc); free(r); free(p);
+    free(h.buf); free(v); free(w); free(c); free(S); free(bgc); free(r); free(p); free(gm); free(gn); free(gh);
     return ORC_OK;
 }
 

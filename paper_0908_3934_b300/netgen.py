@@ -52,6 +52,11 @@ OBS_DEFAULT = dict(tau_ms=5.0, sample_every=20, gain=1.0, offset=0.0, sigma=0.05
 # paper gives the model, not these numbers.
 IZH_RS = dict(C=100.0, k=0.7, vr=-60.0, vt=-40.0, vpeak=35.0, vreset=-50.0, a=0.03, b=-2.0, d=100.0,
               i_ext=0.0, psc_a=0.2, tau_c=20.0)
+# Hodgkin-Huxley squid-axon constants in the modern convention (uF/cm^2, mS/cm^2,
+# mV; rest near -65 mV), V_peak = 0 mV for the spike indicator, and the same PSC
+# and calcium time constants as IZH_RS.
+HH_CLASSIC = dict(C=1.0, gna=120.0, gk=36.0, gl=0.3, ena=50.0, ek=-77.0, el=-54.387, vpeak=0.0, i_ext=0.0,
+                  psc_a=0.2, tau_c=20.0)
 
 
 @dataclasses.dataclass
@@ -74,8 +79,9 @@ class NetSpec:
     ring_depth: int = 0             # 0 = smallest power of two that holds the delays
     radius: float = 0.0             # radius the edges were drawn within (candidate pairs), 0 = unknown
     name: str = ""
-    model: str = "fhn"              # "fhn" or "izh" (Izhikevich + alpha PSC + calcium)
+    model: str = "fhn"              # "fhn", "izh" (Izhikevich) or "hh" (Hodgkin-Huxley), + alpha PSC + calcium
     izh: dict = dataclasses.field(default_factory=lambda: dict(IZH_RS))
+    hh: dict = dataclasses.field(default_factory=lambda: dict(HH_CLASSIC))
 
     @property
     def n_nodes(self) -> int:
@@ -103,6 +109,22 @@ def izhikevich(spec: "NetSpec", w_scale: float = 2000.0, pulse_amp: float = 2500
         pulses=[(j, t0, t1, pulse_amp) for (j, t0, t1, _) in spec.pulses],
         background=None if spec.background is None else dict(spec.background, amp=pulse_amp),
         obs=dict(spec.obs, gain=obs_gain), name=spec.name + "_izh")
+
+
+def hodgkin_huxley(spec: "NetSpec", w_scale: float = 10.0, pulse_amp: float = 20.0, obs_gain: float = 1.0,
+                   dt_ms: float = 0.03):
+    """The same network and controls with Hodgkin-Huxley + alpha-PSC nodes at the
+    paper's HH step dt = 0.03 ms: weights in PSC units (uA/cm^2; spd stays 1 for the
+    ~1 ms a spike spends above 0 mV, so a spike through weight w adds about w x 1 ms
+    to p), pulses and background pulses of pulse_amp uA/cm^2 (2 ms at 20 make a
+    resting node spike), calcium readout gain obs_gain; sample interval kept at 1 ms."""
+    every = max(1, int(round(1.0 / dt_ms)))
+    return dataclasses.replace(
+        spec, model="hh", hh=dict(HH_CLASSIC), dt_ms=dt_ms,
+        weight=(np.asarray(spec.weight) * w_scale).astype(np.float32),
+        pulses=[(j, t0, t1, pulse_amp) for (j, t0, t1, _) in spec.pulses],
+        background=None if spec.background is None else dict(spec.background, amp=pulse_amp),
+        obs=dict(spec.obs, gain=obs_gain, sample_every=every), name=spec.name + "_hh")
 
 
 def _signed_lognormal(rng, n, mu=-2.0, sigma=0.5, neg_frac=0.2):
