@@ -266,23 +266,28 @@ def run_batched(args, local, stream, rank):
             "speedup_vs_loop": t_loop / t}
 
 
-IZH_NODE_BYTES = 60.2  # V r/w 8, (W, c) r/w 16, (r, p) r/w 16, spike-ring write 4, piece list 4,
+IZH_NODE_BYTES = 56.2  # V r/w 8, (W, c) r/w 16, (r, p) r/w 16, spike-ring write 4, piece list 4,
                        # background counter 4 + caller id 4, readout 4 B / 20 steps
+HH_NODE_BYTES = 88.12  # the same + gates (m, n, h, pad) r/w 32, readout 4 B / 33 steps
 
 
-def run_izhikevich(args, spec, local, stream):
-    """The same network with Izhikevich + alpha-PSC + calcium nodes (the paper's own
-    benchmark model): step time of the autotuned kernel on the device, CUDA events
-    on the stream, `izh_steps` steps."""
+def run_spiking(args, spec, local, stream, model: str):
+    """The same network with spiking nodes -- Izhikevich (dt as the network's) or
+    Hodgkin-Huxley (dt = 0.03 ms), both with alpha-function PSCs and calcium, the
+    paper's two benchmark models: step time of the autotuned kernel on the device,
+    CUDA events on the stream."""
     import torch
     from paper_0908_3934_b300 import geonet
-    ispec = netgen.izhikevich(spec)
-    net = geonet.Net(ispec, device=local, stream=stream.cuda_stream, obs_capacity=max(64, args.izh_steps // 20 + 1))
+    hh = model == "hh"
+    ispec = netgen.hodgkin_huxley(spec) if hh else netgen.izhikevich(spec)
+    steps = args.hh_steps if hh else args.izh_steps
+    every = ispec.obs["sample_every"]
+    net = geonet.Net(ispec, device=local, stream=stream.cuda_stream, obs_capacity=max(64, steps // every + 1))
     net.gn_step(max(3, args.warmup))
     net.gn_synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    net.gn_step(args.izh_steps)
+    net.gn_step(steps)
     ev1.record(stream)
     torch.cuda.synchronize()
     t = ev0.elapsed_time(ev1) / 1e3
@@ -291,50 +296,56 @@ def run_izhikevich(args, spec, local, stream):
     net.gn_net_destroy()
     E, N = ispec.n_edges, ispec.n_nodes
     bytes_step = (E * STAGED_EDGE_BYTES + info["step_gathers"] * STAGED_GATHER_BYTES
-                  if info["step_kernel"] == 3 else E * EDGE_BYTES) + N * IZH_NODE_BYTES
+                  if info["step_kernel"] == 3 else E * EDGE_BYTES) + N * (HH_NODE_BYTES if hh else IZH_NODE_BYTES)
     peak, _ = peaks()
-    step_s = t / args.izh_steps
-    return {"workload": f"the same {N}-node network, Izhikevich regular-spiking nodes with alpha-function PSCs "
-                        f"and calcium, 5 Hz background pulses of 2500 pA, dt = {ispec.dt_ms} ms",
-            "value": E * args.izh_steps / t, "unit": METRIC, "ms_per_step": step_s * 1e3,
-            "rtf": ispec.dt_ms * 1e-3 / step_s, "spikes_per_node_per_s": n_spikes / N / (args.izh_steps * ispec.dt_ms * 1e-3),
+    step_s = t / steps
+    nodes = ("Hodgkin-Huxley nodes (classic squid-axon rates) with alpha-function PSCs and calcium, "
+             "5 Hz background pulses of 20 uA/cm^2" if hh else
+             "Izhikevich regular-spiking nodes with alpha-function PSCs and calcium, 5 Hz background pulses of 2500 pA")
+    return {"workload": f"the same {N}-node network, {nodes}, dt = {ispec.dt_ms} ms, max delay {info['max_delay']} steps",
+            "value": E * steps / t, "unit": METRIC, "ms_per_step": step_s * 1e3, "steps": steps,
+            "node_steps_per_s": N * steps / t,
+            "rtf": ispec.dt_ms * 1e-3 / step_s, "spikes_per_node_per_s": n_spikes / N / (steps * ispec.dt_ms * 1e-3),
             "step_kernel": KERNEL_NAMES[info["step_kernel"]],
             "roofline": {"bound": "hbm", "achieved": bytes_step / step_s / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": bytes_step / step_s / 1e9 / peak, "algorithmic_bytes_per_launch": bytes_step},
-            "gpu_launches": args.izh_steps + args.izh_steps // 64}
+            "gpu_launches": steps + steps // 64}
 
 
-def run_test_set(args, local, stream):
+def run_test_set(args, local, stream, model: str = "izh"):
     """The paper's own benchmark layout (Sec. 3.4, Sec. 3.5): the 80 networks of the
     standard test set (2 dimensions x 5 sizes x 4 classes x 2 densities) with
-    Izhikevich + alpha-PSC nodes at dt = 1 ms, each simulated for `test_set_steps`
-    steps (10 s of simulated time by default); real-time factor = simulated time /
-    device time (CUDA events), one network after another, each from its own graph."""
+    Izhikevich + alpha-PSC nodes at dt = 1 ms for `test_set_steps` steps (10 s of
+    simulated time by default), or Hodgkin-Huxley + alpha-PSC nodes at dt = 0.03 ms
+    for `test_set_hh_steps` steps (1 s); real-time factor = simulated time / device
+    time (CUDA events), one network after another, each from its own graph."""
     import statistics as st
     import torch
     from paper_0908_3934_b300 import geonet
+    hh = model == "hh"
+    steps = args.test_set_hh_steps if hh else args.test_set_steps
     rows = []
     for sp in netgen.test_set():
-        ispec = netgen.test_set_izh(sp)
+        ispec = netgen.test_set_hh(sp) if hh else netgen.test_set_izh(sp)
         net = geonet.Net(ispec, device=local, stream=stream.cuda_stream, obs_capacity=64)
         net.gn_step(128)
         net.gn_synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        net.gn_step(args.test_set_steps)
+        net.gn_step(steps)
         ev1.record(stream)
         torch.cuda.synchronize()
         t = ev0.elapsed_time(ev1) / 1e3
         net.gn_net_destroy()
-        rows.append((sp.name, sp.n_nodes, sp.n_edges, args.test_set_steps * ispec.dt_ms * 1e-3 / t))
+        rows.append((sp.name, sp.n_nodes, sp.n_edges, steps * ispec.dt_ms * 1e-3 / t))
     rtf = [r[3] for r in rows]
     by_class = {}
     for cls in netgen.TEST_SET_CLASSES:
         big = [r[3] for r in rows if f"_{cls}_" in r[0] and r[1] == max(netgen.TEST_SET_SIZES)]
         by_class[cls] = {"min": min(big), "max": max(big)}
+    nodes = ("Hodgkin-Huxley + alpha-PSC nodes, dt = 0.03 ms" if hh else "Izhikevich + alpha-PSC nodes, dt = 1 ms")
     return {"workload": f"the 80 test-set networks (N = 10 .. 1000, 2D / 3D, lattice / small world / scale free / "
-                        f"random, low / high density), Izhikevich + alpha-PSC nodes, dt = 1 ms, "
-                        f"{args.test_set_steps} steps each, 20 Hz background pulses",
+                        f"random, low / high density), {nodes}, {steps} steps each, 20 Hz background pulses",
             "metric": "real-time factor (simulated time / device time)",
             "rtf_min": min(rtf), "rtf_median": st.median(rtf), "rtf_max": max(rtf),
             "rtf_n1000_by_class": by_class,
@@ -427,8 +438,11 @@ def main():
     ap.add_argument("--no-estimator", action="store_true")
     ap.add_argument("--no-izh", action="store_true", help="skip the Izhikevich-model measurement")
     ap.add_argument("--izh-steps", type=int, default=2000)
-    ap.add_argument("--no-test-set", action="store_true", help="skip the 80-network test-set sweep")
-    ap.add_argument("--test-set-steps", type=int, default=10000)
+    ap.add_argument("--no-hh", action="store_true", help="skip the Hodgkin-Huxley-model measurements")
+    ap.add_argument("--hh-steps", type=int, default=2000)
+    ap.add_argument("--no-test-set", action="store_true", help="skip the 80-network test-set sweeps")
+    ap.add_argument("--test-set-steps", type=int, default=10000, help="Izhikevich steps per test-set network")
+    ap.add_argument("--test-set-hh-steps", type=int, default=33333, help="Hodgkin-Huxley steps per test-set network")
     ap.add_argument("--step-kernel", type=int, default=0, choices=[0, 1, 2, 3],
                     help="0: autotuned, 1: one row block per CTA, 2: persistent bulk-copy pipelined kernel, "
                          "3: staged tiles (distinct gathers in shared memory)")
@@ -543,9 +557,13 @@ def main():
         bt["value"], _, bt["seconds"] = replica_rate(bt["value"] * bt["seconds"], bt["seconds"], dev)
         line["batched"] = bt
     if not args.no_izh and rank == 0:
-        line["izhikevich"] = run_izhikevich(args, spec, local, stream)
+        line["izhikevich"] = run_spiking(args, spec, local, stream, "izh")
+    if not args.no_hh and rank == 0:
+        line["hodgkin_huxley"] = run_spiking(args, spec, local, stream, "hh")
     if not args.no_test_set and rank == 0:
         line["test_set"] = run_test_set(args, local, stream)
+        if not args.no_hh:
+            line["test_set_hh"] = run_test_set(args, local, stream, "hh")
     if not args.no_estimator and rank == 0:
         line["estimator"] = run_estimator(args, local, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -80,11 +80,27 @@ typedef struct {
  * starts at V = v_r, W = r = p = c = 0 with no spike before t = 0; the history ring
  * holds spd(V); events are spikes (V >= v_peak) and a node's arrival is its first
  * spike.  The coupling field is ignored; the batched form does not take this model
- * (GN_EINVAL). */
-enum { GN_MODEL_FHN = 0, GN_MODEL_IZH = 1 };
+ * (GN_EINVAL).
+ *
+ * Third model: Hodgkin-Huxley nodes (Sec. 3.1 and 3.4 name the model and its state
+ * {v, m, n, h}; the rates are the classic squid-axon ones, modern convention, rest
+ * near -65 mV) with the same alpha-function PSC, spike indicator and calcium, Euler:
+ *   V' = V + dt/C [-g_na m^3 h (V - e_na) - g_k n^4 (V - e_k) - g_l (V - e_l) + r + U + i_ext]
+ *   x' = x + dt (alpha_x(V) (1 - x) - beta_x(V) x),  x in {m, n, h}, with
+ *   alpha_m = 0.1 (V + 40) / (1 - e^-(V+40)/10), beta_m = 4 e^-(V+65)/18,
+ *   alpha_h = 0.07 e^-(V+65)/20,                 beta_h = 1 / (1 + e^-(V+35)/10),
+ *   alpha_n = 0.01 (V + 55) / (1 - e^-(V+55)/10), beta_n = 0.125 e^-(V+65)/80
+ *   (mV, ms; the 0/0 at -40 and -55 mV takes its limit).  r, p, c and y as above with
+ *   spd(V) = 1 while V >= v_peak; no reset, and events are the upward crossings of
+ *   v_peak.  The state starts at V = -65 mV with each gate at alpha / (alpha + beta)
+ *   there, r = p = c = 0; W is unused (0).  The batched form does not take it. */
+enum { GN_MODEL_FHN = 0, GN_MODEL_IZH = 1, GN_MODEL_HH = 2 };
 typedef struct {
     double C, k, v_r, v_t, v_peak, v_reset, a, b, d, i_ext, psc_a, tau_c;
 } gn_izh_params;
+typedef struct {
+    double C, g_na, g_k, g_l, e_na, e_k, e_l, v_peak, i_ext, psc_a, tau_c;
+} gn_hh_params;
 
 /* Readout (Sec. 3.3): c~' = c~ + (dt/tau_ms)(v~' - c~) every step; every
  * sample_every steps y = gain (V* + c~) + offset + sigma xi, xi ~ N(0, 1) drawn
@@ -134,8 +150,9 @@ typedef struct {
                                     explicitly chosen kernel 1 or 3 (default 0) */
     void *cuda_stream;           /* cudaStream_t to run on; NULL: the library makes its own */
     int32_t device;              /* CUDA device ordinal */
-    int32_t model;               /* GN_MODEL_FHN (0) or GN_MODEL_IZH (1) */
+    int32_t model;               /* GN_MODEL_FHN (0), GN_MODEL_IZH (1) or GN_MODEL_HH (2) */
     gn_izh_params izh;           /* used when model == GN_MODEL_IZH (C > 0, tau_c > 0, all finite) */
+    gn_hh_params hh;             /* used when model == GN_MODEL_HH (C > 0, tau_c > 0, all finite) */
 } gn_net_desc;
 
 /* A pulse of amplitude amp on node over [t_on_ms, t_off_ms): the steps
@@ -233,12 +250,17 @@ GN_API gn_status gn_get_state(gn_net *net, float *v, float *w, float *c, int32_t
 GN_API gn_status gn_set_state(gn_net *net, const float *hist, int32_t depth, const float *w, const float *c,
                               const int32_t *bg_count, int64_t step);
 
-/* Izhikevich model only (GN_EINVAL otherwise): V, the PSC variables r and p, in
- * caller node order (any pointer may be NULL).  gn_get_state / gn_set_state carry
- * W and calcium in w and c, and the history is spd(V) in {0, 1}; gn_get_state's v is
- * V as well. */
+/* Spiking models only (Izhikevich or Hodgkin-Huxley; GN_EINVAL otherwise): V, the
+ * PSC variables r and p, in caller node order (any pointer may be NULL).
+ * gn_get_state / gn_set_state carry W (0 for Hodgkin-Huxley) and calcium in w and
+ * c, and the history is spd(V) in {0, 1}; gn_get_state's v is V as well. */
 GN_API gn_status gn_get_izh_state(gn_net *net, float *V, float *r, float *p);
 GN_API gn_status gn_set_izh_state(gn_net *net, const float *V, const float *r, const float *p);
+
+/* Hodgkin-Huxley model only (GN_EINVAL otherwise): the gates m, n, h in caller node
+ * order (any pointer may be NULL; a set leaves a NULL gate as it is). */
+GN_API gn_status gn_get_hh_gates(gn_net *net, float *m, float *n, float *h);
+GN_API gn_status gn_set_hh_gates(gn_net *net, const float *m, const float *n, const float *h);
 
 /* History: out[k][j] = v~_j(step - k), k = 0..depth-1, depth <= ring_depth. */
 GN_API gn_status gn_get_history(gn_net *net, float *out, int32_t depth);

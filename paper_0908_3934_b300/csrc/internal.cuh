@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 namespace gn {
 
@@ -78,13 +79,30 @@ struct StepArgs {
     int32_t st_xcap;         // entry slots of a CTA's shared memory (largest entry count)
     uint32_t wait_limit;     // polls of a bounded mbarrier wait before it reports kStatusTimeout
     // node model: 0 FitzHugh-Nagumo (fields above), 1 Izhikevich + alpha PSC + calcium,
-    // whose ring holds spd(V) and whose state is iz_v (V), wc (W, calcium), rp (r, p)
+    // 2 Hodgkin-Huxley + alpha PSC + calcium.  The spiking models' ring holds spd(V)
+    // and their state is iz_v (V), wc (W, calcium), rp (r, p), plus hh_g (m, n, h, 0)
+    // for model 2; iz_dtc (dt / C), iz_vpeak and iz_iext serve both.
     int32_t model;
     float iz_dtc, iz_k, iz_vr, iz_vt, iz_vpeak, iz_vreset, iz_dta, iz_b, iz_d, iz_iext;
     float ps_a2, ps_2a, ca_q;  // PSC a^2, 2a; calcium 1 / tau_c
+    float hh_gna, hh_gk, hh_gl, hh_ena, hh_ek, hh_el;
     float *iz_v;
     float2 *rp;
+    float4 *hh_g;
 };
+
+// Calls f(std::integral_constant<int, m>) for node model m: every step kernel is
+// instantiated once per model, so no model's code sits in another model's kernel
+// (a branch to the Hodgkin-Huxley update alone cost the FitzHugh-Nagumo kernel 3 %).
+template <class F>
+inline cudaError_t with_model(int model, F &&f)
+{
+    switch (model) {
+        case 1: return f(std::integral_constant<int, 1>{});
+        case 2: return f(std::integral_constant<int, 2>{});
+        default: return f(std::integral_constant<int, 0>{});
+    }
+}
 
 constexpr uint32_t kDefaultWaitLimit = 1u << 22;
 
@@ -127,7 +145,7 @@ struct StagedShape {
 extern const StagedShape kStagedShapes[kNumStagedShapes];
 cudaError_t launch_step_staged(const StepArgs &a, int n_tiles, int k, const StagedShape &shape, bool packed,
                                bool stream_edges, size_t smem_bytes, cudaStream_t s);
-cudaError_t step_staged_prepare(const StagedShape &shape, bool packed, bool stream_edges, size_t smem_bytes);
+cudaError_t step_staged_prepare(const StagedShape &shape, int model, bool packed, bool stream_edges, size_t smem_bytes);
 // batched form with the staged layout: one launch per step over every member's
 // tiles (tile_net[t] = the member of tile t), tiles cut with kBatchStagedShape
 constexpr StagedShape kBatchStagedShape = {128, 3072, 4096, 256, 0};
@@ -137,7 +155,7 @@ cudaError_t batch_staged_prepare(bool packed, bool stream_edges, size_t smem_byt
 // persistent bulk-copy pipelined variant (k_step_pipe.cu); grid = CTAs to launch
 cudaError_t launch_step_pipe(const StepArgs &a, int grid, int k, bool packed, bool stream_edges, cudaStream_t s);
 int step_pipe_smem_bytes(bool packed);
-cudaError_t step_pipe_prepare(bool packed, bool stream_edges, int *ctas_per_sm);
+cudaError_t step_pipe_prepare(int model, bool packed, bool stream_edges, int *ctas_per_sm);
 // batched form (k_batch.cu): one persistent launch over many networks
 constexpr int kNumBatchShapes = 3;
 extern const int kBatchThreads[kNumBatchShapes];

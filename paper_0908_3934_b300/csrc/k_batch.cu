@@ -68,7 +68,7 @@ __device__ __forceinline__ void batch_block(const StepArgs &a, int64_t n, int b,
         if (t == 0) {
             float S = 0.0f;
             for (int i = 0; i < T / 32; ++i) S += s_long[i];
-            node_update(a, r0, n, v, wc, S);
+            node_update<0>(a, r0, n, v, wc, S);
         }
         __syncthreads();
         return;
@@ -113,7 +113,7 @@ __device__ __forceinline__ void batch_block(const StepArgs &a, int64_t n, int b,
     }
     __syncthreads();
     if (warp_row) S = s_long[t];
-    if (t < nr) node_update(a, r, n, v, wc, S);
+    if (t < nr) node_update<0>(a, r, n, v, wc, S);
     __syncthreads();  // s_prod, s_rp and s_long are reused by the next block
 }
 

@@ -30,7 +30,7 @@ using namespace step;
 __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
-template <int T, int EPT, int MINB, bool kPacked, bool kStream>
+template <int kM, int T, int EPT, int MINB, bool kPacked, bool kStream>
 __global__ void __launch_bounds__(T, MINB) k_step(const StepArgs a, const int k)
 {
     constexpr int CAP = T * EPT;
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(T, MINB) k_step(const StepArgs a, const int k)
     float2 wc = make_float2(0.0f, 0.0f);
     int32_t cnt0 = kLoad;
     if (t < nr) {
-        v = a.ring[(n & a.ring_mask) * a.ring_stride + r];
+        if constexpr (kM == 0) v = a.ring[(n & a.ring_mask) * a.ring_stride + r];  // spiking models keep V apart
         wc = a.wc[r];
         if (a.bg_thr) cnt0 = a.bgc[r];
     }
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(T, MINB) k_step(const StepArgs a, const int k)
         if (t == 0) {
             float S = 0.0f;
             for (int i = 0; i < T / 32; ++i) S += s_long[i];
-            node_update(a, r0, n, v, wc, S, orig, cnt0);
+            node_update<kM>(a, r0, n, v, wc, S, orig, cnt0);
         }
         return;
     }
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(T, MINB) k_step(const StepArgs a, const int k)
     if (warp_row) S = s_long[t];
 
     // 4. node update
-    if (t < nr) node_update(a, r, n, v, wc, S, orig, cnt0);
+    if (t < nr) node_update<kM>(a, r, n, v, wc, S, orig, cnt0);
 }
 
 __global__ void k_advance(int64_t *d_step, int64_t by)
@@ -157,7 +157,7 @@ __global__ void k_advance(int64_t *d_step, int64_t by)
     *d_step += by;
 }
 
-template <int T, int EPT, int MINB, bool kPacked, bool kStream>
+template <int kM, int T, int EPT, int MINB, bool kPacked, bool kStream>
 cudaError_t launch_pdl(const StepArgs &a, int n_blocks, int k, cudaStream_t s)
 {
     cudaLaunchConfig_t cfg = {};
@@ -170,17 +170,17 @@ cudaError_t launch_pdl(const StepArgs &a, int n_blocks, int k, cudaStream_t s)
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_step<T, EPT, MINB, kPacked, kStream>, a, k);
+    return cudaLaunchKernelEx(&cfg, k_step<kM, T, EPT, MINB, kPacked, kStream>, a, k);
 }
 
-template <int T, int EPT, int MINB>
+template <int kM, int T, int EPT, int MINB>
 cudaError_t launch_shape(const StepArgs &a, int n_blocks, int k, bool packed, bool stream_edges, cudaStream_t s)
 {
     if (packed)
-        return stream_edges ? launch_pdl<T, EPT, MINB, true, true>(a, n_blocks, k, s)
-                            : launch_pdl<T, EPT, MINB, true, false>(a, n_blocks, k, s);
-    return stream_edges ? launch_pdl<T, EPT, MINB, false, true>(a, n_blocks, k, s)
-                        : launch_pdl<T, EPT, MINB, false, false>(a, n_blocks, k, s);
+        return stream_edges ? launch_pdl<kM, T, EPT, MINB, true, true>(a, n_blocks, k, s)
+                            : launch_pdl<kM, T, EPT, MINB, true, false>(a, n_blocks, k, s);
+    return stream_edges ? launch_pdl<kM, T, EPT, MINB, false, true>(a, n_blocks, k, s)
+                        : launch_pdl<kM, T, EPT, MINB, false, false>(a, n_blocks, k, s);
 }
 
 }  // namespace
@@ -192,14 +192,17 @@ cudaError_t launch_step(const StepArgs &a, int n_blocks, int k, int shape, bool 
                         cudaStream_t s)
 {
     if (n_blocks <= 0) return cudaSuccess;
-    switch (shape) {
-        case 0: return launch_shape<256, 8, 1>(a, n_blocks, k, packed, stream_edges, s);
-        case 1: return launch_shape<256, 8, 8>(a, n_blocks, k, packed, stream_edges, s);
-        case 2: return launch_shape<128, 16, 1>(a, n_blocks, k, packed, stream_edges, s);
-        case 3: return launch_shape<128, 8, 16>(a, n_blocks, k, packed, stream_edges, s);
-        case 4: return launch_shape<512, 8, 1>(a, n_blocks, k, packed, stream_edges, s);
-        default: return cudaErrorInvalidValue;
-    }
+    return with_model(a.model, [&](auto m) {
+        constexpr int M = decltype(m)::value;
+        switch (shape) {
+            case 0: return launch_shape<M, 256, 8, 1>(a, n_blocks, k, packed, stream_edges, s);
+            case 1: return launch_shape<M, 256, 8, 8>(a, n_blocks, k, packed, stream_edges, s);
+            case 2: return launch_shape<M, 128, 16, 1>(a, n_blocks, k, packed, stream_edges, s);
+            case 3: return launch_shape<M, 128, 8, 16>(a, n_blocks, k, packed, stream_edges, s);
+            case 4: return launch_shape<M, 512, 8, 1>(a, n_blocks, k, packed, stream_edges, s);
+            default: return cudaErrorInvalidValue;
+        }
+    });
 }
 
 cudaError_t launch_advance(int64_t *d_step, int64_t by, cudaStream_t s)

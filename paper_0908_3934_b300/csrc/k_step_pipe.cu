@@ -79,7 +79,7 @@ __device__ __forceinline__ void issue_block(const StepArgs &a, int b, uint8_t *s
     bulk_g2s(stage + L::WC, a.wc + wa, bwc, bar);
 }
 
-template <int T, int EPT, int S, int KEYB, bool kStream>
+template <int kM, int T, int EPT, int S, int KEYB, bool kStream>
 __global__ void __launch_bounds__(T) k_step_pipe(const StepArgs a, const int k)
 {
     using L = PipeLayout<T, EPT, KEYB>;
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(T) k_step_pipe(const StepArgs a, const int k)
             if (t == 0) {
                 float S_in = 0.0f;
                 for (int w = 0; w < T / 32; ++w) S_in += s_long[w];
-                node_update(a, r0, n, s_v[0], s_wc[0], S_in);
+                node_update<kM>(a, r0, n, s_v[0], s_wc[0], S_in);
             }
             __syncthreads();
             continue;
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(T) k_step_pipe(const StepArgs a, const int k)
         }
         __syncthreads();
         if (warp_row) S_in = s_long[t];
-        if (t < nr) node_update(a, r0 + t, n, s_v[t], s_wc[t], S_in);
+        if (t < nr) node_update<kM>(a, r0 + t, n, s_v[t], s_wc[t], S_in);
         __syncthreads();  // stage st and s_prod are free again
     }
 
@@ -239,22 +239,22 @@ __global__ void __launch_bounds__(T) k_step_pipe(const StepArgs a, const int k)
     }
 }
 
-template <int T, int EPT, int S, int KEYB, bool kStream>
+template <int kM, int T, int EPT, int S, int KEYB, bool kStream>
 cudaError_t launch_variant(const StepArgs &a, int grid, int k, cudaStream_t s)
 {
     constexpr int smem = pipe_smem<T, EPT, S, KEYB>();
-    k_step_pipe<T, EPT, S, KEYB, kStream><<<grid, T, smem, s>>>(a, k);
+    k_step_pipe<kM, T, EPT, S, KEYB, kStream><<<grid, T, smem, s>>>(a, k);
     return cudaGetLastError();
 }
 
-template <int T, int EPT, int S, int KEYB, bool kStream>
+template <int kM, int T, int EPT, int S, int KEYB, bool kStream>
 cudaError_t prepare_variant(int *ctas)
 {
     constexpr int smem = pipe_smem<T, EPT, S, KEYB>();
-    cudaError_t e = cudaFuncSetAttribute(k_step_pipe<T, EPT, S, KEYB, kStream>,
+    cudaError_t e = cudaFuncSetAttribute(k_step_pipe<kM, T, EPT, S, KEYB, kStream>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_step_pipe<T, EPT, S, KEYB, kStream>, T, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_step_pipe<kM, T, EPT, S, KEYB, kStream>, T, smem);
 }
 
 constexpr int kT = 256, kEPT = 8, kS = 3;  // shape 0 of kStepShapes
@@ -266,23 +266,29 @@ int step_pipe_smem_bytes(bool packed)
     return packed ? pipe_smem<kT, kEPT, kS, 4>() : pipe_smem<kT, kEPT, kS, 8>();
 }
 
-cudaError_t step_pipe_prepare(bool packed, bool stream_edges, int *ctas_per_sm)
+cudaError_t step_pipe_prepare(int model, bool packed, bool stream_edges, int *ctas_per_sm)
 {
-    if (packed)
-        return stream_edges ? prepare_variant<kT, kEPT, kS, 4, true>(ctas_per_sm)
-                            : prepare_variant<kT, kEPT, kS, 4, false>(ctas_per_sm);
-    return stream_edges ? prepare_variant<kT, kEPT, kS, 8, true>(ctas_per_sm)
-                        : prepare_variant<kT, kEPT, kS, 8, false>(ctas_per_sm);
+    return with_model(model, [&](auto m) {
+        constexpr int M = decltype(m)::value;
+        if (packed)
+            return stream_edges ? prepare_variant<M, kT, kEPT, kS, 4, true>(ctas_per_sm)
+                                : prepare_variant<M, kT, kEPT, kS, 4, false>(ctas_per_sm);
+        return stream_edges ? prepare_variant<M, kT, kEPT, kS, 8, true>(ctas_per_sm)
+                            : prepare_variant<M, kT, kEPT, kS, 8, false>(ctas_per_sm);
+    });
 }
 
 cudaError_t launch_step_pipe(const StepArgs &a, int grid, int k, bool packed, bool stream_edges, cudaStream_t s)
 {
     if (grid <= 0 || a.n_blocks <= 0) return cudaSuccess;
-    if (packed)
-        return stream_edges ? launch_variant<kT, kEPT, kS, 4, true>(a, grid, k, s)
-                            : launch_variant<kT, kEPT, kS, 4, false>(a, grid, k, s);
-    return stream_edges ? launch_variant<kT, kEPT, kS, 8, true>(a, grid, k, s)
-                        : launch_variant<kT, kEPT, kS, 8, false>(a, grid, k, s);
+    return with_model(a.model, [&](auto m) {
+        constexpr int M = decltype(m)::value;
+        if (packed)
+            return stream_edges ? launch_variant<M, kT, kEPT, kS, 4, true>(a, grid, k, s)
+                                : launch_variant<M, kT, kEPT, kS, 4, false>(a, grid, k, s);
+        return stream_edges ? launch_variant<M, kT, kEPT, kS, 8, true>(a, grid, k, s)
+                            : launch_variant<M, kT, kEPT, kS, 8, false>(a, grid, k, s);
+    });
 }
 
 }  // namespace gn

@@ -44,7 +44,7 @@ constexpr int kThreadsSE = 1024;
 constexpr int kThreadsL2 = 1536;
 
 // One tile's step (the CTA's work) for network `a`; `tile` indexes a.st_tile.
-template <int T, bool kSE, bool kPacked, bool kStream>
+template <int kM, int T, bool kSE, bool kPacked, bool kStream>
 __device__ __forceinline__ void staged_tile(const StepArgs &a, const int tile, const int k)
 {
     // [mbarrier 16 B][keys][values (wide keys only)][entry weights][entry indices][piece sums];
@@ -105,7 +105,7 @@ __device__ __forceinline__ void staged_tile(const StepArgs &a, const int tile, c
     float2 wc = make_float2(0.0f, 0.0f);
     int32_t cnt0 = kLoad;
     if (own) {
-        v = a.ring[(n & a.ring_mask) * a.ring_stride + r];
+        if constexpr (kM == 0) v = a.ring[(n & a.ring_mask) * a.ring_stride + r];  // spiking models keep V apart
         wc = a.wc[r];
         if (a.bg_thr) cnt0 = a.bgc[r];
     }
@@ -186,14 +186,14 @@ __device__ __forceinline__ void staged_tile(const StepArgs &a, const int tile, c
                 for (int l = 0; l < o; ++l) x[l] = __fadd_rn(x[l], x[l + o]);
             S = x[0];
         }
-        node_update(a, r, n, v, wc, S, orig, cnt0);
+        node_update<kM>(a, r, n, v, wc, S, orig, cnt0);
     }
 }
 
-template <int T, bool kSE, bool kPacked, bool kStream>
+template <int kM, int T, bool kSE, bool kPacked, bool kStream>
 __global__ void __launch_bounds__(T, (kSE ? kThreadsSE : kThreadsL2) / T) k_step_staged(const StepArgs a, const int k)
 {
-    staged_tile<T, kSE, kPacked, kStream>(a, blockIdx.x, k);
+    staged_tile<kM, T, kSE, kPacked, kStream>(a, blockIdx.x, k);
 }
 
 // Batched form, one launch per step over the tiles of every member network: the
@@ -208,10 +208,10 @@ __global__ void __launch_bounds__(T, kThreadsL2 / T) k_batch_staged(const StepAr
     uint32_t *dst = reinterpret_cast<uint32_t *>(&s_a);
     for (int i = threadIdx.x; i < static_cast<int>(sizeof(StepArgs) / 4); i += T) dst[i] = __ldg(src + i);
     __syncthreads();
-    staged_tile<T, false, kPacked, kStream>(s_a, blockIdx.x, k);
+    staged_tile<0, T, false, kPacked, kStream>(s_a, blockIdx.x, k);  // FitzHugh-Nagumo members only
 }
 
-template <int T, bool kSE, bool kPacked, bool kStream>
+template <int kM, int T, bool kSE, bool kPacked, bool kStream>
 cudaError_t launch_t(const StepArgs &a, int n_tiles, int k, size_t smem, cudaStream_t s)
 {
     cudaLaunchConfig_t cfg = {};
@@ -224,44 +224,47 @@ cudaError_t launch_t(const StepArgs &a, int n_tiles, int k, size_t smem, cudaStr
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_step_staged<T, kSE, kPacked, kStream>, a, k);
+    return cudaLaunchKernelEx(&cfg, k_step_staged<kM, T, kSE, kPacked, kStream>, a, k);
 }
 
 // The kernel instance of a shape and edge format: launch it (smem > 0 with a
 // launch) or raise its dynamic shared-memory limit (launch false).
-template <int T, bool kSE>
+template <int kM, int T, bool kSE>
 cudaError_t dispatch_fmt(bool launch, const StepArgs *a, int n_tiles, int k, bool packed, bool stream_edges,
                          size_t smem, cudaStream_t s)
 {
     if (launch) {
         if (packed)
-            return stream_edges ? launch_t<T, kSE, true, true>(*a, n_tiles, k, smem, s)
-                                : launch_t<T, kSE, true, false>(*a, n_tiles, k, smem, s);
-        return stream_edges ? launch_t<T, kSE, false, true>(*a, n_tiles, k, smem, s)
-                            : launch_t<T, kSE, false, false>(*a, n_tiles, k, smem, s);
+            return stream_edges ? launch_t<kM, T, kSE, true, true>(*a, n_tiles, k, smem, s)
+                                : launch_t<kM, T, kSE, true, false>(*a, n_tiles, k, smem, s);
+        return stream_edges ? launch_t<kM, T, kSE, false, true>(*a, n_tiles, k, smem, s)
+                            : launch_t<kM, T, kSE, false, false>(*a, n_tiles, k, smem, s);
     }
     const int b = static_cast<int>(smem);
     const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
     if (packed)
-        return stream_edges ? cudaFuncSetAttribute(k_step_staged<T, kSE, true, true>, at, b)
-                            : cudaFuncSetAttribute(k_step_staged<T, kSE, true, false>, at, b);
-    return stream_edges ? cudaFuncSetAttribute(k_step_staged<T, kSE, false, true>, at, b)
-                        : cudaFuncSetAttribute(k_step_staged<T, kSE, false, false>, at, b);
+        return stream_edges ? cudaFuncSetAttribute(k_step_staged<kM, T, kSE, true, true>, at, b)
+                            : cudaFuncSetAttribute(k_step_staged<kM, T, kSE, true, false>, at, b);
+    return stream_edges ? cudaFuncSetAttribute(k_step_staged<kM, T, kSE, false, true>, at, b)
+                        : cudaFuncSetAttribute(k_step_staged<kM, T, kSE, false, false>, at, b);
 }
 
-cudaError_t dispatch(bool launch, const StagedShape &sh, const StepArgs *a, int n_tiles, int k, bool packed,
-                     bool stream_edges, size_t smem, cudaStream_t s)
+cudaError_t dispatch(bool launch, const StagedShape &sh, int model, const StepArgs *a, int n_tiles, int k,
+                     bool packed, bool stream_edges, size_t smem, cudaStream_t s)
 {
     const bool se = sh.stage_entries != 0;
-    switch (sh.threads) {
-        case 128:
-            return se ? dispatch_fmt<128, true>(launch, a, n_tiles, k, packed, stream_edges, smem, s)
-                      : dispatch_fmt<128, false>(launch, a, n_tiles, k, packed, stream_edges, smem, s);
-        case 256:
-            return se ? dispatch_fmt<256, true>(launch, a, n_tiles, k, packed, stream_edges, smem, s)
-                      : dispatch_fmt<256, false>(launch, a, n_tiles, k, packed, stream_edges, smem, s);
-        default: return cudaErrorInvalidValue;
-    }
+    return with_model(model, [&](auto m) {
+        constexpr int M = decltype(m)::value;
+        switch (sh.threads) {
+            case 128:
+                return se ? dispatch_fmt<M, 128, true>(launch, a, n_tiles, k, packed, stream_edges, smem, s)
+                          : dispatch_fmt<M, 128, false>(launch, a, n_tiles, k, packed, stream_edges, smem, s);
+            case 256:
+                return se ? dispatch_fmt<M, 256, true>(launch, a, n_tiles, k, packed, stream_edges, smem, s)
+                          : dispatch_fmt<M, 256, false>(launch, a, n_tiles, k, packed, stream_edges, smem, s);
+            default: return cudaErrorInvalidValue;
+        }
+    });
 }
 
 }  // namespace
@@ -275,12 +278,12 @@ cudaError_t launch_step_staged(const StepArgs &a, int n_tiles, int k, const Stag
                                bool stream_edges, size_t smem_bytes, cudaStream_t s)
 {
     if (n_tiles <= 0) return cudaSuccess;
-    return dispatch(true, shape, &a, n_tiles, k, packed, stream_edges, smem_bytes, s);
+    return dispatch(true, shape, a.model, &a, n_tiles, k, packed, stream_edges, smem_bytes, s);
 }
 
-cudaError_t step_staged_prepare(const StagedShape &shape, bool packed, bool stream_edges, size_t smem_bytes)
+cudaError_t step_staged_prepare(const StagedShape &shape, int model, bool packed, bool stream_edges, size_t smem_bytes)
 {
-    return dispatch(false, shape, nullptr, 0, 0, packed, stream_edges, smem_bytes, nullptr);
+    return dispatch(false, shape, model, nullptr, 0, 0, packed, stream_edges, smem_bytes, nullptr);
 }
 
 namespace {

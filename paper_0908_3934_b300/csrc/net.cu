@@ -58,6 +58,7 @@ struct gn_net {
     size_t bytes = 0;
     DevArray<float> ring, ew, bias, obs, p_amp, iz_v;
     DevArray<float2> wc, rp;
+    DevArray<float4> hh_g;           // Hodgkin-Huxley gates (m, n, h, 0)
     int32_t model = GN_MODEL_FHN;
     DevArray<uint8_t> ekey;
     DevArray<int32_t> row_ptr, blk, bgc, d_perm, p_node, ev_node, d_npulses;
@@ -105,6 +106,7 @@ struct gn_net {
         for (auto *a : {&ring, &ew, &bias, &obs, &p_amp, &iz_v}) a->release();
         wc.release();
         rp.release();
+        hh_g.release();
         ekey.release();
         for (auto *a : {&row_ptr, &blk, &bgc, &d_perm, &p_node, &ev_node, &d_npulses}) a->release();
         for (auto *a : {&first, &p_on, &p_off, &ev_step, &d_step}) a->release();
@@ -201,7 +203,7 @@ bool set_staged(gn_net *net, int shape)
                         (sh.stage_entries ? static_cast<size_t>(net->st_max_x) * 6 : 0) +
                         static_cast<size_t>(net->st_max_p) * 4;
     if (smem > static_cast<size_t>(max_smem)) return false;
-    cuda_check(gn::step_staged_prepare(sh, net->packed, net->stream_edges, smem), "staged kernel setup");
+    cuda_check(gn::step_staged_prepare(sh, net->model, net->packed, net->stream_edges, smem), "staged kernel setup");
     net->st_smem = smem;
     net->st_shape = shape;
     return true;
@@ -242,7 +244,7 @@ void configure(gn_net *net, int kind, int shape)
     net->step_kernel = kind;
     if (kind == 2) {
         int per_sm = 0, sms = 0;
-        cuda_check(gn::step_pipe_prepare(net->packed, net->stream_edges, &per_sm), "step kernel setup");
+        cuda_check(gn::step_pipe_prepare(net->model, net->packed, net->stream_edges, &per_sm), "step kernel setup");
         cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, net->device), "device query");
         if (per_sm < 1) fail(GN_ECUDA, "the pipelined step kernel does not fit on an SM");
         net->grid = std::min(net->n_blocks, per_sm * sms);
@@ -261,9 +263,9 @@ std::string tune_key(const gn_net *net)
     for (char &ch : name)
         if (ch == ' ') ch = '_';
     char buf[256];
-    snprintf(buf, sizeof buf, "%s|sm%d|N%d|E%lld|R%d|p%d|s%d|bg%d", name.c_str(), prop.multiProcessorCount, net->N,
+    snprintf(buf, sizeof buf, "%s|sm%d|N%d|E%lld|R%d|p%d|s%d|bg%d|m%d", name.c_str(), prop.multiProcessorCount, net->N,
              static_cast<long long>(net->E), net->R, net->packed ? 1 : 0, net->stream_edges ? 1 : 0,
-             net->args.bg_thr ? 1 : 0);
+             net->args.bg_thr ? 1 : 0, net->model);
     return buf;
 }
 
@@ -316,6 +318,7 @@ void autotune(gn_net *net)
     size_t scratch_bytes = 0;
     DevArray<float> ring, obs, iz_v;
     DevArray<float2> wc, rp;
+    DevArray<float4> hh_g;
     DevArray<int32_t> bgc, evn;
     DevArray<int64_t> first, evs, dstep;
     DevArray<unsigned long long> evc;
@@ -324,6 +327,7 @@ void autotune(gn_net *net)
     auto cleanup = [&] {
         ring.release(); obs.release(); wc.release(); bgc.release(); evn.release(); first.release();
         evs.release(); dstep.release(); evc.release(); status.release(); iz_v.release(); rp.release();
+        hh_g.release();
         if (t0) cudaEventDestroy(t0);
         if (t1) cudaEventDestroy(t1);
     };
@@ -339,11 +343,15 @@ void autotune(gn_net *net)
         evc.alloc(1, &scratch_bytes);
         dstep.alloc(1, &scratch_bytes);
         status.alloc(1, &scratch_bytes);
-        if (net->model == GN_MODEL_IZH) {  // the Izhikevich state too, from the net's own values
+        if (net->model != GN_MODEL_FHN) {  // the spiking models' state too, from the net's own values
             iz_v.alloc(N, &scratch_bytes);
             rp.alloc(N, &scratch_bytes);
             cuda_check(cudaMemcpyAsync(iz_v.p, net->iz_v.p, N * 4ull, cudaMemcpyDeviceToDevice, net->stream), "D2D");
             cuda_check(cudaMemcpyAsync(rp.p, net->rp.p, N * 8ull, cudaMemcpyDeviceToDevice, net->stream), "D2D");
+        }
+        if (net->model == GN_MODEL_HH) {
+            hh_g.alloc(N, &scratch_bytes);
+            cuda_check(cudaMemcpyAsync(hh_g.p, net->hh_g.p, N * 16ull, cudaMemcpyDeviceToDevice, net->stream), "D2D");
         }
         cuda_check(cudaMemsetAsync(ring.p, 0, ring.n * 4, net->stream), "memset");
         cuda_check(cudaMemsetAsync(wc.p, 0, wc.n * 8, net->stream), "memset");
@@ -380,6 +388,7 @@ void autotune(gn_net *net)
             a.status = status.p;
             a.iz_v = iz_v.p;
             a.rp = rp.p;
+            a.hh_g = hh_g.p;
             const int warm = 3, timed = 8;
             for (int k = 0; k < warm; ++k)
                 cuda_check(launch_kind(a, net, k, net->stream), "autotune launch");
@@ -578,10 +587,17 @@ gn_status gn_net_create(const gn_net_desc *desc, gn_net **out)
         cuda_check(cudaMemset(net->d_step.p, 0, 8), "memset");
         cuda_check(cudaMemset(net->d_npulses.p, 0, 4), "memset");
         net->model = desc->model;
-        if (net->model == GN_MODEL_IZH) {
-            net->iz_v.upload(std::vector<float>(N, static_cast<float>(desc->izh.v_r)), &net->bytes);
+        if (net->model != GN_MODEL_FHN) {
+            net->iz_v.upload(std::vector<float>(N, static_cast<float>(h.v_rest)), &net->bytes);
             net->rp.alloc(N, &net->bytes);
             cuda_check(cudaMemset(net->rp.p, 0, net->rp.n * 8), "memset");
+        }
+        if (net->model == GN_MODEL_HH) {
+            double m, n, hg;
+            gnrt::hh_rest_gates(&m, &n, &hg);
+            net->hh_g.upload(std::vector<float4>(N, make_float4(static_cast<float>(m), static_cast<float>(n),
+                                                                static_cast<float>(hg), 0.0f)),
+                             &net->bytes);
         }
 
         gn::StepArgs &a = net->args;
@@ -606,6 +622,7 @@ gn_status gn_net_create(const gn_net_desc *desc, gn_net **out)
         a.status = net->status.p;
         a.iz_v = net->iz_v.p;
         a.rp = net->rp.p;
+        a.hh_g = net->hh_g.p;
 
         // the kernel is fixed now or timed on the first gn_step (kind 0)
         if (desc->step_kernel == 0 || desc->step_kernel == 3) net->host = std::make_unique<gnrt::HostNet>(std::move(h));
@@ -791,7 +808,7 @@ gn_status gn_get_state(gn_net *net, float *v, float *w, float *c, int32_t *bg_co
         const int32_t N = net->N;
         std::vector<float> tmp(N);
         if (v) {
-            const float *src = net->model == GN_MODEL_IZH ? net->iz_v.p
+            const float *src = net->model != GN_MODEL_FHN ? net->iz_v.p
                                                           : net->ring.p + (net->step & (net->R - 1)) * net->stride;
             cuda_check(cudaMemcpy(tmp.data(), src, N * 4, cudaMemcpyDeviceToHost), "D2H v");
             permute_rows_to_caller(net, tmp.data(), v, 1);
@@ -852,7 +869,7 @@ gn_status gn_get_izh_state(gn_net *net, float *V, float *r, float *p)
 {
     return guarded([&] {
         check_net(net);
-        if (net->model != GN_MODEL_IZH) fail(GN_EINVAL, "the network does not use the Izhikevich model");
+        if (net->model == GN_MODEL_FHN) fail(GN_EINVAL, "the network does not use a spiking node model");
         DeviceGuard dg(net->device);
         sync(net);
         const int32_t N = net->N;
@@ -876,7 +893,7 @@ gn_status gn_set_izh_state(gn_net *net, const float *V, const float *r, const fl
 {
     return guarded([&] {
         check_net(net);
-        if (net->model != GN_MODEL_IZH) fail(GN_EINVAL, "the network does not use the Izhikevich model");
+        if (net->model == GN_MODEL_FHN) fail(GN_EINVAL, "the network does not use a spiking node model");
         DeviceGuard dg(net->device);
         sync(net);
         const int32_t N = net->N;
@@ -894,6 +911,44 @@ gn_status gn_set_izh_state(gn_net *net, const float *V, const float *r, const fl
             }
             cuda_check(cudaMemcpy(net->rp.p, t.data(), N * 8ull, cudaMemcpyHostToDevice), "H2D rp");
         }
+    });
+}
+
+gn_status gn_get_hh_gates(gn_net *net, float *m, float *n, float *h)
+{
+    return guarded([&] {
+        check_net(net);
+        if (net->model != GN_MODEL_HH) fail(GN_EINVAL, "the network does not use the Hodgkin-Huxley model");
+        DeviceGuard dg(net->device);
+        sync(net);
+        const int32_t N = net->N;
+        std::vector<float4> t(N);
+        cuda_check(cudaMemcpy(t.data(), net->hh_g.p, N * 16ull, cudaMemcpyDeviceToHost), "D2H gates");
+        for (int32_t i = 0; i < N; ++i) {
+            if (m) m[net->perm[i]] = t[i].x;
+            if (n) n[net->perm[i]] = t[i].y;
+            if (h) h[net->perm[i]] = t[i].z;
+        }
+    });
+}
+
+gn_status gn_set_hh_gates(gn_net *net, const float *m, const float *n, const float *h)
+{
+    return guarded([&] {
+        check_net(net);
+        if (net->model != GN_MODEL_HH) fail(GN_EINVAL, "the network does not use the Hodgkin-Huxley model");
+        DeviceGuard dg(net->device);
+        sync(net);
+        const int32_t N = net->N;
+        std::vector<float4> t(N);
+        cuda_check(cudaMemcpy(t.data(), net->hh_g.p, N * 16ull, cudaMemcpyDeviceToHost), "D2H gates");
+        for (int32_t j = 0; j < N; ++j) {
+            float4 &g = t[net->inv[j]];
+            if (m) g.x = m[j];
+            if (n) g.y = n[j];
+            if (h) g.z = h[j];
+        }
+        cuda_check(cudaMemcpy(net->hh_g.p, t.data(), N * 16ull, cudaMemcpyHostToDevice), "H2D gates");
     });
 }
 
@@ -971,7 +1026,8 @@ gn_status gn_save_state(gn_net *net, void *buf, size_t cap, size_t *used)
     return guarded([&] {
         check_net(net);
         const size_t N = net->N, RS = net->ring.n;
-        const size_t extra = net->model == GN_MODEL_IZH ? N * 12 : 0;  // V, (r, p)
+        // spiking models: V, (r, p); Hodgkin-Huxley also (m, n, h, 0)
+        const size_t extra = (net->model != GN_MODEL_FHN ? N * 12 : 0) + (net->model == GN_MODEL_HH ? N * 16 : 0);
         const size_t need = sizeof(CkptHeader) + RS * 4 + N * 8 + N * 4 + N * 8 + extra;
         if (used) *used = need;
         if (!buf) return;
@@ -994,6 +1050,9 @@ gn_status gn_save_state(gn_net *net, void *buf, size_t cap, size_t *used)
             cuda_check(cudaMemcpy(p, net->iz_v.p, N * 4, cudaMemcpyDeviceToHost), "D2H V");
             p += N * 4;
             cuda_check(cudaMemcpy(p, net->rp.p, N * 8, cudaMemcpyDeviceToHost), "D2H rp");
+            p += N * 8;
+            if (net->model == GN_MODEL_HH)
+                cuda_check(cudaMemcpy(p, net->hh_g.p, N * 16, cudaMemcpyDeviceToHost), "D2H gates");
         }
     });
 }
@@ -1004,7 +1063,7 @@ gn_status gn_load_state(gn_net *net, const void *buf, size_t size)
         check_net(net);
         if (!buf) fail(GN_EINVAL, "buf is NULL");
         const size_t N = net->N, RS = net->ring.n;
-        const size_t extra = net->model == GN_MODEL_IZH ? N * 12 : 0;
+        const size_t extra = (net->model != GN_MODEL_FHN ? N * 12 : 0) + (net->model == GN_MODEL_HH ? N * 16 : 0);
         const size_t need = sizeof(CkptHeader) + RS * 4 + N * 8 + N * 4 + N * 8 + extra;
         if (size < need) fail(GN_EINVAL, "checkpoint is truncated");
         CkptHeader h;
@@ -1025,6 +1084,9 @@ gn_status gn_load_state(gn_net *net, const void *buf, size_t size)
             cuda_check(cudaMemcpy(net->iz_v.p, p, N * 4, cudaMemcpyHostToDevice), "H2D V");
             p += N * 4;
             cuda_check(cudaMemcpy(net->rp.p, p, N * 8, cudaMemcpyHostToDevice), "H2D rp");
+            p += N * 8;
+            if (net->model == GN_MODEL_HH)
+                cuda_check(cudaMemcpy(net->hh_g.p, p, N * 16, cudaMemcpyHostToDevice), "H2D gates");
         }
         net->step = h.step;
         net->read_cursor = h.step / net->sample_every;

@@ -115,7 +115,16 @@ void validate_desc(const gn_net_desc *d)
             if (!(s > 0.0) || !std::isfinite(s)) fail(GN_EINVAL, "edge %lld: speed must be positive", (long long)e);
         }
     }
-    if (d->model != GN_MODEL_FHN && d->model != GN_MODEL_IZH) fail(GN_EINVAL, "unknown node model");
+    if (d->model != GN_MODEL_FHN && d->model != GN_MODEL_IZH && d->model != GN_MODEL_HH)
+        fail(GN_EINVAL, "unknown node model");
+    if (d->model == GN_MODEL_HH) {
+        const gn_hh_params &z = d->hh;
+        for (double x : {z.C, z.g_na, z.g_k, z.g_l, z.e_na, z.e_k, z.e_l, z.v_peak, z.i_ext, z.psc_a, z.tau_c})
+            if (!std::isfinite(x)) fail(GN_EINVAL, "Hodgkin-Huxley parameters must be finite");
+        if (!(z.C > 0.0) || !(z.tau_c > 0.0) || z.psc_a < 0.0)
+            fail(GN_EINVAL, "Hodgkin-Huxley parameters need C > 0, tau_c > 0, psc_a >= 0");
+        return;
+    }
     if (d->model == GN_MODEL_IZH) {
         const gn_izh_params &z = d->izh;
         for (double x : {z.C, z.k, z.v_r, z.v_t, z.v_peak, z.v_reset, z.a, z.b, z.d, z.i_ext, z.psc_a, z.tau_c})
@@ -279,6 +288,9 @@ void host_build(const gn_net_desc *d, std::vector<int32_t> delay, int64_t n_clam
     if (d->model == GN_MODEL_IZH) {
         h.v_rest = d->izh.v_r;  // the state without input: V = v_r, W = 0
         h.w_rest = 0.0;
+    } else if (d->model == GN_MODEL_HH) {
+        h.v_rest = -65.0;  // the starting state (the gates at their values there)
+        h.w_rest = 0.0;
     } else {
         rest_point(d->fhn, &h.v_rest, &h.w_rest);
     }
@@ -432,6 +444,34 @@ void fill_step_params(const gn_net_desc *d, const HostNet &h, gn::StepArgs &a)
         a.ca_q = static_cast<float>(1.0 / z.tau_c);
         a.vrest = 0.0f;  // the readout is gain c + offset
     }
+    if (d->model == GN_MODEL_HH) {
+        const gn_hh_params &z = d->hh;
+        a.iz_dtc = static_cast<float>(d->dt_ms / z.C);
+        a.iz_vpeak = static_cast<float>(z.v_peak);
+        a.iz_iext = static_cast<float>(z.i_ext);
+        a.hh_gna = static_cast<float>(z.g_na);
+        a.hh_gk = static_cast<float>(z.g_k);
+        a.hh_gl = static_cast<float>(z.g_l);
+        a.hh_ena = static_cast<float>(z.e_na);
+        a.hh_ek = static_cast<float>(z.e_k);
+        a.hh_el = static_cast<float>(z.e_l);
+        a.ps_a2 = static_cast<float>(z.psc_a * z.psc_a);
+        a.ps_2a = static_cast<float>(2.0 * z.psc_a);
+        a.ca_q = static_cast<float>(1.0 / z.tau_c);
+        a.vrest = 0.0f;
+    }
+}
+
+void hh_rest_gates(double *m, double *n, double *h)
+{
+    // at V = -65 mV: alpha_m = 0.1 (-25) / (1 - e^2.5), beta_m = 4,
+    // alpha_h = 0.07, beta_h = 1 / (1 + e^3), alpha_n = 0.01 (-10) / (1 - e^1), beta_n = 0.125
+    const double am = 2.5 / std::expm1(2.5), bm = 4.0;
+    const double ah = 0.07, bh = 1.0 / (1.0 + std::exp(3.0));
+    const double an = 0.1 / std::expm1(1.0), bn = 0.125;
+    *m = am / (am + bm);
+    *n = an / (an + bn);
+    *h = ah / (ah + bh);
 }
 
 PulseTable make_pulses(const gn_pulse *pulses, int32_t n, int32_t n_nodes, double dt, const std::vector<int32_t> &inv)

@@ -152,6 +152,8 @@ bool build_staged(const HostNet &h, int threads, int ucap, int ecap, int pcap, S
 
 // Scalar fields of the step arguments (FHN about the rest point, readout, sizes).
 void fill_step_params(const gn_net_desc *d, const HostNet &h, gn::StepArgs &a);
+// Hodgkin-Huxley gates at -65 mV, x = alpha / (alpha + beta) of the classic rates.
+void hh_rest_gates(double *m, double *n, double *h);
 
 // Pulses (caller node ids, ms) -> sorted by internal node, steps; invalid -> GN_EINVAL.
 struct PulseTable {

@@ -169,9 +169,61 @@ __device__ __forceinline__ void izh_update(const StepArgs &a, int r, int64_t n, 
     }
 }
 
-// Stimulus, FHN Euler step, history write, readout, noise, events, arrival.
-// `orig` (caller id) and `cnt0` (background counter) may be prefetched by the
-// caller; kLoad makes node_update read them itself.
+// x / (1 - e^(-x / y)) with its limit y at x = 0 (the removable 0/0 of alpha_m, alpha_n)
+__device__ __forceinline__ float hh_trap(float x, float y)
+{
+    return x == 0.0f ? y : x / -expm1f(-x / y);
+}
+
+// Hodgkin-Huxley + alpha-PSC + calcium node (model 2): classic squid-axon rates
+// (mV, ms), forward Euler of V and the gates m, n, h from step-n values, the PSC and
+// calcium as in izh_update; no reset, events are upward crossings of V_peak.
+__device__ __forceinline__ void hh_update(const StepArgs &a, int r, int64_t n, float2 wc, float S, float U,
+                                          int32_t orig)
+{
+    const float V = a.iz_v[r];
+    const float4 g = a.hh_g[r];
+    const float2 rp = a.rp[r];
+    const float c = wc.y;
+    const float e65 = V + 65.0f;
+    const float am = 0.1f * hh_trap(V + 40.0f, 10.0f), bm = 4.0f * expf(-e65 / 18.0f);
+    const float ah = 0.07f * expf(-e65 / 20.0f), bh = 1.0f / (1.0f + expf(-(V + 35.0f) / 10.0f));
+    const float an = 0.01f * hh_trap(V + 55.0f, 10.0f), bn = 0.125f * expf(-e65 / 80.0f);
+    const float m3h = g.x * g.x * g.x * g.z, n2 = g.y * g.y;
+    const float i_ion = a.hh_gna * m3h * (V - a.hh_ena) + a.hh_gk * (n2 * n2) * (V - a.hh_ek) +
+                        a.hh_gl * (V - a.hh_el);
+    const float V1 = V + a.iz_dtc * (-i_ion + rp.x + U + a.iz_iext);
+    const float m1 = g.x + a.dt * (am * (1.0f - g.x) - bm * g.x);
+    const float n1 = g.y + a.dt * (an * (1.0f - g.y) - bn * g.y);
+    const float h1 = g.z + a.dt * (ah * (1.0f - g.z) - bh * g.z);
+    const bool above = V >= a.iz_vpeak;
+    const float r1 = rp.x + a.dt * rp.y;
+    const float p1 = rp.y + a.dt * (-a.ps_a2 * rp.x - a.ps_2a * rp.y + S);
+    const float c1 = c + a.dt * (above ? 1.0f - c * a.ca_q : -c * a.ca_q);
+    const bool above1 = V1 >= a.iz_vpeak;
+
+    a.iz_v[r] = V1;
+    a.hh_g[r] = make_float4(m1, n1, h1, 0.0f);
+    a.wc[r] = make_float2(0.0f, c1);
+    a.rp[r] = make_float2(r1, p1);
+    a.ring[((n + 1) & a.ring_mask) * a.ring_stride + r] = above1 ? 1.0f : 0.0f;
+    if (!above && above1) {
+        record_event(a, r, n + 1);
+        if (a.first[r] < 0) a.first[r] = n + 1;
+    }
+    if (((n + 1) % a.sample_every) == 0) {
+        const int64_t k = (n + 1) / a.sample_every - 1;
+        if (orig == kLoad) orig = __ldg(a.perm + r);
+        const float xi = gauss_from(draw(a.obs_seed, static_cast<uint32_t>(orig), k, kStreamObservation));
+        a.obs[(k % a.obs_cap) * a.N + orig] = fmaf(a.gain, c1, a.offset) + a.sigma * xi;
+    }
+}
+
+// Stimulus, node model kM's Euler step (0 FitzHugh-Nagumo, 1 Izhikevich, 2
+// Hodgkin-Huxley), history write, readout, noise, events, arrival.  `orig` (caller
+// id) and `cnt0` (background counter) may be prefetched by the caller; kLoad makes
+// node_update read them itself.
+template <int kM>
 __device__ __forceinline__ void node_update(const StepArgs &a, int r, int64_t n, float v, float2 wc, float S,
                                             int32_t orig = kLoad, int32_t cnt0 = kLoad)
 {
@@ -197,8 +249,11 @@ __device__ __forceinline__ void node_update(const StepArgs &a, int r, int64_t n,
         }
         if (cnt != c0) a.bgc[r] = cnt;
     }
-    if (a.model == 1) {
+    if constexpr (kM == 1) {
         izh_update(a, r, n, wc, S, U, orig);
+        return;
+    } else if constexpr (kM == 2) {
+        hh_update(a, r, n, wc, S, U, orig);
         return;
     }
     if (a.bias) S += __ldg(a.bias + r);

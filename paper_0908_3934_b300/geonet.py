@@ -42,7 +42,13 @@ class gn_izh_params(C.Structure):
                                           "psc_a", "tau_c")]
 
 
-GN_MODEL_FHN, GN_MODEL_IZH = 0, 1
+class gn_hh_params(C.Structure):
+    _fields_ = [(x, C.c_double) for x in ("C", "g_na", "g_k", "g_l", "e_na", "e_k", "e_l", "v_peak", "i_ext",
+                                          "psc_a", "tau_c")]
+
+
+GN_MODEL_FHN, GN_MODEL_IZH, GN_MODEL_HH = 0, 1, 2
+_MODELS = {"fhn": GN_MODEL_FHN, "izh": GN_MODEL_IZH, "hh": GN_MODEL_HH}
 
 
 class gn_net_desc(C.Structure):
@@ -54,7 +60,7 @@ class gn_net_desc(C.Structure):
         ("ring_depth", C.c_int32), ("obs_capacity", C.c_int64), ("event_capacity", C.c_int64),
         ("renumber", C.c_int32), ("edge_format", C.c_int32), ("step_kernel", C.c_int32),
         ("cuda_stream", C.c_void_p), ("device", C.c_int32),
-        ("model", C.c_int32), ("izh", gn_izh_params),
+        ("model", C.c_int32), ("izh", gn_izh_params), ("hh", gn_hh_params),
     ]
 
 
@@ -97,6 +103,8 @@ _SIGS = {
     "gn_set_state": ([_P, _P, C.c_int32, _P, _P, _P, C.c_int64], C.c_int),
     "gn_get_izh_state": ([_P, _P, _P, _P], C.c_int),
     "gn_set_izh_state": ([_P, _P, _P, _P], C.c_int),
+    "gn_get_hh_gates": ([_P, _P, _P, _P], C.c_int),
+    "gn_set_hh_gates": ([_P, _P, _P, _P], C.c_int),
     "gn_get_arrivals": ([_P, _P], C.c_int),
     "gn_get_events": ([_P, _P, _P, C.c_int64, C.POINTER(C.c_int64)], C.c_int),
     "gn_save_state": ([_P, _P, C.c_size_t, C.POINTER(C.c_size_t)], C.c_int),
@@ -189,8 +197,8 @@ def make_desc(spec, keep: list, *, device: int = 0, stream=None, obs_capacity: i
         ring_depth=spec.ring_depth if ring_depth is None else ring_depth,
         obs_capacity=obs_capacity, event_capacity=event_capacity, renumber=0 if renumber else -1,
         edge_format=1 if wide_edges else 0, step_kernel=step_kernel,
-        cuda_stream=stream, device=device, model=GN_MODEL_IZH if getattr(spec, "model", "fhn") == "izh" else GN_MODEL_FHN,
-        izh=_izh_params(getattr(spec, "izh", None)))
+        cuda_stream=stream, device=device, model=_MODELS[getattr(spec, "model", "fhn")],
+        izh=_izh_params(getattr(spec, "izh", None)), hh=_hh_params(getattr(spec, "hh", None)))
 
 
 def _izh_params(iz) -> gn_izh_params:
@@ -198,6 +206,13 @@ def _izh_params(iz) -> gn_izh_params:
         return gn_izh_params()
     return gn_izh_params(C=iz["C"], k=iz["k"], v_r=iz["vr"], v_t=iz["vt"], v_peak=iz["vpeak"], v_reset=iz["vreset"],
                          a=iz["a"], b=iz["b"], d=iz["d"], i_ext=iz["i_ext"], psc_a=iz["psc_a"], tau_c=iz["tau_c"])
+
+
+def _hh_params(hp) -> gn_hh_params:
+    if not hp:
+        return gn_hh_params()
+    return gn_hh_params(C=hp["C"], g_na=hp["gna"], g_k=hp["gk"], g_l=hp["gl"], e_na=hp["ena"], e_k=hp["ek"],
+                        e_l=hp["el"], v_peak=hp["vpeak"], i_ext=hp["i_ext"], psc_a=hp["psc_a"], tau_c=hp["tau_c"])
 
 
 class Net:
@@ -303,6 +318,16 @@ class Net:
     def gn_set_izh_state(self, V=None, r=None, p=None):
         V, r, p = _c(V, np.float32), _c(r, np.float32), _c(p, np.float32)
         check(lib().gn_set_izh_state(self.h, _ptr(V), _ptr(r), _ptr(p)))
+
+    def gn_get_hh_gates(self):
+        N = self.n_nodes
+        m, n, h = (np.zeros(N, np.float32) for _ in range(3))
+        check(lib().gn_get_hh_gates(self.h, _ptr(m), _ptr(n), _ptr(h)))
+        return dict(m=m, n=n, h=h)
+
+    def gn_set_hh_gates(self, m=None, n=None, h=None):
+        m, n, h = _c(m, np.float32), _c(n, np.float32), _c(h, np.float32)
+        check(lib().gn_set_hh_gates(self.h, _ptr(m), _ptr(n), _ptr(h)))
 
     def gn_get_history(self, depth: int) -> np.ndarray:
         out = np.zeros((depth, self.n_nodes), np.float32)

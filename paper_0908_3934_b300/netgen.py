@@ -117,10 +117,11 @@ def hodgkin_huxley(spec: "NetSpec", w_scale: float = 10.0, pulse_amp: float = 20
     paper's HH step dt = 0.03 ms: weights in PSC units (uA/cm^2; spd stays 1 for the
     ~1 ms a spike spends above 0 mV, so a spike through weight w adds about w x 1 ms
     to p), pulses and background pulses of pulse_amp uA/cm^2 (2 ms at 20 make a
-    resting node spike), calcium readout gain obs_gain; sample interval kept at 1 ms."""
+    resting node spike), calcium readout gain obs_gain; sample interval kept at 1 ms;
+    the ring sized afresh for the longer delays in steps."""
     every = max(1, int(round(1.0 / dt_ms)))
     return dataclasses.replace(
-        spec, model="hh", hh=dict(HH_CLASSIC), dt_ms=dt_ms,
+        spec, model="hh", hh=dict(HH_CLASSIC), dt_ms=dt_ms, ring_depth=0,
         weight=(np.asarray(spec.weight) * w_scale).astype(np.float32),
         pulses=[(j, t0, t1, pulse_amp) for (j, t0, t1, _) in spec.pulses],
         background=None if spec.background is None else dict(spec.background, amp=pulse_amp),
@@ -459,6 +460,16 @@ def test_set(seed0: int = 500, **kw) -> list:
                     out.append(test_set_net(n, dim, cls, density, seed=seed0 + i, **kw))
                     i += 1
     return out
+
+
+def test_set_hh(spec: NetSpec, bg_rate_hz: float = 20.0, w_scale: float = 2.0, seed: int = 0,
+                dt_ms: float = 0.03) -> NetSpec:
+    """A test-set network with Hodgkin-Huxley + alpha-PSC nodes at the paper's HH step
+    dt = 0.03 ms (delays re-quantised to it), driven by background pulses (2 ms of
+    20 uA/cm^2 at bg_rate_hz per node; alone they give about 17 spikes/node/s).  With
+    weight scale 2 the 300-vertex dense nets fire at about 20-70 spikes/node/s."""
+    bg = dict(rate_hz=bg_rate_hz, amp=1.0, dur_ms=2.0, seed=seed + 4242)
+    return hodgkin_huxley(dataclasses.replace(spec, background=bg), w_scale=w_scale, dt_ms=dt_ms)
 
 
 def test_set_izh(spec: NetSpec, bg_rate_hz: float = 20.0, w_scale: float = 100.0, seed: int = 0) -> NetSpec:

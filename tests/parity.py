@@ -87,6 +87,12 @@ def assert_windows(worst):
 
 
 PEAK_MARGIN = 1e-2   # mV: a spike decision this close to V_peak may go either way in FP32
+# Hodgkin-Huxley windows: 8 steps (0.24 ms at dt = 0.03 ms).  The upswing amplifies a
+# perturbation fast enough that over one 33-step observation interval the rounding of
+# the starting state to FP32 alone -- the oracle run from the rounded state against
+# the oracle run from the exact one -- takes up to 0.57 of the tolerance on V; over
+# 8 steps it takes at most 0.12, leaving the rest for the step's own arithmetic.
+HH_WINDOW = 8
 
 
 def ratio_scaled(gpu, ref):
@@ -104,20 +110,27 @@ def ratio_scaled(gpu, ref):
 
 
 def windowed_izh(spec, net, n_steps, window=None, start=0):
-    """windowed() for the Izhikevich + alpha-PSC model: the oracle's full state (V, W,
-    calcium, r, p, spike history, background counters) is loaded at every window
-    start and the next `window` steps of V, W, c, r, p, y (ratio_scaled) and the
-    spikes are compared.  A node is left out of a window's comparison only if the oracle's V
+    """windowed() for the spiking models (Izhikevich or Hodgkin-Huxley + alpha PSC):
+    the oracle's full state (V, W, calcium, r, p, the Hodgkin-Huxley gates, spike
+    history, background counters) is loaded at every window start and the next
+    `window` steps of V, W, c, r, p, m, n, h, y (ratio_scaled) and the spikes are
+    compared.  A node is left out of a window's comparison only if the oracle's V
     came within PEAK_MARGIN of V_peak in it (the spike decision is not defined to
-    FP32 there); the count of such node-windows is returned with the worst ratios.
-    The window defaults to one observation interval (1 ms: 20 steps at dt = 0.05 ms,
-    one step at dt = 1 ms, where a spike's upswing amplifies a perturbation more than
-    twofold per step)."""
-    window = window or spec.obs["sample_every"]
+    FP32 there), or if such a node reaches it through an edge of delay below the
+    window length (its input then depends on that decision); the count of such
+    node-windows is returned with the worst ratios.  The window defaults to one
+    observation interval (1 ms: 20 steps at dt = 0.05 ms, one step at dt = 1 ms,
+    where a spike's upswing amplifies a perturbation more than twofold per step),
+    and to HH_WINDOW steps for Hodgkin-Huxley."""
+    hh = spec.model == "hh"
+    window = window or (HH_WINDOW if hh else spec.obs["sample_every"])
     D = oracle.net_delays(spec)
+    src, dst = np.asarray(spec.src), np.asarray(spec.dst)
     depth = int(D.max(initial=1)) + 1
     ref = oracle.simulate(spec, start, hist_depth=depth, want_y=False)
     worst = dict(v=0.0, w=0.0, c=0.0, r=0.0, p=0.0, y=0.0)
+    if hh:
+        worst.update(m=0.0, n=0.0, h=0.0)
     n_spikes = excused = 0
     n0 = start
     end = start + n_steps
@@ -127,18 +140,31 @@ def windowed_izh(spec, net, n_steps, window=None, start=0):
                          ref["c"].astype(np.float32), ref["bg_count"], n0)
         net.gn_set_izh_state(V=ref["v"].astype(np.float32), r=ref["r"].astype(np.float32),
                              p=ref["p"].astype(np.float32))
+        gates = {}
+        if hh:
+            gates = dict(m=ref["m"], n=ref["n"], h=ref["h"])
+            net.gn_set_hh_gates(**{k: x.astype(np.float32) for k, x in gates.items()})
         nxt = oracle.simulate(spec, K, hist_depth=depth, ev_cap=spec.n_nodes * (K + 1) + 1024,
                               init=dict(n0=n0, v=ref["v"], w=ref["w"], c=ref["c"], r=ref["r"], p=ref["p"],
-                                        bg_count=ref["bg_count"], hist=ref["hist"]))
+                                        bg_count=ref["bg_count"], hist=ref["hist"], **gates))
         net.gn_step(K)
         g = net.gn_get_state()
         gi = net.gn_get_izh_state()
+        if hh:
+            gg = net.gn_get_hh_gates()
         y, _, _ = net.gn_observe()
         ok = nxt["min_peak_gap"] > PEAK_MARGIN
+        # a spike decision left open also changes, within the window, the input of
+        # the targets it reaches in fewer than K steps
+        reach = ~ok[src] & (D < K)
+        ok[dst[reach]] = False
         excused += int((~ok).sum())
         for k, gv, rv in (("v", gi["V"], nxt["v"]), ("w", g["w"], nxt["w"]), ("c", g["c"], nxt["c"]),
                           ("r", gi["r"], nxt["r"]), ("p", gi["p"], nxt["p"])):
             worst[k] = max(worst[k], ratio_scaled(gv[ok], rv[ok]))
+        if hh:
+            for k in ("m", "n", "h"):
+                worst[k] = max(worst[k], ratio_scaled(gg[k][ok], nxt[k][ok]))
         if nxt["y"] is not None and nxt["y"].size:
             worst["y"] = max(worst["y"], ratio_scaled(y[:, ok], nxt["y"][:, ok]))
         assert np.array_equal(g["bg_count"], nxt["bg_count"]), "background counters differ"

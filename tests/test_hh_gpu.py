@@ -1,0 +1,119 @@
+"""Hodgkin-Huxley + alpha-PSC + calcium nodes (the paper's second benchmark model,
+Sec. 3.1 and 3.4, dt = 0.03 ms) on the GPU against the FP64 oracle, through the
+C ABI.
+
+Spikes (upward crossings of 0 mV) and first spikes are compared exactly; V,
+calcium, r, p, the gates m, n, h and y within 1e-4 relative (floor 1e-6 of the
+quantity's largest magnitude) per 1 ms window of 33 steps, the oracle's state
+loaded at each window start (tests/parity.py)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0908_3934_b300 import geonet, netgen
+
+from parity import assert_windows, windowed_izh
+
+pytestmark = pytest.mark.gpu
+
+
+def test_tiny_net_windows_and_spikes():
+    """64 nodes with pulses and self-sustained activity (several hundred spikes in 90 ms)."""
+    spec = netgen.hodgkin_huxley(netgen.tiny())
+    net = geonet.Net(spec)
+    worst, n_spikes, excused = windowed_izh(spec, net, 3000)
+    print("worst ratios", worst)
+    assert_windows(worst)
+    assert n_spikes > 100 and excused < 0.01 * 64 * 90
+
+
+def test_spikes_exact_without_resynchronising():
+    """From rest, with no spike decision near 0 mV in the oracle's run, the GPU's
+    spikes and first spikes equal the oracle's step for step over 1500 steps (45 ms)."""
+    spec = netgen.hodgkin_huxley(netgen.tiny())
+    n = 1500
+    ref = oracle.simulate(spec, n, ev_cap=100000, want_y=False)
+    assert ref["ev_count"] > 10 and ref["min_peak_gap"].min() > 1e-2
+    net = geonet.Net(spec)
+    net.gn_step(n)
+    node, step, _ = net.gn_get_events()
+    assert sorted(zip(node.tolist(), step.tolist())) == sorted(zip(ref["ev_node"].tolist(), ref["ev_step"].tolist()))
+    assert np.array_equal(net.gn_get_arrivals(), ref["first_arrival"].astype(np.int64))
+
+
+@pytest.mark.parametrize("step_kernel", [1, 3])
+def test_multi_block_net_windows(step_kernel):
+    """30k nodes, in-degree 40, 100 Hz background pulses: many row blocks / tiles."""
+    spec = netgen.hodgkin_huxley(netgen.large(n=30000, mean_deg=40, bg_rate_hz=100.0))
+    net = geonet.Net(spec, step_kernel=step_kernel)
+    worst, n_spikes, _ = windowed_izh(spec, net, 330, start=330)
+    print("worst ratios", worst)
+    assert_windows(worst)
+    assert n_spikes > 0
+
+
+def test_every_kernel_and_shape_gives_the_same_bits(monkeypatch):
+    """Every step kernel and CTA shape reaches bit-identical Hodgkin-Huxley states."""
+    spec = netgen.hodgkin_huxley(netgen.roofline(seed=21, n=20000, bg_rate_hz=100.0))
+    ref = None
+    for kind, shape in [(1, s) for s in range(5)] + [(2, 0)] + [(3, s) for s in range(4)]:
+        monkeypatch.setenv("GN_STEP_SHAPE", str(shape))
+        net = geonet.Net(spec, step_kernel=kind)
+        net.gn_step(700)
+        st, iz, gt = net.gn_get_state(), net.gn_get_izh_state(), net.gn_get_hh_gates()
+        cur = [st["c"], iz["V"], iz["r"], iz["p"], gt["m"], gt["n"], gt["h"], net.gn_get_history(8)]
+        if ref is None:
+            ref = cur
+            assert len(net.gn_get_events()[0]) > 0
+            continue
+        for a, b in zip(cur, ref):
+            assert np.array_equal(a, b), (kind, shape)
+
+
+def test_checkpoint_resume_is_bit_exact():
+    spec = netgen.hodgkin_huxley(netgen.large(n=3000, mean_deg=20, bg_rate_hz=200.0))
+    a = geonet.Net(spec)
+    a.gn_step(777)
+    blob = a.gn_save_state()
+    a.gn_step(777)
+    b = geonet.Net(spec)
+    b.gn_load_state(blob)
+    b.gn_step(777)
+    for k in ("V", "r", "p"):
+        assert np.array_equal(a.gn_get_izh_state()[k], b.gn_get_izh_state()[k]), k
+    for k in ("m", "n", "h"):
+        assert np.array_equal(a.gn_get_hh_gates()[k], b.gn_get_hh_gates()[k]), k
+    sa, sb = a.gn_get_state(), b.gn_get_state()
+    for k in ("v", "w", "c", "bg_count"):
+        assert np.array_equal(sa[k], sb[k]), k
+
+
+def test_starting_state_and_model_checks():
+    """A new net rests at -65 mV with the gates at their rest values; the gate calls
+    refuse other models and the batched form refuses this one."""
+    spec = netgen.hodgkin_huxley(netgen.tiny())
+    net = geonet.Net(spec)
+    g = net.gn_get_hh_gates()
+    m0, n0, h0 = oracle.hh_rest_gates()
+    assert np.all(net.gn_get_izh_state()["V"] == np.float32(-65.0))
+    for k, x in (("m", m0), ("n", n0), ("h", h0)):
+        assert np.all(np.abs(g[k] - x) <= 1e-7), k
+    with pytest.raises(geonet.GeonetError) as e:
+        geonet.Net(netgen.izhikevich(netgen.tiny())).gn_get_hh_gates()
+    assert e.value.status == geonet.GN_EINVAL
+    with pytest.raises(geonet.GeonetError) as e:
+        geonet.Batch([spec])
+    assert e.value.status == geonet.GN_EINVAL
+
+
+@pytest.mark.parametrize("cls", ["lattice", "scale_free", "random"])
+def test_test_set_networks_at_the_hh_step(cls):
+    """Networks of the standard test set (Sec. 3.5) with Hodgkin-Huxley nodes at the
+    paper's HH step dt = 0.03 ms, 20 Hz background pulses: 1320 steps (about 40 ms),
+    one 1 ms observation interval (33 steps) per window."""
+    spec = netgen.test_set_hh(netgen.test_set_net(300, 2, cls, "high", seed=7))
+    net = geonet.Net(spec)
+    worst, n_spikes, _ = windowed_izh(spec, net, 1320, start=660)
+    print("worst ratios", worst)
+    assert_windows(worst)
+    assert n_spikes > 20
