@@ -11,13 +11,15 @@
 //      copies have landed, fetches each distinct history value its edges read,
 //      v~_src(n - D) from ring slot (n - D) & (R - 1), once, into shared memory.
 //      The gathers are sorted by (D, src), so a warp's 32 reads fall in a few lines
-//      of one ring slot;
+//      of one ring slot.  While they are in flight, a spiking node (Izhikevich,
+//      Hodgkin-Huxley) runs every part of its update that does not read S -- all
+//      but the PSC variable p;
 //   2. each lane sums one piece of a row in a register, S_piece = sum_e w_e
 //      v~_src(n - D_e) over its edges in order, all from shared memory (Eq. Yjset,
 //      Sec. 2).  A row of at most kWarpRow edges is one piece; a longer row is 32
 //      lane-strided pieces -- the summation order of every step kernel;
 //   3. one thread per row combines its pieces (a long row's 32 by the butterfly
-//      tree of a warp reduction) and runs the node update:
+//      tree of a warp reduction) and runs the node update (a spiking node: p):
 //      stimulus, FHN Euler step about the rest point (Sec. 3.1, Eq. fnstate),
 //      history write, low-pass readout, noisy observation (Sec. 3.3), events and
 //      first arrivals.
@@ -138,6 +140,10 @@ __device__ __forceinline__ void staged_tile(const StepArgs &a, const int tile, c
         const int64_t slot = (n - static_cast<int64_t>(d)) & a.ring_mask;
         cp_async4_hint(s_val + u, a.ring + slot * a.ring_stride + src, pol_ring);
     }
+    // a spiking node's update reads S only in p: the rest runs while the gathers land
+    float2 rp0 = make_float2(0.0f, 0.0f);
+    if constexpr (kM != 0)
+        if (own) rp0 = spiking_begin<kM>(a, r, n, wc, orig, cnt0);
     cp_async_wait_all();
     __syncthreads();
 
@@ -186,7 +192,10 @@ __device__ __forceinline__ void staged_tile(const StepArgs &a, const int tile, c
                 for (int l = 0; l < o; ++l) x[l] = __fadd_rn(x[l], x[l + o]);
             S = x[0];
         }
-        node_update<kM>(a, r, n, v, wc, S, orig, cnt0);
+        if constexpr (kM == 0)
+            node_update<kM>(a, r, n, v, wc, S, orig, cnt0);
+        else
+            psc_finish(a, r, rp0, S);
     }
 }
 

@@ -129,12 +129,31 @@ __device__ __forceinline__ void record_event(const StepArgs &a, int r, int64_t s
     }
 }
 
+// Spiking-node outputs of step n -> n + 1: spike ring (spd(V1)), events, first
+// spike, and the calcium readout every sample_every steps.
+__device__ __forceinline__ void spiking_outputs(const StepArgs &a, int r, int64_t n, bool above, bool above1,
+                                                float c1, int32_t orig)
+{
+    a.ring[((n + 1) & a.ring_mask) * a.ring_stride + r] = above1 ? 1.0f : 0.0f;
+    if (above1 && !above) {
+        record_event(a, r, n + 1);
+        if (a.first[r] < 0) a.first[r] = n + 1;
+    }
+    if (((n + 1) % a.sample_every) == 0) {
+        const int64_t k = (n + 1) / a.sample_every - 1;
+        if (orig == kLoad) orig = __ldg(a.perm + r);
+        const float xi = gauss_from(draw(a.obs_seed, static_cast<uint32_t>(orig), k, kStreamObservation));
+        a.obs[(k % a.obs_cap) * a.N + orig] = fmaf(a.gain, c1, a.offset) + a.sigma * xi;
+    }
+}
+
 // Izhikevich simple model with an alpha-function PSC and the calcium readout
 // (Sec. 3.1 Eq. izsimple / izpsc, Sec. 3.2.1 Eq. alphapsc and spd, Sec. 3.3 Eq.
-// casimple), forward Euler from step n to n + 1.  S is sum_e w_e spd(V_src(n - D_e))
-// (the ring holds spd); the state is absolute.
-__device__ __forceinline__ void izh_update(const StepArgs &a, int r, int64_t n, float2 wc, float S, float U,
-                                           int32_t orig)
+// casimple), forward Euler from step n to n + 1; the state is absolute.  Everything
+// but p, the one variable that reads S = sum_e w_e spd(V_src(n - D_e)), is updated
+// here (the ring holds spd); returns (r, p) at step n for psc_finish.  A spike
+// resets V, so every step with V >= V_peak is a new spike.
+__device__ __forceinline__ float2 izh_begin(const StepArgs &a, int r, int64_t n, float2 wc, float U, int32_t orig)
 {
     const float V = a.iz_v[r];
     const float W = wc.x, c = wc.y;
@@ -148,25 +167,11 @@ __device__ __forceinline__ void izh_update(const StepArgs &a, int r, int64_t n, 
         V1 = a.iz_vreset;
         W1 = W + a.iz_d;
     }
-    const float r1 = rp.x + a.dt * rp.y;
-    const float p1 = rp.y + a.dt * (-a.ps_a2 * rp.x - a.ps_2a * rp.y + S);
     const float c1 = c + a.dt * (spike ? 1.0f - c * a.ca_q : -c * a.ca_q);
-    const bool spike1 = V1 >= a.iz_vpeak;
-
     a.iz_v[r] = V1;
     a.wc[r] = make_float2(W1, c1);
-    a.rp[r] = make_float2(r1, p1);
-    a.ring[((n + 1) & a.ring_mask) * a.ring_stride + r] = spike1 ? 1.0f : 0.0f;
-    if (spike1) {
-        record_event(a, r, n + 1);
-        if (a.first[r] < 0) a.first[r] = n + 1;
-    }
-    if (((n + 1) % a.sample_every) == 0) {
-        const int64_t k = (n + 1) / a.sample_every - 1;
-        if (orig == kLoad) orig = __ldg(a.perm + r);
-        const float xi = gauss_from(draw(a.obs_seed, static_cast<uint32_t>(orig), k, kStreamObservation));
-        a.obs[(k % a.obs_cap) * a.N + orig] = fmaf(a.gain, c1, a.offset) + a.sigma * xi;
-    }
+    spiking_outputs(a, r, n, false, V1 >= a.iz_vpeak, c1, orig);
+    return rp;
 }
 
 // x / (1 - e^(-x / y)) with its limit y at x = 0 (the removable 0/0 of alpha_m, alpha_n)
@@ -177,9 +182,9 @@ __device__ __forceinline__ float hh_trap(float x, float y)
 
 // Hodgkin-Huxley + alpha-PSC + calcium node (model 2): classic squid-axon rates
 // (mV, ms), forward Euler of V and the gates m, n, h from step-n values, the PSC and
-// calcium as in izh_update; no reset, events are upward crossings of V_peak.
-__device__ __forceinline__ void hh_update(const StepArgs &a, int r, int64_t n, float2 wc, float S, float U,
-                                          int32_t orig)
+// calcium as in izh_begin (p is left to psc_finish); no reset, events are upward
+// crossings of V_peak.
+__device__ __forceinline__ float2 hh_begin(const StepArgs &a, int r, int64_t n, float2 wc, float U, int32_t orig)
 {
     const float V = a.iz_v[r];
     const float4 g = a.hh_g[r];
@@ -197,35 +202,27 @@ __device__ __forceinline__ void hh_update(const StepArgs &a, int r, int64_t n, f
     const float n1 = g.y + a.dt * (an * (1.0f - g.y) - bn * g.y);
     const float h1 = g.z + a.dt * (ah * (1.0f - g.z) - bh * g.z);
     const bool above = V >= a.iz_vpeak;
-    const float r1 = rp.x + a.dt * rp.y;
-    const float p1 = rp.y + a.dt * (-a.ps_a2 * rp.x - a.ps_2a * rp.y + S);
     const float c1 = c + a.dt * (above ? 1.0f - c * a.ca_q : -c * a.ca_q);
-    const bool above1 = V1 >= a.iz_vpeak;
-
     a.iz_v[r] = V1;
     a.hh_g[r] = make_float4(m1, n1, h1, 0.0f);
     a.wc[r] = make_float2(0.0f, c1);
-    a.rp[r] = make_float2(r1, p1);
-    a.ring[((n + 1) & a.ring_mask) * a.ring_stride + r] = above1 ? 1.0f : 0.0f;
-    if (!above && above1) {
-        record_event(a, r, n + 1);
-        if (a.first[r] < 0) a.first[r] = n + 1;
-    }
-    if (((n + 1) % a.sample_every) == 0) {
-        const int64_t k = (n + 1) / a.sample_every - 1;
-        if (orig == kLoad) orig = __ldg(a.perm + r);
-        const float xi = gauss_from(draw(a.obs_seed, static_cast<uint32_t>(orig), k, kStreamObservation));
-        a.obs[(k % a.obs_cap) * a.N + orig] = fmaf(a.gain, c1, a.offset) + a.sigma * xi;
-    }
+    spiking_outputs(a, r, n, above, V1 >= a.iz_vpeak, c1, orig);
+    return rp;
 }
 
-// Stimulus, node model kM's Euler step (0 FitzHugh-Nagumo, 1 Izhikevich, 2
-// Hodgkin-Huxley), history write, readout, noise, events, arrival.  `orig` (caller
-// id) and `cnt0` (background counter) may be prefetched by the caller; kLoad makes
-// node_update read them itself.
-template <int kM>
-__device__ __forceinline__ void node_update(const StepArgs &a, int r, int64_t n, float v, float2 wc, float S,
-                                            int32_t orig = kLoad, int32_t cnt0 = kLoad)
+// The alpha-function PSC of either spiking model from its step-n values (r, p):
+// r' = r + dt p, p' = p + dt (-a^2 r - 2 a p + S).
+__device__ __forceinline__ void psc_finish(const StepArgs &a, int r, float2 rp, float S)
+{
+    const float r1 = rp.x + a.dt * rp.y;
+    const float p1 = rp.y + a.dt * (-a.ps_a2 * rp.x - a.ps_2a * rp.y + S);
+    a.rp[r] = make_float2(r1, p1);
+}
+
+// Control input U_j(n): explicit pulses and background pulses.  `orig` (caller id)
+// and `cnt0` (background counter) may be prefetched by the caller; kLoad makes it
+// read them (orig is returned loaded if it was needed).
+__device__ __forceinline__ float stimulus(const StepArgs &a, int r, int64_t n, int32_t &orig, int32_t cnt0)
 {
     float U = 0.0f;
     const int n_pulses = *a.n_pulses;
@@ -249,13 +246,35 @@ __device__ __forceinline__ void node_update(const StepArgs &a, int r, int64_t n,
         }
         if (cnt != c0) a.bgc[r] = cnt;
     }
-    if constexpr (kM == 1) {
-        izh_update(a, r, n, wc, S, U, orig);
-        return;
-    } else if constexpr (kM == 2) {
-        hh_update(a, r, n, wc, S, U, orig);
+    return U;
+}
+
+// The S-independent part of a spiking node's step (model kM = 1 or 2): stimulus
+// and everything but p; returns (r, p) at step n for psc_finish.
+template <int kM>
+__device__ __forceinline__ float2 spiking_begin(const StepArgs &a, int r, int64_t n, float2 wc, int32_t orig,
+                                                int32_t cnt0)
+{
+    const float U = stimulus(a, r, n, orig, cnt0);
+    if constexpr (kM == 1)
+        return izh_begin(a, r, n, wc, U, orig);
+    else
+        return hh_begin(a, r, n, wc, U, orig);
+}
+
+// Stimulus, node model kM's Euler step (0 FitzHugh-Nagumo, 1 Izhikevich, 2
+// Hodgkin-Huxley), history write, readout, noise, events, arrival.  `orig` (caller
+// id) and `cnt0` (background counter) may be prefetched by the caller; kLoad makes
+// node_update read them itself.
+template <int kM>
+__device__ __forceinline__ void node_update(const StepArgs &a, int r, int64_t n, float v, float2 wc, float S,
+                                            int32_t orig = kLoad, int32_t cnt0 = kLoad)
+{
+    if constexpr (kM != 0) {
+        psc_finish(a, r, spiking_begin<kM>(a, r, n, wc, orig, cnt0), S);
         return;
     }
+    const float U = stimulus(a, r, n, orig, cnt0);
     if (a.bias) S += __ldg(a.bias + r);
 
     const float w = wc.x, c = wc.y;
