@@ -60,6 +60,7 @@ class _Net(C.Structure):
         ("hh_C", C.c_double), ("hh_gna", C.c_double), ("hh_gk", C.c_double), ("hh_gl", C.c_double),
         ("hh_ena", C.c_double), ("hh_ek", C.c_double), ("hh_el", C.c_double), ("hh_vpeak", C.c_double),
         ("hh_iext", C.c_double),
+        ("stdp", C.c_int32), ("stdp_alpha", C.c_double), ("stdp_beta", C.c_double),
     ]
 
 
@@ -69,6 +70,7 @@ class _Init(C.Structure):
         ("bg_count", C.c_void_p), ("hist", C.c_void_p), ("hist_depth", C.c_int32),
         ("r", C.c_void_p), ("p", C.c_void_p),
         ("m", C.c_void_p), ("n", C.c_void_p), ("h", C.c_void_p),
+        ("w_edge", C.c_void_p), ("s", C.c_void_p), ("hist_s", C.c_void_p),
     ]
 
 
@@ -83,6 +85,7 @@ class _Out(C.Structure):
         ("hist_out", C.c_void_p), ("hist_out_depth", C.c_int32),
         ("r", C.c_void_p), ("p", C.c_void_p),
         ("m", C.c_void_p), ("n", C.c_void_p), ("h", C.c_void_p), ("min_peak_gap", C.c_void_p),
+        ("w_final", C.c_void_p), ("s", C.c_void_p), ("hist_s_out", C.c_void_p),
     ]
 
 
@@ -206,6 +209,11 @@ def simulate(spec, n_steps: int, *, dense: bool = False, snap_every: int = 0,
     |V - V_peak| seen during the run.  With ``spec.model == "hh"`` (Hodgkin-Huxley
     + alpha PSC + calcium) the same holds with W = 0, the gates m, n, h returned
     (and accepted in ``init``), and events the upward crossings of V_peak.
+
+    With ``spec.stdp = dict(alpha, beta)`` (spiking models) the weights evolve by the
+    plasticity transition: the result adds ``w_final`` [E] (caller edge order), ``s``
+    [N] (time since the last spike) and, with ``hist_depth``, ``hist_s`` [k, j] =
+    s_j(n_end - k); ``init`` accepts ``w_edge``, ``s`` and ``hist_s``.
     """
     L = lib()
     N = spec.n_nodes
@@ -230,6 +238,7 @@ def simulate(spec, n_steps: int, *, dense: bool = False, snap_every: int = 0,
     hp = getattr(spec, "hh", None) or {}
     # the PSC rate and calcium time are shared by the spiking models
     psc = hp if hh else iz
+    stdp = getattr(spec, "stdp", None)
     net = _Net(
         n_nodes=N, n_edges=E, src=_ptr(src), dst=_ptr(dst), weight=_ptr(wgt), delay=_ptr(D),
         dt_ms=spec.dt_ms, a=fhn["a"], b=fhn["b"], c=fhn["c"], e=fhn["e"], f=fhn["f"], g=fhn["g"],
@@ -248,6 +257,7 @@ def simulate(spec, n_steps: int, *, dense: bool = False, snap_every: int = 0,
         psc_a=psc["psc_a"], tau_c=psc["tau_c"],
         **({f"hh_{k}": hp[k] for k in ("C", "gna", "gk", "gl", "ena", "ek", "el", "vpeak")} if hh else {}),
         hh_iext=hp.get("i_ext", 0.0),
+        stdp=1 if stdp else 0, stdp_alpha=stdp["alpha"] if stdp else 0.0, stdp_beta=stdp["beta"] if stdp else 0.0,
     )
     v = np.zeros(N)
     w = np.zeros(N)
@@ -271,7 +281,10 @@ def simulate(spec, n_steps: int, *, dense: bool = False, snap_every: int = 0,
     p_out = np.zeros(N)
     gates = [np.zeros(N) for _ in range(3)]
     gap = np.zeros(N)
-    out = _Out(v=_ptr(v), w=_ptr(w), c=_ptr(c), y=_ptr(y), y_clean=_ptr(yc), bg_count=_ptr(bgc),
+    w_fin = np.array(wgt) if stdp else None
+    s_out = np.zeros(N) if stdp else None
+    hs_out = np.zeros((hist_depth, N)) if stdp and hist_depth > 0 else None
+    out = _Out(w_final=_ptr(w_fin), s=_ptr(s_out), hist_s_out=_ptr(hs_out),v=_ptr(v), w=_ptr(w), c=_ptr(c), y=_ptr(y), y_clean=_ptr(yc), bg_count=_ptr(bgc),
                r=_ptr(r_out), p=_ptr(p_out), min_peak_gap=_ptr(gap) if spiking else None,
                m=_ptr(gates[0]), n=_ptr(gates[1]), h=_ptr(gates[2]),
                hist_out=_ptr(hout), hist_out_depth=hist_depth,
@@ -291,7 +304,8 @@ def simulate(spec, n_steps: int, *, dense: bool = False, snap_every: int = 0,
                     hist=_ptr(hist), hist_depth=hist.shape[0],
                     r=arr(init.get("r"), np.float64), p=arr(init.get("p"), np.float64),
                     m=arr(init.get("m"), np.float64), n=arr(init.get("n"), np.float64),
-                    h=arr(init.get("h"), np.float64))
+                    h=arr(init.get("h"), np.float64), w_edge=arr(init.get("w_edge"), np.float64),
+                    s=arr(init.get("s"), np.float64), hist_s=arr(init.get("hist_s"), np.float64))
         rc = L.orc_simulate_from(C.byref(net), C.byref(ini), n_steps, C.byref(out))
     else:
         fn = L.orc_simulate_dense if dense else L.orc_simulate
@@ -303,4 +317,5 @@ def simulate(spec, n_steps: int, *, dense: bool = False, snap_every: int = 0,
                 ev_node=evn[:ne].copy(), ev_step=evs[:ne].copy(), ev_count=out.ev_count,
                 snap_v=sv, snap_w=sw, snap_c=sc, bg_count=bgc, hist=hout, n_end=n0 + n_steps,
                 delay=D, rest=None if spiking else rest_point(fhn), r=r_out, p=p_out,
-                min_peak_gap=gap if spiking else None, m=gates[0], n=gates[1], h=gates[2])
+                min_peak_gap=gap if spiking else None, m=gates[0], n=gates[1], h=gates[2],
+                w_final=w_fin, s=s_out, hist_s=hs_out)

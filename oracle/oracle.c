@@ -65,6 +65,15 @@
  *   No reset: spd(V) = 1 while V >= V_peak; events are upward crossings of V_peak.
  *   The state starts at V = -65 mV with each gate at alpha / (alpha + beta) there.
  *
+ * Plasticity (stdp = 1, spiking models; Sec. 3.2, the plasticity transition G_ij of
+ * Eq. omegatrans): each node carries the time since its last spike,
+ *       s_j' = (1 - spd(V_j)) (s_j + dt),                      s_j(0) = 0,
+ *   and every weight evolves from step-n values, after w_ij(n) has fed S_j(n):
+ *       q_ij = (s_i(t - tau_ij) - s_j(t)) max(spd(V_i(t - tau_ij)), spd(V_j(t)))
+ *       w_ij' = w_ij + dt alpha sign(q_ij) exp(-beta |q_ij|)
+ *   with s and spd before t = 0 taken as 0 (no spike yet).  alpha and beta are one
+ *   pair for the whole network.
+ *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11), written from the
  * published definition; Box-Muller (1958) for the Gaussian.
  *
@@ -246,6 +255,9 @@ typedef struct {
     double tau_c;            /* calcium removal time (ms) */
     /* model 2: Hodgkin-Huxley */
     double hh_C, hh_gna, hh_gk, hh_gl, hh_ena, hh_ek, hh_el, hh_vpeak, hh_iext;
+    /* spike-time-dependent plasticity of every weight (spiking models only) */
+    int32_t stdp;
+    double stdp_alpha, stdp_beta;
 } orc_net;
 
 typedef struct {
@@ -266,6 +278,9 @@ typedef struct {
     double *r, *p;            /* models 1, 2: [N] final PSC state (or NULL) */
     double *m, *n, *h;        /* model 2: [N] final gates (or NULL) */
     double *min_peak_gap;     /* model 1: [N] min over the run of |V - V_peak| (or NULL) */
+    double *w_final;          /* stdp: [E] weights at the end (or NULL) */
+    double *s;                /* stdp: [N] time since the last spike at the end (or NULL) */
+    double *hist_s_out;       /* stdp: [hist_out_depth * N] s_j(n_end - k) (or NULL) */
 } orc_out;
 
 /* One Euler step of one node (the FHN transition about the rest point).
@@ -400,6 +415,9 @@ typedef struct {
     int32_t hist_depth;
     const double *r, *p;      /* models 1, 2: PSC state (NULL = 0) */
     const double *m, *n, *h;  /* model 2: gates (NULL = their values at -65 mV) */
+    const double *w_edge;     /* stdp: [E] weights (NULL = the net's) */
+    const double *s;          /* stdp: [N] time since the last spike (NULL = 0) */
+    const double *hist_s;     /* stdp: [hist_depth * N] s_j(n0 - k) (NULL = 0) */
 } orc_init;
 
 static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense,
@@ -408,7 +426,10 @@ static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense
     int32_t N = net->n_nodes;
     int64_t E = net->n_edges;
     const int izh = net->model == 1, hh = net->model == 2, spiking = izh || hh;
+    const int stdp = net->stdp != 0;
     if (N <= 0 || E < 0 || n_steps < 0 || !(net->dt_ms > 0.0) || (net->model != 0 && !spiking))
+        return ORC_EINVAL;
+    if (stdp && (!spiking || !isfinite(net->stdp_alpha) || !(net->stdp_beta >= 0.0) || !isfinite(net->stdp_beta)))
         return ORC_EINVAL;
     if (izh && !(net->iz_C > 0.0)) return ORC_EINVAL;
     if (hh && !(net->hh_C > 0.0)) return ORC_EINVAL;
@@ -443,10 +464,19 @@ static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense
     double *gm = (double *)calloc((size_t)N, sizeof(double));
     double *gn = (double *)calloc((size_t)N, sizeof(double));
     double *gh = (double *)calloc((size_t)N, sizeof(double));
-    if (!h.buf || !v || !w || !c || !S || !bgc || !r || !p || !gm || !gn || !gh) {
+    /* STDP: the time since the last spike s_j, its history, and the evolving weights */
+    history hs = h;
+    hs.buf = stdp ? (double *)calloc((size_t)(h.depth * N), sizeof(double)) : NULL;
+    double *sj = stdp ? (double *)calloc((size_t)N, sizeof(double)) : NULL;
+    double *wcur = stdp ? (double *)malloc(sizeof(double) * (size_t)(E > 0 ? E : 1)) : NULL;
+    if (!h.buf || !v || !w || !c || !S || !bgc || !r || !p || !gm || !gn || !gh || (stdp && (!hs.buf || !sj || !wcur))) {
         free(h.buf); free(v); free(w); free(c); free(S); free(bgc); free(r); free(p); free(gm); free(gn); free(gh);
+        free(hs.buf); free(sj); free(wcur);
         return ORC_ENOMEM;
     }
+    if (stdp)
+        for (int64_t e = 0; e < E; ++e) wcur[e] = (init && init->w_edge) ? init->w_edge[e] : net->weight[e];
+    const double *wgt = stdp ? wcur : net->weight;
     if (izh)
         for (int32_t j = 0; j < N; ++j) v[j] = net->iz_vr;
     if (hh) {
@@ -476,10 +506,14 @@ static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense
                 if (init->n) gn[j] = init->n[j];
                 if (init->h) gh[j] = init->h[j];
             }
+            if (stdp && init->s) sj[j] = init->s[j];
         }
         for (int64_t k = 1; k < h.depth && k < init->hist_depth; ++k)
             if (n0 - k >= 0)
-                for (int32_t j = 0; j < N; ++j) hist_put(&h, n0 - k, j, init->hist[k * N + j]);
+                for (int32_t j = 0; j < N; ++j) {
+                    hist_put(&h, n0 - k, j, init->hist[k * N + j]);
+                    if (stdp) hist_put(&hs, n0 - k, j, init->hist_s ? init->hist_s[k * N + j] : 0.0);
+                }
     }
     if (out->first_arrival)
         for (int32_t j = 0; j < N; ++j) out->first_arrival[j] = -1;
@@ -492,12 +526,23 @@ static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense
     for (int64_t n = n0; n < n0 + n_steps; ++n) {
         /* record v~(n) (model 1: spd(V(n))) before anything reads the history of this step */
         for (int32_t j = 0; j < N; ++j) hist_put(&h, n, j, spiking ? (v[j] >= vpeak ? 1.0 : 0.0) : v[j]);
+        if (stdp)
+            for (int32_t j = 0; j < N; ++j) hist_put(&hs, n, j, sj[j]);
         /* S_j(n) = sum over edges i -> j of w_ij * v_i(n - D_ij) */
         for (int32_t j = 0; j < N; ++j) S[j] = 0.0;
         for (int64_t e = 0; e < E; ++e) {
             double past = hist_get(&h, n - net->delay[e], net->src[e]);
             if (!spiking && net->coupling == 1) past = v_rest + past;
-            S[net->dst[e]] += net->weight[e] * past;
+            S[net->dst[e]] += wgt[e] * past;
+            if (stdp) {
+                /* Plasticity: q_ij = (s_i(t - tau_ij) - s_j(t)) max(spd(V_i(t - tau_ij)), spd(V_j(t)));
+                 * w_ij' = w_ij + dt alpha sign(q_ij) exp(-beta |q_ij|), after w_ij(t) fed S. */
+                double post = hist_get(&h, n, net->dst[e]);
+                double gate = past > post ? past : post;
+                double q = (hist_get(&hs, n - net->delay[e], net->src[e]) - sj[net->dst[e]]) * gate;
+                if (q != 0.0)
+                    wcur[e] += net->dt_ms * net->stdp_alpha * (q > 0.0 ? 1.0 : -1.0) * exp(-net->stdp_beta * fabs(q));
+            }
         }
         int sample = ((n + 1) % net->sample_every) == 0;
         int64_t k = (n + 1) / net->sample_every - 1;            /* absolute sample number */
@@ -566,6 +611,9 @@ static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense
             }
             v[j] = v1; w[j] = w1; c[j] = c1;
         }
+        /* s_j(t + dt) = (1 - spd(V_j(t))) (s_j(t) + dt) */
+        if (stdp)
+            for (int32_t j = 0; j < N; ++j) sj[j] = hist_get(&h, n, j) > 0.0 ? 0.0 : sj[j] + net->dt_ms;
         if (out->snap_every > 0 && ((n + 1 - n0) % out->snap_every) == 0) {
             memcpy(out->snap_v + snap_idx * N, v, sizeof(double) * (size_t)N);
             memcpy(out->snap_w + snap_idx * N, w, sizeof(double) * (size_t)N);
@@ -590,7 +638,18 @@ static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense
                 out->hist_out[(int64_t)k * N + j] = (k == 0) ? now : hist_get(&h, n_end - k, j);
             }
     }
+    if (stdp) {
+        if (out->w_final) memcpy(out->w_final, wcur, sizeof(double) * (size_t)E);
+        if (out->s) memcpy(out->s, sj, sizeof(double) * (size_t)N);
+        if (out->hist_s_out && out->hist_out_depth >= 1) {
+            int64_t n_end = n0 + n_steps;
+            for (int32_t k = 0; k < out->hist_out_depth; ++k)
+                for (int32_t j = 0; j < N; ++j)
+                    out->hist_s_out[(int64_t)k * N + j] = (k == 0) ? sj[j] : hist_get(&hs, n_end - k, j);
+        }
+    }
     free(h.buf); free(v); free(w); free(c); free(S); free(bgc); free(r); free(p); free(gm); free(gn); free(gh);
+    free(hs.buf); free(sj); free(wcur);
     return ORC_OK;
 }
 

@@ -82,6 +82,7 @@ class NetSpec:
     model: str = "fhn"              # "fhn", "izh" (Izhikevich) or "hh" (Hodgkin-Huxley), + alpha PSC + calcium
     izh: dict = dataclasses.field(default_factory=lambda: dict(IZH_RS))
     hh: dict = dataclasses.field(default_factory=lambda: dict(HH_CLASSIC))
+    stdp: dict | None = None        # spike-time-dependent plasticity {alpha, beta} (spiking models)
 
     @property
     def n_nodes(self) -> int:
