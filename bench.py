@@ -21,6 +21,7 @@ its own seed (the nets are independent problems: no exchange, weak scaling).
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -269,17 +270,24 @@ def run_batched(args, local, stream, rank):
 IZH_NODE_BYTES = 56.2  # V r/w 8, (W, c) r/w 16, (r, p) r/w 16, spike-ring write 4, piece list 4,
                        # background counter 4 + caller id 4, readout 4 B / 20 steps
 HH_NODE_BYTES = 88.12  # the same + gates (m, n, h, pad) r/w 32, readout 4 B / 33 steps
+PLASTIC_NODE_BYTES = 4.0  # plastic weights: the node's own ring word (s, spd) read 4
+PLASTIC_SLOT_BYTES = 4.0  # per lane slot its piece's length and row
+STDP_DEMO = dict(alpha=5.0, beta=0.05)  # weight units per ms, 1/ms
 
 
-def run_spiking(args, spec, local, stream, model: str):
+def run_spiking(args, spec, local, stream, model: str, plastic: bool = False):
     """The same network with spiking nodes -- Izhikevich (dt as the network's) or
     Hodgkin-Huxley (dt = 0.03 ms), both with alpha-function PSCs and calcium, the
-    paper's two benchmark models: step time of the autotuned kernel on the device,
-    CUDA events on the stream."""
+    paper's two benchmark models -- optionally with plastic weights: step time of
+    the autotuned kernel on the device, CUDA events on the stream.  The weight
+    write-backs of a plastic net (edges next to a spike only) are not counted in
+    its algorithmic bytes."""
     import torch
     from paper_0908_3934_b300 import geonet
     hh = model == "hh"
     ispec = netgen.hodgkin_huxley(spec) if hh else netgen.izhikevich(spec)
+    if plastic:
+        ispec = dataclasses.replace(ispec, stdp=dict(STDP_DEMO))
     steps = args.hh_steps if hh else args.izh_steps
     every = ispec.obs["sample_every"]
     net = geonet.Net(ispec, device=local, stream=stream.cuda_stream, obs_capacity=max(64, steps // every + 1))
@@ -293,16 +301,24 @@ def run_spiking(args, spec, local, stream, model: str):
     t = ev0.elapsed_time(ev1) / 1e3
     info = net.gn_net_get_info()
     n_spikes = int(net.gn_get_events(cap=1 << 24)[0].size)
+    changed = None
+    if plastic:
+        changed = float(np.mean(net.gn_get_weights() != np.asarray(ispec.weight, np.float32)))
     net.gn_net_destroy()
     E, N = ispec.n_edges, ispec.n_nodes
     bytes_step = (E * STAGED_EDGE_BYTES + info["step_gathers"] * STAGED_GATHER_BYTES
                   if info["step_kernel"] == 3 else E * EDGE_BYTES) + N * (HH_NODE_BYTES if hh else IZH_NODE_BYTES)
+    if plastic:
+        bytes_step += N * PLASTIC_NODE_BYTES + info["step_lane_slots"] * PLASTIC_SLOT_BYTES
     peak, _ = peaks()
     step_s = t / steps
     nodes = ("Hodgkin-Huxley nodes (classic squid-axon rates) with alpha-function PSCs and calcium, "
              "5 Hz background pulses of 20 uA/cm^2" if hh else
              "Izhikevich regular-spiking nodes with alpha-function PSCs and calcium, 5 Hz background pulses of 2500 pA")
-    return {"workload": f"the same {N}-node network, {nodes}, dt = {ispec.dt_ms} ms, max delay {info['max_delay']} steps",
+    if plastic:
+        nodes += (f", plastic weights (spike-time-dependent, alpha {STDP_DEMO['alpha']}/ms, "
+                  f"beta {STDP_DEMO['beta']}/ms)")
+    out = {"workload": f"the same {N}-node network, {nodes}, dt = {ispec.dt_ms} ms, max delay {info['max_delay']} steps",
             "value": E * steps / t, "unit": METRIC, "ms_per_step": step_s * 1e3, "steps": steps,
             "node_steps_per_s": N * steps / t,
             "rtf": ispec.dt_ms * 1e-3 / step_s, "spikes_per_node_per_s": n_spikes / N / (steps * ispec.dt_ms * 1e-3),
@@ -310,6 +326,9 @@ def run_spiking(args, spec, local, stream, model: str):
             "roofline": {"bound": "hbm", "achieved": bytes_step / step_s / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": bytes_step / step_s / 1e9 / peak, "algorithmic_bytes_per_launch": bytes_step},
             "gpu_launches": steps + steps // 64}
+    if plastic:
+        out["weights_changed_frac"] = changed
+    return out
 
 
 def run_test_set(args, local, stream, model: str = "izh"):
@@ -439,6 +458,7 @@ def main():
     ap.add_argument("--no-izh", action="store_true", help="skip the Izhikevich-model measurement")
     ap.add_argument("--izh-steps", type=int, default=2000)
     ap.add_argument("--no-hh", action="store_true", help="skip the Hodgkin-Huxley-model measurements")
+    ap.add_argument("--no-stdp", action="store_true", help="skip the plastic-weight measurement")
     ap.add_argument("--hh-steps", type=int, default=2000)
     ap.add_argument("--no-test-set", action="store_true", help="skip the 80-network test-set sweeps")
     ap.add_argument("--test-set-steps", type=int, default=10000, help="Izhikevich steps per test-set network")
@@ -560,6 +580,8 @@ def main():
         line["izhikevich"] = run_spiking(args, spec, local, stream, "izh")
     if not args.no_hh and rank == 0:
         line["hodgkin_huxley"] = run_spiking(args, spec, local, stream, "hh")
+    if not args.no_stdp and rank == 0:
+        line["izhikevich_stdp"] = run_spiking(args, spec, local, stream, "izh", plastic=True)
     if not args.no_test_set and rank == 0:
         line["test_set"] = run_test_set(args, local, stream)
         if not args.no_hh:

@@ -102,6 +102,23 @@ typedef struct {
     double C, g_na, g_k, g_l, e_na, e_k, e_l, v_peak, i_ext, psc_a, tau_c;
 } gn_hh_params;
 
+/* Spike-time-dependent plasticity (Sec. 3.2, the plasticity transition G_ij of
+ * Eq. omegatrans; spiking models only).  Each node carries the time since its last
+ * spike, s_j' = (1 - spd(V_j)) (s_j + dt) from s_j = 0, and every weight evolves from
+ * step-n values after w_ij(n) has fed S_j(n):
+ *   q_ij  = (s_i(t - tau_ij) - s_j(t)) max(spd(V_i(t - tau_ij)), spd(V_j(t)))
+ *   w_ij' = w_ij + dt alpha sign(q_ij) exp(-beta |q_ij|)
+ * with s and spd before t = 0 taken as 0.  alpha (weight units per ms) and beta
+ * (1/ms, >= 0) are one pair for the whole network.  s is kept as a whole number of
+ * steps (exact), saturating at 2^30 steps.  A plastic network runs the staged step
+ * kernel (step_kernel 0 or 3; 1 and 2 fail with GN_EINVAL) in a CTA shape that reads
+ * its edge entries from global memory (GN_STEP_SHAPE, default 3), chosen at create
+ * time; the batched form does not take it. */
+typedef struct {
+    int32_t enable;
+    double alpha, beta;
+} gn_stdp_params;
+
 /* Readout (Sec. 3.3): c~' = c~ + (dt/tau_ms)(v~' - c~) every step; every
  * sample_every steps y = gain (V* + c~) + offset + sigma xi, xi ~ N(0, 1) drawn
  * from Philox4x32-10 keyed by `seed` with counter (node, sample, 2). */
@@ -153,6 +170,7 @@ typedef struct {
     int32_t model;               /* GN_MODEL_FHN (0), GN_MODEL_IZH (1) or GN_MODEL_HH (2) */
     gn_izh_params izh;           /* used when model == GN_MODEL_IZH (C > 0, tau_c > 0, all finite) */
     gn_hh_params hh;             /* used when model == GN_MODEL_HH (C > 0, tau_c > 0, all finite) */
+    gn_stdp_params stdp;         /* plastic weights when stdp.enable != 0 (spiking models) */
 } gn_net_desc;
 
 /* A pulse of amplitude amp on node over [t_on_ms, t_off_ms): the steps
@@ -187,6 +205,7 @@ typedef struct {
                                     kernel 3 the distinct (source, delay) pairs summed over its tiles */
     int64_t step_entries;        /* edge records read per step: n_edges for kernels 1 and 2; for kernel 3
                                     the stored entries including the padding of its slices */
+    int64_t step_lane_slots;     /* kernel 3: lane slots (32 per slice of pieces); 0 for kernels 1 and 2 */
 } gn_net_info;
 
 typedef struct gn_net gn_net;
@@ -262,8 +281,19 @@ GN_API gn_status gn_set_izh_state(gn_net *net, const float *V, const float *r, c
 GN_API gn_status gn_get_hh_gates(gn_net *net, float *m, float *n, float *h);
 GN_API gn_status gn_set_hh_gates(gn_net *net, const float *m, const float *n, const float *h);
 
-/* History: out[k][j] = v~_j(step - k), k = 0..depth-1, depth <= ring_depth. */
+/* History: out[k][j] = v~_j(step - k), k = 0..depth-1, depth <= ring_depth (spiking
+ * models: spd(V) in {0, 1}). */
 GN_API gn_status gn_get_history(gn_net *net, float *out, int32_t depth);
+
+/* Plastic networks only (GN_EINVAL otherwise).  The current weights in the caller's
+ * edge order ([n_edges]; set takes effect from the next step). */
+GN_API gn_status gn_get_weights(gn_net *net, float *w);
+GN_API gn_status gn_set_weights(gn_net *net, const float *w);
+/* The time since the last spike, s_hist[k][j] = s_j(step - k) in ms, k < depth <=
+ * ring_depth (k = 0: the current s).  The set rounds each value to whole steps and
+ * keeps the spike history; call it after gn_set_state, which sets s to 0. */
+GN_API gn_status gn_get_stdp_history(gn_net *net, float *s_hist, int32_t depth);
+GN_API gn_status gn_set_stdp_history(gn_net *net, const float *s_hist, int32_t depth);
 
 /* First step at which v~_j became non-zero ([n_nodes], -1 = not yet). */
 GN_API gn_status gn_get_arrivals(gn_net *net, int64_t *first_arrival);

@@ -71,7 +71,7 @@ struct StepArgs {
     const int4 *st_tile2;    // [tiles] {first slice, slices, pieces, 0}
     const void *st_ukey;     // per gather: packed key, or {src, D} when wide
     const int2 *st_slice;    // {first entry, length}
-    const float *st_w;       // entry weights, column-major in slices of 32 pieces
+    float *st_w;             // entry weights, column-major in slices of 32 pieces (plastic nets write them)
     const uint16_t *st_u;    // entry gather index within its tile
     const int32_t *st_rq;    // [N + 1] first piece-list entry of each row
     const uint16_t *st_plist;  // lane slot of each piece
@@ -89,7 +89,16 @@ struct StepArgs {
     float *iz_v;
     float2 *rp;
     float4 *hh_g;
+    // plasticity (spiking models, staged kernel): the ring word of a node is
+    // (s / dt) << 1 | spd(V), s the time since its last spike; dw = stdp_dta sign(q) e^(-beta |q|)
+    int32_t stdp;
+    float stdp_dta, stdp_beta;   // dt alpha, beta
+    const uint32_t *st_pinfo;    // per lane slot: piece length | local row << 16
 };
+
+// A plastic model's kernel code: the node model | kPlastic.
+constexpr int kPlastic = 4;
+constexpr uint32_t kSpikeStepsMax = 1u << 30;  // s saturates at this many steps
 
 // Calls f(std::integral_constant<int, m>) for node model m: every step kernel is
 // instantiated once per model, so no model's code sits in another model's kernel
@@ -101,6 +110,19 @@ inline cudaError_t with_model(int model, F &&f)
         case 1: return f(std::integral_constant<int, 1>{});
         case 2: return f(std::integral_constant<int, 2>{});
         default: return f(std::integral_constant<int, 0>{});
+    }
+}
+
+// The same for the staged kernel, which also runs the plastic spiking models
+// (codes 1 | kPlastic, 2 | kPlastic).
+template <class F>
+inline cudaError_t with_model_plastic(int model, bool plastic, F &&f)
+{
+    if (!plastic) return with_model(model, static_cast<F &&>(f));
+    switch (model) {
+        case 1: return f(std::integral_constant<int, 1 | kPlastic>{});
+        case 2: return f(std::integral_constant<int, 2 | kPlastic>{});
+        default: return cudaErrorInvalidValue;
     }
 }
 
@@ -145,7 +167,8 @@ struct StagedShape {
 extern const StagedShape kStagedShapes[kNumStagedShapes];
 cudaError_t launch_step_staged(const StepArgs &a, int n_tiles, int k, const StagedShape &shape, bool packed,
                                bool stream_edges, size_t smem_bytes, cudaStream_t s);
-cudaError_t step_staged_prepare(const StagedShape &shape, int model, bool packed, bool stream_edges, size_t smem_bytes);
+cudaError_t step_staged_prepare(const StagedShape &shape, int model, bool plastic, bool packed, bool stream_edges,
+                                size_t smem_bytes);
 // batched form with the staged layout: one launch per step over every member's
 // tiles (tile_net[t] = the member of tile t), tiles cut with kBatchStagedShape
 constexpr StagedShape kBatchStagedShape = {128, 3072, 4096, 256, 0};

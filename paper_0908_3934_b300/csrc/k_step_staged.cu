@@ -51,8 +51,11 @@ __device__ __forceinline__ void staged_tile(const StepArgs &a, const int tile, c
 {
     // [mbarrier 16 B][keys][values (wide keys only)][entry weights][entry indices][piece sums];
     // without entry staging (kSE false) the entry arrays are absent
+    constexpr bool kPl = (kM & kPlastic) != 0;
+    static_assert(!(kPl && kSE), "plastic weights are written back to global memory: no entry staging");
     extern __shared__ __align__(128) unsigned char s_raw[];
     __shared__ int s_fail;
+    __shared__ uint32_t s_post[kPl ? T : 1];  // plastic: each row's ring word of step n
     uint64_t *bar = reinterpret_cast<uint64_t *>(s_raw);
     uint32_t *s_key = reinterpret_cast<uint32_t *>(s_raw + 16);
     float *s_val = kPacked ? reinterpret_cast<float *>(s_key)
@@ -106,8 +109,13 @@ __device__ __forceinline__ void staged_tile(const StepArgs &a, const int tile, c
     float v = 0.0f;
     float2 wc = make_float2(0.0f, 0.0f);
     int32_t cnt0 = kLoad;
+    uint32_t word_now = 0;
     if (own) {
         if constexpr (kM == 0) v = a.ring[(n & a.ring_mask) * a.ring_stride + r];  // spiking models keep V apart
+        if constexpr (kPl) {
+            word_now = reinterpret_cast<const uint32_t *>(a.ring)[(n & a.ring_mask) * a.ring_stride + r];
+            s_post[t] = word_now;
+        }
         wc = a.wc[r];
         if (a.bg_thr) cnt0 = a.bgc[r];
     }
@@ -143,7 +151,7 @@ __device__ __forceinline__ void staged_tile(const StepArgs &a, const int tile, c
     // a spiking node's update reads S only in p: the rest runs while the gathers land
     float2 rp0 = make_float2(0.0f, 0.0f);
     if constexpr (kM != 0)
-        if (own) rp0 = spiking_begin<kM>(a, r, n, wc, orig, cnt0);
+        if (own) rp0 = spiking_begin<kM>(a, r, n, wc, orig, cnt0, word_now);
     cp_async_wait_all();
     __syncthreads();
 
@@ -151,7 +159,27 @@ __device__ __forceinline__ void staged_tile(const StepArgs &a, const int tile, c
     for (int sl = warp; sl < td2.y; sl += T / 32) {
         const int2 sd = sl == warp ? sd0 : __ldg(a.st_slice + td2.x + sl);
         float acc = 0.0f;
-        if constexpr (kSE) {
+        if constexpr (kPl) {
+            // plastic weights: S from w_ij(n), then w_ij(n + 1) written back, over the
+            // piece's own entries (the slice's padding after them stays 0)
+            const uint32_t pi = __ldg(a.st_pinfo + 32 * (td2.x + sl) + lane);
+            const int plen = static_cast<int>(pi & 0xffffu);
+            const uint32_t post = s_post[pi >> 16];
+            const int32_t k_post = static_cast<int32_t>(post >> 1);
+            const uint32_t *s_word = reinterpret_cast<const uint32_t *>(s_val);
+            float *wp = a.st_w + td2.z + sd.x + lane;
+            const uint16_t *up = a.st_u + td2.z + sd.x + lane;
+            for (int kk = 0; kk < plen; ++kk) {
+                const float w = __ldcs(wp + kk * 32);
+                const uint32_t word = s_word[__ldcs(up + kk * 32)];
+                acc = __fadd_rn(acc, __fmul_rn(w, (word & 1u) ? 1.0f : 0.0f));
+                if ((word | post) & 1u) {
+                    // q = (s_i(t - tau) - s_j(t)) max(spd_i, spd_j), both s in whole steps
+                    const float q = static_cast<float>(static_cast<int32_t>(word >> 1) - k_post) * a.dt;
+                    if (q != 0.0f) wp[kk * 32] = w + copysignf(a.stdp_dta * expf(-a.stdp_beta * fabsf(q)), q);
+                }
+            }
+        } else if constexpr (kSE) {
             const float *wp = s_w + sd.x + lane;
             const uint16_t *up = s_u + sd.x + lane;
 #pragma unroll 4
@@ -242,6 +270,9 @@ template <int kM, int T, bool kSE>
 cudaError_t dispatch_fmt(bool launch, const StepArgs *a, int n_tiles, int k, bool packed, bool stream_edges,
                          size_t smem, cudaStream_t s)
 {
+    if constexpr ((kM & kPlastic) != 0 && kSE) {
+        return cudaErrorInvalidValue;  // plastic weights: entries are read from global memory
+    } else {
     if (launch) {
         if (packed)
             return stream_edges ? launch_t<kM, T, kSE, true, true>(*a, n_tiles, k, smem, s)
@@ -256,13 +287,14 @@ cudaError_t dispatch_fmt(bool launch, const StepArgs *a, int n_tiles, int k, boo
                             : cudaFuncSetAttribute(k_step_staged<kM, T, kSE, true, false>, at, b);
     return stream_edges ? cudaFuncSetAttribute(k_step_staged<kM, T, kSE, false, true>, at, b)
                         : cudaFuncSetAttribute(k_step_staged<kM, T, kSE, false, false>, at, b);
+    }
 }
 
-cudaError_t dispatch(bool launch, const StagedShape &sh, int model, const StepArgs *a, int n_tiles, int k,
-                     bool packed, bool stream_edges, size_t smem, cudaStream_t s)
+cudaError_t dispatch(bool launch, const StagedShape &sh, int model, bool plastic, const StepArgs *a, int n_tiles,
+                     int k, bool packed, bool stream_edges, size_t smem, cudaStream_t s)
 {
     const bool se = sh.stage_entries != 0;
-    return with_model(model, [&](auto m) {
+    return with_model_plastic(model, plastic, [&](auto m) {
         constexpr int M = decltype(m)::value;
         switch (sh.threads) {
             case 128:
@@ -287,12 +319,13 @@ cudaError_t launch_step_staged(const StepArgs &a, int n_tiles, int k, const Stag
                                bool stream_edges, size_t smem_bytes, cudaStream_t s)
 {
     if (n_tiles <= 0) return cudaSuccess;
-    return dispatch(true, shape, a.model, &a, n_tiles, k, packed, stream_edges, smem_bytes, s);
+    return dispatch(true, shape, a.model, a.stdp != 0, &a, n_tiles, k, packed, stream_edges, smem_bytes, s);
 }
 
-cudaError_t step_staged_prepare(const StagedShape &shape, int model, bool packed, bool stream_edges, size_t smem_bytes)
+cudaError_t step_staged_prepare(const StagedShape &shape, int model, bool plastic, bool packed, bool stream_edges,
+                                size_t smem_bytes)
 {
-    return dispatch(false, shape, model, nullptr, 0, 0, packed, stream_edges, smem_bytes, nullptr);
+    return dispatch(false, shape, model, plastic, nullptr, 0, 0, packed, stream_edges, smem_bytes, nullptr);
 }
 
 namespace {

@@ -76,7 +76,7 @@ struct gn_net {
     int st_shape = -1;
     int n_tiles = 0;
     size_t st_smem = 0;
-    int64_t st_gathers = 0, st_entries = 0;
+    int64_t st_gathers = 0, st_entries = 0, st_slots = 0;
     int st_max_u = 0, st_max_x = 0, st_max_p = 0;
     DevArray<int4> st_tile, st_tile2;
     DevArray<uint32_t> st_ukey;
@@ -85,6 +85,10 @@ struct gn_net {
     DevArray<uint16_t> st_u, st_plist;
     DevArray<int32_t> st_rq;
     std::unique_ptr<gnrt::HostNet> host;
+    // plastic weights: the entries' caller edges (host) and the lane slots' piece info
+    bool stdp = false;
+    std::vector<int32_t> st_eidx;
+    DevArray<uint32_t> st_pinfo;
 
     void release_staged()
     {
@@ -96,6 +100,8 @@ struct gn_net {
         st_u.release();
         st_plist.release();
         st_rq.release();
+        st_pinfo.release();
+        st_eidx.clear();
         st_shape = -1;
         n_tiles = 0;
     }
@@ -173,6 +179,10 @@ bool set_staged(gn_net *net, int shape)
         net->st_u.upload(L.u, &net->bytes);
         net->st_plist.upload(L.plist, &net->bytes);
         net->st_rq.upload(L.rq, &net->bytes);
+        if (net->stdp) {
+            net->st_pinfo.upload(L.pinfo, &net->bytes);
+            net->st_eidx = std::move(L.eidx);
+        }
         gn::StepArgs &a = net->args;
         a.st_tile = net->st_tile.p;
         a.st_tile2 = net->st_tile2.p;
@@ -182,6 +192,7 @@ bool set_staged(gn_net *net, int shape)
         a.st_u = net->st_u.p;
         a.st_rq = net->st_rq.p;
         a.st_plist = net->st_plist.p;
+        a.st_pinfo = net->st_pinfo.p;
         a.st_ucap = L.max_u;
         a.st_xcap = L.max_x;
         net->st_max_u = L.max_u;
@@ -190,7 +201,8 @@ bool set_staged(gn_net *net, int shape)
         net->n_tiles = static_cast<int>(L.tile.size());
         net->st_gathers = static_cast<int64_t>(L.ukey.size()) / (net->packed ? 1 : 2);
         net->st_entries = static_cast<int64_t>(L.w.size());
-        if (net->E == 0) net->st_gathers = net->st_entries = 0;  // the placeholder entries of an empty layout
+        net->st_slots = 32 * static_cast<int64_t>(L.slice.size());
+        if (net->E == 0) net->st_gathers = net->st_entries = net->st_slots = 0;  // an empty layout's placeholders
         else {
             int64_t g = 0;  // gathers without the alignment padding of each tile's key block
             for (const int4 &t : L.tile) g += t.w;
@@ -203,7 +215,9 @@ bool set_staged(gn_net *net, int shape)
                         (sh.stage_entries ? static_cast<size_t>(net->st_max_x) * 6 : 0) +
                         static_cast<size_t>(net->st_max_p) * 4;
     if (smem > static_cast<size_t>(max_smem)) return false;
-    cuda_check(gn::step_staged_prepare(sh, net->model, net->packed, net->stream_edges, smem), "staged kernel setup");
+    if (net->stdp && sh.stage_entries) return false;  // plastic weights are written back to global memory
+    cuda_check(gn::step_staged_prepare(sh, net->model, net->stdp, net->packed, net->stream_edges, smem),
+               "staged kernel setup");
     net->st_smem = smem;
     net->st_shape = shape;
     return true;
@@ -625,18 +639,23 @@ gn_status gn_net_create(const gn_net_desc *desc, gn_net **out)
         a.hh_g = net->hh_g.p;
 
         // the kernel is fixed now or timed on the first gn_step (kind 0)
-        if (desc->step_kernel == 0 || desc->step_kernel == 3) net->host = std::make_unique<gnrt::HostNet>(std::move(h));
+        // a plastic net runs the staged kernel, fixed now: the weights live in its layout
+        net->stdp = desc->stdp.enable != 0;
+        const int kind = net->stdp ? 3 : desc->step_kernel;
+        if (kind == 0 || kind == 3) net->host = std::make_unique<gnrt::HostNet>(std::move(h));
         // GN_STEP_SHAPE=i picks the CTA shape of an explicitly chosen kernel 1 or 3
-        int shape = 0;
-        if (const char *e = getenv("GN_STEP_SHAPE"); e && *e && (desc->step_kernel == 1 || desc->step_kernel == 3)) {
+        int shape = net->stdp ? 3 : 0;
+        if (const char *e = getenv("GN_STEP_SHAPE"); e && *e && (kind == 1 || kind == 3)) {
             shape = atoi(e);
-            const int n_shapes = desc->step_kernel == 1 ? gn::kNumStepShapes : gn::kNumStagedShapes;
+            const int n_shapes = kind == 1 ? gn::kNumStepShapes : gn::kNumStagedShapes;
             if (shape < 0 || shape >= n_shapes) fail(GN_EINVAL, "GN_STEP_SHAPE=%s is not a shape of kernel %d", e,
-                                                       desc->step_kernel);
+                                                       kind);
+            if (net->stdp && gn::kStagedShapes[shape].stage_entries)
+                fail(GN_EINVAL, "GN_STEP_SHAPE=%s stages the edge entries, which plastic weights cannot use", e);
         }
-        configure(net, desc->step_kernel == 2 ? 2 : 1, desc->step_kernel == 1 ? shape : 0);
-        if (desc->step_kernel == 3) configure(net, 3, shape);
-        if (desc->step_kernel == 0)
+        configure(net, kind == 2 ? 2 : 1, kind == 1 ? shape : 0);
+        if (kind == 3) configure(net, 3, shape);
+        if (kind == 0)
             net->step_kernel = 0;
         else
             finalize_kernel(net);
@@ -686,6 +705,7 @@ gn_status gn_net_get_info(const gn_net *net, gn_net_info *info)
         info->device_bytes = net->bytes;
         info->step_gathers = staged ? net->st_gathers : net->E;
         info->step_entries = staged ? net->st_entries : net->E;
+        info->step_lane_slots = staged ? net->st_slots : 0;
     });
 }
 
@@ -845,7 +865,15 @@ gn_status gn_set_state(gn_net *net, const float *hist, int32_t depth, const floa
         std::vector<float> ring(R * stride, 0.0f);
         for (int32_t k = 0; k < depth; ++k) {
             const int64_t slot = (step - k) & (net->R - 1);
-            for (int32_t j = 0; j < N; ++j) ring[slot * stride + net->inv[j]] = hist[static_cast<int64_t>(k) * N + j];
+            for (int32_t j = 0; j < N; ++j) {
+                const float x = hist[static_cast<int64_t>(k) * N + j];
+                if (net->stdp) {  // the spike bit, s = 0 (gn_set_stdp_history sets s)
+                    const uint32_t word = x != 0.0f ? 1u : 0u;
+                    std::memcpy(&ring[slot * stride + net->inv[j]], &word, 4);
+                } else {
+                    ring[slot * stride + net->inv[j]] = x;
+                }
+            }
         }
         std::vector<float2> wc(N, make_float2(0.0f, 0.0f));
         std::vector<int32_t> bg(N, 0);
@@ -966,7 +994,104 @@ gn_status gn_get_history(gn_net *net, float *out, int32_t depth)
             const int64_t slot = (net->step - k) & (net->R - 1);
             cuda_check(cudaMemcpy(tmp.data(), net->ring.p + slot * net->stride, N * 4, cudaMemcpyDeviceToHost),
                        "D2H history");
+            if (net->stdp)  // the spike bit of a plastic net's ring word
+                for (float &x : tmp) {
+                    uint32_t word;
+                    std::memcpy(&word, &x, 4);
+                    x = (word & 1u) ? 1.0f : 0.0f;
+                }
             permute_rows_to_caller(net, tmp.data(), out + static_cast<int64_t>(k) * N, 1);
+        }
+    });
+}
+
+namespace {
+
+void check_plastic(const gn_net *net)
+{
+    if (!net->stdp) fail(GN_EINVAL, "the network does not have plastic weights");
+}
+
+}  // namespace
+
+gn_status gn_get_weights(gn_net *net, float *w)
+{
+    return guarded([&] {
+        check_net(net);
+        check_plastic(net);
+        if (!w) fail(GN_EINVAL, "w is NULL");
+        DeviceGuard dg(net->device);
+        sync(net);
+        std::vector<float> t(net->st_w.n);
+        cuda_check(cudaMemcpy(t.data(), net->st_w.p, t.size() * 4, cudaMemcpyDeviceToHost), "D2H weights");
+        for (size_t x = 0; x < t.size(); ++x)
+            if (net->st_eidx[x] >= 0) w[net->st_eidx[x]] = t[x];
+    });
+}
+
+gn_status gn_set_weights(gn_net *net, const float *w)
+{
+    return guarded([&] {
+        check_net(net);
+        check_plastic(net);
+        if (!w) fail(GN_EINVAL, "w is NULL");
+        for (int64_t e = 0; e < net->E; ++e)
+            if (!std::isfinite(w[e])) fail(GN_EINVAL, "edge %lld: weight not finite", static_cast<long long>(e));
+        DeviceGuard dg(net->device);
+        sync(net);
+        std::vector<float> t(net->st_w.n, 0.0f);
+        for (size_t x = 0; x < t.size(); ++x)
+            if (net->st_eidx[x] >= 0) t[x] = w[net->st_eidx[x]];
+        cuda_check(cudaMemcpy(net->st_w.p, t.data(), t.size() * 4, cudaMemcpyHostToDevice), "H2D weights");
+    });
+}
+
+gn_status gn_get_stdp_history(gn_net *net, float *s_hist, int32_t depth)
+{
+    return guarded([&] {
+        check_net(net);
+        check_plastic(net);
+        if (depth < 1 || depth > net->R) fail(GN_EINVAL, "depth must be in [1, ring_depth]");
+        if (!s_hist) fail(GN_EINVAL, "s_hist is NULL");
+        DeviceGuard dg(net->device);
+        sync(net);
+        const int32_t N = net->N;
+        std::vector<uint32_t> t(N);
+        for (int32_t k = 0; k < depth; ++k) {
+            const int64_t slot = (net->step - k) & (net->R - 1);
+            cuda_check(cudaMemcpy(t.data(), net->ring.p + slot * net->stride, N * 4ull, cudaMemcpyDeviceToHost),
+                       "D2H history");
+            for (int32_t i = 0; i < N; ++i)
+                s_hist[static_cast<int64_t>(k) * N + net->perm[i]] =
+                    static_cast<float>(static_cast<double>(t[i] >> 1) * net->dt);
+        }
+    });
+}
+
+gn_status gn_set_stdp_history(gn_net *net, const float *s_hist, int32_t depth)
+{
+    return guarded([&] {
+        check_net(net);
+        check_plastic(net);
+        if (depth < 1 || depth > net->R) fail(GN_EINVAL, "depth must be in [1, ring_depth]");
+        if (!s_hist) fail(GN_EINVAL, "s_hist is NULL");
+        const int32_t N = net->N;
+        for (int64_t x = 0; x < static_cast<int64_t>(depth) * N; ++x)
+            if (!(s_hist[x] >= 0.0f) || !std::isfinite(s_hist[x])) fail(GN_EINVAL, "s must be finite and >= 0");
+        DeviceGuard dg(net->device);
+        sync(net);
+        std::vector<uint32_t> t(N);
+        for (int32_t k = 0; k < depth; ++k) {
+            const int64_t slot = (net->step - k) & (net->R - 1);
+            uint32_t *dev = reinterpret_cast<uint32_t *>(net->ring.p + slot * net->stride);
+            cuda_check(cudaMemcpy(t.data(), dev, N * 4ull, cudaMemcpyDeviceToHost), "D2H history");
+            for (int32_t j = 0; j < N; ++j) {
+                const double steps = std::nearbyint(static_cast<double>(s_hist[static_cast<int64_t>(k) * N + j]) / net->dt);
+                const uint32_t kq = static_cast<uint32_t>(std::min(steps, static_cast<double>(gn::kSpikeStepsMax)));
+                uint32_t &word = t[net->inv[j]];
+                word = (kq << 1) | (word & 1u);
+            }
+            cuda_check(cudaMemcpy(dev, t.data(), N * 4ull, cudaMemcpyHostToDevice), "H2D history");
         }
     });
 }
@@ -1027,7 +1152,8 @@ gn_status gn_save_state(gn_net *net, void *buf, size_t cap, size_t *used)
         check_net(net);
         const size_t N = net->N, RS = net->ring.n;
         // spiking models: V, (r, p); Hodgkin-Huxley also (m, n, h, 0)
-        const size_t extra = (net->model != GN_MODEL_FHN ? N * 12 : 0) + (net->model == GN_MODEL_HH ? N * 16 : 0);
+        const size_t extra = (net->model != GN_MODEL_FHN ? N * 12 : 0) + (net->model == GN_MODEL_HH ? N * 16 : 0) +
+                             (net->stdp ? net->st_w.n * 4 : 0);
         const size_t need = sizeof(CkptHeader) + RS * 4 + N * 8 + N * 4 + N * 8 + extra;
         if (used) *used = need;
         if (!buf) return;
@@ -1051,8 +1177,11 @@ gn_status gn_save_state(gn_net *net, void *buf, size_t cap, size_t *used)
             p += N * 4;
             cuda_check(cudaMemcpy(p, net->rp.p, N * 8, cudaMemcpyDeviceToHost), "D2H rp");
             p += N * 8;
-            if (net->model == GN_MODEL_HH)
+            if (net->model == GN_MODEL_HH) {
                 cuda_check(cudaMemcpy(p, net->hh_g.p, N * 16, cudaMemcpyDeviceToHost), "D2H gates");
+                p += N * 16;
+            }
+            if (net->stdp) cuda_check(cudaMemcpy(p, net->st_w.p, net->st_w.n * 4, cudaMemcpyDeviceToHost), "D2H weights");
         }
     });
 }
@@ -1063,7 +1192,8 @@ gn_status gn_load_state(gn_net *net, const void *buf, size_t size)
         check_net(net);
         if (!buf) fail(GN_EINVAL, "buf is NULL");
         const size_t N = net->N, RS = net->ring.n;
-        const size_t extra = (net->model != GN_MODEL_FHN ? N * 12 : 0) + (net->model == GN_MODEL_HH ? N * 16 : 0);
+        const size_t extra = (net->model != GN_MODEL_FHN ? N * 12 : 0) + (net->model == GN_MODEL_HH ? N * 16 : 0) +
+                             (net->stdp ? net->st_w.n * 4 : 0);
         const size_t need = sizeof(CkptHeader) + RS * 4 + N * 8 + N * 4 + N * 8 + extra;
         if (size < need) fail(GN_EINVAL, "checkpoint is truncated");
         CkptHeader h;
@@ -1085,8 +1215,11 @@ gn_status gn_load_state(gn_net *net, const void *buf, size_t size)
             p += N * 4;
             cuda_check(cudaMemcpy(net->rp.p, p, N * 8, cudaMemcpyHostToDevice), "H2D rp");
             p += N * 8;
-            if (net->model == GN_MODEL_HH)
+            if (net->model == GN_MODEL_HH) {
                 cuda_check(cudaMemcpy(net->hh_g.p, p, N * 16, cudaMemcpyHostToDevice), "H2D gates");
+                p += N * 16;
+            }
+            if (net->stdp) cuda_check(cudaMemcpy(net->st_w.p, p, net->st_w.n * 4, cudaMemcpyHostToDevice), "H2D weights");
         }
         net->step = h.step;
         net->read_cursor = h.step / net->sample_every;

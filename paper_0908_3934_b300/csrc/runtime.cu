@@ -117,6 +117,13 @@ void validate_desc(const gn_net_desc *d)
     }
     if (d->model != GN_MODEL_FHN && d->model != GN_MODEL_IZH && d->model != GN_MODEL_HH)
         fail(GN_EINVAL, "unknown node model");
+    if (d->stdp.enable) {
+        if (d->model == GN_MODEL_FHN) fail(GN_EINVAL, "plasticity needs a spiking node model");
+        if (!std::isfinite(d->stdp.alpha) || !std::isfinite(d->stdp.beta) || d->stdp.beta < 0.0)
+            fail(GN_EINVAL, "plasticity needs a finite alpha and a finite beta >= 0");
+        if (d->step_kernel == 1 || d->step_kernel == 2)
+            fail(GN_EINVAL, "plastic networks run the staged step kernel (step_kernel 0 or 3)");
+    }
     if (d->model == GN_MODEL_HH) {
         const gn_hh_params &z = d->hh;
         for (double x : {z.C, z.g_na, z.g_k, z.g_l, z.e_na, z.e_k, z.e_l, z.v_peak, z.i_ext, z.psc_a, z.tau_c})
@@ -353,6 +360,7 @@ void host_build(const gn_net_desc *d, std::vector<int32_t> delay, int64_t n_clam
         }
         h.w[p] = d->weight[e];
     }
+    if (d->stdp.enable) h.eorig = std::move(order);
     if (d->coupling == GN_COUPLE_RAW && d->model == GN_MODEL_FHN) {
         h.bias.assign(N, 0.0f);
         for (int32_t r = 0; r < N; ++r) {
@@ -444,6 +452,9 @@ void fill_step_params(const gn_net_desc *d, const HostNet &h, gn::StepArgs &a)
         a.ca_q = static_cast<float>(1.0 / z.tau_c);
         a.vrest = 0.0f;  // the readout is gain c + offset
     }
+    a.stdp = d->stdp.enable ? 1 : 0;
+    a.stdp_dta = static_cast<float>(d->dt_ms * d->stdp.alpha);
+    a.stdp_beta = static_cast<float>(d->stdp.beta);
     if (d->model == GN_MODEL_HH) {
         const gn_hh_params &z = d->hh;
         a.iz_dtc = static_cast<float>(d->dt_ms / z.C);

@@ -96,6 +96,7 @@ struct HostNet {
     std::vector<int32_t> row_ptr;            // [N + 1 + 8]
     std::vector<int32_t> blk;                // [n_blocks + 1]
     std::vector<int4> desc;                  // [n_blocks] {r0, r1, e0, e1}
+    std::vector<int32_t> eorig;              // plastic nets: caller edge of each CSR position
     int n_blocks() const { return static_cast<int>(blk.size()) - 1; }
 };
 
@@ -133,6 +134,10 @@ struct StagedLayout {
     std::vector<uint16_t> u;       // entry gather index within the tile (0 in the padding)
     std::vector<int32_t> rq;       // [N + 1] first piece-list entry of each row
     std::vector<uint16_t> plist;   // lane slot (32 * slice + lane) of each piece, rows in order
+    // plastic nets only: the caller edge of each entry (-1: padding), and per lane slot
+    // (32 * global slice + lane) its piece's length | local row << 16
+    std::vector<int32_t> eidx;
+    std::vector<uint32_t> pinfo;
     int max_u = 0, max_x = 0, max_p = 0;  // largest padded gather count, entries, lane slots of a tile
     // shared memory of one CTA: mbarrier, keys (wide keys need a separate value
     // array; packed values overwrite their keys), entry weights and indices when

@@ -76,6 +76,7 @@ private:
 
 struct Piece {
     int32_t len, first, stride;  // edges first, first + stride, ... (len of them) of the CSR
+    int32_t row;                 // its row within the tile
 };
 
 // Pieces of a row of L edges, in the summation order every step kernel uses: one
@@ -160,8 +161,8 @@ bool build_staged(const HostNet &h, int threads, int ucap, int ecap, int pcap, S
             const int32_t e0 = h.row_ptr[rr], e1 = h.row_ptr[rr + 1];
             const int32_t L = e1 - e0;
             const int m = pieces_of(L);
-            if (m == 1) pcs.push_back({L, e0, 1});
-            for (int q = 0; q < m && m == 32; ++q) pcs.push_back({(L - q + 31) / 32, e0 + q, 32});
+            if (m == 1) pcs.push_back({L, e0, 1, rr - r0});
+            for (int q = 0; q < m && m == 32; ++q) pcs.push_back({(L - q + 31) / 32, e0 + q, 32, rr - r0});
         }
         ord.resize(np);
         std::iota(ord.begin(), ord.end(), 0);
@@ -178,6 +179,7 @@ bool build_staged(const HostNet &h, int threads, int ucap, int ecap, int pcap, S
         }
 
         // slices of 32 pieces, entries column-major
+        const bool plastic = !h.eorig.empty();
         const size_t x0 = o.w.size();
         for (int s = 0; s < ns; ++s) {
             const int32_t len = pcs[ord[32 * s]].len;
@@ -186,12 +188,19 @@ bool build_staged(const HostNet &h, int threads, int ucap, int ecap, int pcap, S
             o.slice.push_back(make_int2(static_cast<int>(off - x0), len));
             o.w.resize(off + static_cast<size_t>(len) * 32, 0.0f);
             o.u.resize(off + static_cast<size_t>(len) * 32, 0);
-            for (int lane = 0; lane < 32 && 32 * s + lane < np; ++lane) {
+            if (plastic) o.eidx.resize(off + static_cast<size_t>(len) * 32, -1);
+            for (int lane = 0; lane < 32; ++lane) {
+                if (32 * s + lane >= np) {
+                    if (plastic) o.pinfo.push_back(0u);
+                    continue;
+                }
                 const Piece &pc = pcs[ord[32 * s + lane]];
+                if (plastic) o.pinfo.push_back(static_cast<uint32_t>(pc.len) | (static_cast<uint32_t>(pc.row) << 16));
                 for (int32_t k = 0; k < pc.len; ++k) {
                     const int64_t e = pc.first + static_cast<int64_t>(k) * pc.stride;
                     o.w[off + static_cast<size_t>(k) * 32 + lane] = h.w[e];
                     o.u[off + static_cast<size_t>(k) * 32 + lane] = static_cast<uint16_t>(set.index(edge_key(e)));
+                    if (plastic) o.eidx[off + static_cast<size_t>(k) * 32 + lane] = h.eorig[e];
                 }
             }
         }
@@ -208,9 +217,11 @@ bool build_staged(const HostNet &h, int threads, int ucap, int ecap, int pcap, S
     if (o.w.empty()) {
         o.w.push_back(0.0f);
         o.u.push_back(0);
+        if (!h.eorig.empty()) o.eidx.push_back(-1);
     }
     if (o.plist.empty()) o.plist.push_back(0);
     if (o.slice.empty()) o.slice.push_back(make_int2(0, 0));
+    if (!h.eorig.empty() && o.pinfo.empty()) o.pinfo.push_back(0u);
     return true;
 }
 

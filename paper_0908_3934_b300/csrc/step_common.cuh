@@ -130,11 +130,20 @@ __device__ __forceinline__ void record_event(const StepArgs &a, int r, int64_t s
 }
 
 // Spiking-node outputs of step n -> n + 1: spike ring (spd(V1)), events, first
-// spike, and the calcium readout every sample_every steps.
+// spike, and the calcium readout every sample_every steps.  A plastic net's ring
+// word also carries s in whole steps: s_j' = (1 - spd(V_j)) (s_j + dt), from the
+// word of step n.
+template <bool kPl>
 __device__ __forceinline__ void spiking_outputs(const StepArgs &a, int r, int64_t n, bool above, bool above1,
-                                                float c1, int32_t orig)
+                                                float c1, int32_t orig, uint32_t word_now)
 {
-    a.ring[((n + 1) & a.ring_mask) * a.ring_stride + r] = above1 ? 1.0f : 0.0f;
+    const int64_t at = ((n + 1) & a.ring_mask) * a.ring_stride + r;
+    if constexpr (kPl) {
+        const uint32_t k1 = (word_now & 1u) ? 0u : min((word_now >> 1) + 1u, kSpikeStepsMax);
+        reinterpret_cast<uint32_t *>(a.ring)[at] = (k1 << 1) | (above1 ? 1u : 0u);
+    } else {
+        a.ring[at] = above1 ? 1.0f : 0.0f;
+    }
     if (above1 && !above) {
         record_event(a, r, n + 1);
         if (a.first[r] < 0) a.first[r] = n + 1;
@@ -153,7 +162,9 @@ __device__ __forceinline__ void spiking_outputs(const StepArgs &a, int r, int64_
 // but p, the one variable that reads S = sum_e w_e spd(V_src(n - D_e)), is updated
 // here (the ring holds spd); returns (r, p) at step n for psc_finish.  A spike
 // resets V, so every step with V >= V_peak is a new spike.
-__device__ __forceinline__ float2 izh_begin(const StepArgs &a, int r, int64_t n, float2 wc, float U, int32_t orig)
+template <bool kPl>
+__device__ __forceinline__ float2 izh_begin(const StepArgs &a, int r, int64_t n, float2 wc, float U, int32_t orig,
+                                            uint32_t word_now)
 {
     const float V = a.iz_v[r];
     const float W = wc.x, c = wc.y;
@@ -170,7 +181,7 @@ __device__ __forceinline__ float2 izh_begin(const StepArgs &a, int r, int64_t n,
     const float c1 = c + a.dt * (spike ? 1.0f - c * a.ca_q : -c * a.ca_q);
     a.iz_v[r] = V1;
     a.wc[r] = make_float2(W1, c1);
-    spiking_outputs(a, r, n, false, V1 >= a.iz_vpeak, c1, orig);
+    spiking_outputs<kPl>(a, r, n, false, V1 >= a.iz_vpeak, c1, orig, word_now);
     return rp;
 }
 
@@ -184,7 +195,9 @@ __device__ __forceinline__ float hh_trap(float x, float y)
 // (mV, ms), forward Euler of V and the gates m, n, h from step-n values, the PSC and
 // calcium as in izh_begin (p is left to psc_finish); no reset, events are upward
 // crossings of V_peak.
-__device__ __forceinline__ float2 hh_begin(const StepArgs &a, int r, int64_t n, float2 wc, float U, int32_t orig)
+template <bool kPl>
+__device__ __forceinline__ float2 hh_begin(const StepArgs &a, int r, int64_t n, float2 wc, float U, int32_t orig,
+                                           uint32_t word_now)
 {
     const float V = a.iz_v[r];
     const float4 g = a.hh_g[r];
@@ -206,7 +219,7 @@ __device__ __forceinline__ float2 hh_begin(const StepArgs &a, int r, int64_t n, 
     a.iz_v[r] = V1;
     a.hh_g[r] = make_float4(m1, n1, h1, 0.0f);
     a.wc[r] = make_float2(0.0f, c1);
-    spiking_outputs(a, r, n, above, V1 >= a.iz_vpeak, c1, orig);
+    spiking_outputs<kPl>(a, r, n, above, V1 >= a.iz_vpeak, c1, orig, word_now);
     return rp;
 }
 
@@ -249,17 +262,19 @@ __device__ __forceinline__ float stimulus(const StepArgs &a, int r, int64_t n, i
     return U;
 }
 
-// The S-independent part of a spiking node's step (model kM = 1 or 2): stimulus
-// and everything but p; returns (r, p) at step n for psc_finish.
+// The S-independent part of a spiking node's step (model kM & 3 = 1 or 2, kM &
+// kPlastic with plastic weights, where word_now is the node's ring word of step n):
+// stimulus and everything but p; returns (r, p) at step n for psc_finish.
 template <int kM>
 __device__ __forceinline__ float2 spiking_begin(const StepArgs &a, int r, int64_t n, float2 wc, int32_t orig,
-                                                int32_t cnt0)
+                                                int32_t cnt0, uint32_t word_now = 0)
 {
+    constexpr bool kPl = (kM & kPlastic) != 0;
     const float U = stimulus(a, r, n, orig, cnt0);
-    if constexpr (kM == 1)
-        return izh_begin(a, r, n, wc, U, orig);
+    if constexpr ((kM & 3) == 1)
+        return izh_begin<kPl>(a, r, n, wc, U, orig, word_now);
     else
-        return hh_begin(a, r, n, wc, U, orig);
+        return hh_begin<kPl>(a, r, n, wc, U, orig, word_now);
 }
 
 // Stimulus, node model kM's Euler step (0 FitzHugh-Nagumo, 1 Izhikevich, 2

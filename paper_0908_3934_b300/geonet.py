@@ -47,6 +47,10 @@ class gn_hh_params(C.Structure):
                                           "psc_a", "tau_c")]
 
 
+class gn_stdp_params(C.Structure):
+    _fields_ = [("enable", C.c_int32), ("alpha", C.c_double), ("beta", C.c_double)]
+
+
 GN_MODEL_FHN, GN_MODEL_IZH, GN_MODEL_HH = 0, 1, 2
 _MODELS = {"fhn": GN_MODEL_FHN, "izh": GN_MODEL_IZH, "hh": GN_MODEL_HH}
 
@@ -60,7 +64,7 @@ class gn_net_desc(C.Structure):
         ("ring_depth", C.c_int32), ("obs_capacity", C.c_int64), ("event_capacity", C.c_int64),
         ("renumber", C.c_int32), ("edge_format", C.c_int32), ("step_kernel", C.c_int32),
         ("cuda_stream", C.c_void_p), ("device", C.c_int32),
-        ("model", C.c_int32), ("izh", gn_izh_params), ("hh", gn_hh_params),
+        ("model", C.c_int32), ("izh", gn_izh_params), ("hh", gn_hh_params), ("stdp", gn_stdp_params),
     ]
 
 
@@ -82,7 +86,7 @@ class gn_net_info(C.Structure):
         ("step_threads", C.c_int32), ("step_edges_per_thread", C.c_int32), ("grid", C.c_int32),
         ("step", C.c_int64), ("samples", C.c_int64),
         ("v_rest", C.c_double), ("w_rest", C.c_double), ("device_bytes", C.c_size_t),
-        ("step_gathers", C.c_int64), ("step_entries", C.c_int64),
+        ("step_gathers", C.c_int64), ("step_entries", C.c_int64), ("step_lane_slots", C.c_int64),
     ]
 
 
@@ -104,6 +108,10 @@ _SIGS = {
     "gn_get_izh_state": ([_P, _P, _P, _P], C.c_int),
     "gn_set_izh_state": ([_P, _P, _P, _P], C.c_int),
     "gn_get_hh_gates": ([_P, _P, _P, _P], C.c_int),
+    "gn_get_weights": ([_P, _P], C.c_int),
+    "gn_set_weights": ([_P, _P], C.c_int),
+    "gn_get_stdp_history": ([_P, _P, C.c_int32], C.c_int),
+    "gn_set_stdp_history": ([_P, _P, C.c_int32], C.c_int),
     "gn_set_hh_gates": ([_P, _P, _P, _P], C.c_int),
     "gn_get_arrivals": ([_P, _P], C.c_int),
     "gn_get_events": ([_P, _P, _P, C.c_int64, C.POINTER(C.c_int64)], C.c_int),
@@ -198,7 +206,8 @@ def make_desc(spec, keep: list, *, device: int = 0, stream=None, obs_capacity: i
         obs_capacity=obs_capacity, event_capacity=event_capacity, renumber=0 if renumber else -1,
         edge_format=1 if wide_edges else 0, step_kernel=step_kernel,
         cuda_stream=stream, device=device, model=_MODELS[getattr(spec, "model", "fhn")],
-        izh=_izh_params(getattr(spec, "izh", None)), hh=_hh_params(getattr(spec, "hh", None)))
+        izh=_izh_params(getattr(spec, "izh", None)), hh=_hh_params(getattr(spec, "hh", None)),
+        stdp=_stdp_params(getattr(spec, "stdp", None)))
 
 
 def _izh_params(iz) -> gn_izh_params:
@@ -206,6 +215,12 @@ def _izh_params(iz) -> gn_izh_params:
         return gn_izh_params()
     return gn_izh_params(C=iz["C"], k=iz["k"], v_r=iz["vr"], v_t=iz["vt"], v_peak=iz["vpeak"], v_reset=iz["vreset"],
                          a=iz["a"], b=iz["b"], d=iz["d"], i_ext=iz["i_ext"], psc_a=iz["psc_a"], tau_c=iz["tau_c"])
+
+
+def _stdp_params(sp) -> gn_stdp_params:
+    if not sp:
+        return gn_stdp_params()
+    return gn_stdp_params(enable=1, alpha=sp["alpha"], beta=sp["beta"])
 
 
 def _hh_params(hp) -> gn_hh_params:
@@ -328,6 +343,24 @@ class Net:
     def gn_set_hh_gates(self, m=None, n=None, h=None):
         m, n, h = _c(m, np.float32), _c(n, np.float32), _c(h, np.float32)
         check(lib().gn_set_hh_gates(self.h, _ptr(m), _ptr(n), _ptr(h)))
+
+    def gn_get_weights(self) -> np.ndarray:
+        out = np.zeros(self.n_edges, np.float32)
+        check(lib().gn_get_weights(self.h, _ptr(out)))
+        return out
+
+    def gn_set_weights(self, w):
+        w = np.ascontiguousarray(w, np.float32)
+        check(lib().gn_set_weights(self.h, _ptr(w)))
+
+    def gn_get_stdp_history(self, depth: int) -> np.ndarray:
+        out = np.zeros((depth, self.n_nodes), np.float32)
+        check(lib().gn_get_stdp_history(self.h, _ptr(out), depth))
+        return out
+
+    def gn_set_stdp_history(self, s_hist):
+        s_hist = np.ascontiguousarray(s_hist, np.float32)
+        check(lib().gn_set_stdp_history(self.h, _ptr(s_hist), s_hist.shape[0]))
 
     def gn_get_history(self, depth: int) -> np.ndarray:
         out = np.zeros((depth, self.n_nodes), np.float32)

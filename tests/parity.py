@@ -112,7 +112,8 @@ def ratio_scaled(gpu, ref):
 def windowed_izh(spec, net, n_steps, window=None, start=0):
     """windowed() for the spiking models (Izhikevich or Hodgkin-Huxley + alpha PSC):
     the oracle's full state (V, W, calcium, r, p, the Hodgkin-Huxley gates, spike
-    history, background counters) is loaded at every window start and the next
+    history, background counters; with plasticity the weights and the history of
+    s) is loaded at every window start and the next
     `window` steps of V, W, c, r, p, m, n, h, y (ratio_scaled) and the spikes are
     compared.  A node is left out of a window's comparison only if the oracle's V
     came within PEAK_MARGIN of V_peak in it (the spike decision is not defined to
@@ -131,6 +132,9 @@ def windowed_izh(spec, net, n_steps, window=None, start=0):
     worst = dict(v=0.0, w=0.0, c=0.0, r=0.0, p=0.0, y=0.0)
     if hh:
         worst.update(m=0.0, n=0.0, h=0.0)
+    plastic = getattr(spec, "stdp", None) is not None
+    if plastic:
+        worst.update(weight=0.0, s=0.0)
     n_spikes = excused = 0
     n0 = start
     end = start + n_steps
@@ -144,6 +148,11 @@ def windowed_izh(spec, net, n_steps, window=None, start=0):
         if hh:
             gates = dict(m=ref["m"], n=ref["n"], h=ref["h"])
             net.gn_set_hh_gates(**{k: x.astype(np.float32) for k, x in gates.items()})
+        if plastic:
+            w_now = np.asarray(spec.weight, np.float64) if ref["w_final"] is None else ref["w_final"]
+            net.gn_set_stdp_history(ref["hist_s"].astype(np.float32))
+            net.gn_set_weights(w_now.astype(np.float32))
+            gates.update(w_edge=w_now, s=ref["s"], hist_s=ref["hist_s"])
         nxt = oracle.simulate(spec, K, hist_depth=depth, ev_cap=spec.n_nodes * (K + 1) + 1024,
                               init=dict(n0=n0, v=ref["v"], w=ref["w"], c=ref["c"], r=ref["r"], p=ref["p"],
                                         bg_count=ref["bg_count"], hist=ref["hist"], **gates))
@@ -165,6 +174,10 @@ def windowed_izh(spec, net, n_steps, window=None, start=0):
         if hh:
             for k in ("m", "n", "h"):
                 worst[k] = max(worst[k], ratio_scaled(gg[k][ok], nxt[k][ok]))
+        if plastic:
+            ok_e = ok[src] & ok[dst]
+            worst["weight"] = max(worst["weight"], ratio_scaled(net.gn_get_weights()[ok_e], nxt["w_final"][ok_e]))
+            worst["s"] = max(worst["s"], ratio_scaled(net.gn_get_stdp_history(1)[0][ok], nxt["s"][ok]))
         if nxt["y"] is not None and nxt["y"].size:
             worst["y"] = max(worst["y"], ratio_scaled(y[:, ok], nxt["y"][:, ok]))
         assert np.array_equal(g["bg_count"], nxt["bg_count"]), "background counters differ"

@@ -37,6 +37,7 @@ def test_struct_layouts_match_the_header(L, tmp_path):
     """sizeof and offsetof of every ABI struct, from gcc on the header, equal the binding's."""
     structs = {"gn_fhn_params": geonet.gn_fhn_params, "gn_obs_params": geonet.gn_obs_params,
                "gn_izh_params": geonet.gn_izh_params, "gn_hh_params": geonet.gn_hh_params,
+               "gn_stdp_params": geonet.gn_stdp_params,
                "gn_net_desc": geonet.gn_net_desc, "gn_pulse": geonet.gn_pulse, "gn_net_info": geonet.gn_net_info,
                "gn_batch_info": geonet.gn_batch_info}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "geonet.h"', "int main(void) {"]
