@@ -337,15 +337,17 @@ def run_test_set(args, local, stream, model: str = "izh"):
     Izhikevich + alpha-PSC nodes at dt = 1 ms for `test_set_steps` steps (10 s of
     simulated time by default), or Hodgkin-Huxley + alpha-PSC nodes at dt = 0.03 ms
     for `test_set_hh_steps` steps (1 s); real-time factor = simulated time / device
-    time (CUDA events), one network after another, each from its own graph."""
+    time (CUDA events), one network after another, each from its own graph; then
+    all 80 advanced together by the batched form (every network then runs at the
+    batch's real-time factor)."""
     import statistics as st
     import torch
     from paper_0908_3934_b300 import geonet
     hh = model == "hh"
     steps = args.test_set_hh_steps if hh else args.test_set_steps
     rows = []
-    for sp in netgen.test_set():
-        ispec = netgen.test_set_hh(sp) if hh else netgen.test_set_izh(sp)
+    ispecs = [netgen.test_set_hh(sp) if hh else netgen.test_set_izh(sp) for sp in netgen.test_set()]
+    for ispec in ispecs:
         net = geonet.Net(ispec, device=local, stream=stream.cuda_stream, obs_capacity=64)
         net.gn_step(128)
         net.gn_synchronize()
@@ -356,7 +358,19 @@ def run_test_set(args, local, stream, model: str = "izh"):
         torch.cuda.synchronize()
         t = ev0.elapsed_time(ev1) / 1e3
         net.gn_net_destroy()
-        rows.append((sp.name, sp.n_nodes, sp.n_edges, steps * ispec.dt_ms * 1e-3 / t))
+        rows.append((ispec.name, ispec.n_nodes, ispec.n_edges, steps * ispec.dt_ms * 1e-3 / t, t))
+    # the same 80 networks advanced together by the batched form
+    b = geonet.Batch(ispecs, device=local, stream=stream.cuda_stream, obs_capacity=64)
+    b.gn_batch_step(128)
+    b.gn_batch_synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    b.gn_batch_step(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = ev0.elapsed_time(ev1) / 1e3
+    b.gn_batch_destroy()
+    dt = ispecs[0].dt_ms
     rtf = [r[3] for r in rows]
     by_class = {}
     for cls in netgen.TEST_SET_CLASSES:
@@ -369,6 +383,10 @@ def run_test_set(args, local, stream, model: str = "izh"):
             "rtf_min": min(rtf), "rtf_median": st.median(rtf), "rtf_max": max(rtf),
             "rtf_n1000_by_class": by_class,
             "largest": max(rows, key=lambda r: r[2])[0],
+            "batched": {"rtf_every_network": steps * dt * 1e-3 / t_batch,
+                        "network_seconds_per_second": len(ispecs) * steps * dt * 1e-3 / t_batch,
+                        "speedup_vs_one_after_another": sum(r[4] for r in rows) / t_batch,
+                        "gpu_launches": steps + steps // 64},
             "networks": [{"name": r[0], "N": r[1], "E": r[2], "rtf": round(r[3], 1)} for r in rows]}
 
 

@@ -313,6 +313,8 @@ GN_API gn_status gn_load_state(gn_net *net, const void *buf, size_t size);
 /* ---------------------------------------------------------------------------
  * Batched form: many independent networks (of any sizes) advanced together by
  * one persistent launch per gn_batch_step, replayed from a captured CUDA graph.
+ * Every network of a batch uses one node model; spiking batches run the staged
+ * form only, and plastic weights are not taken (GN_EINVAL).
  * CTAs take networks from a work queue ordered largest first and run all the
  * requested steps of a network before taking the next; the CTA size is chosen by
  * timing the candidates on the first gn_batch_step.  Every network follows the
@@ -362,6 +364,8 @@ GN_API gn_status gn_batch_observe(gn_batch *batch, int32_t net, float *out, int6
 GN_API gn_status gn_batch_get_state(gn_batch *batch, int32_t net, float *v, float *w, float *c, int32_t *bg_count,
                                     int64_t *step);
 GN_API gn_status gn_batch_get_history(gn_batch *batch, int32_t net, float *out, int32_t depth);
+GN_API gn_status gn_batch_get_izh_state(gn_batch *batch, int32_t net, float *V, float *r, float *p);
+GN_API gn_status gn_batch_get_hh_gates(gn_batch *batch, int32_t net, float *m, float *n, float *h);
 GN_API gn_status gn_batch_get_arrivals(gn_batch *batch, int32_t net, int64_t *first_arrival);
 GN_API gn_status gn_batch_get_events(gn_batch *batch, int32_t net, int32_t *node, int64_t *step, int64_t cap,
                                      int64_t *n_total);

@@ -88,6 +88,11 @@ struct gn_batch {
     DevArray<float> st_w;
     DevArray<uint16_t> st_u, st_plist;
     DevArray<int32_t> st_rq, st_tile_net;
+    // node model shared by every member; spiking members' V, (r, p), gates
+    int32_t model = GN_MODEL_FHN;
+    DevArray<float> iz_v;
+    DevArray<float2> rp;
+    DevArray<float4> hh_g;
 
     ~gn_batch()
     {
@@ -110,6 +115,9 @@ struct gn_batch {
         st_plist.release();
         st_rq.release();
         st_tile_net.release();
+        iz_v.release();
+        rp.release();
+        hh_g.release();
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 };
@@ -153,7 +161,7 @@ void upload_args(gn_batch *b, int shape)
 void set_shape(gn_batch *b, int shape)
 {
     if (shape == kStaged) {
-        cuda_check(gn::batch_staged_prepare(b->st_packed, b->st_stream, b->st_smem), "staged kernel setup");
+        cuda_check(gn::batch_staged_prepare(b->model, b->st_packed, b->st_stream, b->st_smem), "staged kernel setup");
         b->shape = kStaged;
         b->grid = b->n_tiles;
         upload_args(b, 0);
@@ -181,8 +189,8 @@ void launch_steps(gn_batch *b, const gn::StepArgs *args, int64_t *d_step, int n_
 {
     if (shape == kStaged) {
         for (int k = 0; k < n_steps; ++k)
-            cuda_check(gn::launch_batch_staged(args, b->st_tile_net.p, b->n_tiles, k, b->st_packed, b->st_stream,
-                                               b->st_smem, s),
+            cuda_check(gn::launch_batch_staged(b->model, args, b->st_tile_net.p, b->n_tiles, k, b->st_packed,
+                                               b->st_stream, b->st_smem, s),
                        "staged batch launch");
         return;
     }
@@ -252,7 +260,7 @@ void autotune(gn_batch *b, bool persistent, bool staged)
             cuda_check(cudaMemcpy(dargs.p, a.data(), a.size() * sizeof(gn::StepArgs), cudaMemcpyHostToDevice), "H2D");
             int grid = b->n_tiles;
             if (shape == kStaged) {
-                cuda_check(gn::batch_staged_prepare(b->st_packed, b->st_stream, b->st_smem), "staged kernel setup");
+                cuda_check(gn::batch_staged_prepare(b->model, b->st_packed, b->st_stream, b->st_smem), "staged kernel setup");
             } else {
                 int per_sm = 0, sms = 0;
                 cuda_check(gn::batch_occupancy(shape, &per_sm), "occupancy");
@@ -292,8 +300,8 @@ void build_graph(gn_batch *b, int64_t n_steps)
     if (e == cudaSuccess) {
         if (b->shape == kStaged) {
             for (int k = 0; k < n_steps && e == cudaSuccess; ++k)
-                e = gn::launch_batch_staged(b->d_args.p, b->st_tile_net.p, b->n_tiles, k, b->st_packed, b->st_stream,
-                                            b->st_smem, cs);
+                e = gn::launch_batch_staged(b->model, b->d_args.p, b->st_tile_net.p, b->n_tiles, k, b->st_packed,
+                                            b->st_stream, b->st_smem, cs);
         } else {
             e = cudaMemsetAsync(b->queue.p, 0, 4, cs);
             if (e == cudaSuccess)
@@ -416,11 +424,13 @@ gn_status gn_batch_create(const gn_net_desc *descs, int32_t n_nets, gn_batch **o
         for (int i = 0; i < n_nets; ++i) {
             gnrt::validate_desc(descs + i);
             if (descs[i].device != descs[0].device) fail(GN_EINVAL, "all networks of a batch share one device");
-            if (descs[i].model != GN_MODEL_FHN) fail(GN_EINVAL, "the batched form takes FitzHugh-Nagumo networks only");
+            if (descs[i].model != descs[0].model) fail(GN_EINVAL, "every network of a batch uses one node model");
+            if (descs[i].stdp.enable) fail(GN_EINVAL, "the batched form does not take plastic weights");
         }
         b = new gn_batch();
         b->device = descs[0].device;
         b->n_nets = n_nets;
+        b->model = descs[0].model;
         DeviceGuard dg(b->device);
         if (descs[0].cuda_stream) {
             b->stream = static_cast<cudaStream_t>(descs[0].cuda_stream);
@@ -514,6 +524,24 @@ gn_status gn_batch_create(const gn_net_desc *descs, int32_t n_nets, gn_batch **o
         }
         for (int s = 0; s < gn::kNumBatchShapes; ++s) b->bdesc[s].upload(shape_desc[s], &b->bytes);
         std::vector<int64_t> rq_off = build_staged_pool(b, hs);
+        if (b->model != GN_MODEL_FHN) {
+            // spiking members run the staged form only; they start at their rest state
+            if (!b->staged_ok) fail(GN_EINVAL, "the staged batch kernel cannot hold this batch of spiking networks");
+            std::vector<float> v0(nodes);
+            for (int i = 0; i < n_nets; ++i)
+                std::fill(v0.begin() + b->m[i].node_off, v0.begin() + b->m[i].node_off + b->m[i].N,
+                          static_cast<float>(hs[i].v_rest));
+            b->iz_v.upload(v0, &b->bytes);
+            b->rp.alloc(nodes, &b->bytes);
+            cuda_check(cudaMemset(b->rp.p, 0, b->rp.n * 8), "memset");
+            if (b->model == GN_MODEL_HH) {
+                double gm, gn_, gh;
+                gnrt::hh_rest_gates(&gm, &gn_, &gh);
+                b->hh_g.upload(std::vector<float4>(nodes, make_float4(static_cast<float>(gm), static_cast<float>(gn_),
+                                                                      static_cast<float>(gh), 0.0f)),
+                               &b->bytes);
+            }
+        }
         hs.clear();
         b->ring.alloc(ring, &b->bytes);
         b->wc.alloc(nodes + 2 * static_cast<int64_t>(n_nets), &b->bytes);
@@ -563,6 +591,11 @@ gn_status gn_batch_create(const gn_net_desc *descs, int32_t n_nets, gn_batch **o
             a.ev_cap = mm.ev_cap;
             a.d_step = b->d_step.p;
             a.status = b->status.p;
+            if (b->model != GN_MODEL_FHN) {
+                a.iz_v = b->iz_v.p + mm.node_off;
+                a.rp = b->rp.p + mm.node_off;
+                a.hh_g = b->model == GN_MODEL_HH ? b->hh_g.p + mm.node_off : nullptr;
+            }
             if (b->staged_ok) {
                 a.st_tile = b->st_tile.p;
                 a.st_tile2 = b->st_tile2.p;
@@ -730,7 +763,12 @@ gn_status gn_batch_step(gn_batch *b, int64_t n_steps)
             const int only = e && *e ? atoi(e) : 0;
             if (only != 0 && only != 1 && only != 3) fail(GN_EINVAL, "GN_BATCH_KERNEL must be 1 or 3");
             if (only == 3 && !b->staged_ok) fail(GN_EINVAL, "the staged batch kernel cannot hold this batch");
-            autotune(b, only != 3, only != 1);
+            if (b->model != GN_MODEL_FHN) {
+                if (only == 1) fail(GN_EINVAL, "spiking batches run the staged batch kernel");
+                set_shape(b, kStaged);
+            } else {
+                autotune(b, only != 3, only != 1);
+            }
         }
         if (b->shape == kStaged) {
             if (!b->graph) build_graph(b, kGraphSteps);
@@ -754,6 +792,8 @@ gn_status gn_batch_step_static(gn_batch *b, int64_t n_steps)
     return guarded([&] {
         check_batch(b);
         if (n_steps < 0 || n_steps > 2147483647LL) fail(GN_EINVAL, "n_steps out of range");
+        if (b->model != GN_MODEL_FHN)
+            fail(GN_EINVAL, "the allocation-free step takes FitzHugh-Nagumo batches (the persistent kernel)");
         if (b->n_nets > gn::kStaticQueueNets)
             fail(GN_ERANGE, "a batch of %d networks exceeds the %d networks the static work queue holds", b->n_nets,
                  gn::kStaticQueueNets);
@@ -862,9 +902,9 @@ gn_status gn_batch_get_state(gn_batch *b, int32_t net, float *v, float *w, float
         const Member &mm = b->m[net];
         std::vector<float> t(mm.N);
         if (v) {
-            cuda_check(cudaMemcpy(t.data(), b->ring.p + mm.ring_off + (b->step & (mm.R - 1)) * mm.stride, mm.N * 4,
-                                  cudaMemcpyDeviceToHost),
-                       "D2H v");
+            const float *src = b->model != GN_MODEL_FHN ? b->iz_v.p + mm.node_off
+                                                        : b->ring.p + mm.ring_off + (b->step & (mm.R - 1)) * mm.stride;
+            cuda_check(cudaMemcpy(t.data(), src, mm.N * 4, cudaMemcpyDeviceToHost), "D2H v");
             to_caller(mm, t.data(), v);
         }
         if (w || c) {
@@ -881,6 +921,48 @@ gn_status gn_batch_get_state(gn_batch *b, int32_t net, float *v, float *w, float
             to_caller(mm, t3.data(), bg_count);
         }
         if (step) *step = b->step;
+    });
+}
+
+gn_status gn_batch_get_izh_state(gn_batch *b, int32_t net, float *V, float *r, float *p)
+{
+    return guarded([&] {
+        check_batch(b, net);
+        if (b->model == GN_MODEL_FHN) fail(GN_EINVAL, "the batch does not use a spiking node model");
+        DeviceGuard dg(b->device);
+        sync(b);
+        const Member &mm = b->m[net];
+        if (V) {
+            std::vector<float> t(mm.N);
+            cuda_check(cudaMemcpy(t.data(), b->iz_v.p + mm.node_off, mm.N * 4, cudaMemcpyDeviceToHost), "D2H V");
+            to_caller(mm, t.data(), V);
+        }
+        if (r || p) {
+            std::vector<float2> t(mm.N);
+            cuda_check(cudaMemcpy(t.data(), b->rp.p + mm.node_off, mm.N * 8, cudaMemcpyDeviceToHost), "D2H rp");
+            for (int32_t i = 0; i < mm.N; ++i) {
+                if (r) r[mm.perm[i]] = t[i].x;
+                if (p) p[mm.perm[i]] = t[i].y;
+            }
+        }
+    });
+}
+
+gn_status gn_batch_get_hh_gates(gn_batch *b, int32_t net, float *m, float *n, float *h)
+{
+    return guarded([&] {
+        check_batch(b, net);
+        if (b->model != GN_MODEL_HH) fail(GN_EINVAL, "the batch does not use the Hodgkin-Huxley model");
+        DeviceGuard dg(b->device);
+        sync(b);
+        const Member &mm = b->m[net];
+        std::vector<float4> t(mm.N);
+        cuda_check(cudaMemcpy(t.data(), b->hh_g.p + mm.node_off, mm.N * 16ull, cudaMemcpyDeviceToHost), "D2H gates");
+        for (int32_t i = 0; i < mm.N; ++i) {
+            if (m) m[mm.perm[i]] = t[i].x;
+            if (n) n[mm.perm[i]] = t[i].y;
+            if (h) h[mm.perm[i]] = t[i].z;
+        }
     });
 }
 

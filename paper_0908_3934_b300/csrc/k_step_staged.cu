@@ -250,10 +250,10 @@ __global__ void __launch_bounds__(T, (kSE ? kThreadsSE : (kM & kPlastic) ? kThre
     staged_tile<kM, T, kSE, kPacked, kStream>(a, blockIdx.x, k);
 }
 
-// Batched form, one launch per step over the tiles of every member network: the
-// CTA copies its network's arguments into shared memory, then runs the same tile
-// step (tiles never straddle networks).
-template <int T, bool kPacked, bool kStream>
+// Batched form, one launch per step over the tiles of every member network (all of
+// node model kM): the CTA copies its network's arguments into shared memory, then
+// runs the same tile step (tiles never straddle networks).
+template <int kM, int T, bool kPacked, bool kStream>
 __global__ void __launch_bounds__(T, kThreadsL2 / T) k_batch_staged(const StepArgs *__restrict__ nets,
                                                                     const int *__restrict__ tile_net, const int k)
 {
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(T, kThreadsL2 / T) k_batch_staged(const StepAr
     uint32_t *dst = reinterpret_cast<uint32_t *>(&s_a);
     for (int i = threadIdx.x; i < static_cast<int>(sizeof(StepArgs) / 4); i += T) dst[i] = __ldg(src + i);
     __syncthreads();
-    staged_tile<0, T, false, kPacked, kStream>(s_a, blockIdx.x, k);  // FitzHugh-Nagumo members only
+    staged_tile<kM, T, false, kPacked, kStream>(s_a, blockIdx.x, k);
 }
 
 template <int kM, int T, bool kSE, bool kPacked, bool kStream>
@@ -347,14 +347,14 @@ cudaError_t step_staged_prepare(const StagedShape &shape, int model, bool plasti
 
 namespace {
 
-template <bool kPacked, bool kStream>
+template <int kM, bool kPacked, bool kStream>
 cudaError_t batch_staged_t(bool launch, const StepArgs *nets, const int *tile_net, int n_tiles, int k, size_t smem,
                            cudaStream_t s)
 {
     constexpr int T = kBatchStagedShape.threads;
     if (!launch)
-        return cudaFuncSetAttribute(k_batch_staged<T, kPacked, kStream>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(smem));
+        return cudaFuncSetAttribute(k_batch_staged<kM, T, kPacked, kStream>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(static_cast<unsigned>(n_tiles));
     cfg.blockDim = dim3(T);
@@ -365,31 +365,34 @@ cudaError_t batch_staged_t(bool launch, const StepArgs *nets, const int *tile_ne
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_batch_staged<T, kPacked, kStream>, nets, tile_net, k);
+    return cudaLaunchKernelEx(&cfg, k_batch_staged<kM, T, kPacked, kStream>, nets, tile_net, k);
 }
 
-cudaError_t batch_staged(bool launch, const StepArgs *nets, const int *tile_net, int n_tiles, int k, bool packed,
-                         bool stream_edges, size_t smem, cudaStream_t s)
+cudaError_t batch_staged(bool launch, int model, const StepArgs *nets, const int *tile_net, int n_tiles, int k,
+                         bool packed, bool stream_edges, size_t smem, cudaStream_t s)
 {
-    if (packed)
-        return stream_edges ? batch_staged_t<true, true>(launch, nets, tile_net, n_tiles, k, smem, s)
-                            : batch_staged_t<true, false>(launch, nets, tile_net, n_tiles, k, smem, s);
-    return stream_edges ? batch_staged_t<false, true>(launch, nets, tile_net, n_tiles, k, smem, s)
-                        : batch_staged_t<false, false>(launch, nets, tile_net, n_tiles, k, smem, s);
+    return with_model(model, [&](auto m) {
+        constexpr int M = decltype(m)::value;
+        if (packed)
+            return stream_edges ? batch_staged_t<M, true, true>(launch, nets, tile_net, n_tiles, k, smem, s)
+                                : batch_staged_t<M, true, false>(launch, nets, tile_net, n_tiles, k, smem, s);
+        return stream_edges ? batch_staged_t<M, false, true>(launch, nets, tile_net, n_tiles, k, smem, s)
+                            : batch_staged_t<M, false, false>(launch, nets, tile_net, n_tiles, k, smem, s);
+    });
 }
 
 }  // namespace
 
-cudaError_t launch_batch_staged(const StepArgs *nets, const int *tile_net, int n_tiles, int k, bool packed,
+cudaError_t launch_batch_staged(int model, const StepArgs *nets, const int *tile_net, int n_tiles, int k, bool packed,
                                 bool stream_edges, size_t smem_bytes, cudaStream_t s)
 {
     if (n_tiles <= 0) return cudaSuccess;
-    return batch_staged(true, nets, tile_net, n_tiles, k, packed, stream_edges, smem_bytes, s);
+    return batch_staged(true, model, nets, tile_net, n_tiles, k, packed, stream_edges, smem_bytes, s);
 }
 
-cudaError_t batch_staged_prepare(bool packed, bool stream_edges, size_t smem_bytes)
+cudaError_t batch_staged_prepare(int model, bool packed, bool stream_edges, size_t smem_bytes)
 {
-    return batch_staged(false, nullptr, nullptr, 0, 0, packed, stream_edges, smem_bytes, nullptr);
+    return batch_staged(false, model, nullptr, nullptr, 0, 0, packed, stream_edges, smem_bytes, nullptr);
 }
 
 }  // namespace gn

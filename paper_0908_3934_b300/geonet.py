@@ -131,6 +131,8 @@ _SIGS = {
     "gn_batch_observe": ([_P, C.c_int32, _P, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int64)], C.c_int),
     "gn_batch_get_state": ([_P, C.c_int32, _P, _P, _P, _P, C.POINTER(C.c_int64)], C.c_int),
     "gn_batch_get_history": ([_P, C.c_int32, _P, C.c_int32], C.c_int),
+    "gn_batch_get_izh_state": ([_P, C.c_int32, _P, _P, _P], C.c_int),
+    "gn_batch_get_hh_gates": ([_P, C.c_int32, _P, _P, _P], C.c_int),
     "gn_batch_get_arrivals": ([_P, C.c_int32, _P], C.c_int),
     "gn_batch_get_events": ([_P, C.c_int32, _P, _P, C.c_int64, C.POINTER(C.c_int64)], C.c_int),
     "gn_batch_set_step": ([_P, C.c_int64], C.c_int),
@@ -480,6 +482,18 @@ class Batch:
         out = np.zeros((depth, self.specs[net].n_nodes), np.float32)
         check(lib().gn_batch_get_history(self.h, net, _ptr(out), depth))
         return out
+
+    def gn_batch_get_izh_state(self, net: int):
+        N = self.specs[net].n_nodes
+        V, r, p = (np.zeros(N, np.float32) for _ in range(3))
+        check(lib().gn_batch_get_izh_state(self.h, net, _ptr(V), _ptr(r), _ptr(p)))
+        return dict(V=V, r=r, p=p)
+
+    def gn_batch_get_hh_gates(self, net: int):
+        N = self.specs[net].n_nodes
+        m, n, h = (np.zeros(N, np.float32) for _ in range(3))
+        check(lib().gn_batch_get_hh_gates(self.h, net, _ptr(m), _ptr(n), _ptr(h)))
+        return dict(m=m, n=n, h=h)
 
     def gn_batch_get_arrivals(self, net: int) -> np.ndarray:
         out = np.zeros(self.specs[net].n_nodes, np.int64)

@@ -1,0 +1,70 @@
+"""The batched form with spiking nodes (Izhikevich, Hodgkin-Huxley): networks of
+the standard test set (Sec. 3.5) advanced together by the staged batch kernel give,
+member by member, the bit-identical states of the same networks run alone."""
+import numpy as np
+import pytest
+
+from paper_0908_3934_b300 import geonet, netgen
+
+pytestmark = pytest.mark.gpu
+
+
+def _members(model):
+    nets = [netgen.test_set_net(n, dim, cls, dens, seed=11 + i)
+            for i, (n, dim, cls, dens) in enumerate([(10, 2, "lattice", "low"), (30, 3, "small_world", "high"),
+                                                    (100, 2, "scale_free", "high"), (300, 3, "random", "low"),
+                                                    (1000, 2, "random", "high"), (300, 2, "lattice", "high")])]
+    return [netgen.test_set_hh(sp) if model == "hh" else netgen.test_set_izh(sp) for sp in nets]
+
+
+@pytest.mark.parametrize("model", ["izh", "hh"])
+def test_members_equal_their_networks_run_alone(model):
+    specs = _members(model)
+    steps = 700 if model == "izh" else 1500
+    b = geonet.Batch(specs)
+    b.gn_batch_step(steps)
+    assert b.gn_batch_get_info()["step_kernel"] == 3
+    n_spikes = 0
+    for i, sp in enumerate(specs):
+        net = geonet.Net(sp)
+        net.gn_step(steps)
+        st, bst = net.gn_get_state(), b.gn_batch_get_state(i)
+        for k in ("v", "w", "c", "bg_count"):
+            assert np.array_equal(st[k], bst[k]), (i, k)
+        iz, biz = net.gn_get_izh_state(), b.gn_batch_get_izh_state(i)
+        for k in ("V", "r", "p"):
+            assert np.array_equal(iz[k], biz[k]), (i, k)
+        if model == "hh":
+            g, bg = net.gn_get_hh_gates(), b.gn_batch_get_hh_gates(i)
+            for k in ("m", "n", "h"):
+                assert np.array_equal(g[k], bg[k]), (i, k)
+        assert np.array_equal(net.gn_get_history(4), b.gn_batch_get_history(i, 4))
+        ev, bev = net.gn_get_events(), b.gn_batch_get_events(i)
+        if bev[2] != geonet.GN_EOVERFLOW:  # a member's event buffer holds max(1024, 8 N) events
+            assert np.array_equal(ev[0], bev[0]) and np.array_equal(ev[1], bev[1])
+            n_spikes += len(ev[0])
+        assert np.array_equal(net.gn_get_arrivals(), b.gn_batch_get_arrivals(i))
+    assert n_spikes > 100
+
+
+def test_spiking_batches_are_checked(monkeypatch):
+    izh = _members("izh")[:2]
+    hh = _members("hh")[:1]
+    with pytest.raises(geonet.GeonetError) as e:
+        geonet.Batch(izh + hh)
+    assert e.value.status == geonet.GN_EINVAL
+    plastic = netgen.dataclasses.replace(izh[0], stdp=dict(alpha=1.0, beta=0.1))
+    with pytest.raises(geonet.GeonetError) as e:
+        geonet.Batch([plastic])
+    assert e.value.status == geonet.GN_EINVAL
+    b = geonet.Batch(izh)
+    with pytest.raises(geonet.GeonetError) as e:
+        b.gn_batch_step_static(10)
+    assert e.value.status == geonet.GN_EINVAL
+    with pytest.raises(geonet.GeonetError) as e:
+        b.gn_batch_get_hh_gates(0)
+    assert e.value.status == geonet.GN_EINVAL
+    monkeypatch.setenv("GN_BATCH_KERNEL", "1")
+    with pytest.raises(geonet.GeonetError) as e:
+        geonet.Batch(izh).gn_batch_step(10)
+    assert e.value.status == geonet.GN_EINVAL
