@@ -61,6 +61,7 @@ class _Net(C.Structure):
         ("hh_ena", C.c_double), ("hh_ek", C.c_double), ("hh_el", C.c_double), ("hh_vpeak", C.c_double),
         ("hh_iext", C.c_double),
         ("stdp", C.c_int32), ("stdp_alpha", C.c_double), ("stdp_beta", C.c_double),
+        ("frame_average", C.c_int32),
     ]
 
 
@@ -258,6 +259,7 @@ def simulate(spec, n_steps: int, *, dense: bool = False, snap_every: int = 0,
         **({f"hh_{k}": hp[k] for k in ("C", "gna", "gk", "gl", "ena", "ek", "el", "vpeak")} if hh else {}),
         hh_iext=hp.get("i_ext", 0.0),
         stdp=1 if stdp else 0, stdp_alpha=stdp["alpha"] if stdp else 0.0, stdp_beta=stdp["beta"] if stdp else 0.0,
+        frame_average=1 if obs.get("frame_average") else 0,
     )
     v = np.zeros(N)
     w = np.zeros(N)

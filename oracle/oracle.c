@@ -35,6 +35,10 @@
  *   - Readout c: forward Euler of dc/dt = (v - c)/tau (the calcium model's Euler form
  *     with the voltage in place of the spike train), sampled every `sample_every` steps;
  *     y = gain (V* + c~) + offset + sigma xi.
+ *   - Camera frame averaging (frame_average = 1; Sec. 3.3 notes that a camera slower
+ *     than the step averages the calcium values of a frame): a sample reads the mean
+ *     of c over the sample_every steps of its frame, the values after each step.  A
+ *     run starts a new frame.
  *   - Events: upward crossing of V through theta (V(n) < theta <= V(n+1)).
  *   - Arrival: first step at which v~ becomes non-zero.
  *
@@ -258,6 +262,9 @@ typedef struct {
     /* spike-time-dependent plasticity of every weight (spiking models only) */
     int32_t stdp;
     double stdp_alpha, stdp_beta;
+    /* camera frame averaging: a sample reads the mean of the readout state over the
+     * sample_every steps of its frame instead of its last value */
+    int32_t frame_average;
 } orc_net;
 
 typedef struct {
@@ -477,6 +484,13 @@ static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense
     if (stdp)
         for (int64_t e = 0; e < E; ++e) wcur[e] = (init && init->w_edge) ? init->w_edge[e] : net->weight[e];
     const double *wgt = stdp ? wcur : net->weight;
+    /* frame sums of the readout state (a run starts a new frame) */
+    double *facc = (double *)calloc((size_t)N, sizeof(double));
+    if (!facc) {
+        free(h.buf); free(v); free(w); free(c); free(S); free(bgc); free(r); free(p); free(gm); free(gn); free(gh);
+        free(hs.buf); free(sj); free(wcur);
+        return ORC_ENOMEM;
+    }
     if (izh)
         for (int32_t j = 0; j < N; ++j) v[j] = net->iz_vr;
     if (hh) {
@@ -583,8 +597,11 @@ static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense
                     out->first_arrival[j] = (int32_t)(n + 1);
                     if (out->first_value) out->first_value[j] = v1;
                 }
+                facc[j] += c1;
                 if (sample) {
-                    double clean = net->gain * c1 + net->offset;
+                    double cbar = net->frame_average ? facc[j] / net->sample_every : c1;
+                    facc[j] = 0.0;
+                    double clean = net->gain * cbar + net->offset;
                     if (out->y_clean) out->y_clean[k_out * N + j] = clean;
                     if (out->y) out->y[k_out * N + j] = clean + net->sigma * orc_gauss(net->obs_seed, (uint32_t)j, k);
                 }
@@ -604,8 +621,11 @@ static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense
                 out->first_arrival[j] = (int32_t)(n + 1);
                 if (out->first_value) out->first_value[j] = v1;
             }
+            facc[j] += c1;
             if (sample) {
-                double clean = net->gain * (v_rest + c1) + net->offset;
+                double cbar = net->frame_average ? facc[j] / net->sample_every : c1;
+                facc[j] = 0.0;
+                double clean = net->gain * (v_rest + cbar) + net->offset;
                 if (out->y_clean) out->y_clean[k_out * N + j] = clean;
                 if (out->y) out->y[k_out * N + j] = clean + net->sigma * orc_gauss(net->obs_seed, (uint32_t)j, k);
             }
@@ -649,7 +669,7 @@ static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense
         }
     }
     free(h.buf); free(v); free(w); free(c); free(S); free(bgc); free(r); free(p); free(gm); free(gn); free(gh);
-    free(hs.buf); free(sj); free(wcur);
+    free(hs.buf); free(sj); free(wcur); free(facc);
     return ORC_OK;
 }
 
