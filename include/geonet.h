@@ -121,12 +121,16 @@ typedef struct {
 
 /* Readout (Sec. 3.3): c~' = c~ + (dt/tau_ms)(v~' - c~) every step; every
  * sample_every steps y = gain (V* + c~) + offset + sigma xi, xi ~ N(0, 1) drawn
- * from Philox4x32-10 keyed by `seed` with counter (node, sample, 2). */
+ * from Philox4x32-10 keyed by `seed` with counter (node, sample, 2).  With
+ * frame_average != 0 a camera slower than the step is modelled: a sample reads the
+ * mean of c~ over the sample_every steps of its frame (the values after each step)
+ * instead of the last one; gn_set_state and gn_load_state start a new frame. */
 typedef struct {
     double tau_ms;
     int32_t sample_every;
     float gain, offset, sigma;
     uint64_t seed;
+    int32_t frame_average;
 } gn_obs_params;
 
 /* A network.  pos [n_nodes*dim] (mm, row-major); edges src[e] -> dst[e] with

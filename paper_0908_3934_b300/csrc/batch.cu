@@ -93,6 +93,7 @@ struct gn_batch {
     DevArray<float> iz_v;
     DevArray<float2> rp;
     DevArray<float4> hh_g;
+    DevArray<float> obs_acc;  // frame sums of the readout state (members with frame averaging)
 
     ~gn_batch()
     {
@@ -118,6 +119,7 @@ struct gn_batch {
         iz_v.release();
         rp.release();
         hh_g.release();
+        obs_acc.release();
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 };
@@ -204,7 +206,7 @@ void launch_steps(gn_batch *b, const gn::StepArgs *args, int64_t *d_step, int n_
 void autotune(gn_batch *b, bool persistent, bool staged)
 {
     size_t tmp = 0;
-    DevArray<float> ring, obs;
+    DevArray<float> ring, obs, facc;
     DevArray<float2> wc;
     DevArray<int32_t> bgc, evn;
     DevArray<int64_t> first, evs, dstep;
@@ -213,7 +215,7 @@ void autotune(gn_batch *b, bool persistent, bool staged)
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     auto cleanup = [&] {
         ring.release(); obs.release(); wc.release(); bgc.release(); evn.release(); first.release();
-        evs.release(); dstep.release(); evc.release(); dargs.release();
+        evs.release(); dstep.release(); evc.release(); dargs.release(); facc.release();
         if (t0) cudaEventDestroy(t0);
         if (t1) cudaEventDestroy(t1);
     };
@@ -231,6 +233,10 @@ void autotune(gn_batch *b, bool persistent, bool staged)
         evc.alloc(b->n_nets, &tmp);
         dstep.alloc(1, &tmp);
         dargs.alloc(b->n_nets, &tmp);
+        if (b->obs_acc.p) {
+            facc.alloc(total_nodes, &tmp);
+            cuda_check(cudaMemset(facc.p, 0, facc.n * 4), "memset");
+        }
         cuda_check(cudaMemset(ring.p, 0, ring.n * 4), "memset");
         cuda_check(cudaMemset(wc.p, 0, wc.n * 8), "memset");
         cuda_check(cudaMemset(bgc.p, 0, bgc.n * 4), "memset");
@@ -256,6 +262,7 @@ void autotune(gn_batch *b, bool persistent, bool staged)
                 a[i].ev_step = evs.p + i;
                 a[i].ev_count = evc.p + i;
                 a[i].ev_cap = 1;
+                if (a[i].obs_acc) a[i].obs_acc = facc.p + mm.node_off;
             }
             cuda_check(cudaMemcpy(dargs.p, a.data(), a.size() * sizeof(gn::StepArgs), cudaMemcpyHostToDevice), "H2D");
             int grid = b->n_tiles;
@@ -543,6 +550,12 @@ gn_status gn_batch_create(const gn_net_desc *descs, int32_t n_nets, gn_batch **o
             }
         }
         hs.clear();
+        bool any_frames = false;
+        for (int i = 0; i < n_nets; ++i) any_frames = any_frames || descs[i].obs.frame_average;
+        if (any_frames) {
+            b->obs_acc.alloc(nodes, &b->bytes);
+            cuda_check(cudaMemset(b->obs_acc.p, 0, b->obs_acc.n * 4), "memset");
+        }
         b->ring.alloc(ring, &b->bytes);
         b->wc.alloc(nodes + 2 * static_cast<int64_t>(n_nets), &b->bytes);
         b->bgc.alloc(nodes, &b->bytes);
@@ -591,6 +604,7 @@ gn_status gn_batch_create(const gn_net_desc *descs, int32_t n_nets, gn_batch **o
             a.ev_cap = mm.ev_cap;
             a.d_step = b->d_step.p;
             a.status = b->status.p;
+            a.obs_acc = a.frame_avg ? b->obs_acc.p + mm.node_off : nullptr;
             if (b->model != GN_MODEL_FHN) {
                 a.iz_v = b->iz_v.p + mm.node_off;
                 a.rp = b->rp.p + mm.node_off;
@@ -1006,6 +1020,7 @@ gn_status gn_batch_set_state(gn_batch *b, int32_t net, const float *hist, int32_
         cuda_check(cudaMemcpy(b->bgc.p + mm.node_off, bg.data(), N * 4ull, cudaMemcpyHostToDevice), "H2D");
         cuda_check(cudaMemset(b->first.p + mm.node_off, 0xff, N * 8ull), "memset");
         cuda_check(cudaMemset(b->ev_count.p + net, 0, 8), "memset");
+        if (b->args[net].obs_acc) cuda_check(cudaMemset(b->args[net].obs_acc, 0, N * 4ull), "memset");  // a new frame
     });
 }
 

@@ -50,6 +50,8 @@ struct StepArgs {
     float theta_s;           // event threshold relative to rest, theta - V*
     float gain, offset, sigma, vrest;
     int32_t sample_every;
+    int32_t frame_avg;       // camera frame averaging: a sample reads the frame mean of c
+    float *obs_acc;          // [N] frame sums of c (frame averaging only)
     uint64_t obs_seed;
     uint32_t bg_thr;         // 0 = no background
     float bg_amp;

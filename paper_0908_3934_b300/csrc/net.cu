@@ -57,6 +57,7 @@ struct gn_net {
     std::vector<int32_t> delay;       // caller edge order
     size_t bytes = 0;
     DevArray<float> ring, ew, bias, obs, p_amp, iz_v;
+    DevArray<float> obs_acc;         // frame sums of the readout state (frame averaging)
     DevArray<float2> wc, rp;
     DevArray<float4> hh_g;           // Hodgkin-Huxley gates (m, n, h, 0)
     int32_t model = GN_MODEL_FHN;
@@ -109,7 +110,7 @@ struct gn_net {
     ~gn_net()
     {
         if (graph) cudaGraphExecDestroy(graph);
-        for (auto *a : {&ring, &ew, &bias, &obs, &p_amp, &iz_v}) a->release();
+        for (auto *a : {&ring, &ew, &bias, &obs, &p_amp, &iz_v, &obs_acc}) a->release();
         wc.release();
         rp.release();
         hh_g.release();
@@ -330,7 +331,7 @@ void autotune(gn_net *net)
     }
     const int32_t N = net->N;
     size_t scratch_bytes = 0;
-    DevArray<float> ring, obs, iz_v;
+    DevArray<float> ring, obs, iz_v, obs_acc;
     DevArray<float2> wc, rp;
     DevArray<float4> hh_g;
     DevArray<int32_t> bgc, evn;
@@ -341,7 +342,7 @@ void autotune(gn_net *net)
     auto cleanup = [&] {
         ring.release(); obs.release(); wc.release(); bgc.release(); evn.release(); first.release();
         evs.release(); dstep.release(); evc.release(); status.release(); iz_v.release(); rp.release();
-        hh_g.release();
+        hh_g.release(); obs_acc.release();
         if (t0) cudaEventDestroy(t0);
         if (t1) cudaEventDestroy(t1);
     };
@@ -362,6 +363,10 @@ void autotune(gn_net *net)
             rp.alloc(N, &scratch_bytes);
             cuda_check(cudaMemcpyAsync(iz_v.p, net->iz_v.p, N * 4ull, cudaMemcpyDeviceToDevice, net->stream), "D2D");
             cuda_check(cudaMemcpyAsync(rp.p, net->rp.p, N * 8ull, cudaMemcpyDeviceToDevice, net->stream), "D2D");
+        }
+        if (net->args.frame_avg) {
+            obs_acc.alloc(N, &scratch_bytes);
+            cuda_check(cudaMemsetAsync(obs_acc.p, 0, N * 4ull, net->stream), "memset");
         }
         if (net->model == GN_MODEL_HH) {
             hh_g.alloc(N, &scratch_bytes);
@@ -403,6 +408,7 @@ void autotune(gn_net *net)
             a.iz_v = iz_v.p;
             a.rp = rp.p;
             a.hh_g = hh_g.p;
+            a.obs_acc = obs_acc.p;
             const int warm = 3, timed = 8;
             for (int k = 0; k < warm; ++k)
                 cuda_check(launch_kind(a, net, k, net->stream), "autotune launch");
@@ -616,6 +622,11 @@ gn_status gn_net_create(const gn_net_desc *desc, gn_net **out)
 
         gn::StepArgs &a = net->args;
         gnrt::fill_step_params(desc, h, a);
+        if (a.frame_avg) {
+            net->obs_acc.alloc(N, &net->bytes);
+            cuda_check(cudaMemset(net->obs_acc.p, 0, N * 4ull), "memset");
+        }
+        a.obs_acc = net->obs_acc.p;
         a.ekey = net->ekey.p;
         a.ew = net->ew.p;
         a.row_ptr = net->row_ptr.p;
@@ -887,6 +898,7 @@ gn_status gn_set_state(gn_net *net, const float *hist, int32_t depth, const floa
         cuda_check(cudaMemcpy(net->bgc.p, bg.data(), N * 4ull, cudaMemcpyHostToDevice), "H2D bg");
         cuda_check(cudaMemset(net->first.p, 0xff, N * 8ull), "memset");
         cuda_check(cudaMemset(net->ev_count.p, 0, 8), "memset");
+        if (net->obs_acc.p) cuda_check(cudaMemset(net->obs_acc.p, 0, N * 4ull), "memset");  // a new frame
         cuda_check(cudaMemcpy(net->d_step.p, &step, 8, cudaMemcpyHostToDevice), "H2D step");
         net->step = step;
         net->read_cursor = step / net->sample_every;
@@ -1224,6 +1236,7 @@ gn_status gn_load_state(gn_net *net, const void *buf, size_t size)
         net->step = h.step;
         net->read_cursor = h.step / net->sample_every;
         cuda_check(cudaMemcpy(net->d_step.p, &h.step, 8, cudaMemcpyHostToDevice), "H2D step");
+        if (net->obs_acc.p) cuda_check(cudaMemset(net->obs_acc.p, 0, N * 4), "memset");  // a new frame
         cuda_check(cudaMemset(net->ev_count.p, 0, 8), "memset");
     });
 }

@@ -429,6 +429,7 @@ void fill_step_params(const gn_net_desc *d, const HostNet &h, gn::StepArgs &a)
     a.sigma = d->obs.sigma;
     a.vrest = static_cast<float>(vr);
     a.sample_every = d->obs.sample_every;
+    a.frame_avg = d->obs.frame_average ? 1 : 0;
     a.obs_seed = d->obs.seed;
     a.bg_thr = 0;
     a.bg_amp = 0.0f;

@@ -129,6 +129,16 @@ __device__ __forceinline__ void record_event(const StepArgs &a, int r, int64_t s
     }
 }
 
+// The readout state a sample reads: c1, or with camera frame averaging the mean of
+// c over the sample_every steps of the frame (summed in step order, then divided).
+__device__ __forceinline__ float frame_value(const StepArgs &a, int r, float c1, bool sample)
+{
+    if (!a.frame_avg) return c1;
+    const float acc = a.obs_acc[r] + c1;
+    a.obs_acc[r] = sample ? 0.0f : acc;
+    return sample ? __fdiv_rn(acc, static_cast<float>(a.sample_every)) : c1;
+}
+
 // Spiking-node outputs of step n -> n + 1: spike ring (spd(V1)), events, first
 // spike, and the calcium readout every sample_every steps.  A plastic net's ring
 // word also carries s in whole steps: s_j' = (1 - spd(V_j)) (s_j + dt), from the
@@ -148,11 +158,13 @@ __device__ __forceinline__ void spiking_outputs(const StepArgs &a, int r, int64_
         record_event(a, r, n + 1);
         if (a.first[r] < 0) a.first[r] = n + 1;
     }
-    if (((n + 1) % a.sample_every) == 0) {
+    const bool sample = ((n + 1) % a.sample_every) == 0;
+    const float cs = frame_value(a, r, c1, sample);
+    if (sample) {
         const int64_t k = (n + 1) / a.sample_every - 1;
         if (orig == kLoad) orig = __ldg(a.perm + r);
         const float xi = gauss_from(draw(a.obs_seed, static_cast<uint32_t>(orig), k, kStreamObservation));
-        a.obs[(k % a.obs_cap) * a.N + orig] = fmaf(a.gain, c1, a.offset) + a.sigma * xi;
+        a.obs[(k % a.obs_cap) * a.N + orig] = fmaf(a.gain, cs, a.offset) + a.sigma * xi;
     }
 }
 
@@ -304,11 +316,13 @@ __device__ __forceinline__ void node_update(const StepArgs &a, int r, int64_t n,
     if (v < a.theta_s && v1 >= a.theta_s) record_event(a, r, n + 1);
     if (v1 != 0.0f && v == 0.0f && a.first[r] < 0) a.first[r] = n + 1;
 
-    if (((n + 1) % a.sample_every) == 0) {
+    const bool sample = ((n + 1) % a.sample_every) == 0;
+    const float cs = frame_value(a, r, c1, sample);
+    if (sample) {
         const int64_t k = (n + 1) / a.sample_every - 1;
         if (orig == kLoad) orig = __ldg(a.perm + r);
         const float xi = gauss_from(draw(a.obs_seed, static_cast<uint32_t>(orig), k, kStreamObservation));
-        const float y = fmaf(a.gain, a.vrest + c1, a.offset) + a.sigma * xi;
+        const float y = fmaf(a.gain, a.vrest + cs, a.offset) + a.sigma * xi;
         a.obs[(k % a.obs_cap) * a.N + orig] = y;  // rows are written in the caller's node order
     }
 }

@@ -34,7 +34,7 @@ class gn_fhn_params(C.Structure):
 
 class gn_obs_params(C.Structure):
     _fields_ = [("tau_ms", C.c_double), ("sample_every", C.c_int32), ("gain", C.c_float),
-                ("offset", C.c_float), ("sigma", C.c_float), ("seed", C.c_uint64)]
+                ("offset", C.c_float), ("sigma", C.c_float), ("seed", C.c_uint64), ("frame_average", C.c_int32)]
 
 
 class gn_izh_params(C.Structure):
@@ -202,7 +202,8 @@ def make_desc(spec, keep: list, *, device: int = 0, stream=None, obs_capacity: i
         speed_scalar=float(spec.speed_scalar or 0.0), delay_steps=_ptr(k["delay"]), dt_ms=spec.dt_ms,
         fhn=gn_fhn_params(**{x: fhn[x] for x in ("a", "b", "c", "e", "f", "g", "i_ext")}),
         obs=gn_obs_params(tau_ms=obs["tau_ms"], sample_every=obs["sample_every"], gain=obs["gain"],
-                          offset=obs["offset"], sigma=obs["sigma"], seed=obs["seed"]),
+                          offset=obs["offset"], sigma=obs["sigma"], seed=obs["seed"],
+                          frame_average=1 if obs.get("frame_average") else 0),
         coupling=GN_COUPLE_RAW if cpl == "raw" else GN_COUPLE_REST, theta=spec.theta,
         ring_depth=spec.ring_depth if ring_depth is None else ring_depth,
         obs_capacity=obs_capacity, event_capacity=event_capacity, renumber=0 if renumber else -1,
