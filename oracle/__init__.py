@@ -62,6 +62,7 @@ class _Net(C.Structure):
         ("hh_iext", C.c_double),
         ("stdp", C.c_int32), ("stdp_alpha", C.c_double), ("stdp_beta", C.c_double),
         ("frame_average", C.c_int32),
+        ("n_types", C.c_int32), ("types", C.c_void_p), ("cell_type", C.c_void_p),
     ]
 
 
@@ -240,6 +241,14 @@ def simulate(spec, n_steps: int, *, dense: bool = False, snap_every: int = 0,
     # the PSC rate and calcium time are shared by the spiking models
     psc = hp if hh else iz
     stdp = getattr(spec, "stdp", None)
+    ctypes_ = getattr(spec, "cell_types", None)
+    if ctypes_:
+        keys = ("C", "gna", "gk", "gl", "ena", "ek", "el", "vpeak", "i_ext", "psc_a", "tau_c") if hh else \
+               ("C", "k", "vr", "vt", "vpeak", "vreset", "a", "b", "d", "i_ext", "psc_a", "tau_c")
+        type_tab = np.array([[t[k] for k in keys] for t in ctypes_], np.float64)
+        cell_type = np.ascontiguousarray(spec.cell_type, np.uint8)
+    else:
+        type_tab = cell_type = None
     net = _Net(
         n_nodes=N, n_edges=E, src=_ptr(src), dst=_ptr(dst), weight=_ptr(wgt), delay=_ptr(D),
         dt_ms=spec.dt_ms, a=fhn["a"], b=fhn["b"], c=fhn["c"], e=fhn["e"], f=fhn["f"], g=fhn["g"],
@@ -260,6 +269,7 @@ def simulate(spec, n_steps: int, *, dense: bool = False, snap_every: int = 0,
         hh_iext=hp.get("i_ext", 0.0),
         stdp=1 if stdp else 0, stdp_alpha=stdp["alpha"] if stdp else 0.0, stdp_beta=stdp["beta"] if stdp else 0.0,
         frame_average=1 if obs.get("frame_average") else 0,
+        n_types=len(ctypes_) if ctypes_ else 0, types=_ptr(type_tab), cell_type=_ptr(cell_type),
     )
     v = np.zeros(N)
     w = np.zeros(N)

@@ -92,6 +92,7 @@
 #define ORC_OK 0
 #define ORC_EINVAL -1
 #define ORC_ENOMEM -2
+#define ORC_MAX_TYPES 8   /* cell types of a heterogeneous network */
 
 /* ------------------------------------------------------------------------- */
 /* Philox4x32-10 (Salmon et al., SC'11): 10 rounds of the 4x32 S-box
@@ -265,6 +266,13 @@ typedef struct {
     /* camera frame averaging: a sample reads the mean of the readout state over the
      * sample_every steps of its frame instead of its last value */
     int32_t frame_average;
+    /* heterogeneous cells (spiking models): node j takes parameter set cell_type[j] of
+     * n_types rows of `types`, each (C, k, v_r, v_t, v_peak, v_reset, a, b, d, i_ext,
+     * psc_a, tau_c) for model 1 or (C, g_Na, g_K, g_L, E_Na, E_K, E_L, v_peak, i_ext,
+     * psc_a, tau_c) for model 2, in place of the fields above */
+    int32_t n_types;
+    const double *types;
+    const uint8_t *cell_type;
 } orc_net;
 
 typedef struct {
@@ -441,7 +449,28 @@ static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense
     if (izh && !(net->iz_C > 0.0)) return ORC_EINVAL;
     if (hh && !(net->hh_C > 0.0)) return ORC_EINVAL;
     if (spiking ? !(net->tau_c > 0.0) : !(net->tau_ms > 0.0)) return ORC_EINVAL;
-    const double vpeak = hh ? net->hh_vpeak : net->iz_vpeak;
+    if (net->n_types < 0 || net->n_types > ORC_MAX_TYPES || (net->n_types > 0 && (!spiking || !net->types || !net->cell_type)))
+        return ORC_EINVAL;
+    /* the parameters of each cell type, as whole networks' fields */
+    orc_net tnet[ORC_MAX_TYPES];
+    for (int32_t t = 0; t < net->n_types; ++t) {
+        const double *q = net->types + (size_t)t * (izh ? 12 : 11);
+        tnet[t] = *net;
+        if (izh) {
+            tnet[t].iz_C = q[0]; tnet[t].iz_k = q[1]; tnet[t].iz_vr = q[2]; tnet[t].iz_vt = q[3];
+            tnet[t].iz_vpeak = q[4]; tnet[t].iz_vreset = q[5]; tnet[t].iz_a = q[6]; tnet[t].iz_b = q[7];
+            tnet[t].iz_d = q[8]; tnet[t].iz_iext = q[9]; tnet[t].psc_a = q[10]; tnet[t].tau_c = q[11];
+        } else {
+            tnet[t].hh_C = q[0]; tnet[t].hh_gna = q[1]; tnet[t].hh_gk = q[2]; tnet[t].hh_gl = q[3];
+            tnet[t].hh_ena = q[4]; tnet[t].hh_ek = q[5]; tnet[t].hh_el = q[6]; tnet[t].hh_vpeak = q[7];
+            tnet[t].hh_iext = q[8]; tnet[t].psc_a = q[9]; tnet[t].tau_c = q[10];
+        }
+        if ((izh && !(tnet[t].iz_C > 0.0)) || (hh && !(tnet[t].hh_C > 0.0)) || !(tnet[t].tau_c > 0.0)) return ORC_EINVAL;
+    }
+    for (int32_t j = 0; j < N && net->n_types > 0; ++j)
+        if (net->cell_type[j] >= net->n_types) return ORC_EINVAL;
+#define NODE_NET(j) (net->n_types > 0 ? &tnet[net->cell_type[j]] : net)
+#define VPEAK(j) (hh ? NODE_NET(j)->hh_vpeak : NODE_NET(j)->iz_vpeak)
     double v_rest = 0.0, w_rest = 0.0;
     if (!spiking && orc_rest_point(net->a, net->b, net->c, net->f, net->g, net->i_ext, &v_rest, &w_rest))
         return ORC_EINVAL;
@@ -492,7 +521,7 @@ static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense
         return ORC_ENOMEM;
     }
     if (izh)
-        for (int32_t j = 0; j < N; ++j) v[j] = net->iz_vr;
+        for (int32_t j = 0; j < N; ++j) v[j] = NODE_NET(j)->iz_vr;
     if (hh) {
         double m0, n0_, h0;
         orc_hh_rest_gates(&m0, &n0_, &h0);
@@ -539,7 +568,7 @@ static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense
 
     for (int64_t n = n0; n < n0 + n_steps; ++n) {
         /* record v~(n) (model 1: spd(V(n))) before anything reads the history of this step */
-        for (int32_t j = 0; j < N; ++j) hist_put(&h, n, j, spiking ? (v[j] >= vpeak ? 1.0 : 0.0) : v[j]);
+        for (int32_t j = 0; j < N; ++j) hist_put(&h, n, j, spiking ? (v[j] >= VPEAK(j) ? 1.0 : 0.0) : v[j]);
         if (stdp)
             for (int32_t j = 0; j < N; ++j) hist_put(&hs, n, j, sj[j]);
         /* S_j(n) = sum over edges i -> j of w_ij * v_i(n - D_ij) */
@@ -568,22 +597,22 @@ static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense
                 double r1, p1;
                 int spike;
                 if (izh) {
-                    izh_step(net, v[j], w[j], r[j], p[j], c[j], S[j], U, &v1, &w1, &r1, &p1, &c1);
-                    spike = v1 >= vpeak;
+                    izh_step(NODE_NET(j), v[j], w[j], r[j], p[j], c[j], S[j], U, &v1, &w1, &r1, &p1, &c1);
+                    spike = v1 >= VPEAK(j);
                 } else {
                     double m1, n1, h1;
-                    hh_step(net, v[j], gm[j], gn[j], gh[j], r[j], p[j], c[j], S[j], U, &v1, &m1, &n1, &h1, &r1, &p1,
+                    hh_step(NODE_NET(j), v[j], gm[j], gn[j], gh[j], r[j], p[j], c[j], S[j], U, &v1, &m1, &n1, &h1, &r1, &p1,
                             &c1);
                     gm[j] = m1;
                     gn[j] = n1;
                     gh[j] = h1;
                     w1 = 0.0;
-                    spike = v[j] < vpeak && v1 >= vpeak;   /* an upward crossing (no reset) */
+                    spike = v[j] < VPEAK(j) && v1 >= VPEAK(j);   /* an upward crossing (no reset) */
                 }
                 r[j] = r1;
                 p[j] = p1;
                 if (out->min_peak_gap) {
-                    double gap = fabs(v1 - vpeak);
+                    double gap = fabs(v1 - VPEAK(j));
                     if (gap < out->min_peak_gap[j]) out->min_peak_gap[j] = gap;
                 }
                 if (spike) {
@@ -654,7 +683,7 @@ static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense
         int64_t n_end = n0 + n_steps;
         for (int32_t k = 0; k < out->hist_out_depth; ++k)
             for (int32_t j = 0; j < N; ++j) {
-                double now = spiking ? (v[j] >= vpeak ? 1.0 : 0.0) : v[j];
+                double now = spiking ? (v[j] >= VPEAK(j) ? 1.0 : 0.0) : v[j];
                 out->hist_out[(int64_t)k * N + j] = (k == 0) ? now : hist_get(&h, n_end - k, j);
             }
     }
@@ -671,6 +700,8 @@ static int simulate(const orc_net *net, int64_t n_steps, orc_out *out, int dense
     free(h.buf); free(v); free(w); free(c); free(S); free(bgc); free(r); free(p); free(gm); free(gn); free(gh);
     free(hs.buf); free(sj); free(wcur); free(facc);
     return ORC_OK;
+#undef NODE_NET
+#undef VPEAK
 }
 
 /* Circular history of depth D_max + 1 (the working oracle). */

@@ -52,6 +52,11 @@ OBS_DEFAULT = dict(tau_ms=5.0, sample_every=20, gain=1.0, offset=0.0, sigma=0.05
 # paper gives the model, not these numbers.
 IZH_RS = dict(C=100.0, k=0.7, vr=-60.0, vt=-40.0, vpeak=35.0, vreset=-50.0, a=0.03, b=-2.0, d=100.0,
               i_ext=0.0, psc_a=0.2, tau_c=20.0)
+# A fast-spiking interneuron-like parameter set of the same simple model (small
+# capacitance, fast recovery, no adaptation jump), for excitatory / inhibitory mixes;
+# the PSC and calcium constants are the regular-spiking cell's.
+IZH_FS = dict(C=20.0, k=1.0, vr=-55.0, vt=-40.0, vpeak=25.0, vreset=-45.0, a=0.2, b=-2.0, d=0.0,
+              i_ext=0.0, psc_a=0.2, tau_c=20.0)
 # Hodgkin-Huxley squid-axon constants in the modern convention (uF/cm^2, mS/cm^2,
 # mV; rest near -65 mV), V_peak = 0 mV for the spike indicator, and the same PSC
 # and calcium time constants as IZH_RS.
@@ -83,6 +88,8 @@ class NetSpec:
     izh: dict = dataclasses.field(default_factory=lambda: dict(IZH_RS))
     hh: dict = dataclasses.field(default_factory=lambda: dict(HH_CLASSIC))
     stdp: dict | None = None        # spike-time-dependent plasticity {alpha, beta} (spiking models)
+    cell_types: list | None = None  # heterogeneous cells: parameter sets of the spiking model ...
+    cell_type: np.ndarray | None = None  # ... and each node's set (uint8, < 8 sets)
 
     @property
     def n_nodes(self) -> int:
@@ -110,6 +117,24 @@ def izhikevich(spec: "NetSpec", w_scale: float = 2000.0, pulse_amp: float = 2500
         pulses=[(j, t0, t1, pulse_amp) for (j, t0, t1, _) in spec.pulses],
         background=None if spec.background is None else dict(spec.background, amp=pulse_amp),
         obs=dict(spec.obs, gain=obs_gain), name=spec.name + "_izh")
+
+
+def mixed_cells(spec: "NetSpec", types=None, frac=(0.8, 0.2), inhibitory=(False, True), seed: int = 0):
+    """Heterogeneous cells (Sec. 3.1: networks of different cell types as different
+    parameter sets of one transition function): each node draws a parameter set of
+    the network's spiking model with probabilities `frac`; a source of an inhibitory
+    set makes every out-weight negative, of an excitatory set positive (|w| kept).
+    Default: Izhikevich regular-spiking 80 % / fast-spiking 20 % (inhibitory)."""
+    if spec.model not in ("izh", "hh"):
+        raise ValueError("heterogeneous cells need a spiking model")
+    if types is None:
+        types = [dict(IZH_RS), dict(IZH_FS)] if spec.model == "izh" else [dict(spec.hh), dict(spec.hh)]
+    rng = np.random.default_rng(seed + 777)
+    cell = rng.choice(len(types), size=spec.n_nodes, p=np.asarray(frac, np.float64) / np.sum(frac)).astype(np.uint8)
+    sign = np.where(np.asarray(inhibitory, bool)[cell[np.asarray(spec.src)]], -1.0, 1.0)
+    w = (np.abs(np.asarray(spec.weight, np.float64)) * sign).astype(np.float32)
+    return dataclasses.replace(spec, cell_types=[dict(t) for t in types], cell_type=cell, weight=w,
+                               name=spec.name + "_mixed")
 
 
 def hodgkin_huxley(spec: "NetSpec", w_scale: float = 10.0, pulse_amp: float = 20.0, obs_gain: float = 1.0,
