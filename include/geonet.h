@@ -175,6 +175,14 @@ typedef struct {
     gn_izh_params izh;           /* used when model == GN_MODEL_IZH (C > 0, tau_c > 0, all finite) */
     gn_hh_params hh;             /* used when model == GN_MODEL_HH (C > 0, tau_c > 0, all finite) */
     gn_stdp_params stdp;         /* plastic weights when stdp.enable != 0 (spiking models) */
+    /* Heterogeneous cells (Sec. 3.1: cell types as parameter sets of one transition
+     * function; spiking models): with 1 <= n_cell_types <= 8, node j takes parameter
+     * set cell_type[j] (caller order) of izh_types or hh_types in place of izh / hh,
+     * and an Izhikevich node starts at its set's v_r.  0: every node takes izh / hh. */
+    int32_t n_cell_types;
+    const gn_izh_params *izh_types;
+    const gn_hh_params *hh_types;
+    const uint8_t *cell_type;
 } gn_net_desc;
 
 /* A pulse of amplitude amp on node over [t_on_ms, t_off_ms): the steps

@@ -90,10 +90,13 @@ struct gn_batch {
     DevArray<int32_t> st_rq, st_tile_net;
     // node model shared by every member; spiking members' V, (r, p), gates
     int32_t model = GN_MODEL_FHN;
+    std::vector<uint8_t> hetero;  // members with cell types
     DevArray<float> iz_v;
     DevArray<float2> rp;
     DevArray<float4> hh_g;
     DevArray<float> obs_acc;  // frame sums of the readout state (members with frame averaging)
+    DevArray<uint8_t> cell;   // heterogeneous members: each node's parameter set
+    DevArray<float> type_par; // ... and each member's rows (kMaxCellTypes rows per member)
 
     ~gn_batch()
     {
@@ -120,6 +123,8 @@ struct gn_batch {
         rp.release();
         hh_g.release();
         obs_acc.release();
+        cell.release();
+        type_par.release();
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 };
@@ -535,10 +540,26 @@ gn_status gn_batch_create(const gn_net_desc *descs, int32_t n_nets, gn_batch **o
             // spiking members run the staged form only; they start at their rest state
             if (!b->staged_ok) fail(GN_EINVAL, "the staged batch kernel cannot hold this batch of spiking networks");
             std::vector<float> v0(nodes);
-            for (int i = 0; i < n_nets; ++i)
-                std::fill(v0.begin() + b->m[i].node_off, v0.begin() + b->m[i].node_off + b->m[i].N,
-                          static_cast<float>(hs[i].v_rest));
+            bool hetero = false;
+            for (int i = 0; i < n_nets; ++i) {
+                std::copy(hs[i].v0.begin(), hs[i].v0.end(), v0.begin() + b->m[i].node_off);
+                hetero = hetero || !hs[i].cell.empty();
+            }
             b->iz_v.upload(v0, &b->bytes);
+            if (hetero) {  // every member gets a row block; homogeneous members keep null pointers
+                std::vector<uint8_t> cell(nodes, 0);
+                std::vector<float> rows(static_cast<size_t>(n_nets) * gn::kMaxCellTypes * gn::kTypeStride, 0.0f);
+                for (int i = 0; i < n_nets; ++i) {
+                    if (hs[i].cell.empty()) continue;
+                    std::copy(hs[i].cell.begin(), hs[i].cell.end(), cell.begin() + b->m[i].node_off);
+                    std::copy(hs[i].type_par.begin(), hs[i].type_par.end(),
+                              rows.begin() + static_cast<size_t>(i) * gn::kMaxCellTypes * gn::kTypeStride);
+                }
+                b->cell.upload(cell, &b->bytes);
+                b->type_par.upload(rows, &b->bytes);
+            }
+            b->hetero.assign(n_nets, 0);
+            for (int i = 0; i < n_nets; ++i) b->hetero[i] = hs[i].cell.empty() ? 0 : 1;
             b->rp.alloc(nodes, &b->bytes);
             cuda_check(cudaMemset(b->rp.p, 0, b->rp.n * 8), "memset");
             if (b->model == GN_MODEL_HH) {
@@ -609,6 +630,10 @@ gn_status gn_batch_create(const gn_net_desc *descs, int32_t n_nets, gn_batch **o
                 a.iz_v = b->iz_v.p + mm.node_off;
                 a.rp = b->rp.p + mm.node_off;
                 a.hh_g = b->model == GN_MODEL_HH ? b->hh_g.p + mm.node_off : nullptr;
+                if (b->hetero[i]) {
+                    a.cell_type = b->cell.p + mm.node_off;
+                    a.type_par = b->type_par.p + static_cast<size_t>(i) * gn::kMaxCellTypes * gn::kTypeStride;
+                }
             }
             if (b->staged_ok) {
                 a.st_tile = b->st_tile.p;

@@ -96,7 +96,15 @@ struct StepArgs {
     int32_t stdp;
     float stdp_dta, stdp_beta;   // dt alpha, beta
     const uint32_t *st_pinfo;    // per lane slot: piece length | local row << 16
+    // heterogeneous cells (spiking models): each node's parameter set, rows of
+    // kTypeStride floats in the order of the scalar fields above (null: homogeneous)
+    const uint8_t *cell_type;
+    const float *type_par;
 };
+
+constexpr int kMaxCellTypes = 8;
+constexpr int kTypeStride = 16;
+constexpr int kTypeA2 = 13;  // row offset of a_s^2, then 2 a_s and 1 / tau_c (both spiking models)
 
 // A plastic model's kernel code: the node model | kPlastic.
 constexpr int kPlastic = 4;

@@ -60,6 +60,8 @@ struct gn_net {
     DevArray<float> obs_acc;         // frame sums of the readout state (frame averaging)
     DevArray<float2> wc, rp;
     DevArray<float4> hh_g;           // Hodgkin-Huxley gates (m, n, h, 0)
+    DevArray<uint8_t> cell;          // heterogeneous cells: each node's parameter set
+    DevArray<float> type_par;        // ... and the sets' parameter rows
     int32_t model = GN_MODEL_FHN;
     DevArray<uint8_t> ekey;
     DevArray<int32_t> row_ptr, blk, bgc, d_perm, p_node, ev_node, d_npulses;
@@ -114,6 +116,8 @@ struct gn_net {
         wc.release();
         rp.release();
         hh_g.release();
+        cell.release();
+        type_par.release();
         ekey.release();
         for (auto *a : {&row_ptr, &blk, &bgc, &d_perm, &p_node, &ev_node, &d_npulses}) a->release();
         for (auto *a : {&first, &p_on, &p_off, &ev_step, &d_step}) a->release();
@@ -608,7 +612,7 @@ gn_status gn_net_create(const gn_net_desc *desc, gn_net **out)
         cuda_check(cudaMemset(net->d_npulses.p, 0, 4), "memset");
         net->model = desc->model;
         if (net->model != GN_MODEL_FHN) {
-            net->iz_v.upload(std::vector<float>(N, static_cast<float>(h.v_rest)), &net->bytes);
+            net->iz_v.upload(h.v0, &net->bytes);
             net->rp.alloc(N, &net->bytes);
             cuda_check(cudaMemset(net->rp.p, 0, net->rp.n * 8), "memset");
         }
@@ -627,6 +631,12 @@ gn_status gn_net_create(const gn_net_desc *desc, gn_net **out)
             cuda_check(cudaMemset(net->obs_acc.p, 0, N * 4ull), "memset");
         }
         a.obs_acc = net->obs_acc.p;
+        if (!h.cell.empty()) {
+            net->cell.upload(h.cell, &net->bytes);
+            net->type_par.upload(h.type_par, &net->bytes);
+        }
+        a.cell_type = net->cell.p;
+        a.type_par = net->type_par.p;
         a.ekey = net->ekey.p;
         a.ew = net->ew.p;
         a.row_ptr = net->row_ptr.p;

@@ -124,20 +124,37 @@ void validate_desc(const gn_net_desc *d)
         if (d->step_kernel == 1 || d->step_kernel == 2)
             fail(GN_EINVAL, "plastic networks run the staged step kernel (step_kernel 0 or 3)");
     }
-    if (d->model == GN_MODEL_HH) {
-        const gn_hh_params &z = d->hh;
+    auto check_hh = [](const gn_hh_params &z) {
         for (double x : {z.C, z.g_na, z.g_k, z.g_l, z.e_na, z.e_k, z.e_l, z.v_peak, z.i_ext, z.psc_a, z.tau_c})
             if (!std::isfinite(x)) fail(GN_EINVAL, "Hodgkin-Huxley parameters must be finite");
         if (!(z.C > 0.0) || !(z.tau_c > 0.0) || z.psc_a < 0.0)
             fail(GN_EINVAL, "Hodgkin-Huxley parameters need C > 0, tau_c > 0, psc_a >= 0");
-        return;
-    }
-    if (d->model == GN_MODEL_IZH) {
-        const gn_izh_params &z = d->izh;
+    };
+    auto check_izh = [](const gn_izh_params &z) {
         for (double x : {z.C, z.k, z.v_r, z.v_t, z.v_peak, z.v_reset, z.a, z.b, z.d, z.i_ext, z.psc_a, z.tau_c})
             if (!std::isfinite(x)) fail(GN_EINVAL, "Izhikevich parameters must be finite");
         if (!(z.C > 0.0) || !(z.tau_c > 0.0) || z.psc_a < 0.0)
             fail(GN_EINVAL, "Izhikevich parameters need C > 0, tau_c > 0, psc_a >= 0");
+    };
+    if (d->n_cell_types < 0 || d->n_cell_types > gn::kMaxCellTypes)
+        fail(GN_EINVAL, "n_cell_types must be in [0, %d]", gn::kMaxCellTypes);
+    if (d->n_cell_types > 0) {
+        if (d->model == GN_MODEL_FHN) fail(GN_EINVAL, "cell types need a spiking node model");
+        if (!d->cell_type || (d->model == GN_MODEL_IZH ? !d->izh_types : !d->hh_types))
+            fail(GN_EINVAL, "cell types need the parameter sets and each node's set");
+        for (int t = 0; t < d->n_cell_types; ++t) {
+            if (d->model == GN_MODEL_IZH) check_izh(d->izh_types[t]);
+            else check_hh(d->hh_types[t]);
+        }
+        for (int32_t j = 0; j < d->n_nodes; ++j)
+            if (d->cell_type[j] >= d->n_cell_types) fail(GN_EINVAL, "node %d: cell type out of range", j);
+    }
+    if (d->model == GN_MODEL_HH) {
+        check_hh(d->hh);
+        return;
+    }
+    if (d->model == GN_MODEL_IZH) {
+        check_izh(d->izh);
         return;
     }
     double vr, wr;
@@ -303,6 +320,7 @@ void host_build(const gn_net_desc *d, std::vector<int32_t> delay, int64_t n_clam
     }
     const int32_t N = h.N;
     const int64_t E = h.E;
+    if (d->n_cell_types > 0) h.type_par = cell_type_rows(d);
     int32_t dmax = 1, dmin = E ? INT32_MAX : 1;
     for (int32_t D : h.delay) {
         dmax = std::max(dmax, D);
@@ -326,6 +344,17 @@ void host_build(const gn_net_desc *d, std::vector<int32_t> delay, int64_t n_clam
     if (static_cast<double>(R) * h.stride * 4.0 > 200e9)
         fail(GN_ERANGE, "history ring of %d x %d floats is too large", R, N);
     renumber(d, h);
+    if (d->model != GN_MODEL_FHN) {
+        h.v0.assign(N, static_cast<float>(h.v_rest));
+        if (d->n_cell_types > 0) {
+            h.cell.assign(N, 0);
+            for (int32_t j = 0; j < N; ++j) {
+                const uint8_t t = d->cell_type[j];
+                h.cell[h.inv[j]] = t;
+                if (d->model == GN_MODEL_IZH) h.v0[h.inv[j]] = static_cast<float>(d->izh_types[t].v_r);
+            }
+        }
+    }
 
     // by-target rows sorted by source: stable counting sort by source, then by target
     std::vector<int32_t> order(E), tmp(E);
@@ -472,6 +501,30 @@ void fill_step_params(const gn_net_desc *d, const HostNet &h, gn::StepArgs &a)
         a.ca_q = static_cast<float>(1.0 / z.tau_c);
         a.vrest = 0.0f;
     }
+}
+
+std::vector<float> cell_type_rows(const gn_net_desc *d)
+{
+    std::vector<float> rows(static_cast<size_t>(d->n_cell_types) * gn::kTypeStride, 0.0f);
+    const double dt = d->dt_ms;
+    for (int t = 0; t < d->n_cell_types; ++t) {
+        float *q = rows.data() + static_cast<size_t>(t) * gn::kTypeStride;
+        if (d->model == GN_MODEL_IZH) {
+            const gn_izh_params &z = d->izh_types[t];
+            const double v[10] = {dt / z.C, z.k, z.v_r, z.v_t, z.v_peak, z.v_reset, dt * z.a, z.b, z.d, z.i_ext};
+            for (int i = 0; i < 10; ++i) q[i] = static_cast<float>(v[i]);
+        } else {
+            const gn_hh_params &z = d->hh_types[t];
+            const double v[9] = {dt / z.C, z.g_na, z.g_k, z.g_l, z.e_na, z.e_k, z.e_l, z.v_peak, z.i_ext};
+            for (int i = 0; i < 9; ++i) q[i] = static_cast<float>(v[i]);
+        }
+        const double psc_a = d->model == GN_MODEL_IZH ? d->izh_types[t].psc_a : d->hh_types[t].psc_a;
+        const double tau_c = d->model == GN_MODEL_IZH ? d->izh_types[t].tau_c : d->hh_types[t].tau_c;
+        q[gn::kTypeA2] = static_cast<float>(psc_a * psc_a);
+        q[gn::kTypeA2 + 1] = static_cast<float>(2.0 * psc_a);
+        q[gn::kTypeA2 + 2] = static_cast<float>(1.0 / tau_c);
+    }
+    return rows;
 }
 
 void hh_rest_gates(double *m, double *n, double *h)

@@ -97,6 +97,9 @@ struct HostNet {
     std::vector<int32_t> blk;                // [n_blocks + 1]
     std::vector<int4> desc;                  // [n_blocks] {r0, r1, e0, e1}
     std::vector<int32_t> eorig;              // plastic nets: caller edge of each CSR position
+    std::vector<uint8_t> cell;               // heterogeneous cells: parameter set of each node (internal order)
+    std::vector<float> type_par;             // [n_types][gn::kTypeStride] derived per-set parameters
+    std::vector<float> v0;                   // spiking models: starting V of each node (internal order)
     int n_blocks() const { return static_cast<int>(blk.size()) - 1; }
 };
 
@@ -157,6 +160,11 @@ bool build_staged(const HostNet &h, int threads, int ucap, int ecap, int pcap, S
 
 // Scalar fields of the step arguments (FHN about the rest point, readout, sizes).
 void fill_step_params(const gn_net_desc *d, const HostNet &h, gn::StepArgs &a);
+// Per-set parameter rows of a heterogeneous network, in the order of the step
+// arguments' scalar fields (Izhikevich: dt/C, k, v_r, v_t, v_peak, v_reset, dt a, b,
+// d, i_ext; Hodgkin-Huxley: dt/C, g_Na, g_K, g_L, E_Na, E_K, E_L, v_peak, i_ext),
+// then at gn::kTypeA2 for both: a_s^2, 2 a_s, 1/tau_c.
+std::vector<float> cell_type_rows(const gn_net_desc *d);
 // Hodgkin-Huxley gates at -65 mV, x = alpha / (alpha + beta) of the classic rates.
 void hh_rest_gates(double *m, double *n, double *h);
 

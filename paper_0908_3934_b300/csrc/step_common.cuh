@@ -168,6 +168,38 @@ __device__ __forceinline__ void spiking_outputs(const StepArgs &a, int r, int64_
     }
 }
 
+// Parameters of a spiking node: the network's scalars, or its cell type's row.
+struct IzhPar {
+    float dtc, k, vr, vt, vpeak, vreset, dta, b, d, iext, a2, two_a, caq;
+};
+struct HhPar {
+    float dtc, gna, gk, gl, ena, ek, el, vpeak, iext, a2, two_a, caq;
+};
+
+__device__ __forceinline__ IzhPar izh_par(const StepArgs &a, int r)
+{
+    if (a.cell_type) {
+        const float *q = a.type_par + kTypeStride * __ldg(a.cell_type + r);
+        return {__ldg(q),     __ldg(q + 1), __ldg(q + 2),           __ldg(q + 3),           __ldg(q + 4),
+                __ldg(q + 5), __ldg(q + 6), __ldg(q + 7),           __ldg(q + 8),           __ldg(q + 9),
+                __ldg(q + kTypeA2), __ldg(q + kTypeA2 + 1), __ldg(q + kTypeA2 + 2)};
+    }
+    return {a.iz_dtc, a.iz_k, a.iz_vr, a.iz_vt, a.iz_vpeak, a.iz_vreset, a.iz_dta, a.iz_b, a.iz_d, a.iz_iext,
+            a.ps_a2, a.ps_2a, a.ca_q};
+}
+
+__device__ __forceinline__ HhPar hh_par(const StepArgs &a, int r)
+{
+    if (a.cell_type) {
+        const float *q = a.type_par + kTypeStride * __ldg(a.cell_type + r);
+        return {__ldg(q),     __ldg(q + 1), __ldg(q + 2),       __ldg(q + 3),           __ldg(q + 4),
+                __ldg(q + 5), __ldg(q + 6), __ldg(q + 7),       __ldg(q + 8),           __ldg(q + kTypeA2),
+                __ldg(q + kTypeA2 + 1), __ldg(q + kTypeA2 + 2)};
+    }
+    return {a.iz_dtc, a.hh_gna, a.hh_gk, a.hh_gl, a.hh_ena, a.hh_ek, a.hh_el, a.iz_vpeak, a.iz_iext,
+            a.ps_a2, a.ps_2a, a.ca_q};
+}
+
 // Izhikevich simple model with an alpha-function PSC and the calcium readout
 // (Sec. 3.1 Eq. izsimple / izpsc, Sec. 3.2.1 Eq. alphapsc and spd, Sec. 3.3 Eq.
 // casimple), forward Euler from step n to n + 1; the state is absolute.  Everything
@@ -176,24 +208,25 @@ __device__ __forceinline__ void spiking_outputs(const StepArgs &a, int r, int64_
 // resets V, so every step with V >= V_peak is a new spike.
 template <bool kPl>
 __device__ __forceinline__ float2 izh_begin(const StepArgs &a, int r, int64_t n, float2 wc, float U, int32_t orig,
-                                            uint32_t word_now)
+                                         uint32_t word_now)
 {
+    const IzhPar z = izh_par(a, r);
     const float V = a.iz_v[r];
     const float W = wc.x, c = wc.y;
     const float2 rp = a.rp[r];
-    const bool spike = V >= a.iz_vpeak;
+    const bool spike = V >= z.vpeak;
     float V1, W1;
     if (!spike) {
-        V1 = V + a.iz_dtc * (a.iz_k * (V - a.iz_vr) * (V - a.iz_vt) - W + rp.x + U + a.iz_iext);
-        W1 = W + a.iz_dta * (a.iz_b * (V - a.iz_vr) - W);
+        V1 = V + z.dtc * (z.k * (V - z.vr) * (V - z.vt) - W + rp.x + U + z.iext);
+        W1 = W + z.dta * (z.b * (V - z.vr) - W);
     } else {
-        V1 = a.iz_vreset;
-        W1 = W + a.iz_d;
+        V1 = z.vreset;
+        W1 = W + z.d;
     }
-    const float c1 = c + a.dt * (spike ? 1.0f - c * a.ca_q : -c * a.ca_q);
+    const float c1 = c + a.dt * (spike ? 1.0f - c * z.caq : -c * z.caq);
     a.iz_v[r] = V1;
     a.wc[r] = make_float2(W1, c1);
-    spiking_outputs<kPl>(a, r, n, false, V1 >= a.iz_vpeak, c1, orig, word_now);
+    spiking_outputs<kPl>(a, r, n, false, V1 >= z.vpeak, c1, orig, word_now);
     return rp;
 }
 
@@ -209,8 +242,9 @@ __device__ __forceinline__ float hh_trap(float x, float y)
 // crossings of V_peak.
 template <bool kPl>
 __device__ __forceinline__ float2 hh_begin(const StepArgs &a, int r, int64_t n, float2 wc, float U, int32_t orig,
-                                           uint32_t word_now)
+                                        uint32_t word_now)
 {
+    const HhPar z = hh_par(a, r);
     const float V = a.iz_v[r];
     const float4 g = a.hh_g[r];
     const float2 rp = a.rp[r];
@@ -220,27 +254,34 @@ __device__ __forceinline__ float2 hh_begin(const StepArgs &a, int r, int64_t n, 
     const float ah = 0.07f * expf(-e65 / 20.0f), bh = 1.0f / (1.0f + expf(-(V + 35.0f) / 10.0f));
     const float an = 0.01f * hh_trap(V + 55.0f, 10.0f), bn = 0.125f * expf(-e65 / 80.0f);
     const float m3h = g.x * g.x * g.x * g.z, n2 = g.y * g.y;
-    const float i_ion = a.hh_gna * m3h * (V - a.hh_ena) + a.hh_gk * (n2 * n2) * (V - a.hh_ek) +
-                        a.hh_gl * (V - a.hh_el);
-    const float V1 = V + a.iz_dtc * (-i_ion + rp.x + U + a.iz_iext);
+    const float i_ion = z.gna * m3h * (V - z.ena) + z.gk * (n2 * n2) * (V - z.ek) + z.gl * (V - z.el);
+    const float V1 = V + z.dtc * (-i_ion + rp.x + U + z.iext);
     const float m1 = g.x + a.dt * (am * (1.0f - g.x) - bm * g.x);
     const float n1 = g.y + a.dt * (an * (1.0f - g.y) - bn * g.y);
     const float h1 = g.z + a.dt * (ah * (1.0f - g.z) - bh * g.z);
-    const bool above = V >= a.iz_vpeak;
-    const float c1 = c + a.dt * (above ? 1.0f - c * a.ca_q : -c * a.ca_q);
+    const bool above = V >= z.vpeak;
+    const float c1 = c + a.dt * (above ? 1.0f - c * z.caq : -c * z.caq);
     a.iz_v[r] = V1;
     a.hh_g[r] = make_float4(m1, n1, h1, 0.0f);
     a.wc[r] = make_float2(0.0f, c1);
-    spiking_outputs<kPl>(a, r, n, above, V1 >= a.iz_vpeak, c1, orig, word_now);
+    spiking_outputs<kPl>(a, r, n, above, V1 >= z.vpeak, c1, orig, word_now);
     return rp;
 }
 
 // The alpha-function PSC of either spiking model from its step-n values (r, p):
 // r' = r + dt p, p' = p + dt (-a^2 r - 2 a p + S).
+// (the node's PSC constants are looked up again here rather than kept live across
+// the gathers and piece sums between the two halves of the update)
 __device__ __forceinline__ void psc_finish(const StepArgs &a, int r, float2 rp, float S)
 {
+    float a2 = a.ps_a2, two_a = a.ps_2a;
+    if (a.cell_type) {
+        const float *q = a.type_par + kTypeStride * __ldg(a.cell_type + r);
+        a2 = __ldg(q + kTypeA2);
+        two_a = __ldg(q + kTypeA2 + 1);
+    }
     const float r1 = rp.x + a.dt * rp.y;
-    const float p1 = rp.y + a.dt * (-a.ps_a2 * rp.x - a.ps_2a * rp.y + S);
+    const float p1 = rp.y + a.dt * (-a2 * rp.x - two_a * rp.y + S);
     a.rp[r] = make_float2(r1, p1);
 }
 

@@ -65,6 +65,7 @@ class gn_net_desc(C.Structure):
         ("renumber", C.c_int32), ("edge_format", C.c_int32), ("step_kernel", C.c_int32),
         ("cuda_stream", C.c_void_p), ("device", C.c_int32),
         ("model", C.c_int32), ("izh", gn_izh_params), ("hh", gn_hh_params), ("stdp", gn_stdp_params),
+        ("n_cell_types", C.c_int32), ("izh_types", C.c_void_p), ("hh_types", C.c_void_p), ("cell_type", C.c_void_p),
     ]
 
 
@@ -210,7 +211,21 @@ def make_desc(spec, keep: list, *, device: int = 0, stream=None, obs_capacity: i
         edge_format=1 if wide_edges else 0, step_kernel=step_kernel,
         cuda_stream=stream, device=device, model=_MODELS[getattr(spec, "model", "fhn")],
         izh=_izh_params(getattr(spec, "izh", None)), hh=_hh_params(getattr(spec, "hh", None)),
-        stdp=_stdp_params(getattr(spec, "stdp", None)))
+        stdp=_stdp_params(getattr(spec, "stdp", None)), **_cell_types(spec, keep))
+
+
+def _cell_types(spec, keep) -> dict:
+    types = getattr(spec, "cell_types", None)
+    if not types:
+        return {}
+    hh = getattr(spec, "model", "fhn") == "hh"
+    tab = (gn_hh_params * len(types))(*[_hh_params(t) for t in types]) if hh else \
+        (gn_izh_params * len(types))(*[_izh_params(t) for t in types])
+    cell = np.ascontiguousarray(spec.cell_type, np.uint8)
+    keep += [tab, cell]
+    ptr = C.cast(tab, C.c_void_p)
+    return dict(n_cell_types=len(types), izh_types=None if hh else ptr, hh_types=ptr if hh else None,
+                cell_type=_ptr(cell))
 
 
 def _izh_params(iz) -> gn_izh_params:

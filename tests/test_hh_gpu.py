@@ -90,7 +90,7 @@ def test_checkpoint_resume_is_bit_exact():
 
 def test_starting_state_and_model_checks():
     """A new net rests at -65 mV with the gates at their rest values; the gate calls
-    refuse other models and the batched form refuses this one."""
+    refuse other models, and a batch does not mix node models."""
     spec = netgen.hodgkin_huxley(netgen.tiny())
     net = geonet.Net(spec)
     g = net.gn_get_hh_gates()
@@ -102,7 +102,7 @@ def test_starting_state_and_model_checks():
         geonet.Net(netgen.izhikevich(netgen.tiny())).gn_get_hh_gates()
     assert e.value.status == geonet.GN_EINVAL
     with pytest.raises(geonet.GeonetError) as e:
-        geonet.Batch([spec])
+        geonet.Batch([spec, netgen.izhikevich(netgen.tiny())])
     assert e.value.status == geonet.GN_EINVAL
 
 

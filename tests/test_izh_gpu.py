@@ -86,8 +86,8 @@ def test_model_specific_calls_are_checked():
     with pytest.raises(geonet.GeonetError) as e:
         geonet.Net(netgen.tiny()).gn_get_izh_state()
     assert e.value.status == geonet.GN_EINVAL
-    with pytest.raises(geonet.GeonetError) as e:
-        geonet.Batch([netgen.izhikevich(netgen.tiny())])
+    with pytest.raises(geonet.GeonetError) as e:  # one node model per batch
+        geonet.Batch([netgen.izhikevich(netgen.tiny()), netgen.tiny()])
     assert e.value.status == geonet.GN_EINVAL
 
 
