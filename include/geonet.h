@@ -168,7 +168,10 @@ typedef struct {
                                     (in-degree above about 20,000).  Every kernel sums a node's inputs
                                     in the same order, so results do not depend on this choice.  The
                                     environment variable GN_STEP_SHAPE=i picks the CTA shape of an
-                                    explicitly chosen kernel 1 or 3 (default 0) */
+                                    explicitly chosen kernel 1 or 3 (default 0).  Kernel 3 on a large
+                                    FitzHugh-Nagumo net fetches its history values (all written two
+                                    or more steps back) before it waits for the previous step;
+                                    GN_STAGED_EARLY=0 makes it wait first */
     void *cuda_stream;           /* cudaStream_t to run on; NULL: the library makes its own */
     int32_t device;              /* CUDA device ordinal */
     int32_t model;               /* GN_MODEL_FHN (0), GN_MODEL_IZH (1) or GN_MODEL_HH (2) */

@@ -175,10 +175,12 @@ struct StagedShape {
     int threads, ucap, ecap, pcap, stage_entries;
 };
 extern const StagedShape kStagedShapes[kNumStagedShapes];
+// early: gather before the grid wait (FitzHugh-Nagumo, a grid larger than the
+// CTAs the device holds at once -- see staged_tile)
 cudaError_t launch_step_staged(const StepArgs &a, int n_tiles, int k, const StagedShape &shape, bool packed,
-                               bool stream_edges, size_t smem_bytes, cudaStream_t s);
+                               bool stream_edges, size_t smem_bytes, bool early, cudaStream_t s);
 cudaError_t step_staged_prepare(const StagedShape &shape, int model, bool plastic, bool packed, bool stream_edges,
-                                size_t smem_bytes);
+                                size_t smem_bytes, int *ctas_per_sm);
 // batched form with the staged layout: one launch per step over every member's
 // tiles (tile_net[t] = the member of tile t), tiles cut with kBatchStagedShape
 constexpr StagedShape kBatchStagedShape = {128, 3072, 4096, 256, 0};

@@ -54,7 +54,7 @@ constexpr int kThreadsL2 = 1536;
 constexpr int kThreadsPlastic = 1280;
 
 // One tile's step (the CTA's work) for network `a`; `tile` indexes a.st_tile.
-template <int kM, int T, bool kSE, bool kPacked, bool kStream, bool kEarly = false>
+template <int kM, int T, bool kSE, bool kPacked, bool kStream, bool kEarly, bool kLaunchFirst>
 __device__ __forceinline__ void staged_tile(const StepArgs &a, const int tile, const int k)
 {
     // [mbarrier 16 B][keys][values (wide keys only)][entry weights][entry indices][piece sums];
@@ -75,11 +75,15 @@ __device__ __forceinline__ void staged_tile(const StepArgs &a, const int tile, c
     // kEarly (FitzHugh-Nagumo only): the gathers of step n read history slots
     // n - D <= n - 1, all written by step n - 2 or earlier, so the CTA fetches and
     // sums them before griddepcontrol.wait and waits only before the node update
-    // (its rows' state is step n - 1's); it lets the next step's grid start after
-    // that wait, when step n - 1 is complete.  Otherwise it lets the next grid start
-    // at once, so that grid's prologue (key copies, entry prefetch) overlaps this one.
+    // (its rows' state is step n - 1's).  That needs step n - 2 complete when the
+    // grid starts: with kLaunchFirst false the CTA lets the next grid start only
+    // after its wait; with kLaunchFirst it does so at once (the next grid's prologue
+    // overlaps this one), which the host allows only for a grid of more CTAs than
+    // can be resident at once -- its last CTA then starts after another one has
+    // passed the wait, so step n - 1 is complete before step n + 1 starts.
     static_assert(!kEarly || kM == 0, "a spiking node's update starts during the gathers");
-    if constexpr (!kEarly) pdl_launch_dependents();
+    static_assert(kEarly || kLaunchFirst, "a CTA that waits first lets the next grid start first");
+    if constexpr (kLaunchFirst) pdl_launch_dependents();
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int4 td = __ldg(a.st_tile + tile);   // {r0, rows, u0, gathers}
     const int4 td2 = __ldg(a.st_tile2 + tile); // {s0, slices, x0, entries}
@@ -238,7 +242,7 @@ __device__ __forceinline__ void staged_tile(const StepArgs &a, const int tile, c
     // 3. row sums and the node update
     if constexpr (kEarly) {
         pdl_wait();
-        pdl_launch_dependents();
+        if constexpr (!kLaunchFirst) pdl_launch_dependents();
         load_own();
     }
     if (own) {
@@ -262,18 +266,18 @@ __device__ __forceinline__ void staged_tile(const StepArgs &a, const int tile, c
     }
 }
 
-template <int kM, int T, bool kSE, bool kPacked, bool kStream>
+template <int kM, int T, bool kSE, bool kPacked, bool kStream, bool kEarly>
 __global__ void __launch_bounds__(T, (kSE ? kThreadsSE : (kM & kPlastic) ? kThreadsPlastic : kThreadsL2) / T)
     k_step_staged(const StepArgs a, const int k)
 {
-    staged_tile<kM, T, kSE, kPacked, kStream>(a, blockIdx.x, k);
+    staged_tile<kM, T, kSE, kPacked, kStream, kEarly, true>(a, blockIdx.x, k);
 }
 
 // Batched form, one launch per step over the tiles of every member network (all of
 // node model kM): the CTA copies its network's arguments into shared memory, then
 // runs the same tile step (tiles never straddle networks).  FitzHugh-Nagumo
-// batches gather before the grid wait (4096 nets: 0.226 -> 0.203 ms per step; on
-// the 1M-node network the early start of the next grid's prologue wins instead).
+// batches gather before the grid wait and let the next grid start after it (4096
+// nets: 0.226 -> 0.202 ms per step).
 template <int kM, int T, bool kPacked, bool kStream>
 __global__ void __launch_bounds__(T, kThreadsL2 / T) k_batch_staged(const StepArgs *__restrict__ nets,
                                                                     const int *__restrict__ tile_net, const int k)
@@ -283,10 +287,10 @@ __global__ void __launch_bounds__(T, kThreadsL2 / T) k_batch_staged(const StepAr
     uint32_t *dst = reinterpret_cast<uint32_t *>(&s_a);
     for (int i = threadIdx.x; i < static_cast<int>(sizeof(StepArgs) / 4); i += T) dst[i] = __ldg(src + i);
     __syncthreads();
-    staged_tile<kM, T, false, kPacked, kStream, kM == 0>(s_a, blockIdx.x, k);
+    staged_tile<kM, T, false, kPacked, kStream, kM == 0, kM != 0>(s_a, blockIdx.x, k);
 }
 
-template <int kM, int T, bool kSE, bool kPacked, bool kStream>
+template <int kM, int T, bool kSE, bool kPacked, bool kStream, bool kEarly>
 cudaError_t launch_t(const StepArgs &a, int n_tiles, int k, size_t smem, cudaStream_t s)
 {
     cudaLaunchConfig_t cfg = {};
@@ -299,48 +303,67 @@ cudaError_t launch_t(const StepArgs &a, int n_tiles, int k, size_t smem, cudaStr
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_step_staged<kM, T, kSE, kPacked, kStream>, a, k);
+    return cudaLaunchKernelEx(&cfg, k_step_staged<kM, T, kSE, kPacked, kStream, kEarly>, a, k);
 }
 
-// The kernel instance of a shape and edge format: launch it (smem > 0 with a
-// launch) or raise its dynamic shared-memory limit (launch false).
+// One kernel instance: launch it, or (launch false) raise its dynamic shared-memory
+// limit and report how many of its CTAs an SM holds.
+template <int kM, int T, bool kSE, bool kPacked, bool kStream, bool kEarly>
+cudaError_t instance(bool launch, const StepArgs *a, int n_tiles, int k, size_t smem, cudaStream_t s, int *per_sm)
+{
+    if (launch) return launch_t<kM, T, kSE, kPacked, kStream, kEarly>(*a, n_tiles, k, smem, s);
+    auto *fn = k_step_staged<kM, T, kSE, kPacked, kStream, kEarly>;
+    const cudaError_t e =
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess || !per_sm) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, T, smem);
+}
+
+// The kernel instance of a shape, edge format and gather order.
 template <int kM, int T, bool kSE>
-cudaError_t dispatch_fmt(bool launch, const StepArgs *a, int n_tiles, int k, bool packed, bool stream_edges,
-                         size_t smem, cudaStream_t s)
+cudaError_t dispatch_fmt(bool launch, bool early, const StepArgs *a, int n_tiles, int k, bool packed,
+                         bool stream_edges, size_t smem, cudaStream_t s, int *per_sm)
 {
     if constexpr ((kM & kPlastic) != 0 && kSE) {
         return cudaErrorInvalidValue;  // plastic weights: entries are read from global memory
     } else {
-    if (launch) {
-        if (packed)
-            return stream_edges ? launch_t<kM, T, kSE, true, true>(*a, n_tiles, k, smem, s)
-                                : launch_t<kM, T, kSE, true, false>(*a, n_tiles, k, smem, s);
-        return stream_edges ? launch_t<kM, T, kSE, false, true>(*a, n_tiles, k, smem, s)
-                            : launch_t<kM, T, kSE, false, false>(*a, n_tiles, k, smem, s);
-    }
-    const int b = static_cast<int>(smem);
-    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    if (packed)
-        return stream_edges ? cudaFuncSetAttribute(k_step_staged<kM, T, kSE, true, true>, at, b)
-                            : cudaFuncSetAttribute(k_step_staged<kM, T, kSE, true, false>, at, b);
-    return stream_edges ? cudaFuncSetAttribute(k_step_staged<kM, T, kSE, false, true>, at, b)
-                        : cudaFuncSetAttribute(k_step_staged<kM, T, kSE, false, false>, at, b);
+        auto go = [&](auto e) -> cudaError_t {
+            constexpr bool E = decltype(e)::value;
+            if (packed)
+                return stream_edges ? instance<kM, T, kSE, true, true, E>(launch, a, n_tiles, k, smem, s, per_sm)
+                                    : instance<kM, T, kSE, true, false, E>(launch, a, n_tiles, k, smem, s, per_sm);
+            return stream_edges ? instance<kM, T, kSE, false, true, E>(launch, a, n_tiles, k, smem, s, per_sm)
+                                : instance<kM, T, kSE, false, false, E>(launch, a, n_tiles, k, smem, s, per_sm);
+        };
+        if constexpr (kM == 0) {
+            if (!launch) {  // both gather orders may be launched
+                const cudaError_t e = go(std::true_type{});
+                if (e != cudaSuccess) return e;
+                return go(std::false_type{});
+            }
+            if (early) return go(std::true_type{});
+        } else if (early) {
+            return cudaErrorInvalidValue;
+        }
+        return go(std::false_type{});
     }
 }
 
-cudaError_t dispatch(bool launch, const StagedShape &sh, int model, bool plastic, const StepArgs *a, int n_tiles,
-                     int k, bool packed, bool stream_edges, size_t smem, cudaStream_t s)
+cudaError_t dispatch(bool launch, const StagedShape &sh, int model, bool plastic, bool early, const StepArgs *a,
+                     int n_tiles, int k, bool packed, bool stream_edges, size_t smem, cudaStream_t s, int *per_sm)
 {
     const bool se = sh.stage_entries != 0;
     return with_model_plastic(model, plastic, [&](auto m) {
         constexpr int M = decltype(m)::value;
         switch (sh.threads) {
             case 128:
-                return se ? dispatch_fmt<M, 128, true>(launch, a, n_tiles, k, packed, stream_edges, smem, s)
-                          : dispatch_fmt<M, 128, false>(launch, a, n_tiles, k, packed, stream_edges, smem, s);
+                return se ? dispatch_fmt<M, 128, true>(launch, early, a, n_tiles, k, packed, stream_edges, smem, s, per_sm)
+                          : dispatch_fmt<M, 128, false>(launch, early, a, n_tiles, k, packed, stream_edges, smem, s,
+                                                        per_sm);
             case 256:
-                return se ? dispatch_fmt<M, 256, true>(launch, a, n_tiles, k, packed, stream_edges, smem, s)
-                          : dispatch_fmt<M, 256, false>(launch, a, n_tiles, k, packed, stream_edges, smem, s);
+                return se ? dispatch_fmt<M, 256, true>(launch, early, a, n_tiles, k, packed, stream_edges, smem, s, per_sm)
+                          : dispatch_fmt<M, 256, false>(launch, early, a, n_tiles, k, packed, stream_edges, smem, s,
+                                                        per_sm);
             default: return cudaErrorInvalidValue;
         }
     });
@@ -354,16 +377,18 @@ const StagedShape kStagedShapes[kNumStagedShapes] = {
     {128, 3072, 4096, 256, 1}, {128, 3072, 4096, 256, 0}, {256, 6144, 8192, 512, 1}, {256, 6144, 8192, 512, 0}};
 
 cudaError_t launch_step_staged(const StepArgs &a, int n_tiles, int k, const StagedShape &shape, bool packed,
-                               bool stream_edges, size_t smem_bytes, cudaStream_t s)
+                               bool stream_edges, size_t smem_bytes, bool early, cudaStream_t s)
 {
     if (n_tiles <= 0) return cudaSuccess;
-    return dispatch(true, shape, a.model, a.stdp != 0, &a, n_tiles, k, packed, stream_edges, smem_bytes, s);
+    return dispatch(true, shape, a.model, a.stdp != 0, early, &a, n_tiles, k, packed, stream_edges, smem_bytes, s,
+                    nullptr);
 }
 
 cudaError_t step_staged_prepare(const StagedShape &shape, int model, bool plastic, bool packed, bool stream_edges,
-                                size_t smem_bytes)
+                                size_t smem_bytes, int *ctas_per_sm)
 {
-    return dispatch(false, shape, model, plastic, nullptr, 0, 0, packed, stream_edges, smem_bytes, nullptr);
+    return dispatch(false, shape, model, plastic, false, nullptr, 0, 0, packed, stream_edges, smem_bytes, nullptr,
+                    ctas_per_sm);
 }
 
 namespace {

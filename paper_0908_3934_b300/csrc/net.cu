@@ -81,6 +81,7 @@ struct gn_net {
     size_t st_smem = 0;
     int64_t st_gathers = 0, st_entries = 0, st_slots = 0;
     int st_max_u = 0, st_max_x = 0, st_max_p = 0;
+    bool st_early = false;  // gathers before the grid wait (see staged_tile)
     DevArray<int4> st_tile, st_tile2;
     DevArray<uint32_t> st_ukey;
     DevArray<int2> st_slice;
@@ -152,7 +153,7 @@ cudaError_t launch_kind(const gn::StepArgs &a, const gn_net *net, int k, cudaStr
         case 2: return gn::launch_step_pipe(a, net->grid, k, net->packed, net->stream_edges, s);
         case 3:
             return gn::launch_step_staged(a, net->grid, k, gn::kStagedShapes[net->shape], net->packed,
-                                          net->stream_edges, net->st_smem, s);
+                                          net->stream_edges, net->st_smem, net->st_early, s);
         default: return gn::launch_step(a, a.n_blocks, k, net->shape, net->packed, net->stream_edges, s);
     }
 }
@@ -221,8 +222,14 @@ bool set_staged(gn_net *net, int shape)
                         static_cast<size_t>(net->st_max_p) * 4;
     if (smem > static_cast<size_t>(max_smem)) return false;
     if (net->stdp && sh.stage_entries) return false;  // plastic weights are written back to global memory
-    cuda_check(gn::step_staged_prepare(sh, net->model, net->stdp, net->packed, net->stream_edges, smem),
+    int per_sm = 0, sms = 0;
+    cuda_check(gn::step_staged_prepare(sh, net->model, net->stdp, net->packed, net->stream_edges, smem, &per_sm),
                "staged kernel setup");
+    cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, net->device), "device query");
+    // early gathers need the grid to outnumber the CTAs the device holds at once
+    net->st_early = net->model == GN_MODEL_FHN && !net->stdp && per_sm > 0 &&
+                    static_cast<int64_t>(net->n_tiles) > static_cast<int64_t>(per_sm) * sms;
+    if (const char *e = getenv("GN_STAGED_EARLY"); e && *e == '0') net->st_early = false;
     net->st_smem = smem;
     net->st_shape = shape;
     return true;

@@ -211,6 +211,30 @@ def test_every_kernel_and_shape_gives_the_same_bits(monkeypatch):
         assert np.array_equal(hist, ref[1]), (kind, shape)
 
 
+def test_early_gathers_give_the_same_bits(monkeypatch):
+    """A staged grid with more tiles than the device holds at once gathers before
+    its grid wait (history written two or more steps back); the states equal those
+    of the same kernel waiting first, bit for bit, and the oracle's over one window:
+    300k nodes, mean in-degree 20, 100 Hz background."""
+    spec = netgen.large(n=300000, mean_deg=20, bg_rate_hz=100.0)
+    monkeypatch.setenv("GN_STEP_SHAPE", "3")
+    out = []
+    for early in ("1", "0"):
+        monkeypatch.setenv("GN_STAGED_EARLY", early)
+        net = Net(spec, step_kernel=3)
+        assert net.gn_net_get_info()["n_blocks"] > 148 * 6
+        net.gn_step(400)
+        out.append((net.gn_get_state(), net.gn_get_history(16), net.gn_get_events()))
+    (sa, ha, ea), (sb, hb, eb) = out
+    for k in ("v", "w", "c", "bg_count"):
+        assert np.array_equal(sa[k], sb[k]), k
+    assert np.array_equal(ha, hb)
+    assert np.array_equal(ea[0], eb[0]) and np.array_equal(ea[1], eb[1])
+    monkeypatch.setenv("GN_STAGED_EARLY", "1")
+    worst, _ = windowed(spec, Net(spec, step_kernel=3), 20, start=200)
+    assert_windows(worst)
+
+
 def test_staged_kernel_refuses_a_row_beyond_shared_memory():
     """One target with 70,000 distinct (source, delay) reads needs more shared memory
     than a CTA may have: the staged kernel is refused with GN_EINVAL, while the
