@@ -301,6 +301,7 @@ def run_spiking(args, spec, local, stream, model: str, plastic: bool = False):
     t = ev0.elapsed_time(ev1) / 1e3
     info = net.gn_net_get_info()
     n_spikes = int(net.gn_get_events(cap=1 << 24)[0].size)
+    nonfinite = int((~np.isfinite(net.gn_get_izh_state()["V"])).sum())
     changed = None
     if plastic:
         changed = float(np.mean(net.gn_get_weights() != np.asarray(ispec.weight, np.float32)))
@@ -326,6 +327,7 @@ def run_spiking(args, spec, local, stream, model: str, plastic: bool = False):
             "roofline": {"bound": "hbm", "achieved": bytes_step / step_s / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": bytes_step / step_s / 1e9 / peak, "algorithmic_bytes_per_launch": bytes_step},
             "gpu_launches": steps + steps // 64}
+    out["nonfinite_nodes"] = nonfinite
     if plastic:
         out["weights_changed_frac"] = changed
     return out

@@ -81,7 +81,7 @@ __device__ __forceinline__ void staged_tile(const StepArgs &a, const int tile, c
     // overlaps this one), which the host allows only for a grid of more CTAs than
     // can be resident at once -- its last CTA then starts after another one has
     // passed the wait, so step n - 1 is complete before step n + 1 starts.
-    static_assert(!kEarly || kM == 0, "a spiking node's update starts during the gathers");
+    static_assert(!kEarly || !kPl, "plastic weights are written by the previous step");
     static_assert(kEarly || kLaunchFirst, "a CTA that waits first lets the next grid start first");
     if constexpr (kLaunchFirst) pdl_launch_dependents();
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -171,7 +171,7 @@ __device__ __forceinline__ void staged_tile(const StepArgs &a, const int tile, c
     }
     // a spiking node's update reads S only in p: the rest runs while the gathers land
     float2 rp0 = make_float2(0.0f, 0.0f);
-    if constexpr (kM != 0)
+    if constexpr (kM != 0 && !kEarly)
         if (own) rp0 = spiking_begin<kM>(a, r, n, wc, orig, cnt0, word_now);
     cp_async_wait_all();
     __syncthreads();
@@ -261,6 +261,8 @@ __device__ __forceinline__ void staged_tile(const StepArgs &a, const int tile, c
         }
         if constexpr (kM == 0)
             node_update<kM>(a, r, n, v, wc, S, orig, cnt0);
+        else if constexpr (kEarly)  // the whole spiking update after the wait
+            psc_finish(a, r, spiking_begin<kM>(a, r, n, wc, orig, cnt0, word_now), S);
         else
             psc_finish(a, r, rp0, S);
     }
@@ -335,7 +337,7 @@ cudaError_t dispatch_fmt(bool launch, bool early, const StepArgs *a, int n_tiles
             return stream_edges ? instance<kM, T, kSE, false, true, E>(launch, a, n_tiles, k, smem, s, per_sm)
                                 : instance<kM, T, kSE, false, false, E>(launch, a, n_tiles, k, smem, s, per_sm);
         };
-        if constexpr (kM == 0) {
+        if constexpr ((kM & kPlastic) == 0) {
             if (!launch) {  // both gather orders may be launched
                 const cudaError_t e = go(std::true_type{});
                 if (e != cudaSuccess) return e;

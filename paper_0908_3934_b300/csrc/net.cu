@@ -227,7 +227,7 @@ bool set_staged(gn_net *net, int shape)
                "staged kernel setup");
     cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, net->device), "device query");
     // early gathers need the grid to outnumber the CTAs the device holds at once
-    net->st_early = net->model == GN_MODEL_FHN && !net->stdp && per_sm > 0 &&
+    net->st_early = !net->stdp && per_sm > 0 &&
                     static_cast<int64_t>(net->n_tiles) > static_cast<int64_t>(per_sm) * sms;
     if (const char *e = getenv("GN_STAGED_EARLY"); e && *e == '0') net->st_early = false;
     net->st_smem = smem;

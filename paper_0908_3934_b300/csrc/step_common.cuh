@@ -134,7 +134,7 @@ __device__ __forceinline__ void record_event(const StepArgs &a, int r, int64_t s
 __device__ __forceinline__ float frame_value(const StepArgs &a, int r, float c1, bool sample)
 {
     if (!a.frame_avg) return c1;
-    const float acc = a.obs_acc[r] + c1;
+    const float acc = __fadd_rn(a.obs_acc[r], c1);
     a.obs_acc[r] = sample ? 0.0f : acc;
     return sample ? __fdiv_rn(acc, static_cast<float>(a.sample_every)) : c1;
 }
@@ -164,7 +164,7 @@ __device__ __forceinline__ void spiking_outputs(const StepArgs &a, int r, int64_
         const int64_t k = (n + 1) / a.sample_every - 1;
         if (orig == kLoad) orig = __ldg(a.perm + r);
         const float xi = gauss_from(draw(a.obs_seed, static_cast<uint32_t>(orig), k, kStreamObservation));
-        a.obs[(k % a.obs_cap) * a.N + orig] = fmaf(a.gain, cs, a.offset) + a.sigma * xi;
+        a.obs[(k % a.obs_cap) * a.N + orig] = __fmaf_rn(a.sigma, xi, __fmaf_rn(a.gain, cs, a.offset));
     }
 }
 
@@ -200,6 +200,15 @@ __device__ __forceinline__ HhPar hh_par(const StepArgs &a, int r)
             a.ps_a2, a.ps_2a, a.ca_q};
 }
 
+// c' = c + dt (-c / tau_c + spd), every operation rounded as written (the spiking
+// updates spell out their FP32 operations, so that every kernel that inlines them
+// rounds the same way whatever the compiler would contract)
+__device__ __forceinline__ float calcium_step(const StepArgs &a, float c, float caq, bool spd)
+{
+    const float q = __fmul_rn(c, caq);
+    return __fmaf_rn(a.dt, spd ? __fsub_rn(1.0f, q) : -q, c);
+}
+
 // Izhikevich simple model with an alpha-function PSC and the calcium readout
 // (Sec. 3.1 Eq. izsimple / izpsc, Sec. 3.2.1 Eq. alphapsc and spd, Sec. 3.3 Eq.
 // casimple), forward Euler from step n to n + 1; the state is absolute.  Everything
@@ -217,13 +226,15 @@ __device__ __forceinline__ float2 izh_begin(const StepArgs &a, int r, int64_t n,
     const bool spike = V >= z.vpeak;
     float V1, W1;
     if (!spike) {
-        V1 = V + z.dtc * (z.k * (V - z.vr) * (V - z.vt) - W + rp.x + U + z.iext);
-        W1 = W + z.dta * (z.b * (V - z.vr) - W);
+        const float dv = __fsub_rn(V, z.vr);
+        const float quad = __fmul_rn(__fmul_rn(z.k, dv), __fsub_rn(V, z.vt));
+        V1 = __fmaf_rn(z.dtc, __fadd_rn(__fadd_rn(__fadd_rn(__fsub_rn(quad, W), rp.x), U), z.iext), V);
+        W1 = __fmaf_rn(z.dta, __fsub_rn(__fmul_rn(z.b, dv), W), W);
     } else {
         V1 = z.vreset;
-        W1 = W + z.d;
+        W1 = __fadd_rn(W, z.d);
     }
-    const float c1 = c + a.dt * (spike ? 1.0f - c * z.caq : -c * z.caq);
+    const float c1 = calcium_step(a, c, z.caq, spike);
     a.iz_v[r] = V1;
     a.wc[r] = make_float2(W1, c1);
     spiking_outputs<kPl>(a, r, n, false, V1 >= z.vpeak, c1, orig, word_now);
@@ -233,7 +244,7 @@ __device__ __forceinline__ float2 izh_begin(const StepArgs &a, int r, int64_t n,
 // x / (1 - e^(-x / y)) with its limit y at x = 0 (the removable 0/0 of alpha_m, alpha_n)
 __device__ __forceinline__ float hh_trap(float x, float y)
 {
-    return x == 0.0f ? y : x / -expm1f(-x / y);
+    return x == 0.0f ? y : __fdiv_rn(x, -expm1f(__fdiv_rn(-x, y)));
 }
 
 // Hodgkin-Huxley + alpha-PSC + calcium node (model 2): classic squid-axon rates
@@ -249,18 +260,27 @@ __device__ __forceinline__ float2 hh_begin(const StepArgs &a, int r, int64_t n, 
     const float4 g = a.hh_g[r];
     const float2 rp = a.rp[r];
     const float c = wc.y;
-    const float e65 = V + 65.0f;
-    const float am = 0.1f * hh_trap(V + 40.0f, 10.0f), bm = 4.0f * expf(-e65 / 18.0f);
-    const float ah = 0.07f * expf(-e65 / 20.0f), bh = 1.0f / (1.0f + expf(-(V + 35.0f) / 10.0f));
-    const float an = 0.01f * hh_trap(V + 55.0f, 10.0f), bn = 0.125f * expf(-e65 / 80.0f);
-    const float m3h = g.x * g.x * g.x * g.z, n2 = g.y * g.y;
-    const float i_ion = z.gna * m3h * (V - z.ena) + z.gk * (n2 * n2) * (V - z.ek) + z.gl * (V - z.el);
-    const float V1 = V + z.dtc * (-i_ion + rp.x + U + z.iext);
-    const float m1 = g.x + a.dt * (am * (1.0f - g.x) - bm * g.x);
-    const float n1 = g.y + a.dt * (an * (1.0f - g.y) - bn * g.y);
-    const float h1 = g.z + a.dt * (ah * (1.0f - g.z) - bh * g.z);
+    const float e65 = __fadd_rn(V, 65.0f);
+    const float am = __fmul_rn(0.1f, hh_trap(__fadd_rn(V, 40.0f), 10.0f));
+    const float bm = __fmul_rn(4.0f, expf(__fdiv_rn(-e65, 18.0f)));
+    const float ah = __fmul_rn(0.07f, expf(__fdiv_rn(-e65, 20.0f)));
+    const float bh = __fdiv_rn(1.0f, __fadd_rn(1.0f, expf(__fdiv_rn(-__fadd_rn(V, 35.0f), 10.0f))));
+    const float an = __fmul_rn(0.01f, hh_trap(__fadd_rn(V, 55.0f), 10.0f));
+    const float bn = __fmul_rn(0.125f, expf(__fdiv_rn(-e65, 80.0f)));
+    const float m3h = __fmul_rn(__fmul_rn(__fmul_rn(g.x, g.x), g.x), g.z);
+    const float n2 = __fmul_rn(g.y, g.y);
+    const float i_na = __fmul_rn(__fmul_rn(z.gna, m3h), __fsub_rn(V, z.ena));
+    const float i_k = __fmul_rn(__fmul_rn(z.gk, __fmul_rn(n2, n2)), __fsub_rn(V, z.ek));
+    const float i_l = __fmul_rn(z.gl, __fsub_rn(V, z.el));
+    const float i_ion = __fadd_rn(__fadd_rn(i_na, i_k), i_l);
+    const float V1 = __fmaf_rn(z.dtc, __fadd_rn(__fadd_rn(__fsub_rn(rp.x, i_ion), U), z.iext), V);
+    // x' = x + dt (alpha (1 - x) - beta x)
+    auto gate = [&](float x, float al, float be) {
+        return __fmaf_rn(a.dt, __fsub_rn(__fmul_rn(al, __fsub_rn(1.0f, x)), __fmul_rn(be, x)), x);
+    };
+    const float m1 = gate(g.x, am, bm), n1 = gate(g.y, an, bn), h1 = gate(g.z, ah, bh);
     const bool above = V >= z.vpeak;
-    const float c1 = c + a.dt * (above ? 1.0f - c * z.caq : -c * z.caq);
+    const float c1 = calcium_step(a, c, z.caq, above);
     a.iz_v[r] = V1;
     a.hh_g[r] = make_float4(m1, n1, h1, 0.0f);
     a.wc[r] = make_float2(0.0f, c1);
@@ -280,8 +300,8 @@ __device__ __forceinline__ void psc_finish(const StepArgs &a, int r, float2 rp, 
         a2 = __ldg(q + kTypeA2);
         two_a = __ldg(q + kTypeA2 + 1);
     }
-    const float r1 = rp.x + a.dt * rp.y;
-    const float p1 = rp.y + a.dt * (-a2 * rp.x - two_a * rp.y + S);
+    const float r1 = __fmaf_rn(a.dt, rp.y, rp.x);
+    const float p1 = __fmaf_rn(a.dt, __fadd_rn(__fsub_rn(__fmul_rn(-a2, rp.x), __fmul_rn(two_a, rp.y)), S), rp.y);
     a.rp[r] = make_float2(r1, p1);
 }
 
@@ -363,7 +383,7 @@ __device__ __forceinline__ void node_update(const StepArgs &a, int r, int64_t n,
         const int64_t k = (n + 1) / a.sample_every - 1;
         if (orig == kLoad) orig = __ldg(a.perm + r);
         const float xi = gauss_from(draw(a.obs_seed, static_cast<uint32_t>(orig), k, kStreamObservation));
-        const float y = fmaf(a.gain, a.vrest + cs, a.offset) + a.sigma * xi;
+        const float y = __fmaf_rn(a.sigma, xi, __fmaf_rn(a.gain, __fadd_rn(a.vrest, cs), a.offset));
         a.obs[(k % a.obs_cap) * a.N + orig] = y;  // rows are written in the caller's node order
     }
 }

@@ -137,14 +137,18 @@ def mixed_cells(spec: "NetSpec", types=None, frac=(0.8, 0.2), inhibitory=(False,
                                name=spec.name + "_mixed")
 
 
-def hodgkin_huxley(spec: "NetSpec", w_scale: float = 10.0, pulse_amp: float = 20.0, obs_gain: float = 1.0,
+def hodgkin_huxley(spec: "NetSpec", w_scale: float = 3.0, pulse_amp: float = 20.0, obs_gain: float = 1.0,
                    dt_ms: float = 0.03):
     """The same network and controls with Hodgkin-Huxley + alpha-PSC nodes at the
     paper's HH step dt = 0.03 ms: weights in PSC units (uA/cm^2; spd stays 1 for the
     ~1 ms a spike spends above 0 mV, so a spike through weight w adds about w x 1 ms
     to p), pulses and background pulses of pulse_amp uA/cm^2 (2 ms at 20 make a
     resting node spike), calcium readout gain obs_gain; sample interval kept at 1 ms;
-    the ring sized afresh for the longer delays in steps."""
+    the ring sized afresh for the longer delays in steps.  The default scale keeps
+    the signed-weight nets' hyperpolarisation near E_K: at 10 a strongly inhibited
+    node of the 300k-node net reaches -120 mV, where forward Euler of the gates at
+    dt = 0.03 ms is unstable (beta_m dt > 2) and V becomes NaN -- in the FP64 oracle
+    as on the GPU.  The all-excitatory tiny net needs about 10 to propagate."""
     every = max(1, int(round(1.0 / dt_ms)))
     return dataclasses.replace(
         spec, model="hh", hh=dict(HH_CLASSIC), dt_ms=dt_ms, ring_depth=0,

@@ -28,7 +28,7 @@ def test_mixed_tiny_net_windows(model):
         spec = netgen.mixed_cells(netgen.izhikevich(netgen.tiny(), w_scale=7000.0), seed=3)
         n = 4000
     else:
-        base = netgen.hodgkin_huxley(netgen.tiny())
+        base = netgen.hodgkin_huxley(netgen.tiny(), w_scale=10.0)
         spec = netgen.mixed_cells(base, types=[dict(netgen.HH_CLASSIC), dict(netgen.HH_CLASSIC, gk=24.0, i_ext=2.0)],
                                   frac=(0.5, 0.5), inhibitory=(False, False), seed=3)
         n = 2000

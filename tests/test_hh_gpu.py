@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 
 def test_tiny_net_windows_and_spikes():
     """64 nodes with pulses and self-sustained activity (several hundred spikes in 90 ms)."""
-    spec = netgen.hodgkin_huxley(netgen.tiny())
+    spec = netgen.hodgkin_huxley(netgen.tiny(), w_scale=10.0)
     net = geonet.Net(spec)
     worst, n_spikes, excused = windowed_izh(spec, net, 3000)
     print("worst ratios", worst)
@@ -30,7 +30,7 @@ def test_tiny_net_windows_and_spikes():
 def test_spikes_exact_without_resynchronising():
     """From rest, with no spike decision near 0 mV in the oracle's run, the GPU's
     spikes and first spikes equal the oracle's step for step over 1500 steps (45 ms)."""
-    spec = netgen.hodgkin_huxley(netgen.tiny())
+    spec = netgen.hodgkin_huxley(netgen.tiny(), w_scale=10.0)
     n = 1500
     ref = oracle.simulate(spec, n, ev_cap=100000, want_y=False)
     assert ref["ev_count"] > 10 and ref["min_peak_gap"].min() > 1e-2
@@ -91,7 +91,7 @@ def test_checkpoint_resume_is_bit_exact():
 def test_starting_state_and_model_checks():
     """A new net rests at -65 mV with the gates at their rest values; the gate calls
     refuse other models, and a batch does not mix node models."""
-    spec = netgen.hodgkin_huxley(netgen.tiny())
+    spec = netgen.hodgkin_huxley(netgen.tiny(), w_scale=10.0)
     net = geonet.Net(spec)
     g = net.gn_get_hh_gates()
     m0, n0, h0 = oracle.hh_rest_gates()

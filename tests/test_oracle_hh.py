@@ -140,7 +140,7 @@ def test_one_spike_reaches_its_target_after_the_delay():
 def test_hh_ring_equals_dense_history():
     """The circular history and the full [T][N] history give bit-identical runs on
     a spiking Hodgkin-Huxley network."""
-    sp = netgen.hodgkin_huxley(netgen.tiny())
+    sp = netgen.hodgkin_huxley(netgen.tiny(), w_scale=10.0)
     a = oracle.simulate(sp, 3000, ev_cap=100000)
     b = oracle.simulate(sp, 3000, dense=True, ev_cap=100000)
     assert a["ev_count"] > 20

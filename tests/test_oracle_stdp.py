@@ -15,7 +15,7 @@ IZ = netgen.IZH_RS
 
 def _spiking_tiny(model="izh", stdp=None):
     base = netgen.tiny()
-    spec = netgen.izhikevich(base, w_scale=7000.0) if model == "izh" else netgen.hodgkin_huxley(base)
+    spec = netgen.izhikevich(base, w_scale=7000.0) if model == "izh" else netgen.hodgkin_huxley(base, w_scale=10.0)
     if stdp is not None:
         spec = netgen.dataclasses.replace(spec, stdp=stdp)
     return spec

@@ -211,12 +211,15 @@ def test_every_kernel_and_shape_gives_the_same_bits(monkeypatch):
         assert np.array_equal(hist, ref[1]), (kind, shape)
 
 
-def test_early_gathers_give_the_same_bits(monkeypatch):
+@pytest.mark.parametrize("model", ["fhn", "izh", "hh"])
+def test_early_gathers_give_the_same_bits(monkeypatch, model):
     """A staged grid with more tiles than the device holds at once gathers before
     its grid wait (history written two or more steps back); the states equal those
     of the same kernel waiting first, bit for bit, and the oracle's over one window:
-    300k nodes, mean in-degree 20, 100 Hz background."""
-    spec = netgen.large(n=300000, mean_deg=20, bg_rate_hz=100.0)
+    300k nodes, mean in-degree 20, 100 Hz background, each node model."""
+    from parity import windowed_izh
+    base = netgen.large(n=300000, mean_deg=20, bg_rate_hz=100.0)
+    spec = {"fhn": base, "izh": netgen.izhikevich(base), "hh": netgen.hodgkin_huxley(base)}[model]
     monkeypatch.setenv("GN_STEP_SHAPE", "3")
     out = []
     for early in ("1", "0"):
@@ -224,14 +227,21 @@ def test_early_gathers_give_the_same_bits(monkeypatch):
         net = Net(spec, step_kernel=3)
         assert net.gn_net_get_info()["n_blocks"] > 148 * 6
         net.gn_step(400)
-        out.append((net.gn_get_state(), net.gn_get_history(16), net.gn_get_events()))
-    (sa, ha, ea), (sb, hb, eb) = out
+        extra = net.gn_get_izh_state() if model != "fhn" else {}
+        out.append((net.gn_get_state(), net.gn_get_history(16), net.gn_get_events(), extra))
+    (sa, ha, ea, xa), (sb, hb, eb, xb) = out
     for k in ("v", "w", "c", "bg_count"):
         assert np.array_equal(sa[k], sb[k]), k
+    for k in xa:
+        assert np.array_equal(xa[k], xb[k]), k
     assert np.array_equal(ha, hb)
     assert np.array_equal(ea[0], eb[0]) and np.array_equal(ea[1], eb[1])
     monkeypatch.setenv("GN_STAGED_EARLY", "1")
-    worst, _ = windowed(spec, Net(spec, step_kernel=3), 20, start=200)
+    net = Net(spec, step_kernel=3)
+    if model == "fhn":
+        worst, _ = windowed(spec, net, 20, start=200)
+    else:
+        worst, _, _ = windowed_izh(spec, net, 2 * spec.obs["sample_every"] if model == "izh" else 16, start=200)
     assert_windows(worst)
 
 

@@ -69,7 +69,7 @@ def test_tiny_net_windows(model):
     if model == "izh":
         spec, n = _plastic(netgen.izhikevich(base, w_scale=7000.0), alpha=50.0), 4000
     else:
-        spec, n = _plastic(netgen.hodgkin_huxley(base), alpha=0.05), 1600
+        spec, n = _plastic(netgen.hodgkin_huxley(base, w_scale=10.0), alpha=0.05), 1600
     net = geonet.Net(spec)
     worst, n_spikes, excused = windowed_izh(spec, net, n)
     print("worst ratios", worst, "excused", excused)
