@@ -80,6 +80,7 @@ struct gn_batch {
     int64_t graph_steps = 0;
     // staged form: pooled layouts of every member (tile_net: member of each tile)
     bool staged_ok = false, st_packed = true, st_stream = false;
+    bool st_first = false;  // the staged grid outnumbers the resident CTAs: launch the next grid first
     int n_tiles = 0;
     size_t st_smem = 0;
     DevArray<int4> st_tile, st_tile2;
@@ -168,7 +169,12 @@ void upload_args(gn_batch *b, int shape)
 void set_shape(gn_batch *b, int shape)
 {
     if (shape == kStaged) {
-        cuda_check(gn::batch_staged_prepare(b->model, b->st_packed, b->st_stream, b->st_smem), "staged kernel setup");
+        int per_sm = 0, sms = 0;
+        cuda_check(gn::batch_staged_prepare(b->model, b->st_packed, b->st_stream, b->st_smem, &per_sm),
+                   "staged kernel setup");
+        cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device), "device query");
+        b->st_first = per_sm > 0 && static_cast<int64_t>(b->n_tiles) > static_cast<int64_t>(per_sm) * sms;
+        if (const char *e = getenv("GN_STAGED_EARLY"); e && *e == '0') b->st_first = false;
         b->shape = kStaged;
         b->grid = b->n_tiles;
         upload_args(b, 0);
@@ -197,7 +203,7 @@ void launch_steps(gn_batch *b, const gn::StepArgs *args, int64_t *d_step, int n_
     if (shape == kStaged) {
         for (int k = 0; k < n_steps; ++k)
             cuda_check(gn::launch_batch_staged(b->model, args, b->st_tile_net.p, b->n_tiles, k, b->st_packed,
-                                               b->st_stream, b->st_smem, s),
+                                               b->st_stream, b->st_smem, b->st_first, s),
                        "staged batch launch");
         return;
     }
@@ -272,7 +278,8 @@ void autotune(gn_batch *b, bool persistent, bool staged)
             cuda_check(cudaMemcpy(dargs.p, a.data(), a.size() * sizeof(gn::StepArgs), cudaMemcpyHostToDevice), "H2D");
             int grid = b->n_tiles;
             if (shape == kStaged) {
-                cuda_check(gn::batch_staged_prepare(b->model, b->st_packed, b->st_stream, b->st_smem), "staged kernel setup");
+                cuda_check(gn::batch_staged_prepare(b->model, b->st_packed, b->st_stream, b->st_smem, nullptr),
+                           "staged kernel setup");
             } else {
                 int per_sm = 0, sms = 0;
                 cuda_check(gn::batch_occupancy(shape, &per_sm), "occupancy");
@@ -313,7 +320,7 @@ void build_graph(gn_batch *b, int64_t n_steps)
         if (b->shape == kStaged) {
             for (int k = 0; k < n_steps && e == cudaSuccess; ++k)
                 e = gn::launch_batch_staged(b->model, b->d_args.p, b->st_tile_net.p, b->n_tiles, k, b->st_packed,
-                                            b->st_stream, b->st_smem, cs);
+                                            b->st_stream, b->st_smem, b->st_first, cs);
         } else {
             e = cudaMemsetAsync(b->queue.p, 0, 4, cs);
             if (e == cudaSuccess)

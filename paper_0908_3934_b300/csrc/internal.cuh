@@ -185,9 +185,10 @@ cudaError_t step_staged_prepare(const StagedShape &shape, int model, bool plasti
 // tiles (tile_net[t] = the member of tile t), tiles cut with kBatchStagedShape
 constexpr StagedShape kBatchStagedShape = {128, 3072, 4096, 256, 0};
 // (every member of node model `model`)
+// (launch_first: the grid outnumbers the CTAs the device holds at once)
 cudaError_t launch_batch_staged(int model, const StepArgs *nets, const int *tile_net, int n_tiles, int k, bool packed,
-                                bool stream_edges, size_t smem_bytes, cudaStream_t s);
-cudaError_t batch_staged_prepare(int model, bool packed, bool stream_edges, size_t smem_bytes);
+                                bool stream_edges, size_t smem_bytes, bool launch_first, cudaStream_t s);
+cudaError_t batch_staged_prepare(int model, bool packed, bool stream_edges, size_t smem_bytes, int *ctas_per_sm);
 // persistent bulk-copy pipelined variant (k_step_pipe.cu); grid = CTAs to launch
 cudaError_t launch_step_pipe(const StepArgs &a, int grid, int k, bool packed, bool stream_edges, cudaStream_t s);
 int step_pipe_smem_bytes(bool packed);

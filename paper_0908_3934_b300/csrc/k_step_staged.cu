@@ -277,10 +277,9 @@ __global__ void __launch_bounds__(T, (kSE ? kThreadsSE : (kM & kPlastic) ? kThre
 
 // Batched form, one launch per step over the tiles of every member network (all of
 // node model kM): the CTA copies its network's arguments into shared memory, then
-// runs the same tile step (tiles never straddle networks).  FitzHugh-Nagumo
-// batches gather before the grid wait and let the next grid start after it (4096
-// nets: 0.226 -> 0.202 ms per step).
-template <int kM, int T, bool kPacked, bool kStream>
+// runs the same tile step (tiles never straddle networks), gathering before the
+// grid wait; kLaunchFirst as in staged_tile (a grid larger than the device holds).
+template <int kM, int T, bool kPacked, bool kStream, bool kLaunchFirst>
 __global__ void __launch_bounds__(T, kThreadsL2 / T) k_batch_staged(const StepArgs *__restrict__ nets,
                                                                     const int *__restrict__ tile_net, const int k)
 {
@@ -289,7 +288,7 @@ __global__ void __launch_bounds__(T, kThreadsL2 / T) k_batch_staged(const StepAr
     uint32_t *dst = reinterpret_cast<uint32_t *>(&s_a);
     for (int i = threadIdx.x; i < static_cast<int>(sizeof(StepArgs) / 4); i += T) dst[i] = __ldg(src + i);
     __syncthreads();
-    staged_tile<kM, T, false, kPacked, kStream, kM == 0, kM != 0>(s_a, blockIdx.x, k);
+    staged_tile<kM, T, false, kPacked, kStream, true, kLaunchFirst>(s_a, blockIdx.x, k);
 }
 
 template <int kM, int T, bool kSE, bool kPacked, bool kStream, bool kEarly>
@@ -395,14 +394,18 @@ cudaError_t step_staged_prepare(const StagedShape &shape, int model, bool plasti
 
 namespace {
 
-template <int kM, bool kPacked, bool kStream>
+template <int kM, bool kPacked, bool kStream, bool kFirst>
 cudaError_t batch_staged_t(bool launch, const StepArgs *nets, const int *tile_net, int n_tiles, int k, size_t smem,
-                           cudaStream_t s)
+                           cudaStream_t s, int *per_sm)
 {
     constexpr int T = kBatchStagedShape.threads;
-    if (!launch)
-        return cudaFuncSetAttribute(k_batch_staged<kM, T, kPacked, kStream>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    auto *fn = k_batch_staged<kM, T, kPacked, kStream, kFirst>;
+    if (!launch) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess || !per_sm) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, T, smem);
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(static_cast<unsigned>(n_tiles));
     cfg.blockDim = dim3(T);
@@ -413,34 +416,46 @@ cudaError_t batch_staged_t(bool launch, const StepArgs *nets, const int *tile_ne
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_batch_staged<kM, T, kPacked, kStream>, nets, tile_net, k);
+    return cudaLaunchKernelEx(&cfg, fn, nets, tile_net, k);
 }
 
-cudaError_t batch_staged(bool launch, int model, const StepArgs *nets, const int *tile_net, int n_tiles, int k,
-                         bool packed, bool stream_edges, size_t smem, cudaStream_t s)
+cudaError_t batch_staged(bool launch, int model, bool first, const StepArgs *nets, const int *tile_net, int n_tiles,
+                         int k, bool packed, bool stream_edges, size_t smem, cudaStream_t s, int *per_sm)
 {
     return with_model(model, [&](auto m) {
         constexpr int M = decltype(m)::value;
-        if (packed)
-            return stream_edges ? batch_staged_t<M, true, true>(launch, nets, tile_net, n_tiles, k, smem, s)
-                                : batch_staged_t<M, true, false>(launch, nets, tile_net, n_tiles, k, smem, s);
-        return stream_edges ? batch_staged_t<M, false, true>(launch, nets, tile_net, n_tiles, k, smem, s)
-                            : batch_staged_t<M, false, false>(launch, nets, tile_net, n_tiles, k, smem, s);
+        auto go = [&](auto f) -> cudaError_t {
+            constexpr bool F = decltype(f)::value;
+            if (packed)
+                return stream_edges ? batch_staged_t<M, true, true, F>(launch, nets, tile_net, n_tiles, k, smem, s, per_sm)
+                                    : batch_staged_t<M, true, false, F>(launch, nets, tile_net, n_tiles, k, smem, s,
+                                                                        per_sm);
+            return stream_edges ? batch_staged_t<M, false, true, F>(launch, nets, tile_net, n_tiles, k, smem, s, per_sm)
+                                : batch_staged_t<M, false, false, F>(launch, nets, tile_net, n_tiles, k, smem, s, per_sm);
+        };
+        if (!launch) {  // both launch orders may be used
+            const cudaError_t e = go(std::true_type{});
+            if (e != cudaSuccess) return e;
+            return go(std::false_type{});
+        }
+        return first ? go(std::true_type{}) : go(std::false_type{});
     });
 }
 
 }  // namespace
 
 cudaError_t launch_batch_staged(int model, const StepArgs *nets, const int *tile_net, int n_tiles, int k, bool packed,
-                                bool stream_edges, size_t smem_bytes, cudaStream_t s)
+                                bool stream_edges, size_t smem_bytes, bool launch_first, cudaStream_t s)
 {
     if (n_tiles <= 0) return cudaSuccess;
-    return batch_staged(true, model, nets, tile_net, n_tiles, k, packed, stream_edges, smem_bytes, s);
+    return batch_staged(true, model, launch_first, nets, tile_net, n_tiles, k, packed, stream_edges, smem_bytes, s,
+                        nullptr);
 }
 
-cudaError_t batch_staged_prepare(int model, bool packed, bool stream_edges, size_t smem_bytes)
+cudaError_t batch_staged_prepare(int model, bool packed, bool stream_edges, size_t smem_bytes, int *ctas_per_sm)
 {
-    return batch_staged(false, model, nullptr, nullptr, 0, 0, packed, stream_edges, smem_bytes, nullptr);
+    return batch_staged(false, model, false, nullptr, nullptr, 0, 0, packed, stream_edges, smem_bytes, nullptr,
+                        ctas_per_sm);
 }
 
 }  // namespace gn

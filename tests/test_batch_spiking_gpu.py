@@ -68,3 +68,26 @@ def test_spiking_batches_are_checked(monkeypatch):
     with pytest.raises(geonet.GeonetError) as e:
         geonet.Batch(izh).gn_batch_step(10)
     assert e.value.status == geonet.GN_EINVAL
+
+
+@pytest.mark.parametrize("model", ["fhn", "izh"])
+def test_a_batch_larger_than_the_device_launches_first_bit_identically(monkeypatch, model):
+    """A staged batch grid with more tiles than the device holds at once lets the
+    next step's grid start at once (its gathers read history two or more steps
+    old); its members equal those of the same batch waiting first, bit for bit."""
+    specs = [netgen.batch_member(1000 + i) for i in range(700)]
+    if model == "izh":
+        specs = [netgen.izhikevich(sp) for sp in specs]
+    monkeypatch.setenv("GN_BATCH_KERNEL", "3")
+    out = []
+    for early in ("1", "0"):
+        monkeypatch.setenv("GN_STAGED_EARLY", early)
+        b = geonet.Batch(specs)
+        b.gn_batch_step(300)
+        assert b.gn_batch_get_info()["step_kernel"] == 3
+        out.append([(b.gn_batch_get_state(i), b.gn_batch_get_history(i, 4)) for i in range(0, 700, 37)])
+        b.gn_batch_destroy()
+    for (sa, ha), (sb, hb) in zip(*out):
+        for k in ("v", "w", "c", "bg_count"):
+            assert np.array_equal(sa[k], sb[k]), k
+        assert np.array_equal(ha, hb)
