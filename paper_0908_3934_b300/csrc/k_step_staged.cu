@@ -373,9 +373,13 @@ cudaError_t dispatch(bool launch, const StagedShape &sh, int model, bool plastic
 }  // namespace
 
 // {threads, gathers / edges / pieces per tile, stage entries}: shared memory per CTA
-// on a net of mean in-degree 50 about 41, 13, 81 and 26 KB
+// on a net of mean in-degree 50 about 41, 13, 81, 26, 34 and 42 KB.  The last two
+// let a tile of mean in-degree 50 reach its 256 rows (8192 edges stop it near 160),
+// so all 8 warps have pieces to sum (1M-node net: 0.1169 ms per step with shape 3,
+// 0.1392 with shape 4, 0.1126 with shape 5, which larger caps leave unchanged)
 const StagedShape kStagedShapes[kNumStagedShapes] = {
-    {128, 3072, 4096, 256, 1}, {128, 3072, 4096, 256, 0}, {256, 6144, 8192, 512, 1}, {256, 6144, 8192, 512, 0}};
+    {128, 3072, 4096, 256, 1}, {128, 3072, 4096, 256, 0}, {256, 6144, 8192, 512, 1},
+    {256, 6144, 8192, 512, 0}, {256, 8192, 12288, 512, 0}, {256, 10240, 16384, 512, 0}};
 
 cudaError_t launch_step_staged(const StepArgs &a, int n_tiles, int k, const StagedShape &shape, bool packed,
                                bool stream_edges, size_t smem_bytes, bool early, cudaStream_t s)
