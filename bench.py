@@ -549,10 +549,12 @@ def main():
                 t_sim + (c * chunk + rng.uniform(0, chunk)) * spec.dt_ms + 2.0, 1.0)
                for j in rng.choice(N, 1000, replace=False)] for c in range(n_chunks + 1)]
     max_rows = min(args.obs_cap, chunk // spec.obs["sample_every"] + 1)
-    host = torch.empty((max_rows, N), dtype=torch.float32, pin_memory=True).numpy()
+    # two pinned buffers: the observations of one chunk are copied back while the
+    # next chunk steps (gn_observe_async), each buffer reused only after its copy
+    host = [torch.empty((max_rows, N), dtype=torch.float32, pin_memory=True).numpy() for _ in range(2)]
     net.gn_set_stimulus(pulses[0])
     net.gn_step(chunk)
-    net.gn_observe(max_rows, out=host)
+    net.gn_observe(max_rows, out=host[0])
     barrier()
     h2d = d2h = 0
     t0 = time.perf_counter()
@@ -560,8 +562,10 @@ def main():
         net.gn_set_stimulus(pulses[c + 1])
         h2d += 1000 * 24 + 4
         net.gn_step(chunk)
-        y, _, _ = net.gn_observe(max_rows, out=host)
-        d2h += y.nbytes
+        net.gn_observe_wait()  # the copy into the other buffer (the previous chunk) is done
+        rows, _, _ = net.gn_observe_async(host[c % 2], max_rows)
+        d2h += rows * N * 4
+    net.gn_observe_wait()
     barrier()
     t_e2e = time.perf_counter() - t0
     e2e_steps = n_chunks * chunk

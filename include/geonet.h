@@ -273,6 +273,16 @@ GN_API gn_status gn_synchronize(gn_net *net);
 GN_API gn_status gn_observe(gn_net *net, float *out, int64_t max_samples, int64_t *first_sample,
                      int64_t *written);
 
+/* As gn_observe (the same rows, the read cursor advanced the same way), but the
+ * copies are queued on a copy stream behind the steps taken so far and the call
+ * returns at once, so later gn_step calls overlap them (with pinned `out`).  `out`
+ * must stay valid until gn_observe_wait or gn_synchronize returns, and no more than
+ * obs_capacity samples may be produced before then.  GN_EOVERFLOW as gn_observe. */
+GN_API gn_status gn_observe_async(gn_net *net, float *out, int64_t max_samples, int64_t *first_sample,
+                                  int64_t *written);
+/* Wait for the copies gn_observe_async queued (not for later steps). */
+GN_API gn_status gn_observe_wait(gn_net *net);
+
 /* State relative to rest, caller node order.  Any pointer may be NULL. */
 GN_API gn_status gn_get_state(gn_net *net, float *v, float *w, float *c, int32_t *bg_count, int64_t *step);
 

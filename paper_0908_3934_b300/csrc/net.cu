@@ -35,6 +35,8 @@ struct gn_net {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t copy_stream = nullptr;  // observation copies queued by gn_observe_async
+    cudaEvent_t copy_ready = nullptr;    // recorded on `stream` before each such copy
     int32_t N = 0, dim = 0;
     int64_t E = 0;
     int32_t R = 0, dbits = 0, dmax = 0, dmin = 0;
@@ -126,6 +128,11 @@ struct gn_net {
         bdesc.release();
         status.release();
         release_staged();
+        if (copy_stream) {
+            cudaStreamSynchronize(copy_stream);
+            cudaStreamDestroy(copy_stream);
+        }
+        if (copy_ready) cudaEventDestroy(copy_ready);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 };
@@ -135,6 +142,7 @@ namespace {
 void sync(gn_net *net)
 {
     cuda_check(cudaStreamSynchronize(net->stream), "kernel execution");
+    if (net->copy_stream) cuda_check(cudaStreamSynchronize(net->copy_stream), "observation copies");
     unsigned int st = 0;
     if (!net->status.p) return;
     cuda_check(cudaMemcpy(&st, net->status.p, 4, cudaMemcpyDeviceToHost), "D2H status");
@@ -815,34 +823,72 @@ gn_status gn_synchronize(gn_net *net)
     });
 }
 
+namespace {
+
+// The unread rows (at most max_samples) copied into out on stream s (at most two
+// copies: the ring may wrap); advances the read cursor; true if rows were lost.
+bool copy_observations(gn_net *net, float *out, int64_t max_samples, int64_t *first_sample, int64_t *written,
+                       cudaStream_t s)
+{
+    const int64_t produced = net->step / net->sample_every;
+    bool lost = false;
+    if (produced - net->read_cursor > net->obs_cap) {
+        net->read_cursor = produced - net->obs_cap;
+        lost = true;
+    }
+    const int64_t m = std::min(max_samples, produced - net->read_cursor);
+    if (first_sample) *first_sample = net->read_cursor;
+    if (written) *written = m;
+    const size_t row = static_cast<size_t>(net->N) * 4;
+    int64_t done = out ? 0 : m;  // out == NULL: discard
+    while (done < m) {
+        const int64_t k = (net->read_cursor + done) % net->obs_cap;
+        const int64_t len = std::min(m - done, net->obs_cap - k);
+        cuda_check(cudaMemcpyAsync(out + done * net->N, net->obs.p + k * net->N, len * row, cudaMemcpyDeviceToHost, s),
+                   "D2H observations");
+        done += len;
+    }
+    net->read_cursor += m;
+    return lost;
+}
+
+}  // namespace
+
+gn_status gn_observe_async(gn_net *net, float *out, int64_t max_samples, int64_t *first_sample, int64_t *written)
+{
+    return guarded([&] {
+        check_net(net);
+        if (max_samples < 0) fail(GN_EINVAL, "max_samples < 0");
+        DeviceGuard dg(net->device);
+        if (!net->copy_stream) {
+            cuda_check(cudaStreamCreateWithFlags(&net->copy_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+            cuda_check(cudaEventCreateWithFlags(&net->copy_ready, cudaEventDisableTiming), "cudaEventCreate");
+        }
+        cuda_check(cudaEventRecord(net->copy_ready, net->stream), "event");
+        cuda_check(cudaStreamWaitEvent(net->copy_stream, net->copy_ready, 0), "stream wait");
+        if (copy_observations(net, out, max_samples, first_sample, written, net->copy_stream))
+            fail(GN_EOVERFLOW, "observation buffer overflowed: older samples were lost");
+    });
+}
+
+gn_status gn_observe_wait(gn_net *net)
+{
+    return guarded([&] {
+        check_net(net);
+        DeviceGuard dg(net->device);
+        if (net->copy_stream) cuda_check(cudaStreamSynchronize(net->copy_stream), "observation copies");
+    });
+}
+
 gn_status gn_observe(gn_net *net, float *out, int64_t max_samples, int64_t *first_sample, int64_t *written)
 {
     return guarded([&] {
         check_net(net);
         if (max_samples < 0) fail(GN_EINVAL, "max_samples < 0");
         DeviceGuard dg(net->device);
-        const int64_t produced = net->step / net->sample_every;
-        bool lost = false;
-        if (produced - net->read_cursor > net->obs_cap) {
-            net->read_cursor = produced - net->obs_cap;
-            lost = true;
-        }
-        const int64_t m = std::min(max_samples, produced - net->read_cursor);
-        if (first_sample) *first_sample = net->read_cursor;
-        if (written) *written = m;
-        const size_t row = static_cast<size_t>(net->N) * 4;
-        // rows are already in caller order; at most two copies (the ring may wrap)
-        int64_t done = out ? 0 : m;  // out == NULL: discard
-        while (done < m) {
-            const int64_t k = (net->read_cursor + done) % net->obs_cap;
-            const int64_t len = std::min(m - done, net->obs_cap - k);
-            cuda_check(cudaMemcpyAsync(out + done * net->N, net->obs.p + k * net->N, len * row, cudaMemcpyDeviceToHost,
-                                       net->stream),
-                       "D2H observations");
-            done += len;
-        }
+        // rows are already in caller order
+        const bool lost = copy_observations(net, out, max_samples, first_sample, written, net->stream);
         sync(net);
-        net->read_cursor += m;
         if (lost) fail(GN_EOVERFLOW, "observation buffer overflowed: older samples were lost");
     });
 }

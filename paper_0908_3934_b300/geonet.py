@@ -103,6 +103,8 @@ _SIGS = {
     "gn_step": ([_P, C.c_int64], C.c_int),
     "gn_synchronize": ([_P], C.c_int),
     "gn_observe": ([_P, _P, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int64)], C.c_int),
+    "gn_observe_async": ([_P, _P, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int64)], C.c_int),
+    "gn_observe_wait": ([_P], C.c_int),
     "gn_get_state": ([_P, _P, _P, _P, _P, C.POINTER(C.c_int64)], C.c_int),
     "gn_get_history": ([_P, _P, C.c_int32], C.c_int),
     "gn_set_state": ([_P, _P, C.c_int32, _P, _P, _P, C.c_int64], C.c_int),
@@ -327,6 +329,18 @@ class Net:
         st = check(lib().gn_observe(self.h, None if discard else _ptr(out), max_samples, C.byref(first),
                                     C.byref(wr)), allow=(GN_EOVERFLOW,))
         return (None if discard else out[: wr.value]), first.value, st
+
+    def gn_observe_async(self, out: np.ndarray, max_samples: int):
+        """Queue the copy of up to max_samples unread rows into `out` (which must stay
+        alive until gn_observe_wait); returns (rows written, first sample, status)."""
+        first = C.c_int64()
+        wr = C.c_int64()
+        st = check(lib().gn_observe_async(self.h, _ptr(out), max_samples, C.byref(first), C.byref(wr)),
+                   allow=(GN_EOVERFLOW,))
+        return wr.value, first.value, st
+
+    def gn_observe_wait(self):
+        check(lib().gn_observe_wait(self.h))
 
     def gn_get_state(self):
         N = self.n_nodes

@@ -386,3 +386,28 @@ def test_roofline_full_size_sampled():
     assert info["ring_depth"] == 256 and info["edge_format"] == 0
     worst, _ = windowed(spec, net, 20, start=40)
     assert_windows(worst)
+
+
+def test_asynchronous_observation_copies_match_the_synchronous_ones():
+    """gn_observe_async queues the same rows as gn_observe would return, behind the
+    steps taken so far, while later steps run; two chunks alternate two buffers."""
+    spec = netgen.large(n=20000, mean_deg=20, bg_rate_hz=100.0)
+    a, b = Net(spec), Net(spec)
+    every = spec.obs["sample_every"]
+    rows = 500 // every
+    bufs = [np.zeros((rows, spec.n_nodes), np.float32) for _ in range(2)]
+    got = []
+    for c in range(4):
+        a.gn_step(500)
+        ya, first_a, _ = a.gn_observe(rows)
+        b.gn_step(500)
+        b.gn_observe_wait()
+        if c:
+            got.append(bufs[(c - 1) % 2].copy())
+        n, first_b, _ = b.gn_observe_async(bufs[c % 2], rows)
+        assert n == rows and first_b == first_a == c * rows
+        if c:
+            assert np.array_equal(got[-1], prev)
+        prev = ya.copy()
+    b.gn_observe_wait()
+    assert np.array_equal(bufs[3 % 2], prev)
