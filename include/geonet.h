@@ -112,7 +112,7 @@ typedef struct {
  * (1/ms, >= 0) are one pair for the whole network.  s is kept as a whole number of
  * steps (exact), saturating at 2^30 steps.  A plastic network runs the staged step
  * kernel (step_kernel 0 or 3; 1 and 2 fail with GN_EINVAL) in a CTA shape that reads
- * its edge entries from global memory (GN_STEP_SHAPE, default 3), chosen at create
+ * its edge entries from global memory (GN_STEP_SHAPE, default 4), chosen at create
  * time; the batched form does not take it. */
 typedef struct {
     int32_t enable;
