@@ -388,6 +388,29 @@ def test_roofline_full_size_sampled():
     assert_windows(worst)
 
 
+@pytest.mark.parametrize("model", ["izh", "hh", "izh_stdp"])
+def test_roofline_full_size_spiking_sampled(model):
+    """The benchmark's 1M-node network with each spiking node model (Izhikevich at
+    dt 0.05 ms, Hodgkin-Huxley at dt 0.03 ms, Izhikevich with plastic weights) in
+    the launch configuration bench.py times: one window after 2 ms from rest (the
+    background pulses have made about 10^4 spikes), compared on every node (and
+    every weight)."""
+    from parity import windowed_izh
+    base = netgen.roofline()
+    if model == "hh":
+        spec = netgen.hodgkin_huxley(base)
+    else:
+        spec = netgen.izhikevich(base)
+        if model == "izh_stdp":
+            spec = netgen.dataclasses.replace(spec, stdp=dict(alpha=5.0, beta=0.05))
+    net = Net(spec)
+    every = spec.obs["sample_every"]
+    worst, n_spikes, excused = windowed_izh(spec, net, 8 if model == "hh" else every,
+                                            start=67 if model == "hh" else 40)
+    assert_windows(worst)
+    assert excused < 0.001 * spec.n_nodes
+
+
 def test_asynchronous_observation_copies_match_the_synchronous_ones():
     """gn_observe_async queues the same rows as gn_observe would return, behind the
     steps taken so far, while later steps run; two chunks alternate two buffers."""
