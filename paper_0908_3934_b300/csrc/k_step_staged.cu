@@ -45,10 +45,12 @@ __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepc
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // threads per SM the register allocation must allow, with and without entry
-// staging (measured on the 1M-node net: 1536 threads at 40 registers beat 1280 at
-// 48 and 2048 at 32, which spills)
+// staging.  Without it, 1280 threads at 48 registers with 16-deep entry loads: on
+// the 1M-node net 0.1023 ms per step in 256-row tiles (which shared memory holds 5
+// to an SM anyway) against 0.1126 at 1536 threads and 40 registers with 8-deep
+// loads, and 0.1048 at 1280 threads with 8-deep loads
 constexpr int kThreadsSE = 1024;
-constexpr int kThreadsL2 = 1536;
+constexpr int kThreadsL2 = 1280;
 // plastic weights: 48 registers (one 4-byte spill) at 1280 threads per SM beat 56
 // without spills at 1024 (1M-node net: 0.148 vs 0.160 ms per step)
 constexpr int kThreadsPlastic = 1280;
@@ -222,16 +224,16 @@ __device__ __forceinline__ void staged_tile(const StepArgs &a, const int tile, c
             const float *wp = a.st_w + td2.z + sd.x + lane;
             const uint16_t *up = a.st_u + td2.z + sd.x + lane;
             int kk = 0;
-            for (; kk + 8 <= sd.y; kk += 8) {
-                float w8[8];
-                uint16_t u8[8];
+            for (; kk + 16 <= sd.y; kk += 16) {
+                float w8[16];
+                uint16_t u8[16];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
+                for (int i = 0; i < 16; ++i) {
                     w8[i] = __ldcs(wp + (kk + i) * 32);
                     u8[i] = __ldcs(up + (kk + i) * 32);
                 }
 #pragma unroll
-                for (int i = 0; i < 8; ++i) acc = __fadd_rn(acc, __fmul_rn(w8[i], s_val[u8[i]]));
+                for (int i = 0; i < 16; ++i) acc = __fadd_rn(acc, __fmul_rn(w8[i], s_val[u8[i]]));
             }
             for (; kk < sd.y; ++kk) acc = __fadd_rn(acc, __fmul_rn(__ldcs(wp + kk * 32), s_val[__ldcs(up + kk * 32)]));
         }

@@ -428,7 +428,7 @@ void autotune(gn_net *net)
             a.rp = rp.p;
             a.hh_g = hh_g.p;
             a.obs_acc = obs_acc.p;
-            const int warm = 3, timed = 8;
+            const int warm = 3, timed = 24;  // near ties between shapes need more than a few steps
             for (int k = 0; k < warm; ++k)
                 cuda_check(launch_kind(a, net, k, net->stream), "autotune launch");
             cuda_check(cudaEventRecord(t0, net->stream), "event");
