@@ -99,15 +99,20 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_per_launch(kernel: str, workload_name: str):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    if it was taken on the current kernel source; else None."""
+def traffic_per_launch(kernel: str, workload_name: str, grid: int | None = None):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, if
+    it was taken on the current kernel source and (where the summary lists several
+    tilings by grid size) on the tiling this run uses; else None."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload_name}.json")
     try:
         with open(path) as f:
             p = json.load(f)
-        if p.get("kernel_hash") == kernel_hash():
-            return float(p["dram_bytes_per_launch"])
+        if p.get("kernel_hash") != kernel_hash():
+            return None
+        by_grid = p.get("dram_bytes_per_launch_by_grid")
+        if by_grid is not None:
+            return float(by_grid[str(grid)]) if str(grid) in by_grid else None
+        return float(p["dram_bytes_per_launch"])
     except Exception:
         pass
     return None
@@ -584,7 +589,7 @@ def main():
         "node_steps_per_s": (value / E_total) * N * world, "rtf": spec.dt_ms * 1e-3 / step_s,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_kind,
-                     "traffic": traffic_per_launch(KERNEL_NAMES[info["step_kernel"]], args.workload),
+                     "traffic": traffic_per_launch(KERNEL_NAMES[info["step_kernel"]], args.workload, info["grid"]),
                      "algorithmic_bytes_per_launch": bytes_step,
                      "kernel": KERNEL_NAMES[info["step_kernel"]]},
         "e2e": {"value": e2e_value, "unit": METRIC,
