@@ -204,9 +204,13 @@ def run_reference(args):
         return
     spec = workload(args.workload, 0)
     steps = max(1, min(args.steps, args.ref_steps))
+    warm = max(0, min(args.warmup, 3))  # untimed oracle steps (the oracle has no caches to warm)
+    if warm:
+        cpu_baseline(spec, warm)
     cb = cpu_baseline(spec, steps)
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": METRIC, "n_gpus": args.gpus,
-            "steps": steps, "warmup": 0, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "steps": steps, "warmup": warm, "ms_per_step": cb["seconds"] / steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_of(args, spec, world),
             "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
             "e2e": {"value": cb["value"], "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -1,0 +1,61 @@
+"""Host logic of bench.py (no GPU): the algorithmic byte counts of the roofline,
+the lookup of the profiled DRAM traffic, and the JSON line of the reference arm."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_algorithmic_bytes_per_format():
+    E, N = 1000, 100
+    staged = bench.algorithmic_bytes({"step_kernel": 3, "step_gathers": 400}, E, N)
+    assert staged == pytest.approx(E * 6 + 400 * 8 + N * 36.2)
+    plain = bench.algorithmic_bytes({"step_kernel": 1, "step_gathers": E}, E, N)
+    assert plain == pytest.approx(E * 12 + N * 36.2)
+    # the per-node figures of the spiking models extend the FitzHugh-Nagumo one
+    assert bench.HH_NODE_BYTES == pytest.approx(bench.IZH_NODE_BYTES - 0.2 + 32 + 4 / 33, abs=0.01)
+
+
+def test_traffic_is_taken_only_for_the_profiled_source_and_tiling(tmp_path, monkeypatch):
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_hash", lambda: "abc")
+    p = prof / "k_step_staged_roofline.json"
+    p.write_text(json.dumps({"kernel_hash": "abc", "dram_bytes_per_launch_by_grid": {"4002": 5.0e8}}))
+    assert bench.traffic_per_launch("k_step_staged", "roofline", 4002) == 5.0e8
+    assert bench.traffic_per_launch("k_step_staged", "roofline", 4350) is None
+    p.write_text(json.dumps({"kernel_hash": "abc", "dram_bytes_per_launch": 6.0e8}))
+    assert bench.traffic_per_launch("k_step_staged", "roofline", 1) == 6.0e8
+    p.write_text(json.dumps({"kernel_hash": "old", "dram_bytes_per_launch": 6.0e8}))
+    assert bench.traffic_per_launch("k_step_staged", "roofline", 1) is None
+    assert bench.traffic_per_launch("k_step", "roofline", 1) is None
+
+
+def test_the_committed_profile_matches_the_committed_kernel_source():
+    with open(os.path.join(ROOT, "profiles", "k_step_staged_roofline.json")) as f:
+        p = json.load(f)
+    assert p["kernel_hash"] == bench.kernel_hash()
+
+
+def test_reference_arm_prints_one_contract_line():
+    env = dict(os.environ, PYTHONPATH=ROOT, OMP_NUM_THREADS="1")
+    res = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "tiny",
+                          "--steps", "4", "--warmup", "3"], cwd=ROOT, env=env, capture_output=True, text=True,
+                         timeout=600)
+    assert res.returncode == 0, res.stderr[-2000:]
+    lines = [ln for ln in res.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["higher_is_better"] is True and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
