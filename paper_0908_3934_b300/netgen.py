@@ -320,6 +320,18 @@ def fig2(delay_steps, t_on_ms: float = 10.0, amp: float = 1.0) -> NetSpec:
                    pulses=[(0, t_on_ms, t_on_ms + 2.0, amp)], name="fig2")
 
 
+def fig2_hh(w_scale: float = 10.0, dt_ms: float = 0.03, gap_ms: float = 200.0, pulse_amp: float = 20.0) -> NetSpec:
+    """The Fig. 2 experiment: the five-vertex network with Hodgkin-Huxley nodes at
+    dt_ms, its printed delays quantised to whole steps (half up), its printed weights
+    x w_scale (uA/cm^2), and a 2 ms pulse on each vertex in turn, gap_ms apart from
+    100 ms on (the figure's sequential stimulation)."""
+    delay = [int(math.floor(e[2] / dt_ms + 0.5)) for e in FIG2_EDGES]
+    base = fig2(delay)
+    pulses = [(j, 100.0 + gap_ms * j, 102.0 + gap_ms * j, pulse_amp) for j in range(5)]
+    spec = hodgkin_huxley(base, w_scale=w_scale, dt_ms=dt_ms)
+    return dataclasses.replace(spec, pulses=pulses, delay=np.asarray(delay, np.int32), name="fig2_hh")
+
+
 def chain2(dist_mm: float = 0.5, speed: float = 0.1, t_on_ms: float = 5.0, w: float = 0.5,
            dt_ms: float = 0.05) -> NetSpec:
     """Two nodes on the x axis, one edge 0 -> 1, a pulse on node 0."""

@@ -117,3 +117,19 @@ def test_test_set_networks_at_the_hh_step(cls):
     print("worst ratios", worst)
     assert_windows(worst)
     assert n_spikes > 20
+
+
+def test_fig2_experiment_one_second_spikes_exact():
+    """The Fig. 2 experiment (Sec. 3): the five-vertex network with Hodgkin-Huxley
+    nodes, its printed delays and weights, a pulse on each vertex in turn, one second
+    (33,334 steps) from rest without re-synchronising: the same spikes, step for step,
+    and the same first spikes as the oracle."""
+    spec = netgen.fig2_hh()
+    n = 33334
+    ref = oracle.simulate(spec, n, ev_cap=10000, want_y=False)
+    assert ref["ev_count"] >= 10 and ref["min_peak_gap"].min() > 1e-2
+    net = geonet.Net(spec)
+    net.gn_step(n)
+    node, step, _ = net.gn_get_events()
+    assert sorted(zip(node.tolist(), step.tolist())) == sorted(zip(ref["ev_node"].tolist(), ref["ev_step"].tolist()))
+    assert np.array_equal(net.gn_get_arrivals(), ref["first_arrival"].astype(np.int64))

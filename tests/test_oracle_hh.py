@@ -146,3 +146,29 @@ def test_hh_ring_equals_dense_history():
     assert a["ev_count"] > 20
     for k in ("v", "m", "n", "h", "c", "r", "p", "y", "first_arrival", "ev_node", "ev_step"):
         assert np.array_equal(a[k], b[k]), k
+
+
+def test_fig2_cascade_follows_the_printed_delays():
+    """Fig. 2 (Sec. 3): the five-vertex network with Hodgkin-Huxley nodes, its printed
+    delays and weights (x 10), a pulse on each vertex in turn.  The pulse on vertex 1
+    sets off the cascade 1 -> 3 -> 5, 3 -> 2 -> 4 along the excitatory edges, each
+    spike later than its source's by more than the printed delay; the synaptic input
+    p of a vertex whose only earlier input is one edge leaves 0 exactly D + 1 steps
+    after its source's first spike (Eq. izpsc, with D = round(delay / dt))."""
+    spec = netgen.fig2_hh()
+    assert spec.delay.tolist() == [120, 247, 127, 87, 160, 113, 120, 147]
+    r = oracle.simulate(spec, 33334, ev_cap=10000, want_y=False)
+    first = {}
+    for n, j in sorted(zip(r["ev_step"].tolist(), r["ev_node"].tolist())):
+        first.setdefault(j + 1, n)
+    order = sorted(first, key=first.get)
+    assert order == [1, 3, 5, 2, 4]
+    dt = spec.dt_ms
+    for a, b, d_ms in ((1, 3, 7.4), (3, 5, 3.6), (3, 2, 3.8), (2, 4, 2.6)):
+        assert (first[b] - first[a]) * dt > d_ms
+    D = dict(((e[0], e[1]), int(spec.delay[k])) for k, e in enumerate(netgen.FIG2_EDGES))
+    for a, b in ((1, 3), (1, 2), (3, 5), (2, 4)):
+        n = first[a] + D[(a, b)]
+        before = oracle.simulate(spec, n, want_y=False)
+        after = oracle.simulate(spec, n + 1, want_y=False)
+        assert before["p"][b - 1] == 0.0 and after["p"][b - 1] != 0.0, (a, b)
