@@ -91,11 +91,17 @@ def peaks():
 
 
 def kernel_hash() -> str:
+    """Hash of the step kernels' code: comments and layout do not count, so a
+    profile stays tied to the code it was taken on across comment edits."""
+    import re
     h = hashlib.sha256()
     for f in ("k_step.cu", "k_step_pipe.cu", "k_step_staged.cu", "staged.cu", "step_common.cuh", "ptx.cuh",
               "internal.cuh", "philox.cuh"):
-        with open(os.path.join(ROOT, "paper_0908_3934_b300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_0908_3934_b300", "csrc", f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)   # block comments
+        src = re.sub(r"//[^\n]*", " ", src)                 # line comments
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -7,13 +7,16 @@
 //      threads load the piece list and caller id of their row;
 //   1. once the copies have landed, the CTA fetches each distinct history value its
 //      edges read, v~_src(n - D) from ring slot (n - D) & (R - 1), once, into shared
-//      memory.  Slot n - D (D >= 1) was written by step n - D - 1 <= n - 2, so the
-//      batched FitzHugh-Nagumo kernel does this and step 2 before it waits for the
-//      previous step (griddepcontrol.wait) and lets the next one start
-//      (griddepcontrol.launch_dependents) -- both just before step 3, when step
-//      n - 1 is complete -- and the gathers of one step overlap the end of the
-//      previous one.  The other kernels let the next step start at once (its
-//      prologue overlaps this step) and wait before step 1.
+//      memory.  Slot n - D (D >= 1) was written by step n - D - 1 <= n - 2, so a
+//      kernel that gathers early (kEarly) does this and step 2 before it waits for
+//      the previous step (griddepcontrol.wait), just before step 3, when step n - 1
+//      is complete; the gathers of one step then overlap the end of the previous
+//      one.  Batches always gather early; a single static network does so when its
+//      grid outnumbers the CTAs the device holds at once.  Such a large grid lets
+//      the next step start first thing (kLaunchFirst: its first CTAs only fill the
+//      SMs this grid's last wave leaves free); a smaller early batch grid does so
+//      just before step 3.  Plastic networks and small single-network grids let
+//      the next step start at once and wait before step 1.
 //      The gathers are sorted by (D, src), so a warp's 32 reads fall in a few lines
 //      of one ring slot.  While they are in flight, a spiking node (Izhikevich,
 //      Hodgkin-Huxley) runs every part of its update that does not read S -- all
@@ -74,7 +77,7 @@ __device__ __forceinline__ void staged_tile(const StepArgs &a, const int tile, c
     uint16_t *s_u = reinterpret_cast<uint16_t *>(s_w + a.st_xcap);
     float *s_part = kSE ? reinterpret_cast<float *>(s_u + a.st_xcap) : s_w;
 
-    // kEarly (FitzHugh-Nagumo only): the gathers of step n read history slots
+    // kEarly (static weights, any node model): the gathers of step n read history slots
     // n - D <= n - 1, all written by step n - 2 or earlier, so the CTA fetches and
     // sums them before griddepcontrol.wait and waits only before the node update
     // (its rows' state is step n - 1's).  That needs step n - 2 complete when the

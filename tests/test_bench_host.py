@@ -39,6 +39,21 @@ def test_traffic_is_taken_only_for_the_profiled_source_and_tiling(tmp_path, monk
     assert bench.traffic_per_launch("k_step", "roofline", 1) is None
 
 
+def test_kernel_hash_ignores_comments_and_layout_only(tmp_path, monkeypatch):
+    import shutil
+    src = os.path.join(ROOT, "paper_0908_3934_b300", "csrc")
+    dst = tmp_path / "paper_0908_3934_b300" / "csrc"
+    shutil.copytree(src, dst)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.kernel_hash()
+    f = dst / "k_step_staged.cu"
+    code = f.read_text()
+    f.write_text("// a new comment\n/* and a\n block */\n" + code.replace(";\n", ";   \n", 3))
+    assert bench.kernel_hash() == h0
+    f.write_text(code.replace("kThreadsL2 = 1280", "kThreadsL2 = 1024"))
+    assert bench.kernel_hash() != h0
+
+
 def test_reference_arm_prints_one_contract_line():
     env = dict(os.environ, PYTHONPATH=ROOT, OMP_NUM_THREADS="1")
     res = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "tiny",
