@@ -233,8 +233,9 @@ def config_of(args, spec, world):
 
 def run_batched(args, local, stream, rank):
     """4096 independent 2D networks (N log-uniform in [32, 4096]) advanced
-    `batch_steps` steps by one persistent launch, against looping the
-    single-network path over a random sample of the same networks."""
+    `batch_steps` steps by the batched form (the kernel and schedule its first
+    step times), against looping the single-network path over a random sample of
+    the same networks."""
     import torch
     from paper_0908_3934_b300 import geonet
     specs = workload("batch", rank)
@@ -274,8 +275,13 @@ def run_batched(args, local, stream, rank):
             "value": E * steps / t, "unit": METRIC, "seconds": t, "ms_per_step": t / steps * 1e3,
             "rtf": steps * 0.05e-3 / t, "cta_threads": info["cta_threads"], "grid": info["grid"],
             "step_kernel": info["step_kernel"],
-            # kernel 1: one persistent launch; kernel 3: one per step + one advance per 64-step graph
-            "gpu_launches": 1 if info["step_kernel"] == 1 else steps + (steps + 63) // 64,
+            # kernel 3: member groups stepped a 64-step chunk at a time (L2 blocking), in lanes
+            # of concurrent launch chains; 1 group = every member every step
+            "step_groups": info["step_groups"], "step_lanes": info["step_lanes"],
+            # kernel 1: one persistent launch; kernel 3: one per group and step + one advance per
+            # 64-step graph (and per ragged tail)
+            "gpu_launches": 1 if info["step_kernel"] == 1
+            else steps * max(1, info["step_groups"]) + (steps + 63) // 64,
             "loop_plain": {"value": E * steps / t_loop, "seconds_extrapolated": t_loop,
                            "sample": f"{len(pick)} random nets timed one after another, "
                                      f"{t_sample:.3f} s, extrapolated by count to {len(specs)}"},
@@ -562,7 +568,7 @@ def main():
     t_sim = (net.gn_net_get_info()["step"] + chunk) * spec.dt_ms
     pulses = [[(int(j), t_sim + (c * chunk + rng.uniform(0, chunk)) * spec.dt_ms,
                 t_sim + (c * chunk + rng.uniform(0, chunk)) * spec.dt_ms + 2.0, 1.0)
-               for j in rng.choice(N, 1000, replace=False)] for c in range(n_chunks + 1)]
+               for j in rng.choice(N, min(N, 1000), replace=False)] for c in range(n_chunks + 1)]
     max_rows = min(args.obs_cap, chunk // spec.obs["sample_every"] + 1)
     # two pinned buffers: the observations of one chunk are copied back while the
     # next chunk steps (gn_observe_async), each buffer reused only after its copy

@@ -358,6 +358,9 @@ typedef struct {
     size_t device_bytes;
     int32_t step_kernel;         /* 1: persistent k_batch, one launch per gn_batch_step; 3: staged tiles of
                                     every member, one launch per step; 0 before the first step */
+    int32_t step_groups;         /* kernel 3: member groups, each stepped through a 64-step chunk at a time
+                                    (1: every member every step; see gn_batch_step); else 0 */
+    int32_t step_lanes;          /* kernel 3: groups stepped concurrently (one chain of launches each); else 0 */
 } gn_batch_info;
 
 /* Copy and build n_nets networks on one device (descs[i].device must agree; the
@@ -378,8 +381,18 @@ GN_API gn_status gn_batch_set_background(gn_batch *batch, int32_t net, double ra
 /* Advance every network n_steps (asynchronous): one persistent launch (kernel 1)
  * or one launch per step replayed from a captured graph (kernel 3), whichever the
  * first call measured faster; GN_BATCH_KERNEL=1 or 3 in the environment restricts
- * the choice.  Both sum a node's inputs in the order of the single-network kernels,
- * so results are bit-identical either way. */
+ * the choice.  Kernel 3 has several schedules, also timed on the first call:
+ * every member every step, or (L2 blocking) contiguous groups of members, each
+ * group stepped through the 64 steps of a graph chunk at a time so that its steps
+ * read from L2, with 1, 2 or 4 groups in flight at once (lanes: one chain of
+ * launches each, on streams forked from the batch's stream).  The groups in flight
+ * share an L2 budget for their per-step working sets -- edge entries, gather keys,
+ * live history slots, node state -- of GN_BATCH_GROUP_KB (default 80 MB; 0 turns
+ * the blocking off); GN_BATCH_LANES=1..8 fixes the lanes and GN_BATCH_KERNEL=4
+ * takes the blocked schedule without timing.  The networks are independent, so
+ * neither the kernel nor the schedule changes a result: both sum a node's inputs
+ * in the order of the single-network kernels, and results are bit-identical
+ * either way.  Spiking batches run kernel 3. */
 GN_API gn_status gn_batch_step(gn_batch *batch, int64_t n_steps);
 GN_API gn_status gn_batch_synchronize(gn_batch *batch);
 

@@ -14,7 +14,21 @@
 // graph).  Both sum a node's inputs in the order every step kernel uses, so the
 // choice never changes a result.  The first gn_batch_step picks the kernel (and
 // k_batch's CTA size) by timing the candidates on a scratch copy of the dynamic
-// state; GN_BATCH_KERNEL=1 or 3 restricts the choice to k_batch or the staged form.
+// state; GN_BATCH_KERNEL=1 or 3 restricts the choice to k_batch or the staged form
+// (4: the staged form with L2 blocking, below).
+//
+// L2 blocking of the staged form.  When the members' per-step working set (edge
+// entries, gather keys, live history slots, node state) outgrows L2, every step
+// re-reads it from DRAM.  The members are then cut into contiguous groups, and a
+// graph chunk runs each group's steps back to back: members are independent, so a
+// group may run ahead of the others within the chunk, and after the chunk's first
+// step a group's steps read its data from L2.  A group smaller than a wave of CTAs
+// leaves SMs idle between its steps, so 1, 2 or 4 groups run at once (lanes), each
+// lane a chain of launches on its own stream; the groups in flight share the L2
+// budget.  The launches are the same kernel over a group's tiles (its members'
+// tile pointers start at the group's first tile), so grouping never changes a
+// result either; the first gn_batch_step times the schedules with the other
+// candidates.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -35,6 +49,17 @@ namespace {
 
 constexpr int kGraphSteps = 64;             // staged form: steps per captured graph
 constexpr int kStaged = gn::kNumBatchShapes;  // shape index of the staged form
+// per-step working set of a member beyond its edge structure, per node: the live
+// history slots (max delay + 2, 4 bytes each) come on top of these node-state bytes
+// (w and readout 8, background counter 4, arrival step 8, caller id 4, sample 4)
+constexpr double kNodeStateBytes = 28.0;
+constexpr double kDefaultGroupBytes = 80e6;  // L2 budget of the groups stepped at once (L2 is 126 MB)
+
+// One group of the staged form's L2 blocking: tiles [t0, t0 + nt) of the pool.
+struct StGroup {
+    int t0 = 0, nt = 0;
+    bool first = false;  // its grid outnumbers the resident CTAs: launch the next grid first
+};
 
 // Host view of one member network.
 struct Member {
@@ -48,6 +73,8 @@ struct Member {
     int64_t node_off = 0, ring_off = 0, edge_off = 0, keyw_off = 0, rp_off = 0, obs_off = 0, ev_off = 0;
     int64_t ev_cap = 0, pulse_off = 0, pulse_cap = 0, read_cursor = 0;
     int64_t desc_off[gn::kNumBatchShapes] = {};
+    int32_t st_t0 = 0, st_nt = 0;  // staged form: the member's tiles in the pool
+    double st_bytes = 0.0;         // ... and the bytes of its entries and gather keys
     int32_t n_blocks[gn::kNumBatchShapes] = {};
     std::vector<int32_t> perm, inv, delay;
 };
@@ -80,7 +107,11 @@ struct gn_batch {
     int64_t graph_steps = 0;
     // staged form: pooled layouts of every member (tile_net: member of each tile)
     bool staged_ok = false, st_packed = true, st_stream = false;
-    bool st_first = false;  // the staged grid outnumbers the resident CTAs: launch the next grid first
+    bool st_big = false;      // the ungrouped structure outgrows L2: stream it with evict-first loads
+    std::vector<StGroup> st_groups;  // chosen schedule: one group of every tile, or L2-sized groups
+    int st_lanes = 1;                // groups stepped concurrently, one chain of launches per lane
+    std::vector<cudaStream_t> lane_stream;  // lanes 1, 2, ... (lane 0 runs on the batch's stream)
+    std::vector<cudaEvent_t> lane_event;    // fork, then one join per extra lane
     int n_tiles = 0;
     size_t st_smem = 0;
     DevArray<int4> st_tile, st_tile2;
@@ -126,6 +157,8 @@ struct gn_batch {
         obs_acc.release();
         cell.release();
         type_par.release();
+        for (cudaStream_t x : lane_stream) cudaStreamDestroy(x);
+        for (cudaEvent_t x : lane_event) cudaEventDestroy(x);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 };
@@ -149,39 +182,130 @@ void sync(gn_batch *b)
     }
 }
 
-// Device array of step arguments for a CTA shape (block descriptors differ per shape).
-std::vector<gn::StepArgs> args_for_shape(const gn_batch *b, int shape)
+// The block-descriptor shape of the step arguments: the persistent kernel's chosen
+// CTA size, else the first (the staged form reads no block descriptors).
+int desc_shape(const gn_batch *b) { return b->shape >= 0 && b->shape < gn::kNumBatchShapes ? b->shape : 0; }
+
+// Step arguments for a CTA shape (block descriptors differ per shape) and a staged
+// schedule: a member's tile pointers start at its group's first tile, the tile its
+// group's launches number 0.
+std::vector<gn::StepArgs> args_for(const gn_batch *b, int shape, const std::vector<StGroup> &groups)
 {
     std::vector<gn::StepArgs> out = b->args;
+    size_t g = 0;
     for (int i = 0; i < b->n_nets; ++i) {
         out[i].bdesc = b->bdesc[shape].p + b->m[i].desc_off[shape];
         out[i].n_blocks = b->m[i].n_blocks[shape];
+        if (!b->staged_ok) continue;
+        while (g + 1 < groups.size() && b->m[i].st_t0 >= groups[g + 1].t0) ++g;
+        const int t0 = groups.empty() ? 0 : groups[g].t0;
+        out[i].st_tile = b->st_tile.p + t0;
+        out[i].st_tile2 = b->st_tile2.p + t0;
     }
     return out;
 }
 
-void upload_args(gn_batch *b, int shape)
+void upload_args(gn_batch *b)
 {
-    const std::vector<gn::StepArgs> a = args_for_shape(b, shape);
+    const std::vector<gn::StepArgs> a = args_for(b, desc_shape(b), b->st_groups);
     cuda_check(cudaMemcpy(b->d_args.p, a.data(), a.size() * sizeof(gn::StepArgs), cudaMemcpyHostToDevice), "H2D args");
 }
 
-void set_shape(gn_batch *b, int shape)
+// L2 budget in bytes of the groups stepped at once (each of `lanes` groups takes
+// an equal share): GN_BATCH_GROUP_KB in the environment (0 turns the L2 blocking
+// off), else kDefaultGroupBytes.
+double group_budget()
+{
+    const char *e = getenv("GN_BATCH_GROUP_KB");
+    if (e && *e) return std::max(0.0, atof(e)) * 1024.0;
+    return kDefaultGroupBytes;
+}
+
+// Lanes fixed by GN_BATCH_LANES in the environment (1 to 8), else 0.
+int lanes_env()
+{
+    const char *e = getenv("GN_BATCH_LANES");
+    if (!e || !*e) return 0;
+    const int l = atoi(e);
+    if (l < 1 || l > 8) fail(GN_EINVAL, "GN_BATCH_LANES must be 1 to 8");
+    return l;
+}
+
+// Contiguous groups of members whose per-step working sets fit `budget` bytes
+// (a member larger than the budget is a group of its own); one group of every tile
+// when budget <= 0.
+std::vector<StGroup> make_groups(const gn_batch *b, double budget)
+{
+    std::vector<StGroup> g;
+    double acc = 0.0;
+    int t0 = 0;
+    for (const Member &mm : b->m) {
+        const double live = std::min(mm.R, mm.dmax + 2);
+        const double ws = mm.st_bytes + static_cast<double>(mm.N) * (4.0 * live + kNodeStateBytes);
+        if (budget > 0.0 && acc > 0.0 && acc + ws > budget && mm.st_t0 > t0) {
+            g.push_back({t0, mm.st_t0 - t0, false});
+            t0 = mm.st_t0;
+            acc = 0.0;
+        }
+        acc += ws;
+    }
+    if (b->n_tiles > t0) g.push_back({t0, b->n_tiles - t0, false});
+    return g;
+}
+
+// Prepare the staged kernel for the batch's format and stream setting and mark the
+// groups whose grid outnumbers the CTAs the device holds at once (those launch the
+// next grid first; GN_STAGED_EARLY=0 turns that off).
+void prepare_staged(gn_batch *b, std::vector<StGroup> &groups)
+{
+    int per_sm = 0, sms = 0;
+    cuda_check(gn::batch_staged_prepare(b->model, b->st_packed, b->st_stream, b->st_smem, &per_sm),
+               "staged kernel setup");
+    cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device), "device query");
+    const char *e = getenv("GN_STAGED_EARLY");
+    const bool off = e && *e == '0';
+    for (StGroup &g : groups)
+        g.first = !off && per_sm > 0 && static_cast<int64_t>(g.nt) > static_cast<int64_t>(per_sm) * sms;
+}
+
+void drop_graph(gn_batch *b)
+{
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+}
+
+// Streams and events of `lanes` concurrent chains (created once, kept until the
+// batch is destroyed).
+void ensure_lanes(gn_batch *b, int lanes)
+{
+    while (static_cast<int>(b->lane_stream.size()) < lanes - 1) {
+        cudaStream_t x = nullptr;
+        cuda_check(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking), "cudaStreamCreate");
+        b->lane_stream.push_back(x);
+    }
+    while (static_cast<int>(b->lane_event.size()) < lanes) {
+        cudaEvent_t x = nullptr;
+        cuda_check(cudaEventCreateWithFlags(&x, cudaEventDisableTiming), "cudaEventCreate");
+        b->lane_event.push_back(x);
+    }
+}
+
+void set_shape(gn_batch *b, int shape, bool grouped, int lanes)
 {
     if (shape == kStaged) {
-        int per_sm = 0, sms = 0;
-        cuda_check(gn::batch_staged_prepare(b->model, b->st_packed, b->st_stream, b->st_smem, &per_sm),
-                   "staged kernel setup");
-        cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device), "device query");
-        b->st_first = per_sm > 0 && static_cast<int64_t>(b->n_tiles) > static_cast<int64_t>(per_sm) * sms;
-        if (const char *e = getenv("GN_STAGED_EARLY"); e && *e == '0') b->st_first = false;
+        // grouped members keep their structure in L2 across the chunk; otherwise a
+        // structure larger than L2 is streamed past the history
+        b->st_stream = grouped ? false : b->st_big;
+        b->st_groups = make_groups(b, grouped ? group_budget() / lanes : 0.0);
+        b->st_lanes = grouped ? lanes : 1;
+        ensure_lanes(b, b->st_lanes);
+        prepare_staged(b, b->st_groups);
         b->shape = kStaged;
         b->grid = b->n_tiles;
-        upload_args(b, 0);
-        if (b->graph) {
-            cudaGraphExecDestroy(b->graph);
-            b->graph = nullptr;
-        }
+        upload_args(b);
+        drop_graph(b);
         return;
     }
     int per_sm = 0, sms = 0;
@@ -190,21 +314,46 @@ void set_shape(gn_batch *b, int shape)
     if (per_sm < 1) fail(GN_ECUDA, "the batch kernel does not fit on an SM");
     b->shape = shape;
     b->grid = std::max(1, std::min(b->n_nets, per_sm * sms));
-    upload_args(b, shape);
-    if (b->graph) {
-        cudaGraphExecDestroy(b->graph);
-        b->graph = nullptr;
+    b->st_groups.clear();
+    b->st_lanes = 1;
+    upload_args(b);
+    drop_graph(b);
+}
+
+// Steps k0 .. k0 + n - 1 of the staged form.  Group g runs in lane g % lanes; a
+// lane steps its groups one after another, each through all n steps, as one chain
+// of launches on its own stream (lane 0 on s, the others forked from s and joined
+// back into it).  Lanes touch disjoint members, so they need no ordering.
+cudaError_t launch_staged(const gn_batch *b, const gn::StepArgs *args, const std::vector<StGroup> &groups, int lanes,
+                          int k0, int n, cudaStream_t s)
+{
+    lanes = std::max(1, std::min(lanes, static_cast<int>(groups.size())));
+    cudaError_t e = cudaSuccess;
+    if (lanes > 1) {
+        e = cudaEventRecord(b->lane_event[0], s);
+        for (int l = 1; l < lanes && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(b->lane_stream[l - 1], b->lane_event[0], 0);
     }
+    for (int l = 0; l < lanes && e == cudaSuccess; ++l) {
+        cudaStream_t ls = l == 0 ? s : b->lane_stream[l - 1];
+        for (size_t gi = l; gi < groups.size() && e == cudaSuccess; gi += lanes) {
+            const StGroup &g = groups[gi];
+            for (int k = k0; k < k0 + n && e == cudaSuccess; ++k)
+                e = gn::launch_batch_staged(b->model, args, b->st_tile_net.p + g.t0, g.nt, k, b->st_packed,
+                                            b->st_stream, b->st_smem, g.first, ls);
+        }
+    }
+    for (int l = 1; l < lanes && e == cudaSuccess; ++l) {
+        e = cudaEventRecord(b->lane_event[l], b->lane_stream[l - 1]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->lane_event[l], 0);
+    }
+    return e;
 }
 
 void launch_steps(gn_batch *b, const gn::StepArgs *args, int64_t *d_step, int n_steps, int shape, int grid,
-                  cudaStream_t s)
+                  const std::vector<StGroup> &groups, int lanes, cudaStream_t s)
 {
     if (shape == kStaged) {
-        for (int k = 0; k < n_steps; ++k)
-            cuda_check(gn::launch_batch_staged(b->model, args, b->st_tile_net.p, b->n_tiles, k, b->st_packed,
-                                               b->st_stream, b->st_smem, b->st_first, s),
-                       "staged batch launch");
+        cuda_check(launch_staged(b, args, groups, lanes, 0, n_steps, s), "staged batch launch");
         return;
     }
     cuda_check(cudaMemsetAsync(b->queue.p, 0, 4, s), "queue reset");
@@ -212,13 +361,59 @@ void launch_steps(gn_batch *b, const gn::StepArgs *args, int64_t *d_step, int n_
                "batch launch");
 }
 
-// Time each candidate (k_batch in each CTA shape, the staged form) for a few steps
-// on a scratch copy of the dynamic state.
+// An executable graph of the launches `body` issues on a capturing stream.
+template <class F>
+cudaGraphExec_t capture_graph(F &&body)
+{
+    cudaStream_t cs;
+    cuda_check(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "cudaStreamCreate");
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        e = body(cs);
+        cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    cuda_check(e, "graph capture of the batch step");
+    return ge;
+}
+
+// Time each candidate (k_batch in each CTA shape, the staged form with and without
+// L2 blocking) per step on a scratch copy of the dynamic state: k_batch over 16
+// steps in one launch, the staged form over one graph chunk replayed from a graph
+// as gn_batch_step runs it (a chunk of many small groups issues thousands of
+// launches, which direct launches would time as host work).  A single candidate is
+// taken untimed.
 void autotune(gn_batch *b, bool persistent, bool staged)
 {
+    struct Cand {
+        int shape;
+        bool grouped;
+        int lanes;
+    };
+    std::vector<Cand> cands;
+    if (persistent)
+        for (int shape = 0; shape < gn::kNumBatchShapes; ++shape) cands.push_back({shape, false, 1});
+    if (staged && b->staged_ok) {
+        cands.push_back({kStaged, false, 1});
+        const int fixed = lanes_env();
+        for (int lanes : {1, 2, 4})
+            if ((!fixed || lanes == fixed) && make_groups(b, group_budget() / lanes).size() > 1)
+                cands.push_back({kStaged, true, lanes});
+    }
+    if (cands.empty()) fail(GN_EINVAL, "no batch kernel can step this batch");
+    if (cands.size() == 1) {
+        set_shape(b, cands[0].shape, cands[0].grouped, cands[0].lanes);
+        return;
+    }
     size_t tmp = 0;
-    DevArray<float> ring, obs, facc;
-    DevArray<float2> wc;
+    DevArray<float> ring, obs, facc, izv;
+    DevArray<float2> wc, rpv;
+    DevArray<float4> hhg;
     DevArray<int32_t> bgc, evn;
     DevArray<int64_t> first, evs, dstep;
     DevArray<unsigned long long> evc;
@@ -227,10 +422,11 @@ void autotune(gn_batch *b, bool persistent, bool staged)
     auto cleanup = [&] {
         ring.release(); obs.release(); wc.release(); bgc.release(); evn.release(); first.release();
         evs.release(); dstep.release(); evc.release(); dargs.release(); facc.release();
+        izv.release(); rpv.release(); hhg.release();
         if (t0) cudaEventDestroy(t0);
         if (t1) cudaEventDestroy(t1);
     };
-    int best = 0;
+    Cand best = cands[0];
     try {
         int64_t total_nodes = 0;
         for (const Member &mm : b->m) total_nodes += mm.N;
@@ -253,14 +449,36 @@ void autotune(gn_batch *b, bool persistent, bool staged)
         cuda_check(cudaMemset(bgc.p, 0, bgc.n * 4), "memset");
         cuda_check(cudaMemset(first.p, 0xff, first.n * 8), "memset");
         cuda_check(cudaMemset(evc.p, 0, evc.n * 8), "memset");
+        if (b->model != GN_MODEL_FHN) {  // spiking state, copied so the candidates step a live network
+            izv.alloc(b->iz_v.n, &tmp);
+            rpv.alloc(b->rp.n, &tmp);
+            cuda_check(cudaMemcpy(izv.p, b->iz_v.p, izv.n * 4, cudaMemcpyDeviceToDevice), "D2D");
+            cuda_check(cudaMemcpy(rpv.p, b->rp.p, rpv.n * 8, cudaMemcpyDeviceToDevice), "D2D");
+            if (b->hh_g.p) {
+                hhg.alloc(b->hh_g.n, &tmp);
+                cuda_check(cudaMemcpy(hhg.p, b->hh_g.p, hhg.n * 16, cudaMemcpyDeviceToDevice), "D2D");
+            }
+        }
         cuda_check(cudaMemcpy(dstep.p, &b->step, 8, cudaMemcpyHostToDevice), "H2D");
         cuda_check(cudaEventCreate(&t0), "event");
         cuda_check(cudaEventCreate(&t1), "event");
         float best_ms = 1e30f;
-        best = persistent ? 0 : kStaged;
-        for (int shape = 0; shape <= kStaged; ++shape) {
-            if (shape == kStaged ? !(staged && b->staged_ok) : !persistent) continue;
-            std::vector<gn::StepArgs> a = args_for_shape(b, shape == kStaged ? 0 : shape);
+        for (const Cand &c : cands) {
+            std::vector<StGroup> groups;
+            int grid = b->n_tiles, steps = 16;
+            if (c.shape == kStaged) {
+                b->st_stream = c.grouped ? false : b->st_big;
+                groups = make_groups(b, c.grouped ? group_budget() / c.lanes : 0.0);
+                prepare_staged(b, groups);
+                ensure_lanes(b, c.lanes);
+                steps = kGraphSteps;
+            } else {
+                int per_sm = 0, sms = 0;
+                cuda_check(gn::batch_occupancy(c.shape, &per_sm), "occupancy");
+                cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device), "device query");
+                grid = std::max(1, std::min(b->n_nets, per_sm * sms));
+            }
+            std::vector<gn::StepArgs> a = args_for(b, c.shape == kStaged ? 0 : c.shape, groups);
             for (int i = 0; i < b->n_nets; ++i) {
                 const Member &mm = b->m[i];
                 a[i].ring = ring.p + mm.ring_off;
@@ -274,28 +492,40 @@ void autotune(gn_batch *b, bool persistent, bool staged)
                 a[i].ev_count = evc.p + i;
                 a[i].ev_cap = 1;
                 if (a[i].obs_acc) a[i].obs_acc = facc.p + mm.node_off;
+                if (izv.p) {
+                    a[i].iz_v = izv.p + mm.node_off;
+                    a[i].rp = rpv.p + mm.node_off;
+                    if (hhg.p) a[i].hh_g = hhg.p + mm.node_off;
+                }
             }
             cuda_check(cudaMemcpy(dargs.p, a.data(), a.size() * sizeof(gn::StepArgs), cudaMemcpyHostToDevice), "H2D");
-            int grid = b->n_tiles;
-            if (shape == kStaged) {
-                cuda_check(gn::batch_staged_prepare(b->model, b->st_packed, b->st_stream, b->st_smem, nullptr),
-                           "staged kernel setup");
+            cudaGraphExec_t ge = nullptr;
+            if (c.shape == kStaged) {
+                ge = capture_graph([&](cudaStream_t cs) {
+                    return launch_staged(b, dargs.p, groups, c.lanes, 0, steps, cs);
+                });
+                const cudaError_t e = cudaGraphLaunch(ge, b->stream);  // warm-up
+                if (e != cudaSuccess) cudaGraphExecDestroy(ge);
+                cuda_check(e, "cudaGraphLaunch");
             } else {
-                int per_sm = 0, sms = 0;
-                cuda_check(gn::batch_occupancy(shape, &per_sm), "occupancy");
-                cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device), "device query");
-                grid = std::max(1, std::min(b->n_nets, per_sm * sms));
+                launch_steps(b, dargs.p, dstep.p, 2, c.shape, grid, groups, c.lanes, b->stream);
             }
-            launch_steps(b, dargs.p, dstep.p, 2, shape, grid, b->stream);
-            cuda_check(cudaEventRecord(t0, b->stream), "event");
-            launch_steps(b, dargs.p, dstep.p, 16, shape, grid, b->stream);
-            cuda_check(cudaEventRecord(t1, b->stream), "event");
-            cuda_check(cudaEventSynchronize(t1), "autotune");
+            cudaError_t e = cudaEventRecord(t0, b->stream);
+            if (e == cudaSuccess) {
+                if (ge)
+                    e = cudaGraphLaunch(ge, b->stream);
+                else
+                    launch_steps(b, dargs.p, dstep.p, steps, c.shape, grid, groups, c.lanes, b->stream);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(t1, b->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+            if (ge) cudaGraphExecDestroy(ge);
+            cuda_check(e, "autotune");
             float ms = 0.0f;
             cuda_check(cudaEventElapsedTime(&ms, t0, t1), "event");
-            if (ms < best_ms) {
-                best_ms = ms;
-                best = shape;
+            if (ms / steps < best_ms) {
+                best_ms = ms / steps;
+                best = c;
             }
         }
     } catch (...) {
@@ -303,24 +533,16 @@ void autotune(gn_batch *b, bool persistent, bool staged)
         throw;
     }
     cleanup();
-    set_shape(b, best);
+    set_shape(b, best.shape, best.grouped, best.lanes);
 }
 
 void build_graph(gn_batch *b, int64_t n_steps)
 {
-    if (b->graph) {
-        cudaGraphExecDestroy(b->graph);
-        b->graph = nullptr;
-    }
-    cudaStream_t cs;
-    cuda_check(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "cudaStreamCreate");
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
+    drop_graph(b);
+    b->graph = capture_graph([&](cudaStream_t cs) {
+        cudaError_t e;
         if (b->shape == kStaged) {
-            for (int k = 0; k < n_steps && e == cudaSuccess; ++k)
-                e = gn::launch_batch_staged(b->model, b->d_args.p, b->st_tile_net.p, b->n_tiles, k, b->st_packed,
-                                            b->st_stream, b->st_smem, b->st_first, cs);
+            e = launch_staged(b, b->d_args.p, b->st_groups, b->st_lanes, 0, static_cast<int>(n_steps), cs);
         } else {
             e = cudaMemsetAsync(b->queue.p, 0, 4, cs);
             if (e == cudaSuccess)
@@ -328,13 +550,8 @@ void build_graph(gn_batch *b, int64_t n_steps)
                                      static_cast<int>(n_steps), b->shape, b->grid, cs);
         }
         if (e == cudaSuccess) e = gn::launch_advance(b->d_step.p, n_steps, cs);
-        cudaError_t e2 = cudaStreamEndCapture(cs, &g);
-        if (e == cudaSuccess) e = e2;
-    }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
-    if (g) cudaGraphDestroy(g);
-    cudaStreamDestroy(cs);
-    cuda_check(e, "graph capture of the batch step");
+        return e;
+    });
     b->graph_steps = n_steps;
 }
 
@@ -375,6 +592,9 @@ std::vector<int64_t> build_staged_pool(gn_batch *b, const std::vector<gnrt::Host
             b->staged_ok = false;
             return rq_off;
         }
+        b->m[i].st_t0 = static_cast<int32_t>(tile.size());
+        b->m[i].st_nt = static_cast<int32_t>(L.tile.size());
+        b->m[i].st_bytes = static_cast<double>(L.w.size()) * 6.0 + static_cast<double>(L.ukey.size()) * 4.0;
         for (size_t t = 0; t < L.tile.size(); ++t) {
             int4 a = L.tile[t], c = L.tile2[t];
             a.z += static_cast<int>(u_off);
@@ -402,7 +622,8 @@ std::vector<int64_t> build_staged_pool(gn_batch *b, const std::vector<gnrt::Host
         b->staged_ok = false;
         return rq_off;
     }
-    b->st_stream = static_cast<double>(w.size()) * 6.0 + static_cast<double>(ukey.size()) * 4.0 > 48e6;
+    b->st_big = static_cast<double>(w.size()) * 6.0 + static_cast<double>(ukey.size()) * 4.0 > 48e6;
+    b->st_stream = b->st_big;
     b->n_tiles = static_cast<int>(tile.size());
     b->st_tile.upload(tile, &b->bytes);
     b->st_tile2.upload(tile2, &b->bytes);
@@ -660,8 +881,8 @@ gn_status gn_batch_create(const gn_net_desc *descs, int32_t n_nets, gn_batch **o
             return b->m[x].E + b->m[x].N > b->m[y].E + b->m[y].N;
         });
         b->d_order.upload(b->order, &b->bytes);
-        upload_args(b, 0);
         b->shape = -1;
+        upload_args(b);
         cuda_check(cudaDeviceSynchronize(), "create");
     });
     if (st != GN_OK) {
@@ -701,6 +922,8 @@ gn_status gn_batch_get_info(const gn_batch *b, gn_batch_info *info)
         info->grid = b->grid;
         info->device_bytes = b->bytes;
         info->step_kernel = b->shape == kStaged ? 3 : b->shape >= 0 ? 1 : 0;
+        info->step_groups = b->shape == kStaged ? static_cast<int32_t>(b->st_groups.size()) : 0;
+        info->step_lanes = b->shape == kStaged ? std::min(b->st_lanes, std::max(1, info->step_groups)) : 0;
     });
 }
 
@@ -776,7 +999,7 @@ gn_status gn_batch_set_stimulus_all(gn_batch *b, const gn_pulse *pulses, const i
             a.p_off = has ? b->p_off.p + b->m[i].pulse_off : nullptr;
             a.p_amp = has ? b->p_amp.p + b->m[i].pulse_off : nullptr;
         }
-        upload_args(b, b->shape >= 0 ? b->shape : 0);
+        upload_args(b);
     });
 }
 
@@ -793,7 +1016,7 @@ gn_status gn_batch_set_background(gn_batch *b, int32_t net, double rate_hz, floa
         a.bg_amp = amp;
         a.bg_width = static_cast<int32_t>(llround(dur_ms / b->m[net].dt));
         a.bg_seed = seed;
-        upload_args(b, b->shape >= 0 ? b->shape : 0);
+        upload_args(b);
     });
 }
 
@@ -807,14 +1030,13 @@ gn_status gn_batch_step(gn_batch *b, int64_t n_steps)
         if (b->shape < 0) {
             const char *e = getenv("GN_BATCH_KERNEL");
             const int only = e && *e ? atoi(e) : 0;
-            if (only != 0 && only != 1 && only != 3) fail(GN_EINVAL, "GN_BATCH_KERNEL must be 1 or 3");
-            if (only == 3 && !b->staged_ok) fail(GN_EINVAL, "the staged batch kernel cannot hold this batch");
-            if (b->model != GN_MODEL_FHN) {
-                if (only == 1) fail(GN_EINVAL, "spiking batches run the staged batch kernel");
-                set_shape(b, kStaged);
-            } else {
-                autotune(b, only != 3, only != 1);
-            }
+            if (only != 0 && only != 1 && only != 3 && only != 4) fail(GN_EINVAL, "GN_BATCH_KERNEL must be 1, 3 or 4");
+            if (only >= 3 && !b->staged_ok) fail(GN_EINVAL, "the staged batch kernel cannot hold this batch");
+            if (b->model != GN_MODEL_FHN && only == 1) fail(GN_EINVAL, "spiking batches run the staged batch kernel");
+            if (only == 4)
+                set_shape(b, kStaged, true, std::max(1, lanes_env()));  // the staged form with L2 blocking, untimed
+            else
+                autotune(b, b->model == GN_MODEL_FHN && only != 3, only != 1);
         }
         if (b->shape == kStaged) {
             if (!b->graph) build_graph(b, kGraphSteps);
@@ -822,7 +1044,8 @@ gn_status gn_batch_step(gn_batch *b, int64_t n_steps)
             for (; left >= kGraphSteps; left -= kGraphSteps)
                 cuda_check(cudaGraphLaunch(b->graph, b->stream), "cudaGraphLaunch");
             if (left) {
-                launch_steps(b, b->d_args.p, b->d_step.p, static_cast<int>(left), kStaged, b->grid, b->stream);
+                launch_steps(b, b->d_args.p, b->d_step.p, static_cast<int>(left), kStaged, b->grid, b->st_groups,
+                             b->st_lanes, b->stream);
                 cuda_check(gn::launch_advance(b->d_step.p, left, b->stream), "advance launch");
             }
         } else {

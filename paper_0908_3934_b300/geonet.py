@@ -76,7 +76,8 @@ class gn_pulse(C.Structure):
 class gn_batch_info(C.Structure):
     _fields_ = [("n_nets", C.c_int32), ("n_nodes", C.c_int64), ("n_edges", C.c_int64), ("step", C.c_int64),
                 ("cta_threads", C.c_int32), ("grid", C.c_int32), ("device_bytes", C.c_size_t),
-                ("step_kernel", C.c_int32)]
+                ("step_kernel", C.c_int32), ("step_groups", C.c_int32),
+                ("step_lanes", C.c_int32)]
 
 
 class gn_net_info(C.Structure):

@@ -17,13 +17,22 @@ def _members(model):
     return [netgen.test_set_hh(sp) if model == "hh" else netgen.test_set_izh(sp) for sp in nets]
 
 
+@pytest.mark.parametrize("schedule", ["timed", "l2_groups"])
 @pytest.mark.parametrize("model", ["izh", "hh"])
-def test_members_equal_their_networks_run_alone(model):
+def test_members_equal_their_networks_run_alone(model, schedule, monkeypatch):
+    """Either schedule of the staged form: the one the first step times (these
+    members fit one group), or L2 blocking in three lanes sharing a 48 KB budget
+    (groups of one or two members, each running 64-step chunks)."""
+    if schedule == "l2_groups":
+        monkeypatch.setenv("GN_BATCH_KERNEL", "4")
+        monkeypatch.setenv("GN_BATCH_GROUP_KB", "48")
+        monkeypatch.setenv("GN_BATCH_LANES", "3")
     specs = _members(model)
     steps = 700 if model == "izh" else 1500
     b = geonet.Batch(specs)
     b.gn_batch_step(steps)
-    assert b.gn_batch_get_info()["step_kernel"] == 3
+    info = b.gn_batch_get_info()
+    assert info["step_kernel"] == 3 and (info["step_groups"] > 1) == (schedule == "l2_groups"), info
     n_spikes = 0
     for i, sp in enumerate(specs):
         net = geonet.Net(sp)
@@ -74,20 +83,30 @@ def test_spiking_batches_are_checked(monkeypatch):
 def test_a_batch_larger_than_the_device_launches_first_bit_identically(monkeypatch, model):
     """A staged batch grid with more tiles than the device holds at once lets the
     next step's grid start at once (its gathers read history two or more steps
-    old); its members equal those of the same batch waiting first, bit for bit."""
+    old); its members equal those of the same batch waiting first, bit for bit,
+    and those of the same batch stepped in L2-blocked groups."""
     specs = [netgen.batch_member(1000 + i) for i in range(700)]
     if model == "izh":
         specs = [netgen.izhikevich(sp) for sp in specs]
-    monkeypatch.setenv("GN_BATCH_KERNEL", "3")
     out = []
-    for early in ("1", "0"):
+    # every member every step, launching first or waiting first; then L2 blocking
+    # in one lane with groups of about half the tiles (more than the device holds:
+    # each group launches first), and in four lanes with groups of a few hundred
+    # tiles (fewer: each waits first)
+    for kernel, early, group_kb, lanes in (("3", "1", "0", "1"), ("3", "0", "0", "1"), ("4", "1", "131072", "1"),
+                                           ("4", "1", "24576", "4")):
+        monkeypatch.setenv("GN_BATCH_KERNEL", kernel)
         monkeypatch.setenv("GN_STAGED_EARLY", early)
+        monkeypatch.setenv("GN_BATCH_GROUP_KB", group_kb)
+        monkeypatch.setenv("GN_BATCH_LANES", lanes)
         b = geonet.Batch(specs)
         b.gn_batch_step(300)
-        assert b.gn_batch_get_info()["step_kernel"] == 3
+        info = b.gn_batch_get_info()
+        assert info["step_kernel"] == 3 and (info["step_groups"] > 1) == (kernel == "4"), info
         out.append([(b.gn_batch_get_state(i), b.gn_batch_get_history(i, 4)) for i in range(0, 700, 37)])
         b.gn_batch_destroy()
-    for (sa, ha), (sb, hb) in zip(*out):
-        for k in ("v", "w", "c", "bg_count"):
-            assert np.array_equal(sa[k], sb[k]), k
-        assert np.array_equal(ha, hb)
+    for other in out[1:]:
+        for (sa, ha), (sb, hb) in zip(out[0], other):
+            for k in ("v", "w", "c", "bg_count"):
+                assert np.array_equal(sa[k], sb[k]), k
+            assert np.array_equal(ha, hb)

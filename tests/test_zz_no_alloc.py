@@ -36,3 +36,27 @@ def test_static_step_matches_gn_batch_step_on_two_calls():
             yb, fb, _ = b.gn_batch_observe(i)
             assert fa == fb and ya.shape == yb.shape and ratio(ya, yb) <= 1.0
             assert np.array_equal(a.gn_batch_get_arrivals(i), b.gn_batch_get_arrivals(i))
+
+
+def test_static_step_after_the_staged_form_and_a_new_background(monkeypatch):
+    """gn_batch_step_static runs the persistent kernel on the block descriptors of
+    its first CTA size even when gn_batch_step chose the staged form and a member's
+    background changed afterwards (the argument upload keeps valid descriptors)."""
+    monkeypatch.setenv("GN_BATCH_KERNEL", "3")
+    specs = [netgen.batch_member(9100 + i, n_hi=1200) for i in range(6)]
+    a = geonet.Batch(specs)
+    b = geonet.Batch(specs)
+    L = geonet.lib()
+    for x in (a, b):
+        x.gn_batch_step(100)
+        assert x.gn_batch_get_info()["step_kernel"] == 3
+        geonet.check(L.gn_batch_set_background(x.h, 2, C.c_double(40.0), C.c_float(0.5), C.c_double(1.0),
+                                               C.c_uint64(77)))
+    geonet.check(L.gn_batch_step_static(a.h, C.c_int64(200)))
+    b.gn_batch_step(200)
+    for i in range(len(specs)):
+        sa, sb = a.gn_batch_get_state(i), b.gn_batch_get_state(i)
+        for k in ("v", "w", "c"):
+            assert ratio(sa[k], sb[k]) <= 1.0, (i, k)
+        assert np.array_equal(sa["bg_count"], sb["bg_count"])
+        assert np.array_equal(a.gn_batch_get_arrivals(i), b.gn_batch_get_arrivals(i))
