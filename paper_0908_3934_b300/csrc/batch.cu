@@ -941,7 +941,8 @@ gn_status gn_batch_get_net_info(const gn_batch *b, int32_t net, gn_net_info *inf
         info->min_delay = mm.dmin;
         info->n_clamped = mm.n_clamped;
         info->edge_format = mm.packed ? 0 : 1;
-        info->n_blocks = b->shape >= 0 ? mm.n_blocks[b->shape] : mm.n_blocks[0];
+        // tiles when the staged form steps the batch, else row blocks of k_batch's CTA size
+        info->n_blocks = b->shape == kStaged ? mm.st_nt : mm.n_blocks[desc_shape(b)];
         info->step = b->step;
         info->samples = b->step / mm.sample_every;
         info->v_rest = mm.v_rest;

@@ -41,6 +41,10 @@ def test_batch_equals_single_networks_bit_for_bit(batch_kernel):
     assert info["step_kernel"] == min(batch_kernel, 3)
     assert (info["step_groups"] > 1) == (batch_kernel == 4), info
     assert info["step_lanes"] == (2 if batch_kernel == 4 else 1 if batch_kernel == 3 else 0), info
+    n_blocks = [b.gn_batch_get_net_info(i)["n_blocks"] for i in range(24)]
+    assert min(n_blocks) >= 1
+    if batch_kernel != 1:  # the staged grid is every member's tiles
+        assert sum(n_blocks) == info["grid"], (n_blocks, info)
     for i in range(0, 24, 3):
         net = geonet.Net(specs[i], step_kernel=1)
         net.gn_step(2000)
