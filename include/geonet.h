@@ -276,8 +276,9 @@ GN_API gn_status gn_observe(gn_net *net, float *out, int64_t max_samples, int64_
 /* As gn_observe (the same rows, the read cursor advanced the same way), but the
  * copies are queued on a copy stream behind the steps taken so far and the call
  * returns at once, so later gn_step calls overlap them (with pinned `out`).  `out`
- * must stay valid until gn_observe_wait or gn_synchronize returns, and no more than
- * obs_capacity samples may be produced before then.  GN_EOVERFLOW as gn_observe. */
+ * must stay valid until gn_observe_wait or gn_synchronize returns, and until then
+ * the steps may produce at most obs_capacity - *written new samples (more would
+ * wrap onto the device rows still being copied).  GN_EOVERFLOW as gn_observe. */
 GN_API gn_status gn_observe_async(gn_net *net, float *out, int64_t max_samples, int64_t *first_sample,
                                   int64_t *written);
 /* Wait for the copies gn_observe_async queued (not for later steps). */

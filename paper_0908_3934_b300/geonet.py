@@ -189,6 +189,17 @@ def _c(a, dt):
     return None if a is None else np.ascontiguousarray(a, dtype=dt)
 
 
+def _out_rows(out, rows: int, cols: int):
+    """A caller's output buffer for `rows` rows of `cols` float32 values: checked
+    before the library writes into it."""
+    if not (isinstance(out, np.ndarray) and out.dtype == np.float32 and out.flags.c_contiguous
+            and out.flags.writeable):
+        raise ValueError("out must be a writable C-contiguous float32 array")
+    if out.size < max(0, rows) * cols:
+        raise ValueError(f"out holds {out.size} values, {max(0, rows)} rows of {cols} need more")
+    return out
+
+
 def make_desc(spec, keep: list, *, device: int = 0, stream=None, obs_capacity: int = 0, event_capacity: int = 0,
               renumber: bool = True, ring_depth: int | None = None, coupling: str | None = None,
               wide_edges: bool = False, step_kernel: int = 0) -> gn_net_desc:
@@ -325,6 +336,8 @@ class Net:
             max_samples = info["samples"]
         if out is None and not discard:
             out = np.zeros((max(0, max_samples), self.n_nodes), np.float32)
+        elif not discard:
+            _out_rows(out, max_samples, self.n_nodes)
         first = C.c_int64()
         wr = C.c_int64()
         st = check(lib().gn_observe(self.h, None if discard else _ptr(out), max_samples, C.byref(first),
@@ -334,6 +347,7 @@ class Net:
     def gn_observe_async(self, out: np.ndarray, max_samples: int):
         """Queue the copy of up to max_samples unread rows into `out` (which must stay
         alive until gn_observe_wait); returns (rows written, first sample, status)."""
+        _out_rows(out, max_samples, self.n_nodes)
         first = C.c_int64()
         wr = C.c_int64()
         st = check(lib().gn_observe_async(self.h, _ptr(out), max_samples, C.byref(first), C.byref(wr)),
