@@ -189,6 +189,25 @@ def _c(a, dt):
     return None if a is None else np.ascontiguousarray(a, dtype=dt)
 
 
+def _vec(a, dt, n: int, name: str):
+    """A caller's input of n values as a contiguous array of dtype dt (None stays
+    None, the library's "leave unchanged"): checked before the library reads it."""
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=dt).reshape(-1)
+    if a.size != n:
+        raise ValueError(f"{name} has {a.size} values, {n} expected")
+    return a
+
+
+def _rows_in(a, n: int, name: str):
+    """A caller's input of k >= 1 rows of n float32 values (history rows)."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if a.ndim != 2 or a.shape[0] < 1 or a.shape[1] != n:
+        raise ValueError(f"{name} must have shape (k >= 1, {n}), got {a.shape}")
+    return a
+
+
 def _out_rows(out, rows: int, cols: int):
     """A caller's output buffer for `rows` rows of `cols` float32 values: checked
     before the library writes into it."""
@@ -366,9 +385,10 @@ class Net:
         return dict(v=v, w=w, c=c, bg_count=bg, step=st.value)
 
     def gn_set_state(self, hist, w=None, c=None, bg_count=None, step: int = 0):
-        hist = np.ascontiguousarray(hist, np.float32)
-        w, c = _c(w, np.float32), _c(c, np.float32)
-        bg = _c(bg_count, np.int32)
+        N = self.n_nodes
+        hist = _rows_in(hist, N, "hist")
+        w, c = _vec(w, np.float32, N, "w"), _vec(c, np.float32, N, "c")
+        bg = _vec(bg_count, np.int32, N, "bg_count")
         check(lib().gn_set_state(self.h, _ptr(hist), hist.shape[0], _ptr(w), _ptr(c), _ptr(bg), step))
 
     def gn_get_izh_state(self):
@@ -378,7 +398,8 @@ class Net:
         return dict(V=V, r=r, p=p)
 
     def gn_set_izh_state(self, V=None, r=None, p=None):
-        V, r, p = _c(V, np.float32), _c(r, np.float32), _c(p, np.float32)
+        N = self.n_nodes
+        V, r, p = _vec(V, np.float32, N, "V"), _vec(r, np.float32, N, "r"), _vec(p, np.float32, N, "p")
         check(lib().gn_set_izh_state(self.h, _ptr(V), _ptr(r), _ptr(p)))
 
     def gn_get_hh_gates(self):
@@ -388,7 +409,8 @@ class Net:
         return dict(m=m, n=n, h=h)
 
     def gn_set_hh_gates(self, m=None, n=None, h=None):
-        m, n, h = _c(m, np.float32), _c(n, np.float32), _c(h, np.float32)
+        N = self.n_nodes
+        m, n, h = _vec(m, np.float32, N, "m"), _vec(n, np.float32, N, "n"), _vec(h, np.float32, N, "h")
         check(lib().gn_set_hh_gates(self.h, _ptr(m), _ptr(n), _ptr(h)))
 
     def gn_get_weights(self) -> np.ndarray:
@@ -397,7 +419,9 @@ class Net:
         return out
 
     def gn_set_weights(self, w):
-        w = np.ascontiguousarray(w, np.float32)
+        w = _vec(w, np.float32, self.n_edges, "w")
+        if w is None:
+            raise ValueError("w is required")
         check(lib().gn_set_weights(self.h, _ptr(w)))
 
     def gn_get_stdp_history(self, depth: int) -> np.ndarray:
@@ -406,7 +430,7 @@ class Net:
         return out
 
     def gn_set_stdp_history(self, s_hist):
-        s_hist = np.ascontiguousarray(s_hist, np.float32)
+        s_hist = _rows_in(s_hist, self.n_nodes, "s_hist")
         check(lib().gn_set_stdp_history(self.h, _ptr(s_hist), s_hist.shape[0]))
 
     def gn_get_history(self, depth: int) -> np.ndarray:
@@ -558,9 +582,10 @@ class Batch:
         check(lib().gn_batch_set_step(self.h, step))
 
     def gn_batch_set_state(self, net: int, hist, w=None, c=None, bg_count=None):
-        hist = np.ascontiguousarray(hist, np.float32)
-        w, c = _c(w, np.float32), _c(c, np.float32)
-        bg = _c(bg_count, np.int32)
+        N = self.specs[net].n_nodes
+        hist = _rows_in(hist, N, "hist")
+        w, c = _vec(w, np.float32, N, "w"), _vec(c, np.float32, N, "c")
+        bg = _vec(bg_count, np.int32, N, "bg_count")
         check(lib().gn_batch_set_state(self.h, net, _ptr(hist), hist.shape[0], _ptr(w), _ptr(c), _ptr(bg)))
 
 

@@ -24,3 +24,21 @@ def test_output_buffer_checks():
         geonet._out_rows(ro, 4, 10)
     with pytest.raises(ValueError):
         geonet._out_rows([[0.0] * 10] * 4, 4, 10)
+
+
+def test_input_length_checks():
+    """Inputs the library reads n values from (state vectors, weights) or rows of n
+    values from (history) are converted and their lengths checked first."""
+    v = geonet._vec([1, 2, 3], np.float32, 3, "w")
+    assert v.dtype == np.float32 and v.flags.c_contiguous and v.tolist() == [1.0, 2.0, 3.0]
+    assert geonet._vec(None, np.float32, 3, "w") is None
+    assert geonet._vec(np.arange(6, dtype=np.int64)[::2], np.int32, 3, "bg_count").tolist() == [0, 2, 4]
+    with pytest.raises(ValueError):
+        geonet._vec(np.zeros(2), np.float32, 3, "w")
+    with pytest.raises(ValueError):
+        geonet._vec(np.zeros(4), np.float32, 3, "w")
+    h = geonet._rows_in(np.zeros((2, 5)), 5, "hist")
+    assert h.dtype == np.float32 and h.shape == (2, 5)
+    for bad in (np.zeros(5), np.zeros((2, 4)), np.zeros((0, 5)), np.zeros((1, 2, 5))):
+        with pytest.raises(ValueError):
+            geonet._rows_in(bad, 5, "hist")
