@@ -337,13 +337,15 @@ GN_API gn_status gn_save_state(gn_net *net, void *buf, size_t cap, size_t *used)
 GN_API gn_status gn_load_state(gn_net *net, const void *buf, size_t size);
 
 /* ---------------------------------------------------------------------------
- * Batched form: many independent networks (of any sizes) advanced together by
- * one persistent launch per gn_batch_step, replayed from a captured CUDA graph.
- * Every network of a batch uses one node model; spiking batches run the staged
- * form only, and plastic weights are not taken (GN_EINVAL).
- * CTAs take networks from a work queue ordered largest first and run all the
- * requested steps of a network before taking the next; the CTA size is chosen by
- * timing the candidates on the first gn_batch_step.  Every network follows the
+ * Batched form: many independent networks (of any sizes) advanced together,
+ * from captured CUDA graphs, by one of two kernels: a persistent launch per
+ * gn_batch_step whose CTAs take networks from a work queue ordered largest first
+ * and run all the requested steps of a network before taking the next (kernel 1),
+ * or the staged tiles of every member, one launch per step (kernel 3, with the
+ * schedules described at gn_batch_step).  Every network of a batch uses one node
+ * model; spiking batches run the staged form only, and plastic weights are not
+ * taken (GN_EINVAL).  The kernel, its CTA size and schedule are chosen by timing
+ * the candidates on the first gn_batch_step.  Every network follows the
  * same model and conventions as gn_net (Sec. 2, 3.1, 3.2.1, 3.3); per-network
  * calls take the network's index in the descriptor array.
  * ------------------------------------------------------------------------- */

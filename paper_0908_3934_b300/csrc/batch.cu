@@ -1,6 +1,6 @@
 // Host runtime of the batched form (gn_batch_* in include/geonet.h): many
-// independent networks in pooled device arrays, advanced together by one
-// persistent launch of k_batch replayed from a captured graph.
+// independent networks in pooled device arrays, advanced together from captured
+// graphs by the persistent k_batch or by the staged tile kernel.
 //
 // gn_batch_create builds every network exactly as gn_net_create does (one FP64
 // delay launch for the whole batch, Morton renumbering and the by-target edge list
