@@ -454,8 +454,9 @@ GN_API gn_status gn_batch_export_traces(gn_batch *batch, int64_t first_sample, i
 
 /* Lagged normalised cross-correlation features of candidate pairs i -> j, all
  * pointers on the device.  traces [n_nodes][n_samples] (node-major), pos
- * [n_nodes][dim] (mm), pairs src/dst [n_pairs], radius [n_pairs] (the candidate
- * radius r_c of the pair's network).  With d = |x_i - x_j| and the first lag
+ * [n_nodes][dim] (mm), pairs src/dst [n_pairs] (every entry in [0, n_nodes): the
+ * kernel gathers traces and positions by them unchecked), radius [n_pairs] (the
+ * candidate radius r_c of the pair's network).  With d = |x_i - x_j| and the first lag
  * l0 = floor((d / v_max) / sample_ms) (the shortest delay, Sec. 3.2.1), feature k < 32
  * is the Pearson correlation of y_i(t) and y_j(t + l0 + k) over their overlap, each
  * segment about its own mean (0 if one is constant); feature 32 is d / r_c.
@@ -476,8 +477,9 @@ GN_API gn_status gn_xcorr_features(const float *traces, int64_t n_nodes, int32_t
  * in a fixed order.  Parameters are exchanged as one packed FP32 host array
  * [W1 (in_dim x 256, row-major) | b1 (256) | W2 (256 x 256) | b2 | w3 (256) | b3 (1)];
  * X [rows][in_dim], y [rows] and p [B] are device buffers; with idx (device int64
- * [B], may be NULL) row b of the batch is X[idx[b]] / y[idx[b]], so a resident
- * training set is visited in any order without copies. */
+ * [B], may be NULL; every entry in [0, rows): rows are gathered by it unchecked)
+ * row b of the batch is X[idx[b]] / y[idx[b]], so a resident training set is
+ * visited in any order without copies. */
 typedef struct gn_mlp gn_mlp;
 GN_API gn_status gn_mlp_create(int32_t in_dim, int32_t max_batch, const float *params, int32_t device,
                                void *cuda_stream, gn_mlp **out);

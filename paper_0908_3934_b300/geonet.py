@@ -595,9 +595,26 @@ def _dptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
+def _dev(t, dtype: str, name: str, shape=None, min_len: int | None = None):
+    """A caller's device tensor, checked before its address goes to the library: a
+    contiguous CUDA tensor of `dtype` ("float32", "float64", "int32", "int64"),
+    of `shape` (None entries free) or 1-D with at least `min_len` entries."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()
+            and t.dtype == getattr(torch, dtype)):
+        raise ValueError(f"{name} must be a contiguous CUDA tensor of {dtype}")
+    if shape is not None and (t.dim() != len(shape)
+                              or any(want is not None and got != want for got, want in zip(t.shape, shape))):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, {tuple(shape)} expected")
+    if min_len is not None and (t.dim() != 1 or t.shape[0] < min_len):
+        raise ValueError(f"{name} must be 1-D with at least {min_len} entries, got {tuple(t.shape)}")
+    return t
+
+
 def gn_batch_export_traces(batch: "Batch", first_sample: int, n_samples: int, out):
     """Node-major traces [total nodes, n_samples] of every network of `batch` into
     the CUDA tensor `out`."""
+    _dev(out, "float32", "out", shape=(sum(sp.n_nodes for sp in batch.specs), n_samples))
     check(lib().gn_batch_export_traces(batch.h, first_sample, n_samples, _dptr(out)))
     return out
 
@@ -607,7 +624,15 @@ def gn_xcorr_features(traces, pos, src, dst, radius, features, score, v_max: flo
     """Lagged normalised cross-correlation features of candidate pairs; every
     argument but v_max / sample_ms is a CUDA tensor (traces f32 [M, T], pos f64
     [M, dim], src / dst i32 [P], radius f64 [P], features f32 [P, 33], score f32 [P])."""
+    _dev(traces, "float32", "traces", shape=(None, None))
     M, T = traces.shape
+    _dev(pos, "float64", "pos", shape=(M, None))
+    _dev(src, "int32", "src", shape=(None,))
+    P = src.shape[0]
+    _dev(dst, "int32", "dst", shape=(P,))
+    _dev(radius, "float64", "radius", shape=(P,))
+    _dev(features, "float32", "features", shape=(P, 33))
+    _dev(score, "float32", "score", shape=(P,))
     check(lib().gn_xcorr_features(_dptr(traces), M, T, _dptr(pos), pos.shape[1], src.shape[0], _dptr(src),
                                   _dptr(dst), _dptr(radius), v_max, sample_ms, _dptr(features), _dptr(score),
                                   stream))
@@ -687,7 +712,16 @@ class Mlp:
         check(lib().gn_mlp_get_params(self.h, _ptr(flat)))
         return mlp_unpack(flat, self.in_dim)
 
+    def _xy(self, X, y, idx, min_idx: int = 0):
+        """Check a resident set X [rows, in_dim], y [rows] and an optional int64
+        row index (device tensors)."""
+        _dev(X, "float32", "X", shape=(None, self.in_dim))
+        _dev(y, "float32", "y", shape=(X.shape[0],))
+        if idx is not None:
+            _dev(idx, "int64", "idx", min_len=min_idx)
+
     def gn_mlp_gradients(self, X, y, idx=None):
+        self._xy(X, y, idx)
         flat = np.zeros(self.n_params, np.float32)
         loss = C.c_float()
         B = X.shape[0] if idx is None else idx.shape[0]
@@ -696,6 +730,7 @@ class Mlp:
 
     def gn_mlp_train_step(self, X, y, idx=None, lr: float = 1e-3, weight_decay: float = 0.0,
                           want_loss: bool = True):
+        self._xy(X, y, idx)
         loss = C.c_float()
         B = X.shape[0] if idx is None else idx.shape[0]
         check(lib().gn_mlp_train_step(self.h, _dptr(X), _dptr(y), _dptr(idx), B, lr, weight_decay,
@@ -706,12 +741,17 @@ class Mlp:
                            want_losses: bool = True):
         """n_batches AdamW steps on rows idx[j B .. (j + 1) B) (device int64), one
         replayed graph launch per step; returns the per-step losses (numpy) or None."""
+        if idx is None:
+            raise ValueError("idx is required")
+        self._xy(X, y, idx, min_idx=n_batches * B)
         losses = np.zeros(n_batches, np.float32) if want_losses else None
         check(lib().gn_mlp_train_epoch(self.h, _dptr(X), _dptr(y), _dptr(idx), n_batches, B, lr, weight_decay,
                                        _ptr(losses) if want_losses else None))
         return losses
 
     def gn_mlp_infer(self, X, out):
+        _dev(X, "float32", "X", shape=(None, self.in_dim))
+        _dev(out, "float32", "out", min_len=X.shape[0])
         check(lib().gn_mlp_infer(self.h, _dptr(X), X.shape[0], _dptr(out)))
         return out
 

@@ -42,3 +42,12 @@ def test_input_length_checks():
     for bad in (np.zeros(5), np.zeros((2, 4)), np.zeros((0, 5)), np.zeros((1, 2, 5))):
         with pytest.raises(ValueError):
             geonet._rows_in(bad, 5, "hist")
+
+
+def test_device_tensor_checks_reject_host_tensors_and_arrays():
+    """The estimator calls take device tensors only: host tensors and numpy arrays
+    are refused before their address could reach the library."""
+    import torch
+    for bad in (torch.zeros((4, 33), dtype=torch.float32), np.zeros((4, 33), np.float32)):
+        with pytest.raises(ValueError):
+            geonet._dev(bad, "float32", "X", shape=(None, 33))
