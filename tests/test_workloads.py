@@ -135,3 +135,31 @@ def test_batch_members_recipe():
     assert _within(float((w < 0).mean()), 0.2, math.sqrt(0.16 / w.size))
     assert _within(np.log(np.abs(w)).mean(), -2.0, 0.5 / math.sqrt(w.size))
     assert netgen.batch_member(7, n=512).n_nodes == 512
+
+
+def test_candidate_pairs_and_labels_by_brute_force():
+    """The estimator's candidates are every ordered pair closer than the member's
+    radius, labelled 1 exactly where the pair is an edge (every edge is a candidate,
+    about half the candidates are edges); a table of several members numbers the
+    nodes globally in member order."""
+    from paper_0908_3934_b300 import pipeline
+    members = [netgen.batch_member(40 + i, n=n) for i, n in enumerate((60, 200, 512))]
+    for m in members:
+        src, dst, lab = netgen.candidates(m)
+        D = np.sqrt(((m.pos[:, None, :] - m.pos[None, :, :]) ** 2).sum(-1))
+        want = {(int(i), int(j)) for i, j in zip(*np.nonzero((D < m.radius) & ~np.eye(m.n_nodes, dtype=bool)))}
+        got = list(zip(src.tolist(), dst.tolist()))
+        assert len(got) == len(set(got)) and set(got) == want
+        edges = set(zip(m.src.tolist(), m.dst.tolist()))
+        assert [int(x) for x in lab] == [1 if p in edges else 0 for p in got]
+        assert int(lab.sum()) == m.n_edges
+        assert _within(lab.mean(), 0.5, math.sqrt(0.25 / lab.size))
+    tab = pipeline.candidate_table(members)
+    off = np.cumsum([0] + [m.n_nodes for m in members])
+    assert tab["n_nodes"] == off[-1] and np.array_equal(tab["pos"], np.concatenate([m.pos for m in members]))
+    for i, m in enumerate(members):
+        sel = tab["net"] == i
+        src, dst, lab = netgen.candidates(m)
+        assert np.array_equal(tab["src"][sel], src + off[i]) and np.array_equal(tab["dst"][sel], dst + off[i])
+        assert np.array_equal(tab["label"][sel], lab) and np.all(tab["radius"][sel] == m.radius)
+    assert tab["src"].dtype == np.int32 and tab["radius"].dtype == np.float64
