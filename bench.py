@@ -62,6 +62,11 @@ def workload(name: str, rank: int):
     1M-node net takes ~40 s of host time and it is the same on every call)."""
     import pickle
     gens = {"roofline": lambda: netgen.roofline(seed=4 + 1000 * rank),
+            # secondary sizes of the 1M-node net: the literal 5 % hubs beside non-hubs
+            # of mean in-degree 50 (overall ~97.5) and conduction speeds x 0.1 (delays up
+            # to ~410 steps, ring 512)
+            "roofline_hubs5": lambda: netgen.roofline(seed=4 + 1000 * rank, hub_frac=0.05, mean_deg=97.5),
+            "roofline_slow": lambda: netgen.delay_stress(netgen.roofline(seed=4 + 1000 * rank)),
             "large": lambda: netgen.large(seed=3 + 1000 * rank),
             "tiny": lambda: netgen.tiny(seed=1 + 1000 * rank),
             "batch": lambda: netgen.batch(4096, seed0=1000 + 100000 * rank)}
@@ -224,8 +229,10 @@ def run_reference(args):
 
 
 def config_of(args, spec, world):
-    return {"workload": f"{args.workload}: N={spec.n_nodes}, E={spec.n_edges} per replica, dt=0.05 ms, "
-                        f"FHN nodes, 5 Hz background, ring 256",
+    ring = f"ring {spec.ring_depth}" if spec.ring_depth else "ring sized to the delays"
+    bg = f"{spec.background['rate_hz']:g} Hz background" if spec.background else "no background"
+    return {"workload": f"{args.workload}: N={spec.n_nodes}, E={spec.n_edges} per replica, dt={spec.dt_ms:g} ms, "
+                        f"FHN nodes, {bg}, {ring}",
             "nodes_per_replica": spec.n_nodes, "edges_per_replica": spec.n_edges, "replicas": world,
             "dt_ms": spec.dt_ms, "l2": "inputs larger than L2 (edge stream re-read every step)",
             "parallelism": f"replicas{world}"}
@@ -483,7 +490,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--warmup", type=int, default=100)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="roofline", choices=["roofline", "large", "tiny"])
+    ap.add_argument("--workload", default="roofline",
+                    choices=["roofline", "roofline_hubs5", "roofline_slow", "large", "tiny"])
     ap.add_argument("--cpu-steps", type=int, default=30, help="oracle steps of the cpu_baseline sample")
     ap.add_argument("--ref-steps", type=int, default=30, help="oracle steps timed by --impl reference")
     ap.add_argument("--e2e-chunk", type=int, default=1000, help="steps per host round trip in the e2e run")

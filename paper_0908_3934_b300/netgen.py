@@ -273,6 +273,16 @@ def roofline(seed: int = 4, n: int = 1_000_000, mean_deg: float = 50.0, hub_frac
                    ring_depth=256, name=f"roofline_n{n}")
 
 
+def delay_stress(spec: NetSpec, factor: float = 0.1) -> NetSpec:
+    """The same network with every conduction speed scaled by `factor` (delays in
+    steps grow by 1 / factor: 0.1 takes the 1M-node net's 1-41 steps to about
+    10-410), the ring sized afresh for them."""
+    if spec.speed is None:
+        raise ValueError("the net has one scalar speed; scale speed_scalar instead")
+    return dataclasses.replace(spec, speed=np.asarray(spec.speed) * factor, ring_depth=0,
+                               name=spec.name + f"_speedx{factor:g}")
+
+
 def batch_member(seed: int, n: int | None = None, n_lo: int = 32, n_hi: int = 4096,
                  kept_deg: float = 20.0, keep: float = 0.5) -> NetSpec:
     """One network of the batched ensemble (its own seed decides its size)."""

@@ -163,3 +163,20 @@ def test_candidate_pairs_and_labels_by_brute_force():
         assert np.array_equal(tab["src"][sel], src + off[i]) and np.array_equal(tab["dst"][sel], dst + off[i])
         assert np.array_equal(tab["label"][sel], lab) and np.all(tab["radius"][sel] == m.radius)
     assert tab["src"].dtype == np.int32 and tab["radius"].dtype == np.float64
+
+
+def test_secondary_roofline_variants():
+    """The literal 5 % hub variant (5 % of the nodes with 1000 inputs beside a radius
+    graph of mean in-degree 50: about 97.5 overall) and the delay-stress variant
+    (every speed x 0.1, ring sized afresh)."""
+    n = 40000
+    sp = netgen.roofline(n=n, hub_frac=0.05, mean_deg=97.5)
+    k = _in_deg(sp)
+    hubs = k == 1000
+    assert hubs.sum() == round(0.05 * n) and abs(k.mean() - 97.5) < 2.0 and abs(k[~hubs].mean() - 50.0) < 1.0
+    base = netgen.roofline(n=n)
+    slow = netgen.delay_stress(base)
+    assert np.array_equal(slow.src, base.src) and np.array_equal(slow.weight, base.weight)
+    assert np.allclose(slow.speed, base.speed * 0.1) and slow.ring_depth == 0
+    with pytest.raises(ValueError):
+        netgen.delay_stress(netgen.tiny())
