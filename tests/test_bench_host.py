@@ -68,3 +68,13 @@ def test_reference_arm_prints_one_contract_line():
         assert k in d, k
     assert d["impl"] == "reference" and d["higher_is_better"] is True and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+
+
+def test_config_names_the_workload_as_generated():
+    from types import SimpleNamespace
+    from paper_0908_3934_b300 import netgen
+    tiny = bench.config_of(SimpleNamespace(workload="tiny"), netgen.tiny(), 1)
+    assert "no background" in tiny["workload"] and "ring sized to the delays" in tiny["workload"]
+    big = bench.config_of(SimpleNamespace(workload="large"), netgen.large(n=2000, mean_deg=20.0), 2)
+    assert "5 Hz background" in big["workload"] and "ring 256" in big["workload"]
+    assert big["replicas"] == 2 and big["parallelism"] == "replicas2" and big["dt_ms"] == 0.05
