@@ -310,6 +310,21 @@ def test_largest_delay_that_fits_the_ring():
     assert e.value.status == geonet.GN_ERANGE
 
 
+def test_slow_conduction_deep_ring_windows():
+    """The delay-stress size (every speed x 0.1): delays of up to ~2400 steps in a
+    ring sized afresh (4096 slots, packed keys with 12 delay bits); windows against
+    the oracle from step 2100, where gathers of delays beyond 2000 steps read
+    written history."""
+    spec = netgen.delay_stress(netgen.roofline(seed=23, n=5000, bg_rate_hz=100.0))
+    D = oracle.net_delays(spec)
+    assert 2048 < D.max() < 4094
+    net = Net(spec)
+    info = net.gn_net_get_info()
+    assert info["max_delay"] == D.max() and info["ring_depth"] == 4096 and info["edge_format"] == 0
+    worst, _ = windowed(spec, net, 100, start=2100)
+    assert_windows(worst)
+
+
 def test_background_counters_and_arrivals():
     spec = netgen.large(n=3000, mean_deg=20, bg_rate_hz=200.0)
     worst, _ = windowed(spec, Net(spec), 1000)
