@@ -7,7 +7,7 @@ import pytest
 import oracle
 from paper_0908_3934_b300 import netgen
 
-from parity import REL, ABS, ratio
+from parity import ratio
 
 pytestmark = pytest.mark.gpu
 
