@@ -389,6 +389,48 @@ def test_large_full_size_sampled(large_spec):
     assert_windows(worst)
 
 
+def test_batched_full_size_sampled():
+    """The 4096-network ensemble (3.34M nodes, 61M edges) in the configuration the
+    bench times -- the kernel and schedule its first step picks by timing (on a B300
+    the L2-blocked staged form) -- with 32 sampled members: delays bit-exact, then
+    each loaded with the oracle's state after 500 steps (most members active by
+    then) and compared over one 20-step window, every node of each."""
+    from paper_0908_3934_b300 import geonet
+    specs = netgen.batch(4096, seed0=1000)
+    b = geonet.Batch(specs, obs_capacity=64)
+    b.gn_batch_step(20)  # picks the kernel and schedule, as the bench's warm-up does
+    info = b.gn_batch_get_info()
+    assert info["n_nets"] == 4096 and info["step_kernel"] in (1, 3)
+    sample = [int(i) for i in np.random.default_rng(12).choice(4096, 32, replace=False)]
+    K, n0 = 20, 500
+    refs, depth, nxt = {}, {}, {}
+    for i in sample:
+        D = oracle.net_delays(specs[i])
+        assert np.array_equal(b.gn_batch_get_delays(i), D), i
+        depth[i] = int(D.max()) + 1
+        refs[i] = oracle.simulate(specs[i], n0, hist_depth=depth[i], want_y=False)
+    b.gn_batch_set_step(n0)
+    for i in sample:
+        r = refs[i]
+        b.gn_batch_set_state(i, r["hist"].astype(np.float32), r["w"].astype(np.float32),
+                             r["c"].astype(np.float32), r["bg_count"])
+        nxt[i] = oracle.simulate(specs[i], K, hist_depth=depth[i],
+                                 init=dict(n0=n0, v=r["v"], w=r["w"], c=r["c"], bg_count=r["bg_count"],
+                                           hist=r["hist"]))
+    b.gn_batch_step(K)
+    worst, active = 0.0, 0
+    for i in sample:
+        g = b.gn_batch_get_state(i)
+        for k in ("v", "w", "c"):
+            worst = max(worst, ratio(g[k], nxt[i][k]))
+        y, _, _ = b.gn_batch_observe(i)
+        worst = max(worst, ratio(y, nxt[i]["y"]))
+        active += int(np.abs(nxt[i]["v"]).max() > 1e-3)
+    assert worst <= 1.0, worst
+    assert active >= 16, active
+    b.gn_batch_destroy()
+
+
 def test_roofline_full_size_sampled():
     """N = 1,000,000, ~50M edges with 2.5 % hubs of in-degree 1000, ring of 256
     steps (the benchmark's network): delays bit-exact; one 20-step window after
