@@ -226,6 +226,19 @@ def test_two_node_chain_first_arrival():
         assert f1 == f0 + max(1, D) + 1
 
 
+def test_two_node_chain_first_arrival_at_a_deep_delay():
+    """The same at a delay of 5000 steps, deeper than any ring the benchmark sizes
+    (slow conduction, 0.002 mm/ms over 0.5 mm)."""
+    d, s = 0.5, 0.002
+    spec = netgen.chain2(dist_mm=d, speed=s)
+    D = int(round(d / (s * 0.05)))
+    assert D == 5000
+    r = oracle.simulate(spec, 5200)
+    assert r["delay"][0] == D
+    f0, f1 = r["first_arrival"]
+    assert f0 == 101 and f1 == f0 + D + 1
+
+
 def test_tiny_arrivals_match_dijkstra():
     """Config 'tiny': all first arrivals equal the shortest-path schedule."""
     spec = netgen.tiny()
