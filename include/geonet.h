@@ -424,8 +424,11 @@ GN_API gn_status gn_batch_get_events(gn_batch *batch, int32_t net, int32_t *node
  * inside the library instead of the batch's memory.  The paper has no
  * counterpart; this is a deployment entry point.
  *   Limit: batches of at most 65,536 networks (GN_ERANGE beyond).
- *   The first call on a device looks up that array's device address, so make the
- *   first call on each device before any stream capture begins.
+ *   The first call on a device looks up that array's device address (once per
+ *   device, under a lock), so make the first call on each device before any stream
+ *   capture begins.  Each call copies the batch's schedule into the array from the
+ *   batch's own device memory (device to device, in stream order: the host does not
+ *   wait) and advances the batch's step count on the host when the call is made.
  *   The array is shared by every call in the process and keeps the last call's
  *   contents (the counter is cleared and the schedule rewritten before each
  *   launch); calls that overlap on the GPU -- on different streams, or for

@@ -1079,7 +1079,7 @@ gn_status gn_batch_step_static(gn_batch *b, int64_t n_steps)
             cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device), "device query");
             grid = std::max(1, std::min(b->n_nets, std::max(1, per_sm) * sms));
         }
-        cuda_check(gn::launch_batch_static(b->d_args.p, b->order.data(), b->n_nets, b->d_step.p,
+        cuda_check(gn::launch_batch_static(b->d_args.p, b->d_order.p, b->n_nets, b->d_step.p,
                                            static_cast<int>(n_steps), shape, grid, b->device, b->stream),
                    "batch launch with the static work queue");
         cuda_check(gn::launch_advance(b->d_step.p, n_steps, b->stream), "advance launch");

@@ -108,6 +108,9 @@ constexpr int kTypeA2 = 13;  // row offset of a_s^2, then 2 a_s and 1 / tau_c (b
 
 // A plastic model's kernel code: the node model | kPlastic.
 constexpr int kPlastic = 4;
+// A spiking model's code | kNoRing: the node update leaves the spike ring to its
+// caller (the resident kernel keeps spd as bits).
+constexpr int kNoRing = 8;
 constexpr uint32_t kSpikeStepsMax = 1u << 30;  // s saturates at this many steps
 
 // Calls f(std::integral_constant<int, m>) for node model m: every step kernel is
@@ -189,6 +192,26 @@ constexpr StagedShape kBatchStagedShape = {128, 3072, 4096, 256, 0};
 cudaError_t launch_batch_staged(int model, const StepArgs *nets, const int *tile_net, int n_tiles, int k, bool packed,
                                 bool stream_edges, size_t smem_bytes, bool launch_first, cudaStream_t s);
 cudaError_t batch_staged_prepare(int model, bool packed, bool stream_edges, size_t smem_bytes, int *ctas_per_sm);
+// resident kernel (k_resident.cu): one CTA holds a small network -- edges, row
+// pointers, history ring (FitzHugh-Nagumo FP32, spiking models one bit per node) and
+// node state -- in shared memory and runs n_steps steps per launch.  Byte offsets of
+// each array in the CTA's dynamic shared memory:
+struct ResidentLayout {
+    int32_t N, R, words, stride;  // nodes, ring slots, 32-bit words per spike-ring slot, floats per FHN slot
+    int64_t E;
+    uint32_t off_key, off_w, off_rp, off_S, off_long, off_ring, off_wc, off_v, off_rpq, off_hh, off_bgc, off_acc;
+    size_t bytes;
+};
+constexpr int kNumResidentShapes = 3;
+extern const int kResidentThreads[kNumResidentShapes];
+// the longest row the resident kernel takes: every kernel sums rows up to this length in
+// the same order
+constexpr int kResidentMaxRow = 1021;
+ResidentLayout resident_layout(int N, int64_t E, int R, int model, bool frame_avg);
+// raises the kernel's shared-memory limit to `bytes` of dynamic shared memory; returns
+// the largest dynamic size a CTA can have in *max_bytes
+cudaError_t resident_prepare(int model, int shape, size_t bytes, size_t *max_bytes);
+cudaError_t launch_resident(const StepArgs &a, const ResidentLayout &L, int n_steps, int shape, cudaStream_t s);
 // persistent bulk-copy pipelined variant (k_step_pipe.cu); grid = CTAs to launch
 cudaError_t launch_step_pipe(const StepArgs &a, int grid, int k, bool packed, bool stream_edges, cudaStream_t s);
 int step_pipe_smem_bytes(bool packed);
@@ -201,9 +224,10 @@ cudaError_t launch_batch(const StepArgs *nets, const int *order, int n_nets, int
                          int n_steps, int shape, int grid, cudaStream_t s);
 cudaError_t batch_occupancy(int shape, int *ctas_per_sm);
 // the same launch with its work queue in a file-scope device array (no allocation);
-// host_order must stay valid until the call returns (it is copied in stream order)
+// d_order is the batch's own device copy of the schedule, copied device to device
+// into the array in stream order
 constexpr int kStaticQueueNets = 65536;
-cudaError_t launch_batch_static(const StepArgs *nets, const int *host_order, int n_nets, const int64_t *d_step,
+cudaError_t launch_batch_static(const StepArgs *nets, const int *d_order, int n_nets, const int64_t *d_step,
                                 int n_steps, int shape, int grid, int device, cudaStream_t s);
 
 // estimator (k_est.cu)

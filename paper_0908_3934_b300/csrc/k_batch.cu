@@ -13,6 +13,8 @@
 // The history ring is written and read inside the same launch, so every read of
 // step data is a coherent load (never the read-only path); the barrier between
 // steps makes the CTA's writes of step n visible to its reads of step n + 1.
+#include <mutex>
+
 #include "step_common.cuh"
 
 namespace gn {
@@ -205,25 +207,38 @@ struct StaticQueue {
 static __device__ __align__(256) StaticQueue g_static_queue;
 
 constexpr int kMaxDevices = 64;
+// the array's device address on each device, looked up once per device (under the
+// lock, so host threads making their first calls at once do not race on the cache)
 StaticQueue *g_queue_addr[kMaxDevices] = {};
+std::mutex g_queue_lock;
+
+cudaError_t static_queue_address(int device, StaticQueue **out)
+{
+    std::lock_guard<std::mutex> lock(g_queue_lock);
+    if (!g_queue_addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_queue);  // the caller made `device` current
+        if (e != cudaSuccess) return e;
+        g_queue_addr[device] = static_cast<StaticQueue *>(p);
+    }
+    *out = g_queue_addr[device];
+    return cudaSuccess;
+}
 }  // namespace
 
-cudaError_t launch_batch_static(const StepArgs *nets, const int *host_order, int n_nets, const int64_t *d_step,
+cudaError_t launch_batch_static(const StepArgs *nets, const int *d_order, int n_nets, const int64_t *d_step,
                                 int n_steps, int shape, int grid, int device, cudaStream_t s)
 {
     if (n_nets <= 0 || n_steps <= 0) return cudaSuccess;
     if (n_nets > kStaticQueueNets || device < 0 || device >= kMaxDevices) return cudaErrorInvalidValue;
-    // device address of the array, looked up once per device with that device current
-    if (!g_queue_addr[device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_static_queue);
-        if (e != cudaSuccess) return e;
-        g_queue_addr[device] = static_cast<StaticQueue *>(p);
-    }
-    StaticQueue *q = g_queue_addr[device];
-    cudaError_t e = cudaMemsetAsync(&q->counter, 0, sizeof(int), s);
+    StaticQueue *q = nullptr;
+    cudaError_t e = static_queue_address(device, &q);
     if (e != cudaSuccess) return e;
-    e = cudaMemcpyAsync(q->order, host_order, static_cast<size_t>(n_nets) * sizeof(int), cudaMemcpyHostToDevice, s);
+    e = cudaMemsetAsync(&q->counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    // the schedule comes from the batch's device copy: a device-to-device copy in
+    // stream order, with no host buffer to wait on
+    e = cudaMemcpyAsync(q->order, d_order, static_cast<size_t>(n_nets) * sizeof(int), cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return e;
     switch (shape) {
         case 0: k_batch<128, 8><<<grid, 128, 0, s>>>(nets, q->order, n_nets, &q->counter, d_step, n_steps); break;
