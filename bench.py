@@ -47,6 +47,28 @@ NODE_BYTES = 36.2      # v~ read 4, (w~,c~) read 8 + write 8, ring write 4, row_
 STAGED_EDGE_BYTES = 6
 STAGED_GATHER_BYTES = 8
 KERNEL_NAMES = {1: "k_step", 2: "k_step_pipe", 3: "k_step_staged"}
+# format-independent bytes of one step: per edge-update a 10-byte edge record (weight 4,
+# source 4, delay 2) + the gathered FP32 history value 4; per node-step NODE_BYTES
+SURVEY_EDGE_BYTES = 14
+E2E_MIN_STEPS = 2000   # the end-to-end leg runs at least this many steps ...
+E2E_MIN_CHUNKS = 2     # ... in at least this many host round trips
+
+
+def survey_bytes(E: int, N: int, node_bytes: float = NODE_BYTES) -> float:
+    """Format-independent bytes of one step: 14 B per edge-update + node_bytes per node."""
+    return E * SURVEY_EDGE_BYTES + N * node_bytes
+
+
+def compact(x, digits: int = 4):
+    """The result with every float rounded to `digits` significant digits (the
+    printed line stays short; the details file keeps full precision)."""
+    if isinstance(x, float):
+        return float(f"{x:.{digits}g}")
+    if isinstance(x, dict):
+        return {k: compact(v, digits) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [compact(v, digits) for v in x]
+    return x
 
 
 def algorithmic_bytes(info: dict, E: int, N: int) -> float:
@@ -196,8 +218,28 @@ def replica_rate(units: float, seconds: float, device="cpu"):
     return u.item() / sec.item(), u.item(), sec.item()
 
 
+def host_cpu() -> str:
+    """The host's CPU model and logical core count."""
+    model = "unknown CPU"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return f"{model}, {os.cpu_count()} logical cores"
+
+
+WINDOW_STEPS = 4000  # the first 200 ms at dt = 0.05 ms: the parity window
+
+
 def cpu_baseline(spec, steps: int):
-    """The FP64 oracle as it stands, single-threaded, on the first `steps` steps."""
+    """The FP64 oracle as it stands (single-threaded C), on the first `steps` steps
+    of the network from rest.  Its cost per step does not depend on the activity
+    (every edge and node is visited every step), so the time of the 4000-step
+    window is extrapolated from the sample and labelled as such."""
     import oracle
     D = oracle.net_delays(spec)
     t0 = time.perf_counter()
@@ -206,6 +248,7 @@ def cpu_baseline(spec, steps: int):
     return dict(value=spec.n_edges * steps / dt, unit=METRIC, cores=1, kind="oracle",
                 sample=f"first {steps} steps of the same {spec.n_nodes}-node network from rest "
                        f"(FP64 C oracle, 1 thread; delays precomputed, untimed)",
+                host=host_cpu(), window_steps=WINDOW_STEPS, window_s_extrapolated=dt / steps * WINDOW_STEPS,
                 seconds=dt)
 
 
@@ -223,7 +266,8 @@ def run_reference(args):
             "steps": steps, "warmup": warm, "ms_per_step": cb["seconds"] / steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_of(args, spec, world),
-            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "host",
+                                                "window_steps", "window_s_extrapolated")},
             "e2e": {"value": cb["value"], "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -277,22 +321,58 @@ def run_batched(args, local, stream, rank):
         t_sample += ev0.elapsed_time(ev1) / 1e3
         net.gn_net_destroy()
     t_loop = t_sample / len(pick) * len(specs)
-    return {"workload": f"{len(specs)} independent 2D nets, N log-uniform in [32, 4096], "
+    return {"details_workload": f"{len(specs)} independent 2D nets, N log-uniform in [32, 4096], "
                         f"{N} nodes, {E} edges, {steps} steps ({steps * 0.05:.0f} ms)",
-            "value": E * steps / t, "unit": METRIC, "seconds": t, "ms_per_step": t / steps * 1e3,
-            "rtf": steps * 0.05e-3 / t, "cta_threads": info["cta_threads"], "grid": info["grid"],
+            "value": E * steps / t, "details_unit": METRIC, "seconds": t, "ms_per_step": t / steps * 1e3,
+            "details_rtf": steps * 0.05e-3 / t, "details_cta_threads": info["cta_threads"], "details_grid": info["grid"],
             "step_kernel": info["step_kernel"],
             # kernel 3: member groups stepped a 64-step chunk at a time (L2 blocking), in lanes
             # of concurrent launch chains; 1 group = every member every step
             "step_groups": info["step_groups"], "step_lanes": info["step_lanes"],
             # kernel 1: one persistent launch; kernel 3: one per group and step + one advance per
             # 64-step graph (and per ragged tail)
-            "gpu_launches": 1 if info["step_kernel"] == 1
+            "details_gpu_launches": 1 if info["step_kernel"] == 1
             else steps * max(1, info["step_groups"]) + (steps + 63) // 64,
-            "loop_plain": {"value": E * steps / t_loop, "seconds_extrapolated": t_loop,
-                           "sample": f"{len(pick)} random nets timed one after another, "
+            "loop_plain": {"value": E * steps / t_loop, "details_seconds_extrapolated": t_loop,
+                           "details_sample": f"{len(pick)} random nets timed one after another, "
                                      f"{t_sample:.3f} s, extrapolated by count to {len(specs)}"},
             "speedup_vs_loop": t_loop / t}
+
+
+def run_size(name: str, steps: int, warmup: int, local, stream, rank):
+    """Another size of the plain path (config 2's 100k-node net, the 1M-node net's
+    literal 5 % hubs, its slow-conduction variant): device time per step on the
+    launching stream after `warmup` untimed steps, edge-updates/s, real-time
+    factor, and the step's algorithmic bytes over the measured HBM peak, both in
+    the format-independent count (14 B per edge-update + 36.2 B per node) and in the
+    chosen kernel's own format."""
+    import torch
+    from paper_0908_3934_b300 import geonet
+    t0 = time.perf_counter()
+    spec = workload(name, rank)
+    t_gen = time.perf_counter() - t0
+    net = geonet.Net(spec, device=local, stream=stream.cuda_stream, obs_capacity=64)
+    net.gn_step(max(3, warmup))
+    net.gn_synchronize()
+    info = net.gn_net_get_info()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    net.gn_step(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t = ev0.elapsed_time(ev1) / 1e3
+    net.gn_net_destroy()
+    E, N = spec.n_edges, spec.n_nodes
+    step_s = t / steps
+    peak, _ = peaks()
+    return {"details_workload": f"{name}: N={N}, E={E}, dt={spec.dt_ms:g} ms, max delay {info['max_delay']} steps, "
+                        f"ring {info['ring_depth']}",
+            "details_steps": steps, "ms_per_step": step_s * 1e3, "value": E * steps / t, "details_unit": METRIC,
+            "rtf": spec.dt_ms * 1e-3 / step_s, "details_node_steps_per_s": N * steps / t,
+            "kernel": KERNEL_NAMES[info["step_kernel"]],
+            "frac_survey": survey_bytes(E, N) / step_s / 1e9 / peak,
+            "frac_format": algorithmic_bytes(info, E, N) / step_s / 1e9 / peak,
+            "details_gpu_launches": steps + (steps + 63) // 64, "details_generate_s": t_gen}
 
 
 IZH_NODE_BYTES = 56.2  # V r/w 8, (W, c) r/w 16, (r, p) r/w 16, spike-ring write 4, piece list 4,
@@ -347,14 +427,15 @@ def run_spiking(args, spec, local, stream, model: str, plastic: bool = False):
     if plastic:
         nodes += (f", plastic weights (spike-time-dependent, alpha {STDP_DEMO['alpha']}/ms, "
                   f"beta {STDP_DEMO['beta']}/ms)")
-    out = {"workload": f"the same {N}-node network, {nodes}, dt = {ispec.dt_ms} ms, max delay {info['max_delay']} steps",
-            "value": E * steps / t, "unit": METRIC, "ms_per_step": step_s * 1e3, "steps": steps,
-            "node_steps_per_s": N * steps / t,
+    out = {"details_workload": f"the same {N}-node network, {nodes}, dt = {ispec.dt_ms} ms, max delay {info['max_delay']} steps",
+            "value": E * steps / t, "details_unit": METRIC, "ms_per_step": step_s * 1e3, "details_steps": steps,
+            "details_node_steps_per_s": N * steps / t,
             "rtf": ispec.dt_ms * 1e-3 / step_s, "spikes_per_node_per_s": n_spikes / N / (steps * ispec.dt_ms * 1e-3),
-            "step_kernel": KERNEL_NAMES[info["step_kernel"]],
-            "roofline": {"bound": "hbm", "achieved": bytes_step / step_s / 1e9, "peak": peak, "unit": "GB/s",
-                         "frac": bytes_step / step_s / 1e9 / peak, "algorithmic_bytes_per_launch": bytes_step},
-            "gpu_launches": steps + steps // 64}
+            "details_step_kernel": KERNEL_NAMES[info["step_kernel"]],
+            "frac": bytes_step / step_s / 1e9 / peak,
+            "details_roofline": {"bound": "hbm", "achieved": bytes_step / step_s / 1e9, "peak": peak, "unit": "GB/s",
+                                 "algorithmic_bytes_per_launch": bytes_step},
+            "details_gpu_launches": steps + steps // 64}
     out["nonfinite_nodes"] = nonfinite
     if plastic:
         out["weights_changed_frac"] = changed
@@ -407,17 +488,17 @@ def run_test_set(args, local, stream, model: str = "izh"):
         big = [r[3] for r in rows if f"_{cls}_" in r[0] and r[1] == max(netgen.TEST_SET_SIZES)]
         by_class[cls] = {"min": min(big), "max": max(big)}
     nodes = ("Hodgkin-Huxley + alpha-PSC nodes, dt = 0.03 ms" if hh else "Izhikevich + alpha-PSC nodes, dt = 1 ms")
-    return {"workload": f"the 80 test-set networks (N = 10 .. 1000, 2D / 3D, lattice / small world / scale free / "
+    return {"details_workload": f"the 80 test-set networks (N = 10 .. 1000, 2D / 3D, lattice / small world / scale free / "
                         f"random, low / high density), {nodes}, {steps} steps each, 20 Hz background pulses",
-            "metric": "real-time factor (simulated time / device time)",
+            "details_metric": "real-time factor (simulated time / device time)",
             "rtf_min": min(rtf), "rtf_median": st.median(rtf), "rtf_max": max(rtf),
-            "rtf_n1000_by_class": by_class,
-            "largest": max(rows, key=lambda r: r[2])[0],
+            "details_rtf_n1000_by_class": by_class,
+            "details_largest": max(rows, key=lambda r: r[2])[0],
             "batched": {"rtf_every_network": steps * dt * 1e-3 / t_batch,
                         "network_seconds_per_second": len(ispecs) * steps * dt * 1e-3 / t_batch,
                         "speedup_vs_one_after_another": sum(r[4] for r in rows) / t_batch,
-                        "gpu_launches": steps + steps // 64},
-            "networks": [{"name": r[0], "N": r[1], "E": r[2], "rtf": round(r[3], 1)} for r in rows]}
+                        "details_gpu_launches": steps + steps // 64},
+            "details_networks": [{"name": r[0], "N": r[1], "E": r[2], "rtf": round(r[3], 1)} for r in rows]}
 
 
 def run_estimator(args, local, stream):
@@ -474,14 +555,22 @@ def run_estimator(args, local, stream):
     t_score = ev0.elapsed_time(ev1) / 1e3
     learned = pipeline.scores(p_te, te["label"], thr_learned)
     plain = pipeline.scores(sc, te["label"], thr_plain)
-    return {"workload": f"{args.est_train} training + {args.est_test} held-out nets of N=512 (config-5 laws), "
+    return {"details_workload": f"{args.est_train} training + {args.est_test} held-out nets of N=512 (config-5 laws), "
                         f"{P_tr} + {P} candidate pairs, {args.est_epochs} epochs of batch 8192",
             "auroc_learned": learned["auroc"], "auroc_plain": plain["auroc"],
             "f1_learned": learned["f1"], "f1_plain": plain["f1"],
-            "pairs_scored_per_s": P / t_score, "unit": "candidate pairs/s (features + inference)",
-            "train_samples_per_s": P_tr * args.est_epochs / t_train, "loss_first_last": [losses[0], losses[-1]],
-            "seconds": {"generate_host": t_gen, "simulate_and_features_train": t_sim_train, "train": t_train,
+            "pairs_scored_per_s": P / t_score, "details_unit": "candidate pairs/s (features + inference)",
+            "train_samples_per_s": P_tr * args.est_epochs / t_train, "details_loss_first_last": [losses[0], losses[-1]],
+            "details_seconds": {"generate_host": t_gen, "simulate_and_features_train": t_sim_train, "train": t_train,
                         "score": t_score}}
+
+
+def strip_details(x):
+    """The result without its per-network rows and layout tables (keys starting
+    with 'details_'), which go to the --details file only."""
+    if isinstance(x, dict):
+        return {k: strip_details(v) for k, v in x.items() if not k.startswith("details_")}
+    return x
 
 
 def main():
@@ -500,6 +589,10 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=10000, help="steps of the batched measurement")
     ap.add_argument("--loop-sample", type=int, default=32, help="networks timed by the looped comparison")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--sizes", default="large:4000,roofline_hubs5:2000,roofline_slow:2000",
+                    help="other sizes of the plain path timed after the headline one (name:steps,...)")
+    ap.add_argument("--no-sizes", action="store_true")
+    ap.add_argument("--details", default=None, help="write the full result (every row, full precision) here")
     ap.add_argument("--est-train", type=int, default=2000, help="training nets of the estimator measurement")
     ap.add_argument("--est-test", type=int, default=200, help="held-out nets of the estimator measurement")
     ap.add_argument("--est-epochs", type=int, default=8)
@@ -571,8 +664,8 @@ def main():
     # host memory (the controls u_j), steps, and reads the observations back into a
     # pinned host buffer
     rng = np.random.default_rng(77 + rank)
-    chunk = max(1, min(args.e2e_chunk, args.steps))
-    n_chunks = max(1, args.steps // chunk)
+    chunk = max(1, args.e2e_chunk)
+    n_chunks = max(E2E_MIN_CHUNKS, -(-max(E2E_MIN_STEPS, args.steps) // chunk))
     t_sim = (net.gn_net_get_info()["step"] + chunk) * spec.dt_ms
     pulses = [[(int(j), t_sim + (c * chunk + rng.uniform(0, chunk)) * spec.dt_ms,
                 t_sim + (c * chunk + rng.uniform(0, chunk)) * spec.dt_ms + 2.0, 1.0)
@@ -606,25 +699,39 @@ def main():
     step_s = t / args.steps
     bytes_step = algorithmic_bytes(info, E, N)
     achieved = bytes_step / step_s / 1e9
+    bytes_survey = survey_bytes(E, N)
+    traffic = traffic_per_launch(KERNEL_NAMES[info["step_kernel"]], args.workload, info["grid"])
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_of(args, spec, world),
         "node_steps_per_s": (value / E_total) * N * world, "rtf": spec.dt_ms * 1e-3 / step_s,
+        # frac: the chosen kernel's own format (bytes it must move); frac_survey: the
+        # format-independent 14 B per edge-update; frac_dram: ncu's DRAM bytes per launch
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_source": peak_kind,
-                     "traffic": traffic_per_launch(KERNEL_NAMES[info["step_kernel"]], args.workload, info["grid"]),
-                     "algorithmic_bytes_per_launch": bytes_step,
-                     "kernel": KERNEL_NAMES[info["step_kernel"]]},
+                     "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": bytes_step, "kernel": KERNEL_NAMES[info["step_kernel"]],
+                     "bytes_survey": bytes_survey, "frac_survey": bytes_survey / step_s / 1e9 / peak,
+                     "frac_dram": traffic / step_s / 1e9 / peak if traffic else None},
         "e2e": {"value": e2e_value, "unit": METRIC,
-                "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps},
+                "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps,
+                "steps": e2e_steps, "chunks": n_chunks},
         "gpu_launches": launches, "clocks": clocks,
-        "layout": {"step_kernel": info["step_kernel"], "grid": info["grid"], "cta_threads": info["step_threads"],
+        "details_layout": {"step_kernel": info["step_kernel"], "grid": info["grid"], "cta_threads": info["step_threads"],
                    "edges_per_thread": info["step_edges_per_thread"],
                    "ring_depth": info["ring_depth"], "edge_format": info["edge_format"],
                    "n_blocks": info["n_blocks"], "max_delay": info["max_delay"],
                    "device_bytes": info["device_bytes"]},
     }
+    if not args.no_sizes:
+        sizes = {}
+        for item in args.sizes.split(","):
+            name, steps = item.split(":")
+            r = run_size(name, int(steps), args.warmup, local, stream, rank)
+            sec = r["steps"] * r["ms_per_step"] / 1e3
+            r["value"], _, _ = replica_rate(r["value"] * sec, sec, dev)
+            sizes[name] = r
+        line["sizes"] = sizes
     if not args.no_batched:
         bt = run_batched(args, local, stream, rank)
         bt["value"], _, bt["seconds"] = replica_rate(bt["value"] * bt["seconds"], bt["seconds"], dev)
@@ -643,9 +750,13 @@ def main():
         line["estimator"] = run_estimator(args, local, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(spec, args.cpu_steps)
-        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "host",
+                                                   "window_steps", "window_s_extrapolated")}
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        if args.details:
+            with open(args.details, "w") as f:
+                json.dump(line, f, indent=1)
+        print(json.dumps(compact(strip_details(line))), flush=True)
     net.gn_net_destroy()
     if world > 1:
         dist.destroy_process_group()

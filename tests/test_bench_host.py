@@ -78,3 +78,14 @@ def test_config_names_the_workload_as_generated():
     big = bench.config_of(SimpleNamespace(workload="large"), netgen.large(n=2000, mean_deg=20.0), 2)
     assert "5 Hz background" in big["workload"] and "ring 256" in big["workload"]
     assert big["replicas"] == 2 and big["parallelism"] == "replicas2" and big["dt_ms"] == 0.05
+
+
+def test_printed_line_drops_details_and_rounds():
+    line = {"value": 1.23456789e11, "config": {"workload": "x"}, "steps": 20,
+            "test_set": {"rtf_min": 12.3456, "details_networks": [{"name": "a"}]}, "details_layout": {"grid": 1}}
+    out = bench.compact(bench.strip_details(line))
+    assert out == {"value": 1.235e11, "config": {"workload": "x"}, "steps": 20, "test_set": {"rtf_min": 12.35}}
+
+
+def test_survey_bytes_are_format_independent():
+    assert bench.survey_bytes(1000, 100) == pytest.approx(1000 * 14 + 100 * 36.2)
