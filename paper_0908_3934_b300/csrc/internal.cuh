@@ -248,32 +248,41 @@ int64_t ncc_scratch_floats(int64_t M, int T);
 // MLP of the learned estimator (k_mlp.cu); hidden width 256, inputs padded to 64
 constexpr int kMlpHidden = 256;
 constexpr int kMlpInPad = 64;
+// Device buffers of one MLP (owned by the host runtime, mlp.cu).  Parameters, their
+// gradients and Adam moments are packed FP32 [W1 (in x 256) | b1 | W2 | b2 | w3 | b3];
+// wimg holds the BF16 weight images the tile kernel streams (9 chunks of 32 KB: W1t,
+// W2t in four K-chunks, W2b in four K-chunks); the *_img buffers the batch-major
+// operands of the weight gradients, one image per 64 rows of the batch.
+struct MlpBuffers {
+    int in_dim;
+    int64_t n_params, off_W1, off_b1, off_W2, off_b2, off_w3, off_b3;
+    float *params, *grads, *m, *v;
+    void *wimg, *xt_img, *h1t_img, *dh2t_img, *dh1t_img;
+    float *part_w2;    // [splits][256][256]
+    float *part_w1;    // [splits][256][64] (dW1 transposed)
+    float *part_head;  // [tiles][2 * 256 + 2]
+    float *part_b1;    // [tiles][256]
+    float *loss_sum;   // [1]
+    unsigned int *status;
+};
 cudaError_t mlp_prepare();
-// cursor (device, may be null): batch index of a replayed training epoch, so row b
-// of the batch is idx[cursor * B + b]
-cudaError_t mlp_launch_cast(const float *X, const int64_t *idx, const int64_t *cursor, int B, int in_dim, int Bp,
-                            void *Xb, cudaStream_t s);
-// Every GEMM runs on tcgen05 (k_mlp.cu); *status gets kStatusTimeout if a bounded
-// wait gave up.  Layer: out = epilogue(A [Bp][K] x Bt[256][K]^T), Bp a multiple of
-// 128, K of 64; out_t (may be null) receives the BF16 output transposed, [256][Bp].
-cudaError_t mlp_launch_layer(int epi, const void *A, int Bp, int K, const void *Bt, const float *bias, const void *mask,
-                             void *out, void *out_t, float *col_partial, unsigned int *status, cudaStream_t s);
-// Weight-gradient partials over the batch: AT [M][Bp], BT [N][Bp] (batch-contiguous);
-// split z covers rows [z chunk, (z + 1) chunk) of the batch and writes
-// partial[z][M][N] (N = 256) or, transposed, partial[z][N][M] (N = 64).
-cudaError_t mlp_launch_wgrad(const void *AT, int M, const void *BT, int N, int Bp, int chunk, bool transposed,
-                             float *partial, unsigned int *status, cudaStream_t s);
-cudaError_t mlp_launch_transpose(const void *in, int R, int C, void *out, cudaStream_t s);
-cudaError_t mlp_launch_head(const float *H2, const float *w3, const float *b3, const float *y, const int64_t *idx,
-                            const int64_t *cursor, int B, int Bp, int rows_per_cta, float *p, void *dH2, float *partial,
-                            cudaStream_t s);
-cudaError_t mlp_launch_sum(const float *part, int n, int64_t len, float *out, cudaStream_t s);
-cudaError_t mlp_launch_adamw(float *w, const float *g, float *m, float *v, int64_t n, float lr, float beta1, float beta2,
-                             float eps, float wd, float bc1, float bc2, const float *bc_table, const int64_t *cursor,
-                             cudaStream_t s);
+size_t mlp_wimg_bytes();
+size_t mlp_xt_bytes(int Bp);
+size_t mlp_ht_bytes(int Bp);
+// splits of the weight-gradient reduction over the batch and the 64-row chunks of each
+int mlp_wgrad_splits(int Bp, int *chunks_per_split);
+// Forward (+ backward with labels y) of B rows, Bp = B rounded up to 128; row b of the
+// batch is X[idx[cursor * B + b]] (idx, cursor may be null).  Every kernel sets
+// *status to kStatusTimeout if a bounded wait gave up.
+cudaError_t mlp_launch_tile(const MlpBuffers &b, const float *X, const int64_t *idx, const int64_t *cursor,
+                            const float *y, int B, int Bp, float *p_out, cudaStream_t s);
+cudaError_t mlp_launch_wgrad(const MlpBuffers &b, int Bp, cudaStream_t s);
+// gradients into b.grads and the loss sum into b.loss_sum; with adamw also the AdamW
+// step (bias corrections bc1, bc2, or bc_table[2 cursor + {0, 1}]) and the weight images
+cudaError_t mlp_launch_update(const MlpBuffers &b, int Bp, bool adamw, float lr, float wd, float bc1, float bc2,
+                              const float *bc_table, const int64_t *cursor, cudaStream_t s);
+cudaError_t mlp_launch_refresh(const MlpBuffers &b, cudaStream_t s);
 cudaError_t mlp_launch_epoch_tail(const float *loss_sum, int B, int64_t *cursor, float *losses, cudaStream_t s);
-cudaError_t mlp_launch_refresh(const float *W1, int in_dim, const float *W2, void *W1t, void *W2t, void *W2b,
-                               cudaStream_t s);
 
 cudaError_t launch_delay(int64_t n_edges, int32_t dim, const double *pos, const int32_t *src,
                          const int32_t *dst, const double *speed, double speed_scalar, double dt_ms,

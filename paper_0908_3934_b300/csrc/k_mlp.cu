@@ -1,12 +1,30 @@
 // Kernels of the learned connectivity estimator: an MLP in -> 256 -> 256 -> 1
 // (ReLU hidden layers, sigmoid output, binary cross-entropy), BF16 tensor-core
-// GEMMs with FP32 accumulation, FP32 master weights and AdamW.
+// GEMMs (tcgen05, FP32 accumulation in tensor memory), FP32 master weights, AdamW.
 //
 // Precision (mirrored by the FP64 oracle): inputs, weight copies, the first hidden
-// activation and the backward activations are BF16; every accumulation is FP32;
-// the second hidden activation, the output layer and all reductions are FP32.
-// Every reduction is done in a fixed order (per-CTA partials, then a reduction
-// kernel), so results do not depend on scheduling.
+// activation and the backward activations dH2, dH1 are BF16; every accumulation is
+// FP32; the second hidden activation, the output layer and all reductions are FP32.
+// Every reduction runs in a fixed order (per-CTA partials summed in CTA order), so
+// a result does not depend on scheduling.
+//
+// One training step is four launches:
+//   k_tile   per 128-row tile of the batch: the forward pass (X W1, H1 W2 on the
+//            tensor cores), the output layer and loss, dH2 and dH1 = dH2 W2^T, with
+//            the per-tile column sums of the bias and output-layer gradients; it
+//            writes the batch-major (transposed) operands of the weight gradients
+//            in the shared-memory image the next kernel copies in one piece;
+//   k_wgrad  dW2 = H1^T dH2 and dW1^T = dH1^T X split over the batch (fixed-order
+//            partials), operands brought in by bulk asynchronous copies;
+//   k_update the partials summed in order, AdamW on the FP32 masters, and the BF16
+//            weight images the tile kernel streams;
+//   k_epoch_tail (replayed epochs) the loss of the step and the batch cursor.
+//
+// Shared-memory operand layout (tcgen05 K-major, no swizzle): a matrix of R rows x 64
+// K-elements is a chunk of core matrices of 8 rows x 16 bytes; element (r, c) sits at
+// byte (r / 8) 1024 + (c / 8) 128 + (r % 8) 16 + (c % 8) 2 (LBO 128 B along K, SBO
+// 1024 B along rows).  Weights and the transposed activations are kept in global
+// memory in exactly this image, so one 1D bulk copy lands a chunk.
 #include <cuda_bf16.h>
 
 #include "internal.cuh"
@@ -15,110 +33,140 @@
 namespace gn {
 namespace {
 
-constexpr int kH = 256;    // hidden width
-constexpr int kKP = 64;    // padded input width
+constexpr int kH = kMlpHidden;   // 256
+constexpr int kKP = kMlpInPad;   // 64
+constexpr int kBM = 128;         // batch rows per tile
+constexpr uint32_t kWChunk = 256u * 64u * 2u;  // one weight chunk: 256 rows x 64 K, BF16 (32 KB)
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+__host__ __device__ constexpr uint32_t img_off(uint32_t r, uint32_t c)
 {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+    return (r >> 3) * 1024u + (c >> 3) * 128u + (r & 7u) * 16u + (c & 7u) * 2u;
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// ---------------------------------------------------------------------------
-// Row b of the batch is X[idx[o + b]] (or X[b] without idx), FP32 -> Xb [Bp][64]
-// BF16, zero padded (columns >= in, rows >= B).  o = (*cursor) B with a device batch
-// cursor (a replayed training epoch), else 0.
 __device__ __forceinline__ int64_t batch_row(const int64_t *idx, const int64_t *cursor, int B, int64_t r)
 {
     if (!idx) return r;
     return idx[(cursor ? *cursor * B : 0) + r];
 }
 
-__global__ void k_cast_x(const float *__restrict__ X, const int64_t *__restrict__ idx, const int64_t *__restrict__ cursor,
-                         int B, int in_dim, int Bp, __nv_bfloat16 *__restrict__ Xb)
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b)
 {
-    const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-    if (i >= static_cast<int64_t>(Bp) * kKP) return;
-    const int r = static_cast<int>(i / kKP), c = static_cast<int>(i % kKP);
-    float v = 0.0f;
-    if (r < B && c < in_dim) {
-        v = X[batch_row(idx, cursor, B, r) * in_dim + c];
-    }
-    Xb[i] = __float2bfloat16_rn(v);
+    const __nv_bfloat162 pr = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&pr);
 }
 
-// ---------------------------------------------------------------------------
-// Layer GEMM C[m][n] = sum_k A[m][k] Bt[n][k] (A row-major [M][K] BF16, Bt row-major
-// [256][K] BF16, FP32 accumulation, K a multiple of 64) with a fused epilogue:
-// kReluBf16: BF16 relu(C + bias); kReluF32: FP32 relu(C + bias); kMaskBf16: BF16
-// C where mask > 0 (else 0), plus per-64-row column sums of that output.
-enum Epi { kReluBf16 = 0, kReluF32 = 1, kMaskBf16 = 2 };
+// 32 columns (c0 .. c0 + 31) of this thread's row as BF16 into a K-major operand of
+// 128 rows held as chunks of 64 K-elements (16 KB apart).
+__device__ __forceinline__ void put_row32(uint8_t *op, int row, int c0, const float (&v)[32])
+{
+    uint8_t *base = op + (c0 >> 6) * 16384 + (row >> 3) * 1024 + (row & 7) * 16 + ((c0 & 63) >> 3) * 128;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint4 u = make_uint4(pack_bf16(v[8 * q], v[8 * q + 1]), pack_bf16(v[8 * q + 2], v[8 * q + 3]),
+                                   pack_bf16(v[8 * q + 4], v[8 * q + 5]), pack_bf16(v[8 * q + 6], v[8 * q + 7]));
+        *reinterpret_cast<uint4 *>(base + q * 128) = u;
+    }
+}
 
-// ---------------------------------------------------------------------------
-// Every GEMM of the MLP on tcgen05: C[m][n] = sum_k A[m][k] B[n][k] (both operands
-// K-contiguous BF16, FP32 accumulation in tensor memory).  One CTA of 128 threads
-// computes a 128 x BN tile over `kc` chunks of 64 along K (CTA z of a split-K grid
-// starts at chunk z * kc).  Chunks are double-buffered: the 128 threads copy A and B
-// rows with 16-byte cp.async into the K-major core-matrix layout (8 rows x 16 bytes
-// per core matrix, 128 bytes apart along K, 1024 bytes apart along rows -- thread c
-// writes bytes [16c, 16c + 16) of a buffer), one thread issues four 128 x BN x 16
-// MMAs per chunk and commits them to the chunk's mbarrier.  Epilogue: warp w reads
-// TMEM lanes 32w .. 32w + 31 (its rows) with tcgen05.ld, 32 columns at a time:
-//   kReluBf16   BF16 relu(C + bias) (+ a transposed copy [col][row])
-//   kReluF32    FP32 relu(C + bias)
-//   kMaskBf16   BF16 C where mask > 0, else 0 (+ transposed copy), and per-64-row
-//               column sums of it to col_partial[row / 64][col] in a fixed order
-//               (reduce-scatter over a warp's 32 rows, then the two warps of a group)
-//   kPartF32    FP32 C tile of split z to partial[z][row][col]
-//   kPartF32T   the same transposed, partial[z][col][row]
-// Every wait is bounded: on a time-out the CTA sets *status, waits once more for its
-// MMAs, frees its tensor memory and leaves.
-enum GemmEpi { kPartF32 = 3, kPartF32T = 4 };
+// The warp's 32 rows x 32 features (f0 .. f0 + 31) as BF16 into the batch-major image
+// of a weight-gradient operand: rows = features, K = the 64 batch rows of a chunk.
+// `chunk` points at the 64-row chunk's image (feature f, batch row m at img_off(f, m));
+// mrow0 = the first of the warp's rows within that chunk (0 or 32).  Through a
+// per-warp staging tile so each lane stores 16 contiguous bytes (8 rows of one
+// feature) and 8 lanes cover 128 contiguous bytes.
+__device__ __forceinline__ void put_cols32(uint8_t *chunk, int f0, int mrow0, const float (&v)[32], uint16_t *stage,
+                                           int lane)
+{
+    constexpr int kPitch = 40;  // uint16 per staging row: 32 rows + 8 pad (80 B, 16-byte aligned)
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+        stage[j * kPitch + lane] = __bfloat16_as_ushort(__float2bfloat16_rn(v[j]));
+    __syncwarp();
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+        const int f = 8 * it + (lane & 7), g = lane >> 3;  // feature, group of 8 rows
+        const uint4 u = *reinterpret_cast<const uint4 *>(stage + f * kPitch + 8 * g);
+        *reinterpret_cast<uint4 *>(chunk + img_off(f0 + f, mrow0 + 8 * g)) = u;
+    }
+    __syncwarp();
+}
 
-struct GemmArgs {
-    const __nv_bfloat16 *A;  // [.][lda], rows m0 ..
-    int64_t lda;
-    const __nv_bfloat16 *B;  // [.][ldb], rows n0 ..
-    int64_t ldb;
-    int kc;                  // chunks of 64 along K per CTA
-    const float *bias;
-    const __nv_bfloat16 *mask;
-    void *out;               // row-major, kH columns
-    __nv_bfloat16 *out_t;    // transposed BF16 copy [kH][ldt], or null
-    int64_t ldt;
-    float *col_partial;
-    float *partial;          // split-K tiles
-    int64_t partial_stride;  // floats between the tiles of consecutive splits
+// Column sums of 32 values over the warp's 32 rows (reduce-scatter: lane l ends with
+// column l), a fixed order.
+__device__ __forceinline__ float col_sum32(float (&v)[32], int lane)
+{
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const float send = upper ? v[i] : v[i + o];
+            const float keep = upper ? v[i + o] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return v[0];
+}
+
+struct TileArgs {
+    const float *X;          // [.][in_dim] FP32 features
+    const int64_t *idx;      // row b of the batch is X[idx[cursor B + b]] (null: X[b])
+    const int64_t *cursor;   // device batch cursor of a replayed epoch, or null
+    const float *y;          // labels (null: inference only)
+    int B, Bp, in_dim;
+    const uint8_t *wimg;     // 9 weight chunks: W1t, W2t (4 K-chunks), W2b (4 K-chunks)
+    const float *params;     // FP32 masters: b1, b2, w3, b3 read here
+    int64_t off_b1, off_b2, off_w3, off_b3;
+    float *p_out;            // [B] probabilities
+    uint8_t *xt_img, *h1t_img, *dh2t_img, *dh1t_img;  // batch-major operand images, per 64-row chunk
+    float *part_head;        // [tiles][2 kH + 2]: dw3, db2, db3, loss of each tile
+    float *part_b1;          // [tiles][kH]
     unsigned int *status;
 };
 
-template <int EPI, int BN>
-__global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs g)
+// Shared memory of k_tile (dynamic): weight ring 2 x 32 KB | X 16 KB | H1 64 KB | dH2 64 KB
+// | staging 4 x 2560 B.  The column sums (2 x 4 warps x 256 floats) reuse the X operand,
+// which is dead once layer 1's MMAs are complete.
+constexpr int kOffRing = 0;
+constexpr int kOffX = kOffRing + 2 * static_cast<int>(kWChunk);
+constexpr int kOffH1 = kOffX + 16384;
+constexpr int kOffD2 = kOffH1 + 65536;
+constexpr int kOffStage = kOffD2 + 65536;
+constexpr int kOffCols = kOffX;
+constexpr int kTileSmem = kOffStage + 4 * 2560;
+static_assert(2 * 4 * kH * 4 <= 16384, "column sums fit the X operand");
+
+template <bool kTrain>
+__global__ void __launch_bounds__(128, 1) k_tile(const TileArgs g)
 {
-    constexpr int BM = 128, BK = 64;
-    constexpr int kStageA = BM * BK * 2, kStageB = BN * BK * 2;  // bytes of one buffer
-    constexpr uint32_t kIdesc = idesc_bf16_f32(BM, BN);
-    extern __shared__ __align__(1024) uint8_t smem_raw[];
-    uint8_t *sA = smem_raw;                  // [2][kStageA]
-    uint8_t *sB = smem_raw + 2 * kStageA;    // [2][kStageB]
-    __shared__ __align__(8) uint64_t s_bar[2];
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ __align__(8) uint64_t s_full[2], s_empty[2], s_mma;
     __shared__ uint32_t s_tmem;
     __shared__ int s_fail;
-    __shared__ float s_cs[4][BN];
-
+    __shared__ float s_red[4][2];
+    uint8_t *ring = smem + kOffRing;
+    uint8_t *sX = smem + kOffX;
+    uint8_t *sH1 = smem + kOffH1;
+    uint8_t *sD2 = smem + kOffD2;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int64_t m0 = static_cast<int64_t>(blockIdx.x) * BM;
-    const int n0 = blockIdx.y * BN;
-    const int64_t kbase = static_cast<int64_t>(blockIdx.z) * g.kc * BK;
+    uint16_t *stage = reinterpret_cast<uint16_t *>(smem + kOffStage + warp * 2560);
+    float *cols = reinterpret_cast<float *>(smem + kOffCols);  // [2][4 warps][kH]
+    const int tile = blockIdx.x;
+    const int64_t row = static_cast<int64_t>(tile) * kBM + t;  // this thread's batch row
+    const bool valid = row < g.B;
+    constexpr uint32_t kIdesc = idesc_bf16_f32(128, 256);
+    const int n_chunks = kTrain ? 9 : 5;  // W1t, W2t x 4, (W2b x 4)
+
     if (warp == 0) {
-        tmem_alloc(&s_tmem, BN);
+        tmem_alloc(&s_tmem, 512);
         tmem_relinquish();
     }
     if (t == 0) {
-        mbar_init(&s_bar[0], 1);
-        mbar_init(&s_bar[1], 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&s_full[i], 1);
+            mbar_init(&s_empty[i], 1);
+        }
+        mbar_init(&s_mma, 1);
         fence_barrier_init();
         s_fail = 0;
     }
@@ -126,244 +174,484 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs g)
     __syncthreads();
     tc_fence_after_sync();
     const uint32_t tmem = s_tmem;
-
-    auto load = [&](int stage, int64_t k0) {
-        uint8_t *a = sA + stage * kStageA;
-        uint8_t *b = sB + stage * kStageB;
-#pragma unroll
-        for (int i = 0; i < BM * 8 / 128; ++i) {
-            const int c = t + 128 * i;  // 16-byte piece: row (c & 7) + 8 (c >> 6), K piece (c >> 3) & 7
-            const int r = (c & 7) + 8 * (c >> 6), kp = (c >> 3) & 7;
-            cp_async16(a + 16 * c, g.A + (m0 + r) * g.lda + k0 + kp * 8);
-            if (c < BN * 8) cp_async16(b + 16 * c, g.B + static_cast<int64_t>(n0 + r) * g.ldb + k0 + kp * 8);
+    bool ok = true;
+    auto load = [&](int c) {  // weight chunk c into stage c & 1
+        mbar_arrive_expect_tx(&s_full[c & 1], kWChunk);
+        bulk_g2s(ring + (c & 1) * kWChunk, g.wimg + static_cast<size_t>(c) * kWChunk, kWChunk, &s_full[c & 1]);
+    };
+    int loaded = 0;  // chunks whose copies were issued (thread 0)
+    if (t == 0) {
+        load(0);
+        load(1);
+        loaded = 2;
+    }
+    // refill: chunk c's MMAs are complete -> its stage takes chunk c + 2
+    auto refill = [&](int c) {
+        if (!mbar_wait_bounded(&s_empty[c & 1], (c >> 1) & 1, kDefaultWaitLimit)) ok = false;
+        if (ok && c + 2 < n_chunks) {
+            load(c + 2);
+            loaded = c + 3;
         }
-        cp_async_commit();
+    };
+    // four M=128 N=256 K=16 MMAs of chunk c (A: a K-chunk of an operand in shared memory)
+    auto mma = [&](int c, const uint8_t *a, uint32_t d, bool first) {
+        if (!mbar_wait_bounded(&s_full[c & 1], (c >> 1) & 1, kDefaultWaitLimit)) ok = false;
+        if (!ok) return;
+        tc_fence_after_sync();
+        const uint8_t *b = ring + (c & 1) * kWChunk;
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks)
+            tc_mma_bf16(d, smem_desc_kmajor(a + ks * 256, 128, 1024), smem_desc_kmajor(b + ks * 256, 128, 1024),
+                        kIdesc, (!first || ks) ? 1u : 0u);
+        tc_commit(&s_empty[c & 1]);
+    };
+    // every thread waits for the MMAs committed to s_mma (phase `ph`); the barrier
+    // after it makes s_fail the same for every thread
+    int mma_commits = 0;  // thread 0
+    auto wait_mma = [&](int ph) {
+        if (!mbar_wait_bounded(&s_mma, ph, kDefaultWaitLimit)) {
+            s_fail = 1;
+            atomicOr(g.status, kStatusTimeout);
+        }
+        tc_fence_after_sync();
+        __syncthreads();
     };
 
-    const int nk = g.kc;
-    bool ok = true;
-    load(0, kbase);
-    for (int kc = 0; kc < nk; ++kc) {
-        if (kc + 1 < nk) {
-            // buffer (kc + 1) & 1 was last read by the MMAs of chunk kc - 1
-            if (kc >= 1 && !mbar_wait_bounded(&s_bar[(kc - 1) & 1], ((kc - 1) >> 1) & 1, kDefaultWaitLimit)) ok = false;
-            load((kc + 1) & 1, kbase + static_cast<int64_t>(kc + 1) * BK);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        fence_async_shared();
-        __syncthreads();
-        if (t == 0) {
-            tc_fence_after_sync();
-            const uint8_t *a = sA + (kc & 1) * kStageA;
-            const uint8_t *b = sB + (kc & 1) * kStageB;
+    // ---- X rows: FP32 -> BF16 into the layer-1 operand (and its batch-major image)
+    {
+        float xv[64];
+        const int64_t src = valid ? batch_row(g.idx, g.cursor, g.B, row) : 0;
 #pragma unroll
-            for (int ks = 0; ks < BK / 16; ++ks)
-                tc_mma_bf16(tmem, smem_desc_kmajor(a + ks * 256, 128, 1024), smem_desc_kmajor(b + ks * 256, 128, 1024),
-                            kIdesc, (kc | ks) != 0);
-            tc_commit(&s_bar[kc & 1]);
+        for (int c = 0; c < 64; ++c) xv[c] = (valid && c < g.in_dim) ? g.X[src * g.in_dim + c] : 0.0f;
+        put_row32(sX, t, 0, *reinterpret_cast<float(*)[32]>(&xv[0]));
+        put_row32(sX, t, 32, *reinterpret_cast<float(*)[32]>(&xv[32]));
+        if constexpr (kTrain) {
+            uint8_t *chunk = g.xt_img + (static_cast<size_t>(tile) * 2 + (t >> 6)) * (64 * 64 * 2);
+            put_cols32(chunk, 0, (t & 63) & ~31, *reinterpret_cast<float(*)[32]>(&xv[0]), stage, lane);
+            put_cols32(chunk, 32, (t & 63) & ~31, *reinterpret_cast<float(*)[32]>(&xv[32]), stage, lane);
         }
     }
-    // the last chunk's commit covers every MMA of the tile
-    if (!mbar_wait_bounded(&s_bar[(nk - 1) & 1], ((nk - 1) >> 1) & 1, kDefaultWaitLimit)) ok = false;
-    if (!ok) {
-        s_fail = 1;
+    fence_async_shared();
+    __syncthreads();
+
+    // ---- layer 1: C1 = X W1 (tensor memory columns 0 .. 255)
+    if (t == 0) {
+        mma(0, sX, tmem, true);
+        if (ok) {
+            tc_commit(&s_mma);
+            ++mma_commits;
+        }
+        refill(0);
+    }
+    wait_mma(0);
+    // epilogue 1: H1 = relu(C1 + b1), BF16 into the layer-2 operand (+ its batch-major image)
+    const uint32_t lane_base = static_cast<uint32_t>(32 * warp) << 16;
+    if (!s_fail) {
+#pragma unroll 1
+        for (int c0 = 0; c0 < kH; c0 += 32) {
+            uint32_t raw[32];
+            tmem_ld32(tmem + lane_base + c0, raw);
+            tmem_ld_wait();
+            float v[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = fmaxf(__uint_as_float(raw[j]) + __ldg(g.params + g.off_b1 + c0 + j), 0.0f);
+            put_row32(sH1, t, c0, v);
+            if constexpr (kTrain) {
+                uint8_t *chunk = g.h1t_img + (static_cast<size_t>(tile) * 2 + (t >> 6)) * (kH * 64 * 2);
+                put_cols32(chunk, c0, (t & 63) & ~31, v, stage, lane);
+            }
+        }
+    }
+    fence_async_shared();
+    tc_fence_before_sync();
+    __syncthreads();
+
+    // ---- layer 2: C2 = H1 W2 (columns 256 .. 511), W2t in four K-chunks
+    if (t == 0 && !s_fail) {
+        tc_fence_after_sync();
+        mma(1, sH1, tmem + 256, true);
+        mma(2, sH1 + 16384, tmem + 256, false);
+        refill(1);
+        mma(3, sH1 + 2 * 16384, tmem + 256, false);
+        refill(2);
+        mma(4, sH1 + 3 * 16384, tmem + 256, false);
+        if (ok) {
+            tc_commit(&s_mma);
+            ++mma_commits;
+        }
+        refill(3);
+    }
+    wait_mma(1);
+
+    // ---- output layer: z = relu(C2 + b2) . w3 + b3, p = sigmoid(z)
+    float z = 0.0f;
+    if (!s_fail) {
+#pragma unroll 1
+        for (int c0 = 0; c0 < kH; c0 += 32) {
+            uint32_t raw[32];
+            tmem_ld32(tmem + lane_base + 256 + c0, raw);
+            tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const float h = fmaxf(__uint_as_float(raw[j]) + __ldg(g.params + g.off_b2 + c0 + j), 0.0f);
+                z = fmaf(h, __ldg(g.params + g.off_w3 + c0 + j), z);
+            }
+        }
+    }
+    z += __ldg(g.params + g.off_b3);
+    const float p = 1.0f / (1.0f + expf(-z));
+    if (valid) g.p_out[row] = p;
+
+    if constexpr (kTrain) {
+        // ---- first backward step: dz = (p - y) / B; dH2 = dz w3 [h2 > 0] (BF16); column
+        // sums of dz h2 (dw3) and of dH2 (db2) over the tile's rows; loss and db3
+        const float yy = valid ? g.y[batch_row(g.idx, g.cursor, g.B, row)] : 0.0f;
+        const float dz = valid ? (p - yy) * (1.0f / static_cast<float>(g.B)) : 0.0f;
+        float loss = 0.0f;
+        if (valid) {
+            const float eps = 1e-12f;
+            loss = -(yy * logf(p + eps) + (1.0f - yy) * logf(1.0f - p + eps));
+        }
+        if (!s_fail) {
+#pragma unroll 1
+            for (int c0 = 0; c0 < kH; c0 += 32) {
+                uint32_t raw[32];
+                tmem_ld32(tmem + lane_base + 256 + c0, raw);
+                tmem_ld_wait();
+                float d[32], hw[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float h = fmaxf(__uint_as_float(raw[j]) + __ldg(g.params + g.off_b2 + c0 + j), 0.0f);
+                    d[j] = h > 0.0f ? dz * __ldg(g.params + g.off_w3 + c0 + j) : 0.0f;
+                    hw[j] = dz * h;
+                }
+                put_row32(sD2, t, c0, d);
+                uint8_t *chunk = g.dh2t_img + (static_cast<size_t>(tile) * 2 + (t >> 6)) * (kH * 64 * 2);
+                put_cols32(chunk, c0, (t & 63) & ~31, d, stage, lane);
+                cols[(0 * 4 + warp) * kH + c0 + lane] = col_sum32(hw, lane);  // dw3
+                cols[(1 * 4 + warp) * kH + c0 + lane] = col_sum32(d, lane);   // db2
+            }
+        }
+        float rs[2] = {dz, loss};
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) rs[k] += __shfl_xor_sync(0xffffffffu, rs[k], o);
+        if (lane == 0) {
+            s_red[warp][0] = rs[0];
+            s_red[warp][1] = rs[1];
+        }
+        fence_async_shared();
+        tc_fence_before_sync();
+        __syncthreads();
+        // per-tile partials of dw3, db2 (warps in order), db3 and the loss
+        float *ph = g.part_head + static_cast<int64_t>(tile) * (2 * kH + 2);
+        for (int i = t; i < 2 * kH; i += 128) {
+            const int which = i / kH, c = i % kH;
+            const float *q = cols + which * 4 * kH + c;
+            ph[i] = ((q[0] + q[kH]) + q[2 * kH]) + q[3 * kH];
+        }
+        if (t == 0) {
+            ph[2 * kH] = ((s_red[0][0] + s_red[1][0]) + s_red[2][0]) + s_red[3][0];
+            ph[2 * kH + 1] = ((s_red[0][1] + s_red[1][1]) + s_red[2][1]) + s_red[3][1];
+        }
+        __syncthreads();  // the column sums are read before epilogue 3 rewrites them
+
+        // ---- dH1 = dH2 W2^T (columns 0 .. 255 again), W2b in four K-chunks
+        if (t == 0 && !s_fail) {
+            tc_fence_after_sync();
+            refill(4);
+            mma(5, sD2, tmem, true);
+            mma(6, sD2 + 16384, tmem, false);
+            refill(5);
+            mma(7, sD2 + 2 * 16384, tmem, false);
+            refill(6);
+            mma(8, sD2 + 3 * 16384, tmem, false);
+            if (ok) {
+                tc_commit(&s_mma);
+                ++mma_commits;
+            }
+        }
+        wait_mma(0);
+        // epilogue 3: dH1 = C3 [h1 > 0] (BF16 batch-major image) and its column sums (db1)
+        if (!s_fail) {
+#pragma unroll 1
+            for (int c0 = 0; c0 < kH; c0 += 32) {
+                uint32_t raw[32];
+                tmem_ld32(tmem + lane_base + c0, raw);
+                tmem_ld_wait();
+                // this row's 32 stored H1 values (the mask), 16 bytes at a time
+                const uint8_t *hb = sH1 + (c0 >> 6) * 16384 + (t >> 3) * 1024 + (t & 7) * 16 + ((c0 & 63) >> 3) * 128;
+                float d[32];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint4 u = *reinterpret_cast<const uint4 *>(hb + q * 128);
+                    const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                    for (int h = 0; h < 8; ++h) {
+                        const uint16_t bits = static_cast<uint16_t>((h & 1) ? (w4[h >> 1] >> 16) : (w4[h >> 1] & 0xFFFFu));
+                        const float hv = __bfloat162float(__ushort_as_bfloat16(bits));
+                        d[8 * q + h] = hv > 0.0f ? __uint_as_float(raw[8 * q + h]) : 0.0f;
+                    }
+                }
+                uint8_t *chunk = g.dh1t_img + (static_cast<size_t>(tile) * 2 + (t >> 6)) * (kH * 64 * 2);
+                put_cols32(chunk, c0, (t & 63) & ~31, d, stage, lane);
+                cols[warp * kH + c0 + lane] = col_sum32(d, lane);  // db1
+            }
+        }
+        __syncthreads();
+        float *pb = g.part_b1 + static_cast<int64_t>(tile) * kH;
+        for (int c = t; c < kH; c += 128) {
+            const float *q = cols + c;
+            pb[c] = ((q[0] + q[kH]) + q[2 * kH]) + q[3 * kH];
+        }
+    }
+
+    // leave: on a time-out wait (bounded) for the copies and MMAs in flight first
+    if (t == 0 && !ok) {
         atomicOr(g.status, kStatusTimeout);
-        mbar_wait_bounded(&s_bar[(nk - 1) & 1], ((nk - 1) >> 1) & 1, kDefaultWaitLimit);
+        s_fail = 1;
+        for (int c = 0; c < loaded; ++c) mbar_wait_bounded(&s_full[c & 1], (c >> 1) & 1, kDefaultWaitLimit);
+        tc_commit(&s_mma);  // completes once every MMA this thread issued is done
+        mbar_wait_bounded(&s_mma, mma_commits & 1, kDefaultWaitLimit);
+    }
+    tc_fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after_sync();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradients over the batch, split into `splits` ranges of 64-row chunks:
+//   problem 0 (CTA x = 0, 1):  dW2[k][n]  = sum_m H1T[k][m] dH2T[n][m], k-tile x
+//   problem 1 (CTA x = 2, 3):  dW1T[n][k] = sum_m dH1T[n][m] XT[k][m], n-tile x - 2
+// Each CTA copies its A (128 rows x 64, 16 KB) and B (256 or 64 rows x 64) chunk images
+// with bulk copies through a 3-stage ring, one thread issues the MMAs, and the FP32
+// tile of its split goes to part_w2[split] ([256][256]) or part_w1[split] ([256][64]).
+struct WgradArgs {
+    const uint8_t *h1t_img, *dh2t_img, *dh1t_img, *xt_img;
+    int n_mchunks, chunks_per_split;
+    float *part_w2, *part_w1;
+    unsigned int *status;
+};
+
+constexpr int kWgStages = 3;
+constexpr uint32_t kWgA = 16384, kWgB = 32768;
+constexpr int kWgradSmem = kWgStages * static_cast<int>(kWgA + kWgB);
+
+__global__ void __launch_bounds__(128, 1) k_wgrad(const WgradArgs g)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ __align__(8) uint64_t s_full[kWgStages], s_empty[kWgStages];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_fail;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int prob = blockIdx.x >> 1, mt = blockIdx.x & 1;
+    const int split = blockIdx.y;
+    const int N = prob == 0 ? 256 : 64;
+    const uint32_t bbytes = prob == 0 ? kWgB : 8192u;
+    const int c_begin = split * g.chunks_per_split;
+    const int c_end = min(g.n_mchunks, c_begin + g.chunks_per_split);
+    const int nk = max(0, c_end - c_begin);
+    const uint8_t *A = prob == 0 ? g.h1t_img : g.dh1t_img;
+    const uint8_t *Bm = prob == 0 ? g.dh2t_img : g.xt_img;
+    const size_t a_stride = kH * 64 * 2;                      // one chunk of a 256-feature image
+    const size_t b_stride = prob == 0 ? kH * 64 * 2 : 64 * 64 * 2;
+
+    if (warp == 0) {
+        tmem_alloc(&s_tmem, 256);
+        tmem_relinquish();
+    }
+    if (t == 0) {
+        for (int i = 0; i < kWgStages; ++i) {
+            mbar_init(&s_full[i], 1);
+            mbar_init(&s_empty[i], 1);
+        }
+        fence_barrier_init();
+        s_fail = 0;
+    }
+    tc_fence_before_sync();
+    __syncthreads();
+    tc_fence_after_sync();
+    const uint32_t tmem = s_tmem;
+    const uint32_t idesc = prob == 0 ? idesc_bf16_f32(128, 256) : idesc_bf16_f32(128, 64);
+
+    if (t == 0) {
+        bool ok = true;
+        auto load = [&](int i) {
+            const int s = i % kWgStages;
+            uint8_t *sa = smem + s * (kWgA + kWgB);
+            mbar_arrive_expect_tx(&s_full[s], kWgA + bbytes);
+            const size_t mc = static_cast<size_t>(c_begin + i);
+            bulk_g2s(sa, A + mc * a_stride + mt * kWgA, kWgA, &s_full[s]);
+            bulk_g2s(sa + kWgA, Bm + mc * b_stride, bbytes, &s_full[s]);
+        };
+        int issued = 0;
+        for (; issued < min(nk, kWgStages); ++issued) load(issued);
+        for (int i = 0; i < nk && ok; ++i) {
+            const int s = i % kWgStages;
+            if (!mbar_wait_bounded(&s_full[s], (i / kWgStages) & 1, kDefaultWaitLimit)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after_sync();
+            const uint8_t *sa = smem + s * (kWgA + kWgB);
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+                tc_mma_bf16(tmem, smem_desc_kmajor(sa + ks * 256, 128, 1024),
+                            smem_desc_kmajor(sa + kWgA + ks * 256, 128, 1024), idesc, (i | ks) ? 1u : 0u);
+            tc_commit(&s_empty[s]);
+            if (issued < nk) {
+                // the stage of chunk i is refilled once its MMAs are done
+                if (!mbar_wait_bounded(&s_empty[s], (i / kWgStages) & 1, kDefaultWaitLimit)) {
+                    ok = false;
+                    break;
+                }
+                load(issued++);
+            }
+        }
+        if (ok && nk > 0) {
+            // the last chunk's commit covers every MMA before it
+            const int last = nk - 1;
+            if (!mbar_wait_bounded(&s_empty[last % kWgStages], (last / kWgStages) & 1, kDefaultWaitLimit)) ok = false;
+        }
+        if (!ok) {
+            s_fail = 1;
+            atomicOr(g.status, kStatusTimeout);
+            for (int i = 0; i < issued; ++i) mbar_wait_bounded(&s_full[i % kWgStages], (i / kWgStages) & 1, kDefaultWaitLimit);
+        }
     }
     tc_fence_before_sync();
     __syncthreads();
     tc_fence_after_sync();
 
     if (!s_fail) {
-        const int64_t row = m0 + 32 * warp + lane;
+        const int r = mt * 128 + 32 * warp + lane;  // output row (k of dW2, n of dW1T)
+        float *out = prob == 0 ? g.part_w2 + static_cast<size_t>(split) * kH * kH + static_cast<size_t>(r) * kH
+                               : g.part_w1 + static_cast<size_t>(split) * kH * kKP + static_cast<size_t>(r) * kKP;
 #pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 32) {
+        for (int c0 = 0; c0 < N; c0 += 32) {
             uint32_t raw[32];
-            tmem_ld32(tmem + (static_cast<uint32_t>(32 * warp) << 16) + c0, raw);
-            tmem_ld_wait();
-            float v[32];
-            const int col0 = n0 + c0;
-            uint4 mk[4];  // the row's 32 mask values, 16 bytes at a time
-            if constexpr (EPI == kMaskBf16) {
-                const uint4 *mp = reinterpret_cast<const uint4 *>(g.mask + row * kH + col0);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) mk[q] = mp[q];
-            }
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const float acc = __uint_as_float(raw[j]);
-                if constexpr (EPI == kMaskBf16) {
-                    const uint32_t w = (&mk[j >> 3].x)[(j & 7) >> 1];
-                    const uint16_t h = static_cast<uint16_t>((j & 1) ? (w >> 16) : (w & 0xFFFFu));
-                    v[j] = __bfloat162float(__ushort_as_bfloat16(h)) > 0.0f ? acc : 0.0f;
-                } else if constexpr (EPI == kReluBf16 || EPI == kReluF32)
-                    v[j] = fmaxf(acc + g.bias[col0 + j], 0.0f);
-                else
-                    v[j] = acc;
-            }
-            if constexpr (EPI == kReluF32 || EPI == kPartF32) {
-                float *base = EPI == kReluF32 ? static_cast<float *>(g.out) + row * kH + col0
-                                              : g.partial + blockIdx.z * g.partial_stride + row * kH + col0;
-                float4 *o = reinterpret_cast<float4 *>(base);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-            } else if constexpr (EPI == kPartF32T) {
-                // [col][row]: the warp's lanes write 32 consecutive rows of each column
-                float *base = g.partial + blockIdx.z * g.partial_stride;
-#pragma unroll
-                for (int j = 0; j < 32; ++j) base[static_cast<int64_t>(col0 + j) * kH + row] = v[j];
+            if (nk > 0) {
+                tmem_ld32(tmem + (static_cast<uint32_t>(32 * warp) << 16) + c0, raw);
+                tmem_ld_wait();
             } else {
-                uint4 *o = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(g.out) + row * kH + col0);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    uint32_t w[4];
-#pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        const __nv_bfloat162 pr = __floats2bfloat162_rn(v[8 * q + 2 * h], v[8 * q + 2 * h + 1]);
-                        w[h] = *reinterpret_cast<const uint32_t *>(&pr);
-                    }
-                    o[q] = make_uint4(w[0], w[1], w[2], w[3]);
-                }
-                if (g.out_t) {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        g.out_t[static_cast<int64_t>(col0 + j) * g.ldt + row] = __float2bfloat16_rn(v[j]);
-                }
+                for (int j = 0; j < 32; ++j) raw[j] = 0u;
             }
-            if constexpr (EPI == kMaskBf16) {
-                // reduce-scatter over the warp's rows: lane l ends with column c0 + l
+            float4 *o = reinterpret_cast<float4 *>(out + c0);
 #pragma unroll
-                for (int o = 16; o >= 1; o >>= 1) {
-                    const bool upper = (lane & o) != 0;
-#pragma unroll
-                    for (int i = 0; i < o; ++i) {
-                        const float send = upper ? v[i] : v[i + o];
-                        const float keep = upper ? v[i + o] : v[i];
-                        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-                    }
-                }
-                s_cs[warp][c0 + lane] = v[0];
-            }
-        }
-        if constexpr (EPI == kMaskBf16) {
-            __syncthreads();
-            // t = column: rows 0..63 are warps 0, 1; rows 64..127 warps 2, 3
-            const int64_t grp = static_cast<int64_t>(blockIdx.x) * 2;
-            if (t < BN) {
-                g.col_partial[grp * kH + n0 + t] = s_cs[0][t] + s_cs[1][t];
-                g.col_partial[(grp + 1) * kH + n0 + t] = s_cs[2][t] + s_cs[3][t];
-            }
+            for (int q = 0; q < 8; ++q)
+                o[q] = make_float4(__uint_as_float(raw[4 * q]), __uint_as_float(raw[4 * q + 1]),
+                                   __uint_as_float(raw[4 * q + 2]), __uint_as_float(raw[4 * q + 3]));
         }
     }
     tc_fence_before_sync();
     __syncthreads();
     if (warp == 0) {
         tc_fence_after_sync();
-        tmem_dealloc(tmem, BN);
+        tmem_dealloc(tmem, 256);
     }
-}
-
-// BF16 transpose in[R][C] -> out[C][R] through 32 x 32 shared-memory tiles.
-__global__ void k_transpose_bf16(const __nv_bfloat16 *__restrict__ in, int R, int C, __nv_bfloat16 *__restrict__ out)
-{
-    __shared__ __nv_bfloat16 tile[32][34];
-    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
-    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-    for (int i = ty; i < 32; i += 8)
-        if (r0 + i < R && c0 + tx < C) tile[i][tx] = in[static_cast<int64_t>(r0 + i) * C + c0 + tx];
-    __syncthreads();
-    for (int i = ty; i < 32; i += 8)
-        if (c0 + i < C && r0 + tx < R) out[static_cast<int64_t>(c0 + i) * R + r0 + tx] = tile[tx][i];
 }
 
 // ---------------------------------------------------------------------------
-// Output layer and loss: z = h2 . w3 + b3, p = sigmoid(z).  With labels, also the
-// first backward step: dz = (p - y) / B, dh2 = dz w3 [h2 > 0] (BF16 for the
-// GEMMs), and per-CTA partial sums (fixed order) of dw3 = sum dz h2,
-// db2 = sum dh2, db3 = sum dz and the BCE loss.  One warp per row, 8 warps per CTA,
-// `rows_per_cta` rows per CTA.
-__global__ void __launch_bounds__(256) k_head(const float *__restrict__ H2, const float *__restrict__ w3,
-                                              const float *__restrict__ b3p, const float *__restrict__ y,
-                                              const int64_t *__restrict__ idx, const int64_t *__restrict__ cursor,
-                                              int B, int rows_per_cta,
-                                              float *__restrict__ p_out, __nv_bfloat16 *__restrict__ dH2,
-                                              float *__restrict__ partial)
+// Gradients from the partials (each summed in split / tile order), then optionally
+// AdamW on the FP32 masters and the BF16 weight images.  One thread per parameter of
+// the packed layout [W1 (in x 256) | b1 | W2 (256 x 256) | b2 | w3 | b3]; thread
+// n_params writes the loss sum.
+struct UpdateArgs {
+    const float *part_w2, *part_w1, *part_head, *part_b1;
+    int n_splits, n_tiles, in_dim;
+    int64_t n_params, off_b1, off_W2, off_b2, off_w3, off_b3;
+    float *grads, *loss_sum;
+    // AdamW (null w: gradients only)
+    float *w, *m, *v;
+    float lr, beta1, beta2, eps, wd, bc1, bc2;
+    const float *bc_table;   // replayed epochs: bias corrections [2 cursor + {0, 1}]
+    const int64_t *cursor;
+    uint8_t *wimg;           // the BF16 images of W1t, W2t, W2b
+};
+
+__device__ __forceinline__ void put_img(uint8_t *wimg, int chunk, int r, int c, float x)
 {
-    __shared__ float s_w3[kH];
-    __shared__ float s_acc[8][2 * kH + 2];
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    s_w3[t] = w3[t];
-    for (int i = t; i < 8 * (2 * kH + 2); i += 256) (&s_acc[0][0])[i] = 0.0f;
-    __syncthreads();
-    const int64_t r0 = static_cast<int64_t>(blockIdx.x) * rows_per_cta;
-    const float b3 = *b3p;
-    const bool train = y != nullptr;
-    const float inv_b = 1.0f / static_cast<float>(B);
-    for (int rr = warp; rr < rows_per_cta; rr += 8) {
-        const int64_t r = r0 + rr;
-        float h[8];
-        float z = 0.0f;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            h[q] = H2[r * kH + q * 32 + lane];
-            z = fmaf(h[q], s_w3[q * 32 + lane], z);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
-        z += b3;
-        const float p = 1.0f / (1.0f + expf(-z));
-        if (lane == 0 && r < B) p_out[r] = p;
-        if (!train) continue;
-        const bool valid = r < B;
-        const float yy = valid ? y[batch_row(idx, cursor, B, r)] : 0.0f;
-        const float dz = valid ? (p - yy) * inv_b : 0.0f;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int k = q * 32 + lane;
-            const float d = h[q] > 0.0f ? dz * s_w3[k] : 0.0f;
-            dH2[r * kH + k] = __float2bfloat16_rn(d);
-            s_acc[warp][k] += dz * h[q];      // dw3
-            s_acc[warp][kH + k] += d;         // db2
-        }
-        if (lane == 0 && valid) {
-            s_acc[warp][2 * kH] += dz;
-            const float eps = 1e-12f;
-            s_acc[warp][2 * kH + 1] += -(yy * logf(p + eps) + (1.0f - yy) * logf(1.0f - p + eps));
-        }
-    }
-    if (!train) return;
-    __syncthreads();
-    for (int i = t; i < 2 * kH + 2; i += 256) {
-        float s = 0.0f;
-        for (int w = 0; w < 8; ++w) s += s_acc[w][i];
-        partial[static_cast<int64_t>(blockIdx.x) * (2 * kH + 2) + i] = s;
+    *reinterpret_cast<__nv_bfloat16 *>(wimg + static_cast<size_t>(chunk) * kWChunk + img_off(r, c)) =
+        __float2bfloat16_rn(x);
+}
+
+// BF16 copies of one weight into the images: W1[k][n] -> W1t (row n, col k); W2[k][n] ->
+// W2t chunk k / 64 (row n, col k % 64) and W2b chunk n / 64 (row k, col n % 64).
+__device__ __forceinline__ void put_weight(uint8_t *wimg, bool is_w2, int k, int n, float x)
+{
+    if (!is_w2) {
+        put_img(wimg, 0, n, k, x);
+    } else {
+        put_img(wimg, 1 + (k >> 6), n, k & 63, x);
+        put_img(wimg, 5 + (n >> 6), k, n & 63, x);
     }
 }
 
-// Sum n partial vectors of length len in order: out[i] = sum_j part[j][i].
-__global__ void k_sum_partials(const float *__restrict__ part, int n, int64_t len, float *__restrict__ out)
+__global__ void k_update(const UpdateArgs g)
 {
     const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-    if (i >= len) return;
-    float s = 0.0f;
-    for (int j = 0; j < n; ++j) s += part[static_cast<int64_t>(j) * len + i];
-    out[i] = s;
+    if (i > g.n_params) return;
+    if (i == g.n_params) {
+        float s = 0.0f;
+        for (int tl = 0; tl < g.n_tiles; ++tl) s += g.part_head[static_cast<int64_t>(tl) * (2 * kH + 2) + 2 * kH + 1];
+        *g.loss_sum = s;
+        return;
+    }
+    float gr = 0.0f;
+    bool is_w = false, is_w2 = false;
+    int wk = 0, wn = 0;
+    if (i < g.off_b1) {  // W1[k][n]: partials hold dW1^T [n][k]
+        wk = static_cast<int>(i / kH);
+        wn = static_cast<int>(i % kH);
+        for (int z = 0; z < g.n_splits; ++z) gr += g.part_w1[static_cast<int64_t>(z) * kH * kKP + wn * kKP + wk];
+        is_w = true;
+    } else if (i < g.off_W2) {  // b1
+        const int c = static_cast<int>(i - g.off_b1);
+        for (int tl = 0; tl < g.n_tiles; ++tl) gr += g.part_b1[static_cast<int64_t>(tl) * kH + c];
+    } else if (i < g.off_b2) {  // W2[k][n]
+        const int64_t j = i - g.off_W2;
+        wk = static_cast<int>(j / kH);
+        wn = static_cast<int>(j % kH);
+        for (int z = 0; z < g.n_splits; ++z) gr += g.part_w2[static_cast<int64_t>(z) * kH * kH + j];
+        is_w = is_w2 = true;
+    } else {  // b2, w3, b3 from the tile partials [dw3 | db2 | db3 | loss]
+        int col;
+        if (i < g.off_w3) col = kH + static_cast<int>(i - g.off_b2);
+        else if (i < g.off_b3) col = static_cast<int>(i - g.off_w3);
+        else col = 2 * kH;
+        for (int tl = 0; tl < g.n_tiles; ++tl) gr += g.part_head[static_cast<int64_t>(tl) * (2 * kH + 2) + col];
+    }
+    g.grads[i] = gr;
+    if (!g.w) return;
+    float bc1 = g.bc1, bc2 = g.bc2;
+    if (g.bc_table) {
+        bc1 = g.bc_table[2 * *g.cursor];
+        bc2 = g.bc_table[2 * *g.cursor + 1];
+    }
+    const float mi = g.beta1 * g.m[i] + (1.0f - g.beta1) * gr;
+    const float vi = g.beta2 * g.v[i] + (1.0f - g.beta2) * gr * gr;
+    g.m[i] = mi;
+    g.v[i] = vi;
+    const float mhat = mi / bc1, vhat = vi / bc2;
+    const float wv = g.w[i] * (1.0f - g.lr * g.wd) - g.lr * mhat / (sqrtf(vhat) + g.eps);
+    g.w[i] = wv;
+    if (is_w) put_weight(g.wimg, is_w2, wk, wn, wv);
 }
 
-// The same for short vectors with many partials: a warp per element, lane l adds
-// partials l, l + 32, ... in order, then the warp's butterfly (a fixed order too).
-__global__ void k_sum_partials_warp(const float *__restrict__ part, int n, int64_t len, float *__restrict__ out)
+// All BF16 weight images from the FP32 masters, padding (W1 columns k >= in_dim) zero.
+__global__ void k_refresh(const float *__restrict__ W1, int in_dim, const float *__restrict__ W2, uint8_t *wimg)
 {
-    const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x / 32) + threadIdx.x / 32;
-    const int lane = threadIdx.x & 31;
-    if (i >= len) return;
-    float s = 0.0f;
-    for (int j = lane; j < n; j += 32) s += part[static_cast<int64_t>(j) * len + i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) out[i] = s;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kH * kKP) {
+        const int k = i / kH, n = i % kH;
+        put_weight(wimg, false, k, n, k < in_dim ? W1[k * kH + n] : 0.0f);
+    }
+    if (i < kH * kH) put_weight(wimg, true, i / kH, i % kH, W2[i]);
 }
 
 // End of a replayed training step: its mean loss to losses[cursor], then the
@@ -374,172 +662,127 @@ __global__ void k_epoch_tail(const float *__restrict__ loss_sum, int B, int64_t 
     *cursor += 1;
 }
 
-// AdamW on FP32 masters (decoupled weight decay), then the BF16 copies:
-// W1t[n][k] (k < 64), W2t[n][k] and W2b[k][n] = W2[k][n].
-// With a batch cursor the bias corrections come from bc_table[2 cursor + {0, 1}]
-// (filled by the host with the same arithmetic as the scalar path).
-__global__ void k_adamw(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m, float *__restrict__ v,
-                        int64_t n, float lr, float beta1, float beta2, float eps, float wd, float bc1, float bc2,
-                        const float *__restrict__ bc_table, const int64_t *__restrict__ cursor)
-{
-    const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-    if (i >= n) return;
-    if (bc_table) {
-        bc1 = bc_table[2 * *cursor];
-        bc2 = bc_table[2 * *cursor + 1];
-    }
-    const float gi = g[i];
-    const float mi = beta1 * m[i] + (1.0f - beta1) * gi;
-    const float vi = beta2 * v[i] + (1.0f - beta2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    const float mhat = mi / bc1, vhat = vi / bc2;
-    w[i] = w[i] * (1.0f - lr * wd) - lr * mhat / (sqrtf(vhat) + eps);
-}
-
-__global__ void k_refresh_bf16(const float *__restrict__ W1, int in_dim, const float *__restrict__ W2,
-                               __nv_bfloat16 *__restrict__ W1t, __nv_bfloat16 *__restrict__ W2t,
-                               __nv_bfloat16 *__restrict__ W2b)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < kH * kKP) {
-        const int n = i / kKP, k = i % kKP;
-        W1t[i] = __float2bfloat16_rn(k < in_dim ? W1[k * kH + n] : 0.0f);
-    }
-    if (i < kH * kH) {
-        const int n = i / kH, k = i % kH;
-        W2t[i] = __float2bfloat16_rn(W2[k * kH + n]);
-        W2b[i] = __float2bfloat16_rn(W2[i]);
-    }
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------------------
-cudaError_t mlp_launch_cast(const float *X, const int64_t *idx, const int64_t *cursor, int B, int in_dim, int Bp,
-                            void *Xb, cudaStream_t s)
+size_t mlp_wimg_bytes() { return 9 * static_cast<size_t>(kWChunk); }
+size_t mlp_xt_bytes(int Bp) { return static_cast<size_t>(Bp / 64) * 64 * 64 * 2; }
+size_t mlp_ht_bytes(int Bp) { return static_cast<size_t>(Bp / 64) * kH * 64 * 2; }
+int mlp_wgrad_splits(int Bp, int *chunks_per_split)
 {
-    const int64_t n = static_cast<int64_t>(Bp) * kKP;
-    k_cast_x<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(X, idx, cursor, B, in_dim, Bp,
-                                                                   static_cast<__nv_bfloat16 *>(Xb));
-    return cudaGetLastError();
-}
-
-template <int BN>
-constexpr int gemm_smem() { return 2 * 128 * 64 * 2 + 2 * BN * 64 * 2; }  // two buffers each of A and B chunks
-
-template <int EPI, int BN>
-cudaError_t gemm_attr()
-{
-    return cudaFuncSetAttribute(k_gemm_tc<EPI, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_smem<BN>());
+    const int n = Bp / 64;
+    const int cps = (n + 31) / 32;
+    *chunks_per_split = cps;
+    return (n + cps - 1) / cps;
 }
 
 cudaError_t mlp_prepare()
 {
-    cudaError_t e = gemm_attr<kReluBf16, 128>();
-    if (e == cudaSuccess) e = gemm_attr<kReluF32, 128>();
-    if (e == cudaSuccess) e = gemm_attr<kMaskBf16, 128>();
-    if (e == cudaSuccess) e = gemm_attr<kPartF32, 128>();
-    if (e == cudaSuccess) e = gemm_attr<kPartF32T, 64>();
+    cudaError_t e = cudaFuncSetAttribute(k_tile<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tile<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgradSmem);
     return e;
 }
 
-cudaError_t mlp_launch_layer(int epi, const void *A, int Bp, int K, const void *Bt, const float *bias, const void *mask,
-                             void *out, void *out_t, float *col_partial, unsigned int *status, cudaStream_t s)
+cudaError_t mlp_launch_tile(const MlpBuffers &b, const float *X, const int64_t *idx, const int64_t *cursor,
+                            const float *y, int B, int Bp, float *p_out, cudaStream_t s)
 {
-    if (Bp % 128 != 0 || K % 64 != 0) return cudaErrorInvalidValue;
-    GemmArgs g{};
-    g.A = static_cast<const __nv_bfloat16 *>(A);
-    g.lda = K;
-    g.B = static_cast<const __nv_bfloat16 *>(Bt);
-    g.ldb = K;
-    g.kc = K / 64;
-    g.bias = bias;
-    g.mask = static_cast<const __nv_bfloat16 *>(mask);
-    g.out = out;
-    g.out_t = static_cast<__nv_bfloat16 *>(out_t);
-    g.ldt = Bp;
-    g.col_partial = col_partial;
-    g.status = status;
-    const dim3 grid(Bp / 128, kH / 128);
-    switch (epi) {
-        case kReluBf16: k_gemm_tc<kReluBf16, 128><<<grid, 128, gemm_smem<128>(), s>>>(g); break;
-        case kReluF32: k_gemm_tc<kReluF32, 128><<<grid, 128, gemm_smem<128>(), s>>>(g); break;
-        case kMaskBf16: k_gemm_tc<kMaskBf16, 128><<<grid, 128, gemm_smem<128>(), s>>>(g); break;
-        default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-}
-
-cudaError_t mlp_launch_wgrad(const void *AT, int M, const void *BT, int N, int Bp, int chunk, bool transposed,
-                             float *partial, unsigned int *status, cudaStream_t s)
-{
-    if (M % 128 != 0 || Bp % chunk != 0 || chunk % 64 != 0 || (N != 256 && N != 64) || (N == 64) != transposed)
-        return cudaErrorInvalidValue;
-    GemmArgs g{};
-    g.A = static_cast<const __nv_bfloat16 *>(AT);
-    g.lda = Bp;
-    g.B = static_cast<const __nv_bfloat16 *>(BT);
-    g.ldb = Bp;
-    g.kc = chunk / 64;
-    g.partial = partial;
-    g.partial_stride = static_cast<int64_t>(M) * N;
-    g.status = status;
-    if (transposed) {
-        k_gemm_tc<kPartF32T, 64><<<dim3(M / 128, 1, Bp / chunk), 128, gemm_smem<64>(), s>>>(g);
-    } else {
-        k_gemm_tc<kPartF32, 128><<<dim3(M / 128, N / 128, Bp / chunk), 128, gemm_smem<128>(), s>>>(g);
-    }
-    return cudaGetLastError();
-}
-
-cudaError_t mlp_launch_transpose(const void *in, int R, int C, void *out, cudaStream_t s)
-{
-    const dim3 grid((C + 31) / 32, (R + 31) / 32);
-    k_transpose_bf16<<<grid, dim3(32, 8), 0, s>>>(static_cast<const __nv_bfloat16 *>(in), R, C,
-                                                  static_cast<__nv_bfloat16 *>(out));
-    return cudaGetLastError();
-}
-
-cudaError_t mlp_launch_head(const float *H2, const float *w3, const float *b3, const float *y, const int64_t *idx,
-                            const int64_t *cursor, int B, int Bp, int rows_per_cta, float *p, void *dH2, float *partial,
-                            cudaStream_t s)
-{
-    k_head<<<Bp / rows_per_cta, 256, 0, s>>>(H2, w3, b3, y, idx, cursor, B, rows_per_cta, p,
-                                              static_cast<__nv_bfloat16 *>(dH2), partial);
-    return cudaGetLastError();
-}
-
-cudaError_t mlp_launch_sum(const float *part, int n, int64_t len, float *out, cudaStream_t s)
-{
-    if (len <= 4096 && n > 32)
-        k_sum_partials_warp<<<static_cast<unsigned>((len + 7) / 8), 256, 0, s>>>(part, n, len, out);
+    if (Bp % kBM != 0 || B < 1 || B > Bp) return cudaErrorInvalidValue;
+    TileArgs g{};
+    g.X = X;
+    g.idx = idx;
+    g.cursor = cursor;
+    g.y = y;
+    g.B = B;
+    g.Bp = Bp;
+    g.in_dim = b.in_dim;
+    g.wimg = static_cast<const uint8_t *>(b.wimg);
+    g.params = b.params;
+    g.off_b1 = b.off_b1;
+    g.off_b2 = b.off_b2;
+    g.off_w3 = b.off_w3;
+    g.off_b3 = b.off_b3;
+    g.p_out = p_out;
+    g.xt_img = static_cast<uint8_t *>(b.xt_img);
+    g.h1t_img = static_cast<uint8_t *>(b.h1t_img);
+    g.dh2t_img = static_cast<uint8_t *>(b.dh2t_img);
+    g.dh1t_img = static_cast<uint8_t *>(b.dh1t_img);
+    g.part_head = b.part_head;
+    g.part_b1 = b.part_b1;
+    g.status = b.status;
+    if (y)
+        k_tile<true><<<Bp / kBM, 128, kTileSmem, s>>>(g);
     else
-        k_sum_partials<<<static_cast<unsigned>((len + 255) / 256), 256, 0, s>>>(part, n, len, out);
+        k_tile<false><<<Bp / kBM, 128, kTileSmem, s>>>(g);
     return cudaGetLastError();
 }
 
-cudaError_t mlp_launch_adamw(float *w, const float *g, float *m, float *v, int64_t n, float lr, float beta1, float beta2,
-                             float eps, float wd, float bc1, float bc2, const float *bc_table, const int64_t *cursor,
-                             cudaStream_t s)
+cudaError_t mlp_launch_wgrad(const MlpBuffers &b, int Bp, cudaStream_t s)
 {
-    k_adamw<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(w, g, m, v, n, lr, beta1, beta2, eps, wd, bc1, bc2,
-                                                                   bc_table, cursor);
+    WgradArgs g{};
+    g.h1t_img = static_cast<const uint8_t *>(b.h1t_img);
+    g.dh2t_img = static_cast<const uint8_t *>(b.dh2t_img);
+    g.dh1t_img = static_cast<const uint8_t *>(b.dh1t_img);
+    g.xt_img = static_cast<const uint8_t *>(b.xt_img);
+    g.n_mchunks = Bp / 64;
+    const int splits = mlp_wgrad_splits(Bp, &g.chunks_per_split);
+    g.part_w2 = b.part_w2;
+    g.part_w1 = b.part_w1;
+    g.status = b.status;
+    k_wgrad<<<dim3(4, splits), 128, kWgradSmem, s>>>(g);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_launch_update(const MlpBuffers &b, int Bp, bool adamw, float lr, float wd, float bc1, float bc2,
+                              const float *bc_table, const int64_t *cursor, cudaStream_t s)
+{
+    UpdateArgs g{};
+    g.part_w2 = b.part_w2;
+    g.part_w1 = b.part_w1;
+    g.part_head = b.part_head;
+    g.part_b1 = b.part_b1;
+    int cps = 0;
+    g.n_splits = mlp_wgrad_splits(Bp, &cps);
+    g.n_tiles = Bp / kBM;
+    g.in_dim = b.in_dim;
+    g.n_params = b.n_params;
+    g.off_b1 = b.off_b1;
+    g.off_W2 = b.off_W2;
+    g.off_b2 = b.off_b2;
+    g.off_w3 = b.off_w3;
+    g.off_b3 = b.off_b3;
+    g.grads = b.grads;
+    g.loss_sum = b.loss_sum;
+    if (adamw) {
+        g.w = b.params;
+        g.m = b.m;
+        g.v = b.v;
+    }
+    g.lr = lr;
+    g.beta1 = 0.9f;
+    g.beta2 = 0.999f;
+    g.eps = 1e-8f;
+    g.wd = wd;
+    g.bc1 = bc1;
+    g.bc2 = bc2;
+    g.bc_table = bc_table;
+    g.cursor = cursor;
+    g.wimg = static_cast<uint8_t *>(b.wimg);
+    const int64_t n = b.n_params + 1;
+    k_update<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(g);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_launch_refresh(const MlpBuffers &b, cudaStream_t s)
+{
+    k_refresh<<<(kH * kH + 255) / 256, 256, 0, s>>>(b.params + b.off_W1, b.in_dim, b.params + b.off_W2,
+                                                     static_cast<uint8_t *>(b.wimg));
     return cudaGetLastError();
 }
 
 cudaError_t mlp_launch_epoch_tail(const float *loss_sum, int B, int64_t *cursor, float *losses, cudaStream_t s)
 {
     k_epoch_tail<<<1, 1, 0, s>>>(loss_sum, B, cursor, losses);
-    return cudaGetLastError();
-}
-
-cudaError_t mlp_launch_refresh(const float *W1, int in_dim, const float *W2, void *W1t, void *W2t, void *W2b,
-                               cudaStream_t s)
-{
-    k_refresh_bf16<<<(kH * kH + 255) / 256, 256, 0, s>>>(W1, in_dim, W2, static_cast<__nv_bfloat16 *>(W1t),
-                                                          static_cast<__nv_bfloat16 *>(W2t),
-                                                          static_cast<__nv_bfloat16 *>(W2b));
     return cudaGetLastError();
 }
 

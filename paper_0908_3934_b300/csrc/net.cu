@@ -45,10 +45,11 @@ struct gn_net {
     bool stream_edges = true;
     int n_blocks = 0;
     int step_kernel = 0;       // 0 not chosen yet (autotune), 1 row block per CTA, 2 persistent pipelined,
-                               // 3 staged tiles
+                               // 3 staged tiles, 4 resident (the whole network in one CTA's shared memory)
     int shape = 0;             // index into gn::kStepShapes (kernel 2 uses shape 0; kernel 3: gn::kStagedShapes)
     int grid = 0;              // CTAs per launch
     std::vector<int32_t> h_row_ptr;  // host copy, to cut row blocks for another shape
+    gn::ResidentLayout res{};  // kernel 4: shared-memory layout of the network
     int32_t stride = 0;        // ring slot stride (floats)
     double v_rest = 0.0, w_rest = 0.0, dt = 0.0;
     int32_t sample_every = 1;
@@ -158,6 +159,7 @@ void sync(gn_net *net)
 cudaError_t launch_kind(const gn::StepArgs &a, const gn_net *net, int k, cudaStream_t s)
 {
     switch (net->step_kernel) {
+        case 4: return k == 0 ? gn::launch_resident(a, net->res, 1, net->shape, s) : cudaErrorInvalidValue;
         case 2: return gn::launch_step_pipe(a, net->grid, k, net->packed, net->stream_edges, s);
         case 3:
             return gn::launch_step_staged(a, net->grid, k, gn::kStagedShapes[net->shape], net->packed,
@@ -261,8 +263,35 @@ void set_blocks(gn_net *net, int shape)
     net->shape = shape;
 }
 
+// Whether the resident kernel in CTA shape `shape` holds the network; on success
+// its layout is set and the kernel's shared-memory limit raised.
+bool set_resident(gn_net *net, int shape)
+{
+    if (net->stdp || !net->packed || net->N < 1) return false;
+    int longest = 0;
+    for (int32_t j = 0; j < net->N; ++j) longest = std::max(longest, net->h_row_ptr[j + 1] - net->h_row_ptr[j]);
+    if (longest > gn::kResidentMaxRow) return false;
+    const gn::ResidentLayout L = gn::resident_layout(net->N, net->E, net->R, net->model, net->args.frame_avg != 0);
+    size_t max_bytes = 0;
+    cuda_check(gn::resident_prepare(net->model, shape, L.bytes, &max_bytes), "resident kernel setup");
+    if (L.bytes > max_bytes) return false;
+    net->res = L;
+    return true;
+}
+
 void configure(gn_net *net, int kind, int shape)
 {
+    if (kind == 4) {
+        if (!set_resident(net, shape))
+            fail(GN_EINVAL, "the resident step kernel cannot hold this network (it must fit one CTA's shared "
+                            "memory, with packed edge keys, rows of at most %d edges and static weights)",
+                 gn::kResidentMaxRow);
+        net->step_kernel = 4;
+        net->shape = shape;
+        net->grid = 1;
+        net->graph_stale = true;
+        return;
+    }
     if (kind == 3) {
         if (!set_staged(net, shape))
             fail(GN_EINVAL, "the staged step kernel cannot hold this network (a tile needs more shared memory "
@@ -315,7 +344,8 @@ bool tune_cache_lookup(const std::string &key, int *kind, int *shape)
     bool found = false;
     while (fscanf(f, "%255s %d %d", k, &a, &b) == 3)
         if (key == k && b >= 0 &&
-            (((a == 1 || a == 2) && b < gn::kNumStepShapes) || (a == 3 && b < gn::kNumStagedShapes))) {
+            (((a == 1 || a == 2) && b < gn::kNumStepShapes) || (a == 3 && b < gn::kNumStagedShapes) ||
+             (a == 4 && b < gn::kNumResidentShapes))) {
             *kind = a;
             *shape = b;
             found = true;
@@ -344,7 +374,8 @@ void autotune(gn_net *net)
 {
     const std::string key = tune_key(net);
     int cached_kind = 0, cached_shape = 0;
-    if (tune_cache_lookup(key, &cached_kind, &cached_shape) && (cached_kind != 3 || set_staged(net, cached_shape))) {
+    if (tune_cache_lookup(key, &cached_kind, &cached_shape) && (cached_kind != 3 || set_staged(net, cached_shape)) &&
+        (cached_kind != 4 || set_resident(net, cached_shape))) {
         configure(net, cached_kind, cached_shape);
         return;
     }
@@ -408,8 +439,10 @@ void autotune(gn_net *net)
         for (int sh = 0; sh < gn::kNumStepShapes; ++sh) cands.push_back({1, sh});
         cands.push_back({2, 0});
         for (int sh = 0; sh < gn::kNumStagedShapes; ++sh) cands.push_back({3, sh});
+        for (int sh = 0; sh < gn::kNumResidentShapes; ++sh) cands.push_back({4, sh});
         for (const Cand &c : cands) {
             if (c.kind == 3 && !set_staged(net, c.shape)) continue;
+            if (c.kind == 4 && !set_resident(net, c.shape)) continue;
             configure(net, c.kind, c.shape);
             gn::StepArgs a = net->args;
             a.ring = ring.p;
@@ -429,15 +462,28 @@ void autotune(gn_net *net)
             a.hh_g = hh_g.p;
             a.obs_acc = obs_acc.p;
             const int warm = 3, timed = 24;  // near ties between shapes need more than a few steps
-            for (int k = 0; k < warm; ++k)
-                cuda_check(launch_kind(a, net, k, net->stream), "autotune launch");
+            // the resident kernel runs many steps per launch: one launch of kResidentSteps x
+            // timed steps, its time scaled to `timed` steps
+            constexpr int kResidentSteps = 8;
+            if (c.kind == 4) {
+                cuda_check(gn::launch_resident(a, net->res, kResidentSteps, c.shape, net->stream), "autotune launch");
+            } else {
+                for (int k = 0; k < warm; ++k)
+                    cuda_check(launch_kind(a, net, k, net->stream), "autotune launch");
+            }
             cuda_check(cudaEventRecord(t0, net->stream), "event");
-            for (int k = 0; k < timed; ++k)
-                cuda_check(launch_kind(a, net, k, net->stream), "autotune launch");
+            if (c.kind == 4) {
+                cuda_check(gn::launch_resident(a, net->res, kResidentSteps * timed, c.shape, net->stream),
+                           "autotune launch");
+            } else {
+                for (int k = 0; k < timed; ++k)
+                    cuda_check(launch_kind(a, net, k, net->stream), "autotune launch");
+            }
             cuda_check(cudaEventRecord(t1, net->stream), "event");
             cuda_check(cudaEventSynchronize(t1), "autotune");
             float ms = 0.0f;
             cuda_check(cudaEventElapsedTime(&ms, t0, t1), "event");
+            if (c.kind == 4) ms /= kResidentSteps;
             if (const char *log = getenv("GN_AUTOTUNE_LOG")) {
                 if (FILE *f = fopen(log, "a")) {
                     fprintf(f, "%s kind %d shape %d ms_per_step %.5f\n", key.c_str(), c.kind, c.shape, ms / timed);
@@ -682,17 +728,18 @@ gn_status gn_net_create(const gn_net_desc *desc, gn_net **out)
         // GN_STEP_SHAPE=i picks the CTA shape of an explicitly chosen kernel 1 or 3
         // (plastic default: the 12288-edge tiles, measured best on the 1M-node net --
         // 0.139 ms per step against 0.149 and 0.167 for 8192 and 16384 edges)
-        int shape = net->stdp ? 4 : 0;
-        if (const char *e = getenv("GN_STEP_SHAPE"); e && *e && (kind == 1 || kind == 3)) {
+        int shape = net->stdp ? 4 : kind == 4 ? 1 : 0;
+        if (const char *e = getenv("GN_STEP_SHAPE"); e && *e && (kind == 1 || kind == 3 || kind == 4)) {
             shape = atoi(e);
-            const int n_shapes = kind == 1 ? gn::kNumStepShapes : gn::kNumStagedShapes;
+            const int n_shapes = kind == 1 ? gn::kNumStepShapes : kind == 3 ? gn::kNumStagedShapes
+                                                                            : gn::kNumResidentShapes;
             if (shape < 0 || shape >= n_shapes) fail(GN_EINVAL, "GN_STEP_SHAPE=%s is not a shape of kernel %d", e,
                                                        kind);
             if (net->stdp && gn::kStagedShapes[shape].stage_entries)
                 fail(GN_EINVAL, "GN_STEP_SHAPE=%s stages the edge entries, which plastic weights cannot use", e);
         }
         configure(net, kind == 2 ? 2 : 1, kind == 1 ? shape : 0);
-        if (kind == 3) configure(net, 3, shape);
+        if (kind == 3 || kind == 4) configure(net, kind, shape);
         if (kind == 0)
             net->step_kernel = 0;
         else
@@ -730,11 +777,13 @@ gn_status gn_net_get_info(const gn_net *net, gn_net_info *info)
         info->min_delay = net->dmin;
         info->n_clamped = net->n_clamped;
         info->edge_format = net->packed ? 0 : 1;
-        const bool staged = net->step_kernel == 3;
-        info->n_blocks = staged ? net->n_tiles : net->n_blocks;
+        const bool staged = net->step_kernel == 3, resident = net->step_kernel == 4;
+        info->n_blocks = staged ? net->n_tiles : resident ? 1 : net->n_blocks;
         info->step_kernel = net->step_kernel;
-        info->step_threads = staged ? gn::kStagedShapes[net->shape].threads : gn::kStepShapes[net->shape].threads;
-        info->step_edges_per_thread = staged ? gn::kWarpRow : gn::kStepShapes[net->shape].ept;
+        info->step_threads = staged     ? gn::kStagedShapes[net->shape].threads
+                             : resident ? gn::kResidentThreads[net->shape]
+                                        : gn::kStepShapes[net->shape].threads;
+        info->step_edges_per_thread = (staged || resident) ? gn::kWarpRow : gn::kStepShapes[net->shape].ept;
         info->grid = net->grid;
         info->step = net->step;
         info->samples = net->step / net->sample_every;
@@ -801,6 +850,17 @@ gn_status gn_step(gn_net *net, int64_t n_steps)
         if (net->step_kernel == 0) {
             autotune(net);
             finalize_kernel(net);
+        }
+        if (net->step_kernel == 4) {
+            // the resident kernel: a launch runs up to kResidentChunk steps
+            constexpr int64_t kResidentChunk = 1 << 16;
+            for (int64_t left = n_steps; left > 0; left -= kResidentChunk) {
+                const int chunk = static_cast<int>(std::min(left, kResidentChunk));
+                cuda_check(gn::launch_resident(net->args, net->res, chunk, net->shape, net->stream), "resident launch");
+                cuda_check(gn::launch_advance(net->d_step.p, chunk, net->stream), "advance launch");
+            }
+            net->step += n_steps;
+            return;
         }
         if (net->graph_stale) build_graph(net);
         int64_t left = n_steps;

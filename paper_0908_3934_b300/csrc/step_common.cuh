@@ -143,12 +143,15 @@ __device__ __forceinline__ float frame_value(const StepArgs &a, int r, float c1,
 // spike, and the calcium readout every sample_every steps.  A plastic net's ring
 // word also carries s in whole steps: s_j' = (1 - spd(V_j)) (s_j + dt), from the
 // word of step n.
-template <bool kPl>
+// (kRing false: the caller keeps its own spike ring and writes it; the resident
+// kernel packs spd into bits by warp ballot)
+template <bool kPl, bool kRing = true>
 __device__ __forceinline__ void spiking_outputs(const StepArgs &a, int r, int64_t n, bool above, bool above1,
                                                 float c1, int32_t orig, uint32_t word_now)
 {
     const int64_t at = ((n + 1) & a.ring_mask) * a.ring_stride + r;
-    if constexpr (kPl) {
+    if constexpr (!kRing) {
+    } else if constexpr (kPl) {
         const uint32_t k1 = (word_now & 1u) ? 0u : min((word_now >> 1) + 1u, kSpikeStepsMax);
         reinterpret_cast<uint32_t *>(a.ring)[at] = (k1 << 1) | (above1 ? 1u : 0u);
     } else {
@@ -215,7 +218,7 @@ __device__ __forceinline__ float calcium_step(const StepArgs &a, float c, float 
 // but p, the one variable that reads S = sum_e w_e spd(V_src(n - D_e)), is updated
 // here (the ring holds spd); returns (r, p) at step n for psc_finish.  A spike
 // resets V, so every step with V >= V_peak is a new spike.
-template <bool kPl>
+template <bool kPl, bool kRing = true>
 __device__ __forceinline__ float2 izh_begin(const StepArgs &a, int r, int64_t n, float2 wc, float U, int32_t orig,
                                          uint32_t word_now)
 {
@@ -237,7 +240,7 @@ __device__ __forceinline__ float2 izh_begin(const StepArgs &a, int r, int64_t n,
     const float c1 = calcium_step(a, c, z.caq, spike);
     a.iz_v[r] = V1;
     a.wc[r] = make_float2(W1, c1);
-    spiking_outputs<kPl>(a, r, n, false, V1 >= z.vpeak, c1, orig, word_now);
+    spiking_outputs<kPl, kRing>(a, r, n, false, V1 >= z.vpeak, c1, orig, word_now);
     return rp;
 }
 
@@ -251,7 +254,7 @@ __device__ __forceinline__ float hh_trap(float x, float y)
 // (mV, ms), forward Euler of V and the gates m, n, h from step-n values, the PSC and
 // calcium as in izh_begin (p is left to psc_finish); no reset, events are upward
 // crossings of V_peak.
-template <bool kPl>
+template <bool kPl, bool kRing = true>
 __device__ __forceinline__ float2 hh_begin(const StepArgs &a, int r, int64_t n, float2 wc, float U, int32_t orig,
                                         uint32_t word_now)
 {
@@ -284,7 +287,7 @@ __device__ __forceinline__ float2 hh_begin(const StepArgs &a, int r, int64_t n, 
     a.iz_v[r] = V1;
     a.hh_g[r] = make_float4(m1, n1, h1, 0.0f);
     a.wc[r] = make_float2(0.0f, c1);
-    spiking_outputs<kPl>(a, r, n, above, V1 >= z.vpeak, c1, orig, word_now);
+    spiking_outputs<kPl, kRing>(a, r, n, above, V1 >= z.vpeak, c1, orig, word_now);
     return rp;
 }
 
@@ -336,18 +339,20 @@ __device__ __forceinline__ float stimulus(const StepArgs &a, int r, int64_t n, i
 }
 
 // The S-independent part of a spiking node's step (model kM & 3 = 1 or 2, kM &
-// kPlastic with plastic weights, where word_now is the node's ring word of step n):
-// stimulus and everything but p; returns (r, p) at step n for psc_finish.
+// kPlastic with plastic weights, where word_now is the node's ring word of step n;
+// kM & kNoRing: the spike ring is left to the caller): stimulus and everything but
+// p; returns (r, p) at step n for psc_finish.
 template <int kM>
 __device__ __forceinline__ float2 spiking_begin(const StepArgs &a, int r, int64_t n, float2 wc, int32_t orig,
                                                 int32_t cnt0, uint32_t word_now = 0)
 {
     constexpr bool kPl = (kM & kPlastic) != 0;
+    constexpr bool kRing = (kM & kNoRing) == 0;
     const float U = stimulus(a, r, n, orig, cnt0);
     if constexpr ((kM & 3) == 1)
-        return izh_begin<kPl>(a, r, n, wc, U, orig, word_now);
+        return izh_begin<kPl, kRing>(a, r, n, wc, U, orig, word_now);
     else
-        return hh_begin<kPl>(a, r, n, wc, U, orig, word_now);
+        return hh_begin<kPl, kRing>(a, r, n, wc, U, orig, word_now);
 }
 
 // Stimulus, node model kM's Euler step (0 FitzHugh-Nagumo, 1 Izhikevich, 2
