@@ -259,6 +259,36 @@ def test_every_kernel_and_shape_gives_the_same_bits(monkeypatch):
         assert np.array_equal(hist, ref[1]), (kind, shape)
 
 
+def test_early_gathers_with_the_fastest_slot_reuse(monkeypatch):
+    """The early-gather argument at its tightest: a 4-slot ring and delays of 1 or 2
+    steps, so slot n + 1 written in step n is the slot step n - 3 read, on a grid
+    with more tiles than the device holds at once (gathers before the grid wait).
+    3000 steps bit-identical to the same kernel waiting first, and the first 60
+    steps within the tolerance of the oracle, window by window."""
+    spec = netgen.large(n=300000, mean_deg=20, bg_rate_hz=100.0)
+    rng = np.random.default_rng(17)
+    spec.delay = rng.integers(1, 3, spec.n_edges).astype(np.int32)
+    spec.ring_depth = 4
+    monkeypatch.setenv("GN_STEP_SHAPE", "3")
+    monkeypatch.setenv("GN_STAGED_EARLY", "1")
+    net = Net(spec, step_kernel=3)
+    info = net.gn_net_get_info()
+    assert info["ring_depth"] == 4 and info["max_delay"] == 2 and info["n_blocks"] > 148 * 6
+    worst, _ = windowed(spec, net, 60)
+    assert_windows(worst)
+    out = []
+    for early in ("1", "0"):
+        monkeypatch.setenv("GN_STAGED_EARLY", early)
+        n = Net(spec, step_kernel=3)
+        n.gn_step(3000)
+        out.append((n.gn_get_state(), n.gn_get_history(3), n.gn_get_arrivals()))
+    (sa, ha, fa), (sb, hb, fb) = out
+    assert np.abs(sa["v"]).max() > 0.1
+    for k in ("v", "w", "c", "bg_count"):
+        assert np.array_equal(sa[k], sb[k]), k
+    assert np.array_equal(ha, hb) and np.array_equal(fa, fb)
+
+
 @pytest.mark.parametrize("model", ["fhn", "izh", "hh"])
 def test_early_gathers_give_the_same_bits(monkeypatch, model):
     """A staged grid with more tiles than the device holds at once gathers before
