@@ -306,6 +306,16 @@ def batch_member(seed: int, n: int | None = None, n_lo: int = 32, n_hi: int = 40
                    name=f"batch_s{seed}")
 
 
+def estimator_control(seed: int, n: int = 512, bg_rate_hz: float = 5.0) -> NetSpec:
+    """Positive control of the connectivity estimators: the batch-member laws at a
+    kept in-degree of 1 (sparse, so a spike crosses an edge without setting off a
+    wave through the whole net), no explicit pulses, and background pulses of 1 ms at
+    `bg_rate_hz` that drive every node independently."""
+    sp = batch_member(seed, n=n, kept_deg=1.0)
+    return dataclasses.replace(sp, pulses=[], background=dict(rate_hz=bg_rate_hz, amp=1.0, dur_ms=1.0, seed=seed + 5),
+                               name=f"control_s{seed}")
+
+
 def batch(n_nets: int = 4096, seed0: int = 1000, **kw) -> list:
     return [batch_member(seed0 + i, **kw) for i in range(n_nets)]
 
