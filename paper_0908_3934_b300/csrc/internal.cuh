@@ -199,15 +199,21 @@ cudaError_t batch_staged_prepare(int model, bool packed, bool stream_edges, size
 struct ResidentLayout {
     int32_t N, R, words, stride;  // nodes, ring slots, 32-bit words per spike-ring slot, floats per FHN slot
     int64_t E;
+    int32_t ev_cap;               // events buffered in shared memory (a multiple of N)
+    int32_t pulse_cap;            // pulses kept in shared memory (more stay in global memory)
     uint32_t off_key, off_w, off_rp, off_S, off_long, off_ring, off_wc, off_v, off_rpq, off_hh, off_bgc, off_acc;
+    uint32_t off_perm, off_first, off_evn, off_evs, off_pnode, off_pon, off_poff, off_pamp;
     size_t bytes;
 };
+constexpr int kResidentPulses = 256;
 constexpr int kNumResidentShapes = 3;
 extern const int kResidentThreads[kNumResidentShapes];
 // the longest row the resident kernel takes: every kernel sums rows up to this length in
 // the same order
 constexpr int kResidentMaxRow = 1021;
-ResidentLayout resident_layout(int N, int64_t E, int R, int model, bool frame_avg);
+// ev_factor: events buffered per node (1 or 2; with 1 the buffer is flushed after every
+// step that had an event)
+ResidentLayout resident_layout(int N, int64_t E, int R, int model, bool frame_avg, int ev_factor);
 // raises the kernel's shared-memory limit to `bytes` of dynamic shared memory; returns
 // the largest dynamic size a CTA can have in *max_bytes
 cudaError_t resident_prepare(int model, int shape, size_t bytes, size_t *max_bytes);
@@ -250,8 +256,8 @@ constexpr int kMlpHidden = 256;
 constexpr int kMlpInPad = 64;
 // Device buffers of one MLP (owned by the host runtime, mlp.cu).  Parameters, their
 // gradients and Adam moments are packed FP32 [W1 (in x 256) | b1 | W2 | b2 | w3 | b3];
-// wimg holds the BF16 weight images the tile kernel streams (9 chunks of 32 KB: W1t,
-// W2t in four K-chunks, W2b in four K-chunks); the *_img buffers the batch-major
+// wimg holds the BF16 weight images the tile kernel streams (9 chunks of 32 KB: W1t, W2t
+// in four K-chunks, W2b in four K-chunks); the *_img buffers the batch-major
 // operands of the weight gradients, one image per 64 rows of the batch.
 struct MlpBuffers {
     int in_dim;
@@ -259,7 +265,7 @@ struct MlpBuffers {
     float *params, *grads, *m, *v;
     void *wimg, *xt_img, *h1t_img, *dh2t_img, *dh1t_img;
     float *part_w2;    // [splits][256][256]
-    float *part_w1;    // [splits][256][64] (dW1 transposed)
+    float *part_w1;    // [splits][64][256] (dW1, rows k >= in_dim zero)
     float *part_head;  // [tiles][2 * 256 + 2]
     float *part_b1;    // [tiles][256]
     float *loss_sum;   // [1]

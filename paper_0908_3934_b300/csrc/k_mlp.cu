@@ -20,11 +20,12 @@
 //            weight images the tile kernel streams;
 //   k_epoch_tail (replayed epochs) the loss of the step and the batch cursor.
 //
-// Shared-memory operand layout (tcgen05 K-major, no swizzle): a matrix of R rows x 64
-// K-elements is a chunk of core matrices of 8 rows x 16 bytes; element (r, c) sits at
-// byte (r / 8) 1024 + (c / 8) 128 + (r % 8) 16 + (c % 8) 2 (LBO 128 B along K, SBO
-// 1024 B along rows).  Weights and the transposed activations are kept in global
-// memory in exactly this image, so one 1D bulk copy lands a chunk.
+// Shared-memory operand layout (tcgen05 K-major, 128-byte swizzle): a matrix of R rows x
+// 64 K-elements is a chunk of 128-byte rows; element (r, c) sits at byte r 128 +
+// ((c / 8) xor (r % 8)) 16 + (c % 8) 2 (8-row groups 1024 bytes apart), so the tensor
+// core's operand fetches spread over the shared-memory banks.  Weights and the transposed
+// activations are kept in global memory in exactly this image, so one 1D bulk copy lands a
+// chunk.
 #include <cuda_bf16.h>
 
 #include "internal.cuh"
@@ -37,10 +38,15 @@ constexpr int kH = kMlpHidden;   // 256
 constexpr int kKP = kMlpInPad;   // 64
 constexpr int kBM = 128;         // batch rows per tile
 constexpr uint32_t kWChunk = 256u * 64u * 2u;  // one weight chunk: 256 rows x 64 K, BF16 (32 KB)
+constexpr int kWChunks = 9;                     // W1, W2 x 4, W2^T x 4
+constexpr int kWStages = 2;                     // weight chunks in flight
+constexpr size_t kWImage = static_cast<size_t>(kWChunks) * kWChunk;
 
+// byte of element (r, c) in a K-major chunk of 64 K-elements per row with the 128-byte
+// swizzle (rows 128 bytes apart, 16-byte unit j of row r at position j ^ (r % 8))
 __host__ __device__ constexpr uint32_t img_off(uint32_t r, uint32_t c)
 {
-    return (r >> 3) * 1024u + (c >> 3) * 128u + (r & 7u) * 16u + (c & 7u) * 2u;
+    return r * 128u + ((((c >> 3) ^ r) & 7u) << 4) + (c & 7u) * 2u;
 }
 
 __device__ __forceinline__ int64_t batch_row(const int64_t *idx, const int64_t *cursor, int B, int64_t r)
@@ -55,40 +61,79 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
     return *reinterpret_cast<const uint32_t *>(&pr);
 }
 
-// 32 columns (c0 .. c0 + 31) of this thread's row as BF16 into a K-major operand of
-// 128 rows held as chunks of 64 K-elements (16 KB apart).
+// The 16-byte unit holding columns c .. c + 7 (c % 8 == 0) of `row` in a K-major operand
+// of 128 rows held as swizzled chunks of 64 K-elements (16 KB apart).
+__device__ __forceinline__ uint8_t *op_unit(uint8_t *op, int row, int c)
+{
+    return op + (c >> 6) * 16384 + row * 128 + ((((c & 63) >> 3) ^ row) & 7) * 16;
+}
+
+// 32 columns (c0 .. c0 + 31) of this thread's row as BF16 into such an operand.
 __device__ __forceinline__ void put_row32(uint8_t *op, int row, int c0, const float (&v)[32])
 {
-    uint8_t *base = op + (c0 >> 6) * 16384 + (row >> 3) * 1024 + (row & 7) * 16 + ((c0 & 63) >> 3) * 128;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const uint4 u = make_uint4(pack_bf16(v[8 * q], v[8 * q + 1]), pack_bf16(v[8 * q + 2], v[8 * q + 3]),
                                    pack_bf16(v[8 * q + 4], v[8 * q + 5]), pack_bf16(v[8 * q + 6], v[8 * q + 7]));
-        *reinterpret_cast<uint4 *>(base + q * 128) = u;
+        *reinterpret_cast<uint4 *>(op_unit(op, row, c0 + 8 * q)) = u;
     }
 }
 
-// The warp's 32 rows x 32 features (f0 .. f0 + 31) as BF16 into the batch-major image
-// of a weight-gradient operand: rows = features, K = the 64 batch rows of a chunk.
-// `chunk` points at the 64-row chunk's image (feature f, batch row m at img_off(f, m));
-// mrow0 = the first of the warp's rows within that chunk (0 or 32).  Through a
-// per-warp staging tile so each lane stores 16 contiguous bytes (8 rows of one
-// feature) and 8 lanes cover 128 contiguous bytes.
-__device__ __forceinline__ void put_cols32(uint8_t *chunk, int f0, int mrow0, const float (&v)[32], uint16_t *stage,
-                                           int lane)
+// Transpose of an 8 x 8 block of 16-bit values held by 8 consecutive lanes (lane i: row
+// i as four words of two values); afterwards lane i holds column i (rows in order).
+// Three exchange stages: 4 x 4 blocks (xor 4), 2 x 2 blocks of words (xor 2), halves
+// of words (xor 1).
+__device__ __forceinline__ void transpose8(uint32_t (&w)[4], int i)
 {
-    constexpr int kPitch = 40;  // uint16 per staging row: 32 rows + 8 pad (80 B, 16-byte aligned)
-#pragma unroll
-    for (int j = 0; j < 32; ++j)
-        stage[j * kPitch + lane] = __bfloat16_as_ushort(__float2bfloat16_rn(v[j]));
-    __syncwarp();
-#pragma unroll
-    for (int it = 0; it < 4; ++it) {
-        const int f = 8 * it + (lane & 7), g = lane >> 3;  // feature, group of 8 rows
-        const uint4 u = *reinterpret_cast<const uint4 *>(stage + f * kPitch + 8 * g);
-        *reinterpret_cast<uint4 *>(chunk + img_off(f0 + f, mrow0 + 8 * g)) = u;
+    {
+        const bool top = (i & 4) == 0;
+        const uint32_t r0 = __shfl_xor_sync(0xffffffffu, top ? w[2] : w[0], 4);
+        const uint32_t r1 = __shfl_xor_sync(0xffffffffu, top ? w[3] : w[1], 4);
+        if (top) {
+            w[2] = r0;
+            w[3] = r1;
+        } else {
+            w[0] = r0;
+            w[1] = r1;
+        }
     }
-    __syncwarp();
+    {
+        const bool hi = (i & 2) != 0;
+        const uint32_t r0 = __shfl_xor_sync(0xffffffffu, hi ? w[0] : w[1], 2);
+        const uint32_t r1 = __shfl_xor_sync(0xffffffffu, hi ? w[2] : w[3], 2);
+        if (!hi) {
+            w[1] = r0;
+            w[3] = r1;
+        } else {
+            w[0] = r0;
+            w[2] = r1;
+        }
+    }
+    const bool odd = (i & 1) != 0;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const uint32_t r = __shfl_xor_sync(0xffffffffu, odd ? (w[p] & 0xFFFFu) : (w[p] >> 16), 1);
+        w[p] = odd ? ((w[p] & 0xFFFF0000u) | r) : ((w[p] & 0xFFFFu) | (r << 16));
+    }
+}
+
+// 32 features (f0 .. f0 + 31) of the warp's 32 rows (this thread: row `mrow` of the
+// 64-row chunk, a multiple-of-8 group per 8 lanes) as BF16 into the batch-major image of
+// a weight-gradient operand (rows = features, K = the chunk's 64 batch rows).  Blocks of
+// 8 rows x 8 features are transposed across 8 lanes, so each lane stores 16 bytes (8 rows
+// of one feature) and the four lanes of a feature fill 64 contiguous bytes.
+__device__ __forceinline__ void put_col32(uint8_t *chunk, int f0, int mrow, const float (&v)[32], int lane)
+{
+    const int mg = mrow >> 3, i = lane & 7;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        uint32_t w[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) w[p] = pack_bf16(v[8 * b + 2 * p], v[8 * b + 2 * p + 1]);
+        transpose8(w, i);
+        const int f = f0 + 8 * b + i;
+        *reinterpret_cast<uint4 *>(chunk + f * 128 + (((mg ^ f) & 7) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
 }
 
 // Column sums of 32 values over the warp's 32 rows (reduce-scatter: lane l ends with
@@ -124,45 +169,58 @@ struct TileArgs {
     unsigned int *status;
 };
 
-// Shared memory of k_tile (dynamic): weight ring 2 x 32 KB | X 16 KB | H1 64 KB | dH2 64 KB
-// | staging 4 x 2560 B.  The column sums (2 x 4 warps x 256 floats) reuse the X operand,
-// which is dead once layer 1's MMAs are complete.
+// Shared memory of k_tile (dynamic, from a 1024-byte aligned base): weight ring 2 x 32 KB |
+// X 16 KB | H1 64 KB | dH2 64 KB.
+// The column sums (2 x 4 lane groups x 256 floats) reuse the X operand, which is dead
+// once layer 1's MMAs are complete.
 constexpr int kOffRing = 0;
-constexpr int kOffX = kOffRing + 2 * static_cast<int>(kWChunk);
+constexpr int kOffX = kOffRing + kWStages * static_cast<int>(kWChunk);
 constexpr int kOffH1 = kOffX + 16384;
 constexpr int kOffD2 = kOffH1 + 65536;
-constexpr int kOffStage = kOffD2 + 65536;
 constexpr int kOffCols = kOffX;
-constexpr int kTileSmem = kOffStage + 4 * 2560;
+constexpr int kTileSmem = kOffD2 + 65536 + 1024;  // + the alignment of the base
 static_assert(2 * 4 * kH * 4 <= 16384, "column sums fit the X operand");
+constexpr int kTileThreads = 512;
 
+// 16 warps: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (its lane group: rows of
+// the tile) and owns columns 64 (w / 4) .. + 63 (its column quarter) of every 256-wide
+// layer, so each epilogue pass is two 32-column loads per warp.
 template <bool kTrain>
-__global__ void __launch_bounds__(128, 1) k_tile(const TileArgs g)
+__global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs g)
 {
-    extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t s_full[2], s_empty[2], s_mma;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);  // swizzle atoms: 1 KB aligned
+    __shared__ __align__(8) uint64_t s_full[kWStages], s_empty[kWStages], s_mma;
     __shared__ uint32_t s_tmem;
     __shared__ int s_fail;
+    __shared__ float s_b1[kH], s_b2[kH], s_w3[kH];
+    __shared__ float s_zp[4][kBM];  // partial output-layer sums per column quarter
+    __shared__ float s_dz[kBM];
     __shared__ float s_red[4][2];
     uint8_t *ring = smem + kOffRing;
     uint8_t *sX = smem + kOffX;
     uint8_t *sH1 = smem + kOffH1;
     uint8_t *sD2 = smem + kOffD2;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    uint16_t *stage = reinterpret_cast<uint16_t *>(smem + kOffStage + warp * 2560);
-    float *cols = reinterpret_cast<float *>(smem + kOffCols);  // [2][4 warps][kH]
+    const int lg = warp & 3, cq = warp >> 2;
+    const int rl = 32 * lg + lane;                              // this thread's row in the tile
+    float *cols = reinterpret_cast<float *>(smem + kOffCols);   // [2][4 lane groups][kH]
     const int tile = blockIdx.x;
-    const int64_t row = static_cast<int64_t>(tile) * kBM + t;  // this thread's batch row
+    const int64_t row = static_cast<int64_t>(tile) * kBM + rl;
     const bool valid = row < g.B;
+    const size_t img_chunk = static_cast<size_t>(tile) * 2 + (rl >> 6);  // this row's 64-row chunk
+    const int mrow = rl & 63;
+    const uint32_t lane_base = static_cast<uint32_t>(32 * lg) << 16;
     constexpr uint32_t kIdesc = idesc_bf16_f32(128, 256);
-    const int n_chunks = kTrain ? 9 : 5;  // W1t, W2t x 4, (W2b x 4)
+    const int n_chunks = kTrain ? kWChunks : 5;  // W1t, W2t x 4, (W2b x 4)
+    const uint8_t *wimg = g.wimg;
 
     if (warp == 0) {
         tmem_alloc(&s_tmem, 512);
         tmem_relinquish();
     }
     if (t == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < kWStages; ++i) {
             mbar_init(&s_full[i], 1);
             mbar_init(&s_empty[i], 1);
         }
@@ -170,44 +228,55 @@ __global__ void __launch_bounds__(128, 1) k_tile(const TileArgs g)
         fence_barrier_init();
         s_fail = 0;
     }
+    for (int i = t; i < kH; i += kTileThreads) {
+        s_b1[i] = g.params[g.off_b1 + i];
+        s_b2[i] = g.params[g.off_b2 + i];
+        s_w3[i] = g.params[g.off_w3 + i];
+    }
     tc_fence_before_sync();
     __syncthreads();
     tc_fence_after_sync();
     const uint32_t tmem = s_tmem;
     bool ok = true;
-    auto load = [&](int c) {  // weight chunk c into stage c & 1
-        mbar_arrive_expect_tx(&s_full[c & 1], kWChunk);
-        bulk_g2s(ring + (c & 1) * kWChunk, g.wimg + static_cast<size_t>(c) * kWChunk, kWChunk, &s_full[c & 1]);
+    auto load = [&](int c) {  // weight chunk c into stage c % kWStages
+        const int st = c % kWStages;
+        mbar_arrive_expect_tx(&s_full[st], kWChunk);
+        bulk_g2s(ring + st * kWChunk, wimg + static_cast<size_t>(c) * kWChunk, kWChunk, &s_full[st]);
     };
     int loaded = 0;  // chunks whose copies were issued (thread 0)
     if (t == 0) {
-        load(0);
-        load(1);
-        loaded = 2;
+        for (; loaded < kWStages; ++loaded) load(loaded);
     }
-    // refill: chunk c's MMAs are complete -> its stage takes chunk c + 2
+    // refill: chunk c's MMAs are complete -> its stage takes chunk c + kWStages
     auto refill = [&](int c) {
-        if (!mbar_wait_bounded(&s_empty[c & 1], (c >> 1) & 1, kDefaultWaitLimit)) ok = false;
-        if (ok && c + 2 < n_chunks) {
-            load(c + 2);
-            loaded = c + 3;
+        if (!mbar_wait_bounded(&s_empty[c % kWStages], (c / kWStages) & 1, kDefaultWaitLimit)) ok = false;
+        if (ok && c + kWStages < n_chunks) {
+            load(c + kWStages);
+            loaded = c + kWStages + 1;
         }
     };
-    // four M=128 N=256 K=16 MMAs of chunk c (A: a K-chunk of an operand in shared memory)
+    // four M=128 N=256 K=16 MMAs of chunk c; A: the matching 64-element K-chunk of an
+    // operand in shared memory (both operands 128-byte swizzled)
     auto mma = [&](int c, const uint8_t *a, uint32_t d, bool first) {
-        if (!mbar_wait_bounded(&s_full[c & 1], (c >> 1) & 1, kDefaultWaitLimit)) ok = false;
+        if (!mbar_wait_bounded(&s_full[c % kWStages], (c / kWStages) & 1, kDefaultWaitLimit)) ok = false;
         if (!ok) return;
         tc_fence_after_sync();
-        const uint8_t *b = ring + (c & 1) * kWChunk;
+        const uint8_t *b = ring + (c % kWStages) * kWChunk;
 #pragma unroll
         for (int ks = 0; ks < 4; ++ks)
-            tc_mma_bf16(d, smem_desc_kmajor(a + ks * 256, 128, 1024), smem_desc_kmajor(b + ks * 256, 128, 1024),
-                        kIdesc, (!first || ks) ? 1u : 0u);
-        tc_commit(&s_empty[c & 1]);
+            tc_mma_bf16(d, smem_desc_sw128(a + ks * 32), smem_desc_sw128(b + ks * 32), kIdesc,
+                        (!first || ks) ? 1u : 0u);
+        tc_commit(&s_empty[c % kWStages]);
+    };
+    int mma_commits = 0;  // thread 0
+    auto commit_mma = [&]() {
+        if (ok) {
+            tc_commit(&s_mma);
+            ++mma_commits;
+        }
     };
     // every thread waits for the MMAs committed to s_mma (phase `ph`); the barrier
     // after it makes s_fail the same for every thread
-    int mma_commits = 0;  // thread 0
     auto wait_mma = [&](int ph) {
         if (!mbar_wait_bounded(&s_mma, ph, kDefaultWaitLimit)) {
             s_fail = 1;
@@ -216,20 +285,27 @@ __global__ void __launch_bounds__(128, 1) k_tile(const TileArgs g)
         tc_fence_after_sync();
         __syncthreads();
     };
+    // 32 accumulator columns (c0 ..) of this thread's row
+    auto acc32 = [&](uint32_t col, float (&v)[32]) {
+        uint32_t raw[32];
+        tmem_ld32(tmem + lane_base + col, raw);
+        tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(raw[j]);
+    };
 
-    // ---- X rows: FP32 -> BF16 into the layer-1 operand (and its batch-major image)
-    {
-        float xv[64];
+    // ---- X rows: FP32 -> BF16 into the layer-1 operand (and its batch-major image);
+    // column quarters 0 and 1 take input columns 0 .. 31 and 32 .. 63
+    if (cq < 2) {
+        float xv[32];
         const int64_t src = valid ? batch_row(g.idx, g.cursor, g.B, row) : 0;
 #pragma unroll
-        for (int c = 0; c < 64; ++c) xv[c] = (valid && c < g.in_dim) ? g.X[src * g.in_dim + c] : 0.0f;
-        put_row32(sX, t, 0, *reinterpret_cast<float(*)[32]>(&xv[0]));
-        put_row32(sX, t, 32, *reinterpret_cast<float(*)[32]>(&xv[32]));
-        if constexpr (kTrain) {
-            uint8_t *chunk = g.xt_img + (static_cast<size_t>(tile) * 2 + (t >> 6)) * (64 * 64 * 2);
-            put_cols32(chunk, 0, (t & 63) & ~31, *reinterpret_cast<float(*)[32]>(&xv[0]), stage, lane);
-            put_cols32(chunk, 32, (t & 63) & ~31, *reinterpret_cast<float(*)[32]>(&xv[32]), stage, lane);
+        for (int j = 0; j < 32; ++j) {
+            const int c = 32 * cq + j;
+            xv[j] = (valid && c < g.in_dim) ? g.X[src * g.in_dim + c] : 0.0f;
         }
+        put_row32(sX, rl, 32 * cq, xv);
+        if constexpr (kTrain) put_col32(g.xt_img + img_chunk * (64 * 64 * 2), 32 * cq, mrow, xv, lane);
     }
     fence_async_shared();
     __syncthreads();
@@ -237,29 +313,20 @@ __global__ void __launch_bounds__(128, 1) k_tile(const TileArgs g)
     // ---- layer 1: C1 = X W1 (tensor memory columns 0 .. 255)
     if (t == 0) {
         mma(0, sX, tmem, true);
-        if (ok) {
-            tc_commit(&s_mma);
-            ++mma_commits;
-        }
+        commit_mma();
         refill(0);
     }
     wait_mma(0);
     // epilogue 1: H1 = relu(C1 + b1), BF16 into the layer-2 operand (+ its batch-major image)
-    const uint32_t lane_base = static_cast<uint32_t>(32 * warp) << 16;
     if (!s_fail) {
 #pragma unroll 1
-        for (int c0 = 0; c0 < kH; c0 += 32) {
-            uint32_t raw[32];
-            tmem_ld32(tmem + lane_base + c0, raw);
-            tmem_ld_wait();
+        for (int c0 = 64 * cq; c0 < 64 * cq + 64; c0 += 32) {
             float v[32];
+            acc32(c0, v);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] = fmaxf(__uint_as_float(raw[j]) + __ldg(g.params + g.off_b1 + c0 + j), 0.0f);
-            put_row32(sH1, t, c0, v);
-            if constexpr (kTrain) {
-                uint8_t *chunk = g.h1t_img + (static_cast<size_t>(tile) * 2 + (t >> 6)) * (kH * 64 * 2);
-                put_cols32(chunk, c0, (t & 63) & ~31, v, stage, lane);
-            }
+            for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + s_b1[c0 + j], 0.0f);
+            put_row32(sH1, rl, c0, v);
+            if constexpr (kTrain) put_col32(g.h1t_img + img_chunk * (kH * 64 * 2), c0, mrow, v, lane);
         }
     }
     fence_async_shared();
@@ -269,84 +336,86 @@ __global__ void __launch_bounds__(128, 1) k_tile(const TileArgs g)
     // ---- layer 2: C2 = H1 W2 (columns 256 .. 511), W2t in four K-chunks
     if (t == 0 && !s_fail) {
         tc_fence_after_sync();
-        mma(1, sH1, tmem + 256, true);
-        mma(2, sH1 + 16384, tmem + 256, false);
-        refill(1);
-        mma(3, sH1 + 2 * 16384, tmem + 256, false);
-        refill(2);
-        mma(4, sH1 + 3 * 16384, tmem + 256, false);
-        if (ok) {
-            tc_commit(&s_mma);
-            ++mma_commits;
+        // one chunk queued ahead: chunk c's MMAs are issued before chunk c - 1's stage is
+        // refilled (that wait is for MMAs the tensor pipe is already past)
+        for (int c = 1; c < 5; ++c) {
+            mma(c, sH1 + (c - 1) * 16384, tmem + 256, c == 1);
+            if (c > 1) refill(c - 1);
         }
-        refill(3);
+        commit_mma();
+        refill(4);
     }
     wait_mma(1);
 
-    // ---- output layer: z = relu(C2 + b2) . w3 + b3, p = sigmoid(z)
-    float z = 0.0f;
-    if (!s_fail) {
+    // ---- output layer: z = relu(C2 + b2) . w3 + b3 (each quarter's columns in order,
+    // then the quarters in order), p = sigmoid(z)
+    {
+        float zq = 0.0f;
+        if (!s_fail) {
 #pragma unroll 1
-        for (int c0 = 0; c0 < kH; c0 += 32) {
-            uint32_t raw[32];
-            tmem_ld32(tmem + lane_base + 256 + c0, raw);
-            tmem_ld_wait();
+            for (int c0 = 64 * cq; c0 < 64 * cq + 64; c0 += 32) {
+                float v[32];
+                acc32(256 + c0, v);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const float h = fmaxf(__uint_as_float(raw[j]) + __ldg(g.params + g.off_b2 + c0 + j), 0.0f);
-                z = fmaf(h, __ldg(g.params + g.off_w3 + c0 + j), z);
+                for (int j = 0; j < 32; ++j) zq = fmaf(fmaxf(v[j] + s_b2[c0 + j], 0.0f), s_w3[c0 + j], zq);
+            }
+        }
+        s_zp[cq][rl] = zq;
+    }
+    __syncthreads();
+    if (cq == 0) {
+        const float z = (((s_zp[0][rl] + s_zp[1][rl]) + s_zp[2][rl]) + s_zp[3][rl]) + g.params[g.off_b3];
+        const float p = 1.0f / (1.0f + expf(-z));
+        if (valid) g.p_out[row] = p;
+        if constexpr (kTrain) {
+            const float yy = valid ? g.y[batch_row(g.idx, g.cursor, g.B, row)] : 0.0f;
+            const float dz = valid ? (p - yy) * (1.0f / static_cast<float>(g.B)) : 0.0f;
+            float loss = 0.0f;
+            if (valid) {
+                const float eps = 1e-12f;
+                loss = -(yy * logf(p + eps) + (1.0f - yy) * logf(1.0f - p + eps));
+            }
+            s_dz[rl] = dz;
+            float rs[2] = {dz, loss};
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) rs[k] += __shfl_xor_sync(0xffffffffu, rs[k], o);
+            if (lane == 0) {
+                s_red[lg][0] = rs[0];
+                s_red[lg][1] = rs[1];
             }
         }
     }
-    z += __ldg(g.params + g.off_b3);
-    const float p = 1.0f / (1.0f + expf(-z));
-    if (valid) g.p_out[row] = p;
 
     if constexpr (kTrain) {
-        // ---- first backward step: dz = (p - y) / B; dH2 = dz w3 [h2 > 0] (BF16); column
-        // sums of dz h2 (dw3) and of dH2 (db2) over the tile's rows; loss and db3
-        const float yy = valid ? g.y[batch_row(g.idx, g.cursor, g.B, row)] : 0.0f;
-        const float dz = valid ? (p - yy) * (1.0f / static_cast<float>(g.B)) : 0.0f;
-        float loss = 0.0f;
-        if (valid) {
-            const float eps = 1e-12f;
-            loss = -(yy * logf(p + eps) + (1.0f - yy) * logf(1.0f - p + eps));
-        }
+        __syncthreads();
+        // ---- first backward step: dH2 = dz w3 [h2 > 0] (BF16); column sums of dz h2 (dw3)
+        // and of dH2 (db2) over each lane group's rows
+        const float dz = s_dz[rl];
         if (!s_fail) {
 #pragma unroll 1
-            for (int c0 = 0; c0 < kH; c0 += 32) {
-                uint32_t raw[32];
-                tmem_ld32(tmem + lane_base + 256 + c0, raw);
-                tmem_ld_wait();
-                float d[32], hw[32];
+            for (int c0 = 64 * cq; c0 < 64 * cq + 64; c0 += 32) {
+                float v[32], d[32];
+                acc32(256 + c0, v);
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const float h = fmaxf(__uint_as_float(raw[j]) + __ldg(g.params + g.off_b2 + c0 + j), 0.0f);
-                    d[j] = h > 0.0f ? dz * __ldg(g.params + g.off_w3 + c0 + j) : 0.0f;
-                    hw[j] = dz * h;
+                    const float h = fmaxf(v[j] + s_b2[c0 + j], 0.0f);
+                    d[j] = h > 0.0f ? dz * s_w3[c0 + j] : 0.0f;
+                    v[j] = dz * h;
                 }
-                put_row32(sD2, t, c0, d);
-                uint8_t *chunk = g.dh2t_img + (static_cast<size_t>(tile) * 2 + (t >> 6)) * (kH * 64 * 2);
-                put_cols32(chunk, c0, (t & 63) & ~31, d, stage, lane);
-                cols[(0 * 4 + warp) * kH + c0 + lane] = col_sum32(hw, lane);  // dw3
-                cols[(1 * 4 + warp) * kH + c0 + lane] = col_sum32(d, lane);   // db2
+                put_row32(sD2, rl, c0, d);
+                put_col32(g.dh2t_img + img_chunk * (kH * 64 * 2), c0, mrow, d, lane);
+                cols[(0 * 4 + lg) * kH + c0 + lane] = col_sum32(v, lane);  // dw3
+                cols[(1 * 4 + lg) * kH + c0 + lane] = col_sum32(d, lane);  // db2
             }
-        }
-        float rs[2] = {dz, loss};
-#pragma unroll
-        for (int k = 0; k < 2; ++k)
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) rs[k] += __shfl_xor_sync(0xffffffffu, rs[k], o);
-        if (lane == 0) {
-            s_red[warp][0] = rs[0];
-            s_red[warp][1] = rs[1];
         }
         fence_async_shared();
         tc_fence_before_sync();
         __syncthreads();
-        // per-tile partials of dw3, db2 (warps in order), db3 and the loss
+        // per-tile partials of dw3, db2 (lane groups in order), db3 and the loss
         float *ph = g.part_head + static_cast<int64_t>(tile) * (2 * kH + 2);
-        for (int i = t; i < 2 * kH; i += 128) {
+        for (int i = t; i < 2 * kH; i += kTileThreads) {
             const int which = i / kH, c = i % kH;
             const float *q = cols + which * 4 * kH + c;
             ph[i] = ((q[0] + q[kH]) + q[2 * kH]) + q[3 * kH];
@@ -360,48 +429,37 @@ __global__ void __launch_bounds__(128, 1) k_tile(const TileArgs g)
         // ---- dH1 = dH2 W2^T (columns 0 .. 255 again), W2b in four K-chunks
         if (t == 0 && !s_fail) {
             tc_fence_after_sync();
-            refill(4);
-            mma(5, sD2, tmem, true);
-            mma(6, sD2 + 16384, tmem, false);
-            refill(5);
-            mma(7, sD2 + 2 * 16384, tmem, false);
-            refill(6);
-            mma(8, sD2 + 3 * 16384, tmem, false);
-            if (ok) {
-                tc_commit(&s_mma);
-                ++mma_commits;
+            for (int c = 5; c < kWChunks; ++c) {
+                mma(c, sD2 + (c - 5) * 16384, tmem, c == 5);
+                if (c > 5) refill(c - 1);
             }
+            commit_mma();
         }
         wait_mma(0);
         // epilogue 3: dH1 = C3 [h1 > 0] (BF16 batch-major image) and its column sums (db1)
         if (!s_fail) {
 #pragma unroll 1
-            for (int c0 = 0; c0 < kH; c0 += 32) {
-                uint32_t raw[32];
-                tmem_ld32(tmem + lane_base + c0, raw);
-                tmem_ld_wait();
-                // this row's 32 stored H1 values (the mask), 16 bytes at a time
-                const uint8_t *hb = sH1 + (c0 >> 6) * 16384 + (t >> 3) * 1024 + (t & 7) * 16 + ((c0 & 63) >> 3) * 128;
+            for (int c0 = 64 * cq; c0 < 64 * cq + 64; c0 += 32) {
                 float d[32];
+                acc32(c0, d);
+                // this row's 32 stored H1 values (the mask), 16 bytes at a time
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const uint4 u = *reinterpret_cast<const uint4 *>(hb + q * 128);
+                    const uint4 u = *reinterpret_cast<const uint4 *>(op_unit(sH1, rl, c0 + 8 * q));
                     const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
                     for (int h = 0; h < 8; ++h) {
                         const uint16_t bits = static_cast<uint16_t>((h & 1) ? (w4[h >> 1] >> 16) : (w4[h >> 1] & 0xFFFFu));
-                        const float hv = __bfloat162float(__ushort_as_bfloat16(bits));
-                        d[8 * q + h] = hv > 0.0f ? __uint_as_float(raw[8 * q + h]) : 0.0f;
+                        if (!(__bfloat162float(__ushort_as_bfloat16(bits)) > 0.0f)) d[8 * q + h] = 0.0f;
                     }
                 }
-                uint8_t *chunk = g.dh1t_img + (static_cast<size_t>(tile) * 2 + (t >> 6)) * (kH * 64 * 2);
-                put_cols32(chunk, c0, (t & 63) & ~31, d, stage, lane);
-                cols[warp * kH + c0 + lane] = col_sum32(d, lane);  // db1
+                put_col32(g.dh1t_img + img_chunk * (kH * 64 * 2), c0, mrow, d, lane);
+                cols[lg * kH + c0 + lane] = col_sum32(d, lane);  // db1
             }
         }
         __syncthreads();
         float *pb = g.part_b1 + static_cast<int64_t>(tile) * kH;
-        for (int c = t; c < kH; c += 128) {
+        for (int c = t; c < kH; c += kTileThreads) {
             const float *q = cols + c;
             pb[c] = ((q[0] + q[kH]) + q[2 * kH]) + q[3 * kH];
         }
@@ -411,7 +469,8 @@ __global__ void __launch_bounds__(128, 1) k_tile(const TileArgs g)
     if (t == 0 && !ok) {
         atomicOr(g.status, kStatusTimeout);
         s_fail = 1;
-        for (int c = 0; c < loaded; ++c) mbar_wait_bounded(&s_full[c & 1], (c >> 1) & 1, kDefaultWaitLimit);
+        for (int c = 0; c < loaded; ++c)
+            mbar_wait_bounded(&s_full[c % kWStages], (c / kWStages) & 1, kDefaultWaitLimit);
         tc_commit(&s_mma);  // completes once every MMA this thread issued is done
         mbar_wait_bounded(&s_mma, mma_commits & 1, kDefaultWaitLimit);
     }
@@ -428,8 +487,9 @@ __global__ void __launch_bounds__(128, 1) k_tile(const TileArgs g)
 //   problem 0 (CTA x = 0, 1):  dW2[k][n]  = sum_m H1T[k][m] dH2T[n][m], k-tile x
 //   problem 1 (CTA x = 2, 3):  dW1T[n][k] = sum_m dH1T[n][m] XT[k][m], n-tile x - 2
 // Each CTA copies its A (128 rows x 64, 16 KB) and B (256 or 64 rows x 64) chunk images
-// with bulk copies through a 3-stage ring, one thread issues the MMAs, and the FP32
-// tile of its split goes to part_w2[split] ([256][256]) or part_w1[split] ([256][64]).
+// with bulk copies through a 3-stage ring, one thread issues the MMAs, and 8 warps (a
+// lane group and a column half each) write the FP32 tile of its split to
+// part_w2[split] ([k][n], 256 x 256) or part_w1[split] (dW1 itself, [k][n], 64 x 256).
 struct WgradArgs {
     const uint8_t *h1t_img, *dh2t_img, *dh1t_img, *xt_img;
     int n_mchunks, chunks_per_split;
@@ -439,11 +499,14 @@ struct WgradArgs {
 
 constexpr int kWgStages = 3;
 constexpr uint32_t kWgA = 16384, kWgB = 32768;
-constexpr int kWgradSmem = kWgStages * static_cast<int>(kWgA + kWgB);
+constexpr int kWgradSmem = kWgStages * static_cast<int>(kWgA + kWgB) + 1024;  // + the alignment of the base
 
-__global__ void __launch_bounds__(128, 1) k_wgrad(const WgradArgs g)
+constexpr int kWgradThreads = 256;
+
+__global__ void __launch_bounds__(kWgradThreads, 1) k_wgrad(const WgradArgs g)
 {
-    extern __shared__ __align__(1024) uint8_t smem[];
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);  // swizzle atoms: 1 KB aligned
     __shared__ __align__(8) uint64_t s_full[kWgStages], s_empty[kWgStages];
     __shared__ uint32_t s_tmem;
     __shared__ int s_fail;
@@ -500,8 +563,8 @@ __global__ void __launch_bounds__(128, 1) k_wgrad(const WgradArgs g)
             const uint8_t *sa = smem + s * (kWgA + kWgB);
 #pragma unroll
             for (int ks = 0; ks < 4; ++ks)
-                tc_mma_bf16(tmem, smem_desc_kmajor(sa + ks * 256, 128, 1024),
-                            smem_desc_kmajor(sa + kWgA + ks * 256, 128, 1024), idesc, (i | ks) ? 1u : 0u);
+                tc_mma_bf16(tmem, smem_desc_sw128(sa + ks * 32), smem_desc_sw128(sa + kWgA + ks * 32), idesc,
+                            (i | ks) ? 1u : 0u);
             tc_commit(&s_empty[s]);
             if (issued < nk) {
                 // the stage of chunk i is refilled once its MMAs are done
@@ -528,24 +591,31 @@ __global__ void __launch_bounds__(128, 1) k_wgrad(const WgradArgs g)
     tc_fence_after_sync();
 
     if (!s_fail) {
-        const int r = mt * 128 + 32 * warp + lane;  // output row (k of dW2, n of dW1T)
-        float *out = prob == 0 ? g.part_w2 + static_cast<size_t>(split) * kH * kH + static_cast<size_t>(r) * kH
-                               : g.part_w1 + static_cast<size_t>(split) * kH * kKP + static_cast<size_t>(r) * kKP;
+        const int lg = warp & 3, half = warp >> 2;
+        const int r = mt * 128 + 32 * lg + lane;  // output row (k of dW2, n of dW1T)
 #pragma unroll 1
-        for (int c0 = 0; c0 < N; c0 += 32) {
+        for (int c0 = half * (N / 2); c0 < (half + 1) * (N / 2); c0 += 32) {
             uint32_t raw[32];
             if (nk > 0) {
-                tmem_ld32(tmem + (static_cast<uint32_t>(32 * warp) << 16) + c0, raw);
+                tmem_ld32(tmem + (static_cast<uint32_t>(32 * lg) << 16) + c0, raw);
                 tmem_ld_wait();
             } else {
 #pragma unroll
                 for (int j = 0; j < 32; ++j) raw[j] = 0u;
             }
-            float4 *o = reinterpret_cast<float4 *>(out + c0);
+            if (prob == 0) {
+                float4 *o = reinterpret_cast<float4 *>(g.part_w2 + static_cast<size_t>(split) * kH * kH +
+                                                       static_cast<size_t>(r) * kH + c0);
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-                o[q] = make_float4(__uint_as_float(raw[4 * q]), __uint_as_float(raw[4 * q + 1]),
-                                   __uint_as_float(raw[4 * q + 2]), __uint_as_float(raw[4 * q + 3]));
+                for (int q = 0; q < 8; ++q)
+                    o[q] = make_float4(__uint_as_float(raw[4 * q]), __uint_as_float(raw[4 * q + 1]),
+                                       __uint_as_float(raw[4 * q + 2]), __uint_as_float(raw[4 * q + 3]));
+            } else {
+                // dW1[k][n]: the warp's lanes (consecutive n) write 128 contiguous bytes per k
+                float *o = g.part_w1 + static_cast<size_t>(split) * kKP * kH + r;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) o[static_cast<size_t>(c0 + j) * kH] = __uint_as_float(raw[j]);
+            }
         }
     }
     tc_fence_before_sync();
@@ -580,8 +650,9 @@ __device__ __forceinline__ void put_img(uint8_t *wimg, int chunk, int r, int c, 
         __float2bfloat16_rn(x);
 }
 
-// BF16 copies of one weight into the images: W1[k][n] -> W1t (row n, col k); W2[k][n] ->
-// W2t chunk k / 64 (row n, col k % 64) and W2b chunk n / 64 (row k, col n % 64).
+// BF16 copies of one weight into the images (chunks of 64 K-elements): W1[k][n] -> W1t
+// (row n, col k); W2[k][n] -> W2t chunk 1 + k / 64 (row n, col k % 64) and W2b chunk
+// 5 + n / 64 (row k, col n % 64).
 __device__ __forceinline__ void put_weight(uint8_t *wimg, bool is_w2, int k, int n, float x)
 {
     if (!is_w2) {
@@ -605,10 +676,10 @@ __global__ void k_update(const UpdateArgs g)
     float gr = 0.0f;
     bool is_w = false, is_w2 = false;
     int wk = 0, wn = 0;
-    if (i < g.off_b1) {  // W1[k][n]: partials hold dW1^T [n][k]
+    if (i < g.off_b1) {  // W1[k][n]
         wk = static_cast<int>(i / kH);
         wn = static_cast<int>(i % kH);
-        for (int z = 0; z < g.n_splits; ++z) gr += g.part_w1[static_cast<int64_t>(z) * kH * kKP + wn * kKP + wk];
+        for (int z = 0; z < g.n_splits; ++z) gr += g.part_w1[static_cast<int64_t>(z) * kH * kKP + i];
         is_w = true;
     } else if (i < g.off_W2) {  // b1
         const int c = static_cast<int>(i - g.off_b1);
@@ -665,7 +736,7 @@ __global__ void k_epoch_tail(const float *__restrict__ loss_sum, int B, int64_t 
 }  // namespace
 
 // ---------------------------------------------------------------------------
-size_t mlp_wimg_bytes() { return 9 * static_cast<size_t>(kWChunk); }
+size_t mlp_wimg_bytes() { return kWImage; }
 size_t mlp_xt_bytes(int Bp) { return static_cast<size_t>(Bp / 64) * 64 * 64 * 2; }
 size_t mlp_ht_bytes(int Bp) { return static_cast<size_t>(Bp / 64) * kH * 64 * 2; }
 int mlp_wgrad_splits(int Bp, int *chunks_per_split)
@@ -711,9 +782,9 @@ cudaError_t mlp_launch_tile(const MlpBuffers &b, const float *X, const int64_t *
     g.part_b1 = b.part_b1;
     g.status = b.status;
     if (y)
-        k_tile<true><<<Bp / kBM, 128, kTileSmem, s>>>(g);
+        k_tile<true><<<Bp / kBM, kTileThreads, kTileSmem, s>>>(g);
     else
-        k_tile<false><<<Bp / kBM, 128, kTileSmem, s>>>(g);
+        k_tile<false><<<Bp / kBM, kTileThreads, kTileSmem, s>>>(g);
     return cudaGetLastError();
 }
 
@@ -729,7 +800,7 @@ cudaError_t mlp_launch_wgrad(const MlpBuffers &b, int Bp, cudaStream_t s)
     g.part_w2 = b.part_w2;
     g.part_w1 = b.part_w1;
     g.status = b.status;
-    k_wgrad<<<dim3(4, splits), 128, kWgradSmem, s>>>(g);
+    k_wgrad<<<dim3(4, splits), kWgradThreads, kWgradSmem, s>>>(g);
     return cudaGetLastError();
 }
 

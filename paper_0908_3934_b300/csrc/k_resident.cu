@@ -32,14 +32,17 @@ __global__ void __launch_bounds__(T, 1) k_resident(const StepArgs g, const Resid
     extern __shared__ __align__(16) uint8_t sm[];
     __shared__ StepArgs sa;
     __shared__ int s_nlong;
+    __shared__ unsigned long long s_evc, s_evbase;
+    __shared__ int32_t s_npulses;
     constexpr bool kSpk = (kM & 3) != 0;
+    constexpr int W = T / 32;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int N = L.N, R = L.R;
     const int64_t E = L.E;
     uint32_t *key = reinterpret_cast<uint32_t *>(sm + L.off_key);
     float *w = reinterpret_cast<float *>(sm + L.off_w);
     int32_t *rp = reinterpret_cast<int32_t *>(sm + L.off_rp);
-    float *S = reinterpret_cast<float *>(sm + L.off_S);
+    float *S = reinterpret_cast<float *>(sm + L.off_S);  // [2][N]: step n writes half n & 1
     int32_t *lng = reinterpret_cast<int32_t *>(sm + L.off_long);
     float *ring_f = reinterpret_cast<float *>(sm + L.off_ring);      // FitzHugh-Nagumo: [R][stride]
     uint32_t *bits = reinterpret_cast<uint32_t *>(sm + L.off_ring);  // spiking: [R][words]
@@ -49,6 +52,16 @@ __global__ void __launch_bounds__(T, 1) k_resident(const StepArgs g, const Resid
     float4 *hh = reinterpret_cast<float4 *>(sm + L.off_hh);
     int32_t *bgc = reinterpret_cast<int32_t *>(sm + L.off_bgc);
     float *acc = reinterpret_cast<float *>(sm + L.off_acc);
+    int32_t *perm = reinterpret_cast<int32_t *>(sm + L.off_perm);
+    int64_t *first = reinterpret_cast<int64_t *>(sm + L.off_first);
+    int32_t *ev_node = reinterpret_cast<int32_t *>(sm + L.off_evn);
+    int64_t *ev_step = reinterpret_cast<int64_t *>(sm + L.off_evs);
+    int32_t *p_node = reinterpret_cast<int32_t *>(sm + L.off_pnode);
+    int64_t *p_on = reinterpret_cast<int64_t *>(sm + L.off_pon);
+    int64_t *p_off = reinterpret_cast<int64_t *>(sm + L.off_poff);
+    float *p_amp = reinterpret_cast<float *>(sm + L.off_pamp);
+    const int n_pulses = *g.n_pulses;
+    const bool local_pulses = n_pulses <= L.pulse_cap;
 
     if (t == 0) {
         sa = g;
@@ -57,12 +70,27 @@ __global__ void __launch_bounds__(T, 1) k_resident(const StepArgs g, const Resid
         sa.wc = wc;
         sa.bgc = bgc;  // background counters always have a place (a background may be set later)
         sa.obs_acc = g.frame_avg ? acc : nullptr;
+        sa.first = first;
+        // events gather in shared memory and go to the network's buffer in batches
+        sa.ev_node = ev_node;
+        sa.ev_step = ev_step;
+        sa.ev_count = &s_evc;
+        sa.ev_cap = L.ev_cap;
+        if (local_pulses) {
+            sa.n_pulses = &s_npulses;
+            sa.p_node = p_node;
+            sa.p_on = p_on;
+            sa.p_off = p_off;
+            sa.p_amp = p_amp;
+            s_npulses = n_pulses;
+        }
         if constexpr (kSpk) {
             sa.iz_v = iz_v;
             sa.rp = rpq;
             sa.hh_g = (kM & 3) == 2 ? hh : nullptr;
         }
         s_nlong = 0;
+        s_evc = 0;
     }
     // everything into shared memory
     const uint32_t *gkey = static_cast<const uint32_t *>(g.ekey);
@@ -94,7 +122,16 @@ __global__ void __launch_bounds__(T, 1) k_resident(const StepArgs g, const Resid
         }
         bgc[j] = g.bgc[j];
         if (g.frame_avg) acc[j] = g.obs_acc[j];
+        perm[j] = __ldg(g.perm + j);
+        first[j] = g.first[j];
     }
+    if (local_pulses)
+        for (int i = t; i < n_pulses; i += T) {
+            p_node[i] = g.p_node[i];
+            p_on[i] = g.p_on[i];
+            p_off[i] = g.p_off[i];
+            p_amp[i] = g.p_amp[i];
+        }
     __syncthreads();
     for (int r = t; r < N; r += T)
         if (rp[r + 1] - rp[r] > kWarpRow) lng[atomicAdd(&s_nlong, 1)] = r;
@@ -102,57 +139,117 @@ __global__ void __launch_bounds__(T, 1) k_resident(const StepArgs g, const Resid
     const int n_long = s_nlong;
     const int dbits = g.dbits;
     const uint32_t dmask = (1u << dbits) - 1u;
-    const int64_t rmask = g.ring_mask;
+    const uint32_t rmask = static_cast<uint32_t>(g.ring_mask);
     const int64_t n0 = *g.d_step;
+    // each thread's own copy of the step arguments: the node update reads its fields from
+    // registers instead of shared memory
+    const StepArgs la = sa;
+
+    // the buffered events to the network's event list (every thread; after a barrier)
+    auto flush = [&]() {
+        if (t == 0) {
+            s_evbase = atomicAdd(g.ev_count, s_evc);
+        }
+        __syncthreads();
+        const unsigned long long cnt = s_evc, base = s_evbase;
+        for (unsigned long long i = t; i < cnt; i += T)
+            if (base + i < static_cast<unsigned long long>(g.ev_cap)) {
+                g.ev_node[base + i] = ev_node[i];
+                g.ev_step[base + i] = ev_step[i];
+            }
+        __syncthreads();
+        if (t == 0) s_evc = 0;
+        __syncthreads();
+    };
 
     for (int s = 0; s < n_steps; ++s) {
         const int64_t n = n0 + s;
+        const uint32_t n32 = static_cast<uint32_t>(n);
+        float *Sn = S + (s & 1) * N;
         // the delayed input value of a packed edge key
         auto val = [&](uint32_t k) -> float {
             const uint32_t src = k >> dbits;
-            const int slot = static_cast<int>((n - static_cast<int64_t>(k & dmask)) & rmask);
+            const uint32_t slot = (n32 - (k & dmask)) & rmask;
             if constexpr (kSpk)
                 return ((bits[slot * L.words + (src >> 5)] >> (src & 31u)) & 1u) ? 1.0f : 0.0f;
             else
                 return ring_f[slot * L.stride + src];
         };
-        // 1. input sums
+        // 1. input sums (reads ring slots n - D <= n - 1, written a step or more ago)
         for (int r = t; r < N; r += T) {
             const int a0 = rp[r], a1 = rp[r + 1];
             if (a1 - a0 <= kWarpRow) {
                 float sum = 0.0f;
-#pragma unroll 4
-                for (int e = a0; e < a1; ++e) sum = __fadd_rn(sum, __fmul_rn(w[e], val(key[e])));
-                S[r] = sum;
+                int e = a0;
+                for (; e + 8 <= a1; e += 8) {  // loads of 8 terms in flight, added in row order
+                    uint32_t k8[8];
+                    float w8[8], x8[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        k8[j] = key[e + j];
+                        w8[j] = w[e + j];
+                    }
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) x8[j] = val(k8[j]);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) sum = __fadd_rn(sum, __fmul_rn(w8[j], x8[j]));
+                }
+                for (; e < a1; ++e) sum = __fadd_rn(sum, __fmul_rn(w[e], val(key[e])));
+                Sn[r] = sum;
             }
         }
-        for (int i = warp; i < n_long; i += T / 32) {
-            const int r = lng[i], a0 = rp[r], a1 = rp[r + 1];
-            float p = 0.0f;
-            for (int e = a0 + lane; e < a1; e += 32) p = __fadd_rn(p, __fmul_rn(w[e], val(key[e])));
-            p = warp_sum(p);
-            if (lane == 0) S[r] = p;
+        // long rows: four rows per warp at a time, each lane's partial in row order
+        for (int i = warp; i < n_long; i += 4 * W) {
+            int a0[4], a1[4];
+            float p[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int ii = i + q * W;
+                const int r = ii < n_long ? lng[ii] : 0;
+                a0[q] = ii < n_long ? rp[r] : 0;
+                a1[q] = ii < n_long ? rp[r + 1] : 0;
+                p[q] = 0.0f;
+            }
+            const int len = max(max(a1[0] - a0[0], a1[1] - a0[1]), max(a1[2] - a0[2], a1[3] - a0[3]));
+            for (int o = lane; o < len; o += 32) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (a0[q] + o < a1[q]) p[q] = __fadd_rn(p[q], __fmul_rn(w[a0[q] + o], val(key[a0[q] + o])));
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float x = warp_sum(p[q]);
+                const int ii = i + q * W;
+                if (lane == 0 && ii < n_long) Sn[lng[ii]] = x;
+            }
         }
-        __syncthreads();
-        // 2. node updates (spiking: spd(V(n + 1)) of 32 consecutive nodes per ring word)
+        // barrier; flush the buffered events if this step could overflow the buffer (at
+        // most one event per node and step).  Each thread reads the count after its own
+        // updates of the previous step; the last of them sees every event of that step
+        // (the others wait at this barrier), so the largest reading is the exact count and
+        // every thread takes the same decision.
+        const unsigned long long seen = *static_cast<volatile unsigned long long *>(&s_evc);
+        if (__syncthreads_or(seen > static_cast<unsigned long long>(L.ev_cap - N))) flush();
+        // 2. node updates: node r by thread r % T (its own state, its own ring entries);
+        // slot n + 1 is read by no gather of step n + 1 (every delay is at least one step)
         for (int base = 0; base < N; base += T) {
             const int r = base + t;
             if constexpr (kSpk) {
                 bool spike = false;
                 if (r < N) {
-                    node_update<kM | kNoRing>(sa, r, n, 0.0f, wc[r], S[r]);
-                    const float vpeak = (kM & 3) == 1 ? izh_par(sa, r).vpeak : hh_par(sa, r).vpeak;
+                    node_update<kM | kNoRing>(la, r, n, 0.0f, wc[r], Sn[r], perm[r]);
+                    const float vpeak = (kM & 3) == 1 ? izh_par(la, r).vpeak : hh_par(la, r).vpeak;
                     spike = iz_v[r] >= vpeak;
                 }
                 const uint32_t b = __ballot_sync(0xffffffffu, spike);
-                if (lane == 0 && base + 32 * warp < N)
-                    bits[static_cast<int>((n + 1) & rmask) * L.words + (base + 32 * warp) / 32] = b;
+                if (lane == 0 && base + 32 * warp < N) bits[((n32 + 1u) & rmask) * L.words + (base + 32 * warp) / 32] = b;
             } else {
-                if (r < N) node_update<kM>(sa, r, n, ring_f[static_cast<int>(n & rmask) * L.stride + r], wc[r], S[r]);
+                if (r < N) node_update<kM>(la, r, n, ring_f[(n32 & rmask) * L.stride + r], wc[r], Sn[r], perm[r]);
             }
         }
-        __syncthreads();
     }
+    __syncthreads();
+    flush();
 
     // write the ring and the state back
     if constexpr (kSpk) {
@@ -176,6 +273,7 @@ __global__ void __launch_bounds__(T, 1) k_resident(const StepArgs g, const Resid
         }
         g.bgc[j] = bgc[j];
         if (g.frame_avg) g.obs_acc[j] = acc[j];
+        g.first[j] = first[j];
     }
 }
 
@@ -207,7 +305,7 @@ cudaError_t prepare_res(size_t bytes, size_t *max_bytes)
 
 const int kResidentThreads[kNumResidentShapes] = {256, 512, 1024};
 
-ResidentLayout resident_layout(int N, int64_t E, int R, int model, bool frame_avg)
+ResidentLayout resident_layout(int N, int64_t E, int R, int model, bool frame_avg, int ev_factor)
 {
     ResidentLayout L{};
     L.N = N;
@@ -215,6 +313,8 @@ ResidentLayout resident_layout(int N, int64_t E, int R, int model, bool frame_av
     L.R = R;
     L.words = (N + 31) / 32;
     L.stride = N;
+    L.ev_cap = ev_factor * N;
+    L.pulse_cap = kResidentPulses;
     const bool spk = model != 0;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -222,18 +322,27 @@ ResidentLayout resident_layout(int N, int64_t E, int R, int model, bool frame_av
         off = (off + bytes + 15) & ~static_cast<size_t>(15);
         return static_cast<uint32_t>(at);
     };
+    const size_t n = static_cast<size_t>(N);
     L.off_key = take(4 * static_cast<size_t>(E));
     L.off_w = take(4 * static_cast<size_t>(E));
-    L.off_rp = take(4 * static_cast<size_t>(N + 1));
-    L.off_S = take(4 * static_cast<size_t>(N));
-    L.off_long = take(4 * static_cast<size_t>(N));
-    L.off_ring = take(spk ? 4 * static_cast<size_t>(R) * L.words : 4 * static_cast<size_t>(R) * N);
-    L.off_wc = take(8 * static_cast<size_t>(N));
-    L.off_v = take(spk ? 4 * static_cast<size_t>(N) : 0);
-    L.off_rpq = take(spk ? 8 * static_cast<size_t>(N) : 0);
-    L.off_hh = take(model == 2 ? 16 * static_cast<size_t>(N) : 0);
-    L.off_bgc = take(4 * static_cast<size_t>(N));
-    L.off_acc = take(frame_avg ? 4 * static_cast<size_t>(N) : 0);
+    L.off_rp = take(4 * (n + 1));
+    L.off_S = take(8 * n);
+    L.off_long = take(4 * n);
+    L.off_ring = take(spk ? 4 * static_cast<size_t>(R) * L.words : 4 * static_cast<size_t>(R) * n);
+    L.off_wc = take(8 * n);
+    L.off_v = take(spk ? 4 * n : 0);
+    L.off_rpq = take(spk ? 8 * n : 0);
+    L.off_hh = take(model == 2 ? 16 * n : 0);
+    L.off_bgc = take(4 * n);
+    L.off_acc = take(frame_avg ? 4 * n : 0);
+    L.off_perm = take(4 * n);
+    L.off_first = take(8 * n);
+    L.off_evn = take(4 * static_cast<size_t>(L.ev_cap));
+    L.off_evs = take(8 * static_cast<size_t>(L.ev_cap));
+    L.off_pnode = take(4 * static_cast<size_t>(L.pulse_cap));
+    L.off_pon = take(8 * static_cast<size_t>(L.pulse_cap));
+    L.off_poff = take(8 * static_cast<size_t>(L.pulse_cap));
+    L.off_pamp = take(4 * static_cast<size_t>(L.pulse_cap));
     L.bytes = off;
     return L;
 }

@@ -271,12 +271,17 @@ bool set_resident(gn_net *net, int shape)
     int longest = 0;
     for (int32_t j = 0; j < net->N; ++j) longest = std::max(longest, net->h_row_ptr[j + 1] - net->h_row_ptr[j]);
     if (longest > gn::kResidentMaxRow) return false;
-    const gn::ResidentLayout L = gn::resident_layout(net->N, net->E, net->R, net->model, net->args.frame_avg != 0);
-    size_t max_bytes = 0;
-    cuda_check(gn::resident_prepare(net->model, shape, L.bytes, &max_bytes), "resident kernel setup");
-    if (L.bytes > max_bytes) return false;
-    net->res = L;
-    return true;
+    for (int ev_factor : {2, 1}) {  // a buffer of two events per node where it fits
+        const gn::ResidentLayout L =
+            gn::resident_layout(net->N, net->E, net->R, net->model, net->args.frame_avg != 0, ev_factor);
+        size_t max_bytes = 0;
+        cuda_check(gn::resident_prepare(net->model, shape, L.bytes, &max_bytes), "resident kernel setup");
+        if (L.bytes <= max_bytes) {
+            net->res = L;
+            return true;
+        }
+    }
+    return false;
 }
 
 void configure(gn_net *net, int kind, int shape)

@@ -155,6 +155,18 @@ __device__ __forceinline__ uint64_t smem_desc_kmajor(const void *p, uint32_t lbo
            (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);  // descriptor version 1, no swizzle
 }
 
+// Shared-memory matrix descriptor, K-major operand with the 128-byte swizzle: rows of
+// 64 BF16 K-elements (128 bytes) stored consecutively, the 16-byte unit j of row r at
+// position j ^ (r % 8); 8-row groups 1024 bytes apart (SBO), the operand 1024-byte
+// aligned.  Steps along K within a row advance the start address by 32 bytes per 16
+// elements.
+__device__ __forceinline__ uint64_t smem_desc_sw128(const void *p)
+{
+    const uint64_t addr = smem_u32(p);
+    return ((addr & 0x3FFFFull) >> 4) | (1ull << 16) | (static_cast<uint64_t>(1024 >> 4) << 32) | (1ull << 46) |
+           (2ull << 61);  // descriptor version 1, swizzle mode 2 (128-byte)
+}
+
 // Instruction descriptor of kind::f16 with BF16 A and B (both K-major) and an FP32
 // accumulator, M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
