@@ -501,68 +501,150 @@ def run_test_set(args, local, stream, model: str = "izh"):
             "details_networks": [{"name": r[0], "N": r[1], "E": r[2], "rtf": round(r[3], 1)} for r in rows]}
 
 
-def run_estimator(args, local, stream):
-    """Connectivity estimation with config-5 laws: networks of N = 512 (2D, kept
-    in-degree ~20, 1-8 pulsed nodes, 500 ms observed at 1 ms); the MLP is trained on
-    `est_train` networks (seeds 10^6 + i) and both estimators are scored on
-    `est_test` held-out ones (seeds 2 10^6 + i).  Thresholds for F1 are chosen on
-    the training networks.  Throughput: candidate pairs scored per second by
-    features + inference on resident traces."""
+def _host_pool():
+    """A process pool for the host-side input generation (networks and their candidate
+    tables), started with spawn so no worker inherits the parent's CUDA state."""
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1)))
+
+
+def _estimator_set(specs, chunk: int, local, stream, pool):
+    """Features [P, 33], plain scores [P] (device), labels [P] (host) and pairs per
+    network of the candidate pairs of `specs`, simulated `chunk` networks at a time
+    (one batched run each); rows are grouped by network in order."""
+    import torch
+    from paper_0908_3934_b300 import pipeline
+    feats, score, label, per_net = [], [], [], []
+    for c0 in range(0, len(specs), chunk):
+        part = specs[c0:c0 + chunk]
+        cands = pool.map(netgen.candidates, part, chunksize=32)
+        r = pipeline.simulate_features(part, n_samples=500, device=local, stream=stream.cuda_stream, cands=cands)
+        feats.append(r["features"])
+        score.append(r["score"])
+        label.append(r["label"])
+        per_net.append(np.bincount(r["net"], minlength=len(part)))
+        del r
+    cat = (lambda xs: xs[0]) if len(feats) == 1 else torch.cat
+    return cat(feats), cat(score), np.concatenate(label), np.concatenate(per_net)
+
+
+def _train_score(args, tr, te, n_rows, local, stream, seed, timed=False):
+    """Train a fresh MLP on the first n_rows training pairs for args.est_epochs epochs
+    (visiting orders drawn on the device before the timed region) and score both
+    estimators on the held-out pairs (F1 thresholds chosen on the training pairs)."""
     import torch
     from paper_0908_3934_b300 import geonet, pipeline
-    t0 = time.perf_counter()
-    tr_specs = [netgen.batch_member(10**6 + i, n=512) for i in range(args.est_train)]
-    te_specs = [netgen.batch_member(2 * 10**6 + i, n=512) for i in range(args.est_test)]
-    t_gen = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    tr = pipeline.simulate_features(tr_specs, n_samples=500, device=local, stream=stream.cuda_stream)
-    torch.cuda.synchronize()
-    t_sim_train = time.perf_counter() - t0
+    Xtr, Str, Ltr = tr[0][:n_rows], tr[1][:n_rows], tr[2][:n_rows]
+    dev = Xtr.device
     mlp = geonet.Mlp(netgen.mlp_init(2024), max_batch=8192, device=local, stream=stream.cuda_stream)
-    # the epochs' visiting orders are drawn (host) and copied up before the timed training
-    P_rows = tr["features"].shape[0]
-    orders = [torch.from_numpy(o).to(tr["features"].device) for o in netgen.shuffles(2025, P_rows, args.est_epochs)]
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    orders = [torch.randperm(n_rows, generator=gen, device=dev) for _ in range(args.est_epochs)]
+    yl = torch.from_numpy(Ltr.astype(np.float32)).to(dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    losses = pipeline.train(mlp, tr["features"], tr["label"], epochs=args.est_epochs, batch=8192, seed=2025,
-                            orders=orders)
+    losses = pipeline.train(mlp, Xtr, yl, epochs=args.est_epochs, batch=8192, seed=seed, orders=orders)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    P_tr = tr["features"].shape[0]
-    p_tr = torch.empty(P_tr, device=tr["features"].device)
-    mlp.gn_mlp_infer(tr["features"], p_tr)
+    del orders
+    # F1 thresholds on the first training pairs (the first few hundred training nets)
+    n_thr = min(n_rows, args.est_thr_rows)
+    p_tr = torch.empty(n_thr, device=dev)
+    mlp.gn_mlp_infer(Xtr[:n_thr], p_tr)
     mlp.gn_mlp_synchronize()
-    thr_learned, _ = geonet.gn_score_best_f1(p_tr.cpu().numpy(), tr["label"])
-    thr_plain, _ = geonet.gn_score_best_f1(tr["score"].cpu().numpy(), tr["label"])
-    te = pipeline.simulate_features(te_specs, n_samples=500, device=local, stream=stream.cuda_stream)
-    # throughput of scoring: features + inference from resident traces
-    tab = pipeline.candidate_table(te_specs)
-    dev = te["features"].device
-    pos, srcd = torch.from_numpy(tab["pos"]).to(dev), torch.from_numpy(tab["src"]).to(dev)
-    dstd, rad = torch.from_numpy(tab["dst"]).to(dev), torch.from_numpy(tab["radius"]).to(dev)
-    P = srcd.shape[0]
-    feats = torch.empty((P, 33), dtype=torch.float32, device=dev)
-    sc = torch.empty(P, dtype=torch.float32, device=dev)
-    p_te = torch.empty(P, device=dev)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
+    thr_learned, _ = geonet.gn_score_best_f1(p_tr.cpu().numpy(), Ltr[:n_thr])
+    thr_plain, _ = geonet.gn_score_best_f1(Str[:n_thr].cpu().numpy(), Ltr[:n_thr])
+    p_te = torch.empty(te[0].shape[0], device=dev)
+    mlp.gn_mlp_infer(te[0], p_te)
+    mlp.gn_mlp_synchronize()
+    learned = pipeline.scores(p_te, te[2], thr_learned)
+    plain = pipeline.scores(te[1], te[2], thr_plain)
+    out = {"auroc_learned": learned["auroc"], "auroc_plain": plain["auroc"], "f1_learned": learned["f1"],
+           "f1_plain": plain["f1"], "details_loss_first_last": [losses[0], losses[-1]], "details_pairs": n_rows}
+    if timed:
+        out["train_samples_per_s"] = n_rows * args.est_epochs / t_train
+    return out, mlp
+
+
+def run_estimator(args, local, stream):
+    """Connectivity estimation.  Workload: networks of N = 512 with config-5 laws (2D,
+    kept in-degree ~20, 1-8 pulsed nodes, 500 ms observed at 1 ms), `est_train`
+    training nets (seeds 10^6 + i) and `est_test` held-out ones (seeds 2 10^6 + i);
+    the MLP is trained on the first 500, 2000 and all training nets (the learning
+    curve) and both estimators are scored on the held-out nets.  Positive control:
+    sparse, independently driven nets (netgen.estimator_control; `est_ctl_train` /
+    `est_ctl_test` nets, seeds 3 10^6 + i and 4 10^6 + i), where lagged correlation
+    does reveal edges.  Throughput: candidate pairs scored per second by features +
+    inference from resident traces, and training samples per second."""
+    import functools
+    import torch
+    from paper_0908_3934_b300 import geonet, pipeline
+    pool = _host_pool()
+    member = functools.partial(netgen.batch_member, n=512)
+    t0 = time.perf_counter()
+    tr_specs = pool.map(member, [10**6 + i for i in range(args.est_train)], chunksize=64)
+    te_specs = pool.map(member, [2 * 10**6 + i for i in range(args.est_test)], chunksize=64)
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    tr = _estimator_set(tr_specs, args.est_chunk, local, stream, pool)
+    te = _estimator_set(te_specs, args.est_chunk, local, stream, pool)
     torch.cuda.synchronize()
-    ev0.record(stream)
-    geonet.gn_xcorr_features(te["traces"], pos, srcd, dstd, rad, feats, sc, stream=stream.cuda_stream)
-    mlp.gn_mlp_infer(feats, p_te)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    t_score = ev0.elapsed_time(ev1) / 1e3
-    learned = pipeline.scores(p_te, te["label"], thr_learned)
-    plain = pipeline.scores(sc, te["label"], thr_plain)
-    return {"details_workload": f"{args.est_train} training + {args.est_test} held-out nets of N=512 (config-5 laws), "
-                        f"{P_tr} + {P} candidate pairs, {args.est_epochs} epochs of batch 8192",
-            "auroc_learned": learned["auroc"], "auroc_plain": plain["auroc"],
-            "f1_learned": learned["f1"], "f1_plain": plain["f1"],
-            "pairs_scored_per_s": P / t_score, "details_unit": "candidate pairs/s (features + inference)",
-            "train_samples_per_s": P_tr * args.est_epochs / t_train, "details_loss_first_last": [losses[0], losses[-1]],
-            "details_seconds": {"generate_host": t_gen, "simulate_and_features_train": t_sim_train, "train": t_train,
-                        "score": t_score}}
+    t_sim = time.perf_counter() - t0
+    # rows of the first n training nets (rows are grouped by network in order)
+    counts = np.concatenate([[0], np.cumsum(tr[3])])
+    curve = {}
+    full = None
+    for n_nets in sorted({min(n, args.est_train) for n in (500, 2000, args.est_train)}):
+        res, mlp = _train_score(args, tr, te, int(counts[n_nets]), local, stream, seed=2025,
+                                timed=n_nets == args.est_train)
+        curve[str(n_nets)] = {k: res[k] for k in ("auroc_learned", "auroc_plain", "f1_learned", "f1_plain")}
+        if n_nets == args.est_train:
+            full = res
+            # throughput of scoring: features + inference from resident traces
+            tab = pipeline.candidate_table(te_specs[: min(len(te_specs), args.est_chunk)])
+            sim = pipeline.simulate_features(te_specs[: min(len(te_specs), args.est_chunk)], n_samples=500,
+                                             device=local, stream=stream.cuda_stream)
+            dev = sim["features"].device
+            pos, srcd = torch.from_numpy(tab["pos"]).to(dev), torch.from_numpy(tab["src"]).to(dev)
+            dstd, rad = torch.from_numpy(tab["dst"]).to(dev), torch.from_numpy(tab["radius"]).to(dev)
+            P = srcd.shape[0]
+            feats = torch.empty((P, 33), dtype=torch.float32, device=dev)
+            sc = torch.empty(P, dtype=torch.float32, device=dev)
+            p_te = torch.empty(P, device=dev)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            geonet.gn_xcorr_features(sim["traces"], pos, srcd, dstd, rad, feats, sc, stream=stream.cuda_stream)
+            mlp.gn_mlp_infer(feats, p_te)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            t_score = ev0.elapsed_time(ev1) / 1e3
+            full["pairs_scored_per_s"] = P / t_score
+            del sim, feats, sc, p_te
+        mlp.gn_mlp_destroy()
+    del tr, te
+    # positive control
+    ctl_tr = pool.map(netgen.estimator_control, [3 * 10**6 + i for i in range(args.est_ctl_train)], chunksize=64)
+    ctl_te = pool.map(netgen.estimator_control, [4 * 10**6 + i for i in range(args.est_ctl_test)], chunksize=64)
+    ctr = _estimator_set(ctl_tr, args.est_chunk, local, stream, pool)
+    cte = _estimator_set(ctl_te, args.est_chunk, local, stream, pool)
+    pool.close()
+    pool.join()
+    ctl, mlp = _train_score(args, ctr, cte, ctr[0].shape[0], local, stream, seed=2026)
+    mlp.gn_mlp_destroy()
+    out = {"details_workload": f"{args.est_train} training + {args.est_test} held-out nets of N=512 (config-5 laws), "
+                               f"{int(counts[-1])} training candidate pairs, {args.est_epochs} epochs of batch 8192; "
+                               f"control: {args.est_ctl_train} + {args.est_ctl_test} sparse nets driven by 5 Hz "
+                               f"background pulses",
+           "auroc_learned": full["auroc_learned"], "auroc_plain": full["auroc_plain"],
+           "f1_learned": full["f1_learned"], "f1_plain": full["f1_plain"],
+           "pairs_scored_per_s": full["pairs_scored_per_s"], "details_unit": "candidate pairs/s (features + inference)",
+           "train_samples_per_s": full["train_samples_per_s"],
+           "curve_auroc": {k: [v["auroc_plain"], v["auroc_learned"]] for k, v in curve.items()},
+           "control_auroc": [ctl["auroc_plain"], ctl["auroc_learned"]],
+           "details_curve": curve, "details_control": ctl,
+           "details_seconds": {"generate_host": t_gen, "simulate_and_features": t_sim}}
+    return out
 
 
 def strip_details(x):
@@ -593,9 +675,13 @@ def main():
                     help="other sizes of the plain path timed after the headline one (name:steps,...)")
     ap.add_argument("--no-sizes", action="store_true")
     ap.add_argument("--details", default=None, help="write the full result (every row, full precision) here")
-    ap.add_argument("--est-train", type=int, default=2000, help="training nets of the estimator measurement")
-    ap.add_argument("--est-test", type=int, default=200, help="held-out nets of the estimator measurement")
-    ap.add_argument("--est-epochs", type=int, default=8)
+    ap.add_argument("--est-train", type=int, default=20000, help="training nets of the estimator measurement")
+    ap.add_argument("--est-test", type=int, default=1000, help="held-out nets of the estimator measurement")
+    ap.add_argument("--est-epochs", type=int, default=4)
+    ap.add_argument("--est-chunk", type=int, default=4096, help="networks simulated per batched run")
+    ap.add_argument("--est-thr-rows", type=int, default=4_000_000, help="training pairs the F1 thresholds are chosen on")
+    ap.add_argument("--est-ctl-train", type=int, default=2000, help="training nets of the positive control")
+    ap.add_argument("--est-ctl-test", type=int, default=200, help="held-out nets of the positive control")
     ap.add_argument("--no-estimator", action="store_true")
     ap.add_argument("--no-izh", action="store_true", help="skip the Izhikevich-model measurement")
     ap.add_argument("--izh-steps", type=int, default=2000)

@@ -179,8 +179,11 @@ def _pairs_within(pos, r):
 
 
 def _sort_by_dst(src, dst, *extra):
-    """Edges in (dst, src) order: a deterministic caller order."""
-    order = np.lexsort((src, dst))
+    """Edges in (dst, src) order (ties, i.e. repeated pairs, kept in their order): a
+    deterministic caller order."""
+    key = np.asarray(dst, np.int64) * (int(max(np.max(src, initial=0), np.max(dst, initial=0))) + 1) + \
+        np.asarray(src, np.int64)
+    order = np.argsort(key, kind="stable")
     return (src[order], dst[order]) + tuple(x[order] for x in extra)
 
 
@@ -384,9 +387,13 @@ def candidates(spec: NetSpec):
     src, dst = _pairs_within(spec.pos, spec.radius)
     src, dst = _sort_by_dst(src, dst)
     N = np.int64(spec.n_nodes)
-    edge_key = spec.src.astype(np.int64) * N + spec.dst.astype(np.int64)
-    key = src.astype(np.int64) * N + dst.astype(np.int64)
-    label = np.isin(key, edge_key).astype(np.uint8)
+    # (dst, src) keys: the candidates are in this order; the edges are sorted for the lookup
+    edge_key = np.sort(np.asarray(spec.dst, np.int64) * N + np.asarray(spec.src, np.int64))
+    key = dst.astype(np.int64) * N + src.astype(np.int64)
+    if edge_key.size == 0:
+        return src, dst, np.zeros(key.shape[0], np.uint8)
+    at = np.minimum(np.searchsorted(edge_key, key), edge_key.size - 1)
+    label = (edge_key[at] == key).astype(np.uint8)
     return src, dst, label
 
 

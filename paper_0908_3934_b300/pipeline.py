@@ -13,14 +13,15 @@ import numpy as np
 from . import geonet, netgen
 
 
-def candidate_table(specs):
+def candidate_table(specs, cands=None):
     """Candidate pairs of several networks with global node ids (networks
     concatenated in order), their labels, the candidate radius of each pair, the
-    network index of each pair and the concatenated positions."""
+    network index of each pair and the concatenated positions.  `cands`: the
+    networks' netgen.candidates results if already computed."""
     src, dst, lab, rad, net = [], [], [], [], []
     off = 0
     for i, sp in enumerate(specs):
-        s, d, lb = netgen.candidates(sp)
+        s, d, lb = netgen.candidates(sp) if cands is None else cands[i]
         src.append(s.astype(np.int64) + off)
         dst.append(d.astype(np.int64) + off)
         lab.append(lb)
@@ -32,16 +33,17 @@ def candidate_table(specs):
                 pos=np.ascontiguousarray(np.concatenate([sp.pos for sp in specs]), np.float64), n_nodes=off)
 
 
-def simulate_features(specs, n_samples: int = 500, device: int = 0, stream=None):
+def simulate_features(specs, n_samples: int = 500, device: int = 0, stream=None, cands=None):
     """Simulate `specs` for n_samples observation intervals from rest (one batched
     run) and return the features [P, 33] and plain scores [P] of their candidate
-    pairs (CUDA tensors) with the labels and network index of each pair (numpy)."""
+    pairs (CUDA tensors) with the labels and network index of each pair (numpy).
+    `cands`: the networks' netgen.candidates results if already computed."""
     import torch
     dev = torch.device("cuda", device)
     every = specs[0].obs["sample_every"]
     batch = geonet.Batch(specs, device=device, stream=stream, obs_capacity=n_samples)
     batch.gn_batch_step(n_samples * every)
-    tab = candidate_table(specs)
+    tab = candidate_table(specs, cands)
     traces = torch.empty((tab["n_nodes"], n_samples), dtype=torch.float32, device=dev)
     geonet.gn_batch_export_traces(batch, 0, n_samples, traces)
     batch.gn_batch_destroy()
