@@ -523,6 +523,23 @@ def test_roofline_full_size_sampled():
     assert_windows(worst)
 
 
+@pytest.mark.parametrize("size", ["hubs5", "slow"])
+def test_secondary_roofline_sizes_full_size_window(size):
+    """The 1M-node net's two secondary sizes in the launch configuration bench.py
+    times: the literal 5 % hubs of in-degree 1000 beside non-hubs of mean in-degree 50
+    (~97.5M edges), and every conduction speed x 0.1 (delays to ~410 steps, a 512-slot
+    ring).  Delays bit-exact; one 20-step window after 40 steps, compared on every node."""
+    spec = (netgen.roofline(hub_frac=0.05, mean_deg=97.5) if size == "hubs5"
+            else netgen.delay_stress(netgen.roofline()))
+    net = Net(spec)
+    assert np.array_equal(net.gn_get_delays(), oracle.net_delays(spec))
+    info = net.gn_net_get_info()
+    if size == "slow":
+        assert info["ring_depth"] == 512 and info["max_delay"] > 300
+    worst, _ = windowed(spec, net, 20, start=40)
+    assert_windows(worst)
+
+
 @pytest.mark.parametrize("model", ["izh", "hh", "izh_stdp"])
 def test_roofline_full_size_spiking_sampled(model):
     """The benchmark's 1M-node network with each spiking node model (Izhikevich at
