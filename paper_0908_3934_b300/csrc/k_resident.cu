@@ -144,6 +144,12 @@ __global__ void __launch_bounds__(T, 1) k_resident(const StepArgs g, const Resid
     // each thread's own copy of the step arguments: the node update reads its fields from
     // registers instead of shared memory
     const StepArgs la = sa;
+    // the observation bookkeeping as counters: step n samples when (n + 1) % sample_every
+    // == 0, its sample number is (n + 1) / sample_every - 1 and its row that modulo obs_cap
+    const int se = la.sample_every;
+    int ph = static_cast<int>((n0 + 1) % se);
+    int64_t kk = (n0 + 1) / se;
+    int64_t cidx = kk >= 1 ? (kk - 1) % la.obs_cap : la.obs_cap - 1;
 
     // the buffered events to the network's event list (every thread; after a barrier)
     auto flush = [&]() {
@@ -165,6 +171,10 @@ __global__ void __launch_bounds__(T, 1) k_resident(const StepArgs g, const Resid
     for (int s = 0; s < n_steps; ++s) {
         const int64_t n = n0 + s;
         const uint32_t n32 = static_cast<uint32_t>(n);
+        StepClock ck;
+        ck.sample = ph == 0;
+        ck.k = kk - 1;
+        ck.row = cidx * N;
         float *Sn = S + (s & 1) * N;
         // the delayed input value of a packed edge key
         auto val = [&](uint32_t k) -> float {
@@ -237,15 +247,20 @@ __global__ void __launch_bounds__(T, 1) k_resident(const StepArgs g, const Resid
             if constexpr (kSpk) {
                 bool spike = false;
                 if (r < N) {
-                    node_update<kM | kNoRing>(la, r, n, 0.0f, wc[r], Sn[r], perm[r]);
+                    node_update<kM | kNoRing>(la, r, n, ck, 0.0f, wc[r], Sn[r], perm[r]);
                     const float vpeak = (kM & 3) == 1 ? izh_par(la, r).vpeak : hh_par(la, r).vpeak;
                     spike = iz_v[r] >= vpeak;
                 }
                 const uint32_t b = __ballot_sync(0xffffffffu, spike);
                 if (lane == 0 && base + 32 * warp < N) bits[((n32 + 1u) & rmask) * L.words + (base + 32 * warp) / 32] = b;
             } else {
-                if (r < N) node_update<kM>(la, r, n, ring_f[(n32 & rmask) * L.stride + r], wc[r], Sn[r], perm[r]);
+                if (r < N) node_update<kM>(la, r, n, ck, ring_f[(n32 & rmask) * L.stride + r], wc[r], Sn[r], perm[r]);
             }
+        }
+        if (++ph == se) {
+            ph = 0;
+            ++kk;
+            cidx = cidx + 1 == la.obs_cap ? 0 : cidx + 1;
         }
     }
     __syncthreads();

@@ -129,6 +129,27 @@ __device__ __forceinline__ void record_event(const StepArgs &a, int r, int64_t s
     }
 }
 
+// The observation bookkeeping of step n -> n + 1: whether it takes a sample (every
+// sample_every steps), the sample's number k and the offset of its row in the
+// observation ring.  Kernels compute it per node (step_clock); the resident kernel
+// keeps it as counters across its steps.
+struct StepClock {
+    bool sample;
+    int64_t k;    // sample number (when sample)
+    int64_t row;  // (k % obs_cap) * N (when sample)
+};
+
+__device__ __forceinline__ StepClock step_clock(const StepArgs &a, int64_t n)
+{
+    StepClock c{};
+    c.sample = ((n + 1) % a.sample_every) == 0;
+    if (c.sample) {
+        c.k = (n + 1) / a.sample_every - 1;
+        c.row = (c.k % a.obs_cap) * a.N;
+    }
+    return c;
+}
+
 // The readout state a sample reads: c1, or with camera frame averaging the mean of
 // c over the sample_every steps of the frame (summed in step order, then divided).
 __device__ __forceinline__ float frame_value(const StepArgs &a, int r, float c1, bool sample)
@@ -146,8 +167,8 @@ __device__ __forceinline__ float frame_value(const StepArgs &a, int r, float c1,
 // (kRing false: the caller keeps its own spike ring and writes it; the resident
 // kernel packs spd into bits by warp ballot)
 template <bool kPl, bool kRing = true>
-__device__ __forceinline__ void spiking_outputs(const StepArgs &a, int r, int64_t n, bool above, bool above1,
-                                                float c1, int32_t orig, uint32_t word_now)
+__device__ __forceinline__ void spiking_outputs(const StepArgs &a, int r, int64_t n, const StepClock &ck, bool above,
+                                                bool above1, float c1, int32_t orig, uint32_t word_now)
 {
     const int64_t at = ((n + 1) & a.ring_mask) * a.ring_stride + r;
     if constexpr (!kRing) {
@@ -161,13 +182,11 @@ __device__ __forceinline__ void spiking_outputs(const StepArgs &a, int r, int64_
         record_event(a, r, n + 1);
         if (a.first[r] < 0) a.first[r] = n + 1;
     }
-    const bool sample = ((n + 1) % a.sample_every) == 0;
-    const float cs = frame_value(a, r, c1, sample);
-    if (sample) {
-        const int64_t k = (n + 1) / a.sample_every - 1;
+    const float cs = frame_value(a, r, c1, ck.sample);
+    if (ck.sample) {
         if (orig == kLoad) orig = __ldg(a.perm + r);
-        const float xi = gauss_from(draw(a.obs_seed, static_cast<uint32_t>(orig), k, kStreamObservation));
-        a.obs[(k % a.obs_cap) * a.N + orig] = __fmaf_rn(a.sigma, xi, __fmaf_rn(a.gain, cs, a.offset));
+        const float xi = gauss_from(draw(a.obs_seed, static_cast<uint32_t>(orig), ck.k, kStreamObservation));
+        a.obs[ck.row + orig] = __fmaf_rn(a.sigma, xi, __fmaf_rn(a.gain, cs, a.offset));
     }
 }
 
@@ -219,8 +238,8 @@ __device__ __forceinline__ float calcium_step(const StepArgs &a, float c, float 
 // here (the ring holds spd); returns (r, p) at step n for psc_finish.  A spike
 // resets V, so every step with V >= V_peak is a new spike.
 template <bool kPl, bool kRing = true>
-__device__ __forceinline__ float2 izh_begin(const StepArgs &a, int r, int64_t n, float2 wc, float U, int32_t orig,
-                                         uint32_t word_now)
+__device__ __forceinline__ float2 izh_begin(const StepArgs &a, int r, int64_t n, const StepClock &ck, float2 wc, float U,
+                                         int32_t orig, uint32_t word_now)
 {
     const IzhPar z = izh_par(a, r);
     const float V = a.iz_v[r];
@@ -240,7 +259,7 @@ __device__ __forceinline__ float2 izh_begin(const StepArgs &a, int r, int64_t n,
     const float c1 = calcium_step(a, c, z.caq, spike);
     a.iz_v[r] = V1;
     a.wc[r] = make_float2(W1, c1);
-    spiking_outputs<kPl, kRing>(a, r, n, false, V1 >= z.vpeak, c1, orig, word_now);
+    spiking_outputs<kPl, kRing>(a, r, n, ck, false, V1 >= z.vpeak, c1, orig, word_now);
     return rp;
 }
 
@@ -255,8 +274,8 @@ __device__ __forceinline__ float hh_trap(float x, float y)
 // calcium as in izh_begin (p is left to psc_finish); no reset, events are upward
 // crossings of V_peak.
 template <bool kPl, bool kRing = true>
-__device__ __forceinline__ float2 hh_begin(const StepArgs &a, int r, int64_t n, float2 wc, float U, int32_t orig,
-                                        uint32_t word_now)
+__device__ __forceinline__ float2 hh_begin(const StepArgs &a, int r, int64_t n, const StepClock &ck, float2 wc, float U,
+                                        int32_t orig, uint32_t word_now)
 {
     const HhPar z = hh_par(a, r);
     const float V = a.iz_v[r];
@@ -287,7 +306,7 @@ __device__ __forceinline__ float2 hh_begin(const StepArgs &a, int r, int64_t n, 
     a.iz_v[r] = V1;
     a.hh_g[r] = make_float4(m1, n1, h1, 0.0f);
     a.wc[r] = make_float2(0.0f, c1);
-    spiking_outputs<kPl, kRing>(a, r, n, above, V1 >= z.vpeak, c1, orig, word_now);
+    spiking_outputs<kPl, kRing>(a, r, n, ck, above, V1 >= z.vpeak, c1, orig, word_now);
     return rp;
 }
 
@@ -343,28 +362,35 @@ __device__ __forceinline__ float stimulus(const StepArgs &a, int r, int64_t n, i
 // kM & kNoRing: the spike ring is left to the caller): stimulus and everything but
 // p; returns (r, p) at step n for psc_finish.
 template <int kM>
-__device__ __forceinline__ float2 spiking_begin(const StepArgs &a, int r, int64_t n, float2 wc, int32_t orig,
-                                                int32_t cnt0, uint32_t word_now = 0)
+__device__ __forceinline__ float2 spiking_begin(const StepArgs &a, int r, int64_t n, const StepClock &ck, float2 wc,
+                                                int32_t orig, int32_t cnt0, uint32_t word_now = 0)
 {
     constexpr bool kPl = (kM & kPlastic) != 0;
     constexpr bool kRing = (kM & kNoRing) == 0;
     const float U = stimulus(a, r, n, orig, cnt0);
     if constexpr ((kM & 3) == 1)
-        return izh_begin<kPl, kRing>(a, r, n, wc, U, orig, word_now);
+        return izh_begin<kPl, kRing>(a, r, n, ck, wc, U, orig, word_now);
     else
-        return hh_begin<kPl, kRing>(a, r, n, wc, U, orig, word_now);
+        return hh_begin<kPl, kRing>(a, r, n, ck, wc, U, orig, word_now);
+}
+
+template <int kM>
+__device__ __forceinline__ float2 spiking_begin(const StepArgs &a, int r, int64_t n, float2 wc, int32_t orig,
+                                                int32_t cnt0, uint32_t word_now = 0)
+{
+    return spiking_begin<kM>(a, r, n, step_clock(a, n), wc, orig, cnt0, word_now);
 }
 
 // Stimulus, node model kM's Euler step (0 FitzHugh-Nagumo, 1 Izhikevich, 2
 // Hodgkin-Huxley), history write, readout, noise, events, arrival.  `orig` (caller
 // id) and `cnt0` (background counter) may be prefetched by the caller; kLoad makes
-// node_update read them itself.
+// node_update read them itself.  `ck`: the step's observation bookkeeping.
 template <int kM>
-__device__ __forceinline__ void node_update(const StepArgs &a, int r, int64_t n, float v, float2 wc, float S,
-                                            int32_t orig = kLoad, int32_t cnt0 = kLoad)
+__device__ __forceinline__ void node_update(const StepArgs &a, int r, int64_t n, const StepClock &ck, float v,
+                                            float2 wc, float S, int32_t orig = kLoad, int32_t cnt0 = kLoad)
 {
     if constexpr (kM != 0) {
-        psc_finish(a, r, spiking_begin<kM>(a, r, n, wc, orig, cnt0), S);
+        psc_finish(a, r, spiking_begin<kM>(a, r, n, ck, wc, orig, cnt0), S);
         return;
     }
     const float U = stimulus(a, r, n, orig, cnt0);
@@ -382,15 +408,20 @@ __device__ __forceinline__ void node_update(const StepArgs &a, int r, int64_t n,
     if (v < a.theta_s && v1 >= a.theta_s) record_event(a, r, n + 1);
     if (v1 != 0.0f && v == 0.0f && a.first[r] < 0) a.first[r] = n + 1;
 
-    const bool sample = ((n + 1) % a.sample_every) == 0;
-    const float cs = frame_value(a, r, c1, sample);
-    if (sample) {
-        const int64_t k = (n + 1) / a.sample_every - 1;
+    const float cs = frame_value(a, r, c1, ck.sample);
+    if (ck.sample) {
         if (orig == kLoad) orig = __ldg(a.perm + r);
-        const float xi = gauss_from(draw(a.obs_seed, static_cast<uint32_t>(orig), k, kStreamObservation));
+        const float xi = gauss_from(draw(a.obs_seed, static_cast<uint32_t>(orig), ck.k, kStreamObservation));
         const float y = __fmaf_rn(a.sigma, xi, __fmaf_rn(a.gain, __fadd_rn(a.vrest, cs), a.offset));
-        a.obs[(k % a.obs_cap) * a.N + orig] = y;  // rows are written in the caller's node order
+        a.obs[ck.row + orig] = y;  // rows are written in the caller's node order
     }
+}
+
+template <int kM>
+__device__ __forceinline__ void node_update(const StepArgs &a, int r, int64_t n, float v, float2 wc, float S,
+                                            int32_t orig = kLoad, int32_t cnt0 = kLoad)
+{
+    node_update<kM>(a, r, n, step_clock(a, n), v, wc, S, orig, cnt0);
 }
 
 }  // namespace step
