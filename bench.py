@@ -814,7 +814,7 @@ def main():
         for item in args.sizes.split(","):
             name, steps = item.split(":")
             r = run_size(name, int(steps), args.warmup, local, stream, rank)
-            sec = r["steps"] * r["ms_per_step"] / 1e3
+            sec = r["details_steps"] * r["ms_per_step"] / 1e3
             r["value"], _, _ = replica_rate(r["value"] * sec, sec, dev)
             sizes[name] = r
         line["sizes"] = sizes

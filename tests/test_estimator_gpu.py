@@ -189,6 +189,30 @@ def test_learned_estimator_beats_the_plain_one_and_plain_matches_the_oracle():
     assert abs(auc_gpu - est.auroc(So, lab)) <= 0.02
 
 
+def test_learned_estimator_in_the_positive_control_regime():
+    """Sparse, independently driven nets (netgen.estimator_control: kept in-degree 1,
+    5 Hz background pulses), where a spike crosses an edge without setting off the
+    whole net: the plain peak-correlation estimator is well above chance on the GPU's
+    own traces, as on the FP64 oracle's, and the MLP trained on 400 such nets beats it
+    clearly on 100 held-out ones (the bench's run with 2,000 training nets: plain
+    0.745, learned 0.865)."""
+    torch = _torch()
+    from paper_0908_3934_b300 import geonet, pipeline
+    tr = pipeline.simulate_features([netgen.estimator_control(50000 + i) for i in range(400)], n_samples=500)
+    te = pipeline.simulate_features([netgen.estimator_control(60000 + i) for i in range(100)], n_samples=500)
+    plain = pipeline.scores(te["score"], te["label"])
+    mlp = geonet.Mlp(netgen.mlp_init(8), max_batch=4096)
+    losses = pipeline.train(mlp, tr["features"], tr["label"], epochs=12, batch=4096, seed=9)
+    assert losses[-1] < losses[0]
+    p = torch.empty(te["features"].shape[0], device=te["features"].device)
+    mlp.gn_mlp_infer(te["features"], p)
+    mlp.gn_mlp_synchronize()
+    learned = pipeline.scores(p, te["label"])
+    print("control regime: plain", plain["auroc"], "learned", learned["auroc"])
+    assert plain["auroc"] > 0.68
+    assert learned["auroc"] >= plain["auroc"] + 0.05, (learned, plain)
+
+
 def oracle_sim(spec):
     import oracle
     r = oracle.simulate(spec, 500 * spec.obs["sample_every"])
