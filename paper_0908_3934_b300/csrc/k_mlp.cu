@@ -39,7 +39,7 @@ constexpr int kKP = kMlpInPad;   // 64
 constexpr int kBM = 128;         // batch rows per tile
 constexpr uint32_t kWChunk = 256u * 64u * 2u;  // one weight chunk: 256 rows x 64 K, BF16 (32 KB)
 constexpr int kWChunks = 9;                     // W1, W2 x 4, W2^T x 4
-constexpr int kWStages = 2;                     // weight chunks in flight
+constexpr int kWStages = 2;                     // ring slots of the tile kernel's weight chunks
 constexpr size_t kWImage = static_cast<size_t>(kWChunks) * kWChunk;
 
 // byte of element (r, c) in a K-major chunk of 64 K-elements per row with the 128-byte
@@ -48,6 +48,13 @@ __host__ __device__ constexpr uint32_t img_off(uint32_t r, uint32_t c)
 {
     return r * 128u + ((((c >> 3) ^ r) & 7u) << 4) + (c & 7u) * 2u;
 }
+
+// Programmatic dependent launch: the kernels of a step are launched with the PDL
+// attribute, each lets the next one start at once (its prologue -- tensor-memory
+// allocation, barrier set-up -- overlaps this kernel) and waits for the previous grid
+// (griddepcontrol.wait: complete, its writes visible) before it reads that grid's output.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 __device__ __forceinline__ int64_t batch_row(const int64_t *idx, const int64_t *cursor, int B, int64_t r)
 {
@@ -170,7 +177,10 @@ struct TileArgs {
 };
 
 // Shared memory of k_tile (dynamic, from a 1024-byte aligned base): weight ring 2 x 32 KB |
-// X 16 KB | H1 64 KB | dH2 64 KB.
+// X 16 KB | H1 64 KB | dH2 64 KB.  Weight chunks also land in buffers that are dead at
+// the time: W2t K-chunks 2 and 3 in the dH2 operand (written only after layer 2), W2^T
+// K-chunks 2 and 3 in the H1 operand once layer 2 is done with it (the ReLU mask of H1
+// is kept apart as bits), so every chunk of a GEMM is in flight before the GEMM starts.
 // The column sums (2 x 4 lane groups x 256 floats) reuse the X operand, which is dead
 // once layer 1's MMAs are complete.
 constexpr int kOffRing = 0;
@@ -190,7 +200,8 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs g)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);  // swizzle atoms: 1 KB aligned
-    __shared__ __align__(8) uint64_t s_full[kWStages], s_empty[kWStages], s_mma;
+    __shared__ __align__(8) uint64_t s_full[kWChunks], s_empty[2], s_mma;
+    __shared__ uint32_t s_mask[kBM][kH / 32];  // H1 > 0 (as stored, BF16), bit per column
     __shared__ uint32_t s_tmem;
     __shared__ int s_fail;
     __shared__ float s_b1[kH], s_b2[kH], s_w3[kH];
@@ -215,19 +226,19 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs g)
     const int n_chunks = kTrain ? kWChunks : 5;  // W1t, W2t x 4, (W2b x 4)
     const uint8_t *wimg = g.wimg;
 
+    pdl_trigger();
     if (warp == 0) {
         tmem_alloc(&s_tmem, 512);
         tmem_relinquish();
     }
     if (t == 0) {
-        for (int i = 0; i < kWStages; ++i) {
-            mbar_init(&s_full[i], 1);
-            mbar_init(&s_empty[i], 1);
-        }
+        for (int i = 0; i < kWChunks; ++i) mbar_init(&s_full[i], 1);
+        for (int i = 0; i < 2; ++i) mbar_init(&s_empty[i], 1);
         mbar_init(&s_mma, 1);
         fence_barrier_init();
         s_fail = 0;
     }
+    pdl_wait();  // the previous step's parameters, weight images and batch cursor
     for (int i = t; i < kH; i += kTileThreads) {
         s_b1[i] = g.params[g.off_b1 + i];
         s_b2[i] = g.params[g.off_b2 + i];
@@ -238,35 +249,44 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs g)
     tc_fence_after_sync();
     const uint32_t tmem = s_tmem;
     bool ok = true;
-    auto load = [&](int c) {  // weight chunk c into stage c % kWStages
-        const int st = c % kWStages;
-        mbar_arrive_expect_tx(&s_full[st], kWChunk);
-        bulk_g2s(ring + st * kWChunk, wimg + static_cast<size_t>(c) * kWChunk, kWChunk, &s_full[st]);
+    // the buffer each weight chunk lands in: W1t and W2t K-chunks 0, 1 in the ring, W2t
+    // K-chunks 2, 3 in the dH2 operand, W2^T K-chunks 0, 1 back in the ring, 2, 3 in the H1
+    // operand; each chunk completes on its own mbarrier (one phase each)
+    auto wbuf = [&](int c) -> uint8_t * {
+        constexpr int kRingOf[kWChunks] = {0, 1, 0, -1, -2, 1, 0, -3, -4};
+        const int r = kRingOf[c];
+        return r >= 0 ? ring + r * kWChunk : r >= -2 ? sD2 + (-1 - r) * kWChunk : sH1 + (-3 - r) * kWChunk;
     };
-    int loaded = 0;  // chunks whose copies were issued (thread 0)
+    unsigned loaded = 0;  // bit c: chunk c's copy was issued (thread 0)
+    auto load = [&](int c) {
+        if (c >= n_chunks) return;
+        mbar_arrive_expect_tx(&s_full[c], kWChunk);
+        bulk_g2s(wbuf(c), wimg + static_cast<size_t>(c) * kWChunk, kWChunk, &s_full[c]);
+        loaded |= 1u << c;
+    };
     if (t == 0) {
-        for (; loaded < kWStages; ++loaded) load(loaded);
+        load(0);
+        load(1);
+        load(3);
+        load(4);
     }
-    // refill: chunk c's MMAs are complete -> its stage takes chunk c + kWStages
-    auto refill = [&](int c) {
-        if (!mbar_wait_bounded(&s_empty[c % kWStages], (c / kWStages) & 1, kDefaultWaitLimit)) ok = false;
-        if (ok && c + kWStages < n_chunks) {
-            load(c + kWStages);
-            loaded = c + kWStages + 1;
-        }
-    };
     // four M=128 N=256 K=16 MMAs of chunk c; A: the matching 64-element K-chunk of an
-    // operand in shared memory (both operands 128-byte swizzled)
+    // operand in shared memory (both operands 128-byte swizzled); completion of the ring
+    // chunks 0, 1, 2 is committed to the ring slot's mbarrier
     auto mma = [&](int c, const uint8_t *a, uint32_t d, bool first) {
-        if (!mbar_wait_bounded(&s_full[c % kWStages], (c / kWStages) & 1, kDefaultWaitLimit)) ok = false;
+        if (!mbar_wait_bounded(&s_full[c], 0, kDefaultWaitLimit)) ok = false;
         if (!ok) return;
         tc_fence_after_sync();
-        const uint8_t *b = ring + (c % kWStages) * kWChunk;
+        const uint8_t *b = wbuf(c);
 #pragma unroll
         for (int ks = 0; ks < 4; ++ks)
             tc_mma_bf16(d, smem_desc_sw128(a + ks * 32), smem_desc_sw128(b + ks * 32), kIdesc,
                         (!first || ks) ? 1u : 0u);
-        tc_commit(&s_empty[c % kWStages]);
+        if (c <= 2) tc_commit(&s_empty[c & 1]);
+    };
+    // the ring slot of chunk c (0, 1 or 2) is free again once its MMAs are complete
+    auto slot_free = [&](int c) {
+        if (!mbar_wait_bounded(&s_empty[c & 1], c >> 1, kDefaultWaitLimit)) ok = false;
     };
     int mma_commits = 0;  // thread 0
     auto commit_mma = [&]() {
@@ -314,7 +334,8 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs g)
     if (t == 0) {
         mma(0, sX, tmem, true);
         commit_mma();
-        refill(0);
+        slot_free(0);
+        if (ok) load(2);
     }
     wait_mma(0);
     // epilogue 1: H1 = relu(C1 + b1), BF16 into the layer-2 operand (+ its batch-major image)
@@ -324,7 +345,13 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs g)
             float v[32];
             acc32(c0, v);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + s_b1[c0 + j], 0.0f);
+            uint32_t m = 0;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                v[j] = fmaxf(v[j] + s_b1[c0 + j], 0.0f);
+                m |= (__bfloat162float(__float2bfloat16_rn(v[j])) > 0.0f ? 1u : 0u) << j;
+            }
+            s_mask[rl][c0 >> 5] = m;
             put_row32(sH1, rl, c0, v);
             if constexpr (kTrain) put_col32(g.h1t_img + img_chunk * (kH * 64 * 2), c0, mrow, v, lane);
         }
@@ -336,14 +363,24 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs g)
     // ---- layer 2: C2 = H1 W2 (columns 256 .. 511), W2t in four K-chunks
     if (t == 0 && !s_fail) {
         tc_fence_after_sync();
-        // one chunk queued ahead: chunk c's MMAs are issued before chunk c - 1's stage is
-        // refilled (that wait is for MMAs the tensor pipe is already past)
-        for (int c = 1; c < 5; ++c) {
-            mma(c, sH1 + (c - 1) * 16384, tmem + 256, c == 1);
-            if (c > 1) refill(c - 1);
-        }
+        mma(1, sH1, tmem + 256, true);
+        mma(2, sH1 + 16384, tmem + 256, false);
+        slot_free(1);
+        if (ok) load(5);
+        mma(3, sH1 + 2 * 16384, tmem + 256, false);
+        mma(4, sH1 + 3 * 16384, tmem + 256, false);
         commit_mma();
-        refill(4);
+        slot_free(2);
+        if (ok) load(6);
+        // layer 2 is done with H1 (and with the W2t chunks in the dH2 operand): W2^T
+        // K-chunks 2, 3 go to the H1 operand
+        if (kTrain && ok) {
+            if (!mbar_wait_bounded(&s_mma, 1, kDefaultWaitLimit)) ok = false;
+            if (ok) {
+                load(7);
+                load(8);
+            }
+        }
     }
     wait_mma(1);
 
@@ -429,10 +466,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs g)
         // ---- dH1 = dH2 W2^T (columns 0 .. 255 again), W2b in four K-chunks
         if (t == 0 && !s_fail) {
             tc_fence_after_sync();
-            for (int c = 5; c < kWChunks; ++c) {
-                mma(c, sD2 + (c - 5) * 16384, tmem, c == 5);
-                if (c > 5) refill(c - 1);
-            }
+            for (int c = 5; c < kWChunks; ++c) mma(c, sD2 + (c - 5) * 16384, tmem, c == 5);
             commit_mma();
         }
         wait_mma(0);
@@ -442,17 +476,11 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs g)
             for (int c0 = 64 * cq; c0 < 64 * cq + 64; c0 += 32) {
                 float d[32];
                 acc32(c0, d);
-                // this row's 32 stored H1 values (the mask), 16 bytes at a time
+                // the ReLU mask of this row's stored H1 values
+                const uint32_t m = s_mask[rl][c0 >> 5];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const uint4 u = *reinterpret_cast<const uint4 *>(op_unit(sH1, rl, c0 + 8 * q));
-                    const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-                    for (int h = 0; h < 8; ++h) {
-                        const uint16_t bits = static_cast<uint16_t>((h & 1) ? (w4[h >> 1] >> 16) : (w4[h >> 1] & 0xFFFFu));
-                        if (!(__bfloat162float(__ushort_as_bfloat16(bits)) > 0.0f)) d[8 * q + h] = 0.0f;
-                    }
-                }
+                for (int j = 0; j < 32; ++j)
+                    if (!((m >> j) & 1u)) d[j] = 0.0f;
                 put_col32(g.dh1t_img + img_chunk * (kH * 64 * 2), c0, mrow, d, lane);
                 cols[lg * kH + c0 + lane] = col_sum32(d, lane);  // db1
             }
@@ -469,8 +497,8 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile(const TileArgs g)
     if (t == 0 && !ok) {
         atomicOr(g.status, kStatusTimeout);
         s_fail = 1;
-        for (int c = 0; c < loaded; ++c)
-            mbar_wait_bounded(&s_full[c % kWStages], (c / kWStages) & 1, kDefaultWaitLimit);
+        for (int c = 0; c < kWChunks; ++c)
+            if (loaded & (1u << c)) mbar_wait_bounded(&s_full[c], 0, kDefaultWaitLimit);
         tc_commit(&s_mma);  // completes once every MMA this thread issued is done
         mbar_wait_bounded(&s_mma, mma_commits & 1, kDefaultWaitLimit);
     }
@@ -497,7 +525,7 @@ struct WgradArgs {
     unsigned int *status;
 };
 
-constexpr int kWgStages = 3;
+constexpr int kWgStages = 4;  // a split's chunks (4 at a batch of 8192) all in flight at once
 constexpr uint32_t kWgA = 16384, kWgB = 32768;
 constexpr int kWgradSmem = kWgStages * static_cast<int>(kWgA + kWgB) + 1024;  // + the alignment of the base
 
@@ -523,6 +551,7 @@ __global__ void __launch_bounds__(kWgradThreads, 1) k_wgrad(const WgradArgs g)
     const size_t a_stride = kH * 64 * 2;                      // one chunk of a 256-feature image
     const size_t b_stride = prob == 0 ? kH * 64 * 2 : 64 * 64 * 2;
 
+    pdl_trigger();
     if (warp == 0) {
         tmem_alloc(&s_tmem, 256);
         tmem_relinquish();
@@ -540,6 +569,7 @@ __global__ void __launch_bounds__(kWgradThreads, 1) k_wgrad(const WgradArgs g)
     tc_fence_after_sync();
     const uint32_t tmem = s_tmem;
     const uint32_t idesc = prob == 0 ? idesc_bf16_f32(128, 256) : idesc_bf16_f32(128, 64);
+    pdl_wait();  // the tile kernel's operand images
 
     if (t == 0) {
         bool ok = true;
@@ -665,6 +695,8 @@ __device__ __forceinline__ void put_weight(uint8_t *wimg, bool is_w2, int k, int
 
 __global__ void k_update(const UpdateArgs g)
 {
+    pdl_trigger();
+    pdl_wait();  // the partials of the tile and weight-gradient kernels
     const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
     if (i > g.n_params) return;
     if (i == g.n_params) {
@@ -729,6 +761,8 @@ __global__ void k_refresh(const float *__restrict__ W1, int in_dim, const float 
 // cursor moves to the next batch.
 __global__ void k_epoch_tail(const float *__restrict__ loss_sum, int B, int64_t *cursor, float *__restrict__ losses)
 {
+    pdl_trigger();
+    pdl_wait();
     losses[*cursor] = *loss_sum / static_cast<float>(B);
     *cursor += 1;
 }
@@ -736,6 +770,22 @@ __global__ void k_epoch_tail(const float *__restrict__ loss_sum, int B, int64_t 
 }  // namespace
 
 // ---------------------------------------------------------------------------
+template <class... KArgs, class... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 size_t mlp_wimg_bytes() { return kWImage; }
 size_t mlp_xt_bytes(int Bp) { return static_cast<size_t>(Bp / 64) * 64 * 64 * 2; }
 size_t mlp_ht_bytes(int Bp) { return static_cast<size_t>(Bp / 64) * kH * 64 * 2; }
@@ -781,11 +831,8 @@ cudaError_t mlp_launch_tile(const MlpBuffers &b, const float *X, const int64_t *
     g.part_head = b.part_head;
     g.part_b1 = b.part_b1;
     g.status = b.status;
-    if (y)
-        k_tile<true><<<Bp / kBM, kTileThreads, kTileSmem, s>>>(g);
-    else
-        k_tile<false><<<Bp / kBM, kTileThreads, kTileSmem, s>>>(g);
-    return cudaGetLastError();
+    if (y) return launch_pdl(k_tile<true>, dim3(Bp / kBM), dim3(kTileThreads), kTileSmem, s, g);
+    return launch_pdl(k_tile<false>, dim3(Bp / kBM), dim3(kTileThreads), kTileSmem, s, g);
 }
 
 cudaError_t mlp_launch_wgrad(const MlpBuffers &b, int Bp, cudaStream_t s)
@@ -800,8 +847,7 @@ cudaError_t mlp_launch_wgrad(const MlpBuffers &b, int Bp, cudaStream_t s)
     g.part_w2 = b.part_w2;
     g.part_w1 = b.part_w1;
     g.status = b.status;
-    k_wgrad<<<dim3(4, splits), kWgradThreads, kWgradSmem, s>>>(g);
-    return cudaGetLastError();
+    return launch_pdl(k_wgrad, dim3(4, splits), dim3(kWgradThreads), kWgradSmem, s, g);
 }
 
 cudaError_t mlp_launch_update(const MlpBuffers &b, int Bp, bool adamw, float lr, float wd, float bc1, float bc2,
@@ -840,8 +886,7 @@ cudaError_t mlp_launch_update(const MlpBuffers &b, int Bp, bool adamw, float lr,
     g.cursor = cursor;
     g.wimg = static_cast<uint8_t *>(b.wimg);
     const int64_t n = b.n_params + 1;
-    k_update<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(g);
-    return cudaGetLastError();
+    return launch_pdl(k_update, dim3(static_cast<unsigned>((n + 255) / 256)), dim3(256), 0, s, g);
 }
 
 cudaError_t mlp_launch_refresh(const MlpBuffers &b, cudaStream_t s)
@@ -853,8 +898,7 @@ cudaError_t mlp_launch_refresh(const MlpBuffers &b, cudaStream_t s)
 
 cudaError_t mlp_launch_epoch_tail(const float *loss_sum, int B, int64_t *cursor, float *losses, cudaStream_t s)
 {
-    k_epoch_tail<<<1, 1, 0, s>>>(loss_sum, B, cursor, losses);
-    return cudaGetLastError();
+    return launch_pdl(k_epoch_tail, dim3(1), dim3(1), 0, s, loss_sum, B, cursor, losses);
 }
 
 }  // namespace gn
