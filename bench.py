@@ -46,7 +46,8 @@ NODE_BYTES = 36.2      # v~ read 4, (w~,c~) read 8 + write 8, ring write 4, row_
 # delay) of a tile its packed key 4 B + the FP32 history value 4 B
 STAGED_EDGE_BYTES = 6
 STAGED_GATHER_BYTES = 8
-KERNEL_NAMES = {1: "k_step", 2: "k_step_pipe", 3: "k_step_staged"}
+KERNEL_NAMES = {1: "k_step", 2: "k_step_pipe", 3: "k_step_staged", 4: "k_resident"}
+RESIDENT_CHUNK = 65536  # steps per launch of the resident kernel
 # format-independent bytes of one step: per edge-update a 10-byte edge record (weight 4,
 # source 4, delay 2) + the gathered FP32 history value 4; per node-step NODE_BYTES
 SURVEY_EDGE_BYTES = 14
@@ -326,12 +327,15 @@ def run_batched(args, local, stream, rank):
             "value": E * steps / t, "details_unit": METRIC, "seconds": t, "ms_per_step": t / steps * 1e3,
             "details_rtf": steps * 0.05e-3 / t, "details_cta_threads": info["cta_threads"], "details_grid": info["grid"],
             "step_kernel": info["step_kernel"],
-            # kernel 3: member groups stepped a 64-step chunk at a time (L2 blocking), in lanes
-            # of concurrent launch chains; 1 group = every member every step
+            # kernels 3 and 5: member groups stepped a 64-step chunk at a time (L2 blocking),
+            # in lanes (3: concurrent launch chains; 5: CTA lanes of one persistent launch);
+            # 1 group = every member every step
             "step_groups": info["step_groups"], "step_lanes": info["step_lanes"],
             # kernel 1: one persistent launch; kernel 3: one per group and step + one advance per
-            # 64-step graph (and per ragged tail)
+            # 64-step graph (and per ragged tail); kernel 5: one cooperative launch + one advance
+            # per chunk
             "details_gpu_launches": 1 if info["step_kernel"] == 1
+            else 2 * ((steps + 63) // 64) if info["step_kernel"] == 5
             else steps * max(1, info["step_groups"]) + (steps + 63) // 64,
             "loop_plain": {"value": E * steps / t_loop, "details_seconds_extrapolated": t_loop,
                            "details_sample": f"{len(pick)} random nets timed one after another, "
@@ -480,6 +484,7 @@ def run_test_set(args, local, stream, model: str = "izh"):
     ev1.record(stream)
     torch.cuda.synchronize()
     t_batch = ev0.elapsed_time(ev1) / 1e3
+    binfo = b.gn_batch_get_info()
     b.gn_batch_destroy()
     dt = ispecs[0].dt_ms
     rtf = [r[3] for r in rows]
@@ -497,7 +502,9 @@ def run_test_set(args, local, stream, model: str = "izh"):
             "batched": {"rtf_every_network": steps * dt * 1e-3 / t_batch,
                         "network_seconds_per_second": len(ispecs) * steps * dt * 1e-3 / t_batch,
                         "speedup_vs_one_after_another": sum(r[4] for r in rows) / t_batch,
-                        "details_gpu_launches": steps + steps // 64},
+                        "step_kernel": binfo["step_kernel"], "step_lanes": binfo["step_lanes"],
+                        "details_gpu_launches": 2 * ((steps + 63) // 64) if binfo["step_kernel"] == 5
+                        else steps * max(1, binfo["step_groups"]) + (steps + 63) // 64},
             "details_networks": [{"name": r[0], "N": r[1], "E": r[2], "rtf": round(r[3], 1)} for r in rows]}
 
 
@@ -743,7 +750,10 @@ def main():
     barrier()
     clocks = sampler.stop()
     t = ev0.elapsed_time(ev1) / 1e3
-    launches = args.steps + args.steps // 64 + (1 if args.steps % 64 else 0)
+    if info["step_kernel"] == 4:  # one resident launch and one advance per chunk
+        launches = 2 * (-(-args.steps // RESIDENT_CHUNK))
+    else:  # one step launch per step, one advance per 64-step graph and per ragged tail
+        launches = args.steps + args.steps // 64 + (1 if args.steps % 64 else 0)
     net.gn_observe(discard=True)
 
     # ---- end to end through the public API: every chunk uploads a new pulse set from

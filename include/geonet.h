@@ -360,10 +360,12 @@ typedef struct {
     int32_t grid;                /* CTAs per launch: persistent CTAs (kernel 1) or tiles (kernel 3) */
     size_t device_bytes;
     int32_t step_kernel;         /* 1: persistent k_batch, one launch per gn_batch_step; 3: staged tiles of
-                                    every member, one launch per step; 0 before the first step */
-    int32_t step_groups;         /* kernel 3: member groups, each stepped through a 64-step chunk at a time
-                                    (1: every member every step; see gn_batch_step); else 0 */
-    int32_t step_lanes;          /* kernel 3: groups stepped concurrently (one chain of launches each); else 0 */
+                                    every member, one launch per step; 5: the staged tile step in one
+                                    persistent cooperative launch per 64-step chunk; 0 before the first step */
+    int32_t step_groups;         /* kernels 3 and 5: member groups, each stepped through a 64-step chunk at a
+                                    time (1: every member every step; see gn_batch_step); else 0 */
+    int32_t step_lanes;          /* kernels 3 and 5: groups stepped concurrently (3: one chain of launches
+                                    each; 5: one lane of the launch's CTAs each); else 0 */
 } gn_batch_info;
 
 /* Copy and build n_nets networks on one device (descs[i].device must agree; the
@@ -381,21 +383,28 @@ GN_API gn_status gn_batch_set_stimulus_all(gn_batch *batch, const gn_pulse *puls
 GN_API gn_status gn_batch_set_background(gn_batch *batch, int32_t net, double rate_hz, float amp, double dur_ms,
                                          uint64_t seed);
 
-/* Advance every network n_steps (asynchronous): one persistent launch (kernel 1)
- * or one launch per step replayed from a captured graph (kernel 3), whichever the
- * first call measured faster; GN_BATCH_KERNEL=1 or 3 in the environment restricts
- * the choice.  Kernel 3 has several schedules, also timed on the first call:
- * every member every step, or (L2 blocking) contiguous groups of members, each
- * group stepped through the 64 steps of a graph chunk at a time so that its steps
- * read from L2, with 1, 2 or 4 groups in flight at once (lanes: one chain of
- * launches each, on streams forked from the batch's stream).  The groups in flight
- * share an L2 budget for their per-step working sets -- edge entries, gather keys,
- * live history slots, node state -- of GN_BATCH_GROUP_KB (default 80 MB; 0 turns
- * the blocking off); GN_BATCH_LANES=1..8 fixes the lanes and GN_BATCH_KERNEL=4
- * takes the blocked schedule without timing.  The networks are independent, so
- * neither the kernel nor the schedule changes a result: both sum a node's inputs
- * in the order of the single-network kernels, and results are bit-identical
- * either way.  Spiking batches run kernel 3. */
+/* Advance every network n_steps (asynchronous): one persistent launch (kernel 1),
+ * one launch per step replayed from a captured graph (kernel 3) or one persistent
+ * cooperative launch per 64-step chunk (kernel 5, the same tile step), whichever
+ * the first call measured faster; GN_BATCH_KERNEL=1 or 3 in the environment
+ * restricts the choice to that kernel.  Kernel 3 has several schedules, also timed
+ * on the first call: every member every step, or (L2 blocking) contiguous groups
+ * of members, each group stepped through the 64 steps of a graph chunk at a time
+ * so that its steps read from L2, with 1, 2 or 4 groups in flight at once (lanes:
+ * one chain of launches each, on streams forked from the batch's stream).  Kernel
+ * 5 runs the blocked schedule in 1, 2, 4 or 8 lanes of one launch's CTAs (every
+ * CTA the device holds at once), a lane's CTAs meeting at a counting barrier in
+ * global memory after each step instead of a launch boundary.  The groups in
+ * flight share an L2 budget for their per-step working sets -- edge entries,
+ * gather keys, live history slots, node state -- of GN_BATCH_GROUP_KB (default
+ * 80 MB; 0 turns the blocking off); GN_BATCH_LANES=1..8 fixes the lanes,
+ * GN_BATCH_KERNEL=4 takes kernel 3's blocked schedule and GN_BATCH_KERNEL=5
+ * kernel 5, without timing.  The networks are independent, so neither the kernel
+ * nor the schedule changes a result: all sum a node's inputs in the order of the
+ * single-network kernels, and results are bit-identical either way.  Spiking
+ * batches run kernel 3 or 5.  A bounded wait of kernel 5 that gives up (its copy
+ * waits, its barrier polls) records a timeout that the next synchronising call
+ * reports as GN_ETIMEOUT. */
 GN_API gn_status gn_batch_step(gn_batch *batch, int64_t n_steps);
 GN_API gn_status gn_batch_synchronize(gn_batch *batch);
 

@@ -28,7 +28,9 @@
 // budget.  The launches are the same kernel over a group's tiles (its members'
 // tile pointers start at the group's first tile), so grouping never changes a
 // result either; the first gn_batch_step times the schedules with the other
-// candidates.
+// candidates.  The lanes schedule runs the same groups in one cooperative launch
+// per chunk (k_batch_lanes): lanes of CTAs instead of launch chains, a counting
+// barrier in global memory instead of each launch boundary.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -49,6 +51,7 @@ namespace {
 
 constexpr int kGraphSteps = 64;             // staged form: steps per captured graph
 constexpr int kStaged = gn::kNumBatchShapes;  // shape index of the staged form
+constexpr int kLanes = kStaged + 1;            // ... and of its persistent lanes schedule (k_batch_lanes)
 // per-step working set of a member beyond its edge structure, per node: the live
 // history slots (max delay + 2, 4 bytes each) come on top of these node-state bytes
 // (w and readout 8, background counter 4, arrival step 8, caller id 4, sample 4)
@@ -112,6 +115,8 @@ struct gn_batch {
     int st_lanes = 1;                // groups stepped concurrently, one chain of launches per lane
     std::vector<cudaStream_t> lane_stream;  // lanes 1, 2, ... (lane 0 runs on the batch's stream)
     std::vector<cudaEvent_t> lane_event;    // fork, then one join per extra lane
+    DevArray<int2> st_gtab;                 // lanes schedule: {first tile, tiles} of each group
+    DevArray<unsigned int> lane_count;      // ... and the lanes' barrier counters (32 words each)
     int n_tiles = 0;
     size_t st_smem = 0;
     DevArray<int4> st_tile, st_tile2;
@@ -151,6 +156,8 @@ struct gn_batch {
         st_plist.release();
         st_rq.release();
         st_tile_net.release();
+        st_gtab.release();
+        lane_count.release();
         iz_v.release();
         rp.release();
         hh_g.release();
@@ -292,8 +299,54 @@ void ensure_lanes(gn_batch *b, int lanes)
     }
 }
 
+// The lanes schedule: its kernel prepared for the batch's format; returns its
+// cooperative grid (every CTA the device holds at once).
+// GN_BATCH_LANE_CTAS=k in the environment holds it to k CTAs per SM.
+int lanes_grid(gn_batch *b)
+{
+    int per_sm = 0, sms = 0;
+    cuda_check(gn::batch_lanes_prepare(b->model, b->st_packed, b->st_smem, &per_sm), "lanes kernel setup");
+    cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device), "device query");
+    if (const char *e = getenv("GN_BATCH_LANE_CTAS"); e && *e) per_sm = std::min(per_sm, std::max(1, atoi(e)));
+    if (per_sm < 1) fail(GN_ECUDA, "the lanes kernel does not fit on an SM");
+    if (!b->lane_count.p) b->lane_count.alloc(gn::kLaneWords * gn::kMaxBatchLanes, &b->bytes);
+    return per_sm * sms;
+}
+
+void upload_groups(const std::vector<StGroup> &groups, DevArray<int2> &out, size_t *bytes)
+{
+    std::vector<int2> t;
+    for (const StGroup &g : groups) t.push_back(make_int2(g.t0, g.nt));
+    out.release();
+    out.upload(t, bytes);
+}
+
+// Steps 0 .. n - 1 of the lanes schedule over `gtab` (n_groups groups): the barrier
+// counters cleared, then one cooperative launch in min(lanes, n_groups) lanes.
+cudaError_t launch_lanes(const gn_batch *b, const gn::StepArgs *args, const int2 *gtab, int n_groups, int lanes,
+                         int grid, int n, cudaStream_t s)
+{
+    lanes = std::max(1, std::min(lanes, n_groups));
+    cudaError_t e = cudaMemsetAsync(b->lane_count.p, 0, b->lane_count.n * sizeof(unsigned int), s);
+    if (e == cudaSuccess)
+        e = gn::launch_batch_lanes(b->model, args, b->st_tile_net.p, gtab, n_groups, lanes, n, b->lane_count.p,
+                                   b->status.p, b->args[0].wait_limit, b->st_packed, grid, b->st_smem, s);
+    return e;
+}
+
 void set_shape(gn_batch *b, int shape, bool grouped, int lanes)
 {
+    if (shape == kLanes) {
+        b->st_stream = false;
+        b->st_groups = make_groups(b, group_budget() / lanes);
+        b->st_lanes = lanes;
+        b->grid = lanes_grid(b);
+        upload_groups(b->st_groups, b->st_gtab, &b->bytes);
+        b->shape = kLanes;
+        upload_args(b);
+        drop_graph(b);
+        return;
+    }
     if (shape == kStaged) {
         // grouped members keep their structure in L2 across the chunk; otherwise a
         // structure larger than L2 is streamed past the history
@@ -350,10 +403,15 @@ cudaError_t launch_staged(const gn_batch *b, const gn::StepArgs *args, const std
 }
 
 void launch_steps(gn_batch *b, const gn::StepArgs *args, int64_t *d_step, int n_steps, int shape, int grid,
-                  const std::vector<StGroup> &groups, int lanes, cudaStream_t s)
+                  const std::vector<StGroup> &groups, int lanes, cudaStream_t s, const int2 *gtab = nullptr)
 {
     if (shape == kStaged) {
         cuda_check(launch_staged(b, args, groups, lanes, 0, n_steps, s), "staged batch launch");
+        return;
+    }
+    if (shape == kLanes) {
+        cuda_check(launch_lanes(b, args, gtab, static_cast<int>(groups.size()), lanes, grid, n_steps, s),
+                   "lanes batch launch");
         return;
     }
     cuda_check(cudaMemsetAsync(b->queue.p, 0, 4, s), "queue reset");
@@ -383,12 +441,13 @@ cudaGraphExec_t capture_graph(F &&body)
 }
 
 // Time each candidate (k_batch in each CTA shape, the staged form with and without
-// L2 blocking) per step on a scratch copy of the dynamic state: k_batch over 16
-// steps in one launch, the staged form over one graph chunk replayed from a graph
-// as gn_batch_step runs it (a chunk of many small groups issues thousands of
-// launches, which direct launches would time as host work).  A single candidate is
-// taken untimed.
-void autotune(gn_batch *b, bool persistent, bool staged)
+// L2 blocking, the lanes schedule in 1 to 8 lanes) per step on a scratch copy of
+// the dynamic state: k_batch over 16 steps in one launch, the staged form over one
+// graph chunk replayed from a graph as gn_batch_step runs it (a chunk of many
+// small groups issues thousands of launches, which direct launches would time as
+// host work).  A single candidate is taken untimed.  A lanes candidate that cannot
+// be launched (a cooperative launch refused) is left out.
+void autotune(gn_batch *b, bool persistent, bool staged, bool lanes_ok)
 {
     struct Cand {
         int shape;
@@ -404,6 +463,11 @@ void autotune(gn_batch *b, bool persistent, bool staged)
         for (int lanes : {1, 2, 4})
             if ((!fixed || lanes == fixed) && make_groups(b, group_budget() / lanes).size() > 1)
                 cands.push_back({kStaged, true, lanes});
+        if (lanes_ok)
+            for (int lanes : {1, 2, 4, 8})
+                if ((!fixed || lanes == fixed) &&
+                    (lanes == 1 || static_cast<int>(make_groups(b, group_budget() / lanes).size()) >= lanes))
+                    cands.push_back({kLanes, true, lanes});
     }
     if (cands.empty()) fail(GN_EINVAL, "no batch kernel can step this batch");
     if (cands.size() == 1) {
@@ -418,8 +482,10 @@ void autotune(gn_batch *b, bool persistent, bool staged)
     DevArray<int64_t> first, evs, dstep;
     DevArray<unsigned long long> evc;
     DevArray<gn::StepArgs> dargs;
+    DevArray<int2> gtab;
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     auto cleanup = [&] {
+        gtab.release();
         ring.release(); obs.release(); wc.release(); bgc.release(); evn.release(); first.release();
         evs.release(); dstep.release(); evc.release(); dargs.release(); facc.release();
         izv.release(); rpv.release(); hhg.release();
@@ -472,13 +538,19 @@ void autotune(gn_batch *b, bool persistent, bool staged)
                 prepare_staged(b, groups);
                 ensure_lanes(b, c.lanes);
                 steps = kGraphSteps;
+            } else if (c.shape == kLanes) {
+                b->st_stream = false;
+                groups = make_groups(b, group_budget() / c.lanes);
+                grid = lanes_grid(b);
+                upload_groups(groups, gtab, &tmp);
+                steps = kGraphSteps;
             } else {
                 int per_sm = 0, sms = 0;
                 cuda_check(gn::batch_occupancy(c.shape, &per_sm), "occupancy");
                 cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device), "device query");
                 grid = std::max(1, std::min(b->n_nets, per_sm * sms));
             }
-            std::vector<gn::StepArgs> a = args_for(b, c.shape == kStaged ? 0 : c.shape, groups);
+            std::vector<gn::StepArgs> a = args_for(b, c.shape >= kStaged ? 0 : c.shape, groups);
             for (int i = 0; i < b->n_nets; ++i) {
                 const Member &mm = b->m[i];
                 a[i].ring = ring.p + mm.ring_off;
@@ -500,7 +572,15 @@ void autotune(gn_batch *b, bool persistent, bool staged)
             }
             cuda_check(cudaMemcpy(dargs.p, a.data(), a.size() * sizeof(gn::StepArgs), cudaMemcpyHostToDevice), "H2D");
             cudaGraphExec_t ge = nullptr;
-            if (c.shape == kStaged) {
+            if (c.shape == kLanes) {
+                // direct launches, as gn_batch_step issues them (one per chunk)
+                const cudaError_t e =
+                    launch_lanes(b, dargs.p, gtab.p, static_cast<int>(groups.size()), c.lanes, grid, steps, b->stream);
+                if (e != cudaSuccess) {  // a cooperative launch the device refuses
+                    cudaGetLastError();
+                    continue;
+                }
+            } else if (c.shape == kStaged) {
                 ge = capture_graph([&](cudaStream_t cs) {
                     return launch_staged(b, dargs.p, groups, c.lanes, 0, steps, cs);
                 });
@@ -514,6 +594,9 @@ void autotune(gn_batch *b, bool persistent, bool staged)
             if (e == cudaSuccess) {
                 if (ge)
                     e = cudaGraphLaunch(ge, b->stream);
+                else if (c.shape == kLanes)
+                    e = launch_lanes(b, dargs.p, gtab.p, static_cast<int>(groups.size()), c.lanes, grid, steps,
+                                     b->stream);
                 else
                     launch_steps(b, dargs.p, dstep.p, steps, c.shape, grid, groups, c.lanes, b->stream);
             }
@@ -916,14 +999,14 @@ gn_status gn_batch_get_info(const gn_batch *b, gn_batch_info *info)
             info->n_edges += mm.E;
         }
         info->step = b->step;
-        info->cta_threads = b->shape == kStaged ? gn::kBatchStagedShape.threads
+        info->cta_threads = b->shape >= kStaged ? gn::kBatchStagedShape.threads
                             : b->shape >= 0       ? gn::kBatchThreads[b->shape]
                                                   : 0;
         info->grid = b->grid;
         info->device_bytes = b->bytes;
-        info->step_kernel = b->shape == kStaged ? 3 : b->shape >= 0 ? 1 : 0;
-        info->step_groups = b->shape == kStaged ? static_cast<int32_t>(b->st_groups.size()) : 0;
-        info->step_lanes = b->shape == kStaged ? std::min(b->st_lanes, std::max(1, info->step_groups)) : 0;
+        info->step_kernel = b->shape == kLanes ? 5 : b->shape == kStaged ? 3 : b->shape >= 0 ? 1 : 0;
+        info->step_groups = b->shape >= kStaged ? static_cast<int32_t>(b->st_groups.size()) : 0;
+        info->step_lanes = b->shape >= kStaged ? std::min(b->st_lanes, std::max(1, info->step_groups)) : 0;
     });
 }
 
@@ -942,7 +1025,7 @@ gn_status gn_batch_get_net_info(const gn_batch *b, int32_t net, gn_net_info *inf
         info->n_clamped = mm.n_clamped;
         info->edge_format = mm.packed ? 0 : 1;
         // tiles when the staged form steps the batch, else row blocks of k_batch's CTA size
-        info->n_blocks = b->shape == kStaged ? mm.st_nt : mm.n_blocks[desc_shape(b)];
+        info->n_blocks = b->shape >= kStaged ? mm.st_nt : mm.n_blocks[desc_shape(b)];
         info->step = b->step;
         info->samples = b->step / mm.sample_every;
         info->v_rest = mm.v_rest;
@@ -1031,15 +1114,26 @@ gn_status gn_batch_step(gn_batch *b, int64_t n_steps)
         if (b->shape < 0) {
             const char *e = getenv("GN_BATCH_KERNEL");
             const int only = e && *e ? atoi(e) : 0;
-            if (only != 0 && only != 1 && only != 3 && only != 4) fail(GN_EINVAL, "GN_BATCH_KERNEL must be 1, 3 or 4");
+            if (only != 0 && only != 1 && only != 3 && only != 4 && only != 5)
+                fail(GN_EINVAL, "GN_BATCH_KERNEL must be 1, 3, 4 or 5");
             if (only >= 3 && !b->staged_ok) fail(GN_EINVAL, "the staged batch kernel cannot hold this batch");
             if (b->model != GN_MODEL_FHN && only == 1) fail(GN_EINVAL, "spiking batches run the staged batch kernel");
             if (only == 4)
                 set_shape(b, kStaged, true, std::max(1, lanes_env()));  // the staged form with L2 blocking, untimed
+            else if (only == 5)
+                set_shape(b, kLanes, true, std::max(1, lanes_env()));   // its persistent lanes schedule, untimed
             else
-                autotune(b, b->model == GN_MODEL_FHN && only != 3, only != 1);
+                autotune(b, b->model == GN_MODEL_FHN && only != 3, only != 1, only == 0);
         }
-        if (b->shape == kStaged) {
+        if (b->shape == kLanes) {  // one cooperative launch per chunk, no graph
+            for (int64_t left = n_steps; left > 0;) {
+                const int n = static_cast<int>(std::min<int64_t>(left, kGraphSteps));
+                launch_steps(b, b->d_args.p, b->d_step.p, n, kLanes, b->grid, b->st_groups, b->st_lanes, b->stream,
+                             b->st_gtab.p);
+                cuda_check(gn::launch_advance(b->d_step.p, n, b->stream), "advance launch");
+                left -= n;
+            }
+        } else if (b->shape == kStaged) {
             if (!b->graph) build_graph(b, kGraphSteps);
             int64_t left = n_steps;
             for (; left >= kGraphSteps; left -= kGraphSteps)
@@ -1072,7 +1166,7 @@ gn_status gn_batch_step_static(gn_batch *b, int64_t n_steps)
         // the CTA size chosen by an earlier gn_batch_step, else the default one
         // (choosing it here would time candidates on newly allocated scratch state)
         int shape = b->shape, grid = b->grid;
-        if (shape < 0 || shape == kStaged) {
+        if (shape < 0 || shape >= kStaged) {
             int per_sm = 0, sms = 0;
             shape = 0;
             cuda_check(gn::batch_occupancy(shape, &per_sm), "occupancy");

@@ -192,6 +192,16 @@ constexpr StagedShape kBatchStagedShape = {128, 3072, 4096, 256, 0};
 cudaError_t launch_batch_staged(int model, const StepArgs *nets, const int *tile_net, int n_tiles, int k, bool packed,
                                 bool stream_edges, size_t smem_bytes, bool launch_first, cudaStream_t s);
 cudaError_t batch_staged_prepare(int model, bool packed, bool stream_edges, size_t smem_bytes, int *ctas_per_sm);
+// ... persistent, for L2-blocked groups: one cooperative launch of `grid` CTAs (all
+// resident at once) in `lanes` lanes steps each group {first tile, tiles} of
+// `groups` n_steps times (group g in lane g % lanes); counts: kLaneWords words per
+// lane, zero at launch (the lanes' barrier words); status: the batch's status word
+constexpr int kMaxBatchLanes = 8;
+constexpr int kLaneWords = 64;  // per lane: arrivals at word 0, steps complete at word 32
+cudaError_t launch_batch_lanes(int model, const StepArgs *nets, const int *tile_net, const int2 *groups, int n_groups,
+                               int lanes, int n_steps, unsigned int *counts, unsigned int *status, uint32_t limit,
+                               bool packed, int grid, size_t smem_bytes, cudaStream_t s);
+cudaError_t batch_lanes_prepare(int model, bool packed, size_t smem_bytes, int *ctas_per_sm);
 // resident kernel (k_resident.cu): one CTA holds a small network -- edges, row
 // pointers, history ring (FitzHugh-Nagumo FP32, spiking models one bit per node) and
 // node state -- in shared memory and runs n_steps steps per launch.  Byte offsets of

@@ -58,9 +58,26 @@ constexpr int kThreadsL2 = 1280;
 // without spills at 1024 (1M-node net: 0.148 vs 0.160 ms per step)
 constexpr int kThreadsPlastic = 1280;
 
+// How a tile waits, before its node update, for the previous step to be complete
+// everywhere: a launch of a chain waits for the previous grid (griddepcontrol.wait).
+struct PdlWait {
+    static constexpr bool kPdl = true;
+    __device__ __forceinline__ bool operator()() const
+    {
+        pdl_wait();
+        return true;
+    }
+};
+
 // One tile's step (the CTA's work) for network `a`; `tile` indexes a.st_tile.
-template <int kM, int T, bool kSE, bool kPacked, bool kStream, bool kEarly, bool kLaunchFirst>
-__device__ __forceinline__ void staged_tile(const StepArgs &a, const int tile, const int k)
+// `wait` is called by every thread before the node update (kEarly) and returns
+// false if the CTA must give up; `phase` is the parity of the CTA's next copy
+// completion (a kernel that runs one tile per CTA initialises the mbarrier for it;
+// a persistent one, Wait::kPdl false, initialises it once and flips `phase` per
+// use).  Returns false if the tile gave up (its rows are left untouched).
+template <int kM, int T, bool kSE, bool kPacked, bool kStream, bool kEarly, bool kLaunchFirst, class Wait = PdlWait>
+__device__ __forceinline__ bool staged_tile(const StepArgs &a, const int tile, const int k, Wait &wait,
+                                            uint32_t &phase)
 {
     // [mbarrier 16 B][keys][values (wide keys only)][entry weights][entry indices][piece sums];
     // without entry staging (kSE false) the entry arrays are absent
@@ -88,7 +105,8 @@ __device__ __forceinline__ void staged_tile(const StepArgs &a, const int tile, c
     // passed the wait, so step n - 1 is complete before step n + 1 starts.
     static_assert(!kEarly || !kPl, "plastic weights are written by the previous step");
     static_assert(kEarly || kLaunchFirst, "a CTA that waits first lets the next grid start first");
-    if constexpr (kLaunchFirst) pdl_launch_dependents();
+    static_assert(kEarly || Wait::kPdl, "a persistent kernel gathers before it waits");
+    if constexpr (kLaunchFirst && Wait::kPdl) pdl_launch_dependents();
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int4 td = __ldg(a.st_tile + tile);   // {r0, rows, u0, gathers}
     const int4 td2 = __ldg(a.st_tile2 + tile); // {s0, slices, x0, entries}
@@ -98,8 +116,12 @@ __device__ __forceinline__ void staged_tile(const StepArgs &a, const int tile, c
     if (t == 0) {
         s_fail = 0;
         if (bytes) {
-            mbar_init(bar, 1);
-            fence_barrier_init();
+            if constexpr (Wait::kPdl) {
+                mbar_init(bar, 1);
+                fence_barrier_init();
+            } else {
+                fence_async_shared();  // the previous tile's reads and writes of shared memory come first
+            }
             mbar_arrive_expect_tx(bar, bytes);
             const char *keys = static_cast<const char *>(a.st_ukey) + static_cast<size_t>(td.z) * (kPacked ? 4 : 8);
             // a stream larger than L2 is read once per step: evict it first
@@ -128,7 +150,7 @@ __device__ __forceinline__ void staged_tile(const StepArgs &a, const int tile, c
     int2 sd0 = make_int2(0, 0);
     if (warp < td2.y) sd0 = __ldg(a.st_slice + td2.x + warp);
 
-    if constexpr (!kEarly) pdl_wait();
+    if constexpr (!kEarly) wait();
     const int64_t n = *a.d_step + k;  // the step counter changes only between graphs
     float v = 0.0f;
     float2 wc = make_float2(0.0f, 0.0f);
@@ -145,13 +167,14 @@ __device__ __forceinline__ void staged_tile(const StepArgs &a, const int tile, c
         if (a.bg_thr) cnt0 = a.bgc[r];
     };
     if constexpr (!kEarly) load_own();
-    if (t == 0 && bytes && !mbar_wait_bounded(bar, 0, a.wait_limit)) {
+    if (t == 0 && bytes && !mbar_wait_bounded(bar, phase, a.wait_limit)) {
         atomicOr(a.status, kStatusTimeout);
         s_fail = 1;
-        mbar_wait_bounded(bar, 0, kDefaultWaitLimit);  // the copies must land before the CTA leaves
+        mbar_wait_bounded(bar, phase, kDefaultWaitLimit);  // the copies must land before the CTA leaves
     }
+    if (bytes) phase ^= 1u;
     __syncthreads();
-    if (s_fail) return;
+    if (s_fail) return false;
 
     // 1. the tile's distinct history values, copied asynchronously straight into
     // shared memory (packed keys are overwritten in place: a thread reads key u
@@ -246,8 +269,8 @@ __device__ __forceinline__ void staged_tile(const StepArgs &a, const int tile, c
 
     // 3. row sums and the node update
     if constexpr (kEarly) {
-        pdl_wait();
-        if constexpr (!kLaunchFirst) pdl_launch_dependents();
+        if (!wait()) return false;
+        if constexpr (!kLaunchFirst && Wait::kPdl) pdl_launch_dependents();
         load_own();
     }
     if (own) {
@@ -271,13 +294,16 @@ __device__ __forceinline__ void staged_tile(const StepArgs &a, const int tile, c
         else
             psc_finish(a, r, rp0, S);
     }
+    return true;
 }
 
 template <int kM, int T, bool kSE, bool kPacked, bool kStream, bool kEarly>
 __global__ void __launch_bounds__(T, (kSE ? kThreadsSE : (kM & kPlastic) ? kThreadsPlastic : kThreadsL2) / T)
     k_step_staged(const StepArgs a, const int k)
 {
-    staged_tile<kM, T, kSE, kPacked, kStream, kEarly, true>(a, blockIdx.x, k);
+    PdlWait w;
+    uint32_t phase = 0;
+    staged_tile<kM, T, kSE, kPacked, kStream, kEarly, true>(a, blockIdx.x, k, w, phase);
 }
 
 // Batched form, one launch per step over the tiles of every member network (all of
@@ -293,7 +319,129 @@ __global__ void __launch_bounds__(T, kThreadsL2 / T) k_batch_staged(const StepAr
     uint32_t *dst = reinterpret_cast<uint32_t *>(&s_a);
     for (int i = threadIdx.x; i < static_cast<int>(sizeof(StepArgs) / 4); i += T) dst[i] = __ldg(src + i);
     __syncthreads();
-    staged_tile<kM, T, false, kPacked, kStream, true, kLaunchFirst>(s_a, blockIdx.x, k);
+    PdlWait w;
+    uint32_t phase = 0;
+    staged_tile<kM, T, false, kPacked, kStream, true, kLaunchFirst>(s_a, blockIdx.x, k, w, phase);
+}
+
+// The lanes schedule of the batched form's L2 blocking, persistent: one cooperative
+// launch steps every group n_steps times.  CTA b works in lane b % lanes and takes
+// tiles b / lanes, b / lanes + C, ... of each group of its lane (C: the lane's
+// CTAs); a lane runs its groups one after another (groups g = lane, lane + lanes,
+// ...), each through all the steps, so a group's data stays in L2 across them.
+// A lane's CTAs meet at a counting barrier in global memory (two words of their
+// own 128-byte lines: arrivals, and steps complete).  After its tiles' node
+// updates of the lane's j-th step (counted over its groups) a CTA adds 1 to the
+// arrivals; the CTA whose add completes the step's C arrivals sets the steps
+// complete to j + 1.  A CTA's node updates of step j wait until steps complete
+// >= j (slot n + 1, which step n writes, is read by step n - 1's longest delay).
+// Its gathers do not wait: they read history slots n - D, D >= 1, written by step
+// n - 2 or earlier, which the CTA's own wait in step n - 1 covered -- the argument
+// of the early gathers in a chain of launches.  A CTA without a tile in a step
+// still waits for step j - 1 before it arrives, so no CTA is two arrivals ahead of
+// another and the C-th arrival of a step is the last one of that step.  Memory
+// order: fence then add (release), the last adder's fence then store; waits poll
+// with relaxed loads and fence once the value is seen (acquire).  Waits are
+// bounded: after `limit` polls, or once another CTA has set kStatusTimeout, the
+// CTA gives up and returns.
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+__device__ __forceinline__ unsigned int ld_relaxed(const unsigned int *p)
+{
+    unsigned int v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed(unsigned int *p, unsigned int v)
+{
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Thread 0's wait until `done` reaches `target`: 1 on success, 0 on giving up.
+__device__ __forceinline__ int lane_poll(const unsigned int *done, unsigned int target, uint32_t limit,
+                                         unsigned int *status)
+{
+    for (uint32_t i = 0; i < limit; ++i) {
+        if (ld_relaxed(done) >= target) {
+            fence_acq_rel();
+            return 1;
+        }
+        if ((i & 15u) == 15u && (ld_relaxed(status) & kStatusTimeout)) return 0;
+        __nanosleep(64);
+    }
+    atomicOr(status, kStatusTimeout);
+    return 0;
+}
+
+// The wait of one step (at most one poll loop per step; `done_here` is the thread's
+// copy of its outcome).
+struct LaneWait {
+    static constexpr bool kPdl = false;
+    const unsigned int *done;
+    unsigned int target;
+    uint32_t limit;
+    unsigned int *status;
+    int *s_ok;
+    bool done_here;
+    __device__ __forceinline__ bool operator()()
+    {
+        if (done_here) return true;
+        if (threadIdx.x == 0) *s_ok = target == 0 ? 1 : lane_poll(done, target, limit, status);
+        __syncthreads();
+        done_here = *s_ok != 0;
+        return done_here;
+    }
+};
+
+template <int kM, int T, bool kPacked>
+__global__ void __launch_bounds__(T, kThreadsL2 / T)
+    k_batch_lanes(const StepArgs *__restrict__ nets, const int *__restrict__ tile_net, const int2 *__restrict__ groups,
+                  const int n_groups, const int lanes, const int n_steps, unsigned int *__restrict__ counts,
+                  unsigned int *status, const uint32_t limit)
+{
+    extern __shared__ __align__(128) unsigned char s_raw[];
+    __shared__ StepArgs s_a;
+    __shared__ int s_ok;
+    const int lane = static_cast<int>(blockIdx.x) % lanes, me = static_cast<int>(blockIdx.x) / lanes;
+    const unsigned int C = (gridDim.x - static_cast<unsigned int>(lane) + lanes - 1) / lanes;
+    unsigned int *arrivals = counts + kLaneWords * lane;
+    unsigned int *done = arrivals + 32;
+    if (threadIdx.x == 0) {
+        mbar_init(reinterpret_cast<uint64_t *>(s_raw), 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    int cur = -1;
+    unsigned int j = 0;
+    for (int g = lane; g < n_groups; g += lanes) {
+        const int2 gr = __ldg(groups + g);  // {first tile, tiles}
+        for (int k = 0; k < n_steps; ++k, ++j) {
+            LaneWait w{done, j, limit, status, &s_ok, false};
+            for (int i = me; i < gr.y; i += static_cast<int>(C)) {
+                __syncthreads();  // the previous tile is done with shared memory
+                const int net = __ldg(tile_net + gr.x + i);
+                if (net != cur) {
+                    const uint32_t *src = reinterpret_cast<const uint32_t *>(nets + net);
+                    uint32_t *dst = reinterpret_cast<uint32_t *>(&s_a);
+                    for (int x = threadIdx.x; x < static_cast<int>(sizeof(StepArgs) / 4); x += T) dst[x] = __ldg(src + x);
+                    __syncthreads();
+                    cur = net;
+                }
+                if (!staged_tile<kM, T, false, kPacked, false, true, false>(s_a, i, k, w, phase)) return;
+            }
+            if (!w()) return;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                fence_acq_rel();
+                if (atomicAdd(arrivals, 1u) == (j + 1) * C - 1) {
+                    fence_acq_rel();
+                    st_relaxed(done, j + 1);
+                }
+            }
+        }
+    }
 }
 
 template <int kM, int T, bool kSE, bool kPacked, bool kStream, bool kEarly>
@@ -451,7 +599,62 @@ cudaError_t batch_staged(bool launch, int model, bool first, const StepArgs *net
     });
 }
 
+template <int kM, bool kPacked>
+cudaError_t batch_lanes_t(bool launch, const StepArgs *nets, const int *tile_net, const int2 *groups, int n_groups,
+                          int lanes, int n_steps, unsigned int *counts, unsigned int *status, uint32_t limit, int grid,
+                          size_t smem, cudaStream_t s, int *per_sm)
+{
+    constexpr int T = kBatchStagedShape.threads;
+    auto *fn = k_batch_lanes<kM, T, kPacked>;
+    if (!launch) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess || !per_sm) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, T, smem);
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(grid));
+    cfg.blockDim = dim3(T);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;  // every CTA resident at once: the lane barriers need it
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fn, nets, tile_net, groups, n_groups, lanes, n_steps, counts, status, limit);
+}
+
+cudaError_t batch_lanes(bool launch, int model, const StepArgs *nets, const int *tile_net, const int2 *groups,
+                        int n_groups, int lanes, int n_steps, unsigned int *counts, unsigned int *status,
+                        uint32_t limit, bool packed, int grid, size_t smem, cudaStream_t s, int *per_sm)
+{
+    return with_model(model, [&](auto m) {
+        constexpr int M = decltype(m)::value;
+        return packed ? batch_lanes_t<M, true>(launch, nets, tile_net, groups, n_groups, lanes, n_steps, counts,
+                                               status, limit, grid, smem, s, per_sm)
+                      : batch_lanes_t<M, false>(launch, nets, tile_net, groups, n_groups, lanes, n_steps, counts,
+                                                status, limit, grid, smem, s, per_sm);
+    });
+}
+
 }  // namespace
+
+cudaError_t launch_batch_lanes(int model, const StepArgs *nets, const int *tile_net, const int2 *groups, int n_groups,
+                               int lanes, int n_steps, unsigned int *counts, unsigned int *status, uint32_t limit,
+                               bool packed, int grid, size_t smem_bytes, cudaStream_t s)
+{
+    if (n_steps <= 0 || n_groups <= 0) return cudaSuccess;
+    if (lanes < 1 || lanes > kMaxBatchLanes || grid < lanes) return cudaErrorInvalidValue;
+    return batch_lanes(true, model, nets, tile_net, groups, n_groups, lanes, n_steps, counts, status, limit, packed,
+                       grid, smem_bytes, s, nullptr);
+}
+
+cudaError_t batch_lanes_prepare(int model, bool packed, size_t smem_bytes, int *ctas_per_sm)
+{
+    return batch_lanes(false, model, nullptr, nullptr, nullptr, 0, 1, 0, nullptr, nullptr, 0, packed, 0, smem_bytes,
+                       nullptr, ctas_per_sm);
+}
 
 cudaError_t launch_batch_staged(int model, const StepArgs *nets, const int *tile_net, int n_tiles, int k, bool packed,
                                 bool stream_edges, size_t smem_bytes, bool launch_first, cudaStream_t s)

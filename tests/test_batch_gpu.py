@@ -12,11 +12,12 @@ from parity import ratio
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(params=[1, 3, 4], ids=["persistent", "staged", "staged_l2_groups"], autouse=True)
+@pytest.fixture(params=[1, 3, 4, 5], ids=["persistent", "staged", "staged_l2_groups", "staged_lanes"], autouse=True)
 def batch_kernel(request, monkeypatch):
     """Every test runs with each batch kernel (GN_BATCH_KERNEL); the staged form
     also with L2 blocking in two lanes sharing a 512 KB budget, which cuts these
-    small members into groups of one to a few networks."""
+    small members into groups of one to a few networks -- as a chain of launches
+    per lane (4) and as one persistent launch of both lanes (5)."""
     monkeypatch.setenv("GN_BATCH_KERNEL", str(request.param))
     monkeypatch.setenv("GN_BATCH_GROUP_KB", "512")
     monkeypatch.setenv("GN_BATCH_LANES", "2")
@@ -38,12 +39,12 @@ def test_batch_equals_single_networks_bit_for_bit(batch_kernel):
     b.gn_batch_step(500)
     info = b.gn_batch_get_info()
     assert info["n_nets"] == 24 and info["step"] == 2000 and info["cta_threads"] in (128, 256, 512)
-    assert info["step_kernel"] == min(batch_kernel, 3)
-    assert (info["step_groups"] > 1) == (batch_kernel == 4), info
-    assert info["step_lanes"] == (2 if batch_kernel == 4 else 1 if batch_kernel == 3 else 0), info
+    assert info["step_kernel"] == {1: 1, 3: 3, 4: 3, 5: 5}[batch_kernel]
+    assert (info["step_groups"] > 1) == (batch_kernel >= 4), info
+    assert info["step_lanes"] == (2 if batch_kernel >= 4 else 1 if batch_kernel == 3 else 0), info
     n_blocks = [b.gn_batch_get_net_info(i)["n_blocks"] for i in range(24)]
     assert min(n_blocks) >= 1
-    if batch_kernel != 1:  # the staged grid is every member's tiles
+    if batch_kernel in (3, 4):  # the staged grid is every member's tiles
         assert sum(n_blocks) == info["grid"], (n_blocks, info)
     for i in range(0, 24, 3):
         net = geonet.Net(specs[i], step_kernel=1)

@@ -17,14 +17,15 @@ def _members(model):
     return [netgen.test_set_hh(sp) if model == "hh" else netgen.test_set_izh(sp) for sp in nets]
 
 
-@pytest.mark.parametrize("schedule", ["timed", "l2_groups"])
+@pytest.mark.parametrize("schedule", ["timed", "l2_groups", "lanes"])
 @pytest.mark.parametrize("model", ["izh", "hh"])
 def test_members_equal_their_networks_run_alone(model, schedule, monkeypatch):
-    """Either schedule of the staged form: the one the first step times (these
+    """Each schedule of the staged form: the one the first step times (these
     members fit one group), or L2 blocking in three lanes sharing a 48 KB budget
-    (groups of one or two members, each running 64-step chunks)."""
-    if schedule == "l2_groups":
-        monkeypatch.setenv("GN_BATCH_KERNEL", "4")
+    (groups of one or two members, each running 64-step chunks) as chains of
+    launches or as one persistent launch."""
+    if schedule != "timed":
+        monkeypatch.setenv("GN_BATCH_KERNEL", "4" if schedule == "l2_groups" else "5")
         monkeypatch.setenv("GN_BATCH_GROUP_KB", "48")
         monkeypatch.setenv("GN_BATCH_LANES", "3")
     specs = _members(model)
@@ -32,7 +33,8 @@ def test_members_equal_their_networks_run_alone(model, schedule, monkeypatch):
     b = geonet.Batch(specs)
     b.gn_batch_step(steps)
     info = b.gn_batch_get_info()
-    assert info["step_kernel"] == 3 and (info["step_groups"] > 1) == (schedule == "l2_groups"), info
+    assert info["step_kernel"] in ((5,) if schedule == "lanes" else (3,) if schedule == "l2_groups" else (3, 5)), info
+    assert (info["step_groups"] > 1) == (schedule != "timed"), info
     n_spikes = 0
     for i, sp in enumerate(specs):
         net = geonet.Net(sp)
@@ -94,7 +96,7 @@ def test_a_batch_larger_than_the_device_launches_first_bit_identically(monkeypat
     # each group launches first), and in four lanes with groups of a few hundred
     # tiles (fewer: each waits first)
     for kernel, early, group_kb, lanes in (("3", "1", "0", "1"), ("3", "0", "0", "1"), ("4", "1", "131072", "1"),
-                                           ("4", "1", "24576", "4")):
+                                           ("4", "1", "24576", "4"), ("5", "1", "24576", "4")):
         monkeypatch.setenv("GN_BATCH_KERNEL", kernel)
         monkeypatch.setenv("GN_STAGED_EARLY", early)
         monkeypatch.setenv("GN_BATCH_GROUP_KB", group_kb)
@@ -102,7 +104,7 @@ def test_a_batch_larger_than_the_device_launches_first_bit_identically(monkeypat
         b = geonet.Batch(specs)
         b.gn_batch_step(300)
         info = b.gn_batch_get_info()
-        assert info["step_kernel"] == 3 and (info["step_groups"] > 1) == (kernel == "4"), info
+        assert info["step_kernel"] == (5 if kernel == "5" else 3) and (info["step_groups"] > 1) == (kernel != "3"), info
         out.append([(b.gn_batch_get_state(i), b.gn_batch_get_history(i, 4)) for i in range(0, 700, 37)])
         b.gn_batch_destroy()
     for other in out[1:]:
