@@ -741,6 +741,9 @@ def main():
         uuid = None
     sampler = ClockSampler(uuid)
     time.sleep(0.3)
+    # the W untimed steps again, right before the timed ones: the GPU idled while the
+    # clock sampler started, and its first steps after an idle run below full clock
+    net.gn_step(args.warmup)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     barrier()

@@ -294,11 +294,13 @@ cudaError_t mlp_launch_tile(const MlpBuffers &b, const float *X, const int64_t *
                             const float *y, int B, int Bp, float *p_out, cudaStream_t s);
 cudaError_t mlp_launch_wgrad(const MlpBuffers &b, int Bp, cudaStream_t s);
 // gradients into b.grads and the loss sum into b.loss_sum; with adamw also the AdamW
-// step (bias corrections bc1, bc2, or bc_table[2 cursor + {0, 1}]) and the weight images
+// step (bias corrections bc1, bc2, or bc_table[2 cursor + {0, 1}]) and the weight
+// images; with `losses` (a replayed epoch) also the step's mean loss over B rows to
+// losses[cursor] and the cursor moved on (`ticket`: a zeroed counter of the launch)
 cudaError_t mlp_launch_update(const MlpBuffers &b, int Bp, bool adamw, float lr, float wd, float bc1, float bc2,
-                              const float *bc_table, const int64_t *cursor, cudaStream_t s);
+                              const float *bc_table, int64_t *cursor, float *losses, unsigned int *ticket, int B,
+                              cudaStream_t s);
 cudaError_t mlp_launch_refresh(const MlpBuffers &b, cudaStream_t s);
-cudaError_t mlp_launch_epoch_tail(const float *loss_sum, int B, int64_t *cursor, float *losses, cudaStream_t s);
 
 cudaError_t launch_delay(int64_t n_edges, int32_t dim, const double *pos, const int32_t *src,
                          const int32_t *dst, const double *speed, double speed_scalar, double dt_ms,

@@ -17,8 +17,8 @@
 //   k_wgrad  dW2 = H1^T dH2 and dW1^T = dH1^T X split over the batch (fixed-order
 //            partials), operands brought in by bulk asynchronous copies;
 //   k_update the partials summed in order, AdamW on the FP32 masters, and the BF16
-//            weight images the tile kernel streams;
-//   k_epoch_tail (replayed epochs) the loss of the step and the batch cursor.
+//            weight images the tile kernel streams; in a replayed epoch its last
+//            CTA also records the step's loss and moves the batch cursor on.
 //
 // Shared-memory operand layout (tcgen05 K-major, 128-byte swizzle): a matrix of R rows x
 // 64 K-elements is a chunk of 128-byte rows; element (r, c) sits at byte r 128 +
@@ -670,7 +670,10 @@ struct UpdateArgs {
     float *w, *m, *v;
     float lr, beta1, beta2, eps, wd, bc1, bc2;
     const float *bc_table;   // replayed epochs: bias corrections [2 cursor + {0, 1}]
-    const int64_t *cursor;
+    int64_t *cursor;
+    float *losses;           // replayed epochs: the step's mean loss to losses[cursor] (null: single steps)
+    unsigned int *ticket;    // ... counted CTAs (zero between steps)
+    int B;
     uint8_t *wimg;           // the BF16 images of W1t, W2t, W2b
 };
 
@@ -693,48 +696,57 @@ __device__ __forceinline__ void put_weight(uint8_t *wimg, bool is_w2, int k, int
     }
 }
 
-__global__ void k_update(const UpdateArgs g)
+// sum_{z < n} p[z * stride] in order z = 0, 1, ...: the loads of 32 partials are
+// issued together, then added one after another (the order a plain loop has)
+__device__ __forceinline__ float sum_partials(const float *p, int n, int64_t stride)
 {
-    pdl_trigger();
-    pdl_wait();  // the partials of the tile and weight-gradient kernels
-    const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-    if (i > g.n_params) return;
-    if (i == g.n_params) {
-        float s = 0.0f;
-        for (int tl = 0; tl < g.n_tiles; ++tl) s += g.part_head[static_cast<int64_t>(tl) * (2 * kH + 2) + 2 * kH + 1];
-        *g.loss_sum = s;
-        return;
+    float s = 0.0f;
+    int z0 = 0;
+    for (; z0 + 32 <= n; z0 += 32) {
+        float x[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) x[j] = __ldg(p + static_cast<int64_t>(z0 + j) * stride);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) s += x[j];
     }
+    for (; z0 < n; ++z0) s += __ldg(p + static_cast<int64_t>(z0) * stride);
+    return s;
+}
+
+// Parameter i's gradient from the partials (and its AdamW step); `cur` is the batch
+// cursor of a replayed epoch.
+__device__ __forceinline__ void update_param(const UpdateArgs &g, int64_t i, int64_t cur)
+{
     float gr = 0.0f;
     bool is_w = false, is_w2 = false;
     int wk = 0, wn = 0;
     if (i < g.off_b1) {  // W1[k][n]
         wk = static_cast<int>(i / kH);
         wn = static_cast<int>(i % kH);
-        for (int z = 0; z < g.n_splits; ++z) gr += g.part_w1[static_cast<int64_t>(z) * kH * kKP + i];
+        gr = sum_partials(g.part_w1 + i, g.n_splits, static_cast<int64_t>(kH) * kKP);
         is_w = true;
     } else if (i < g.off_W2) {  // b1
         const int c = static_cast<int>(i - g.off_b1);
-        for (int tl = 0; tl < g.n_tiles; ++tl) gr += g.part_b1[static_cast<int64_t>(tl) * kH + c];
+        gr = sum_partials(g.part_b1 + c, g.n_tiles, kH);
     } else if (i < g.off_b2) {  // W2[k][n]
         const int64_t j = i - g.off_W2;
         wk = static_cast<int>(j / kH);
         wn = static_cast<int>(j % kH);
-        for (int z = 0; z < g.n_splits; ++z) gr += g.part_w2[static_cast<int64_t>(z) * kH * kH + j];
+        gr = sum_partials(g.part_w2 + j, g.n_splits, static_cast<int64_t>(kH) * kH);
         is_w = is_w2 = true;
     } else {  // b2, w3, b3 from the tile partials [dw3 | db2 | db3 | loss]
         int col;
         if (i < g.off_w3) col = kH + static_cast<int>(i - g.off_b2);
         else if (i < g.off_b3) col = static_cast<int>(i - g.off_w3);
         else col = 2 * kH;
-        for (int tl = 0; tl < g.n_tiles; ++tl) gr += g.part_head[static_cast<int64_t>(tl) * (2 * kH + 2) + col];
+        gr = sum_partials(g.part_head + col, g.n_tiles, 2 * kH + 2);
     }
     g.grads[i] = gr;
     if (!g.w) return;
     float bc1 = g.bc1, bc2 = g.bc2;
     if (g.bc_table) {
-        bc1 = g.bc_table[2 * *g.cursor];
-        bc2 = g.bc_table[2 * *g.cursor + 1];
+        bc1 = g.bc_table[2 * cur];
+        bc2 = g.bc_table[2 * cur + 1];
     }
     const float mi = g.beta1 * g.m[i] + (1.0f - g.beta1) * gr;
     const float vi = g.beta2 * g.v[i] + (1.0f - g.beta2) * gr * gr;
@@ -746,6 +758,41 @@ __global__ void k_update(const UpdateArgs g)
     if (is_w) put_weight(g.wimg, is_w2, wk, wn, wv);
 }
 
+// One thread per parameter; the loss sum by thread n_params, or, in a replayed epoch,
+// by the CTA that finishes last (a ticket counter): it writes the step's mean loss to
+// losses[cursor] and advances the cursor once every CTA has read it.
+__global__ void k_update(const UpdateArgs g)
+{
+    __shared__ int64_t s_cur;
+    __shared__ int s_last;
+    pdl_trigger();
+    pdl_wait();  // the partials of the tile and weight-gradient kernels
+    const bool epoch = g.losses != nullptr;
+    if (epoch) {
+        if (threadIdx.x == 0) s_cur = *g.cursor;
+        __syncthreads();
+    }
+    const int64_t cur = epoch ? s_cur : (g.cursor ? *g.cursor : 0);
+    const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (i < g.n_params) update_param(g, i, cur);
+    else if (i == g.n_params && !epoch) *g.loss_sum = sum_partials(g.part_head + 2 * kH + 1, g.n_tiles, 2 * kH + 2);
+    if (!epoch) return;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(g.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        const float loss = sum_partials(g.part_head + 2 * kH + 1, g.n_tiles, 2 * kH + 2);
+        *g.loss_sum = loss;
+        g.losses[cur] = loss / static_cast<float>(g.B);
+        *g.cursor = cur + 1;
+        *g.ticket = 0;
+    }
+}
+
 // All BF16 weight images from the FP32 masters, padding (W1 columns k >= in_dim) zero.
 __global__ void k_refresh(const float *__restrict__ W1, int in_dim, const float *__restrict__ W2, uint8_t *wimg)
 {
@@ -755,16 +802,6 @@ __global__ void k_refresh(const float *__restrict__ W1, int in_dim, const float 
         put_weight(wimg, false, k, n, k < in_dim ? W1[k * kH + n] : 0.0f);
     }
     if (i < kH * kH) put_weight(wimg, true, i / kH, i % kH, W2[i]);
-}
-
-// End of a replayed training step: its mean loss to losses[cursor], then the
-// cursor moves to the next batch.
-__global__ void k_epoch_tail(const float *__restrict__ loss_sum, int B, int64_t *cursor, float *__restrict__ losses)
-{
-    pdl_trigger();
-    pdl_wait();
-    losses[*cursor] = *loss_sum / static_cast<float>(B);
-    *cursor += 1;
 }
 
 }  // namespace
@@ -851,7 +888,8 @@ cudaError_t mlp_launch_wgrad(const MlpBuffers &b, int Bp, cudaStream_t s)
 }
 
 cudaError_t mlp_launch_update(const MlpBuffers &b, int Bp, bool adamw, float lr, float wd, float bc1, float bc2,
-                              const float *bc_table, const int64_t *cursor, cudaStream_t s)
+                              const float *bc_table, int64_t *cursor, float *losses, unsigned int *ticket, int B,
+                              cudaStream_t s)
 {
     UpdateArgs g{};
     g.part_w2 = b.part_w2;
@@ -884,6 +922,9 @@ cudaError_t mlp_launch_update(const MlpBuffers &b, int Bp, bool adamw, float lr,
     g.bc2 = bc2;
     g.bc_table = bc_table;
     g.cursor = cursor;
+    g.losses = losses;
+    g.ticket = ticket;
+    g.B = B;
     g.wimg = static_cast<uint8_t *>(b.wimg);
     const int64_t n = b.n_params + 1;
     return launch_pdl(k_update, dim3(static_cast<unsigned>((n + 255) / 256)), dim3(256), 0, s, g);
@@ -896,9 +937,5 @@ cudaError_t mlp_launch_refresh(const MlpBuffers &b, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t mlp_launch_epoch_tail(const float *loss_sum, int B, int64_t *cursor, float *losses, cudaStream_t s)
-{
-    return launch_pdl(k_epoch_tail, dim3(1), dim3(1), 0, s, loss_sum, B, cursor, losses);
-}
 
 }  // namespace gn

@@ -4,10 +4,11 @@
 //
 // Parameters, gradients and Adam moments are packed FP32 buffers in one layout,
 // [W1 (in x 256) | b1 | W2 (256 x 256) | b2 | w3 | b3]; the BF16 weight images the
-// tile kernel streams are rewritten by every AdamW step.  A training step is four
-// launches: the tile kernel (forward, loss, dH2, dH1), the weight-gradient GEMMs,
-// the update (fixed-order sums, AdamW, images) and, in a replayed epoch, the loss
-// of the step with the batch cursor.
+// tile kernel streams are rewritten by every AdamW step.  A training step is three
+// launches: the tile kernel (forward, loss, dH2, dH1), the weight-gradient GEMMs and
+// the update (fixed-order sums, AdamW, images; in a replayed epoch also the loss of
+// the step and the batch cursor).  A replayed epoch runs graphs of 16 steps, the
+// launches chained by programmatic dependent launch across the steps.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -23,6 +24,7 @@ using gnrt::guarded;
 namespace {
 constexpr int H = gn::kMlpHidden;
 constexpr int kTileRows = 128;  // batch padding granularity (rows of one tile)
+constexpr int kEpochGraphSteps = 16;  // training steps per replayed graph of an epoch
 }  // namespace
 
 struct gn_mlp {
@@ -41,8 +43,11 @@ struct gn_mlp {
     DevArray<unsigned int> status;  // kStatusTimeout when a kernel's bounded wait gave up
     // replayed training epochs: batch cursor, bias-correction table, per-step losses
     DevArray<int64_t> ep_cursor;
+    DevArray<unsigned int> ep_ticket;  // the update kernel's count of finished CTAs (zero between steps)
     DevArray<float> ep_bc, ep_losses;
-    cudaGraphExec_t ep_graph = nullptr;
+    // kEpochGraphSteps steps chained in one graph (programmatic dependent launch across
+    // the steps too), and one step for the remainder
+    cudaGraphExec_t ep_graph = nullptr, ep_graph1 = nullptr;
     struct EpochKey {
         const void *X, *y, *idx;
         int B;
@@ -87,7 +92,9 @@ struct gn_mlp {
     ~gn_mlp()
     {
         if (ep_graph) cudaGraphExecDestroy(ep_graph);
+        if (ep_graph1) cudaGraphExecDestroy(ep_graph1);
         ep_cursor.release();
+        ep_ticket.release();
         ep_bc.release();
         ep_losses.release();
         status.release();
@@ -122,15 +129,18 @@ int padded(int B) { return (B + kTileRows - 1) / kTileRows * kTileRows; }
 // (and the loss sum on the device), then with `adamw` the AdamW step.  With a device
 // batch cursor the rows are idx[cursor B + b] and the bias corrections come from
 // bc_table.
-void run(gn_mlp *m, const float *X, const float *y, const int64_t *idx, int B, float *p_out, const int64_t *cursor,
-         bool adamw, float lr, float wd, float bc1, float bc2, const float *bc_table, cudaStream_t s)
+void run(gn_mlp *m, const float *X, const float *y, const int64_t *idx, int B, float *p_out, int64_t *cursor,
+         bool adamw, float lr, float wd, float bc1, float bc2, const float *bc_table, cudaStream_t s,
+         float *losses = nullptr)
 {
     const int Bp = padded(B);
     const gn::MlpBuffers b = m->buffers();
     cuda_check(gn::mlp_launch_tile(b, X, idx, cursor, y, B, Bp, p_out, s), "MLP tile kernel");
     if (!y) return;
     cuda_check(gn::mlp_launch_wgrad(b, Bp, s), "MLP weight gradients");
-    cuda_check(gn::mlp_launch_update(b, Bp, adamw, lr, wd, bc1, bc2, bc_table, cursor, s), "MLP update");
+    cuda_check(gn::mlp_launch_update(b, Bp, adamw, lr, wd, bc1, bc2, bc_table, cursor, losses,
+                                     losses ? m->ep_ticket.p : nullptr, B, s),
+               "MLP update");
 }
 
 float read_loss(gn_mlp *m, int B)
@@ -292,25 +302,33 @@ gn_status gn_mlp_train_epoch(gn_mlp *m, const float *X, const float *y, const in
             m->ep_bc.alloc(bc.size(), &m->bytes);
             m->ep_losses.alloc(n_batches, &m->bytes);
             if (!m->ep_cursor.p) m->ep_cursor.alloc(1, &m->bytes);
+            if (!m->ep_ticket.p) {
+                m->ep_ticket.alloc(1, &m->bytes);
+                cuda_check(cudaMemset(m->ep_ticket.p, 0, 4), "memset");
+            }
         }
         cuda_check(cudaMemcpyAsync(m->ep_bc.p, bc.data(), bc.size() * 4, cudaMemcpyHostToDevice, m->stream), "H2D");
         cuda_check(cudaMemsetAsync(m->ep_cursor.p, 0, 8, m->stream), "memset");
         const gn_mlp::EpochKey key{X, y, idx, B, lr, weight_decay, m->ep_bc.p, m->ep_losses.p};
-        if (!m->ep_graph || !(key == m->ep_key)) {
-            if (m->ep_graph) {
-                cudaGraphExecDestroy(m->ep_graph);
-                m->ep_graph = nullptr;
-            }
-            // one training step, the batch picked by the device cursor
+        if (!(key == m->ep_key)) {
+            for (cudaGraphExec_t *ge : {&m->ep_graph, &m->ep_graph1})
+                if (*ge) {
+                    cudaGraphExecDestroy(*ge);
+                    *ge = nullptr;
+                }
+        }
+        // `steps` training steps, each taking the batch the device cursor points at
+        auto capture = [&](int steps) {
             cudaStream_t cs;
             cuda_check(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "cudaStreamCreate");
             cudaGraph_t g = nullptr;
+            cudaGraphExec_t ge = nullptr;
             cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
                 try {
-                    run(m, X, y, idx, B, m->p.p, m->ep_cursor.p, true, lr, weight_decay, 1.0f, 1.0f, m->ep_bc.p, cs);
-                    cuda_check(gn::mlp_launch_epoch_tail(m->loss_sum.p, B, m->ep_cursor.p, m->ep_losses.p, cs),
-                               "epoch tail");
+                    for (int j = 0; j < steps; ++j)
+                        run(m, X, y, idx, B, m->p.p, m->ep_cursor.p, true, lr, weight_decay, 1.0f, 1.0f, m->ep_bc.p,
+                            cs, m->ep_losses.p);
                 } catch (...) {
                     cudaStreamEndCapture(cs, &g);
                     if (g) cudaGraphDestroy(g);
@@ -319,13 +337,18 @@ gn_status gn_mlp_train_epoch(gn_mlp *m, const float *X, const float *y, const in
                 }
                 e = cudaStreamEndCapture(cs, &g);
             }
-            if (e == cudaSuccess) e = cudaGraphInstantiate(&m->ep_graph, g, 0);
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
             if (g) cudaGraphDestroy(g);
             cudaStreamDestroy(cs);
-            cuda_check(e, "graph capture of the training step");
-            m->ep_key = key;
-        }
-        for (int32_t j = 0; j < n_batches; ++j) cuda_check(cudaGraphLaunch(m->ep_graph, m->stream), "cudaGraphLaunch");
+            cuda_check(e, "graph capture of the training steps");
+            return ge;
+        };
+        const int32_t full = n_batches / kEpochGraphSteps, rest = n_batches % kEpochGraphSteps;
+        if (full && !m->ep_graph) m->ep_graph = capture(kEpochGraphSteps);
+        if (rest && !m->ep_graph1) m->ep_graph1 = capture(1);
+        m->ep_key = key;
+        for (int32_t j = 0; j < full; ++j) cuda_check(cudaGraphLaunch(m->ep_graph, m->stream), "cudaGraphLaunch");
+        for (int32_t j = 0; j < rest; ++j) cuda_check(cudaGraphLaunch(m->ep_graph1, m->stream), "cudaGraphLaunch");
         m->adam_t += n_batches;
         if (losses) {
             cuda_check(cudaMemcpyAsync(losses, m->ep_losses.p, static_cast<size_t>(n_batches) * 4,
