@@ -253,6 +253,51 @@ def cpu_baseline(spec, steps: int):
                 seconds=dt)
 
 
+def _oracle_copy(name: str, steps: int, barrier, out):
+    """One core's copy of the cpu_baseline sample, in a spawned process: the network
+    from the workload cache, its delays, then (all copies together) the timed steps."""
+    import oracle
+    spec = workload(name, 0)
+    D = oracle.net_delays(spec)
+    barrier.wait(timeout=900)
+    t0 = time.perf_counter()
+    oracle.simulate(spec, steps, delay=D, want_y=False, ev_cap=1)
+    out.put((spec.n_edges * steps, time.perf_counter() - t0))
+
+
+def cpu_baseline_all_cores(name: str, spec, steps: int, bytes_per_copy: float = 4e9):
+    """The same oracle sample run as one independent copy per host core (as many as
+    the free memory holds, about 4 GB each for the 1M-node net), all copies timed
+    together: the host's aggregate oracle throughput.  The oracle itself is one
+    thread; one network is not split across cores (that would change the oracle)."""
+    import multiprocessing as mp
+    try:
+        import psutil
+        avail = psutil.virtual_memory().available
+    except Exception:
+        avail = bytes_per_copy
+    copies = max(1, min(os.cpu_count() or 1, int(avail // bytes_per_copy)))
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(copies)
+    out = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_copy, args=(name, steps, barrier, out)) for _ in range(copies)]
+    for p in procs:
+        p.start()
+    try:
+        res = [out.get(timeout=1800) for _ in range(copies)]
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.terminate()
+    units = sum(u for u, _ in res)
+    t = max(s for _, s in res)
+    return dict(value=units / t, unit=METRIC, cores=copies, kind="oracle",
+                sample=f"{copies} independent copies of the first {steps} steps of the same "
+                       f"{spec.n_nodes}-node network, one per core, timed together (edge-updates of all copies "
+                       f"over the slowest copy's time)", seconds=t)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -674,6 +719,7 @@ def main():
     ap.add_argument("--ref-steps", type=int, default=30, help="oracle steps timed by --impl reference")
     ap.add_argument("--e2e-chunk", type=int, default=1000, help="steps per host round trip in the e2e run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-all-cores", action="store_true", help="skip the one-copy-per-core oracle run")
     ap.add_argument("--obs-cap", type=int, default=4096, help="observation rows kept on the device")
     ap.add_argument("--batch-steps", type=int, default=10000, help="steps of the batched measurement")
     ap.add_argument("--loop-sample", type=int, default=32, help="networks timed by the looped comparison")
@@ -851,6 +897,9 @@ def main():
         cb = cpu_baseline(spec, args.cpu_steps)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "host",
                                                    "window_steps", "window_s_extrapolated")}
+        if not args.no_cpu_all_cores:
+            ac = cpu_baseline_all_cores(args.workload, spec, args.cpu_steps)
+            line["cpu_baseline"]["all_cores"] = {k: ac[k] for k in ("value", "unit", "cores", "kind", "sample")}
     if rank == 0:
         if args.details:
             with open(args.details, "w") as f:

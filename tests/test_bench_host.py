@@ -89,3 +89,16 @@ def test_printed_line_drops_details_and_rounds():
 
 def test_survey_bytes_are_format_independent():
     assert bench.survey_bytes(1000, 100) == pytest.approx(1000 * 14 + 100 * 36.2)
+
+
+def test_all_cores_oracle_run_times_independent_copies():
+    """The all-cores leg of cpu_baseline: one spawned copy of the plain oracle sample
+    per core (bounded by the memory allowance), the copies' edge-updates over the
+    slowest copy's time; the same network as the one-thread sample."""
+    spec = bench.workload("tiny", 0)
+    one = bench.cpu_baseline(spec, 50)
+    ac = bench.cpu_baseline_all_cores("tiny", spec, 50, bytes_per_copy=1e8)
+    assert 1 <= ac["cores"] <= (os.cpu_count() or 1)
+    assert ac["kind"] == "oracle" and ac["unit"] == one["unit"]
+    assert ac["value"] > 0 and ac["seconds"] > 0
+    assert f"{ac['cores']} independent copies" in ac["sample"]
