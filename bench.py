@@ -265,17 +265,29 @@ def _oracle_copy(name: str, steps: int, barrier, out):
     out.put((spec.n_edges * steps, time.perf_counter() - t0))
 
 
-def cpu_baseline_all_cores(name: str, spec, steps: int, bytes_per_copy: float = 4e9):
+def cpu_baseline_all_cores(name: str, spec, steps: int, bytes_per_copy: float = 3e9):
     """The same oracle sample run as one independent copy per host core (as many as
-    the free memory holds, about 4 GB each for the 1M-node net), all copies timed
+    the free memory holds, 2.5 GB at peak each for the 1M-node net), all copies timed
     together: the host's aggregate oracle throughput.  The oracle itself is one
     thread; one network is not split across cores (that would change the oracle)."""
     import multiprocessing as mp
+    avail = bytes_per_copy
     try:
-        import psutil
-        avail = psutil.virtual_memory().available
-    except Exception:
-        avail = bytes_per_copy
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    avail = int(line.split()[1]) * 1024
+                    break
+    except (OSError, ValueError, IndexError):
+        pass
+    try:  # a container's memory limit, where one is set
+        with open("/sys/fs/cgroup/memory.max") as f:
+            lim = f.read().strip()
+        if lim != "max":
+            with open("/sys/fs/cgroup/memory.current") as f:
+                avail = min(avail, int(lim) - int(f.read().strip()))
+    except (OSError, ValueError):
+        pass
     copies = max(1, min(os.cpu_count() or 1, int(avail // bytes_per_copy)))
     ctx = mp.get_context("spawn")
     barrier = ctx.Barrier(copies)
@@ -856,6 +868,7 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
                      "algorithmic_bytes_per_launch": bytes_step, "kernel": KERNEL_NAMES[info["step_kernel"]],
+                     "grid": info["grid"],
                      "bytes_survey": bytes_survey, "frac_survey": bytes_survey / step_s / 1e9 / peak,
                      "frac_dram": traffic / step_s / 1e9 / peak if traffic else None},
         "e2e": {"value": e2e_value, "unit": METRIC,
