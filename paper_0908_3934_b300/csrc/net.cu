@@ -644,8 +644,10 @@ gn_status gn_net_create(const gn_net_desc *desc, gn_net **out)
         net->inv = h.inv;
         net->delay = h.delay;
         net->h_row_ptr = h.row_ptr;
-        // edges are streamed past L2 unless they fit comfortably in it
+        // edges are streamed past L2 unless they fit comfortably in it (GN_STREAM_EDGES=0 or 1
+        // in the environment overrides the rule)
         net->stream_edges = static_cast<double>(net->E) * (net->packed ? 8.0 : 12.0) > 48e6;
+        if (const char *e = getenv("GN_STREAM_EDGES"); e && (*e == '0' || *e == '1')) net->stream_edges = *e == '1';
 
         const int32_t N = net->N;
         net->ekey.alloc(h.key.size() * 4, &net->bytes);
