@@ -46,8 +46,8 @@ NODE_BYTES = 36.2      # v~ read 4, (w~,c~) read 8 + write 8, ring write 4, row_
 # delay) of a tile its packed key 4 B + the FP32 history value 4 B
 STAGED_EDGE_BYTES = 6
 STAGED_GATHER_BYTES = 8
-KERNEL_NAMES = {1: "k_step", 2: "k_step_pipe", 3: "k_step_staged", 4: "k_resident"}
-RESIDENT_CHUNK = 65536  # steps per launch of the resident kernel
+KERNEL_NAMES = {1: "k_step", 2: "k_step_pipe", 3: "k_step_staged", 4: "k_resident", 5: "k_step_persist"}
+RESIDENT_CHUNK = 65536  # steps per launch of the resident and persistent kernels
 # format-independent bytes of one step: per edge-update a 10-byte edge record (weight 4,
 # source 4, delay 2) + the gathered FP32 history value 4; per node-step NODE_BYTES
 SURVEY_EDGE_BYTES = 14
@@ -77,6 +77,8 @@ def algorithmic_bytes(info: dict, E: int, N: int) -> float:
     re-reads excluded)."""
     if info["step_kernel"] == 3:
         return E * STAGED_EDGE_BYTES + info["step_gathers"] * STAGED_GATHER_BYTES + N * NODE_BYTES
+    if info["step_kernel"] == 5:  # keys and entries stay in shared memory: the gathered values and node state
+        return info["step_gathers"] * 4 + N * NODE_BYTES
     return E * EDGE_BYTES + N * NODE_BYTES
 
 
@@ -756,9 +758,10 @@ def main():
     ap.add_argument("--no-test-set", action="store_true", help="skip the 80-network test-set sweeps")
     ap.add_argument("--test-set-steps", type=int, default=10000, help="Izhikevich steps per test-set network")
     ap.add_argument("--test-set-hh-steps", type=int, default=33333, help="Hodgkin-Huxley steps per test-set network")
-    ap.add_argument("--step-kernel", type=int, default=0, choices=[0, 1, 2, 3],
+    ap.add_argument("--step-kernel", type=int, default=0, choices=[0, 1, 2, 3, 4, 5],
                     help="0: autotuned, 1: one row block per CTA, 2: persistent bulk-copy pipelined kernel, "
-                         "3: staged tiles (distinct gathers in shared memory)")
+                         "3: staged tiles (distinct gathers in shared memory), 4: the whole network in one CTA, "
+                         "5: staged tiles resident in shared memory across the steps of one launch")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -811,7 +814,7 @@ def main():
     barrier()
     clocks = sampler.stop()
     t = ev0.elapsed_time(ev1) / 1e3
-    if info["step_kernel"] == 4:  # one resident launch and one advance per chunk
+    if info["step_kernel"] in (4, 5):  # one resident / persistent launch and one advance per chunk
         launches = 2 * (-(-args.steps // RESIDENT_CHUNK))
     else:  # one step launch per step, one advance per 64-step graph and per ragged tail
         launches = args.steps + args.steps // 64 + (1 if args.steps % 64 else 0)

@@ -168,7 +168,14 @@ typedef struct {
                                     (in-degree above about 20,000).  Every kernel sums a node's inputs
                                     in the same order, so results do not depend on this choice.  The
                                     environment variable GN_STEP_SHAPE=i picks the CTA shape of an
-                                    explicitly chosen kernel 1 or 3 (default 0).  Kernel 3 on a large
+                                    explicitly chosen kernel 1, 3, 4 or 5 (default 0).  4: the whole
+                                    network resident in one CTA's shared memory, many steps per launch.
+                                    5: kernel 3's tiles in one persistent cooperative launch per call
+                                    (up to 65,536 steps), each CTA holding its tile's keys and entries
+                                    in shared memory for the whole launch, the CTAs meeting at a counting
+                                    barrier in global memory between steps; 4 and 5 fail with GN_EINVAL
+                                    if the network does not fit (5: every tile's CTA resident at once),
+                                    and neither takes plastic weights.  Kernel 3 on a large
                                     FitzHugh-Nagumo net fetches its history values (all written two
                                     or more steps back) before it waits for the previous step;
                                     GN_STAGED_EARLY=0 makes it wait first */
@@ -207,7 +214,7 @@ typedef struct {
     int64_t n_clamped;           /* geometric delays that rounded below one step */
     int32_t edge_format;         /* 0: packed 32-bit (src << log2 R | D); 1: 64-bit (src, D) */
     int32_t n_blocks;            /* row blocks (kernels 1, 2) or tiles (kernel 3) of the step kernel */
-    int32_t step_kernel;         /* 1, 2 or 3 once chosen (0 before the first gn_step when autotuning) */
+    int32_t step_kernel;         /* 1 to 5 once chosen (0 before the first gn_step when autotuning) */
     int32_t step_threads;        /* CTA size of the chosen kernel */
     int32_t step_edges_per_thread; /* kernels 1, 2: edges per thread of a row block; 3: longest row summed
                                       by one thread (longer rows: 32 lane-strided pieces) */

@@ -184,6 +184,14 @@ cudaError_t launch_step_staged(const StepArgs &a, int n_tiles, int k, const Stag
                                bool stream_edges, size_t smem_bytes, bool early, cudaStream_t s);
 cudaError_t step_staged_prepare(const StagedShape &shape, int model, bool plastic, bool packed, bool stream_edges,
                                 size_t smem_bytes, int *ctas_per_sm);
+// persistent staged step of one network (kind 5): one cooperative launch of one CTA
+// per tile (all resident at once) runs n_steps steps with each tile's gather keys and
+// entries held in shared memory; counts: 64 words (the launch zeroes them first);
+// smem_bytes: 16 + max_u (4 or 8 key bytes + 4 value bytes) + max_x 6 + max_p 4
+cudaError_t launch_step_persist(const StepArgs &a, int n_tiles, int n_steps, const StagedShape &shape, bool packed,
+                                unsigned int *counts, size_t smem_bytes, cudaStream_t s);
+cudaError_t step_persist_prepare(const StagedShape &shape, int model, bool packed, size_t smem_bytes,
+                                 int *ctas_per_sm);
 // batched form with the staged layout: one launch per step over every member's
 // tiles (tile_net[t] = the member of tile t), tiles cut with kBatchStagedShape
 constexpr StagedShape kBatchStagedShape = {128, 3072, 4096, 256, 0};

@@ -444,6 +444,142 @@ __global__ void __launch_bounds__(T, kThreadsL2 / T)
     }
 }
 
+// Persistent staged step of one network whose tiles the device holds all at once
+// (kind 5): one cooperative launch of one CTA per tile runs n_steps steps.  The CTA
+// copies its tile's gather keys and edge entries into shared memory once and keeps
+// them for the whole launch (the gathered values have their own array), so a step is
+// the gathers, the piece sums from shared memory, the wait for the previous step and
+// the node update -- the tile step of the staged kernel with its entries staged, in the
+// same summation order.  The CTAs meet at a counting barrier in global memory as the
+// lanes schedule's CTAs do (arrivals, steps complete; see above): a CTA's node updates
+// of step k wait until steps complete >= k; its gathers of step k read slots written
+// in step k - 2 or earlier, covered by its own wait in step k - 1.  Bounded waits; a
+// CTA that gives up sets kStatusTimeout and returns, and the others stop polling.
+template <int kM, int T, bool kPacked>
+__global__ void __launch_bounds__(T, 1)
+    k_step_persist(const StepArgs a, const int n_steps, unsigned int *__restrict__ counts, const uint32_t limit)
+{
+    extern __shared__ __align__(128) unsigned char s_raw[];
+    __shared__ int s_ok;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(s_raw);
+    uint32_t *s_key = reinterpret_cast<uint32_t *>(s_raw + 16);
+    float *s_val = reinterpret_cast<float *>(s_raw + 16 + static_cast<size_t>(a.st_ucap) * (kPacked ? 4 : 8));
+    float *s_w = s_val + a.st_ucap;
+    uint16_t *s_u = reinterpret_cast<uint16_t *>(s_w + a.st_xcap);
+    float *s_part = reinterpret_cast<float *>(s_u + a.st_xcap);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int tile = blockIdx.x;
+    const int4 td = __ldg(a.st_tile + tile);   // {r0, rows, u0, gathers}
+    const int4 td2 = __ldg(a.st_tile2 + tile); // {s0, slices, x0, entries}
+    const int nu = td.w, nx = td2.w;
+    const uint32_t kbytes = static_cast<uint32_t>((nu + 3) & ~3) * (kPacked ? 4u : 8u);
+    const uint32_t bytes = kbytes + static_cast<uint32_t>(nx) * 6u;
+    if (t == 0) {
+        s_ok = 1;
+        if (bytes) {
+            mbar_init(bar, 1);
+            fence_barrier_init();
+            mbar_arrive_expect_tx(bar, bytes);
+            const char *keys = static_cast<const char *>(a.st_ukey) + static_cast<size_t>(td.z) * (kPacked ? 4 : 8);
+            const uint64_t pol = l2_evict_last();
+            if (kbytes) bulk_g2s_hint(s_key, keys, kbytes, bar, pol);
+            if (nx) {
+                bulk_g2s_hint(s_w, a.st_w + td2.z, static_cast<uint32_t>(nx) * 4u, bar, pol);
+                bulk_g2s_hint(s_u, a.st_u + td2.z, static_cast<uint32_t>(nx) * 2u, bar, pol);
+            }
+        }
+    }
+    const int r = td.x + t;
+    const bool own = t < td.y;
+    int q0 = 0, q1 = 0;
+    int32_t orig = kLoad;
+    if (own) {
+        q0 = __ldg(a.st_rq + r);
+        q1 = __ldg(a.st_rq + r + 1);
+        orig = __ldg(a.perm + r);
+    }
+    if (t == 0 && bytes && !mbar_wait_bounded(bar, 0, a.wait_limit)) {
+        atomicOr(a.status, kStatusTimeout);
+        s_ok = 0;
+        mbar_wait_bounded(bar, 0, kDefaultWaitLimit);  // the copies must land before the CTA leaves
+    }
+    __syncthreads();
+    if (!s_ok) return;
+
+    unsigned int *arrivals = counts, *done = counts + 32;
+    const unsigned int C = gridDim.x;
+    const uint32_t dmask = (1u << a.dbits) - 1u;
+    const uint64_t pol_ring = l2_evict_last();
+    const int64_t n0 = *a.d_step;  // the step counter changes only between launches
+    for (int k = 0; k < n_steps; ++k) {
+        const int64_t n = n0 + k;
+        // 1. the tile's distinct history values
+#pragma unroll 4
+        for (int u = t; u < nu; u += T) {
+            uint32_t src, d;
+            if constexpr (kPacked) {
+                const uint32_t kk = s_key[u];
+                src = kk >> a.dbits;
+                d = kk & dmask;
+            } else {
+                const uint2 kk = reinterpret_cast<const uint2 *>(s_key)[u];
+                src = kk.x;
+                d = kk.y;
+            }
+            const int64_t slot = (n - static_cast<int64_t>(d)) & a.ring_mask;
+            cp_async4_hint(s_val + u, a.ring + slot * a.ring_stride + src, pol_ring);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        // 2. one piece per lane, 32 pieces per warp at a time, entries from shared memory
+        for (int sl = warp; sl < td2.y; sl += T / 32) {
+            const int2 sd = __ldg(a.st_slice + td2.x + sl);
+            const float *wp = s_w + sd.x + lane;
+            const uint16_t *up = s_u + sd.x + lane;
+            float acc = 0.0f;
+#pragma unroll 4
+            for (int kk = 0; kk < sd.y; ++kk) acc = __fadd_rn(acc, __fmul_rn(wp[kk * 32], s_val[up[kk * 32]]));
+            s_part[sl * 32 + lane] = acc;
+        }
+        __syncthreads();
+        // 3. wait until step k - 1 is complete everywhere
+        if (t == 0) s_ok = k == 0 ? 1 : lane_poll(done, static_cast<unsigned int>(k), limit, a.status);
+        __syncthreads();
+        if (!s_ok) return;
+        // 4. row sums and the node update of the own rows
+        if (own) {
+            float S = 0.0f;
+            if (q1 - q0 == 1) {
+                S = s_part[__ldg(a.st_plist + q0)];
+            } else if (q1 - q0 == 32) {
+                float x[32];
+#pragma unroll
+                for (int l = 0; l < 32; ++l) x[l] = s_part[__ldg(a.st_plist + q0 + l)];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                    for (int l = 0; l < o; ++l) x[l] = __fadd_rn(x[l], x[l + o]);
+                S = x[0];
+            }
+            const float2 wc = a.wc[r];
+            const int32_t cnt0 = a.bg_thr ? a.bgc[r] : kLoad;
+            if constexpr (kM == 0)
+                node_update<kM>(a, r, n, a.ring[(n & a.ring_mask) * a.ring_stride + r], wc, S, orig, cnt0);
+            else
+                psc_finish(a, r, spiking_begin<kM>(a, r, n, wc, orig, cnt0, 0u), S);
+        }
+        // 5. arrive: this CTA's step k is complete
+        __syncthreads();
+        if (t == 0) {
+            fence_acq_rel();
+            if (atomicAdd(arrivals, 1u) == (static_cast<unsigned int>(k) + 1u) * C - 1u) {
+                fence_acq_rel();
+                st_relaxed(done, static_cast<unsigned int>(k) + 1u);
+            }
+        }
+    }
+}
+
 template <int kM, int T, bool kSE, bool kPacked, bool kStream, bool kEarly>
 cudaError_t launch_t(const StepArgs &a, int n_tiles, int k, size_t smem, cudaStream_t s)
 {
@@ -638,7 +774,63 @@ cudaError_t batch_lanes(bool launch, int model, const StepArgs *nets, const int 
     });
 }
 
+template <int kM, int T, bool kPacked>
+cudaError_t persist_t(bool launch, const StepArgs *a, int n_tiles, int n_steps, unsigned int *counts, size_t smem,
+                      cudaStream_t s, int *per_sm)
+{
+    auto *fn = k_step_persist<kM, T, kPacked>;
+    if (!launch) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess || !per_sm) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, T, smem);
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(n_tiles));
+    cfg.blockDim = dim3(T);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;  // every CTA resident at once: the step barrier needs it
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fn, *a, n_steps, counts, a->wait_limit);
+}
+
+cudaError_t persist(bool launch, const StagedShape &sh, int model, const StepArgs *a, int n_tiles, int n_steps,
+                    unsigned int *counts, bool packed, size_t smem, cudaStream_t s, int *per_sm)
+{
+    return with_model(model, [&](auto m) {
+        constexpr int M = decltype(m)::value;
+        auto go = [&](auto tt) -> cudaError_t {
+            constexpr int T = decltype(tt)::value;
+            return packed ? persist_t<M, T, true>(launch, a, n_tiles, n_steps, counts, smem, s, per_sm)
+                          : persist_t<M, T, false>(launch, a, n_tiles, n_steps, counts, smem, s, per_sm);
+        };
+        switch (sh.threads) {
+            case 128: return go(std::integral_constant<int, 128>{});
+            case 256: return go(std::integral_constant<int, 256>{});
+            default: return cudaErrorInvalidValue;
+        }
+    });
+}
+
 }  // namespace
+
+cudaError_t launch_step_persist(const StepArgs &a, int n_tiles, int n_steps, const StagedShape &shape, bool packed,
+                                unsigned int *counts, size_t smem_bytes, cudaStream_t s)
+{
+    if (n_steps <= 0 || n_tiles <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(counts, 0, 64 * sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    return persist(true, shape, a.model, &a, n_tiles, n_steps, counts, packed, smem_bytes, s, nullptr);
+}
+
+cudaError_t step_persist_prepare(const StagedShape &shape, int model, bool packed, size_t smem_bytes, int *ctas_per_sm)
+{
+    return persist(false, shape, model, nullptr, 0, 0, nullptr, packed, smem_bytes, nullptr, ctas_per_sm);
+}
 
 cudaError_t launch_batch_lanes(int model, const StepArgs *nets, const int *tile_net, const int2 *groups, int n_groups,
                                int lanes, int n_steps, unsigned int *counts, unsigned int *status, uint32_t limit,

@@ -85,6 +85,8 @@ struct gn_net {
     int64_t st_gathers = 0, st_entries = 0, st_slots = 0;
     int st_max_u = 0, st_max_x = 0, st_max_p = 0;
     bool st_early = false;  // gathers before the grid wait (see staged_tile)
+    size_t ps_smem = 0;                   // kind 5 (persistent staged tiles): shared memory per CTA
+    DevArray<unsigned int> ps_counts;     // ... and its step barrier (64 words)
     DevArray<int4> st_tile, st_tile2;
     DevArray<uint32_t> st_ukey;
     DevArray<int2> st_slice;
@@ -129,6 +131,7 @@ struct gn_net {
         bdesc.release();
         status.release();
         release_staged();
+        ps_counts.release();
         if (copy_stream) {
             cudaStreamSynchronize(copy_stream);
             cudaStreamDestroy(copy_stream);
@@ -245,6 +248,26 @@ bool set_staged(gn_net *net, int shape)
     return true;
 }
 
+// The persistent staged kernel (kind 5) on the staged layout of `shape`: its tiles'
+// keys, entries, gathered values and piece sums in one CTA's shared memory each, and
+// every tile's CTA resident at once; false if the network does not fit.
+bool set_persist(gn_net *net, int shape)
+{
+    if (net->stdp || !set_staged(net, shape) || net->n_tiles < 1) return false;
+    const gn::StagedShape sh = gn::kStagedShapes[shape];
+    const size_t smem = 16 + static_cast<size_t>(net->st_max_u) * (net->packed ? 8 : 12) +
+                        static_cast<size_t>(net->st_max_x) * 6 + static_cast<size_t>(net->st_max_p) * 4;
+    int max_smem = 0, per_sm = 0, sms = 0;
+    cuda_check(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, net->device), "device query");
+    if (smem > static_cast<size_t>(max_smem)) return false;
+    cuda_check(gn::step_persist_prepare(sh, net->model, net->packed, smem, &per_sm), "persistent kernel setup");
+    cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, net->device), "device query");
+    if (static_cast<int64_t>(net->n_tiles) > static_cast<int64_t>(per_sm) * sms) return false;
+    if (!net->ps_counts.p) net->ps_counts.alloc(64, &net->bytes);
+    net->ps_smem = smem;
+    return true;
+}
+
 // Cut the row blocks for a CTA shape and point the kernel arguments at them.
 void set_blocks(gn_net *net, int shape)
 {
@@ -286,6 +309,16 @@ bool set_resident(gn_net *net, int shape)
 
 void configure(gn_net *net, int kind, int shape)
 {
+    if (kind == 5) {
+        if (!set_persist(net, shape))
+            fail(GN_EINVAL, "the persistent staged kernel cannot hold this network (every tile's CTA must be "
+                            "resident at once, with its keys and entries in shared memory; static weights)");
+        net->step_kernel = 5;
+        net->shape = shape;
+        net->grid = net->n_tiles;
+        net->graph_stale = true;
+        return;
+    }
     if (kind == 4) {
         if (!set_resident(net, shape))
             fail(GN_EINVAL, "the resident step kernel cannot hold this network (it must fit one CTA's shared "
@@ -380,7 +413,7 @@ void autotune(gn_net *net)
     const std::string key = tune_key(net);
     int cached_kind = 0, cached_shape = 0;
     if (tune_cache_lookup(key, &cached_kind, &cached_shape) && (cached_kind != 3 || set_staged(net, cached_shape)) &&
-        (cached_kind != 4 || set_resident(net, cached_shape))) {
+        (cached_kind != 4 || set_resident(net, cached_shape)) && (cached_kind != 5 || set_persist(net, cached_shape))) {
         configure(net, cached_kind, cached_shape);
         return;
     }
@@ -445,9 +478,11 @@ void autotune(gn_net *net)
         cands.push_back({2, 0});
         for (int sh = 0; sh < gn::kNumStagedShapes; ++sh) cands.push_back({3, sh});
         for (int sh = 0; sh < gn::kNumResidentShapes; ++sh) cands.push_back({4, sh});
+        for (int sh = 0; sh < gn::kNumStagedShapes; ++sh) cands.push_back({5, sh});
         for (const Cand &c : cands) {
             if (c.kind == 3 && !set_staged(net, c.shape)) continue;
             if (c.kind == 4 && !set_resident(net, c.shape)) continue;
+            if (c.kind == 5 && !set_persist(net, c.shape)) continue;
             configure(net, c.kind, c.shape);
             gn::StepArgs a = net->args;
             a.ring = ring.p;
@@ -472,6 +507,10 @@ void autotune(gn_net *net)
             constexpr int kResidentSteps = 8;
             if (c.kind == 4) {
                 cuda_check(gn::launch_resident(a, net->res, kResidentSteps, c.shape, net->stream), "autotune launch");
+            } else if (c.kind == 5) {
+                cuda_check(gn::launch_step_persist(a, net->n_tiles, warm, gn::kStagedShapes[c.shape], net->packed,
+                                                   net->ps_counts.p, net->ps_smem, net->stream),
+                           "autotune launch");
             } else {
                 for (int k = 0; k < warm; ++k)
                     cuda_check(launch_kind(a, net, k, net->stream), "autotune launch");
@@ -479,6 +518,10 @@ void autotune(gn_net *net)
             cuda_check(cudaEventRecord(t0, net->stream), "event");
             if (c.kind == 4) {
                 cuda_check(gn::launch_resident(a, net->res, kResidentSteps * timed, c.shape, net->stream),
+                           "autotune launch");
+            } else if (c.kind == 5) {
+                cuda_check(gn::launch_step_persist(a, net->n_tiles, timed, gn::kStagedShapes[c.shape], net->packed,
+                                                   net->ps_counts.p, net->ps_smem, net->stream),
                            "autotune launch");
             } else {
                 for (int k = 0; k < timed; ++k)
@@ -516,7 +559,7 @@ void autotune(gn_net *net)
 // The kernel is final: drop the host edge list and any staged layout it does not use.
 void finalize_kernel(gn_net *net)
 {
-    if (net->step_kernel != 3) net->release_staged();
+    if (net->step_kernel != 3 && net->step_kernel != 5) net->release_staged();
     net->host.reset();
 }
 
@@ -731,22 +774,23 @@ gn_status gn_net_create(const gn_net_desc *desc, gn_net **out)
         // a plastic net runs the staged kernel, fixed now: the weights live in its layout
         net->stdp = desc->stdp.enable != 0;
         const int kind = net->stdp ? 3 : desc->step_kernel;
-        if (kind == 0 || kind == 3) net->host = std::make_unique<gnrt::HostNet>(std::move(h));
-        // GN_STEP_SHAPE=i picks the CTA shape of an explicitly chosen kernel 1 or 3
+        if (kind == 0 || kind == 3 || kind == 5) net->host = std::make_unique<gnrt::HostNet>(std::move(h));
+        // GN_STEP_SHAPE=i picks the CTA shape of an explicitly chosen kernel 1, 3, 4 or 5
         // (plastic default: the 12288-edge tiles, measured best on the 1M-node net --
         // 0.139 ms per step against 0.149 and 0.167 for 8192 and 16384 edges)
         int shape = net->stdp ? 4 : kind == 4 ? 1 : 0;
-        if (const char *e = getenv("GN_STEP_SHAPE"); e && *e && (kind == 1 || kind == 3 || kind == 4)) {
+        if (const char *e = getenv("GN_STEP_SHAPE"); e && *e && kind >= 1 && kind != 2) {
             shape = atoi(e);
-            const int n_shapes = kind == 1 ? gn::kNumStepShapes : kind == 3 ? gn::kNumStagedShapes
-                                                                            : gn::kNumResidentShapes;
+            const int n_shapes = kind == 1                ? gn::kNumStepShapes
+                                 : kind == 3 || kind == 5 ? gn::kNumStagedShapes
+                                                          : gn::kNumResidentShapes;
             if (shape < 0 || shape >= n_shapes) fail(GN_EINVAL, "GN_STEP_SHAPE=%s is not a shape of kernel %d", e,
                                                        kind);
             if (net->stdp && gn::kStagedShapes[shape].stage_entries)
                 fail(GN_EINVAL, "GN_STEP_SHAPE=%s stages the edge entries, which plastic weights cannot use", e);
         }
         configure(net, kind == 2 ? 2 : 1, kind == 1 ? shape : 0);
-        if (kind == 3 || kind == 4) configure(net, kind, shape);
+        if (kind >= 3) configure(net, kind, shape);
         if (kind == 0)
             net->step_kernel = 0;
         else
@@ -784,7 +828,7 @@ gn_status gn_net_get_info(const gn_net *net, gn_net_info *info)
         info->min_delay = net->dmin;
         info->n_clamped = net->n_clamped;
         info->edge_format = net->packed ? 0 : 1;
-        const bool staged = net->step_kernel == 3, resident = net->step_kernel == 4;
+        const bool staged = net->step_kernel == 3 || net->step_kernel == 5, resident = net->step_kernel == 4;
         info->n_blocks = staged ? net->n_tiles : resident ? 1 : net->n_blocks;
         info->step_kernel = net->step_kernel;
         info->step_threads = staged     ? gn::kStagedShapes[net->shape].threads
@@ -857,6 +901,19 @@ gn_status gn_step(gn_net *net, int64_t n_steps)
         if (net->step_kernel == 0) {
             autotune(net);
             finalize_kernel(net);
+        }
+        if (net->step_kernel == 5) {
+            // the persistent staged kernel: a launch runs up to kPersistChunk steps
+            constexpr int64_t kPersistChunk = 1 << 16;
+            for (int64_t left = n_steps; left > 0; left -= kPersistChunk) {
+                const int chunk = static_cast<int>(std::min(left, kPersistChunk));
+                cuda_check(gn::launch_step_persist(net->args, net->n_tiles, chunk, gn::kStagedShapes[net->shape],
+                                                   net->packed, net->ps_counts.p, net->ps_smem, net->stream),
+                           "persistent launch");
+                cuda_check(gn::launch_advance(net->d_step.p, chunk, net->stream), "advance launch");
+            }
+            net->step += n_steps;
+            return;
         }
         if (net->step_kernel == 4) {
             // the resident kernel: a launch runs up to kResidentChunk steps

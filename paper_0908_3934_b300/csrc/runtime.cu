@@ -98,7 +98,7 @@ void validate_desc(const gn_net_desc *d)
     if (d->coupling != GN_COUPLE_REST && d->coupling != GN_COUPLE_RAW) fail(GN_EINVAL, "unknown coupling");
     if (d->ring_depth < 0 || (d->ring_depth & (d->ring_depth - 1))) fail(GN_EINVAL, "ring_depth must be a power of two");
     if (d->edge_format != 0 && d->edge_format != 1) fail(GN_EINVAL, "edge_format must be 0 or 1");
-    if (d->step_kernel < 0 || d->step_kernel > 4) fail(GN_EINVAL, "step_kernel must be 0, 1, 2, 3 or 4");
+    if (d->step_kernel < 0 || d->step_kernel > 5) fail(GN_EINVAL, "step_kernel must be 0 to 5");
     const int64_t np = static_cast<int64_t>(d->n_nodes) * d->dim;
     for (int64_t i = 0; i < np; ++i)
         if (!std::isfinite(d->pos[i])) fail(GN_EINVAL, "position %lld is not finite", (long long)i);
@@ -121,7 +121,7 @@ void validate_desc(const gn_net_desc *d)
         if (d->model == GN_MODEL_FHN) fail(GN_EINVAL, "plasticity needs a spiking node model");
         if (!std::isfinite(d->stdp.alpha) || !std::isfinite(d->stdp.beta) || d->stdp.beta < 0.0)
             fail(GN_EINVAL, "plasticity needs a finite alpha and a finite beta >= 0");
-        if (d->step_kernel == 1 || d->step_kernel == 2 || d->step_kernel == 4)
+        if (d->step_kernel == 1 || d->step_kernel == 2 || d->step_kernel == 4 || d->step_kernel == 5)
             fail(GN_EINVAL, "plastic networks run the staged step kernel (step_kernel 0 or 3)");
     }
     auto check_hh = [](const gn_hh_params &z) {

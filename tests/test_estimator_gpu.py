@@ -126,6 +126,32 @@ def test_adamw_training_matches_the_oracle():
         assert _rel(got[k], ref[k]) <= 1e-2, k
 
 
+def test_adamw_step_on_the_kernels_own_gradients():
+    """The AdamW arithmetic of the update kernel alone: each step, the FP64 oracle
+    applies AdamW (its own FP64 moments) to the kernel's current FP32 parameters with
+    the gradients the same kernels give for them (gn_mlp_gradients on the same batch
+    and parameters is the gradient the training step uses), and the training step's
+    update must agree with it to FP32 rounding -- there is no BF16 sign ambiguity
+    left to allow for.  Weight decay 0.01, 5 steps."""
+    torch = _torch()
+    from paper_0908_3934_b300 import geonet
+    X, y = netgen.mlp_toy_batch(8, 2048)
+    m = geonet.Mlp(netgen.mlp_init(9), max_batch=2048)
+    dev = torch.device("cuda")
+    Xd, yd = torch.from_numpy(X).to(dev), torch.from_numpy(y).to(dev)
+    state = {}
+    for step in range(5):
+        before = {k: v.astype(np.float64) for k, v in m.gn_mlp_get_params().items()}
+        g, _ = m.gn_mlp_gradients(Xd, yd)
+        ref = est.adamw(before, g, state, lr=1e-3, weight_decay=0.01)
+        m.gn_mlp_train_step(Xd, yd, lr=1e-3, weight_decay=0.01, want_loss=False)
+        got = m.gn_mlp_get_params()
+        for k in before:
+            d_ref, d_got = ref[k] - before[k], got[k].astype(np.float64) - before[k]
+            assert _rel(d_got, d_ref) <= 1e-4, (step, k, _rel(d_got, d_ref))
+            assert np.all(np.sign(d_got[np.abs(d_ref) > 1e-6]) == np.sign(d_ref[np.abs(d_ref) > 1e-6])), (step, k)
+
+
 def test_replayed_epoch_equals_single_steps_bit_for_bit():
     """gn_mlp_train_epoch (one step captured as a graph, the batch chosen by a device
     cursor, replayed) gives the same parameters and losses, bit for bit, as the same
