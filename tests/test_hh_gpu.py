@@ -56,9 +56,15 @@ def test_every_kernel_and_shape_gives_the_same_bits(monkeypatch):
     """Every step kernel and CTA shape reaches bit-identical Hodgkin-Huxley states."""
     spec = netgen.hodgkin_huxley(netgen.roofline(seed=21, n=20000, bg_rate_hz=100.0))
     ref = None
-    for kind, shape in [(1, s) for s in range(5)] + [(2, 0)] + [(3, s) for s in range(6)]:
+    persistent = 0
+    for kind, shape in [(1, s) for s in range(5)] + [(2, 0)] + [(3, s) for s in range(6)] + [(5, s) for s in range(6)]:
         monkeypatch.setenv("GN_STEP_SHAPE", str(shape))
-        net = geonet.Net(spec, step_kernel=kind)
+        try:
+            net = geonet.Net(spec, step_kernel=kind)
+        except geonet.GeonetError as e:  # kernel 5 in a shape whose tiles the device cannot hold at once
+            assert kind == 5 and e.status == geonet.GN_EINVAL, (kind, shape)
+            continue
+        persistent += kind == 5
         net.gn_step(700)
         st, iz, gt = net.gn_get_state(), net.gn_get_izh_state(), net.gn_get_hh_gates()
         cur = [st["c"], iz["V"], iz["r"], iz["p"], gt["m"], gt["n"], gt["h"], net.gn_get_history(8)]
@@ -68,6 +74,7 @@ def test_every_kernel_and_shape_gives_the_same_bits(monkeypatch):
             continue
         for a, b in zip(cur, ref):
             assert np.array_equal(a, b), (kind, shape)
+    assert persistent >= 2
 
 
 def test_checkpoint_resume_is_bit_exact():

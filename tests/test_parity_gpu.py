@@ -243,10 +243,16 @@ def test_every_kernel_and_shape_gives_the_same_bits(monkeypatch):
     hubs of in-degree 1000 and 100 Hz background, 300 steps from rest."""
     spec = netgen.roofline(seed=21, n=20000, bg_rate_hz=100.0)
     ref = None
-    cases = [(1, s) for s in range(5)] + [(2, 0)] + [(3, s) for s in range(6)]
+    cases = [(1, s) for s in range(5)] + [(2, 0)] + [(3, s) for s in range(6)] + [(5, s) for s in range(6)]
+    persistent = 0
     for kind, shape in cases:
         monkeypatch.setenv("GN_STEP_SHAPE", str(shape))
-        net = Net(spec, step_kernel=kind)
+        try:
+            net = Net(spec, step_kernel=kind)
+        except geonet.GeonetError as e:  # kernel 5 in a shape whose tiles the device cannot hold at once
+            assert kind == 5 and e.status == geonet.GN_EINVAL, (kind, shape)
+            continue
+        persistent += kind == 5
         net.gn_step(300)
         st = net.gn_get_state()
         hist = net.gn_get_history(8)
@@ -257,6 +263,7 @@ def test_every_kernel_and_shape_gives_the_same_bits(monkeypatch):
         for k in ("v", "w", "c", "bg_count"):
             assert np.array_equal(st[k], ref[0][k]), (kind, shape, k)
         assert np.array_equal(hist, ref[1]), (kind, shape)
+    assert persistent >= 2
 
 
 def test_early_gathers_with_the_fastest_slot_reuse(monkeypatch):
