@@ -205,7 +205,7 @@ cudaError_t batch_staged_prepare(int model, bool packed, bool stream_edges, size
 // `groups` n_steps times (group g in lane g % lanes); counts: kLaneWords words per
 // lane, zero at launch (the lanes' barrier words); status: the batch's status word
 constexpr int kMaxBatchLanes = 8;
-constexpr int kLaneWords = 64;  // per lane: arrivals at word 0, steps complete at word 32
+constexpr int kLaneWords = 64;  // per lane: the arrival count at word 0 (lanes 256 bytes apart)
 cudaError_t launch_batch_lanes(int model, const StepArgs *nets, const int *tile_net, const int2 *groups, int n_groups,
                                int lanes, int n_steps, unsigned int *counts, unsigned int *status, uint32_t limit,
                                bool packed, int grid, size_t smem_bytes, cudaStream_t s);

@@ -329,19 +329,20 @@ __global__ void __launch_bounds__(T, kThreadsL2 / T) k_batch_staged(const StepAr
 // tiles b / lanes, b / lanes + C, ... of each group of its lane (C: the lane's
 // CTAs); a lane runs its groups one after another (groups g = lane, lane + lanes,
 // ...), each through all the steps, so a group's data stays in L2 across them.
-// A lane's CTAs meet at a counting barrier in global memory (two words of their
-// own 128-byte lines: arrivals, and steps complete).  After its tiles' node
-// updates of the lane's j-th step (counted over its groups) a CTA adds 1 to the
-// arrivals; the CTA whose add completes the step's C arrivals sets the steps
-// complete to j + 1.  A CTA's node updates of step j wait until steps complete
-// >= j (slot n + 1, which step n writes, is read by step n - 1's longest delay).
+// A lane's CTAs meet at a counting barrier in global memory (the lane's arrival
+// count, on a 128-byte line of its own).  After its tiles' node updates of the
+// lane's j-th step (counted over its groups) a CTA adds 1 to the count; its node
+// updates of step j wait until the count reaches j C, i.e. until step j - 1 is
+// complete in the whole lane (slot n + 1, which step n writes, is read by step
+// n - 1's longest delay).
 // Its gathers do not wait: they read history slots n - D, D >= 1, written by step
 // n - 2 or earlier, which the CTA's own wait in step n - 1 covered -- the argument
 // of the early gathers in a chain of launches.  A CTA without a tile in a step
 // still waits for step j - 1 before it arrives, so no CTA is two arrivals ahead of
-// another and the C-th arrival of a step is the last one of that step.  Memory
-// order: fence then add (release), the last adder's fence then store; waits poll
-// with relaxed loads and fence once the value is seen (acquire).  Waits are
+// another and a count of (j + 1) C can only mean that every CTA has arrived for step
+// j.  Memory order: the add is a release reduction (no reply awaited) after a CTA
+// barrier; waits poll with relaxed loads and fence once the count is seen (acquire).
+// Waits are
 // bounded: after `limit` polls, or once another CTA has set kStatusTimeout, the
 // CTA gives up and returns.
 __device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
@@ -353,17 +354,19 @@ __device__ __forceinline__ unsigned int ld_relaxed(const unsigned int *p)
     return v;
 }
 
-__device__ __forceinline__ void st_relaxed(unsigned int *p, unsigned int v)
+// Fire-and-forget add with release semantics (the CTA's writes before it, ordered by
+// a CTA barrier, are visible to whoever observes the new count and then fences).
+__device__ __forceinline__ void red_release_add(unsigned int *p, unsigned int v)
 {
-    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Thread 0's wait until `done` reaches `target`: 1 on success, 0 on giving up.
-__device__ __forceinline__ int lane_poll(const unsigned int *done, unsigned int target, uint32_t limit,
+// Thread 0's wait until `count` reaches `target`: 1 on success, 0 on giving up.
+__device__ __forceinline__ int lane_poll(const unsigned int *count, unsigned int target, uint32_t limit,
                                          unsigned int *status)
 {
     for (uint32_t i = 0; i < limit; ++i) {
-        if (ld_relaxed(done) >= target) {
+        if (ld_relaxed(count) >= target) {
             fence_acq_rel();
             return 1;
         }
@@ -378,7 +381,7 @@ __device__ __forceinline__ int lane_poll(const unsigned int *done, unsigned int 
 // copy of its outcome).
 struct LaneWait {
     static constexpr bool kPdl = false;
-    const unsigned int *done;
+    const unsigned int *count;
     unsigned int target;
     uint32_t limit;
     unsigned int *status;
@@ -387,7 +390,7 @@ struct LaneWait {
     __device__ __forceinline__ bool operator()()
     {
         if (done_here) return true;
-        if (threadIdx.x == 0) *s_ok = target == 0 ? 1 : lane_poll(done, target, limit, status);
+        if (threadIdx.x == 0) *s_ok = target == 0 ? 1 : lane_poll(count, target, limit, status);
         __syncthreads();
         done_here = *s_ok != 0;
         return done_here;
@@ -406,7 +409,6 @@ __global__ void __launch_bounds__(T, kThreadsL2 / T)
     const int lane = static_cast<int>(blockIdx.x) % lanes, me = static_cast<int>(blockIdx.x) / lanes;
     const unsigned int C = (gridDim.x - static_cast<unsigned int>(lane) + lanes - 1) / lanes;
     unsigned int *arrivals = counts + kLaneWords * lane;
-    unsigned int *done = arrivals + 32;
     if (threadIdx.x == 0) {
         mbar_init(reinterpret_cast<uint64_t *>(s_raw), 1);
         fence_barrier_init();
@@ -418,7 +420,7 @@ __global__ void __launch_bounds__(T, kThreadsL2 / T)
     for (int g = lane; g < n_groups; g += lanes) {
         const int2 gr = __ldg(groups + g);  // {first tile, tiles}
         for (int k = 0; k < n_steps; ++k, ++j) {
-            LaneWait w{done, j, limit, status, &s_ok, false};
+            LaneWait w{arrivals, j * C, limit, status, &s_ok, false};
             for (int i = me; i < gr.y; i += static_cast<int>(C)) {
                 __syncthreads();  // the previous tile is done with shared memory
                 const int net = __ldg(tile_net + gr.x + i);
@@ -433,13 +435,7 @@ __global__ void __launch_bounds__(T, kThreadsL2 / T)
             }
             if (!w()) return;
             __syncthreads();
-            if (threadIdx.x == 0) {
-                fence_acq_rel();
-                if (atomicAdd(arrivals, 1u) == (j + 1) * C - 1) {
-                    fence_acq_rel();
-                    st_relaxed(done, j + 1);
-                }
-            }
+            if (threadIdx.x == 0) red_release_add(arrivals, 1u);
         }
     }
 }
@@ -450,11 +446,15 @@ __global__ void __launch_bounds__(T, kThreadsL2 / T)
 // them for the whole launch (the gathered values have their own array), so a step is
 // the gathers, the piece sums from shared memory, the wait for the previous step and
 // the node update -- the tile step of the staged kernel with its entries staged, in the
-// same summation order.  The CTAs meet at a counting barrier in global memory as the
-// lanes schedule's CTAs do (arrivals, steps complete; see above): a CTA's node updates
-// of step k wait until steps complete >= k; its gathers of step k read slots written
-// in step k - 2 or earlier, covered by its own wait in step k - 1.  Bounded waits; a
-// CTA that gives up sets kStatusTimeout and returns, and the others stop polling.
+// same summation order.  The CTAs meet at a counting barrier in global memory: after
+// its node updates of step k a CTA adds 1 to the arrival count (a release reduction, no
+// reply awaited), and its node updates of step k wait until the count reaches k C (C:
+// the grid), i.e. until step k - 1 is complete everywhere (relaxed polls, then a
+// fence).  A CTA arrives at step k only after that wait, so no CTA is two arrivals
+// ahead and k C arrivals can only be every CTA's k.  Its gathers of step k read slots
+// written in step k - 2 or earlier, covered by its own wait in step k - 1.  Bounded
+// waits; a CTA that gives up sets kStatusTimeout and returns, and the others stop
+// polling.
 template <int kM, int T, bool kPacked>
 __global__ void __launch_bounds__(T, 1)
     k_step_persist(const StepArgs a, const int n_steps, unsigned int *__restrict__ counts, const uint32_t limit)
@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(T, 1)
     __syncthreads();
     if (!s_ok) return;
 
-    unsigned int *arrivals = counts, *done = counts + 32;
+    unsigned int *arrivals = counts;
     const unsigned int C = gridDim.x;
     const uint32_t dmask = (1u << a.dbits) - 1u;
     const uint64_t pol_ring = l2_evict_last();
@@ -542,8 +542,8 @@ __global__ void __launch_bounds__(T, 1)
             s_part[sl * 32 + lane] = acc;
         }
         __syncthreads();
-        // 3. wait until step k - 1 is complete everywhere
-        if (t == 0) s_ok = k == 0 ? 1 : lane_poll(done, static_cast<unsigned int>(k), limit, a.status);
+        // 3. wait until step k - 1 is complete everywhere: k C arrivals
+        if (t == 0) s_ok = k == 0 ? 1 : lane_poll(arrivals, static_cast<unsigned int>(k) * C, limit, a.status);
         __syncthreads();
         if (!s_ok) return;
         // 4. row sums and the node update of the own rows
@@ -570,13 +570,7 @@ __global__ void __launch_bounds__(T, 1)
         }
         // 5. arrive: this CTA's step k is complete
         __syncthreads();
-        if (t == 0) {
-            fence_acq_rel();
-            if (atomicAdd(arrivals, 1u) == (static_cast<unsigned int>(k) + 1u) * C - 1u) {
-                fence_acq_rel();
-                st_relaxed(done, static_cast<unsigned int>(k) + 1u);
-            }
-        }
+        if (t == 0) red_release_add(arrivals, 1u);
     }
 }
 
