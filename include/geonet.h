@@ -228,6 +228,8 @@ typedef struct {
     int64_t step_entries;        /* edge records read per step: n_edges for kernels 1 and 2; for kernel 3
                                     the stored entries including the padding of its slices */
     int64_t step_lane_slots;     /* kernel 3: lane slots (32 per slice of pieces); 0 for kernels 1 and 2 */
+    int32_t step_cluster;        /* kernel 5: 1 if the grid runs as one thread-block cluster (at most 16 tiles,
+                                    the cluster's own barrier between steps), 0 for the cooperative grid */
 } gn_net_info;
 
 typedef struct gn_net gn_net;

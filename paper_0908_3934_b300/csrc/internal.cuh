@@ -173,7 +173,7 @@ cudaError_t launch_advance(int64_t *d_step, int64_t by, cudaStream_t s);
 // stage_entries: 1 copies a tile's edge entries into shared memory with its gather
 // keys; 0 keeps only the keys there and prefetches the entries into L2 (less
 // shared memory per CTA, more CTAs per SM)
-constexpr int kNumStagedShapes = 6;
+constexpr int kNumStagedShapes = 7;
 struct StagedShape {
     int threads, ucap, ecap, pcap, stage_entries;
 };
@@ -188,10 +188,14 @@ cudaError_t step_staged_prepare(const StagedShape &shape, int model, bool plasti
 // per tile (all resident at once) runs n_steps steps with each tile's gather keys and
 // entries held in shared memory; counts: 64 words (the launch zeroes them first);
 // smem_bytes: 16 + max_u (4 or 8 key bytes + 4 value bytes) + max_x 6 + max_p 4
+// cluster: the grid (at most kMaxClusterTiles tiles) is one thread-block cluster and the
+// step barrier the cluster's; prepare reports CTAs per SM, or (cluster) how many such
+// clusters the device holds at once
+constexpr int kMaxClusterTiles = 16;
 cudaError_t launch_step_persist(const StepArgs &a, int n_tiles, int n_steps, const StagedShape &shape, bool packed,
-                                unsigned int *counts, size_t smem_bytes, cudaStream_t s);
-cudaError_t step_persist_prepare(const StagedShape &shape, int model, bool packed, size_t smem_bytes,
-                                 int *ctas_per_sm);
+                                bool cluster, unsigned int *counts, size_t smem_bytes, cudaStream_t s);
+cudaError_t step_persist_prepare(const StagedShape &shape, int model, bool packed, bool cluster, int n_tiles,
+                                 size_t smem_bytes, int *fits);
 // batched form with the staged layout: one launch per step over every member's
 // tiles (tile_net[t] = the member of tile t), tiles cut with kBatchStagedShape
 constexpr StagedShape kBatchStagedShape = {128, 3072, 4096, 256, 0};

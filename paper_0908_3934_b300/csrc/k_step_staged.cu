@@ -455,7 +455,17 @@ __global__ void __launch_bounds__(T, kThreadsL2 / T)
 // written in step k - 2 or earlier, covered by its own wait in step k - 1.  Bounded
 // waits; a CTA that gives up sets kStatusTimeout and returns, and the others stop
 // polling.
-template <int kM, int T, bool kPacked>
+// kCluster: a network of at most 16 tiles runs as one thread-block cluster, and the
+// step barrier is the cluster's own (barrier.cluster.arrive.release after the node
+// updates of step k, barrier.cluster.wait.acquire before those of step k + 1, the
+// next step's gathers and sums in between).  That barrier has no time limit, so every
+// CTA passes every arrive and wait the same number of times: a CTA whose copy wait
+// gave up (kStatusTimeout) runs the remaining steps' barriers without their work
+// instead of returning, and it waits once more after the last arrive.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
+template <int kM, int T, bool kPacked, bool kCluster>
 __global__ void __launch_bounds__(T, 1)
     k_step_persist(const StepArgs a, const int n_steps, unsigned int *__restrict__ counts, const uint32_t limit)
 {
@@ -504,7 +514,10 @@ __global__ void __launch_bounds__(T, 1)
         mbar_wait_bounded(bar, 0, kDefaultWaitLimit);  // the copies must land before the CTA leaves
     }
     __syncthreads();
-    if (!s_ok) return;
+    const bool work = s_ok != 0;  // uniform over the CTA
+    if constexpr (!kCluster) {
+        if (!work) return;
+    }
 
     unsigned int *arrivals = counts;
     const unsigned int C = gridDim.x;
@@ -513,6 +526,11 @@ __global__ void __launch_bounds__(T, 1)
     const int64_t n0 = *a.d_step;  // the step counter changes only between launches
     for (int k = 0; k < n_steps; ++k) {
         const int64_t n = n0 + k;
+        if (kCluster && !work) {  // a CTA that gave up keeps the cluster's barriers
+            if (k > 0) cluster_wait();
+            cluster_arrive();
+            continue;
+        }
         // 1. the tile's distinct history values
 #pragma unroll 4
         for (int u = t; u < nu; u += T) {
@@ -543,9 +561,13 @@ __global__ void __launch_bounds__(T, 1)
         }
         __syncthreads();
         // 3. wait until step k - 1 is complete everywhere: k C arrivals
-        if (t == 0) s_ok = k == 0 ? 1 : lane_poll(arrivals, static_cast<unsigned int>(k) * C, limit, a.status);
-        __syncthreads();
-        if (!s_ok) return;
+        if constexpr (kCluster) {
+            if (k > 0) cluster_wait();
+        } else {
+            if (t == 0) s_ok = k == 0 ? 1 : lane_poll(arrivals, static_cast<unsigned int>(k) * C, limit, a.status);
+            __syncthreads();
+            if (!s_ok) return;
+        }
         // 4. row sums and the node update of the own rows
         if (own) {
             float S = 0.0f;
@@ -569,8 +591,15 @@ __global__ void __launch_bounds__(T, 1)
                 psc_finish(a, r, spiking_begin<kM>(a, r, n, wc, orig, cnt0, 0u), S);
         }
         // 5. arrive: this CTA's step k is complete
-        __syncthreads();
-        if (t == 0) red_release_add(arrivals, 1u);
+        if constexpr (kCluster) {
+            cluster_arrive();
+        } else {
+            __syncthreads();
+            if (t == 0) red_release_add(arrivals, 1u);
+        }
+    }
+    if constexpr (kCluster) {
+        if (n_steps > 0) cluster_wait();  // every CTA's last step is complete before any leaves
     }
 }
 
@@ -659,10 +688,15 @@ cudaError_t dispatch(bool launch, const StagedShape &sh, int model, bool plastic
 // on a net of mean in-degree 50 about 41, 13, 81, 26, 34 and 42 KB.  The last two
 // let a tile of mean in-degree 50 reach its 256 rows (8192 edges stop it near 160),
 // so all 8 warps have pieces to sum (1M-node net: 0.1169 ms per step with shape 3,
-// 0.1392 with shape 4, 0.1126 with shape 5, which larger caps leave unchanged)
+// 0.1392 with shape 4, 0.1126 with shape 5, which larger caps leave unchanged).  The
+// last holds 1024 pieces, 32 rows of over kWarpRow edges (32 pieces each) per tile
+// where the others stop at 8 or 16: a dense net of a few hundred nodes (the test set's
+// 300-node random nets, in-degree about 60) becomes about 10 tiles instead of 38, few
+// enough for the persistent kernel to run as one thread-block cluster.
 const StagedShape kStagedShapes[kNumStagedShapes] = {
     {128, 3072, 4096, 256, 1}, {128, 3072, 4096, 256, 0}, {256, 6144, 8192, 512, 1},
-    {256, 6144, 8192, 512, 0}, {256, 8192, 12288, 512, 0}, {256, 10240, 16384, 512, 0}};
+    {256, 6144, 8192, 512, 0}, {256, 8192, 12288, 512, 0}, {256, 10240, 16384, 512, 0},
+    {128, 4096, 8192, 1024, 1}};
 
 cudaError_t launch_step_staged(const StepArgs &a, int n_tiles, int k, const StagedShape &shape, bool packed,
                                bool stream_edges, size_t smem_bytes, bool early, cudaStream_t s)
@@ -768,39 +802,56 @@ cudaError_t batch_lanes(bool launch, int model, const StepArgs *nets, const int 
     });
 }
 
-template <int kM, int T, bool kPacked>
+// One instance: launch it, or (launch false) raise its shared-memory limits and report
+// how many of its CTAs an SM holds (kCluster: how many clusters of n_tiles CTAs the
+// device holds at once).
+template <int kM, int T, bool kPacked, bool kCluster>
 cudaError_t persist_t(bool launch, const StepArgs *a, int n_tiles, int n_steps, unsigned int *counts, size_t smem,
                       cudaStream_t s, int *per_sm)
 {
-    auto *fn = k_step_persist<kM, T, kPacked>;
-    if (!launch) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-        if (e != cudaSuccess || !per_sm) return e;
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, T, smem);
-    }
+    auto *fn = k_step_persist<kM, T, kPacked, kCluster>;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(static_cast<unsigned>(n_tiles));
     cfg.blockDim = dim3(T);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;  // every CTA resident at once: the step barrier needs it
-    attr[0].val.cooperative = 1;
+    if constexpr (kCluster) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;  // the whole grid is one cluster
+        attr[0].val.clusterDim.x = static_cast<unsigned>(n_tiles);
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+    } else {
+        attr[0].id = cudaLaunchAttributeCooperative;  // every CTA resident at once: the step barrier needs it
+        attr[0].val.cooperative = 1;
+    }
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    if (!launch) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess || !per_sm) return e;
+        if constexpr (kCluster) {
+            e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            if (e != cudaSuccess) return e;
+            return cudaOccupancyMaxActiveClusters(per_sm, fn, &cfg);
+        }
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, T, smem);
+    }
     return cudaLaunchKernelEx(&cfg, fn, *a, n_steps, counts, a->wait_limit);
 }
 
-cudaError_t persist(bool launch, const StagedShape &sh, int model, const StepArgs *a, int n_tiles, int n_steps,
-                    unsigned int *counts, bool packed, size_t smem, cudaStream_t s, int *per_sm)
+cudaError_t persist(bool launch, bool cluster, const StagedShape &sh, int model, const StepArgs *a, int n_tiles,
+                    int n_steps, unsigned int *counts, bool packed, size_t smem, cudaStream_t s, int *per_sm)
 {
     return with_model(model, [&](auto m) {
         constexpr int M = decltype(m)::value;
         auto go = [&](auto tt) -> cudaError_t {
             constexpr int T = decltype(tt)::value;
-            return packed ? persist_t<M, T, true>(launch, a, n_tiles, n_steps, counts, smem, s, per_sm)
-                          : persist_t<M, T, false>(launch, a, n_tiles, n_steps, counts, smem, s, per_sm);
+            if (cluster)
+                return packed ? persist_t<M, T, true, true>(launch, a, n_tiles, n_steps, counts, smem, s, per_sm)
+                              : persist_t<M, T, false, true>(launch, a, n_tiles, n_steps, counts, smem, s, per_sm);
+            return packed ? persist_t<M, T, true, false>(launch, a, n_tiles, n_steps, counts, smem, s, per_sm)
+                          : persist_t<M, T, false, false>(launch, a, n_tiles, n_steps, counts, smem, s, per_sm);
         };
         switch (sh.threads) {
             case 128: return go(std::integral_constant<int, 128>{});
@@ -813,17 +864,22 @@ cudaError_t persist(bool launch, const StagedShape &sh, int model, const StepArg
 }  // namespace
 
 cudaError_t launch_step_persist(const StepArgs &a, int n_tiles, int n_steps, const StagedShape &shape, bool packed,
-                                unsigned int *counts, size_t smem_bytes, cudaStream_t s)
+                                bool cluster, unsigned int *counts, size_t smem_bytes, cudaStream_t s)
 {
     if (n_steps <= 0 || n_tiles <= 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(counts, 0, 64 * sizeof(unsigned int), s);
-    if (e != cudaSuccess) return e;
-    return persist(true, shape, a.model, &a, n_tiles, n_steps, counts, packed, smem_bytes, s, nullptr);
+    if (cluster && n_tiles > kMaxClusterTiles) return cudaErrorInvalidValue;
+    if (!cluster) {
+        const cudaError_t e = cudaMemsetAsync(counts, 0, 64 * sizeof(unsigned int), s);
+        if (e != cudaSuccess) return e;
+    }
+    return persist(true, cluster, shape, a.model, &a, n_tiles, n_steps, counts, packed, smem_bytes, s, nullptr);
 }
 
-cudaError_t step_persist_prepare(const StagedShape &shape, int model, bool packed, size_t smem_bytes, int *ctas_per_sm)
+cudaError_t step_persist_prepare(const StagedShape &shape, int model, bool packed, bool cluster, int n_tiles,
+                                 size_t smem_bytes, int *fits)
 {
-    return persist(false, shape, model, nullptr, 0, 0, nullptr, packed, smem_bytes, nullptr, ctas_per_sm);
+    if (cluster && (n_tiles < 1 || n_tiles > kMaxClusterTiles)) return cudaErrorInvalidValue;
+    return persist(false, cluster, shape, model, nullptr, n_tiles, 0, nullptr, packed, smem_bytes, nullptr, fits);
 }
 
 cudaError_t launch_batch_lanes(int model, const StepArgs *nets, const int *tile_net, const int2 *groups, int n_groups,

@@ -86,6 +86,7 @@ struct gn_net {
     int st_max_u = 0, st_max_x = 0, st_max_p = 0;
     bool st_early = false;  // gathers before the grid wait (see staged_tile)
     size_t ps_smem = 0;                   // kind 5 (persistent staged tiles): shared memory per CTA
+    bool ps_cluster = false;              // ... the grid is one thread-block cluster (at most 16 tiles)
     DevArray<unsigned int> ps_counts;     // ... and its step barrier (64 words)
     DevArray<int4> st_tile, st_tile2;
     DevArray<uint32_t> st_ukey;
@@ -260,9 +261,28 @@ bool set_persist(gn_net *net, int shape)
     int max_smem = 0, per_sm = 0, sms = 0;
     cuda_check(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, net->device), "device query");
     if (smem > static_cast<size_t>(max_smem)) return false;
-    cuda_check(gn::step_persist_prepare(sh, net->model, net->packed, smem, &per_sm), "persistent kernel setup");
-    cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, net->device), "device query");
-    if (static_cast<int64_t>(net->n_tiles) > static_cast<int64_t>(per_sm) * sms) return false;
+    // a net of at most kMaxClusterTiles tiles runs as one cluster (GN_PERSIST_CLUSTER=0 turns that off)
+    net->ps_cluster = false;
+    const char *ce = getenv("GN_PERSIST_CLUSTER");
+    if (net->n_tiles <= gn::kMaxClusterTiles && !(ce && *ce == '0')) {
+        int clusters = 0;
+        const cudaError_t e =
+            gn::step_persist_prepare(sh, net->model, net->packed, true, net->n_tiles, smem, &clusters);
+        if (e == cudaSuccess && clusters >= 1) net->ps_cluster = true;
+        else cudaGetLastError();
+        if (const char *log = getenv("GN_PERSIST_LOG"))
+            if (FILE *f = fopen(log, "a")) {
+                fprintf(f, "persistent shape %d tiles %d smem %zu: cluster query %s, %d clusters\n", shape,
+                        net->n_tiles, smem, cudaGetErrorString(e), clusters);
+                fclose(f);
+            }
+    }
+    if (!net->ps_cluster) {
+        cuda_check(gn::step_persist_prepare(sh, net->model, net->packed, false, net->n_tiles, smem, &per_sm),
+                   "persistent kernel setup");
+        cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, net->device), "device query");
+        if (static_cast<int64_t>(net->n_tiles) > static_cast<int64_t>(per_sm) * sms) return false;
+    }
     if (!net->ps_counts.p) net->ps_counts.alloc(64, &net->bytes);
     net->ps_smem = smem;
     return true;
@@ -382,7 +402,7 @@ bool tune_cache_lookup(const std::string &key, int *kind, int *shape)
     bool found = false;
     while (fscanf(f, "%255s %d %d", k, &a, &b) == 3)
         if (key == k && b >= 0 &&
-            (((a == 1 || a == 2) && b < gn::kNumStepShapes) || (a == 3 && b < gn::kNumStagedShapes) ||
+            (((a == 1 || a == 2) && b < gn::kNumStepShapes) || ((a == 3 || a == 5) && b < gn::kNumStagedShapes) ||
              (a == 4 && b < gn::kNumResidentShapes))) {
             *kind = a;
             *shape = b;
@@ -501,34 +521,49 @@ void autotune(gn_net *net)
             a.rp = rp.p;
             a.hh_g = hh_g.p;
             a.obs_acc = obs_acc.p;
-            const int warm = 3, timed = 24;  // near ties between shapes need more than a few steps
-            // the resident kernel runs many steps per launch: one launch of kResidentSteps x
-            // timed steps, its time scaled to `timed` steps
+            // each candidate is timed as gn_step runs it: kernels 1 to 3 as a captured graph
+            // of kGraphSteps step launches (replayed once untimed, then timed), the resident
+            // kernel as one launch of kResidentSteps x kGraphSteps steps, the persistent
+            // kernel as one launch of kGraphSteps steps (each after an untimed launch)
+            const int timed = kGraphSteps;
             constexpr int kResidentSteps = 8;
+            cudaGraphExec_t ge = nullptr;
             if (c.kind == 4) {
                 cuda_check(gn::launch_resident(a, net->res, kResidentSteps, c.shape, net->stream), "autotune launch");
             } else if (c.kind == 5) {
-                cuda_check(gn::launch_step_persist(a, net->n_tiles, warm, gn::kStagedShapes[c.shape], net->packed,
-                                                   net->ps_counts.p, net->ps_smem, net->stream),
+                cuda_check(gn::launch_step_persist(a, net->n_tiles, 3, gn::kStagedShapes[c.shape], net->packed,
+                                                   net->ps_cluster, net->ps_counts.p, net->ps_smem, net->stream),
                            "autotune launch");
             } else {
-                for (int k = 0; k < warm; ++k)
-                    cuda_check(launch_kind(a, net, k, net->stream), "autotune launch");
+                cudaStream_t cs = nullptr;
+                cuda_check(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "cudaStreamCreate");
+                cudaGraph_t g = nullptr;
+                cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+                for (int k = 0; k < timed && e == cudaSuccess; ++k) e = launch_kind(a, net, k, cs);
+                const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+                if (e == cudaSuccess) e = e2;
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+                if (g) cudaGraphDestroy(g);
+                cudaStreamDestroy(cs);
+                cuda_check(e, "autotune graph capture");
+                e = cudaGraphLaunch(ge, net->stream);  // untimed
+                if (e != cudaSuccess) cudaGraphExecDestroy(ge);
+                cuda_check(e, "autotune launch");
             }
-            cuda_check(cudaEventRecord(t0, net->stream), "event");
-            if (c.kind == 4) {
-                cuda_check(gn::launch_resident(a, net->res, kResidentSteps * timed, c.shape, net->stream),
-                           "autotune launch");
-            } else if (c.kind == 5) {
-                cuda_check(gn::launch_step_persist(a, net->n_tiles, timed, gn::kStagedShapes[c.shape], net->packed,
-                                                   net->ps_counts.p, net->ps_smem, net->stream),
-                           "autotune launch");
-            } else {
-                for (int k = 0; k < timed; ++k)
-                    cuda_check(launch_kind(a, net, k, net->stream), "autotune launch");
+            cudaError_t te = cudaEventRecord(t0, net->stream);
+            if (te == cudaSuccess) {
+                if (c.kind == 4)
+                    te = gn::launch_resident(a, net->res, kResidentSteps * timed, c.shape, net->stream);
+                else if (c.kind == 5)
+                    te = gn::launch_step_persist(a, net->n_tiles, timed, gn::kStagedShapes[c.shape], net->packed,
+                                                 net->ps_cluster, net->ps_counts.p, net->ps_smem, net->stream);
+                else
+                    te = cudaGraphLaunch(ge, net->stream);
             }
-            cuda_check(cudaEventRecord(t1, net->stream), "event");
-            cuda_check(cudaEventSynchronize(t1), "autotune");
+            if (te == cudaSuccess) te = cudaEventRecord(t1, net->stream);
+            if (te == cudaSuccess) te = cudaEventSynchronize(t1);
+            if (ge) cudaGraphExecDestroy(ge);
+            cuda_check(te, "autotune");
             float ms = 0.0f;
             cuda_check(cudaEventElapsedTime(&ms, t0, t1), "event");
             if (c.kind == 4) ms /= kResidentSteps;
@@ -844,6 +879,7 @@ gn_status gn_net_get_info(const gn_net *net, gn_net_info *info)
         info->step_gathers = staged ? net->st_gathers : net->E;
         info->step_entries = staged ? net->st_entries : net->E;
         info->step_lane_slots = staged ? net->st_slots : 0;
+        info->step_cluster = net->step_kernel == 5 && net->ps_cluster ? 1 : 0;
     });
 }
 
@@ -908,7 +944,8 @@ gn_status gn_step(gn_net *net, int64_t n_steps)
             for (int64_t left = n_steps; left > 0; left -= kPersistChunk) {
                 const int chunk = static_cast<int>(std::min(left, kPersistChunk));
                 cuda_check(gn::launch_step_persist(net->args, net->n_tiles, chunk, gn::kStagedShapes[net->shape],
-                                                   net->packed, net->ps_counts.p, net->ps_smem, net->stream),
+                                                   net->packed, net->ps_cluster, net->ps_counts.p, net->ps_smem,
+                                                   net->stream),
                            "persistent launch");
                 cuda_check(gn::launch_advance(net->d_step.p, chunk, net->stream), "advance launch");
             }

@@ -89,6 +89,7 @@ class gn_net_info(C.Structure):
         ("step", C.c_int64), ("samples", C.c_int64),
         ("v_rest", C.c_double), ("w_rest", C.c_double), ("device_bytes", C.c_size_t),
         ("step_gathers", C.c_int64), ("step_entries", C.c_int64), ("step_lane_slots", C.c_int64),
+        ("step_cluster", C.c_int32),
     ]
 
 
