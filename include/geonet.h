@@ -175,10 +175,10 @@ typedef struct {
                                     in shared memory for the whole launch, the CTAs meeting at a counting
                                     barrier in global memory between steps; 4 and 5 fail with GN_EINVAL
                                     if the network does not fit (5: every tile's CTA resident at once),
-                                    and neither takes plastic weights.  Kernel 3 on a large
-                                    FitzHugh-Nagumo net fetches its history values (all written two
-                                    or more steps back) before it waits for the previous step;
-                                    GN_STAGED_EARLY=0 makes it wait first */
+                                    and neither takes plastic weights.  Kernel 3 with static weights
+                                    fetches its history values (all written two or more steps back)
+                                    before it waits for the previous step; GN_STAGED_EARLY=0 makes it
+                                    wait first */
     void *cuda_stream;           /* cudaStream_t to run on; NULL: the library makes its own */
     int32_t device;              /* CUDA device ordinal */
     int32_t model;               /* GN_MODEL_FHN (0), GN_MODEL_IZH (1) or GN_MODEL_HH (2) */

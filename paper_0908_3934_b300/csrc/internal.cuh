@@ -178,10 +178,12 @@ struct StagedShape {
     int threads, ucap, ecap, pcap, stage_entries;
 };
 extern const StagedShape kStagedShapes[kNumStagedShapes];
-// early: gather before the grid wait (FitzHugh-Nagumo, a grid larger than the
-// CTAs the device holds at once -- see staged_tile)
+// early: 0 gather after the grid wait; 1 gather before it and let the next grid start
+// at once (a grid larger than the CTAs the device holds at once); 2 gather before it
+// and let the next grid start after the CTA's own wait (any grid) -- see staged_tile;
+// static weights only for 1 and 2
 cudaError_t launch_step_staged(const StepArgs &a, int n_tiles, int k, const StagedShape &shape, bool packed,
-                               bool stream_edges, size_t smem_bytes, bool early, cudaStream_t s);
+                               bool stream_edges, size_t smem_bytes, int early, cudaStream_t s);
 cudaError_t step_staged_prepare(const StagedShape &shape, int model, bool plastic, bool packed, bool stream_edges,
                                 size_t smem_bytes, int *ctas_per_sm);
 // persistent staged step of one network (kind 5): one cooperative launch of one CTA

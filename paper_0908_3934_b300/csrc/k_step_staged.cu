@@ -11,12 +11,11 @@
 //      kernel that gathers early (kEarly) does this and step 2 before it waits for
 //      the previous step (griddepcontrol.wait), just before step 3, when step n - 1
 //      is complete; the gathers of one step then overlap the end of the previous
-//      one.  Batches always gather early; a single static network does so when its
-//      grid outnumbers the CTAs the device holds at once.  Such a large grid lets
-//      the next step start first thing (kLaunchFirst: its first CTAs only fill the
-//      SMs this grid's last wave leaves free); a smaller early batch grid does so
-//      just before step 3.  Plastic networks and small single-network grids let
-//      the next step start at once and wait before step 1.
+//      one.  Every network with static weights gathers early.  A grid that
+//      outnumbers the CTAs the device holds at once lets the next step start first
+//      thing (kLaunchFirst: its first CTAs only fill the SMs this grid's last wave
+//      leaves free); a smaller grid does so just before step 3, after its wait.
+//      Plastic networks let the next step start at once and wait before step 1.
 //      The gathers are sorted by (D, src), so a warp's 32 reads fall in a few lines
 //      of one ring slot.  While they are in flight, a spiking node (Izhikevich,
 //      Hodgkin-Huxley) runs every part of its update that does not read S -- all
@@ -297,13 +296,16 @@ __device__ __forceinline__ bool staged_tile(const StepArgs &a, const int tile, c
     return true;
 }
 
-template <int kM, int T, bool kSE, bool kPacked, bool kStream, bool kEarly>
+// kMode: 0 gathers after the grid wait (the next grid starts at once); 1 gathers
+// early and lets the next grid start at once (a grid larger than the device holds);
+// 2 gathers early and lets the next grid start only after its own wait (any grid)
+template <int kM, int T, bool kSE, bool kPacked, bool kStream, int kMode>
 __global__ void __launch_bounds__(T, (kSE ? kThreadsSE : (kM & kPlastic) ? kThreadsPlastic : kThreadsL2) / T)
     k_step_staged(const StepArgs a, const int k)
 {
     PdlWait w;
     uint32_t phase = 0;
-    staged_tile<kM, T, kSE, kPacked, kStream, kEarly, true>(a, blockIdx.x, k, w, phase);
+    staged_tile<kM, T, kSE, kPacked, kStream, kMode != 0, kMode != 2>(a, blockIdx.x, k, w, phase);
 }
 
 // Batched form, one launch per step over the tiles of every member network (all of
@@ -603,7 +605,7 @@ __global__ void __launch_bounds__(T, 1)
     }
 }
 
-template <int kM, int T, bool kSE, bool kPacked, bool kStream, bool kEarly>
+template <int kM, int T, bool kSE, bool kPacked, bool kStream, int kMode>
 cudaError_t launch_t(const StepArgs &a, int n_tiles, int k, size_t smem, cudaStream_t s)
 {
     cudaLaunchConfig_t cfg = {};
@@ -616,32 +618,32 @@ cudaError_t launch_t(const StepArgs &a, int n_tiles, int k, size_t smem, cudaStr
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_step_staged<kM, T, kSE, kPacked, kStream, kEarly>, a, k);
+    return cudaLaunchKernelEx(&cfg, k_step_staged<kM, T, kSE, kPacked, kStream, kMode>, a, k);
 }
 
 // One kernel instance: launch it, or (launch false) raise its dynamic shared-memory
 // limit and report how many of its CTAs an SM holds.
-template <int kM, int T, bool kSE, bool kPacked, bool kStream, bool kEarly>
+template <int kM, int T, bool kSE, bool kPacked, bool kStream, int kMode>
 cudaError_t instance(bool launch, const StepArgs *a, int n_tiles, int k, size_t smem, cudaStream_t s, int *per_sm)
 {
-    if (launch) return launch_t<kM, T, kSE, kPacked, kStream, kEarly>(*a, n_tiles, k, smem, s);
-    auto *fn = k_step_staged<kM, T, kSE, kPacked, kStream, kEarly>;
+    if (launch) return launch_t<kM, T, kSE, kPacked, kStream, kMode>(*a, n_tiles, k, smem, s);
+    auto *fn = k_step_staged<kM, T, kSE, kPacked, kStream, kMode>;
     const cudaError_t e =
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess || !per_sm) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, T, smem);
 }
 
-// The kernel instance of a shape, edge format and gather order.
+// The kernel instance of a shape, edge format and gather order (mode: see k_step_staged).
 template <int kM, int T, bool kSE>
-cudaError_t dispatch_fmt(bool launch, bool early, const StepArgs *a, int n_tiles, int k, bool packed,
+cudaError_t dispatch_fmt(bool launch, int mode, const StepArgs *a, int n_tiles, int k, bool packed,
                          bool stream_edges, size_t smem, cudaStream_t s, int *per_sm)
 {
     if constexpr ((kM & kPlastic) != 0 && kSE) {
         return cudaErrorInvalidValue;  // plastic weights: entries are read from global memory
     } else {
         auto go = [&](auto e) -> cudaError_t {
-            constexpr bool E = decltype(e)::value;
+            constexpr int E = decltype(e)::value;
             if (packed)
                 return stream_edges ? instance<kM, T, kSE, true, true, E>(launch, a, n_tiles, k, smem, s, per_sm)
                                     : instance<kM, T, kSE, true, false, E>(launch, a, n_tiles, k, smem, s, per_sm);
@@ -649,20 +651,22 @@ cudaError_t dispatch_fmt(bool launch, bool early, const StepArgs *a, int n_tiles
                                 : instance<kM, T, kSE, false, false, E>(launch, a, n_tiles, k, smem, s, per_sm);
         };
         if constexpr ((kM & kPlastic) == 0) {
-            if (!launch) {  // both gather orders may be launched
-                const cudaError_t e = go(std::true_type{});
+            if (!launch) {  // every gather order may be launched
+                cudaError_t e = go(std::integral_constant<int, 1>{});
+                if (e == cudaSuccess) e = go(std::integral_constant<int, 2>{});
                 if (e != cudaSuccess) return e;
-                return go(std::false_type{});
+                return go(std::integral_constant<int, 0>{});
             }
-            if (early) return go(std::true_type{});
-        } else if (early) {
+            if (mode == 1) return go(std::integral_constant<int, 1>{});
+            if (mode == 2) return go(std::integral_constant<int, 2>{});
+        } else if (mode != 0) {
             return cudaErrorInvalidValue;
         }
-        return go(std::false_type{});
+        return go(std::integral_constant<int, 0>{});
     }
 }
 
-cudaError_t dispatch(bool launch, const StagedShape &sh, int model, bool plastic, bool early, const StepArgs *a,
+cudaError_t dispatch(bool launch, const StagedShape &sh, int model, bool plastic, int early, const StepArgs *a,
                      int n_tiles, int k, bool packed, bool stream_edges, size_t smem, cudaStream_t s, int *per_sm)
 {
     const bool se = sh.stage_entries != 0;
@@ -699,7 +703,7 @@ const StagedShape kStagedShapes[kNumStagedShapes] = {
     {128, 4096, 8192, 1024, 1}};
 
 cudaError_t launch_step_staged(const StepArgs &a, int n_tiles, int k, const StagedShape &shape, bool packed,
-                               bool stream_edges, size_t smem_bytes, bool early, cudaStream_t s)
+                               bool stream_edges, size_t smem_bytes, int early, cudaStream_t s)
 {
     if (n_tiles <= 0) return cudaSuccess;
     return dispatch(true, shape, a.model, a.stdp != 0, early, &a, n_tiles, k, packed, stream_edges, smem_bytes, s,
@@ -709,7 +713,7 @@ cudaError_t launch_step_staged(const StepArgs &a, int n_tiles, int k, const Stag
 cudaError_t step_staged_prepare(const StagedShape &shape, int model, bool plastic, bool packed, bool stream_edges,
                                 size_t smem_bytes, int *ctas_per_sm)
 {
-    return dispatch(false, shape, model, plastic, false, nullptr, 0, 0, packed, stream_edges, smem_bytes, nullptr,
+    return dispatch(false, shape, model, plastic, 0, nullptr, 0, 0, packed, stream_edges, smem_bytes, nullptr,
                     ctas_per_sm);
 }
 

@@ -330,6 +330,46 @@ def test_early_gathers_give_the_same_bits(monkeypatch, model):
     assert_windows(worst)
 
 
+@pytest.mark.parametrize("model", ["fhn", "izh", "hh"])
+def test_small_grid_early_gathers_give_the_same_bits(monkeypatch, model):
+    """A staged grid the device holds at once gathers before its grid wait too, the
+    next grid starting only after each CTA's own wait (so step n - 2 is complete when
+    step n gathers); at the tightest slot reuse -- a 4-slot ring, delays of 1 or 2 steps
+    -- 1500 steps in uneven launches equal those of the same kernel waiting first, bit
+    for bit, and the first 60 steps equal the oracle's window by window (FHN)."""
+    from parity import windowed_izh
+    base = netgen.large(n=6000, mean_deg=20.0, bg_rate_hz=100.0, seed=23)
+    rng = np.random.default_rng(29)
+    base.delay = rng.integers(1, 3, base.n_edges).astype(np.int32)
+    base.ring_depth = 4
+    spec = {"fhn": base, "izh": netgen.izhikevich(base), "hh": netgen.hodgkin_huxley(base)}[model]
+    monkeypatch.setenv("GN_STEP_SHAPE", "0")
+    out = []
+    for early in ("", "0"):
+        if early:
+            monkeypatch.setenv("GN_STAGED_EARLY", early)
+        else:
+            monkeypatch.delenv("GN_STAGED_EARLY", raising=False)
+        net = Net(spec, step_kernel=3)
+        assert 1 < net.gn_net_get_info()["n_blocks"] < 148
+        for c in (1, 499, 1000):
+            net.gn_step(c)
+        extra = net.gn_get_izh_state() if model != "fhn" else {}
+        out.append((net.gn_get_state(), net.gn_get_history(3), net.gn_get_events(), extra, net.gn_get_arrivals()))
+    (sa, ha, ea, xa, fa), (sb, hb, eb, xb, fb) = out
+    assert np.abs(sa["v"]).max() > 0.1 or len(ea[0]) > 0
+    for k in ("v", "w", "c", "bg_count"):
+        assert np.array_equal(sa[k], sb[k]), k
+    for k in xa:
+        assert np.array_equal(xa[k], xb[k]), k
+    assert np.array_equal(ha, hb) and np.array_equal(fa, fb)
+    assert np.array_equal(ea[0], eb[0]) and np.array_equal(ea[1], eb[1])
+    if model == "fhn":
+        monkeypatch.delenv("GN_STAGED_EARLY", raising=False)
+        worst, _ = windowed(spec, Net(spec, step_kernel=3), 60)
+        assert_windows(worst)
+
+
 def test_staged_kernel_refuses_a_row_beyond_shared_memory():
     """One target with 70,000 distinct (source, delay) reads needs more shared memory
     than a CTA may have: the staged kernel is refused with GN_EINVAL, while the
