@@ -332,20 +332,18 @@ __global__ void __launch_bounds__(T, kThreadsL2 / T) k_batch_staged(const StepAr
 // CTAs); a lane runs its groups one after another (groups g = lane, lane + lanes,
 // ...), each through all the steps, so a group's data stays in L2 across them.
 // A lane's CTAs meet at a counting barrier in global memory (the lane's arrival
-// count, on a 128-byte line of its own).  After its tiles' node updates of the
-// lane's j-th step (counted over its groups) a CTA adds 1 to the count; its node
-// updates of step j wait until the count reaches j C, i.e. until step j - 1 is
-// complete in the whole lane (slot n + 1, which step n writes, is read by step
-// n - 1's longest delay).
-// Its gathers do not wait: they read history slots n - D, D >= 1, written by step
-// n - 2 or earlier, which the CTA's own wait in step n - 1 covered -- the argument
-// of the early gathers in a chain of launches.  A CTA without a tile in a step
-// still waits for step j - 1 before it arrives, so no CTA is two arrivals ahead of
-// another and a count of (j + 1) C can only mean that every CTA has arrived for step
-// j.  Memory order: the add is a release reduction (no reply awaited) after a CTA
-// barrier; waits poll with relaxed loads and fence once the count is seen (acquire).
-// Waits are
-// bounded: after `limit` polls, or once another CTA has set kStatusTimeout, the
+// count, on a line of its own).  After its tiles' node updates of the lane's j-th
+// step (counted over its groups) a CTA adds 1 to the count; its node updates of step
+// j wait until the count reaches j C, i.e. until step j - 1 is complete in the whole
+// lane (slot n + 1, which step n writes, is read by step n - 1's longest delay).  Its
+// gathers do not wait: they read history slots n - D, D >= 1, written by step n - 2
+// or earlier, which the CTA's own wait in step n - 1 covered -- the argument of the
+// early gathers in a chain of launches.  A CTA without a tile in a step still waits
+// for step j - 1 before it arrives, so no CTA is two arrivals ahead of another and a
+// count of (j + 1) C can only mean that every CTA has arrived for step j.  Memory
+// order: the add is a release reduction (no reply awaited) after a CTA barrier;
+// waits poll with relaxed loads and fence once the count is seen (acquire).  Waits
+// are bounded: after `limit` polls, or once another CTA has set kStatusTimeout, the
 // CTA gives up and returns.
 __device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
