@@ -173,7 +173,7 @@ cudaError_t launch_advance(int64_t *d_step, int64_t by, cudaStream_t s);
 // stage_entries: 1 copies a tile's edge entries into shared memory with its gather
 // keys; 0 keeps only the keys there and prefetches the entries into L2 (less
 // shared memory per CTA, more CTAs per SM)
-constexpr int kNumStagedShapes = 7;
+constexpr int kNumStagedShapes = 8;
 struct StagedShape {
     int threads, ucap, ecap, pcap, stage_entries;
 };

@@ -693,11 +693,12 @@ cudaError_t dispatch(bool launch, const StagedShape &sh, int model, bool plastic
 // 0.1392 with shape 4, 0.1126 with shape 5, which larger caps leave unchanged).  The
 // last holds 1024 pieces, 32 rows of over kWarpRow edges (32 pieces each) per tile
 // where the others stop at 8 or 16: at in-degree 100 (the 100k-node net) its tiles
-// stop cutting short, 0.0336 ms per step against 0.0393 for the next shape.
+// stop cutting short, 0.0336 ms per step against 0.0393 for the next shape; the last,
+// 2048 pieces in 256-thread tiles, 0.0311.
 const StagedShape kStagedShapes[kNumStagedShapes] = {
     {128, 3072, 4096, 256, 1}, {128, 3072, 4096, 256, 0}, {256, 6144, 8192, 512, 1},
     {256, 6144, 8192, 512, 0}, {256, 8192, 12288, 512, 0}, {256, 10240, 16384, 512, 0},
-    {128, 4096, 8192, 1024, 1}};
+    {128, 4096, 8192, 1024, 1}, {256, 8192, 16384, 2048, 0}};
 
 cudaError_t launch_step_staged(const StepArgs &a, int n_tiles, int k, const StagedShape &shape, bool packed,
                                bool stream_edges, size_t smem_bytes, int early, cudaStream_t s)

@@ -51,7 +51,7 @@ def test_mixed_multi_block_net_windows(step_kernel):
 def test_every_kernel_and_shape_gives_the_same_bits(monkeypatch):
     spec = netgen.mixed_cells(netgen.izhikevich(netgen.roofline(seed=21, n=20000, bg_rate_hz=100.0)), seed=7)
     ref = None
-    for kind, shape in [(1, s) for s in range(5)] + [(2, 0)] + [(3, s) for s in range(7)]:
+    for kind, shape in [(1, s) for s in range(5)] + [(2, 0)] + [(3, s) for s in range(8)]:
         monkeypatch.setenv("GN_STEP_SHAPE", str(shape))
         net = geonet.Net(spec, step_kernel=kind)
         net.gn_step(600)

@@ -57,7 +57,7 @@ def test_every_kernel_and_shape_gives_the_same_bits(monkeypatch):
     spec = netgen.hodgkin_huxley(netgen.roofline(seed=21, n=20000, bg_rate_hz=100.0))
     ref = None
     persistent = 0
-    for kind, shape in [(1, s) for s in range(5)] + [(2, 0)] + [(3, s) for s in range(7)] + [(5, s) for s in range(7)]:
+    for kind, shape in [(1, s) for s in range(5)] + [(2, 0)] + [(3, s) for s in range(8)] + [(5, s) for s in range(8)]:
         monkeypatch.setenv("GN_STEP_SHAPE", str(shape))
         try:
             net = geonet.Net(spec, step_kernel=kind)

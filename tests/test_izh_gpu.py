@@ -52,7 +52,7 @@ def test_every_kernel_and_shape_gives_the_same_bits(monkeypatch):
     CTA shape reaches bit-identical Izhikevich states (hubs of in-degree 1000)."""
     spec = netgen.izhikevich(netgen.roofline(seed=21, n=20000, bg_rate_hz=100.0))
     ref = None
-    for kind, shape in [(1, s) for s in range(5)] + [(2, 0)] + [(3, s) for s in range(7)]:
+    for kind, shape in [(1, s) for s in range(5)] + [(2, 0)] + [(3, s) for s in range(8)]:
         monkeypatch.setenv("GN_STEP_SHAPE", str(shape))
         net = geonet.Net(spec, step_kernel=kind)
         net.gn_step(600)

@@ -243,7 +243,7 @@ def test_every_kernel_and_shape_gives_the_same_bits(monkeypatch):
     hubs of in-degree 1000 and 100 Hz background, 300 steps from rest."""
     spec = netgen.roofline(seed=21, n=20000, bg_rate_hz=100.0)
     ref = None
-    cases = [(1, s) for s in range(5)] + [(2, 0)] + [(3, s) for s in range(7)] + [(5, s) for s in range(7)]
+    cases = [(1, s) for s in range(5)] + [(2, 0)] + [(3, s) for s in range(8)] + [(5, s) for s in range(8)]
     persistent = 0
     for kind, shape in cases:
         monkeypatch.setenv("GN_STEP_SHAPE", str(shape))
